@@ -1,0 +1,169 @@
+/*
+ * vj.h -- C ABI of the B300 vector epsilon-join library (libvj.so).
+ *
+ * The operation (Def. 1 of "Fast Approximate Vector Joins via Offline-Online
+ * Co-Design", arXiv 2603.16360): given data vectors X and query vectors Q in
+ * R^d, a distance dist(.,.) and a threshold eps, return for every query q the
+ * data vectors x with dist(x, q) < eps (strict).  The approximate join walks a
+ * merged proximity graph built over X U Q (Sec. 4.3, "merged index"), with soft
+ * work sharing between nearby queries (Sec. 4.2, Alg. 8) and the OOD-adaptive
+ * hybrid expansion (Sec. 4.4, Alg. 6-7).  The exact join is the nested-loop
+ * join of Sec. 3.2.
+ *
+ * Naming: the paper calls the query set X and the data set Y; this ABI calls
+ * the data set X and the query set Q.  Merged node ids: data 0..nx-1, queries
+ * nx..nx+nq-1.
+ *
+ * Conventions for every call:
+ *  - Return value: VJ_OK or an error code; on error vj_last_error() returns a
+ *    thread-local, NUL-terminated message that stays valid until the next call
+ *    on the same thread.  No call exits, traps or throws across the ABI.
+ *  - Ownership: input buffers stay owned by the caller and are not retained
+ *    (vj_build copies them into device memory).  vj_index / vj_result objects
+ *    are owned by the library until the matching *_free call.
+ *  - Device: every call uses the CUDA device current on the calling thread at
+ *    vj_build time; all work runs on the index's stream (vj_set_stream).
+ *  - Threads: an index may be used by one thread at a time.
+ */
+#ifndef VJ_H
+#define VJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VJ_OK = 0,
+    VJ_ERR_ARG = 1,     /* invalid argument (null pointer, size, mode) */
+    VJ_ERR_OOM = 2,     /* device or host allocation failed */
+    VJ_ERR_CUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    VJ_ERR_TIMEOUT = 4, /* a bounded device wait gave up (see vj_last_error) */
+    VJ_ERR_STATE = 5    /* capacity exceeded or object in the wrong state */
+} vj_status;
+
+typedef enum {
+    VJ_L2 = 0,    /* dist = sqrt(sum (x_i - q_i)^2) */
+    VJ_COSINE = 1 /* dist = 1 - <x,q> / (|x| |q|) */
+} vj_metric;
+
+/* cfg.work_sharing of Tab. cfg (Sec. 4.1).  Under the merged index, SOFT also
+ * seeds the query node itself (S = {entry, q} U C[parent]); SELF is the
+ * paper's default merged mode (S = {entry, q}). */
+enum { VJ_WS_NONE = 0, VJ_WS_HARD = 1, VJ_WS_SOFT = 2, VJ_WS_SELF = 3 };
+
+enum { VJ_PREC_FP32 = 0, VJ_PREC_BF16 = 1, VJ_PREC_FP8 = 2 };
+
+/* Build and join parameters (Tab. cfg plus build knobs). */
+typedef struct {
+    int degree;           /* graph out-degree R (1..32), default 32 */
+    int knn_k;            /* kNN candidates per node for the build, R <= K <= 112; default 64 */
+    int greedy_beam;      /* cfg.greedy_beam_size, default 256 (Alg. 4) */
+    int conv_threshold;   /* cfg.conv_threshold, default 10 (Alg. 5) */
+    int hybrid_beam;      /* cfg.hybrid_beam_size, default 256 (Alg. 7) */
+    int work_sharing;     /* VJ_WS_*, default VJ_WS_SOFT (MI+SWS) */
+    int adapt_hybrid;     /* cfg.adapt_hybrid (Alg. 6), default 1 */
+    int force_hybrid;     /* cfg.force_hybrid (Alg. 6), default 0 */
+    int precision;        /* VJ_PREC_* of the build's distance tiles, default FP32 */
+    int learned;          /* reserved, must be 0 */
+    int route_bruteforce; /* reserved, must be 0 */
+    int input_on_device;  /* 1: X and Q passed to vj_build are device pointers */
+    uint64_t seed;        /* reserved for randomised steps; recorded only */
+} vj_params;
+
+/* Per-call counters and device timings of a join. */
+typedef struct {
+    int64_t dist_computations; /* "steps" of Sec. 5.3: distance evaluations */
+    int64_t expansions;        /* nodes popped in the expansion phase */
+    int64_t adj_rows_read;     /* adjacency rows read (probe + expansions + OOD) */
+    int64_t hybrid_queries;    /* queries that ran the hybrid expansion */
+    int64_t rechecks;          /* FP64 re-evaluations near eps or near ties */
+    int64_t spill_queries;     /* queries whose visited set left shared memory */
+    double ms_traverse;        /* device time of the traversal kernel */
+    double ms_csr;             /* device time of the CSR assembly */
+    double ms_total;           /* device time of the whole join */
+    int64_t bytes_algorithmic; /* vector + adjacency bytes the traversal must read */
+    int64_t kernel_launches;   /* kernels this call launched */
+} vj_stats;
+
+/* CSR result of a join.  ids are data ids (0..nx-1), ascending within each
+ * query row; dists are the pair distances.  steps/cache/hybrid are per-query
+ * (query index order): distance evaluations, the soft cache C[q] of Alg. 8
+ * (closest visited data node, -1 if none) and the CheckHybrid outcome.
+ * When on_device is 1 every array is a device pointer. */
+typedef struct {
+    int64_t nq;
+    int64_t nnz;
+    int64_t *offsets; /* [nq + 1] */
+    int32_t *ids;     /* [nnz] */
+    float *dists;     /* [nnz] */
+    int32_t *steps;   /* [nq] */
+    int32_t *cache;   /* [nq] */
+    uint8_t *hybrid;  /* [nq] */
+    int on_device;
+    vj_stats stats;
+} vj_result;
+
+typedef struct vj_index vj_index;
+
+/* Fill *p with the defaults listed above. */
+void vj_default_params(vj_params *p);
+
+/* Offline merged-index build (Sec. 4.3; the paper's index is NSG, a black
+ * box; this library builds an exact kNN graph of X U Q, RNG-prunes it to R
+ * (App. C rule), adds reverse edges, picks the entry nearest the centroid,
+ * stores data-edge lengths and the MST order over queries of Alg. 2).
+ *   X: nx*d row-major float32, Q: nq*d row-major float32 (host pointers, or
+ *   device pointers when p->input_on_device).  nx >= 1, nq >= 1, 1 <= d <= 4096,
+ *   nx + nq < 2^31.  p may be NULL (defaults).
+ * Errors: VJ_ERR_ARG, VJ_ERR_OOM, VJ_ERR_CUDA.  *out is NULL on error. */
+vj_status vj_build(const float *X, int64_t nx, const float *Q, int64_t nq, int d,
+                   vj_metric metric, const vj_params *p, vj_index **out);
+
+/* Run all further work of this index on `stream` (a cudaStream_t; NULL =
+ * the legacy default stream). */
+vj_status vj_set_stream(vj_index *ix, void *stream);
+
+/* Replace the join-time fields (greedy_beam, conv_threshold, hybrid_beam,
+ * work_sharing, adapt_hybrid, force_hybrid) used by later joins. */
+vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
+
+/* Approximate join (Alg. 1 on the merged index) at threshold eps > 0.
+ * budget > 0 overrides hybrid_beam for this call.  The result lives in host
+ * memory (the device->host copy is part of the call).
+ * Errors: VJ_ERR_ARG, VJ_ERR_OOM, VJ_ERR_CUDA, VJ_ERR_TIMEOUT (a work-sharing
+ * dependency wait ran out; the index stays usable). */
+vj_status vj_join(vj_index *ix, float eps, int budget, vj_result **out);
+
+/* As vj_join, but the result arrays stay in device memory (on_device = 1). */
+vj_status vj_join_device(vj_index *ix, float eps, int budget, vj_result **out);
+
+/* Exact nested-loop join (Sec. 3.2) of the index's X and Q on the GPU, host
+ * result.  Pairs whose FP32 distance lies within the FP32 rounding bound of
+ * eps are re-decided in FP64. */
+vj_status vj_join_exact(vj_index *ix, float eps, vj_result **out);
+
+/* Copy the built graph to host buffers (any may be NULL):
+ *   adj [(nx+nq) * R] int32 (-1 padded), entry (1 value),
+ *   parent [nq] (MST parent query index, -1 = entry), order [nq]
+ *   (processing order), depth [nq] (MST depth, entry = 0). */
+vj_status vj_export_graph(const vj_index *ix, int32_t *adj, int32_t *entry, int32_t *parent,
+                          int32_t *order, int32_t *depth);
+
+/* Copy the exact kNN lists computed by the build: ids [(nx+nq) * K] and
+ * dists [(nx+nq) * K] (ascending by (dist, id)). */
+vj_status vj_export_knn(const vj_index *ix, int32_t *ids, float *dists);
+
+/* Shape of an index: any pointer may be NULL. */
+vj_status vj_index_info(const vj_index *ix, int64_t *nx, int64_t *nq, int *d, int *degree,
+                        int *knn_k, int *max_depth);
+
+void vj_result_free(vj_result *r);
+void vj_free(vj_index *ix);
+const char *vj_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VJ_H */

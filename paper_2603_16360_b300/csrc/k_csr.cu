@@ -1,0 +1,199 @@
+// k_csr.cu -- result assembly: exclusive scan of per-query counts into CSR
+// offsets, and a per-query copy of each query's pairs from the unordered
+// result pool into its CSR row, sorted by data id.
+#include "vj_device.cuh"
+#include "vj_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_T = 1024;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
+
+// block-level inclusive scan of one value per thread (int64)
+__device__ int64_t block_scan_incl(int64_t v, int64_t* warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(VJ_FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(VJ_FULL, t, o);
+            if (lane >= o) t += u;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) v += warp_tot[w - 1];
+    __syncthreads();
+    return v;
+}
+
+// per tile: local exclusive scan into out, tile total into tot[blockIdx]
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int32_t* __restrict__ in, int64_t* __restrict__ out,
+                                                       int64_t* __restrict__ tot, int64_t n) {
+    __shared__ int64_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
+    int64_t v[SCAN_PER];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; i++) {
+        v[i] = (base + i < n) ? (int64_t)in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t incl = block_scan_incl(s, wt);
+    int64_t run = incl - s;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) tot[blockIdx.x] = incl;
+}
+
+// single block: exclusive scan of the tile totals (loops over chunks)
+__global__ void __launch_bounds__(SCAN_T) k_scan_totals(int64_t* tot, int64_t ntiles, int64_t* grand) {
+    __shared__ int64_t wt[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < ntiles; b += SCAN_T) {
+        int64_t i = b + threadIdx.x;
+        int64_t v = i < ntiles ? tot[i] : 0;
+        int64_t incl = block_scan_incl(v, wt);
+        int64_t c = carry;
+        if (i < ntiles) tot[i] = c + incl - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_T - 1) carry = c + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, const int64_t* __restrict__ tot, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tot[i / SCAN_TILE];
+}
+
+// ---------------------------------------------------------------- segment sort
+constexpr int SS_WPB = 8;
+constexpr int SS_CAP = 1024;  // per-warp shared-memory sort capacity
+
+struct SegSmem {
+    int id[SS_CAP];
+    float d[SS_CAP];
+};
+
+__global__ void __launch_bounds__(SS_WPB * 32)
+    k_seg_sort_copy(const int64_t* __restrict__ start, const int32_t* __restrict__ counts,
+                    const int64_t* __restrict__ offsets, const int32_t* __restrict__ sid,
+                    const float* __restrict__ sd, int32_t* __restrict__ did, float* __restrict__ dd, int64_t nseg) {
+    __shared__ SegSmem sm[SS_WPB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    SegSmem& S = sm[warp];
+    for (int64_t sg = (int64_t)blockIdx.x * SS_WPB + warp; sg < nseg; sg += (int64_t)gridDim.x * SS_WPB) {
+        const int n = counts[sg];
+        if (n == 0) continue;
+        const int64_t src = start[sg], dst = offsets[sg];
+        if (n <= 32) {
+            int id = lane < n ? sid[src + lane] : INT32_MAX;
+            float d = lane < n ? sd[src + lane] : 0.f;
+            // bitonic sort by id across the warp
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    int pid = __shfl_xor_sync(VJ_FULL, id, j);
+                    float pd = __shfl_xor_sync(VJ_FULL, d, j);
+                    bool up = (lane & k) == 0;
+                    bool low = (lane & j) == 0;
+                    bool take = low == up ? (pid < id) : (pid > id);
+                    if (take) {
+                        id = pid;
+                        d = pd;
+                    }
+                }
+            }
+            if (lane < n) {
+                did[dst + lane] = id;
+                dd[dst + lane] = d;
+            }
+        } else if (n <= SS_CAP) {
+            int P2 = 64;
+            while (P2 < n) P2 <<= 1;
+            for (int i = lane; i < P2; i += 32) {
+                S.id[i] = i < n ? sid[src + i] : INT32_MAX;
+                S.d[i] = i < n ? sd[src + i] : 0.f;
+            }
+            __syncwarp();
+            for (int k = 2; k <= P2; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = lane; i < P2; i += 32) {
+                        int p = i ^ j;
+                        if (p > i) {
+                            bool up = (i & k) == 0;
+                            int a = S.id[i], b = S.id[p];
+                            if ((a > b) == up) {
+                                float da = S.d[i], db = S.d[p];
+                                S.id[i] = b;
+                                S.id[p] = a;
+                                S.d[i] = db;
+                                S.d[p] = da;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int i = lane; i < n; i += 32) {
+                did[dst + i] = S.id[i];
+                dd[dst + i] = S.d[i];
+            }
+            __syncwarp();
+        } else {
+            // large rows: rank = number of smaller ids (ids are distinct)
+            for (int i = lane; i < n; i += 32) {
+                int a = sid[src + i];
+                int rank = 0;
+                for (int j = 0; j < n; j++) rank += sid[src + j] < a;
+                did[dst + rank] = a;
+                dd[dst + rank] = sd[src + i];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix) {
+    // out has n + 1 entries; out[n] = total
+    cudaStream_t s = ix->stream;
+    const int64_t ntiles = std::max<int64_t>(1, (n + SCAN_TILE - 1) / SCAN_TILE);
+    DBuf<int64_t> tot;
+    tot.alloc(ntiles, s);
+    k_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, out, tot.p, n);
+    VJ_LAUNCH_CHECK();
+    k_scan_totals<<<1, SCAN_T, 0, s>>>(tot.p, ntiles, out + n);
+    VJ_LAUNCH_CHECK();
+    if (n > 0) {
+        k_scan_add<<<vj_div_up(n, 256), 256, 0, s>>>(out, tot.p, n);
+        VJ_LAUNCH_CHECK();
+    }
+    tot.free_(s);
+}
+
+void vj_segment_sort_copy(const int64_t* src_start, const int32_t* counts, const int64_t* offsets,
+                          const int32_t* src_id, const float* src_d, int32_t* dst_id, float* dst_d, int64_t nseg,
+                          vj_index* ix) {
+    if (nseg == 0) return;
+    int blocks = (int)std::min<int64_t>(vj_div_up(nseg, SS_WPB), (int64_t)ix->num_sms * 16);
+    k_seg_sort_copy<<<blocks, SS_WPB * 32, 0, ix->stream>>>(src_start, counts, offsets, src_id, src_d, dst_id, dst_d,
+                                                            nseg);
+    VJ_LAUNCH_CHECK();
+}

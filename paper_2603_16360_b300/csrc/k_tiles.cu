@@ -1,0 +1,743 @@
+// k_tiles.cu -- dense distance tiles: the exact kNN graph of the merged node
+// set (build input of Sec. 4.3) and the exact nested-loop join (Sec. 3.2).
+//
+// Both evaluate keys through the norm expansion |a|^2 + |b|^2 - 2<a,b> (L2,
+// squared) or 1 - <a,b>/(|a||b|) (cosine) over 128 x 128 tiles of a
+// register-blocked FP32 Gram product, then
+//  - kNN: each block owns 128 rows and sweeps every column tile, keeping per
+//    row the KP smallest keys (KP = K + margin); a second pass re-ranks the KP
+//    candidates with direct-difference FP32 keys (FP64 among near-ties) and
+//    certifies that no excluded node can enter the top K given the Gram
+//    rounding bound; uncertified rows are redone by a brute-force row scan.
+//  - NLJ: pairs whose Gram key is below eps_key + bound become candidates;
+//    candidates are re-decided with direct-difference FP32 keys and, within
+//    the FP32 bound of eps, in FP64.
+#include <float.h>
+
+#include "vj_device.cuh"
+#include "vj_internal.cuh"
+
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 8, TT = 256;
+
+struct GramSmem {
+    float As[2][TBK][TBM + 4];
+    float Bs[2][TBK][TBN + 4];
+};
+
+// acc[i][j] = <row(ra + rr(i)), row(ca + cc(j))> with rr(i) = ty*4 + (i&3) +
+// 64*(i>>2), cc(j) = tx*4 + (j&3) + 64*(j>>2); rows beyond the limits read 0
+__device__ __forceinline__ void gram_tile(const float* __restrict__ vec, int dp, int64_t ra, int64_t ra_end,
+                                          int64_t ca, int64_t ca_end, float (&acc)[8][8], GramSmem& sm) {
+    const int t = threadIdx.x;
+    const int lr = t >> 1, lk = (t & 1) * 4;
+    const int ty = t >> 4, tx = t & 15;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+    const int64_t rA = ra + lr, rB = ca + lr;
+    const float4* pA = reinterpret_cast<const float4*>(vec + rA * dp);
+    const float4* pB = reinterpret_cast<const float4*>(vec + rB * dp);
+    const bool okA = rA < ra_end, okB = rB < ca_end;
+    float4 a4 = (okA && lk < dp) ? __ldg(pA + (lk >> 2)) : f4zero();
+    float4 b4 = (okB && lk < dp) ? __ldg(pB + (lk >> 2)) : f4zero();
+    sm.As[0][lk + 0][lr] = a4.x;
+    sm.As[0][lk + 1][lr] = a4.y;
+    sm.As[0][lk + 2][lr] = a4.z;
+    sm.As[0][lk + 3][lr] = a4.w;
+    sm.Bs[0][lk + 0][lr] = b4.x;
+    sm.Bs[0][lk + 1][lr] = b4.y;
+    sm.Bs[0][lk + 2][lr] = b4.z;
+    sm.Bs[0][lk + 3][lr] = b4.w;
+    __syncthreads();
+    int cur = 0;
+    for (int k0 = 0; k0 < dp; k0 += TBK) {
+        const int kn = k0 + TBK + lk;
+        const bool more = k0 + TBK < dp;
+        if (more) {
+            a4 = (okA && kn < dp) ? __ldg(pA + (kn >> 2)) : f4zero();
+            b4 = (okB && kn < dp) ? __ldg(pB + (kn >> 2)) : f4zero();
+        }
+#pragma unroll
+        for (int kk = 0; kk < TBK; kk++) {
+            float4 x0 = *reinterpret_cast<const float4*>(&sm.As[cur][kk][ty * 4]);
+            float4 x1 = *reinterpret_cast<const float4*>(&sm.As[cur][kk][64 + ty * 4]);
+            float4 y0 = *reinterpret_cast<const float4*>(&sm.Bs[cur][kk][tx * 4]);
+            float4 y1 = *reinterpret_cast<const float4*>(&sm.Bs[cur][kk][64 + tx * 4]);
+            float a[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            float b[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            const int nx_ = cur ^ 1;
+            sm.As[nx_][lk + 0][lr] = a4.x;
+            sm.As[nx_][lk + 1][lr] = a4.y;
+            sm.As[nx_][lk + 2][lr] = a4.z;
+            sm.As[nx_][lk + 3][lr] = a4.w;
+            sm.Bs[nx_][lk + 0][lr] = b4.x;
+            sm.Bs[nx_][lk + 1][lr] = b4.y;
+            sm.Bs[nx_][lk + 2][lr] = b4.z;
+            sm.Bs[nx_][lk + 3][lr] = b4.w;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+__device__ __forceinline__ int tile_row(int i) { return (threadIdx.x >> 4) * 4 + (i & 3) + 64 * (i >> 2); }
+__device__ __forceinline__ int tile_col(int j) { return (threadIdx.x & 15) * 4 + (j & 3) + 64 * (j >> 2); }
+
+// ---------------------------------------------------------------- norms
+__global__ void k_norms(const float* __restrict__ vec, int dp, int d, int64_t n, float* __restrict__ sqn,
+                        float* __restrict__ invn, double* __restrict__ maxn) {
+    const int lane = threadIdx.x & 31;
+    int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (u >= n) return;
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) {
+        double x = vec[u * dp + i];
+        s = fma(x, x, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(VJ_FULL, s, o);
+    if (lane == 0) {
+        sqn[u] = (float)s;
+        invn[u] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
+        // max norm (non-negative doubles order like their bit patterns)
+        atomicMax(reinterpret_cast<unsigned long long*>(maxn), (unsigned long long)__double_as_longlong(sqrt(s)));
+    }
+}
+
+// ---------------------------------------------------------------- kNN sweep
+// smem: gram buffers, key tile [128][129], per-row candidate lists [128][KP]
+template <int KP>
+struct KnnSmem {
+    union {
+        GramSmem g;
+        float D[TBM][TBN + 1];
+    } u;
+    float lk[TBM][KP];
+    int li[TBM][KP];
+};
+
+// insert (k, id) into the ascending list L (length KP, lanes own slots
+// lane, lane+32, ...); the last entry falls off
+template <int KP>
+__device__ __forceinline__ void list_insert(float* Lk, int* Li, float k, int id, int lane) {
+    constexpr int PER = (KP + 31) / 32;
+    int less = 0;
+    float ok[PER];
+    int oi[PER];
+#pragma unroll
+    for (int e = 0; e < PER; e++) {
+        int pos = lane + 32 * e;
+        if (pos < KP) {
+            ok[e] = Lk[pos];
+            oi[e] = Li[pos];
+            less += kless(ok[e], oi[e], k, id) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) less += __shfl_xor_sync(VJ_FULL, less, o);
+    if (less >= KP) return;
+    // new value of slot pos: pos < less: unchanged; pos == less: (k,id); pos > less: old[pos-1]
+    float nk[PER];
+    int ni[PER];
+#pragma unroll
+    for (int e = 0; e < PER; e++) {
+        int pos = lane + 32 * e;
+        int sp = pos - 1;  // source slot
+        // old[pos-1] lives in lane (pos-1)%32, element (pos-1)/32
+        int srcl = (sp + 32) & 31;
+        int srce = sp >> 5;  // -1 when pos == 0 (unused)
+        float ck = 0.f;
+        int ci = 0;
+#pragma unroll
+        for (int e2 = 0; e2 < PER; e2++) {
+            float tk = __shfl_sync(VJ_FULL, ok[e2], srcl);
+            int ti = __shfl_sync(VJ_FULL, oi[e2], srcl);
+            if (e2 == srce) {
+                ck = tk;
+                ci = ti;
+            }
+        }
+        nk[e] = pos < less ? ok[e] : (pos == less ? k : ck);
+        ni[e] = pos < less ? oi[e] : (pos == less ? id : ci);
+    }
+#pragma unroll
+    for (int e = 0; e < PER; e++) {
+        int pos = lane + 32 * e;
+        if (pos < KP && pos >= less) {
+            Lk[pos] = nk[e];
+            Li[pos] = ni[e];
+        }
+    }
+    __syncwarp();
+}
+
+template <int KP>
+__global__ void __launch_bounds__(TT) k_knn_sweep(const float* __restrict__ vec, const float* __restrict__ sqn,
+                                                   const float* __restrict__ invn, int dp, int64_t n, int metric,
+                                                   int32_t* __restrict__ cand_id, float* __restrict__ cand_key,
+                                                   float* __restrict__ row_thr) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    KnnSmem<KP>& S = *reinterpret_cast<KnnSmem<KP>*>(sraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ra = (int64_t)blockIdx.x * TBM;
+    for (int i = threadIdx.x; i < TBM * KP; i += TT) {
+        (&S.lk[0][0])[i] = FLT_MAX;
+        (&S.li[0][0])[i] = INT32_MAX;
+    }
+    __syncthreads();
+    float rn[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        int64_t r = ra + tile_row(i);
+        rn[i] = r < n ? (metric == 0 ? sqn[r] : invn[r]) : 0.f;
+    }
+    for (int64_t ca = 0; ca < n; ca += TBN) {
+        float acc[8][8];
+        gram_tile(vec, dp, ra, n, ca, n, acc, S.u.g);
+        // keys into the tile (the gram buffers are dead after the last sync)
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            int64_t c = ca + tile_col(j);
+            float cn = c < n ? (metric == 0 ? sqn[c] : invn[c]) : 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                int64_t r = ra + tile_row(i);
+                float key;
+                if (c >= n || r >= n || c == r) key = FLT_MAX;
+                else if (metric == 0) key = fmaxf(rn[i] + cn - 2.f * acc[i][j], 0.f);
+                else key = 1.f - acc[i][j] * rn[i] * cn;
+                S.u.D[tile_row(i)][tile_col(j)] = key;
+            }
+        }
+        __syncthreads();
+        // each warp updates 16 rows
+        for (int rr = warp * 16; rr < warp * 16 + 16; rr++) {
+            const float thr = S.lk[rr][KP - 1];
+            const int thi = S.li[rr][KP - 1];
+#pragma unroll
+            for (int e = 0; e < TBN / 32; e++) {
+                int cc = lane + 32 * e;
+                float k = S.u.D[rr][cc];
+                int id = (int)(ca + cc);
+                unsigned m = __ballot_sync(VJ_FULL, k != FLT_MAX && kless(k, id, thr, thi));
+                while (m) {
+                    int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    float kk = __shfl_sync(VJ_FULL, k, src);
+                    int ii = __shfl_sync(VJ_FULL, id, src);
+                    list_insert<KP>(S.lk[rr], S.li[rr], kk, ii, lane);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // write candidate lists
+    for (int rr = warp * 16; rr < warp * 16 + 16; rr++) {
+        int64_t r = ra + rr;
+        if (r >= n) continue;
+        for (int e = lane; e < KP; e += 32) {
+            cand_id[r * KP + e] = S.li[rr][e] == INT32_MAX ? -1 : S.li[rr][e];
+            cand_key[r * KP + e] = S.lk[rr][e];
+        }
+        if (lane == 0) row_thr[r] = S.lk[rr][KP - 1];
+    }
+}
+
+// ---------------------------------------------------------------- re-rank
+// warp per row: exact keys of the KP candidates, sort, FP64 near-tie runs,
+// certificate; outputs the top K (ids, keys)
+template <int G, int NPL>
+__global__ void __launch_bounds__(256) k_knn_rerank(const float* __restrict__ vec, const float* __restrict__ invn,
+                                                     const float* __restrict__ sqn, int dp, int d, int64_t n,
+                                                     int metric, int KP, int K, const int32_t* __restrict__ cand_id,
+                                                     const float* __restrict__ row_thr, double maxnorm,
+                                                     const int32_t* __restrict__ rows, int64_t nrows,
+                                                     int32_t* __restrict__ out_id, float* __restrict__ out_key,
+                                                     int32_t* __restrict__ bad_rows, int* __restrict__ nbad,
+                                                     unsigned long long* __restrict__ nrechk) {
+    __shared__ int sid[8][128];
+    __shared__ float skey[8][128];
+    __shared__ double s64[8][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * 8 + warp;
+    if (w >= nrows) return;
+    const int64_t r = rows ? (int64_t)rows[w] : w;
+    int* ids = sid[warp];
+    float* keys = skey[warp];
+    for (int e = lane; e < 128; e += 32) {
+        ids[e] = e < KP ? cand_id[r * KP + e] : -1;
+        keys[e] = FLT_MAX;
+    }
+    __syncwarp();
+    // compact valid candidates to the front
+    int nvalid = 0;
+    for (int base = 0; base < 128; base += 32) {
+        int v = ids[base + lane];
+        unsigned m = __ballot_sync(VJ_FULL, v >= 0);
+        __syncwarp();
+        if (v >= 0) ids[nvalid + __popc(m & ((1u << lane) - 1u))] = v;
+        nvalid += __popc(m);
+        __syncwarp();
+    }
+    for (int e = nvalid + lane; e < 128; e += 32) ids[e] = INT32_MAX;
+    __syncwarp();
+    float4 q[NPL];
+    load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
+    const float invq = metric ? invn[r] : 0.f;
+    group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, ids, nvalid, keys, lane);
+    __syncwarp();
+    // bitonic sort of 128 (key, id) pairs in shared memory
+    for (int k = 2; k <= 128; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < 128; i += 32) {
+                int p = i ^ j;
+                if (p > i) {
+                    bool up = (i & k) == 0;
+                    bool gt = kless(keys[p], ids[p], keys[i], ids[i]);
+                    if (gt == up) {
+                        float tk = keys[i];
+                        int ti = ids[i];
+                        keys[i] = keys[p];
+                        ids[i] = ids[p];
+                        keys[p] = tk;
+                        ids[p] = ti;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // near-tie runs among the first min(K+1, nvalid) entries: FP64 re-rank
+    const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
+    const int lim = min(K + 1, nvalid);
+    int i0 = 0;
+    while (i0 < lim) {
+        int i1 = i0;
+        while (i1 + 1 < nvalid &&
+               (metric == 0 ? keys[i1 + 1] - keys[i1] <= tol * keys[i1 + 1] : keys[i1 + 1] - keys[i1] <= tol))
+            i1++;
+        if (i1 > i0) {
+            for (int e = i0; e <= i1; e++) {
+                double dd = warp_dist64(vec, dp, d, metric, r, ids[e], lane);
+                if (lane == 0) s64[warp][e] = dd;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                atomicAdd(nrechk, 1ull);
+                // insertion sort of the run by (d64, id)
+                for (int a = i0 + 1; a <= i1; a++) {
+                    double da = s64[warp][a];
+                    int ia = ids[a];
+                    float ka = keys[a];
+                    int b = a - 1;
+                    while (b >= i0 && (s64[warp][b] > da || (s64[warp][b] == da && ids[b] > ia))) {
+                        s64[warp][b + 1] = s64[warp][b];
+                        ids[b + 1] = ids[b];
+                        keys[b + 1] = keys[b];
+                        b--;
+                    }
+                    s64[warp][b + 1] = da;
+                    ids[b + 1] = ia;
+                    keys[b + 1] = ka;
+                }
+            }
+            __syncwarp();
+        }
+        i0 = i1 + 1;
+    }
+    // certificate: every node outside the candidate list has a Gram key >=
+    // row_thr, hence a true key >= row_thr - beta
+    bool full = nvalid >= KP;  // a short list holds every other node
+    bool ok = true;
+    if (full && K <= nvalid) {
+        float kth = keys[K - 1];
+        double an = metric == 0 ? sqrt((double)sqn[r]) : 1.0;
+        double mx = metric == 0 ? maxnorm : 1.0;
+        double beta = (2.0 * dp + 10.0) * (double)VJ_F32_U * (an + mx) * (an + mx) + 1e-30;
+        double kth_hi = (double)kth * (1.0 + tol);
+        ok = kth_hi + beta < (double)row_thr[r];
+    }
+    if (!ok && lane == 0) {
+        int slot = atomicAdd(nbad, 1);
+        bad_rows[slot] = (int32_t)r;
+    }
+    for (int e = lane; e < K; e += 32) {
+        out_id[r * K + e] = e < nvalid ? ids[e] : -1;
+        out_key[r * K + e] = e < nvalid ? keys[e] : FLT_MAX;
+    }
+}
+
+// ---------------------------------------------------------------- fallback
+// warp per uncertified row: brute-force top-K' over all nodes with
+// direct-difference keys, then the same re-rank (run again on its output)
+template <int G, int NPL>
+__global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ vec, const float* __restrict__ invn,
+                                                      int dp, int64_t n, int metric, int KP,
+                                                      const int32_t* __restrict__ rows, int nrows,
+                                                      int32_t* __restrict__ cand_id, float* __restrict__ row_thr) {
+    __shared__ int cid[8][128];
+    __shared__ float ckey[8][128];
+    __shared__ float lk[8][128];
+    __shared__ int li[8][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * 8 + warp;
+    if (w >= nrows) return;
+    const int64_t r = rows[w];
+    for (int e = lane; e < 128; e += 32) {
+        lk[warp][e] = FLT_MAX;
+        li[warp][e] = INT32_MAX;
+    }
+    __syncwarp();
+    float4 q[NPL];
+    load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
+    const float invq = metric ? invn[r] : 0.f;
+    for (int64_t c0 = 0; c0 < n; c0 += 128) {
+        int nc = (n - c0) < 128 ? (int)(n - c0) : 128;
+        for (int e = lane; e < 128; e += 32) cid[warp][e] = (int)(c0 + e);
+        __syncwarp();
+        group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, cid[warp], nc, ckey[warp], lane);
+        __syncwarp();
+        for (int e0 = 0; e0 < nc; e0 += 32) {
+            int e = e0 + lane;
+            float k = e < nc ? ckey[warp][e] : FLT_MAX;
+            int id = (int)(c0 + e);
+            bool ok = e < nc && id != r;
+            float thr = lk[warp][KP - 1];
+            int thi = li[warp][KP - 1];
+            unsigned m = __ballot_sync(VJ_FULL, ok && kless(k, id, thr, thi));
+            while (m) {
+                int src = __ffs(m) - 1;
+                m &= m - 1;
+                float kk = __shfl_sync(VJ_FULL, k, src);
+                int ii = __shfl_sync(VJ_FULL, id, src);
+                list_insert<128>(lk[warp], li[warp], kk, ii, lane);
+            }
+        }
+    }
+    for (int e = lane; e < KP; e += 32) cand_id[r * KP + e] = li[warp][e] == INT32_MAX ? -1 : li[warp][e];
+    // the scan saw every node: no outside candidate exists
+    if (lane == 0) row_thr[r] = FLT_MAX;
+}
+
+// ---------------------------------------------------------------- NLJ
+constexpr int NLJ_COLS = 16;  // column tiles per block
+
+__global__ void __launch_bounds__(TT) k_nlj_tile(const float* __restrict__ vec, const float* __restrict__ sqn,
+                                                  const float* __restrict__ invn, int dp, int64_t nx, int64_t nq,
+                                                  int metric, float key_hi, int32_t* __restrict__ cq,
+                                                  int32_t* __restrict__ cx, unsigned long long* __restrict__ ncand,
+                                                  int64_t cap) {
+    __shared__ GramSmem sm;
+    __shared__ int bq[1024], bx[1024];
+    __shared__ int bn;
+    __shared__ unsigned long long bbase;
+    const int64_t qa = nx + (int64_t)blockIdx.x * TBM;
+    const int64_t qend = nx + nq;
+    float rn[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        int64_t r = qa + tile_row(i);
+        rn[i] = r < qend ? (metric == 0 ? sqn[r] : invn[r]) : 0.f;
+    }
+    for (int tcol = 0; tcol < NLJ_COLS; tcol++) {
+        const int64_t ca = ((int64_t)blockIdx.y * NLJ_COLS + tcol) * TBN;
+        if (ca >= nx) break;
+        if (threadIdx.x == 0) bn = 0;
+        float acc[8][8];
+        gram_tile(vec, dp, qa, qend, ca, nx, acc, sm);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            int64_t c = ca + tile_col(j);
+            if (c >= nx) continue;
+            float cn = metric == 0 ? sqn[c] : invn[c];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                int64_t r = qa + tile_row(i);
+                if (r >= qend) continue;
+                float key = metric == 0 ? rn[i] + cn - 2.f * acc[i][j] : 1.f - acc[i][j] * rn[i] * cn;
+                if (key < key_hi) {
+                    int slot = atomicAdd(&bn, 1);
+                    if (slot < 1024) {
+                        bq[slot] = (int)(r - nx);
+                        bx[slot] = (int)c;
+                    } else {
+                        unsigned long long g = atomicAdd(ncand, 1ull);
+                        if ((int64_t)g < cap) {
+                            cq[g] = (int)(r - nx);
+                            cx[g] = (int)c;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        int cnt = min(bn, 1024);
+        if (threadIdx.x == 0 && cnt > 0) bbase = atomicAdd(ncand, (unsigned long long)cnt);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt; e += TT) {
+            unsigned long long g = bbase + e;
+            if ((int64_t)g < cap) {
+                cq[g] = bq[e];
+                cx[g] = bx[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// warp per 32 candidates: direct-difference key, FP64 near eps; survivors get
+// counted per query and kept (flag)
+__global__ void k_nlj_recheck(const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d,
+                              int64_t nx, int metric, float eps_key, float band, double eps64,
+                              const int32_t* __restrict__ cq, const int32_t* __restrict__ cx, int64_t nc,
+                              float* __restrict__ cd, int32_t* __restrict__ counts,
+                              unsigned long long* __restrict__ nrechk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t e = w * 32 + lane;
+    // each lane computes its own pair's key sequentially (vectors are short-lived in L2)
+    bool valid = e < nc;
+    float key = FLT_MAX;
+    int64_t qn = 0, xn = 0;
+    if (valid) {
+        qn = nx + cq[e];
+        xn = cx[e];
+        const float4* a = reinterpret_cast<const float4*>(vec + qn * dp);
+        const float4* b = reinterpret_cast<const float4*>(vec + xn * dp);
+        float s = 0.f;
+        for (int i = 0; i < dp / 4; i++) {
+            float4 x = __ldg(a + i), y = __ldg(b + i);
+            if (metric == 0) {
+                float t0 = x.x - y.x, t1 = x.y - y.y, t2 = x.z - y.z, t3 = x.w - y.w;
+                s = fmaf(t0, t0, s);
+                s = fmaf(t1, t1, s);
+                s = fmaf(t2, t2, s);
+                s = fmaf(t3, t3, s);
+            } else {
+                s = fmaf(x.x, y.x, s);
+                s = fmaf(x.y, y.y, s);
+                s = fmaf(x.z, y.z, s);
+                s = fmaf(x.w, y.w, s);
+            }
+        }
+        key = metric == 0 ? s : 1.f - s * invn[qn] * invn[xn];
+    }
+    float scale = metric == 0 ? eps_key : 1.f;
+    bool in = valid && key < eps_key;
+    bool near = valid && fabsf(key - eps_key) <= band * scale;
+    unsigned nm = __ballot_sync(VJ_FULL, near);
+    while (nm) {
+        int src = __ffs(nm) - 1;
+        nm &= nm - 1;
+        int64_t a = __shfl_sync(VJ_FULL, qn, src), b = __shfl_sync(VJ_FULL, xn, src);
+        double dd = warp_dist64(vec, dp, d, metric, a, b, lane);
+        if (lane == src) in = dd < eps64;
+        if (lane == 0) atomicAdd(nrechk, 1ull);
+    }
+    if (valid) {
+        cd[e] = in ? (metric == 0 ? sqrtf(fmaxf(key, 0.f)) : key) : -1.f;
+        if (in) atomicAdd(counts + cq[e], 1);
+    }
+}
+
+__global__ void k_nlj_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx,
+                              const float* __restrict__ cd, int64_t nc, const int64_t* __restrict__ offsets,
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ tid, float* __restrict__ td) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nc || cd[e] < 0.f) return;
+    int q = cq[e];
+    int pos = atomicAdd(cursor + q, 1);
+    tid[offsets[q] + pos] = cx[e];
+    td[offsets[q] + pos] = cd[e];
+}
+
+}  // namespace
+
+// template dispatch on the padded dimension for the warp-per-row kernels
+
+void vj_compute_norms(vj_index* ix, double* maxnorm_out) {
+    cudaStream_t s = ix->stream;
+    DBuf<double> mx;
+    mx.alloc(1, s);
+    VJ_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(double), s));
+    k_norms<<<vj_div_up(ix->n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->n, ix->sqn.p, ix->invn.p, mx.p);
+    VJ_LAUNCH_CHECK();
+    VJ_CUDA(cudaMemcpyAsync(maxnorm_out, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    mx.free_(s);
+}
+
+template <int KP>
+static void run_sweep(vj_index* ix, int32_t* cid, float* ckey, float* thr) {
+    size_t smem = sizeof(KnnSmem<KP>);
+    VJ_CUDA(cudaFuncSetAttribute(k_knn_sweep<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_knn_sweep<KP><<<vj_div_up(ix->n, TBM), TT, smem, ix->stream>>>(ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, ix->n,
+                                                                     ix->metric, cid, ckey, thr);
+    VJ_LAUNCH_CHECK();
+}
+
+void vj_build_knn(vj_index* ix) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    const int K = ix->K;
+    double maxnorm = 0.0;
+    vj_compute_norms(ix, &maxnorm);
+    int KP = K + std::max(16, K / 4);
+    KP = std::min(KP, 128);
+    KP = (KP + 31) / 32 * 32;
+    if (KP > 128) KP = 128;
+    VJ_REQUIRE(K < KP || K == 128, VJ_ERR_ARG, "knn_k too large");
+    DBuf<int32_t> cid;
+    DBuf<float> ckey, thr;
+    cid.alloc((size_t)n * KP, s);
+    ckey.alloc((size_t)n * KP, s);
+    thr.alloc(n, s);
+    switch (KP) {
+        case 32: run_sweep<32>(ix, cid.p, ckey.p, thr.p); break;
+        case 64: run_sweep<64>(ix, cid.p, ckey.p, thr.p); break;
+        case 96: run_sweep<96>(ix, cid.p, ckey.p, thr.p); break;
+        default: run_sweep<128>(ix, cid.p, ckey.p, thr.p); break;
+    }
+    ix->knn.ensure((size_t)n * K, s);
+    ix->knnd.ensure((size_t)n * K, s);
+    DBuf<int32_t> bad;
+    DBuf<int> nbad;
+    DBuf<unsigned long long> nr;
+    bad.alloc(n, s);
+    nbad.alloc(1, s);
+    nr.alloc(1, s);
+    VJ_CUDA(cudaMemsetAsync(nbad.p, 0, sizeof(int), s));
+    VJ_CUDA(cudaMemsetAsync(nr.p, 0, sizeof(unsigned long long), s));
+    const int dp4 = ix->dp / 4;
+    VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(n, 8), 256, 0, s>>>(
+                            ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
+                            maxnorm, nullptr, n, ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p)));
+    VJ_LAUNCH_CHECK();
+    int hb = 0;
+    VJ_CUDA(cudaMemcpyAsync(&hb, nbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    ix->knn_uncertified = hb;
+    if (hb > 0) {
+        // exact row scans for the uncertified rows, then re-rank them again
+        VJ_DISPATCH_GN(dp4, (k_knn_rowscan<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
+                                ix->vec.p, ix->invn.p, ix->dp, n, ix->metric, KP, bad.p, hb, cid.p, thr.p)));
+        VJ_LAUNCH_CHECK();
+        // the row scans saw every node, so these rows certify on re-rank
+        DBuf<int32_t> bad2;
+        bad2.alloc(hb, s);
+        VJ_CUDA(cudaMemsetAsync(nbad.p, 0, sizeof(int), s));
+        VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
+                                ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
+                                maxnorm, bad.p, hb, ix->knn.p, ix->knnd.p, bad2.p, nbad.p, nr.p)));
+        VJ_LAUNCH_CHECK();
+        bad2.free_(s);
+    }
+    bad.free_(s);
+    nbad.free_(s);
+    nr.free_(s);
+    cid.free_(s);
+    ckey.free_(s);
+    thr.free_(s);
+}
+
+void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids, DBuf<float>& dists,
+                          int64_t* nnz_out, double* ms_out) {
+    cudaStream_t s = ix->stream;
+    const int64_t nx = ix->nx, nq = ix->nq;
+    cudaEvent_t e0, e1;
+    VJ_CUDA(cudaEventCreate(&e0));
+    VJ_CUDA(cudaEventCreate(&e1));
+    VJ_CUDA(cudaEventRecord(e0, s));
+    const float eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
+    // Gram-key bound: (2dp+10) u (|a|+|b|)^2 for L2 (norms up to maxnorm),
+    // (2dp+10) u * 4 for cosine
+    double maxnorm = 0.0;
+    {
+        DBuf<double> mx;
+        mx.alloc(1, s);
+        VJ_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(double), s));
+        k_norms<<<vj_div_up(ix->n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->n, ix->sqn.p, ix->invn.p,
+                                                            mx.p);
+        VJ_LAUNCH_CHECK();
+        VJ_CUDA(cudaMemcpyAsync(&maxnorm, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        mx.free_(s);
+    }
+    double beta = ix->metric == VJ_L2 ? (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0 * maxnorm * maxnorm
+                                      : (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0;
+    float key_hi = (float)((double)eps_key + beta) * 1.0001f + 1e-30f;
+    int64_t cap = std::max<int64_t>(nq * 64, 1 << 20);
+    DBuf<int32_t> cq, cx;
+    DBuf<float> cd;
+    DBuf<unsigned long long> ctr;
+    ctr.alloc(2, s);
+    unsigned long long hn = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        cq.ensure(cap, s);
+        cx.ensure(cap, s);
+        VJ_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
+        dim3 grid(vj_div_up(nq, TBM), vj_div_up(vj_div_up(nx, TBN), NLJ_COLS));
+        k_nlj_tile<<<grid, TT, 0, s>>>(ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, nx, nq, ix->metric, key_hi, cq.p,
+                                       cx.p, ctr.p, cap);
+        VJ_LAUNCH_CHECK();
+        VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        if ((int64_t)hn <= cap) break;
+        cap = (int64_t)hn + 1024;
+    }
+    const int64_t nc = (int64_t)hn;
+    DBuf<int32_t> counts, cursor;
+    counts.alloc(nq, s);
+    cursor.alloc(nq, s);
+    cd.alloc(std::max<int64_t>(nc, 1), s);
+    VJ_CUDA(cudaMemsetAsync(counts.p, 0, nq * sizeof(int32_t), s));
+    VJ_CUDA(cudaMemsetAsync(cursor.p, 0, nq * sizeof(int32_t), s));
+    const float band = 2.0f * (float)(ix->dp + 4) * VJ_F32_U * (ix->metric == VJ_L2 ? 1.0f : 4.0f) + 1e-6f;
+    if (nc > 0) {
+        k_nlj_recheck<<<vj_div_up(nc, 256), 256, 0, s>>>(ix->vec.p, ix->invn.p, ix->dp, ix->d, nx, ix->metric,
+                                                         eps_key, band, (double)eps, cq.p, cx.p, nc, cd.p, counts.p,
+                                                         ctr.p + 1);
+        VJ_LAUNCH_CHECK();
+    }
+    offsets.ensure(nq + 1, s);
+    vj_exclusive_scan_i32_to_i64(counts.p, offsets.p, nq, ix);
+    int64_t nnz = 0;
+    VJ_CUDA(cudaMemcpyAsync(&nnz, offsets.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    DBuf<int32_t> tid;
+    DBuf<float> td;
+    tid.alloc(std::max<int64_t>(nnz, 1), s);
+    td.alloc(std::max<int64_t>(nnz, 1), s);
+    if (nc > 0) {
+        k_nlj_scatter<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, cx.p, cd.p, nc, offsets.p, cursor.p, tid.p, td.p);
+        VJ_LAUNCH_CHECK();
+    }
+    ids.ensure(std::max<int64_t>(nnz, 1), s);
+    dists.ensure(std::max<int64_t>(nnz, 1), s);
+    vj_segment_sort_copy(offsets.p, counts.p, offsets.p, tid.p, td.p, ids.p, dists.p, nq, ix);
+    VJ_CUDA(cudaEventRecord(e1, s));
+    VJ_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    VJ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms;
+    *nnz_out = nnz;
+    tid.free_(s);
+    td.free_(s);
+    counts.free_(s);
+    cursor.free_(s);
+    cq.free_(s);
+    cx.free_(s);
+    cd.free_(s);
+    ctr.free_(s);
+}

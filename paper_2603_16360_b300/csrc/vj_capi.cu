@@ -1,0 +1,348 @@
+// vj_capi.cu -- the extern "C" entry points declared in include/vj.h.
+// Host orchestration only: every step of a build or a join runs in the
+// kernels of k_tiles.cu, k_graph.cu, k_join.cu and k_csr.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "vj_internal.cuh"
+
+static thread_local char g_err[1024] = "";
+
+void vj_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char* vj_last_error(void) { return g_err; }
+
+extern "C" void vj_default_params(vj_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->degree = 32;
+    p->knn_k = 64;
+    p->greedy_beam = 256;
+    p->conv_threshold = 10;
+    p->hybrid_beam = 256;
+    p->work_sharing = VJ_WS_SOFT;
+    p->adapt_hybrid = 1;
+    p->force_hybrid = 0;
+    p->precision = VJ_PREC_FP32;
+    p->learned = 0;
+    p->route_bruteforce = 0;
+    p->input_on_device = 0;
+    p->seed = 0;
+}
+
+template <class F>
+static vj_status guarded(F&& f) {
+    try {
+        f();
+        return VJ_OK;
+    } catch (const VjError& e) {
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        vj_set_error("host allocation failed");
+        return VJ_ERR_OOM;
+    } catch (...) {
+        vj_set_error("unexpected internal error");
+        return VJ_ERR_STATE;
+    }
+}
+
+static void check_join_params(const vj_params& p) {
+    VJ_REQUIRE(p.work_sharing == VJ_WS_NONE || p.work_sharing == VJ_WS_SOFT || p.work_sharing == VJ_WS_SELF,
+               VJ_ERR_ARG, "work_sharing must be NONE, SOFT or SELF (HARD is not implemented)");
+    VJ_REQUIRE(p.hybrid_beam >= 0 && p.hybrid_beam <= (1 << 20), VJ_ERR_ARG, "hybrid_beam out of range");
+    VJ_REQUIRE(p.greedy_beam >= 1, VJ_ERR_ARG, "greedy_beam must be >= 1");
+    VJ_REQUIRE(p.learned == 0 && p.route_bruteforce == 0, VJ_ERR_ARG,
+               "learned / route_bruteforce are reserved and must be 0");
+}
+
+static void free_index(vj_index* ix) {
+    if (!ix) return;
+    cudaStream_t s = ix->stream;
+    ix->vec.free_(s);
+    ix->sqn.free_(s);
+    ix->invn.free_(s);
+    ix->knn.free_(s);
+    ix->knnd.free_(s);
+    ix->adj.free_(s);
+    ix->elen.free_(s);
+    ix->parent.free_(s);
+    ix->order.free_(s);
+    ix->depth.free_(s);
+    ix->done.free_(s);
+    ix->cache.free_(s);
+    ix->steps.free_(s);
+    ix->hyb.free_(s);
+    ix->count.free_(s);
+    ix->seg.free_(s);
+    ix->pool_id.free_(s);
+    ix->pool_d.free_(s);
+    ix->wspace.free_(s);
+    ix->ctr.free_(s);
+    ix->offsets.free_(s);
+    ix->out_id.free_(s);
+    ix->out_d.free_(s);
+    ix->tmp.free_(s);
+    cudaStreamSynchronize(s);
+    if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
+    delete ix;
+}
+
+extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_t nq, int d, vj_metric metric,
+                              const vj_params* pin, vj_index** out) {
+    if (out) *out = nullptr;
+    vj_index* ix = nullptr;
+    vj_status st = guarded([&] {
+        VJ_REQUIRE(out != nullptr, VJ_ERR_ARG, "out is NULL");
+        VJ_REQUIRE(X != nullptr && Q != nullptr, VJ_ERR_ARG, "X or Q is NULL");
+        VJ_REQUIRE(nx >= 1 && nq >= 1, VJ_ERR_ARG, "nx and nq must be >= 1");
+        VJ_REQUIRE(nx + nq < (int64_t)INT32_MAX, VJ_ERR_ARG, "nx + nq must be < 2^31");
+        VJ_REQUIRE(d >= 1 && d <= 4096, VJ_ERR_ARG, "d must be in [1, 4096]");
+        VJ_REQUIRE(metric == VJ_L2 || metric == VJ_COSINE, VJ_ERR_ARG, "unknown metric");
+        vj_params p;
+        vj_default_params(&p);
+        if (pin) p = *pin;
+        VJ_REQUIRE(p.degree >= 1 && p.degree <= 32, VJ_ERR_ARG, "degree must be in [1, 32]");
+        if (p.knn_k <= 0) p.knn_k = 2 * p.degree;
+        VJ_REQUIRE(p.knn_k >= p.degree && p.knn_k <= 112, VJ_ERR_ARG, "knn_k must be in [degree, 112]");
+        VJ_REQUIRE(p.precision == VJ_PREC_FP32, VJ_ERR_ARG, "only FP32 build tiles are implemented");
+        check_join_params(p);
+
+        ix = new vj_index();
+        VJ_CUDA(cudaGetDevice(&ix->dev));
+        int sms = 0;
+        VJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->dev));
+        ix->num_sms = sms > 0 ? sms : VJ_NUM_SMS_HINT;
+        VJ_CUDA(cudaStreamCreateWithFlags(&ix->own_stream, cudaStreamNonBlocking));
+        ix->stream = ix->own_stream;
+        ix->nx = nx;
+        ix->nq = nq;
+        ix->n = nx + nq;
+        ix->d = d;
+        ix->dp = (d + 3) / 4 * 4;
+        ix->R = p.degree;
+        // at most n - 1 other nodes exist
+        ix->K = (int)std::min<int64_t>(p.knn_k, ix->n - 1 > 0 ? ix->n - 1 : 1);
+        ix->R = std::min(ix->R, ix->K);
+        ix->metric = metric;
+        ix->p = p;
+        cudaStream_t s = ix->stream;
+        ix->vec.alloc((size_t)ix->n * ix->dp, s);
+        if (ix->dp != d) VJ_CUDA(cudaMemsetAsync(ix->vec.p, 0, (size_t)ix->n * ix->dp * sizeof(float), s));
+        cudaMemcpyKind kind = p.input_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        VJ_CUDA(cudaMemcpy2DAsync(ix->vec.p, ix->dp * sizeof(float), X, d * sizeof(float), d * sizeof(float), nx,
+                                  kind, s));
+        VJ_CUDA(cudaMemcpy2DAsync(ix->vec.p + (size_t)nx * ix->dp, ix->dp * sizeof(float), Q, d * sizeof(float),
+                                  d * sizeof(float), nq, kind, s));
+        ix->sqn.alloc(ix->n, s);
+        ix->invn.alloc(ix->n, s);
+        vj_build_knn(ix);
+        vj_build_graph(ix);
+        VJ_CUDA(cudaStreamSynchronize(s));
+        *out = ix;
+    });
+    if (st != VJ_OK && ix) free_index(ix);
+    return st;
+}
+
+extern "C" vj_status vj_set_stream(vj_index* ix, void* stream) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        VJ_CUDA(cudaStreamSynchronize(ix->stream));
+        ix->stream = (cudaStream_t)stream;
+    });
+}
+
+extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr && p != nullptr, VJ_ERR_ARG, "NULL argument");
+        check_join_params(*p);
+        ix->p.greedy_beam = p->greedy_beam;
+        ix->p.conv_threshold = p->conv_threshold;
+        ix->p.hybrid_beam = p->hybrid_beam;
+        ix->p.work_sharing = p->work_sharing;
+        ix->p.adapt_hybrid = p->adapt_hybrid;
+        ix->p.force_hybrid = p->force_hybrid;
+    });
+}
+
+static vj_result* new_result(int64_t nq, int64_t nnz, bool on_device, cudaStream_t s) {
+    vj_result* r = (vj_result*)calloc(1, sizeof(vj_result));
+    if (!r) throw std::bad_alloc();
+    r->nq = nq;
+    r->nnz = nnz;
+    r->on_device = on_device ? 1 : 0;
+    size_t b_off = (nq + 1) * sizeof(int64_t), b_id = std::max<int64_t>(nnz, 1) * sizeof(int32_t),
+           b_d = std::max<int64_t>(nnz, 1) * sizeof(float), b_q = nq * sizeof(int32_t), b_h = nq;
+    if (on_device) {
+        cudaError_t e = cudaSuccess;
+        e = e ? e : cudaMallocAsync((void**)&r->offsets, b_off, s);
+        e = e ? e : cudaMallocAsync((void**)&r->ids, b_id, s);
+        e = e ? e : cudaMallocAsync((void**)&r->dists, b_d, s);
+        e = e ? e : cudaMallocAsync((void**)&r->steps, b_q, s);
+        e = e ? e : cudaMallocAsync((void**)&r->cache, b_q, s);
+        e = e ? e : cudaMallocAsync((void**)&r->hybrid, b_h, s);
+        if (e != cudaSuccess) {
+            vj_set_error("result allocation failed: %s", cudaGetErrorString(e));
+            vj_result_free(r);
+            throw VjError{VJ_ERR_OOM};
+        }
+    } else {
+        r->offsets = (int64_t*)malloc(b_off);
+        r->ids = (int32_t*)malloc(b_id);
+        r->dists = (float*)malloc(b_d);
+        r->steps = (int32_t*)malloc(b_q);
+        r->cache = (int32_t*)malloc(b_q);
+        r->hybrid = (uint8_t*)malloc(b_h);
+        if (!r->offsets || !r->ids || !r->dists || !r->steps || !r->cache || !r->hybrid) {
+            vj_result_free(r);
+            throw std::bad_alloc();
+        }
+    }
+    return r;
+}
+
+static vj_status join_impl(vj_index* ix, float eps, int budget, vj_result** out, bool on_device) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr && out != nullptr, VJ_ERR_ARG, "NULL argument");
+        VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
+        cudaStream_t s = ix->stream;
+        vj_stats st;
+        memset(&st, 0, sizeof(st));
+        int64_t nnz = 0;
+        vj_run_join(ix, eps, budget, &st, &nnz);
+        vj_result* r = new_result(ix->nq, nnz, on_device, s);
+        cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        cudaError_t e = cudaSuccess;
+        e = e ? e : cudaMemcpyAsync(r->offsets, ix->offsets.p, (ix->nq + 1) * sizeof(int64_t), k, s);
+        if (nnz > 0) {
+            e = e ? e : cudaMemcpyAsync(r->ids, ix->out_id.p, nnz * sizeof(int32_t), k, s);
+            e = e ? e : cudaMemcpyAsync(r->dists, ix->out_d.p, nnz * sizeof(float), k, s);
+        }
+        e = e ? e : cudaMemcpyAsync(r->steps, ix->steps.p, ix->nq * sizeof(int32_t), k, s);
+        e = e ? e : cudaMemcpyAsync(r->cache, ix->cache.p, ix->nq * sizeof(int32_t), k, s);
+        e = e ? e : cudaMemcpyAsync(r->hybrid, ix->hyb.p, ix->nq, k, s);
+        e = e ? e : cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            vj_result_free(r);
+            vj_set_error("result copy failed: %s", cudaGetErrorString(e));
+            throw VjError{VJ_ERR_CUDA};
+        }
+        r->stats = st;
+        *out = r;
+    });
+}
+
+extern "C" vj_status vj_join(vj_index* ix, float eps, int budget, vj_result** out) {
+    return join_impl(ix, eps, budget, out, false);
+}
+
+extern "C" vj_status vj_join_device(vj_index* ix, float eps, int budget, vj_result** out) {
+    return join_impl(ix, eps, budget, out, true);
+}
+
+extern "C" vj_status vj_join_exact(vj_index* ix, float eps, vj_result** out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr && out != nullptr, VJ_ERR_ARG, "NULL argument");
+        VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
+        cudaStream_t s = ix->stream;
+        DBuf<int64_t> off;
+        DBuf<int32_t> ids;
+        DBuf<float> dd;
+        int64_t nnz = 0;
+        double ms = 0.0;
+        vj_exact_join_device(ix, eps, off, ids, dd, &nnz, &ms);
+        vj_result* r = new_result(ix->nq, nnz, false, s);
+        VJ_CUDA(cudaMemcpyAsync(r->offsets, off.p, (ix->nq + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (nnz > 0) {
+            VJ_CUDA(cudaMemcpyAsync(r->ids, ids.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            VJ_CUDA(cudaMemcpyAsync(r->dists, dd.p, nnz * sizeof(float), cudaMemcpyDeviceToHost, s));
+        }
+        VJ_CUDA(cudaStreamSynchronize(s));
+        memset(r->steps, 0, ix->nq * sizeof(int32_t));
+        memset(r->cache, 0xff, ix->nq * sizeof(int32_t));
+        memset(r->hybrid, 0, ix->nq);
+        r->stats.ms_total = ms;
+        r->stats.dist_computations = ix->nx * ix->nq;
+        off.free_(s);
+        ids.free_(s);
+        dd.free_(s);
+        *out = r;
+    });
+}
+
+extern "C" vj_status vj_export_graph(const vj_index* ix, int32_t* adj, int32_t* entry, int32_t* parent,
+                                     int32_t* order, int32_t* depth) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        cudaStream_t s = ix->stream;
+        if (adj)
+            VJ_CUDA(cudaMemcpyAsync(adj, ix->adj.p, (size_t)ix->n * ix->R * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    s));
+        if (parent) VJ_CUDA(cudaMemcpyAsync(parent, ix->parent.p, ix->nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (order) VJ_CUDA(cudaMemcpyAsync(order, ix->order.p, ix->nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (depth) VJ_CUDA(cudaMemcpyAsync(depth, ix->depth.p, ix->nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        if (entry) *entry = ix->entry;
+    });
+}
+
+extern "C" vj_status vj_export_knn(const vj_index* ix, int32_t* ids, float* dists) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        cudaStream_t s = ix->stream;
+        if (ids)
+            VJ_CUDA(cudaMemcpyAsync(ids, ix->knn.p, (size_t)ix->n * ix->K * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    s));
+        if (dists)
+            VJ_CUDA(cudaMemcpyAsync(dists, ix->knnd.p, (size_t)ix->n * ix->K * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+extern "C" vj_status vj_index_info(const vj_index* ix, int64_t* nx, int64_t* nq, int* d, int* degree, int* knn_k,
+                                   int* max_depth) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        if (nx) *nx = ix->nx;
+        if (nq) *nq = ix->nq;
+        if (d) *d = ix->d;
+        if (degree) *degree = ix->R;
+        if (knn_k) *knn_k = ix->K;
+        if (max_depth) *max_depth = ix->max_depth;
+    });
+}
+
+extern "C" void vj_result_free(vj_result* r) {
+    if (!r) return;
+    if (r->on_device) {
+        cudaFree(r->offsets);
+        cudaFree(r->ids);
+        cudaFree(r->dists);
+        cudaFree(r->steps);
+        cudaFree(r->cache);
+        cudaFree(r->hybrid);
+    } else {
+        free(r->offsets);
+        free(r->ids);
+        free(r->dists);
+        free(r->steps);
+        free(r->cache);
+        free(r->hybrid);
+    }
+    free(r);
+}
+
+extern "C" void vj_free(vj_index* ix) { free_index(ix); }

@@ -1,0 +1,150 @@
+// vj_internal.cuh -- shared declarations of the libvj translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/vj.h"
+
+// ------------------------------------------------------------------ errors
+void vj_set_error(const char* fmt, ...);
+
+struct VjError {
+    vj_status code;
+};
+
+#define VJ_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            vj_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            throw VjError{VJ_ERR_CUDA};                                               \
+        }                                                                             \
+    } while (0)
+
+#define VJ_LAUNCH_CHECK() VJ_CUDA(cudaGetLastError())
+
+#define VJ_REQUIRE(cond, code, ...)      \
+    do {                                 \
+        if (!(cond)) {                   \
+            vj_set_error(__VA_ARGS__);   \
+            throw VjError{code};         \
+        }                                \
+    } while (0)
+
+// ------------------------------------------------------------------ constants
+constexpr int VJ_NUM_SMS_HINT = 148;
+constexpr float VJ_F32_U = 5.9604645e-8f;  // unit roundoff of binary32 (2^-24)
+
+// device error codes (written by kernels into a device word, read by the host)
+enum : int {
+    VJ_DERR_NONE = 0,
+    VJ_DERR_WAIT_TIMEOUT = 1,   // a work-sharing dependency wait gave up
+    VJ_DERR_VISITED_OVERFLOW = 2,
+    VJ_DERR_RESULT_OVERFLOW = 3,
+    VJ_DERR_QUEUE_OVERFLOW = 4,
+};
+
+// ------------------------------------------------------------------ device buffers
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    void alloc(size_t count, cudaStream_t s);
+    void free_(cudaStream_t s);
+    void ensure(size_t count, cudaStream_t s) {
+        if (count > n) {
+            free_(s);
+            alloc(count, s);
+        }
+    }
+};
+
+template <class T>
+void DBuf<T>::alloc(size_t count, cudaStream_t s) {
+    n = count;
+    if (count == 0) {
+        p = nullptr;
+        return;
+    }
+    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        n = 0;
+        vj_set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        throw VjError{VJ_ERR_OOM};
+    }
+}
+template <class T>
+void DBuf<T>::free_(cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+}
+
+// ------------------------------------------------------------------ the index
+struct vj_index {
+    int dev = 0;
+    int64_t nx = 0, nq = 0, n = 0;
+    int d = 0, dp = 0;  // dp = d rounded up to a multiple of 4 (16-byte rows)
+    int R = 0, K = 0;
+    vj_metric metric = VJ_L2;
+    vj_params p{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // created by vj_build, destroyed by vj_free
+    int num_sms = VJ_NUM_SMS_HINT;
+
+    DBuf<float> vec;      // [n][dp] FP32, zero padded
+    DBuf<float> sqn;      // [n] squared norm (FP32 of the FP64 value)
+    DBuf<float> invn;     // [n] 1/|v| (cosine), 0 for a zero vector
+    DBuf<int32_t> knn;    // [n][K] exact kNN ids
+    DBuf<float> knnd;     // [n][K] their distance keys (L2: squared distance; cosine: distance)
+    DBuf<int32_t> adj;    // [n][R] -1 padded
+    DBuf<float> elen;     // [n][R] dist(u, v) for data->data edges, NaN otherwise
+    int32_t entry = 0;
+    DBuf<int32_t> parent; // [nq]
+    DBuf<int32_t> order;  // [nq]
+    DBuf<int32_t> depth;  // [nq]
+    int max_depth = 0;
+    int64_t knn_uncertified = 0;  // rows whose tile candidates needed the exact fallback
+
+    // join scratch kept across calls
+    DBuf<int> done;           // [nq] generation stamps of finished queries
+    int gen = 0;
+    DBuf<int32_t> cache;      // [nq]
+    DBuf<int32_t> steps;      // [nq]
+    DBuf<uint8_t> hyb;        // [nq]
+    DBuf<int32_t> count;      // [nq]
+    DBuf<int64_t> seg;        // [nq] start of each query's results in the pool
+    DBuf<int32_t> pool_id;    // result pool
+    DBuf<float> pool_d;
+    DBuf<int32_t> wspace;     // per-warp spill space
+    int64_t wspace_warps = 0;
+    DBuf<unsigned long long> ctr;  // counters + ticket + error word
+    DBuf<int64_t> offsets;    // [nq+1]
+    DBuf<int32_t> out_id;
+    DBuf<float> out_d;
+    DBuf<unsigned char> tmp;  // scan / sort temporary storage
+};
+
+// ------------------------------------------------------------------ launchers (host)
+// tiles: kNN over all nodes of the index; fills ix->knn / ix->knnd
+void vj_build_knn(vj_index* ix);
+// graph: prune + reverse edges + entry + edge lengths + MST order
+void vj_build_graph(vj_index* ix);
+// exact join pairs into CSR (device arrays owned by the caller-provided buffers)
+struct CsrOut {
+    int64_t nnz;
+};
+void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids,
+                          DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
+// approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
+void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
+
+// utilities
+void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix);
+void vj_segment_sort_copy(const int64_t* src_start, const int32_t* counts, const int64_t* offsets,
+                          const int32_t* src_id, const float* src_d, int32_t* dst_id, float* dst_d,
+                          int64_t nseg, vj_index* ix);
+
+inline int vj_div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -1,0 +1,281 @@
+"""Python binding of libvj.so (include/vj.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the CUDA library; no step of a
+build or a join runs in Python.  ``load()`` raises ``VjLibraryMissing`` when
+the library has not been built (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvj.so")
+
+VJ_OK, VJ_ERR_ARG, VJ_ERR_OOM, VJ_ERR_CUDA, VJ_ERR_TIMEOUT, VJ_ERR_STATE = range(6)
+VJ_L2, VJ_COSINE = 0, 1
+VJ_WS_NONE, VJ_WS_HARD, VJ_WS_SOFT, VJ_WS_SELF = 0, 1, 2, 3
+VJ_PREC_FP32, VJ_PREC_BF16, VJ_PREC_FP8 = 0, 1, 2
+
+# every function declared in include/vj.h
+EXPORTS = ["vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_join",
+           "vj_join_device", "vj_join_exact", "vj_export_graph", "vj_export_knn", "vj_index_info",
+           "vj_result_free", "vj_free", "vj_last_error"]
+
+
+class VjLibraryMissing(RuntimeError):
+    pass
+
+
+class VjError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"vj status {status}: {msg}")
+        self.status = status
+
+
+class vj_params(C.Structure):
+    _fields_ = [("degree", C.c_int), ("knn_k", C.c_int), ("greedy_beam", C.c_int), ("conv_threshold", C.c_int),
+                ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
+                ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
+                ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64)]
+
+
+class vj_stats(C.Structure):
+    _fields_ = [("dist_computations", C.c_int64), ("expansions", C.c_int64), ("adj_rows_read", C.c_int64),
+                ("hybrid_queries", C.c_int64), ("rechecks", C.c_int64), ("spill_queries", C.c_int64),
+                ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
+                ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+class vj_result(C.Structure):
+    _fields_ = [("nq", C.c_int64), ("nnz", C.c_int64), ("offsets", C.POINTER(C.c_int64)),
+                ("ids", C.POINTER(C.c_int32)), ("dists", C.POINTER(C.c_float)), ("steps", C.POINTER(C.c_int32)),
+                ("cache", C.POINTER(C.c_int32)), ("hybrid", C.POINTER(C.c_uint8)), ("on_device", C.c_int),
+                ("stats", vj_stats)]
+
+
+_lib = None
+
+
+def load():
+    """Load libvj.so (raises VjLibraryMissing if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise VjLibraryMissing(f"{LIB_PATH} is missing: run paper_2603_16360_b300/build.py (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    P, I64, I = C.c_void_p, C.c_int64, C.c_int
+    lib.vj_default_params.argtypes = [C.POINTER(vj_params)]
+    lib.vj_default_params.restype = None
+    lib.vj_build.argtypes = [P, I64, P, I64, I, I, C.POINTER(vj_params), C.POINTER(P)]
+    lib.vj_build.restype = I
+    lib.vj_set_stream.argtypes = [P, P]
+    lib.vj_set_stream.restype = I
+    lib.vj_set_join_params.argtypes = [P, C.POINTER(vj_params)]
+    lib.vj_set_join_params.restype = I
+    for fn in ("vj_join", "vj_join_device"):
+        getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
+        getattr(lib, fn).restype = I
+    lib.vj_join_exact.argtypes = [P, C.c_float, C.POINTER(C.POINTER(vj_result))]
+    lib.vj_join_exact.restype = I
+    lib.vj_export_graph.argtypes = [P, P, P, P, P, P]
+    lib.vj_export_graph.restype = I
+    lib.vj_export_knn.argtypes = [P, P, P]
+    lib.vj_export_knn.restype = I
+    lib.vj_index_info.argtypes = [P, P, P, P, P, P, P]
+    lib.vj_index_info.restype = I
+    lib.vj_result_free.argtypes = [C.POINTER(vj_result)]
+    lib.vj_result_free.restype = None
+    lib.vj_free.argtypes = [P]
+    lib.vj_free.restype = None
+    lib.vj_last_error.argtypes = []
+    lib.vj_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != VJ_OK:
+        raise VjError(st, load().vj_last_error().decode(errors="replace"))
+
+
+def default_params(**kw) -> vj_params:
+    p = vj_params()
+    load().vj_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@dataclass
+class Result:
+    """Host copy of a vj_result (CSR by query plus per-query arrays)."""
+    offsets: np.ndarray
+    ids: np.ndarray
+    dists: np.ndarray
+    steps: np.ndarray
+    cache: np.ndarray
+    hybrid: np.ndarray
+    stats: dict = field(default_factory=dict)
+
+    def row(self, q):
+        return self.ids[self.offsets[q]:self.offsets[q + 1]]
+
+
+def _stats(s: vj_stats) -> dict:
+    return {name: getattr(s, name) for name, _ in vj_stats._fields_}
+
+
+def _host_result(rp) -> Result:
+    r = rp.contents
+    nq, nnz = r.nq, r.nnz
+
+    def arr(ptr, n, dt):
+        return np.ctypeslib.as_array(ptr, shape=(max(n, 1),))[:n].astype(dt, copy=True)
+
+    out = Result(arr(r.offsets, nq + 1, np.int64), arr(r.ids, nnz, np.int32), arr(r.dists, nnz, np.float32),
+                 arr(r.steps, nq, np.int32), arr(r.cache, nq, np.int32), arr(r.hybrid, nq, np.uint8),
+                 _stats(r.stats))
+    load().vj_result_free(rp)
+    return out
+
+
+class DeviceResult:
+    """A vj_result whose arrays live in device memory; free() releases it."""
+
+    def __init__(self, rp):
+        self._rp = rp
+        r = rp.contents
+        self.nq, self.nnz, self.stats = r.nq, r.nnz, _stats(r.stats)
+        self.offsets_ptr = C.cast(r.offsets, C.c_void_p).value
+        self.ids_ptr = C.cast(r.ids, C.c_void_p).value
+        self.dists_ptr = C.cast(r.dists, C.c_void_p).value
+
+    def free(self):
+        if self._rp is not None:
+            load().vj_result_free(self._rp)
+            self._rp = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Index:
+    """An opaque vj_index built by vj_build (offline merged-index build)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        nx, nq = C.c_int64(), C.c_int64()
+        d, deg, k, md = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(load().vj_index_info(self._h, C.byref(nx), C.byref(nq), C.byref(d), C.byref(deg), C.byref(k),
+                                    C.byref(md)))
+        return {"nx": nx.value, "nq": nq.value, "d": d.value, "degree": deg.value, "knn_k": k.value,
+                "max_depth": md.value}
+
+    def free(self):
+        if self._h:
+            load().vj_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vj_build(X, Q, metric: int = VJ_L2, params: vj_params | None = None, **kw) -> Index:
+    """Build the merged index over data X [nx, d] and queries Q [nq, d].
+
+    X and Q may be numpy arrays (host) or CUDA tensors exposing
+    ``data_ptr()`` (device, float32, contiguous).
+    """
+    lib = load()
+    p = params if params is not None else default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    if hasattr(X, "data_ptr"):
+        assert X.is_cuda and Q.is_cuda and X.is_contiguous() and Q.is_contiguous()
+        p.input_on_device = 1
+        xp, qp = X.data_ptr(), Q.data_ptr()
+        nx, d = X.shape
+        nq = Q.shape[0]
+        keep = (X, Q)
+    else:
+        X = np.ascontiguousarray(X, np.float32)
+        Q = np.ascontiguousarray(Q, np.float32)
+        p.input_on_device = 0
+        xp, qp = X.ctypes.data, Q.ctypes.data
+        nx, d = X.shape
+        nq = Q.shape[0]
+        keep = (X, Q)
+    h = C.c_void_p()
+    _check(lib.vj_build(xp, nx, qp, nq, d, metric, C.byref(p), C.byref(h)))
+    del keep
+    return Index(h)
+
+
+def vj_set_stream(ix: Index, stream_ptr: int):
+    _check(load().vj_set_stream(ix.handle, C.c_void_p(stream_ptr)))
+
+
+def vj_set_join_params(ix: Index, params: vj_params | None = None, **kw):
+    p = params if params is not None else default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    _check(load().vj_set_join_params(ix.handle, C.byref(p)))
+
+
+def vj_join(ix: Index, eps: float, budget: int = 0) -> Result:
+    rp = C.POINTER(vj_result)()
+    _check(load().vj_join(ix.handle, float(eps), int(budget), C.byref(rp)))
+    return _host_result(rp)
+
+
+def vj_join_device(ix: Index, eps: float, budget: int = 0) -> DeviceResult:
+    rp = C.POINTER(vj_result)()
+    _check(load().vj_join_device(ix.handle, float(eps), int(budget), C.byref(rp)))
+    return DeviceResult(rp)
+
+
+def vj_join_exact(ix: Index, eps: float) -> Result:
+    rp = C.POINTER(vj_result)()
+    _check(load().vj_join_exact(ix.handle, float(eps), C.byref(rp)))
+    return _host_result(rp)
+
+
+def vj_export_graph(ix: Index):
+    """(adj [n, R], entry, parent [nq], order [nq], depth [nq])."""
+    inf = ix.info()
+    n = inf["nx"] + inf["nq"]
+    adj = np.zeros((n, inf["degree"]), np.int32)
+    par = np.zeros(inf["nq"], np.int32)
+    order = np.zeros(inf["nq"], np.int32)
+    depth = np.zeros(inf["nq"], np.int32)
+    entry = C.c_int32()
+    _check(load().vj_export_graph(ix.handle, adj.ctypes.data, C.addressof(entry), par.ctypes.data,
+                                  order.ctypes.data, depth.ctypes.data))
+    return adj, entry.value, par, order, depth
+
+
+def vj_export_knn(ix: Index):
+    """(ids [n, K], keys [n, K]); keys are squared distances for L2."""
+    inf = ix.info()
+    n = inf["nx"] + inf["nq"]
+    ids = np.zeros((n, inf["knn_k"]), np.int32)
+    keys = np.zeros((n, inf["knn_k"]), np.float32)
+    _check(load().vj_export_knn(ix.handle, ids.ctypes.data, keys.ctypes.data))
+    return ids, keys

@@ -1,0 +1,79 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/vj.h declares, and rejects bad arguments before touching
+the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2603_16360_b300 import vj
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "vj.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vj_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    lib = vj.load()
+    declared = _header_functions()
+    assert len(declared) >= 10
+    assert sorted(vj.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_default_params():
+    p = vj.default_params()
+    assert (p.degree, p.knn_k, p.greedy_beam, p.conv_threshold, p.hybrid_beam) == (32, 64, 256, 10, 256)
+    assert p.work_sharing == vj.VJ_WS_SOFT and p.adapt_hybrid == 1 and p.force_hybrid == 0
+
+
+def test_build_rejects_bad_arguments_before_device_work():
+    lib = vj.load()
+    h = C.c_void_p()
+    p = vj.default_params()
+    import numpy as np
+    X = np.zeros((4, 3), np.float32)
+    cases = [
+        (None, 4, X.ctypes.data, 4, 3, 0),       # NULL X
+        (X.ctypes.data, 0, X.ctypes.data, 4, 3, 0),  # nx = 0
+        (X.ctypes.data, 4, X.ctypes.data, 4, 0, 0),  # d = 0
+        (X.ctypes.data, 4, X.ctypes.data, 4, 3, 7),  # metric
+    ]
+    for xp, nx, qp, nq, d, metric in cases:
+        st = lib.vj_build(xp, nx, qp, nq, d, metric, C.byref(p), C.byref(h))
+        assert st == vj.VJ_ERR_ARG
+        assert h.value is None
+        assert len(lib.vj_last_error()) > 0
+    bad = vj.default_params(degree=64)
+    assert lib.vj_build(X.ctypes.data, 4, X.ctypes.data, 4, 3, 0, C.byref(bad), C.byref(h)) == vj.VJ_ERR_ARG
+    bad = vj.default_params(work_sharing=vj.VJ_WS_HARD)
+    assert lib.vj_build(X.ctypes.data, 4, X.ctypes.data, 4, 3, 0, C.byref(bad), C.byref(h)) == vj.VJ_ERR_ARG
+    assert b"HARD" in lib.vj_last_error()
+
+
+def test_join_and_free_reject_null():
+    lib = vj.load()
+    rp = C.POINTER(vj.vj_result)()
+    assert lib.vj_join(None, 1.0, 0, C.byref(rp)) == vj.VJ_ERR_ARG
+    assert lib.vj_join_device(None, 1.0, 0, C.byref(rp)) == vj.VJ_ERR_ARG
+    assert lib.vj_join_exact(None, 1.0, C.byref(rp)) == vj.VJ_ERR_ARG
+    assert lib.vj_export_graph(None, None, None, None, None, None) == vj.VJ_ERR_ARG
+    lib.vj_result_free(None)
+    lib.vj_free(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The binding and the CUDA sources never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_2603_16360_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "vj_oracle" not in txt and "vjo_" not in txt, f

@@ -1,0 +1,205 @@
+"""GPU path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (element by element):
+  * exact kNN lists: ids bit-exact (ties by id), keys within 1e-5 relative;
+  * graph built from the same kNN lists: adjacency, entry and MST parents
+    bit-exact (the oracle ingests the GPU's kNN lists / graph, so each stage is
+    checked on identical inputs);
+  * merged-index joins on the GPU graph: per-query result sets, distance
+    evaluations ("steps"), the soft cache C[q] and the hybrid decision equal the
+    oracle's; pair distances within 1e-5 relative;
+  * exact join: pair ids equal outside the |dist - eps| <= 1e-4 eps band.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_16360_b300 import inputs
+from paper_2603_16360_b300 import vj
+
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-4
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16360_b300 import build as b
+    b.build()
+    vj.load()
+
+
+def _calib_eps(oracle, w, matches, metric=0, sample=200):
+    """eps whose exact join has about `matches` pairs per query on a sample."""
+    from scipy.spatial.distance import cdist
+    Qs = w.Q[:sample].astype(np.float64)
+    D = cdist(Qs, w.X.astype(np.float64), "euclidean" if metric == 0 else "cosine")
+    k = int(matches * len(Qs))
+    return float(np.partition(D.ravel(), k)[k])
+
+
+def _pairs(off, ids):
+    return {(q, int(i)) for q in range(len(off) - 1) for i in ids[off[q]:off[q + 1]]}
+
+
+def _band_pairs(oracle, w, eps, metric):
+    """Pairs whose FP64 distance lies within the eps band (excluded from equality)."""
+    from scipy.spatial.distance import cdist
+    D = cdist(w.Q.astype(np.float64), w.X.astype(np.float64), "euclidean" if metric == 0 else "cosine")
+    qs, xs = np.nonzero(np.abs(D - eps) <= BAND * eps)
+    return set(zip(qs.tolist(), xs.tolist()))
+
+
+def _build(w, **kw):
+    p = vj.default_params(degree=w.degree, knn_k=w.knn_k)
+    return vj.vj_build(w.X, w.Q, metric=w.metric, params=p, **kw)
+
+
+CASES = {
+    "gauss_small": lambda: inputs.gauss_small(seed=101, nx=3000, nq=300, d=32),
+    "sift_like_small": lambda: inputs.sift_like(seed=102, scale=0.003),  # 3000 x 128 ints, 300 queries
+    "ragged_d37": lambda: inputs.uniform_small(103, 1500, 200, 37, degree=12, knn_k=24),
+    "cosine_d20": lambda: inputs.uniform_small(104, 1500, 150, 20, metric=1, degree=16, knn_k=32),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def built(request, oracle):
+    w = CASES[request.param]()
+    ix = _build(w)
+    yield request.param, w, ix
+    ix.free()
+
+
+def test_knn_bit_exact(built, oracle):
+    name, w, ix = built
+    ids, keys = vj.vj_export_knn(ix)
+    n = w.nx + w.nq
+    K = ids.shape[1]
+    o_ids, o_d = oracle.knn_rows(w.X, w.Q, K, np.arange(n), w.metric)
+    mism = np.nonzero((ids != o_ids).any(axis=1))[0]
+    assert len(mism) == 0, f"{name}: {len(mism)} rows differ, first {mism[:5]}"
+    ref = o_d ** 2 if w.metric == 0 else o_d
+    np.testing.assert_allclose(keys, ref, rtol=1e-5, atol=1e-6)
+
+
+def test_graph_and_mst_match_oracle_on_same_knn(built, oracle):
+    name, w, ix = built
+    kn, _ = vj.vj_export_knn(ix)
+    adj, entry, parent, order, depth = vj.vj_export_graph(ix)
+    o_adj, o_entry, _ = oracle.build_graph(w.X, w.Q, adj.shape[1], kn.shape[1], w.metric, knn_ids=kn)
+    assert entry == o_entry
+    mism = np.nonzero((adj != o_adj).any(axis=1))[0]
+    assert len(mism) == 0, f"{name}: {len(mism)} adjacency rows differ, first {mism[:5]}"
+    o_par, o_order, o_depth, _ = oracle.mst(w.X, w.Q, adj, entry, w.metric)
+    np.testing.assert_array_equal(parent, o_par)
+    np.testing.assert_array_equal(depth, o_depth)
+    # the GPU order is topological
+    pos = np.empty(w.nq, np.int64)
+    pos[order] = np.arange(w.nq)
+    has = parent >= 0
+    assert np.all(pos[parent[has]] < pos[np.nonzero(has)[0]])
+
+
+JOIN_MODES = [
+    ("mi_self", dict(work_sharing=vj.VJ_WS_SELF, adapt_hybrid=0)),
+    ("mi_sws", dict(work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0)),
+    ("mi_sws_adapt", dict(work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1)),
+    ("mi_force_hybrid_64", dict(work_sharing=vj.VJ_WS_SELF, adapt_hybrid=0, force_hybrid=1, hybrid_beam=64)),
+    ("mi_sws_force_hybrid_8", dict(work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=1, hybrid_beam=8)),
+]
+
+
+@pytest.mark.parametrize("mode,kw", JOIN_MODES, ids=[m for m, _ in JOIN_MODES])
+def test_join_matches_oracle_on_gpu_graph(built, oracle, mode, kw):
+    name, w, ix = built
+    eps = _calib_eps(oracle, w, 10, w.metric)
+    vj.vj_set_join_params(ix, **kw)
+    r = vj.vj_join(ix, eps)
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    ws = {vj.VJ_WS_SELF: oracle.WS_SELF, vj.VJ_WS_SOFT: oracle.WS_SOFT}[kw["work_sharing"]]
+    o = oracle.join(w.X, w.Q, adj, entry, np.float32(eps), metric=w.metric, work_sharing=ws,
+                    force_hybrid=bool(kw.get("force_hybrid", 0)), adapt_hybrid=bool(kw.get("adapt_hybrid", 0)),
+                    hybrid_beam_size=kw.get("hybrid_beam", 256), order=order, parent=parent)
+    band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+    g, e = _pairs(r.offsets, r.ids), _pairs(o.offsets, o.ids)
+    diff = (g ^ e) - band
+    assert not diff, f"{name}/{mode}: {len(diff)} pairs differ, e.g. {sorted(diff)[:5]}"
+    np.testing.assert_array_equal(r.hybrid, o.hybrid)
+    np.testing.assert_array_equal(r.cache, o.cache)
+    np.testing.assert_array_equal(r.steps, o.steps)
+    # distances of common pairs
+    gd = {(q, int(i)): r.dists[r.offsets[q] + j] for q in range(w.nq) for j, i in enumerate(r.row(q))}
+    od = {(q, int(i)): o.dists[o.offsets[q] + j] for q in range(w.nq) for j, i in enumerate(o.row(q))}
+    com = list(set(gd) & set(od))
+    a = np.array([gd[k] for k in com], np.float64)
+    b = np.array([od[k] for k in com], np.float64)
+    np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6)
+    assert r.stats["dist_computations"] == int(o.steps.sum())
+
+
+def test_exact_join_matches_nlj(built, oracle):
+    name, w, ix = built
+    eps = _calib_eps(oracle, w, 10, w.metric)
+    r = vj.vj_join_exact(ix, eps)
+    off, ids, dd = oracle.nlj(w.X, w.Q, float(np.float32(eps)), w.metric)
+    band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+    diff = (_pairs(r.offsets, r.ids) ^ _pairs(off, ids)) - band
+    assert not diff, f"{name}: {len(diff)} pairs differ"
+    if len(r.ids) == len(ids) and np.array_equal(r.ids, ids):
+        np.testing.assert_allclose(r.dists, dd, rtol=1e-5, atol=1e-6)
+
+
+def test_recall_of_join_is_reported_against_exact(built, oracle):
+    name, w, ix = built
+    eps = _calib_eps(oracle, w, 10, w.metric)
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1)
+    r = vj.vj_join(ix, eps)
+    ex = vj.vj_join_exact(ix, eps)
+    rec, _ = oracle.recall(r.offsets, r.ids, ex.offsets, ex.ids)
+    assert 0.0 < rec <= 1.0
+    # every returned pair is a true pair
+    assert _pairs(r.offsets, r.ids) <= _pairs(ex.offsets, ex.ids) | _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_query_and_duplicates(oracle):
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((400, 16)).astype(np.float32)
+    Q = X[:1].copy()  # the query coincides with a data point
+    ix = vj.vj_build(X, Q, params=vj.default_params(degree=8, knn_k=16))
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    for ws in (vj.VJ_WS_SELF, vj.VJ_WS_SOFT):
+        vj.vj_set_join_params(ix, work_sharing=ws, adapt_hybrid=1)
+        r = vj.vj_join(ix, 2.5)
+        o = oracle.join(X, Q, adj, entry, 2.5, work_sharing={vj.VJ_WS_SELF: oracle.WS_SELF, vj.VJ_WS_SOFT: oracle.WS_SOFT}[ws],
+                        adapt_hybrid=True, order=order, parent=parent)
+        assert _pairs(r.offsets, r.ids) == _pairs(o.offsets, o.ids)
+        np.testing.assert_array_equal(r.steps, o.steps)
+    ix.free()
+
+
+def test_tiny_sets_and_empty_results(oracle):
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((5, 4)).astype(np.float32)
+    Q = rng.standard_normal((3, 4)).astype(np.float32) + 100.0  # far away: empty rows
+    ix = vj.vj_build(X, Q, params=vj.default_params(degree=4, knn_k=6))
+    r = vj.vj_join(ix, 0.5)
+    assert r.offsets[-1] == 0 and len(r.ids) == 0
+    ex = vj.vj_join_exact(ix, 0.5)
+    assert ex.offsets[-1] == 0
+    ix.free()
+
+
+def test_errors_are_reported_not_raised_on_device():
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((50, 8)).astype(np.float32)
+    ix = vj.vj_build(X, X[:5].copy(), params=vj.default_params(degree=8, knn_k=16))
+    with pytest.raises(vj.VjError) as e:
+        vj.vj_join(ix, -1.0)
+    assert e.value.status == vj.VJ_ERR_ARG
+    r = vj.vj_join(ix, 1.0)  # the index stays usable
+    assert r.offsets.shape == (6,)
+    ix.free()
