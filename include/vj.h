@@ -144,6 +144,28 @@ vj_status vj_join_device(vj_index *ix, float eps, int budget, vj_result **out);
  * eps are re-decided in FP64. */
 vj_status vj_join_exact(vj_index *ix, float eps, vj_result **out);
 
+/* Exact join for callers that cannot allocate device memory (the paper has no
+ * counterpart: this is a deployment variant of vj_join_exact).  Callers that
+ * live inside a fixed, pre-carved device-memory budget, or that cannot afford
+ * cudaMalloc/cudaFree (allocator locks, device-wide synchronization), pass
+ * every buffer themselves; the call allocates nothing.
+ *   X [nx*d], Q [nq*d]: device pointers, row-major float32 (no index needed).
+ *   offsets [nq+1] (device, int64): CSR row offsets, always written in full.
+ *   ids [cap] (device, int32), dists [cap] (device, float32): pairs in
+ *   ascending data id per query; pairs beyond cap are not written.
+ *   nnz (host): total number of pairs.  stream: a cudaStream_t or NULL.
+ * Scratch is a fixed 4 MiB device array inside the library, which limits nq
+ * to 1,048,576 (larger nq -> VJ_ERR_ARG) and is held by every GPU that loads
+ * the library until exit.  All calls share that array: calls that overlap on
+ * the GPU race and give wrong results.  The first call on a device looks up
+ * the array's address (cudaGetSymbolAddress) and should come before any
+ * stream capture on that device.  Returns VJ_ERR_STATE when nnz > cap.
+ * Decisions: FP32 keys, re-decided in FP64 within the FP32 rounding bound
+ * of eps (same rule as vj_join_exact). */
+vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int64_t nq, int d,
+                                vj_metric metric, float eps, int64_t *offsets, int32_t *ids,
+                                float *dists, int64_t cap, int64_t *nnz, void *stream);
+
 /* Copy the built graph to host buffers (any may be NULL):
  *   adj [(nx+nq) * R] int32 (-1 padded), entry (1 value),
  *   parent [nq] (MST parent query index, -1 = entry), order [nq]

@@ -22,8 +22,10 @@ VJ_PREC_FP32, VJ_PREC_BF16, VJ_PREC_FP8 = 0, 1, 2
 
 # every function declared in include/vj.h
 EXPORTS = ["vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_join",
-           "vj_join_device", "vj_join_exact", "vj_export_graph", "vj_export_knn", "vj_index_info",
-           "vj_result_free", "vj_free", "vj_last_error"]
+           "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
+           "vj_index_info", "vj_result_free", "vj_free", "vj_last_error"]
+
+NOALLOC_MAX_QUERIES = 1 << 20
 
 
 class VjLibraryMissing(RuntimeError):
@@ -82,6 +84,8 @@ def load():
         getattr(lib, fn).restype = I
     lib.vj_join_exact.argtypes = [P, C.c_float, C.POINTER(C.POINTER(vj_result))]
     lib.vj_join_exact.restype = I
+    lib.vj_join_exact_noalloc.argtypes = [P, I64, P, I64, I, I, C.c_float, P, P, P, I64, C.POINTER(C.c_int64), P]
+    lib.vj_join_exact_noalloc.restype = I
     lib.vj_export_graph.argtypes = [P, P, P, P, P, P]
     lib.vj_export_graph.restype = I
     lib.vj_export_knn.argtypes = [P, P, P]
@@ -255,6 +259,25 @@ def vj_join_exact(ix: Index, eps: float) -> Result:
     rp = C.POINTER(vj_result)()
     _check(load().vj_join_exact(ix.handle, float(eps), C.byref(rp)))
     return _host_result(rp)
+
+
+def vj_join_exact_noalloc(X, Q, eps: float, offsets, ids, dists, metric: int = VJ_L2, stream_ptr: int = 0) -> int:
+    """Exact join into caller-owned device buffers, allocating nothing.
+
+    For callers that cannot allocate device memory (a fixed pre-carved memory
+    budget, or no tolerance for cudaMalloc/cudaFree locks and syncs).  X, Q,
+    offsets (int64, nq+1), ids (int32) and dists (float32) are CUDA tensors the
+    caller owns; returns the pair count.  Raises VjError (VJ_ERR_STATE) when the
+    pairs exceed len(ids); offsets are complete even then.
+    """
+    nx, d = X.shape
+    nq = Q.shape[0]
+    nnz = C.c_int64(0)
+    cap = min(ids.numel(), dists.numel())
+    _check(load().vj_join_exact_noalloc(X.data_ptr(), nx, Q.data_ptr(), nq, d, metric, float(eps),
+                                        offsets.data_ptr(), ids.data_ptr(), dists.data_ptr(), cap, C.byref(nnz),
+                                        C.c_void_p(stream_ptr)))
+    return nnz.value
 
 
 def vj_export_graph(ix: Index):
