@@ -143,14 +143,15 @@ def sample_subtrees(parent, order, target=1000):
     return np.array([q for q in order if int(q) in chosen], np.int32)
 
 
-def run_cpu_oracle(w, vj, ix, target, sample_q=1000, repeats=1):
+def run_cpu_oracle(w, vj, ix, eps, sample_q=1000, repeats=1, mode="adapt", budget=256):
     import oracle
     adj, entry, parent, order, _ = vj.vj_export_graph(ix)
     sub = sample_subtrees(parent, order, sample_q)
     t0 = time.perf_counter()
     for _ in range(repeats):
-        oracle.join(w.X, w.Q, adj, entry, target, work_sharing=oracle.WS_SOFT, adapt_hybrid=True,
-                    order=sub, parent=parent, queries=sub)
+        oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SOFT, adapt_hybrid=(mode == "adapt"),
+                    force_hybrid=(mode == "force"), hybrid_beam_size=budget, order=sub, parent=parent,
+                    queries=sub)
     dt = (time.perf_counter() - t0) / repeats
     return len(sub), dt
 
@@ -191,26 +192,30 @@ def main():
     eps = calibrate_eps(vj, ix, w, target)
     ex = vj.vj_join_exact(ix, eps)
 
-    # operating point: plain FP32 MI+SWS with the adaptive hybrid rule; the
-    # hybrid budget grows until recall >= 0.95
+    # operating point: plain FP32 MI+SWS with the adaptive hybrid rule; if its
+    # recall is below 0.95, hybrid search for every query with the smallest
+    # queue size (hybrid_beam_size, the paper's latency-recall knob) that
+    # reaches 0.95
     op = None
-    for budget in (256, 512, 1024, 2048):
-        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1, hybrid_beam=budget)
+    ladder = [("adapt", 256)] + [("force", b) for b in (2, 4, 8, 16, 32, 64, 128, 256)]
+    for mode, budget in ladder:
+        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
+                              force_hybrid=int(mode == "force"), hybrid_beam=budget)
         r = vj.vj_join(ix, eps)
         rec = recall_of(r, ex)
-        op = (budget, rec, r)
+        op = (mode, budget, rec, r)
         if rec >= 0.95:
             break
-    budget, rec, r0 = op
+    mode, budget, rec, r0 = op
     wl_desc = (f"{w.name}: X={w.nx} Q={w.nq} d={w.d} "
                f"{'L2' if w.metric == 0 else 'cosine'}, eps for mean {target:g} matches/query")
 
     if args.impl == "reference":
         n_s, dt = [], []
         for _ in range(args.warmup):
-            run_cpu_oracle(w, vj, ix, eps, 200)
+            run_cpu_oracle(w, vj, ix, eps, 200, mode=mode, budget=budget)
         for _ in range(args.steps):
-            n, t = run_cpu_oracle(w, vj, ix, eps, 1000)
+            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, mode=mode, budget=budget)
             n_s.append(n)
             dt.append(t)
         v = sum(n_s) / sum(dt)
@@ -218,8 +223,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dt) / len(dt),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": wl_desc, "arm": "CPU oracle MI+SWS+Adapt (Alg. 1), FP64, 1 thread",
-                           "eps": eps, "budget": budget},
+                "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS hybrid={mode} (Alg. 1), FP64, 1 thread",
+                           "eps": eps, "hybrid": mode, "budget": budget},
                 "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                  "sample": f"whole MST subtrees, {n_s[0]} queries per step, on the GPU-built graph"},
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,8 +283,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl_desc, "arm": "plain FP32 MI+SWS, adaptive hybrid (learned+BF16 arm not built)",
-                   "recall": rec, "eps": eps, "hybrid_budget": budget, "degree": info["degree"],
+        "config": {"workload": wl_desc,
+                   "arm": f"plain FP32 MI+SWS, hybrid={mode} beam {budget} (learned+BF16 arm not built)",
+                   "recall": rec, "eps": eps, "hybrid": mode, "hybrid_budget": budget, "degree": info["degree"],
                    "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "pairs": int(pairs),
                    "pairs_per_s": world * pairs / (step_ms / 1e3), "build_s": build_s,
                    "l2": "inputs larger than L2 (vectors %.0f MB)" % (w.X.nbytes / 1e6 + w.Q.nbytes / 1e6),
@@ -293,10 +299,10 @@ def main():
         "gpu_launches": int(launches),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt = run_cpu_oracle(w, vj, ix, eps, 1000)
+        n, dt = run_cpu_oracle(w, vj, ix, eps, 1000, mode=mode, budget=budget)
         line["cpu_baseline"] = {"value": n / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} queries (whole MST subtrees) of the same workload on the GPU-built "
-                                          f"graph, oracle MI+SWS+Adapt join, FP64, single thread"}
+                                          f"graph, oracle MI+SWS join (hybrid={mode}, beam {budget}), FP64, single thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ix.free()

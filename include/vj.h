@@ -85,6 +85,8 @@ typedef struct {
     double ms_total;           /* device time of the whole join */
     int64_t bytes_algorithmic; /* vector + adjacency bytes the traversal must read */
     int64_t kernel_launches;   /* kernels this call launched */
+    double ms_scan;            /* device time of the tensor-core brute-force scan (exact join / routed queries) */
+    int64_t scan_candidates;   /* pairs the scan passed to the exact re-check */
 } vj_stats;
 
 /* CSR result of a join.  ids are data ids (0..nx-1), ascending within each

@@ -1,5 +1,5 @@
 // k_join.cu -- the online merged-index join (Alg. 1 with Alg. 3-8), one warp
-// per query, persistent grid fed by a device ticket counter.
+// per query, persistent grid fed by a device ready queue.
 //
 // Per query q (merged node id qn = nx + qi), following Alg. 1's order:
 //   Seed (Alg. 3)      S = {entry} (+ C[parent] under soft sharing) (+ q for
@@ -16,22 +16,26 @@
 //                      depend on pop order, so it runs frontier-parallel
 //                      (several nodes' neighbour lists per batch).  Hybrid:
 //                      exact pop order (in-range points first, then the
-//                      bounded out-range queue, (key, id) order) with the
-//                      trim-after-insert rule.
+//                      bounded out-range queue, (key, id) order).  The
+//                      insert-then-trim rule is applied per neighbour list as a
+//                      batch: the queue after a list equals the k smallest of
+//                      (queue U list's out-range nodes), k given by the size
+//                      recurrence of the per-insert rule (each trim removes the
+//                      current maximum, so no removed key can be smaller than a
+//                      kept one).
 //   UpdateCache (8)    C[q] = closest visited data node, ties by id, FP64
-//                      re-decided among FP32 near-ties; then q is published
-//                      (release) so its MST children can start.
+//                      re-decided among FP32 near-ties.
 //
-// Work sharing dependencies: queries are taken in a topological order of the
-// MST (BFS by depth), so a query's parent was taken earlier by a running warp;
-// the child spins (bounded, with back-off) on the parent's done stamp.  On
-// timeout the kernel records VJ_DERR_WAIT_TIMEOUT, raises an abort flag and
-// every warp returns.
+// Work sharing: a query is dispatched only once its MST parent is done.  The
+// ready queue starts with the roots; a finished query appends its children
+// (release stores) and warps take slots in order (acquire loads, bounded
+// spin).  A slot is only awaited when no ready query exists.
 //
-// Visited set: open-addressing hash in shared memory (HCAP slots, spills to a
-// per-warp global table above half load).  Results: shared-memory list
-// (RCAP) spilling to per-warp global memory.  In-range decisions whose FP32 key
-// lies within the FP32 rounding bound of eps are re-decided in FP64.
+// Visited set: open-addressing hash in shared memory (HCAP slots), moved on
+// overflow to a per-warp global table that grows by 4x (two alternating
+// regions).  Results: shared-memory list (RCAP) spilling to global memory.
+// In-range decisions whose FP32 key lies within the FP32 rounding bound of eps
+// are re-decided in FP64.
 #include <float.h>
 
 #include "vj_device.cuh"
@@ -39,10 +43,12 @@
 
 namespace {
 
-constexpr int WPB = 8;     // warps per block
-constexpr int HCAP = 2048; // shared-memory visited slots per warp
-constexpr int RCAP = 256;  // shared-memory result slots per warp
-constexpr int CCAP = 128;  // candidate slots per batch
+constexpr int WPB = 8;      // warps per block
+constexpr int HCAP = 2048;  // shared-memory visited slots per warp
+constexpr int RCAP = 256;   // shared-memory result slots per warp
+constexpr int CCAP = 128;   // candidate slots per batch
+constexpr int FB = 4;       // frontier nodes per BFS batch (FB * 32 <= CCAP)
+constexpr int GCAP0 = 8192; // first global visited table
 
 struct WarpSmem {
     int htab[HCAP];
@@ -63,7 +69,8 @@ enum {
     C_RECHK = 7,
     C_SPILL = 8,
     C_ABORT = 9,
-    C_NUM = 10
+    C_TAIL = 10,
+    C_NUM = 11
 };
 
 struct JoinParams {
@@ -71,8 +78,10 @@ struct JoinParams {
     const float* invn;
     const int32_t* adj;
     const float* elen;
-    const int32_t* order;
     const int32_t* parent;
+    const int32_t* child_off;
+    const int32_t* child_list;
+    int* ready;
     int64_t nx, nq;
     int dp4, dp, d, R, metric;
     int32_t entry;
@@ -82,8 +91,6 @@ struct JoinParams {
     float tie_tol;  // keys closer than this (relative / absolute) are re-decided in FP64
     double eps64;
     int32_t* cache;
-    int* done;
-    int gen;
     int32_t* steps;
     uint8_t* hyb;
     int32_t* count;
@@ -93,8 +100,9 @@ struct JoinParams {
     int64_t pool_cap;
     int32_t* wspace;
     int64_t wstride;
-    int gcap;   // global visited slots per warp (power of two)
-    int oqcap;  // out-range queue capacity
+    int gmax;   // slots of each global visited region (power of two)
+    int grcap;  // global result slots per warp
+    int oqcap;  // out-range queue capacity (per buffer)
     unsigned long long* ctr;
     long long spin_limit;
 };
@@ -106,12 +114,21 @@ __device__ __forceinline__ float key_to_dist(const JoinParams& P, float k) {
     return P.metric == 0 ? sqrtf(fmaxf(k, 0.f)) : k;
 }
 
+struct WarpSpace {
+    int* hA;
+    int* hB;
+    int* grid;
+    float* grd;
+    float* qk[2];
+    int* qi[2];
+};
+
 struct QueryState {
     int* tab;
     unsigned mask;
     int nvis;
     int vislimit;
-    bool vspill;
+    int region;  // -1: shared memory, 0: hA, 1: hB
     int* rid;
     float* rd;
     int rcap;
@@ -131,47 +148,48 @@ __device__ __forceinline__ void raise_err(const JoinParams& P, int code) {
     atomicExch(P.ctr + C_ABORT, 1ull);
 }
 
-// make room for `m` more visited entries (spills shared -> global once)
-__device__ bool vis_reserve(const JoinParams& P, QueryState& s, int m, int* gtab, int lane, long long& c_spill) {
+// make room for `m` more visited entries: move to (or grow) the global table
+__device__ bool vis_reserve(const JoinParams& P, QueryState& s, int m, const WarpSpace& W, int lane,
+                            long long& c_spill) {
     if (s.nvis + m <= s.vislimit) return true;
-    if (s.vspill) {
+    int cap = s.region < 0 ? GCAP0 : (int)(s.mask + 1u) * 4;
+    while (cap / 2 < s.nvis + m && cap <= P.gmax / 4) cap *= 4;
+    if (cap > P.gmax || cap / 2 < s.nvis + m) {
         if (lane == 0) raise_err(P, VJ_DERR_VISITED_OVERFLOW);
         return false;
     }
-    for (int i = lane; i < P.gcap; i += 32) gtab[i] = -1;
+    int* dst = s.region == 0 ? W.hB : W.hA;
+    for (int i = lane; i < cap; i += 32) dst[i] = -1;
     __syncwarp();
-    unsigned gmask = (unsigned)P.gcap - 1u;
-    for (int i = lane; i < HCAP; i += 32) {
+    const unsigned nmask = (unsigned)cap - 1u;
+    const int oldcap = (int)s.mask + 1;
+    for (int i = lane; i < oldcap; i += 32) {
         int k = s.tab[i];
-        if (k >= 0) hash_insert(gtab, gmask, k);
+        if (k >= 0) hash_insert(dst, nmask, k);
     }
     __syncwarp();
-    s.tab = gtab;
-    s.mask = gmask;
-    s.vislimit = P.gcap / 2;
-    s.vspill = true;
-    if (lane == 0) c_spill++;
-    if (s.nvis + m > s.vislimit) {
-        if (lane == 0) raise_err(P, VJ_DERR_VISITED_OVERFLOW);
-        return false;
-    }
+    if (s.region < 0 && lane == 0) c_spill++;
+    s.region = s.region == 0 ? 1 : 0;
+    s.tab = dst;
+    s.mask = nmask;
+    s.vislimit = cap / 2;
     return true;
 }
 
-__device__ bool res_reserve(const JoinParams& P, QueryState& s, int m, int* grid, float* grd, int lane) {
+__device__ bool res_reserve(const JoinParams& P, QueryState& s, int m, const WarpSpace& W, int lane) {
     if (s.nres + m <= s.rcap) return true;
     if (s.rspill) {
         if (lane == 0) raise_err(P, VJ_DERR_RESULT_OVERFLOW);
         return false;
     }
     for (int i = lane; i < s.nres; i += 32) {
-        grid[i] = s.rid[i];
-        grd[i] = s.rd[i];
+        W.grid[i] = s.rid[i];
+        W.grd[i] = s.rd[i];
     }
     __syncwarp();
-    s.rid = grid;
-    s.rd = grd;
-    s.rcap = P.gcap / 2;
+    s.rid = W.grid;
+    s.rd = W.grd;
+    s.rcap = P.grcap;
     s.rspill = true;
     if (s.nres + m > s.rcap) {
         if (lane == 0) raise_err(P, VJ_DERR_RESULT_OVERFLOW);
@@ -194,7 +212,6 @@ __device__ __forceinline__ void best_update(const JoinParams& P, QueryState& s, 
         s.bid = mi;
     }
     const float thr = P.metric == 0 ? s.bk * (1.0f + P.tie_tol) : s.bk + P.tie_tol;
-    const unsigned lt = (1u << lane) - 1u;
     const unsigned km = __ballot_sync(VJ_FULL, lane < s.nt && s.tk <= thr);
     const unsigned am = __ballot_sync(VJ_FULL, valid && k <= thr);
     const unsigned all_old = s.nt >= 32 ? VJ_FULL : ((1u << s.nt) - 1u);
@@ -225,7 +242,6 @@ __device__ __forceinline__ void best_update(const JoinParams& P, QueryState& s, 
             outi = b;
         }
     }
-    (void)lt;
     int total = nk + __popc(am);
     if (total > 8) {
         s.tover = true;
@@ -255,21 +271,52 @@ __device__ __forceinline__ bool inrange_decide(const JoinParams& P, bool valid, 
     return in;
 }
 
-// append in-range candidates (one per lane) to the result list
+// append in-range candidates (one per lane) to the result list (keys stored)
 __device__ __forceinline__ bool append_results(const JoinParams& P, QueryState& s, bool in, int node, float k,
-                                               int* grid, float* grd, int lane) {
+                                               const WarpSpace& W, int lane) {
     unsigned m = __ballot_sync(VJ_FULL, in);
     int cnt = __popc(m);
     if (cnt == 0) return true;
-    if (!res_reserve(P, s, cnt, grid, grd, lane)) return false;
+    if (!res_reserve(P, s, cnt, W, lane)) return false;
     if (in) {
         int pos = s.nres + __popc(m & ((1u << lane) - 1u));
         s.rid[pos] = node;
-        s.rd[pos] = k;  // keys stay keys until the output copy
+        s.rd[pos] = k;
     }
     s.nres += cnt;
     __syncwarp();
     return true;
+}
+
+// warp bitonic sort of one (key, id) per lane, ascending
+__device__ __forceinline__ void warp_sort_pairs(float& k, int& id, int lane) {
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            float pk = __shfl_xor_sync(VJ_FULL, k, j);
+            int pi = __shfl_xor_sync(VJ_FULL, id, j);
+            bool up = (lane & kk) == 0;
+            bool low = (lane & j) == 0;
+            bool pless = kless(pk, pi, k, id);
+            bool take = (low == up) ? pless : !pless;
+            if (take) {
+                k = pk;
+                id = pi;
+            }
+        }
+    }
+}
+
+// number of entries of the ascending list L[0..n) that are less than (k, id)
+__device__ __forceinline__ int lower_rank(const float* Lk, const int* Li, int n, float k, int id) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (kless(Lk[mid], Li[mid], k, id)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int G, int NPL, int U>
@@ -279,14 +326,18 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
     WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
     const int64_t gw = (int64_t)blockIdx.x * WPB + warp;
     int32_t* wbase = P.wspace + gw * P.wstride;
-    int* gtab = wbase;
-    int* grid = wbase + P.gcap;
-    float* grd = reinterpret_cast<float*>(wbase + P.gcap + P.gcap / 2);
-    float* oqk = reinterpret_cast<float*>(wbase + 2 * P.gcap);
-    int* oqi = wbase + 2 * P.gcap + P.oqcap;
+    WarpSpace W;
+    W.hA = wbase;
+    W.hB = wbase + P.gmax;
+    W.grid = wbase + 2 * (int64_t)P.gmax;
+    W.grd = reinterpret_cast<float*>(W.grid + P.grcap);
+    int32_t* qbase = wbase + 2 * (int64_t)P.gmax + 2 * (int64_t)P.grcap;
+    W.qk[0] = reinterpret_cast<float*>(qbase);
+    W.qi[0] = qbase + P.oqcap;
+    W.qk[1] = reinterpret_cast<float*>(qbase + 2 * P.oqcap);
+    W.qi[1] = qbase + 3 * P.oqcap;
     const int g = lane & (G - 1);
     const int R = P.R;
-    const int FB = R <= 32 ? (CCAP / 32) / ((R + 31) / 32) : 1;  // frontier nodes per BFS batch
     long long c_dist = 0, c_exp = 0, c_adj = 0, c_hyb = 0, c_rechk = 0, c_spill = 0;
 
     for (;;) {
@@ -294,35 +345,33 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         if (lane == 0) t = (int)atomicAdd(P.ctr + C_TICKET, 1ull);
         t = __shfl_sync(VJ_FULL, t, 0);
         if (t >= P.nq) break;
-        if (*((volatile unsigned long long*)(P.ctr + C_ABORT))) break;
-        const int qi = P.order[t];
+        // ---- dispatch: wait (bounded) until slot t of the ready queue is filled
+        int qi = -1;
+        if (lane == 0) {
+            long long spins = 0;
+            unsigned ns = 32;
+            for (;;) {
+                qi = ld_acquire(P.ready + t);
+                if (qi >= 0) break;
+                if (*((volatile unsigned long long*)(P.ctr + C_ABORT))) break;
+                if (++spins > P.spin_limit) {
+                    raise_err(P, VJ_DERR_WAIT_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
+            }
+        }
+        qi = __shfl_sync(VJ_FULL, qi, 0);
+        if (qi < 0) break;
         const int64_t qn = P.nx + qi;
 
-        // ---- Alg. 3 SeedPhase (dependency on the MST parent under soft sharing)
+        // ---- Alg. 3 SeedPhase: the parent (if any) finished before q was queued
         int seedc = -1;
         if (P.ws == VJ_WS_SOFT) {
             int par = P.parent[qi];
-            if (par >= 0) {
-                int ok = 1;
-                if (lane == 0) {
-                    long long spins = 0;
-                    unsigned ns = 32;
-                    while (ld_acquire(P.done + par) != P.gen) {
-                        if (++spins > P.spin_limit ||
-                            *((volatile unsigned long long*)(P.ctr + C_ABORT))) {
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(ns);
-                        if (ns < 1024) ns <<= 1;
-                    }
-                    if (!ok && spins > P.spin_limit) raise_err(P, VJ_DERR_WAIT_TIMEOUT);
-                }
-                ok = __shfl_sync(VJ_FULL, ok, 0);
-                if (!ok) break;
-                if (lane == 0) seedc = *((volatile int*)(P.cache + par));
-                seedc = __shfl_sync(VJ_FULL, seedc, 0);
-            }
+            if (par >= 0 && lane == 0) seedc = *((volatile int*)(P.cache + par));
+            seedc = __shfl_sync(VJ_FULL, seedc, 0);
         }
 
         float4 q[NPL];
@@ -334,7 +383,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         s.mask = HCAP - 1;
         s.nvis = 0;
         s.vislimit = HCAP / 2;
-        s.vspill = false;
+        s.region = -1;
         s.rid = S->rid;
         s.rd = S->rd;
         s.rcap = RCAP;
@@ -350,13 +399,11 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         __syncwarp();
         bool failed = false;
 
-        // ---- Alg. 4 greedy: the seeds
-        // lanes 0..2 hold the seed candidates: entry, cached seed, q itself
+        // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
         int sid = -1;
         if (lane == 0) sid = P.entry;
         if (lane == 1 && seedc >= 0) sid = seedc;
         if (lane == 2 && (P.ws == VJ_WS_SELF || P.ws == VJ_WS_SOFT)) sid = (int)qn;
-        // dedup in seed order (lane order), insert into visited
         bool snew = false;
 #pragma unroll 1
         for (int src = 0; src < 3; src++) {
@@ -381,11 +428,10 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             skey = (snode == (int)qn) ? 0.f : S->ckey[lane];
         }
         __syncwarp();
-        // keys of the two possible data seeds, kept for the OOD rule
         bool sdata = lane < ns && snode < P.nx;
         bool sin = inrange_decide(P, sdata, skey, snode, qn, lane, c_rechk);
         best_update(P, s, sdata, skey, snode, lane);
-        if (!append_results(P, s, sin, snode, skey, grid, grd, lane)) failed = true;
+        if (!append_results(P, s, sin, snode, skey, W, lane)) failed = true;
 
         // StopGreedy on the front = argmin (key, id) over the seeds
         float fk = lane < ns ? skey : FLT_MAX;
@@ -398,85 +444,83 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             unsigned who = __ballot_sync(VJ_FULL, fi == mi && lane < ns);
             int src = who ? __ffs(who) - 1 : 0;
             fin = __shfl_sync(VJ_FULL, sin, src);
-            fk = mk;
             fi = mi;
         }
         bool probe = !failed && ns > 0 && !(fi < P.nx && fin) && P.conv > 0 && fi == (int)qn;
 
-        // ---- probe N(q)
-        // per-lane copy of q's adjacency slot (R <= 32 handled per lane; wider
-        // rows loop) with the neighbour's key for the OOD rule
+        // ---- probe N(q); lane j keeps slot j of q's list and that neighbour's key
         float nkey_l = FLT_MAX;
         int nid_l = -1;
         int entry_in_nq = 0, seed_in_nq = 0;
         if (probe) {
             c_adj++;
-            for (int base = 0; base < R && !failed; base += 32) {
-                int j = base + lane;
-                int v = j < R ? __ldg(P.adj + qn * R + j) : -1;
-                if (base == 0) nid_l = v;
-                if (v == P.entry) entry_in_nq = 1;
-                if (v >= 0 && v == seedc) seed_in_nq = 1;
-                unsigned vm = __ballot_sync(VJ_FULL, v >= 0);
-                if (!vis_reserve(P, s, __popc(vm), gtab, lane, c_spill)) {
-                    failed = true;
-                    break;
-                }
+            int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+            nid_l = v;
+            if (v == P.entry) entry_in_nq = 1;
+            if (v >= 0 && v == seedc) seed_in_nq = 1;
+            unsigned vm = __ballot_sync(VJ_FULL, v >= 0);
+            if (!vis_reserve(P, s, __popc(vm), W, lane, c_spill)) failed = true;
+            if (!failed) {
                 bool nw = v >= 0 && hash_insert(s.tab, s.mask, v) == 1;
                 unsigned nm = __ballot_sync(VJ_FULL, nw);
                 int nc = __popc(nm);
-                if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
+                int mypos = __popc(nm & ((1u << lane) - 1u));
+                if (nw) S->cand[mypos] = v;
                 __syncwarp();
                 group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane);
                 __syncwarp();
                 s.nvis += nc;
                 int cv = lane < nc ? S->cand[lane] : -1;
                 float ck = lane < nc ? S->ckey[lane] : FLT_MAX;
+                float kk = S->ckey[nw ? mypos : 0];
                 __syncwarp();
                 bool dat = lane < nc && cv < P.nx;
                 bool in = inrange_decide(P, dat, ck, cv, qn, lane, c_rechk);
                 best_update(P, s, dat, ck, cv, lane);
-                if (!append_results(P, s, in, cv, ck, grid, grd, lane)) {
-                    failed = true;
-                    break;
-                }
-                // neighbour keys for the OOD rule (first 32 slots): freshly
-                // computed ones from the candidate list, seeds from the seed lanes
-                if (base == 0) {
-                    int pos = nw ? __popc(nm & ((1u << lane) - 1u)) : -1;
-                    float kk = __shfl_sync(VJ_FULL, ck, pos < 0 ? 0 : pos);
-                    if (nw) nkey_l = kk;
-                    // a neighbour that was already a seed: take the seed key
-                    for (int src = 0; src < ns; src++) {
-                        int sn = __shfl_sync(VJ_FULL, snode, src);
-                        float sk2 = __shfl_sync(VJ_FULL, skey, src);
-                        if (!nw && v == sn) nkey_l = sk2;
-                    }
+                if (!append_results(P, s, in, cv, ck, W, lane)) failed = true;
+                if (nw) nkey_l = kk;
+                // a neighbour that was a seed keeps the seed's key
+                for (int src = 0; src < ns; src++) {
+                    int sn = __shfl_sync(VJ_FULL, snode, src);
+                    float sk2 = __shfl_sync(VJ_FULL, skey, src);
+                    if (!nw && v == sn) nkey_l = sk2;
                 }
             }
         }
         entry_in_nq = __any_sync(VJ_FULL, entry_in_nq);
         seed_in_nq = __any_sync(VJ_FULL, seed_in_nq);
 
-        // ---- Alg. 6 CheckHybrid
+        // ---- Alg. 6 CheckHybrid (adapt on the merged index decides; force otherwise)
         int hyb = P.force;
         if (P.adapt && !failed) {
-            // d1 over data neighbours of q; d2 over their data neighbours that
-            // are not neighbours of q (and not q)
-            bool isd = nid_l >= 0 && nid_l < P.nx;
+            const bool isd = nid_l >= 0 && nid_l < P.nx;
             float d1s = isd ? key_to_dist(P, nkey_l) : 0.f;
-            int n1 = __popc(__ballot_sync(VJ_FULL, isd));
+            const unsigned dmask = __ballot_sync(VJ_FULL, isd);
+            const int n1 = __popc(dmask);
             float d2s = 0.f;
             int n2 = 0;
-            unsigned dm = __ballot_sync(VJ_FULL, isd);
+            unsigned dm = dmask;
             while (dm) {
-                int src = __ffs(dm) - 1;
-                dm &= dm - 1;
-                int v = __shfl_sync(VJ_FULL, nid_l, src);
-                c_adj++;
-                for (int base = 0; base < R; base += 32) {
-                    int j = base + lane;
-                    int w = j < R ? __ldg(P.adj + (int64_t)v * R + j) : -1;
+                // four data neighbours' rows per round, loads issued together
+                int vr[4];
+                int w4[4];
+                float e4[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    int src = dm ? __ffs(dm) - 1 : -1;
+                    if (dm) dm &= dm - 1;
+                    vr[k] = src >= 0 ? __shfl_sync(VJ_FULL, nid_l, src) : -1;
+                    if (src < 0) (void)__shfl_sync(VJ_FULL, nid_l, 0);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    w4[k] = (vr[k] >= 0 && lane < R) ? __ldg(P.adj + (int64_t)vr[k] * R + lane) : -1;
+                    e4[k] = (vr[k] >= 0 && lane < R) ? __ldg(P.elen + (int64_t)vr[k] * R + lane) : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (vr[k] >= 0) c_adj += (lane == 0);
+                    int w = w4[k];
                     bool ok = w >= 0 && w < P.nx;
                     if (ok) {
                         bool inq = hash_contains(s.tab, s.mask, w);
@@ -485,7 +529,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                         ok = !inq;
                     }
                     if (ok) {
-                        d2s += __ldg(P.elen + (int64_t)v * R + j);
+                        d2s += e4[k];
                         n2++;
                     }
                 }
@@ -504,7 +548,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 if (fabsf(r - 1.5f) <= 1e-3f) {
                     // FP64 re-decision of the ratio
                     double a1 = 0.0, a2 = 0.0;
-                    unsigned dm2 = __ballot_sync(VJ_FULL, isd);
+                    unsigned dm2 = dmask;
                     while (dm2) {
                         int src = __ffs(dm2) - 1;
                         dm2 &= dm2 - 1;
@@ -524,7 +568,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     if (lane == 0) c_rechk++;
                 }
             }
-            hyb = ood;  // Alg. 6: on the merged index adapt_hybrid decides, force otherwise
+            hyb = ood;
         }
         int expansions = 0;
 
@@ -532,23 +576,26 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         if (!failed && !hyb) {
             int fp = 0;
             while (fp < s.nres) {
-                int nb = min(FB, s.nres - fp);
-                // gather the neighbour lists of nb frontier nodes
-                if (!vis_reserve(P, s, nb * R, gtab, lane, c_spill)) {
+                const int nb = min(FB, s.nres - fp);
+                if (!vis_reserve(P, s, nb * R, W, lane, c_spill)) {
                     failed = true;
                     break;
                 }
+                // neighbour rows of nb frontier nodes, loads issued together
+                int vv[FB];
+#pragma unroll
+                for (int f = 0; f < FB; f++) {
+                    int u = f < nb ? s.rid[fp + f] : -1;
+                    vv[f] = (u >= 0 && lane < R) ? __ldg(P.adj + (int64_t)u * R + lane) : -1;
+                }
                 int nc = 0;
-                for (int f = 0; f < nb; f++) {
-                    int u = s.rid[fp + f];
-                    for (int base = 0; base < R; base += 32) {
-                        int j = base + lane;
-                        int v = j < R ? __ldg(P.adj + (int64_t)u * R + j) : -1;
-                        bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
-                        unsigned nm = __ballot_sync(VJ_FULL, nw);
-                        if (nw) S->cand[nc + __popc(nm & ((1u << lane) - 1u))] = v;
-                        nc += __popc(nm);
-                    }
+#pragma unroll
+                for (int f = 0; f < FB; f++) {
+                    int v = vv[f];
+                    bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
+                    unsigned nm = __ballot_sync(VJ_FULL, nw);
+                    if (nw) S->cand[nc + __popc(nm & ((1u << lane) - 1u))] = v;
+                    nc += __popc(nm);
                 }
                 __syncwarp();
                 c_adj += nb;
@@ -565,7 +612,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     bool val = ci < nc;
                     bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
                     best_update(P, s, val, ck, cv, lane);
-                    if (!append_results(P, s, in, cv, ck, grid, grd, lane)) {
+                    if (!append_results(P, s, in, cv, ck, W, lane)) {
                         failed = true;
                         break;
                     }
@@ -576,7 +623,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         } else if (!failed && hyb) {
             if (lane == 0) c_hyb++;
             int npend = s.nres;  // in-range entries not yet popped (rid >= 0)
-            int osz = 0;
+            int osz = 0, oqh = 0, cur = 0;
             for (;;) {
                 int u;
                 if (npend > 0) {
@@ -601,108 +648,94 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     __syncwarp();
                     npend--;
                 } else if (osz > 0) {
-                    u = oqi[0];
-                    // shift the out-range queue left by one
-                    for (int base = 1; base < osz; base += 32) {
-                        int i = base + lane;
-                        float kk = i < osz ? oqk[i] : 0.f;
-                        int ii = i < osz ? oqi[i] : 0;
-                        __syncwarp();
-                        if (i < osz) {
-                            oqk[i - 1] = kk;
-                            oqi[i - 1] = ii;
-                        }
-                        __syncwarp();
-                    }
+                    u = W.qi[cur][oqh];
+                    oqh++;
                     osz--;
                 } else {
                     break;
                 }
                 expansions++;
                 c_adj++;
-                if (!vis_reserve(P, s, R, gtab, lane, c_spill)) {
+                if (!vis_reserve(P, s, R, W, lane, c_spill)) {
                     failed = true;
                     break;
                 }
-                int nc = 0;
-                for (int base = 0; base < R; base += 32) {
-                    int j = base + lane;
-                    int v = j < R ? __ldg(P.adj + (int64_t)u * R + j) : -1;
-                    bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
-                    unsigned nm = __ballot_sync(VJ_FULL, nw);
-                    if (nw) S->cand[nc + __popc(nm & ((1u << lane) - 1u))] = v;
-                    nc += __popc(nm);
-                }
+                int v = lane < R ? __ldg(P.adj + (int64_t)u * R + lane) : -1;
+                bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
+                unsigned nm = __ballot_sync(VJ_FULL, nw);
+                int nc = __popc(nm);
+                if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
                 __syncwarp();
                 if (nc == 0) continue;
                 group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane);
                 __syncwarp();
                 s.nvis += nc;
-                for (int base = 0; base < nc && !failed; base += 32) {
-                    int ci = base + lane;
-                    bool val = ci < nc;
-                    int cv = val ? S->cand[ci] : -1;
-                    float ck = val ? S->ckey[ci] : FLT_MAX;
-                    bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
-                    best_update(P, s, val, ck, cv, lane);
-                    // in adjacency order: in-range -> result (pending);
-                    // out-range -> sorted insert, then trim if |Q| > beam
-                    unsigned inm = __ballot_sync(VJ_FULL, in && val);
-                    unsigned outm = __ballot_sync(VJ_FULL, !in && val);
-                    int cnt_chunk = min(32, nc - base);
-                    for (int c = 0; c < cnt_chunk; c++) {
-                        float kc = __shfl_sync(VJ_FULL, ck, c);
-                        int vc = __shfl_sync(VJ_FULL, cv, c);
-                        if ((inm >> c) & 1u) {
-                            if (!res_reserve(P, s, 1, grid, grd, lane)) {
-                                failed = true;
-                                break;
-                            }
-                            if (lane == 0) {
-                                s.rid[s.nres] = vc;
-                                s.rd[s.nres] = kc;
-                            }
-                            s.nres++;
-                            npend++;
-                            __syncwarp();
-                        } else if ((outm >> c) & 1u) {
-                            // position = number of queued entries less than (kc, vc)
-                            int less = 0;
-                            for (int i = lane; i < osz; i += 32) less += kless(oqk[i], oqi[i], kc, vc) ? 1 : 0;
-                            for (int o = 16; o > 0; o >>= 1) less += __shfl_xor_sync(VJ_FULL, less, o);
-                            // shift [less, osz) right by one, from the back
-                            for (int top = osz - 1; top >= less; top -= 32) {
-                                int i = top - lane;
-                                float kk = 0.f;
-                                int ii = 0;
-                                bool mv = i >= less;
-                                if (mv) {
-                                    kk = oqk[i];
-                                    ii = oqi[i];
-                                }
-                                __syncwarp();
-                                if (mv) {
-                                    oqk[i + 1] = kk;
-                                    oqi[i + 1] = ii;
-                                }
-                                __syncwarp();
-                            }
-                            if (lane == 0) {
-                                oqk[less] = kc;
-                                oqi[less] = vc;
-                            }
-                            __syncwarp();
-                            osz++;
-                            if (npend + osz > P.hbeam) osz--;  // drop the largest key
-                        }
+                // one candidate per lane, in adjacency order (nc <= 32)
+                const bool val = lane < nc;
+                const int cv = val ? S->cand[lane] : -1;
+                const float ck = val ? S->ckey[lane] : FLT_MAX;
+                __syncwarp();
+                const bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
+                best_update(P, s, val, ck, cv, lane);
+                const bool isout = val && !in;
+                const unsigned inm = __ballot_sync(VJ_FULL, in);
+                const unsigned outm = __ballot_sync(VJ_FULL, isout);
+                // queue size after the per-insert rule, in adjacency order
+                int np = npend, o = osz;
+                for (int c = 0; c < nc; c++) {
+                    if ((inm >> c) & 1u) np++;
+                    else if ((outm >> c) & 1u) {
+                        if (np + o + 1 <= P.hbeam) o++;
                     }
                 }
-                if (failed) break;
+                const int kfin = o;
+                if (!append_results(P, s, in, cv, ck, W, lane)) {
+                    failed = true;
+                    break;
+                }
+                npend = np;
+                const int m = __popc(outm);
+                if (m > 0 || oqh > 0) {
+                    // new out-range entries, sorted, staged in shared memory
+                    float nk = isout ? ck : FLT_MAX;
+                    int ni = isout ? cv : INT32_MAX;
+                    warp_sort_pairs(nk, ni, lane);
+                    if (lane < m) {
+                        S->ckey[lane] = nk;
+                        S->cand[lane] = ni;
+                    }
+                    __syncwarp();
+                    const float* ok_ = W.qk[cur] + oqh;
+                    const int* oi_ = W.qi[cur] + oqh;
+                    float* dk = W.qk[cur ^ 1];
+                    int* di = W.qi[cur ^ 1];
+                    // merge: the kfin smallest of old (osz) U new (m)
+                    for (int i = lane; i < osz; i += 32) {
+                        float a = ok_[i];
+                        int b = oi_[i];
+                        int pos = i + lower_rank(S->ckey, S->cand, m, a, b);
+                        if (pos < kfin) {
+                            dk[pos] = a;
+                            di[pos] = b;
+                        }
+                    }
+                    if (lane < m) {
+                        int pos = lane + lower_rank(ok_, oi_, osz, nk, ni);
+                        if (pos < kfin) {
+                            dk[pos] = nk;
+                            di[pos] = ni;
+                        }
+                    }
+                    __syncwarp();
+                    cur ^= 1;
+                    oqh = 0;
+                }
+                osz = kfin;
             }
         }
         c_exp += expansions;
 
-        // ---- Alg. 8 UpdateCache (soft): FP64 re-decision among near-ties
+        // ---- Alg. 8 UpdateCache: FP64 re-decision among near-ties
         int best = (s.bid == INT32_MAX) ? -1 : s.bid;
         if (!failed && s.nt > 1) {
             double bd = 1e300;
@@ -721,11 +754,18 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
 
         if (lane == 0) {
             P.cache[qi] = best;
-            __threadfence();
-            st_release(P.done + qi, P.gen);
             P.steps[qi] = s.nvis;
             P.hyb[qi] = (uint8_t)hyb;
             c_dist += s.nvis;
+            if (P.ws == VJ_WS_SOFT) {
+                // publish the children: cache[qi] is visible before any slot
+                __threadfence();
+                const int c0 = P.child_off[qi], c1 = P.child_off[qi + 1];
+                if (c1 > c0) {
+                    unsigned long long pos = atomicAdd(P.ctr + C_TAIL, (unsigned long long)(c1 - c0));
+                    for (int c = c0; c < c1; c++) st_release(P.ready + pos + (c - c0), P.child_list[c]);
+                }
+            }
         }
         if (failed) {
             if (lane == 0) P.count[qi] = 0;
@@ -762,13 +802,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
 template <int G, int NPL, int U>
 void launch_join_t(const JoinParams& P, int blocks, cudaStream_t st) {
     size_t smem = sizeof(WarpSmem) * WPB;
-    auto kern = k_join<G, NPL, U>;
-    static bool attr = false;
-    if (!attr) {
-        VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
-    kern<<<blocks, WPB * 32, smem, st>>>(P);
+    k_join<G, NPL, U><<<blocks, WPB * 32, smem, st>>>(P);
     VJ_LAUNCH_CHECK();
 }
 
@@ -812,27 +846,26 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
                "work_sharing=hard is not implemented by the GPU join");
     VJ_REQUIRE(ix->p.work_sharing >= 0 && ix->p.work_sharing <= 3, VJ_ERR_ARG, "bad work_sharing");
 
-    ix->done.ensure(nq, s);
     ix->cache.ensure(nq, s);
     ix->steps.ensure(nq, s);
     ix->hyb.ensure(nq, s);
     ix->count.ensure(nq, s);
     ix->seg.ensure(nq, s);
+    ix->ready.ensure(nq, s);
     ix->ctr.ensure(16, s);
-    if (ix->gen == 0) VJ_CUDA(cudaMemsetAsync(ix->done.p, 0, nq * sizeof(int), s));
-    ix->gen++;
-    if (ix->gen == 0x7fffffff) {
-        VJ_CUDA(cudaMemsetAsync(ix->done.p, 0, nq * sizeof(int), s));
-        ix->gen = 1;
-    }
 
+    static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
     JoinDispatch jd = pick(ix->dp / 4, ix->num_sms);
     const int64_t warps = (int64_t)jd.blocks * WPB;
-    int gcap = 1 << 18;
-    while (gcap > 4096 && (int64_t)gcap / 4 > ix->n) gcap >>= 1;
+    // global visited regions: up to 2^17 slots (64K visited nodes per query),
+    // no larger than needed for the whole node set
+    int gmax = 1 << 17;
+    while (gmax > GCAP0 && (int64_t)gmax / 4 >= ix->n) gmax >>= 1;
+    if (gmax < GCAP0) gmax = GCAP0;
+    const int grcap = gmax / 2;
     const int hbeam = budget > 0 ? budget : ix->p.hybrid_beam;
     const int oqcap = hbeam + 2;
-    const int64_t wstride = ((int64_t)2 * gcap + 2 * oqcap + 31) / 32 * 32;
+    const int64_t wstride = ((int64_t)2 * gmax + 2 * grcap + 4 * oqcap + 31) / 32 * 32;
     if (ix->wspace_warps < warps || ix->wspace.n < (size_t)(warps * wstride)) {
         ix->wspace.free_(s);
         ix->wspace.alloc((size_t)(warps * wstride), s);
@@ -849,8 +882,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.invn = ix->invn.p;
     P.adj = ix->adj.p;
     P.elen = ix->elen.p;
-    P.order = ix->order.p;
     P.parent = ix->parent.p;
+    P.child_off = ix->child_off.p;
+    P.child_list = ix->child_list.p;
+    P.ready = ix->ready.p;
     P.nx = ix->nx;
     P.nq = nq;
     P.dp4 = ix->dp / 4;
@@ -871,15 +906,14 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.tie_tol = P.band;
     P.eps64 = (double)eps;
     P.cache = ix->cache.p;
-    P.done = ix->done.p;
-    P.gen = ix->gen;
     P.steps = ix->steps.p;
     P.hyb = ix->hyb.p;
     P.count = ix->count.p;
     P.seg = ix->seg.p;
     P.wspace = ix->wspace.p;
     P.wstride = wstride;
-    P.gcap = gcap;
+    P.gmax = gmax;
+    P.grcap = grcap;
     P.oqcap = oqcap;
     P.ctr = ix->ctr.p;
     P.spin_limit = 1ll << 24;  // ~seconds with back-off; then VJ_DERR_WAIT_TIMEOUT
@@ -888,14 +922,25 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     VJ_CUDA(cudaEventCreate(&e0));
     VJ_CUDA(cudaEventCreate(&e1));
     VJ_CUDA(cudaEventCreate(&e2));
-    unsigned long long hc[C_NUM];
+    unsigned long long hc[16];
     int64_t launches = 0;
+    const bool soft = ix->p.work_sharing == VJ_WS_SOFT;
     for (int attempt = 0; attempt < 3; attempt++) {
         launches++;
         P.pool_id = ix->pool_id.p;
         P.pool_d = ix->pool_d.p;
         P.pool_cap = (int64_t)ix->pool_id.n;
+        // ready queue: the roots (soft sharing) or every query in MST order
         VJ_CUDA(cudaMemsetAsync(ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
+        if (soft) {
+            VJ_CUDA(cudaMemsetAsync(ix->ready.p, 0xff, nq * sizeof(int32_t), s));
+            VJ_CUDA(cudaMemcpyAsync(ix->ready.p, ix->roots.p, ix->nroots * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                    s));
+            unsigned long long tail = (unsigned long long)ix->nroots;
+            VJ_CUDA(cudaMemcpyAsync(ix->ctr.p + C_TAIL, &tail, sizeof(tail), cudaMemcpyHostToDevice, s));
+        } else {
+            VJ_CUDA(cudaMemcpyAsync(ix->ready.p, ix->order.p, nq * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        }
         VJ_CUDA(cudaEventRecord(e0, s));
         jd.launch(P, jd.blocks, s);
         VJ_CUDA(cudaEventRecord(e1, s));
@@ -909,8 +954,6 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         ix->pool_d.free_(s);
         ix->pool_id.alloc(cap, s);
         ix->pool_d.alloc(cap, s);
-        ix->gen++;
-        P.gen = ix->gen;
     }
     if (hc[C_ERR] != 0) {
         cudaEventDestroy(e0);
@@ -918,7 +961,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         cudaEventDestroy(e2);
         int code = (int)hc[C_ERR];
         if (code == VJ_DERR_WAIT_TIMEOUT) {
-            vj_set_error("join: a soft work-sharing wait on an MST parent timed out");
+            vj_set_error("join: a wait on the work-sharing ready queue timed out");
             throw VjError{VJ_ERR_TIMEOUT};
         }
         vj_set_error("join: device error %d (%s)", code,
@@ -955,7 +998,6 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     st->ms_csr = t_csr;
     st->ms_total = t_trav + t_csr;
     // algorithmic bytes: one vector per distance, one adjacency row per row read
-    // (plus the edge-length row for each OOD row read)
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
     st->kernel_launches = launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort
     *nnz_out = nnz;

@@ -1,0 +1,634 @@
+// k_tc.cu -- tensor-core distance tiles (tcgen05 + TMA + TMEM, sm_103a).
+//
+// Gram tiles G = A B^T of BF16 row matrices with FP32 accumulation; the
+// norm expansion |a|^2 + |b|^2 - 2<a,b> turns them into squared L2 keys
+// (cosine: 1 - <a,b>/(|a||b|)).  Used for the exact join / brute-force scan
+// (Sec. 3.2 NLJ): a pair becomes a candidate when its low-precision key is
+// below eps_key plus a per-pair rounding bound, and every candidate is
+// re-decided from the FP32 vectors (FP64 near eps) by the existing recheck
+// kernel, so the result is exact.
+//
+// Kernel organisation (one CTA per SM, persistent over 128 x 256 output tiles):
+//   warp 0      TMA producer: A (128 x 64) and B (256 x 64) BF16 boxes with
+//               128-byte swizzle into a 4-stage shared-memory ring;
+//   warp 1      allocates 512 TMEM columns (two 256-column FP32 accumulators)
+//               and issues tcgen05.mma (M=128, N=256, K=16) from one lane;
+//               tcgen05.commit releases ring stages and hands finished
+//               accumulators to the epilogue;
+//   warps 2-9   epilogue: tcgen05.ld 32 columns at a time from their TMEM lane
+//               quarter, key + bound test, candidate append.
+// Every mbarrier wait is bounded; on timeout the CTA records an error, stops,
+// waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <float.h>
+#include <stdint.h>
+
+#include "vj_device.cuh"
+#include "vj_internal.cuh"
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_EPI_WARPS = 16;
+constexpr int TC_CG = TC_EPI_WARPS / 4;    // column groups: warps sharing a TMEM lane quarter
+constexpr int TC_CW = TC_BN / TC_CG;       // columns per epilogue warp
+constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
+constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
+constexpr uint32_t TC_TMEM_COLS = 512;
+
+struct __align__(1024) TcSmem {
+    uint8_t A[TC_STAGES][TC_A_BYTES];
+    uint8_t B[TC_STAGES][TC_B_BYTES];
+    uint64_t full[TC_STAGES];
+    uint64_t empty[TC_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float cn[2][TC_BN];   // column squared norms (L2) / inverse norms (cosine)
+    float cnr[2][TC_BN];  // column norms
+    __align__(16) float g[2][TC_BN];  // per-column filter thresholds
+    uint8_t cvalid[2][TC_BN];
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when the CTA is aborting
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, long long limit) {
+    for (long long i = 0; i < limit; i++) {
+        if (mbar_test(b, parity)) return true;
+        if ((i & 63) == 63 && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+// wait for outstanding TMEM loads; the destination registers are in/out
+// operands so no use of them can be scheduled above the wait
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row groups of 128-byte rows, 1024 B apart
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
+// K-major, M = 128, N = 256
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                              ((uint32_t)(TC_BM >> 4) << 24);
+
+struct TcScanParams {
+    int64_t nrows, ncols;  // A rows (queries), B rows (data)
+    int nkb;               // K blocks of 64
+    int nrt, nct;          // row / column tiles
+    int metric;
+    const float* a_n;      // per A row: squared norm (L2) or inverse norm (cosine)
+    const float* b_n;      // per B row: same
+    const int32_t* a_ids;  // query index of each A row
+    float eps_key;
+    float cb, c3;          // candidate bound: key - cb*|a||b| - c3*(|a|^2+|b|^2) < eps_key
+    float cbmax;           // cb * (largest row norm): row-independent form of the bound
+    int32_t* cq;
+    int32_t* cx;
+    unsigned long long* ncand;
+    int64_t cap;
+    int* err;
+    long long spin_limit;
+};
+
+// MODE 0: exact L2 keys, 1: L2 keys with the BF16 rounding bound, 2: cosine
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_scan(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcScanParams P) {
+    extern __shared__ uint8_t tc_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &S.abort;
+    const int ntiles = P.nrt * P.nct;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; s++) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&S.tfull[b], 1);
+            mbar_init(&S.tempty[b], TC_EPI_WARPS);
+        }
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&S.tmem_base)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued = 0, last_ph = 0;  // stages ever filled, parity of their last fill
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int rt = t % P.nrt, ct = t / P.nrt;
+                for (int kb = 0; kb < P.nkb; kb++) {
+                    if (!mbar_wait(&S.empty[s], ph ^ 1u, abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(&S.full[s], TC_A_BYTES + TC_B_BYTES);
+                    tma_load_2d(S.A[s], &tA, &S.full[s], kb * TC_BK, rt * TC_BM);
+                    tma_load_2d(S.B[s], &tB, &S.full[s], kb * TC_BK, ct * TC_BN);
+                    issued |= 1u << s;
+                    last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                    if (++s == TC_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+                // let this CTA's copies land before shared memory goes away
+                for (int st = 0; st < TC_STAGES; st++)
+                    if ((issued >> st) & 1u) {
+                        for (long long i = 0; i < P.spin_limit && !mbar_test(&S.full[st], (last_ph >> st) & 1u);
+                             i++) {
+                        }
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, i++) {
+                const int acc = i & 1;
+                if (!mbar_wait(&S.tempty[acc], ((i >> 1) & 1) ^ 1u, abort, P.spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
+                for (int kb = 0; kb < P.nkb; kb++) {
+                    if (!mbar_wait(&S.full[s], ph, abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = sdesc_sw128(su32(S.A[s]));
+                    const uint64_t bd = sdesc_sw128(su32(S.B[s]));
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; kk++) {
+                        // advance 16 BF16 (32 bytes) along K inside the swizzled rows
+                        tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), TC_IDESC, (kb | kk) != 0);
+                    }
+                    tc_commit(&S.empty[s]);
+                    if (++s == TC_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                tc_commit(&S.tfull[acc]);
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+            }
+            // all issued MMAs complete before TMEM is released
+            tc_commit(&S.drain);
+            for (long long k = 0; k < P.spin_limit && !mbar_test(&S.drain, 0); k++) {
+            }
+        }
+    } else {
+        // ---------------- epilogue
+        const int e = warp - 2;              // 0..TC_EPI_WARPS-1
+        const int quarter = warp & 3;        // TMEM lane quarter this warp may access
+        const int cg = e >> 2;               // column group
+        const int etid = e * 32 + lane;      // threads < TC_BN stage one column each
+        // the next tile's column norm and row info are loaded one tile ahead,
+        // so their latency overlaps the current tile
+        auto col_norm = [&](int tt) -> float {
+            const int64_t c = (int64_t)(tt / P.nrt) * TC_BN + etid;
+            return (etid < TC_BN && tt < ntiles && c < P.ncols) ? P.b_n[c] : -1.f;
+        };
+        auto row_norm = [&](int tt) -> float {
+            const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
+            return (tt < ntiles && r < P.nrows) ? P.a_n[r] : -1.f;
+        };
+        auto row_id = [&](int tt) -> int {
+            const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
+            return (tt < ntiles && r < P.nrows) ? P.a_ids[r] : -1;
+        };
+        float nc_next = col_norm(blockIdx.x), rn_next = row_norm(blockIdx.x);
+        int qid_next = row_id(blockIdx.x);
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
+            const int acc = i & 1;
+            const int ct = t / P.nrt;
+            // ---- per-tile staging (overlaps the MMA of this tile)
+            // filter: a pair can only be a candidate when v - g[c] > h[r]
+            //   L2:     v > ((1-c3)(|r|^2 + |c|^2) - eps^2 - cbmax |c|)/2, with
+            //           cbmax >= cb |r| for every row (a conservative bound)
+            //   cosine: v * cinv > (1 - cb - eps) |r|
+            if (etid < TC_BN) {
+                const float n = nc_next;
+                const bool cvld = n >= 0.f;
+                float g;
+                if (MODE == 2) g = cvld ? n : 0.f;
+                else g = cvld ? 0.5f * ((1.f - P.c3) * n - P.eps_key - P.cbmax * sqrtf(n)) : INFINITY;
+                S.g[acc][etid] = g;
+                S.cn[acc][etid] = cvld ? n : FLT_MAX;
+                S.cnr[acc][etid] = cvld ? (MODE == 2 ? 1.f : sqrtf(n)) : 0.f;
+                S.cvalid[acc][etid] = cvld;
+            }
+            const bool rv = rn_next >= 0.f;
+            const float rn = rv ? rn_next : 0.f;
+            const int qid = qid_next;
+            if (t + (int)gridDim.x < ntiles) {
+                nc_next = col_norm(t + gridDim.x);
+                rn_next = row_norm(t + gridDim.x);
+                qid_next = row_id(t + gridDim.x);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
+            const float cbr = MODE == 1 ? P.cb * sqrtf(rn) : 0.f;
+            float hr, marg;
+            if (MODE == 2) {
+                hr = (1.f - P.cb - P.eps_key) * (rn > 0.f ? 1.f / rn : 0.f);
+                marg = 1e-5f * (fabsf(hr) + 1.f);
+            } else {
+                hr = 0.5f * (1.f - P.c3) * rn;
+                marg = 1e-5f * (rn + P.eps_key) + 1e-30f;
+            }
+            const float thr = hr - marg;
+            bool ok = mbar_wait(&S.tfull[acc], (i >> 1) & 1, abort, P.spin_limit);
+            if (!__all_sync(VJ_FULL, ok)) {
+                if (lane == 0) {
+                    *abort = 1;
+                    atomicExch(P.err, 1);
+                }
+                break;
+            }
+            tc_fence_after();
+            const float eps_k = P.eps_key;
+            const uint32_t tbase = tmem + (uint32_t)(acc * TC_BN + cg * TC_CW) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int ch = 0; ch < TC_CW / 32; ch++) {
+                const int col0 = cg * TC_CW + ch * 32;
+                uint32_t va[32];
+                tmem_ld32_issue(tbase + (uint32_t)(ch * 32), va);
+                tmem_wait_ld(va);
+                // fast filter: two instructions per pair, four independent chains
+                float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+                const float4* g4 = reinterpret_cast<const float4*>(&S.g[acc][col0]);
+#pragma unroll
+                for (int j4 = 0; j4 < 8; j4++) {
+                    const float4 g = g4[j4];
+                    if (MODE == 2) {
+                        m0 = fmaxf(m0, __uint_as_float(va[4 * j4 + 0]) * g.x);
+                        m1 = fmaxf(m1, __uint_as_float(va[4 * j4 + 1]) * g.y);
+                        m2 = fmaxf(m2, __uint_as_float(va[4 * j4 + 2]) * g.z);
+                        m3 = fmaxf(m3, __uint_as_float(va[4 * j4 + 3]) * g.w);
+                    } else {
+                        m0 = fmaxf(m0, __uint_as_float(va[4 * j4 + 0]) - g.x);
+                        m1 = fmaxf(m1, __uint_as_float(va[4 * j4 + 1]) - g.y);
+                        m2 = fmaxf(m2, __uint_as_float(va[4 * j4 + 2]) - g.z);
+                        m3 = fmaxf(m3, __uint_as_float(va[4 * j4 + 3]) - g.w);
+                    }
+                }
+                const bool maybe = rv && fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr;
+                if (!__any_sync(VJ_FULL, maybe)) continue;
+                uint32_t hit = 0;
+                if (maybe) {
+                    // exact candidate test for this row's 32 columns (unrolled:
+                    // the TMEM registers must stay registers)
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const float v = __uint_as_float(va[j]);
+                        const float cn = S.cn[acc][col0 + j];
+                        bool h;
+                        if (MODE == 0) {
+                            h = fmaf(-2.f, v, rn + cn) < eps_k;
+                        } else if (MODE == 1) {
+                            const float t = rn + cn;
+                            h = fmaf(-2.f, v, t) - fmaf(cbr, S.cnr[acc][col0 + j], P.c3 * t) < eps_k;
+                        } else {
+                            h = 1.f - v * rn * cn - P.cb < eps_k;
+                        }
+                        if (h && S.cvalid[acc][col0 + j]) hit |= 1u << j;
+                    }
+                }
+                // warp-aggregated append: one atomic per warp and chunk
+                const int mine = __popc(hit);
+                int incl = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t2 = __shfl_up_sync(VJ_FULL, incl, o);
+                    if (lane >= o) incl += t2;
+                }
+                const int total = __shfl_sync(VJ_FULL, incl, 31);
+                if (total > 0) {
+                    unsigned long long base = 0;
+                    if (lane == 31) base = atomicAdd(P.ncand, (unsigned long long)total);
+                    base = __shfl_sync(VJ_FULL, base, 31);
+                    unsigned long long gq = base + (unsigned long long)(incl - mine);
+                    while (hit) {
+                        const int j = __ffs(hit) - 1;
+                        hit &= hit - 1;
+                        if ((int64_t)gq < P.cap) {
+                            P.cq[gq] = qid;
+                            P.cx[gq] = (int)((int64_t)ct * TC_BN + col0 + j);
+                        }
+                        gq++;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.tempty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// FP32 rows (optionally gathered) -> BF16 rows of kp columns, zero padded
+__global__ void k_to_bf16(const float* __restrict__ vec, int dp, int d, const int32_t* __restrict__ rows,
+                          int64_t row0, int64_t nrows, int kp, __nv_bfloat16* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows * kp) return;
+    const int64_t r = i / kp;
+    const int k = (int)(i % kp);
+    const int64_t src = rows ? (int64_t)rows[r] : row0 + r;
+    out[i] = __float2bfloat16_rn(k < d ? vec[src * dp + k] : 0.f);
+}
+
+__global__ void k_gather_f(const float* __restrict__ src, const int32_t* __restrict__ rows, int64_t n,
+                           float* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[rows[i]];
+}
+
+// flag[0] |= any non-integer coordinate; flag[1] = max |coordinate| (integer part)
+__global__ void k_int_check(const float* __restrict__ v, int64_t n, unsigned int* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = v[i];
+    const bool nonint = !(x == rintf(x)) || fabsf(x) > 1e9f;
+    if (__any_sync(__activemask(), nonint) && nonint) atomicOr(flag, 1u);
+    const unsigned int m = (unsigned int)fminf(fabsf(x), 4e9f);
+    atomicMax(flag + 1, m);
+}
+
+// query index and merged node id of each scanned row
+__global__ void k_query_rows(const int32_t* __restrict__ qrows, int64_t n, int32_t nx, int32_t* __restrict__ qid,
+                             int32_t* __restrict__ node) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t q = qrows ? qrows[i] : (int32_t)i;
+    qid[i] = q;
+    node[i] = nx + q;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        VJ_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        VJ_REQUIRE(q == cudaDriverEntryPointSuccess && p, VJ_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map: rows x kp, box (64 x box_rows), 128-byte swizzle
+CUtensorMap make_map(const void* base, int64_t rows, int kp, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    VJ_REQUIRE(r == CUDA_SUCCESS, VJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return m;
+}
+
+}  // namespace
+
+// BF16 copy of the data rows (built once per index, kept for later scans)
+static void ensure_data_bf16(vj_index* ix) {
+    const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
+    if (ix->xbf.n >= (size_t)ix->nx * kp) return;
+    ix->xbf.ensure((size_t)ix->nx * kp, ix->stream);
+    k_to_bf16<<<vj_div_up(ix->nx * kp, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->nx, kp,
+                                                                    ix->xbf.p);
+    VJ_LAUNCH_CHECK();
+    // Exact-key test: when every coordinate is an integer of magnitude <= 256
+    // it is exact in BF16, every product is an integer below 2^16 and, with
+    // d * max^2 <= 2^23, every partial sum, both norms, their sum (<= 2^24)
+    // and the norm expansion stay integers exactly representable in FP32, so
+    // the FP32-accumulated key is exact and needs no bound.
+    DBuf<unsigned int> flag;
+    flag.alloc(2, ix->stream);
+    VJ_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(unsigned int), ix->stream));
+    k_int_check<<<vj_div_up(ix->n * ix->dp, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->n * ix->dp, flag.p);
+    VJ_LAUNCH_CHECK();
+    unsigned int h[2] = {0, 0};
+    VJ_CUDA(cudaMemcpyAsync(h, flag.p, sizeof(h), cudaMemcpyDeviceToHost, ix->stream));
+    VJ_CUDA(cudaStreamSynchronize(ix->stream));
+    flag.free_(ix->stream);
+    const double mx = (double)h[1];
+    ix->bf16_exact = h[0] == 0 && mx <= 256.0 && (double)ix->d * mx * mx <= 8388608.0;
+}
+
+// Candidate pairs (query index, data id) of the BF16 tensor-core scan of the
+// queries `qrows` (query indices; nullptr = all) against every data row.
+// Returns the candidate count (the arrays are grown and the scan re-run when
+// they are too small).
+int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
+                              DBuf<int32_t>& cx, double* ms_out) {
+    cudaStream_t s = ix->stream;
+    const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
+    ensure_data_bf16(ix);
+    DBuf<__nv_bfloat16> abf;
+    DBuf<int32_t> aid, anode;
+    DBuf<float> an;
+    abf.alloc((size_t)nr * kp, s);
+    aid.alloc(nr, s);
+    anode.alloc(nr, s);
+    an.alloc(nr, s);
+    k_query_rows<<<vj_div_up(nr, 256), 256, 0, s>>>(qrows, nr, (int32_t)ix->nx, aid.p, anode.p);
+    VJ_LAUNCH_CHECK();
+    const int32_t* arow = anode.p;
+    k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, abf.p);
+    VJ_LAUNCH_CHECK();
+    const float* nsrc = ix->metric == VJ_L2 ? ix->sqn.p : ix->invn.p;
+    k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(nsrc, arow, nr, an.p);
+    VJ_LAUNCH_CHECK();
+
+    CUtensorMap ta = make_map(abf.p, nr, kp, TC_BM);
+    CUtensorMap tb = make_map(ix->xbf.p, ix->nx, kp, TC_BN);
+    TcScanParams P;
+    P.nrows = nr;
+    P.ncols = ix->nx;
+    P.nkb = kp / TC_BK;
+    P.nrt = vj_div_up(nr, TC_BM);
+    P.nct = vj_div_up(ix->nx, TC_BN);
+    P.metric = ix->metric;
+    P.a_n = an.p;
+    P.b_n = nsrc;  // data rows are the first nx nodes
+    P.a_ids = aid.p;
+    P.eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
+    const double ub = 1.0 / 256.0, u = VJ_F32_U;
+    // |key_bf16 - key| <= (4ub + 2ub^2 + 2 kp 2^-23 + 4u) |a||b| + 3u (|a|^2 + |b|^2), with a 1.25 margin
+    P.cb = (float)(1.25 * (4 * ub + 2 * ub * ub + 2.0 * kp * 2 * u + 4 * u));
+    P.c3 = (float)(1.25 * 3 * u);
+    if (ix->metric != VJ_L2) P.cb = (float)(1.25 * (2 * ub + ub * ub + 2.0 * kp * 2 * u + 8 * u));
+    if (ix->metric == VJ_L2 && ix->bf16_exact) {
+        P.cb = 0.f;  // exact integer keys (see ensure_data_bf16)
+        P.c3 = 0.f;
+    }
+    // row-independent form of the bound (after the exact-key adjustment)
+    P.cbmax = ix->metric == VJ_L2 ? (float)(P.cb * ix->maxnorm * 1.0001) : 0.f;
+    DBuf<unsigned long long> ctr;
+    DBuf<int> err;
+    ctr.alloc(1, s);
+    err.alloc(1, s);
+    P.ncand = ctr.p;
+    P.err = err.p;
+    P.spin_limit = 1ll << 22;  // try_wait polls; seconds at most, then an error
+    const int ntiles = P.nrt * P.nct;
+    const int grid = std::min(ntiles, ix->num_sms);
+    const size_t smem = sizeof(TcSmem) + 1024;
+    const int mode = ix->metric != VJ_L2 ? 2 : (ix->bf16_exact ? 0 : 1);
+    auto kern = mode == 0 ? k_tc_scan<0> : (mode == 1 ? k_tc_scan<1> : k_tc_scan<2>);
+    VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t cap = std::max<int64_t>(cq.n, std::max<int64_t>(nr * 64, 1 << 20));
+    unsigned long long hn = 0;
+    int herr = 0;
+    cudaEvent_t e0, e1;
+    VJ_CUDA(cudaEventCreate(&e0));
+    VJ_CUDA(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        cq.ensure(cap, s);
+        cx.ensure(cap, s);
+        P.cq = cq.p;
+        P.cx = cx.p;
+        P.cap = (int64_t)cq.n;
+        VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
+        VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+        VJ_CUDA(cudaEventRecord(e0, s));
+        kern<<<grid, TC_THREADS, smem, s>>>(ta, tb, P);
+        VJ_LAUNCH_CHECK();
+        VJ_CUDA(cudaEventRecord(e1, s));
+        VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        VJ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core scan: a pipeline wait timed out");
+        if ((int64_t)hn <= P.cap) break;
+        cap = (int64_t)hn + 1024;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms_out) *ms_out = ms;
+    abf.free_(s);
+    aid.free_(s);
+    an.free_(s);
+    anode.free_(s);
+    ctr.free_(s);
+    err.free_(s);
+    return (int64_t)hn;
+}

@@ -591,6 +591,7 @@ void vj_build_knn(vj_index* ix) {
     const int K = ix->K;
     double maxnorm = 0.0;
     vj_compute_norms(ix, &maxnorm);
+    ix->maxnorm = maxnorm;
     int KP = K + std::max(16, K / 4);
     KP = std::min(KP, 128);
     KP = (KP + 31) / 32 * 32;
@@ -675,26 +676,18 @@ void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<
     double beta = ix->metric == VJ_L2 ? (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0 * maxnorm * maxnorm
                                       : (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0;
     float key_hi = (float)((double)eps_key + beta) * 1.0001f + 1e-30f;
-    int64_t cap = std::max<int64_t>(nq * 64, 1 << 20);
+    (void)key_hi;
+    // candidates from the BF16 tensor-core scan (bounded superset), then the
+    // exact FP32 / FP64 re-decision below
     DBuf<int32_t> cq, cx;
     DBuf<float> cd;
     DBuf<unsigned long long> ctr;
     ctr.alloc(2, s);
-    unsigned long long hn = 0;
-    for (int attempt = 0; attempt < 2; attempt++) {
-        cq.ensure(cap, s);
-        cx.ensure(cap, s);
-        VJ_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
-        dim3 grid(vj_div_up(nq, TBM), vj_div_up(vj_div_up(nx, TBN), NLJ_COLS));
-        k_nlj_tile<<<grid, TT, 0, s>>>(ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, nx, nq, ix->metric, key_hi, cq.p,
-                                       cx.p, ctr.p, cap);
-        VJ_LAUNCH_CHECK();
-        VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
-        VJ_CUDA(cudaStreamSynchronize(s));
-        if ((int64_t)hn <= cap) break;
-        cap = (int64_t)hn + 1024;
-    }
-    const int64_t nc = (int64_t)hn;
+    VJ_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
+    double ms_scan = 0.0;
+    const int64_t nc = vj_tc_scan_candidates(ix, nullptr, nq, eps, cq, cx, &ms_scan);
+    ix->last_scan_ms = ms_scan;
+    ix->last_scan_cand = nc;
     DBuf<int32_t> counts, cursor;
     counts.alloc(nq, s);
     cursor.alloc(nq, s);

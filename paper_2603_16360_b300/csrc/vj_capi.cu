@@ -78,6 +78,10 @@ static void free_index(vj_index* ix) {
     ix->parent.free_(s);
     ix->order.free_(s);
     ix->depth.free_(s);
+    ix->child_off.free_(s);
+    ix->child_list.free_(s);
+    ix->roots.free_(s);
+    ix->ready.free_(s);
     ix->done.free_(s);
     ix->cache.free_(s);
     ix->steps.free_(s);
@@ -274,6 +278,8 @@ extern "C" vj_status vj_join_exact(vj_index* ix, float eps, vj_result** out) {
         memset(r->cache, 0xff, ix->nq * sizeof(int32_t));
         memset(r->hybrid, 0, ix->nq);
         r->stats.ms_total = ms;
+        r->stats.ms_scan = ix->last_scan_ms;
+        r->stats.scan_candidates = ix->last_scan_cand;
         r->stats.dist_computations = ix->nx * ix->nq;
         off.free_(s);
         ids.free_(s);

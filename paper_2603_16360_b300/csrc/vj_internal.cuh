@@ -1,8 +1,12 @@
 // vj_internal.cuh -- shared declarations of the libvj translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/vj.h"
 
@@ -106,6 +110,16 @@ struct vj_index {
     DBuf<int32_t> order;  // [nq]
     DBuf<int32_t> depth;  // [nq]
     int max_depth = 0;
+    DBuf<int32_t> child_off;   // [nq+1] MST children CSR
+    DBuf<int32_t> child_list;  // [nq]
+    DBuf<int32_t> roots;       // queries whose MST parent is the data entry (or none)
+    int64_t nroots = 0;
+    DBuf<int32_t> ready;       // [nq] join dispatch queue
+    DBuf<__nv_bfloat16> xbf;   // [nx][kp] BF16 copy of the data rows (tensor-core scans)
+    bool bf16_exact = false;   // BF16 Gram keys are exact for these inputs (small integers)
+    double maxnorm = 0.0;      // largest vector norm (FP64)
+    double last_scan_ms = 0.0; // device time of the last tensor-core scan
+    int64_t last_scan_cand = 0;
     int64_t knn_uncertified = 0;  // rows whose tile candidates needed the exact fallback
 
     // join scratch kept across calls
@@ -140,6 +154,11 @@ void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<
                           DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
+
+// tensor-core (tcgen05) BF16 scan of query rows against all data rows:
+// candidate (query index, data id) pairs, exact after re-check
+int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
+                              DBuf<int32_t>& cx, double* ms_out);
 
 // utilities
 void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix);

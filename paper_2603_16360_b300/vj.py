@@ -49,7 +49,8 @@ class vj_stats(C.Structure):
     _fields_ = [("dist_computations", C.c_int64), ("expansions", C.c_int64), ("adj_rows_read", C.c_int64),
                 ("hybrid_queries", C.c_int64), ("rechecks", C.c_int64), ("spill_queries", C.c_int64),
                 ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
-                ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
+                ("scan_candidates", C.c_int64)]
 
 
 class vj_result(C.Structure):
