@@ -131,6 +131,18 @@ vj_status vj_set_stream(vj_index *ix, void *stream);
  * work_sharing, adapt_hybrid, force_hybrid) used by later joins. */
 vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
 
+/* Per-query plan used by later joins in place of Alg. 6's CheckHybrid rule
+ * (a predictor's output; the paper has the rule only).  Host arrays of nq
+ * entries, copied; either may be NULL (NULL for both clears the plan):
+ *   route[q] != 0: after its greedy phase (seeds + probe of N(q), so soft
+ *     work sharing still hands C[q] to its children) the query's row is its
+ *     exact nested-loop-join row, computed by the tensor-core brute-force scan
+ *     with exact re-check; hybrid flag 2 in the result.
+ *   beam[q] > 0: hybrid expansion with hybrid_beam_size = beam[q];
+ *   beam[q] == 0: the BFS expansion.
+ * Errors: VJ_ERR_ARG (beam outside [0, 2^20]). */
+vj_status vj_set_plan(vj_index *ix, const uint8_t *route, const int32_t *beam);
+
 /* Approximate join (Alg. 1 on the merged index) at threshold eps > 0.
  * budget > 0 overrides hybrid_beam for this call.  The result lives in host
  * memory (the device->host copy is part of the call).

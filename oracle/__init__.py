@@ -78,6 +78,8 @@ class _Cfg(C.Structure):
         ("greedy_beam_size", C.c_int),
         ("conv_threshold", C.c_int),
         ("hybrid_beam_size", C.c_int),
+        ("route", C.c_void_p),
+        ("beam", C.c_void_p),
     ]
 
 
@@ -184,8 +186,13 @@ class JoinResult:
 def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: int = WS_SELF,
          force_hybrid: bool = False, adapt_hybrid: bool = False, greedy_beam_size: int = 256,
          conv_threshold: int = 10, hybrid_beam_size: int = 256, order=None, parent=None,
-         queries=None) -> JoinResult:
+         queries=None, route=None, beam=None) -> JoinResult:
     """Alg. 1 VectorJoin on the merged index.
+
+    route/beam (optional, per query) replace Alg. 6's rule with a plan:
+    route[q] = 1 sends q to the brute-force scan after its greedy phase
+    (hybrid flag 2), beam[q] > 0 runs the hybrid expansion with that queue
+    size, beam[q] = 0 the BFS expansion.
 
     order/parent default to the MST of `mst()` when work sharing is hard/soft,
     else to index order.  `queries` (optional) restricts the run to that list of
@@ -203,7 +210,10 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
         order = o if order is None else order
     if queries is not None:
         order = np.ascontiguousarray(queries, dtype=np.int32)
-    cfg = _Cfg(work_sharing, int(force_hybrid), int(adapt_hybrid), greedy_beam_size, conv_threshold, hybrid_beam_size)
+    route_a = None if route is None else np.ascontiguousarray(route, dtype=np.uint8)
+    beam_a = None if beam is None else np.ascontiguousarray(beam, dtype=np.int32)
+    cfg = _Cfg(work_sharing, int(force_hybrid), int(adapt_hybrid), greedy_beam_size, conv_threshold, hybrid_beam_size,
+               _ptr(route_a), _ptr(beam_a))
     lib = _load()
     order_a = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     parent_a = None if parent is None else np.ascontiguousarray(parent, dtype=np.int32)

@@ -544,6 +544,14 @@ typedef struct {
     int greedy_beam_size; /* Alg. 4 trim */
     int conv_threshold;   /* Alg. 5 */
     int hybrid_beam_size; /* Alg. 7 trim */
+    /* Optional per-query plan (a predictor in place of Alg. 6's rule; not in
+     * the paper).  route[qi] != 0: after the greedy phase the query's result
+     * is its exact NLJ row (brute-force scan) and no expansion runs; the soft
+     * cache is taken over the nodes the greedy phase visited.  beam[qi]: the
+     * query runs the hybrid expansion with hybrid_beam_size = beam[qi] when
+     * beam[qi] > 0, the plain BFS expansion when beam[qi] == 0.  NULL: unused. */
+    const uint8_t *route;
+    const int32_t *beam;
 } vjo_cfg;
 
 /* per-query outputs of vjo_join */
@@ -707,14 +715,22 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
             if (npq > cfg->greedy_beam_size) npq = cfg->greedy_beam_size;
         }
 
-        /* --- Alg. 6 CheckHybrid */
+        /* --- Alg. 6 CheckHybrid (or the per-query plan, when given) */
         int hyb;
-        if (cfg->adapt_hybrid) hyb = vjo_ood(X, nx, Q, d, metric, adj, R, qn, NULL, NULL);
-        else hyb = cfg->force_hybrid;
+        int beam = cfg->hybrid_beam_size;
+        const int routed = cfg->route && cfg->route[qi];
+        if (cfg->beam) {
+            beam = cfg->beam[qi];
+            hyb = beam > 0;
+        } else if (cfg->adapt_hybrid) {
+            hyb = vjo_ood(X, nx, Q, d, metric, adj, R, qn, NULL, NULL);
+        } else {
+            hyb = cfg->force_hybrid;
+        }
 
         /* --- Alg. 7 ExpansionPhase (merged index: min-priority queue by dist) */
         npq = 0;
-        for (int64_t j = 0; j < nI; j++) {
+        for (int64_t j = 0; j < nI && !routed; j++) {
             cand_t c = {dv[I[j]], I[j]};
             PQ_PUSH(c);
         }
@@ -739,7 +755,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
                     PQ_PUSH(c);
                     /* reading of "trim to at most max(beam, |Q|-1)": after an  */
                     /* out-range insert, if |Q| > beam drop the largest key     */
-                    if (npq > cfg->hybrid_beam_size) npq--;
+                    if (npq > beam) npq--;
                 }
             }
         }
@@ -764,6 +780,18 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
             hard[qi] = (int32_t *)malloc((size_t)(nI + 1) * sizeof(int32_t));
             memcpy(hard[qi], I, (size_t)nI * sizeof(int32_t));
             hard_n[qi] = nI;
+        }
+        if (routed) {
+            /* brute-force route: the exact NLJ row replaces the expansion */
+            nI = 0;
+            for (int64_t x = 0; x < nx; x++) {
+                double dd = vjo_dist(X + (size_t)x * d, qv, d, metric);
+                if (dd < eps) {
+                    dv[x] = dd;
+                    I_PUSH((int32_t)x);
+                }
+            }
+            hyb = 2;
         }
 
         /* R <- R U I (sorted by data id for the CSR) */

@@ -81,6 +81,8 @@ struct JoinParams {
     const int32_t* parent;
     const int32_t* child_off;
     const int32_t* child_list;
+    const uint8_t* route;  // per-query plan (nullptr: none)
+    const int32_t* qbeam;
     int* ready;
     int64_t nx, nq;
     int dp4, dp, d, R, metric;
@@ -490,9 +492,18 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         entry_in_nq = __any_sync(VJ_FULL, entry_in_nq);
         seed_in_nq = __any_sync(VJ_FULL, seed_in_nq);
 
-        // ---- Alg. 6 CheckHybrid (adapt on the merged index decides; force otherwise)
+        // ---- Alg. 6 CheckHybrid (adapt on the merged index decides; force
+        // otherwise), or the per-query plan when one is set: a routed query
+        // stops after its greedy phase (its row comes from the brute-force
+        // scan); a planned beam > 0 selects the hybrid expansion with that
+        // queue size, 0 the BFS expansion
+        const bool routed = P.route != nullptr && P.route[qi] != 0;
+        int hbq = P.hbeam;
         int hyb = P.force;
-        if (P.adapt && !failed) {
+        if (P.qbeam) {
+            hbq = P.qbeam[qi];
+            hyb = hbq > 0;
+        } else if (P.adapt && !failed && !routed) {
             const bool isd = nid_l >= 0 && nid_l < P.nx;
             float d1s = isd ? key_to_dist(P, nkey_l) : 0.f;
             const unsigned dmask = __ballot_sync(VJ_FULL, isd);
@@ -571,9 +582,14 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             hyb = ood;
         }
         int expansions = 0;
+        if (routed) {
+            s.nres = 0;  // the scan supplies the row
+            hyb = 2;
+        }
 
         // ---- Alg. 7 ExpansionPhase
-        if (!failed && !hyb) {
+        if (routed) {
+        } else if (!failed && !hyb) {
             int fp = 0;
             while (fp < s.nres) {
                 const int nb = min(FB, s.nres - fp);
@@ -685,7 +701,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 for (int c = 0; c < nc; c++) {
                     if ((inm >> c) & 1u) np++;
                     else if ((outm >> c) & 1u) {
-                        if (np + o + 1 <= P.hbeam) o++;
+                        if (np + o + 1 <= hbq) o++;
                     }
                 }
                 const int kfin = o;
@@ -799,6 +815,16 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
     }
 }
 
+// rows of routed queries: CSR rows of the scan, placed at `base` in the pool
+__global__ void k_merge_routed(const int32_t* __restrict__ routed, int64_t nr, const int64_t* __restrict__ soff,
+                               int64_t base, int64_t* __restrict__ seg, int32_t* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    const int q = routed[i];
+    seg[q] = base + soff[q];
+    count[q] = (int32_t)(soff[q + 1] - soff[q]);
+}
+
 template <int G, int NPL, int U>
 void launch_join_t(const JoinParams& P, int blocks, cudaStream_t st) {
     size_t smem = sizeof(WarpSmem) * WPB;
@@ -864,7 +890,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     if (gmax < GCAP0) gmax = GCAP0;
     const int grcap = gmax / 2;
     const int hbeam = budget > 0 ? budget : ix->p.hybrid_beam;
-    const int oqcap = hbeam + 2;
+    const int oqcap = std::max(hbeam, ix->has_beam ? ix->plan_max_beam : 0) + 2;
     const int64_t wstride = ((int64_t)2 * gmax + 2 * grcap + 4 * oqcap + 31) / 32 * 32;
     if (ix->wspace_warps < warps || ix->wspace.n < (size_t)(warps * wstride)) {
         ix->wspace.free_(s);
@@ -885,6 +911,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.parent = ix->parent.p;
     P.child_off = ix->child_off.p;
     P.child_list = ix->child_list.p;
+    P.route = ix->has_route ? ix->plan_route.p : nullptr;
+    P.qbeam = ix->has_beam ? ix->plan_beam.p : nullptr;
     P.ready = ix->ready.p;
     P.nx = ix->nx;
     P.nq = nq;
@@ -970,7 +998,49 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
                                                         : "queue overflow");
         throw VjError{VJ_ERR_STATE};
     }
-    const int64_t nnz = (int64_t)hc[C_POOL];
+    int64_t nnz = (int64_t)hc[C_POOL];
+
+    // ---- brute-force route: rows of the routed queries from the tensor-core
+    // scan, appended to the pool behind the traversal's pairs
+    double ms_scan = 0.0;
+    int64_t scand = 0;
+    if (ix->has_route && ix->nrouted > 0) {
+        DBuf<int64_t> soff;
+        DBuf<int32_t> sid;
+        DBuf<float> sd;
+        int64_t snnz = 0;
+        vj_scan_rows_csr(ix, ix->routed.p, ix->nrouted, eps, soff, sid, sd, &snnz, &ms_scan);
+        scand = ix->last_scan_cand;
+        launches += 8;
+        if (nnz + snnz > (int64_t)ix->pool_id.n) {
+            DBuf<int32_t> nid;
+            DBuf<float> nd;
+            const int64_t cap = nnz + snnz + (nnz + snnz) / 4 + 1024;
+            nid.alloc(cap, s);
+            nd.alloc(cap, s);
+            if (nnz > 0) {
+                VJ_CUDA(cudaMemcpyAsync(nid.p, ix->pool_id.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                VJ_CUDA(cudaMemcpyAsync(nd.p, ix->pool_d.p, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            }
+            ix->pool_id.free_(s);
+            ix->pool_d.free_(s);
+            ix->pool_id = nid;
+            ix->pool_d = nd;
+            nid.p = nullptr;
+            nd.p = nullptr;
+        }
+        if (snnz > 0) {
+            VJ_CUDA(cudaMemcpyAsync(ix->pool_id.p + nnz, sid.p, snnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            VJ_CUDA(cudaMemcpyAsync(ix->pool_d.p + nnz, sd.p, snnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+        k_merge_routed<<<vj_div_up(ix->nrouted, 256), 256, 0, s>>>(ix->routed.p, ix->nrouted, soff.p, nnz, ix->seg.p,
+                                                                  ix->count.p);
+        VJ_LAUNCH_CHECK();
+        nnz += snnz;
+        soff.free_(s);
+        sid.free_(s);
+        sd.free_(s);
+    }
 
     // ---- CSR: offsets by scan, then per-query sorted copy
     ix->offsets.ensure(nq + 1, s);
@@ -1000,5 +1070,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     // algorithmic bytes: one vector per distance, one adjacency row per row read
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
     st->kernel_launches = launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort
+    st->ms_scan = ms_scan;
+    st->scan_candidates = scand;
     *nnz_out = nnz;
 }

@@ -652,6 +652,14 @@ void vj_build_knn(vj_index* ix) {
 
 void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids, DBuf<float>& dists,
                           int64_t* nnz_out, double* ms_out) {
+    vj_scan_rows_csr(ix, nullptr, ix->nq, eps, offsets, ids, dists, nnz_out, ms_out);
+}
+
+// Exact join rows of the queries `qrows` (nullptr: all queries) by the
+// tensor-core scan and the exact re-check; CSR over all nq queries, rows of
+// queries not listed are empty.
+void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int64_t>& offsets,
+                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out) {
     cudaStream_t s = ix->stream;
     const int64_t nx = ix->nx, nq = ix->nq;
     cudaEvent_t e0, e1;
@@ -685,7 +693,7 @@ void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<
     ctr.alloc(2, s);
     VJ_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
     double ms_scan = 0.0;
-    const int64_t nc = vj_tc_scan_candidates(ix, nullptr, nq, eps, cq, cx, &ms_scan);
+    const int64_t nc = nr > 0 ? vj_tc_scan_candidates(ix, qrows, nr, eps, cq, cx, &ms_scan) : 0;
     ix->last_scan_ms = ms_scan;
     ix->last_scan_cand = nc;
     DBuf<int32_t> counts, cursor;

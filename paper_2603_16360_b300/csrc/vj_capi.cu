@@ -78,6 +78,10 @@ static void free_index(vj_index* ix) {
     ix->parent.free_(s);
     ix->order.free_(s);
     ix->depth.free_(s);
+    ix->plan_route.free_(s);
+    ix->plan_beam.free_(s);
+    ix->routed.free_(s);
+    ix->xbf.free_(s);
     ix->child_off.free_(s);
     ix->child_list.free_(s);
     ix->roots.free_(s);
@@ -176,6 +180,44 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
         ix->p.work_sharing = p->work_sharing;
         ix->p.adapt_hybrid = p->adapt_hybrid;
         ix->p.force_hybrid = p->force_hybrid;
+    });
+}
+
+extern "C" vj_status vj_set_plan(vj_index* ix, const uint8_t* route, const int32_t* beam) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        cudaStream_t s = ix->stream;
+        const int64_t nq = ix->nq;
+        ix->has_route = false;
+        ix->has_beam = false;
+        ix->nrouted = 0;
+        ix->plan_max_beam = 0;
+        if (route) {
+            std::vector<int32_t> ids;
+            for (int64_t q = 0; q < nq; q++)
+                if (route[q]) ids.push_back((int32_t)q);
+            ix->plan_route.ensure(nq, s);
+            VJ_CUDA(cudaMemcpyAsync(ix->plan_route.p, route, nq, cudaMemcpyHostToDevice, s));
+            ix->routed.ensure(std::max<size_t>(ids.size(), 1), s);
+            if (!ids.empty())
+                VJ_CUDA(cudaMemcpyAsync(ix->routed.p, ids.data(), ids.size() * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice, s));
+            ix->nrouted = (int64_t)ids.size();
+            ix->has_route = true;
+        }
+        if (beam) {
+            int mx = 0;
+            for (int64_t q = 0; q < nq; q++) {
+                VJ_REQUIRE(beam[q] >= 0 && beam[q] <= (1 << 20), VJ_ERR_ARG, "beam[%lld] out of range",
+                           (long long)q);
+                mx = std::max(mx, (int)beam[q]);
+            }
+            ix->plan_beam.ensure(nq, s);
+            VJ_CUDA(cudaMemcpyAsync(ix->plan_beam.p, beam, nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            ix->plan_max_beam = mx;
+            ix->has_beam = true;
+        }
+        VJ_CUDA(cudaStreamSynchronize(s));
     });
 }
 

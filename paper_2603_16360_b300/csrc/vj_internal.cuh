@@ -116,6 +116,13 @@ struct vj_index {
     int64_t nroots = 0;
     DBuf<int32_t> ready;       // [nq] join dispatch queue
     DBuf<__nv_bfloat16> xbf;   // [nx][kp] BF16 copy of the data rows (tensor-core scans)
+    // per-query plan (route to the brute-force scan / hybrid budget), optional
+    DBuf<uint8_t> plan_route;  // [nq]
+    DBuf<int32_t> plan_beam;   // [nq]
+    DBuf<int32_t> routed;      // routed query indices
+    int64_t nrouted = 0;
+    bool has_route = false, has_beam = false;
+    int plan_max_beam = 0;
     bool bf16_exact = false;   // BF16 Gram keys are exact for these inputs (small integers)
     double maxnorm = 0.0;      // largest vector norm (FP64)
     double last_scan_ms = 0.0; // device time of the last tensor-core scan
@@ -152,6 +159,8 @@ struct CsrOut {
 };
 void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids,
                           DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
+void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int64_t>& offsets,
+                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
 

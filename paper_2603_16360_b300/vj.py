@@ -21,7 +21,7 @@ VJ_WS_NONE, VJ_WS_HARD, VJ_WS_SOFT, VJ_WS_SELF = 0, 1, 2, 3
 VJ_PREC_FP32, VJ_PREC_BF16, VJ_PREC_FP8 = 0, 1, 2
 
 # every function declared in include/vj.h
-EXPORTS = ["vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_join",
+EXPORTS = ["vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_result_free", "vj_free", "vj_last_error"]
 
@@ -80,6 +80,8 @@ def load():
     lib.vj_set_stream.restype = I
     lib.vj_set_join_params.argtypes = [P, C.POINTER(vj_params)]
     lib.vj_set_join_params.restype = I
+    lib.vj_set_plan.argtypes = [P, P, P]
+    lib.vj_set_plan.restype = I
     for fn in ("vj_join", "vj_join_device"):
         getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
         getattr(lib, fn).restype = I
@@ -242,6 +244,13 @@ def vj_set_join_params(ix: Index, params: vj_params | None = None, **kw):
     for k, v in kw.items():
         setattr(p, k, v)
     _check(load().vj_set_join_params(ix.handle, C.byref(p)))
+
+
+def vj_set_plan(ix: Index, route=None, beam=None):
+    """Per-query plan (route to the brute-force scan, hybrid queue size) for later joins."""
+    r = None if route is None else np.ascontiguousarray(route, dtype=np.uint8)
+    b = None if beam is None else np.ascontiguousarray(beam, dtype=np.int32)
+    _check(load().vj_set_plan(ix.handle, None if r is None else r.ctypes.data, None if b is None else b.ctypes.data))
 
 
 def vj_join(ix: Index, eps: float, budget: int = 0) -> Result:

@@ -203,3 +203,40 @@ def test_errors_are_reported_not_raised_on_device():
     r = vj.vj_join(ix, 1.0)  # the index stays usable
     assert r.offsets.shape == (6,)
     ix.free()
+
+
+# ------------------------------------------------------------------ per-query plan
+@pytest.mark.parametrize("ws", [vj.VJ_WS_SELF, vj.VJ_WS_SOFT], ids=["self", "sws"])
+def test_plan_route_and_beams_match_oracle(built, oracle, ws):
+    """Routed queries take their rows from the tensor-core scan (exact after
+    re-check), others run BFS or hybrid with their planned queue size; every
+    row, visited count, soft cache and route/hybrid flag equals the oracle's
+    run of the same plan on the same graph."""
+    name, w, ix = built
+    eps = _calib_eps(oracle, w, 10, w.metric)
+    rng = np.random.default_rng(11)
+    route = (rng.random(w.nq) < 0.25).astype(np.uint8)
+    beam = np.where(rng.random(w.nq) < 0.4, 8, 0).astype(np.int32)
+    vj.vj_set_join_params(ix, work_sharing=ws, adapt_hybrid=1)
+    vj.vj_set_plan(ix, route, beam)
+    try:
+        r = vj.vj_join(ix, eps)
+    finally:
+        vj.vj_set_plan(ix, None, None)
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    o = oracle.join(w.X, w.Q, adj, entry, np.float32(eps), metric=w.metric,
+                    work_sharing={vj.VJ_WS_SELF: oracle.WS_SELF, vj.VJ_WS_SOFT: oracle.WS_SOFT}[ws],
+                    adapt_hybrid=True, order=order, parent=parent, route=route, beam=beam)
+    band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+    diff = (_pairs(r.offsets, r.ids) ^ _pairs(o.offsets, o.ids)) - band
+    assert not diff, f"{name}: {len(diff)} pairs differ, e.g. {sorted(diff)[:5]}"
+    np.testing.assert_array_equal(r.hybrid, o.hybrid)
+    np.testing.assert_array_equal(r.steps, o.steps)
+    np.testing.assert_array_equal(r.cache, o.cache)
+    # routed rows are complete: they equal the exact join's rows
+    off, ids, _ = oracle.nlj(w.X, w.Q[route.astype(bool)], float(np.float32(eps)), w.metric)
+    rq = np.nonzero(route)[0]
+    got = {(int(rq[i]), int(x)) for i in range(len(rq)) for x in r.row(int(rq[i]))}
+    exp = {(int(rq[i]), int(x)) for i in range(len(rq)) for x in ids[off[i]:off[i + 1]]}
+    assert not ((got ^ exp) - band)
+    assert r.stats["scan_candidates"] >= len(exp) - len(band)

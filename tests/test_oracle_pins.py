@@ -384,3 +384,37 @@ def test_adapt_flags_shifted_queries(oracle):
     flags = np.array([oracle.ood(w.X, w.Q, adj, w.nx + q)[0] for q in range(w.nq)])
     assert flags[~w.ood].mean() < 0.1
     assert flags[w.ood].mean() > 0.6
+
+
+# ---------------------------------------------------------------- per-query plan
+def test_plan_reduces_to_paper_modes_and_nlj(oracle):
+    """A per-query plan (route to brute force / hybrid beam) must reduce to the
+    paper's modes: all-zero beams = BFS, all-b beams = forced hybrid with beam b,
+    routed rows = the NLJ rows; a mixed plan (self seeding, no cross-query
+    dependency) equals each query's uniform-mode row."""
+    w = inputs.gauss_small(seed=21, nx=500, nq=60, d=6, k=4, ood_frac=0.3, shift=6.0)
+    adj, entry, _ = oracle.build_graph(w.X, w.Q, 8, 16)
+    eps = 2.0
+    nq = w.nq
+    bfs = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF)
+    hyb8 = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF, force_hybrid=True, hybrid_beam_size=8)
+    off, ids, _ = oracle.nlj(w.X, w.Q, eps)
+    p0 = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF, beam=np.zeros(nq, np.int32))
+    p8 = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF, beam=np.full(nq, 8, np.int32))
+    pr = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF, route=np.ones(nq, np.uint8))
+    assert _pairs(p0.offsets, p0.ids) == _pairs(bfs.offsets, bfs.ids)
+    assert np.array_equal(p0.steps, bfs.steps)
+    assert _pairs(p8.offsets, p8.ids) == _pairs(hyb8.offsets, hyb8.ids)
+    assert np.array_equal(p8.steps, hyb8.steps)
+    assert _pairs(pr.offsets, pr.ids) == _pairs(off, ids)
+    assert np.all(pr.hybrid == 2)
+    # routed queries only run the greedy phase: their visited set is the probe
+    probe_only = oracle.join(w.X, w.Q, adj, entry, 1e-9, work_sharing=oracle.WS_SELF)
+    assert np.array_equal(pr.steps, probe_only.steps)
+    rng = np.random.default_rng(3)
+    route = (rng.random(nq) < 0.3).astype(np.uint8)
+    beam = np.where(rng.random(nq) < 0.5, 8, 0).astype(np.int32)
+    mix = oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SELF, route=route, beam=beam)
+    for q in range(nq):
+        ref = pr if route[q] else (p8 if beam[q] else p0)
+        assert list(mix.row(q)) == list(ref.row(q)), q
