@@ -87,6 +87,7 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this call launched */
     double ms_scan;            /* device time of the tensor-core brute-force scan (exact join / routed queries) */
     int64_t scan_candidates;   /* pairs the scan passed to the exact re-check */
+    double ms_prologue;        /* device time of the learned prologue (features + predictor + plan) */
 } vj_stats;
 
 /* CSR result of a join.  ids are data ids (0..nx-1), ascending within each
@@ -142,6 +143,46 @@ vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
  *   beam[q] == 0: the BFS expansion.
  * Errors: VJ_ERR_ARG (beam outside [0, 2^20]). */
 vj_status vj_set_plan(vj_index *ix, const uint8_t *route, const int32_t *beam);
+
+/* ---- Learned route / budget predictor (not in the paper, which decides with
+ * the d1/d2 > 1.5 rule of Sec. 4.4 only; that rule stays the default).
+ * A 3-layer MLP din -> h1 -> h2 -> 2 (ReLU): output 0 regresses
+ * log2(budget + 1), output 1 is the route logit.  Loss = mean squared error on
+ * output 0 + binary cross-entropy with logits on output 1, averaged over rows.
+ * Parameters: one flat FP32 array W1[h1][din] b1 W2[h2][h1] b2 W3[2][h2] b3.
+ * Inputs are standardised per feature with the training rows' mean / std. */
+typedef struct vj_mlp vj_mlp;
+vj_status vj_mlp_create(int din, int h1, int h2, uint64_t seed, vj_mlp **out); /* He-uniform init */
+int64_t vj_mlp_num_params(const vj_mlp *m);
+/* host buffers: flat [num_params], mu/sd [din] (mu/sd may be NULL) */
+vj_status vj_mlp_get_params(const vj_mlp *m, float *flat, float *mu, float *sd);
+/* mu and sd both NULL: no standardisation */
+vj_status vj_mlp_set_params(vj_mlp *m, const float *flat, const float *mu, const float *sd);
+/* Mean loss and its gradient (flat, host) over n host rows x [n][din] with
+ * targets t_reg [n], t_cls [n] (0/1); rows used as given (no standardisation). */
+vj_status vj_mlp_loss_grad(vj_mlp *m, const float *x, const float *t_reg, const float *t_cls, int64_t n,
+                           double *loss, float *grad);
+/* Adam (beta 0.9 / 0.999, eps 1e-8) over seeded shuffled mini-batches;
+ * sets the standardisation from x first.  final_loss: last epoch's mean. */
+vj_status vj_mlp_train(vj_mlp *m, const float *x, const float *t_reg, const float *t_cls, int64_t n, int epochs,
+                       int batch, float lr, uint64_t seed, double *final_loss);
+/* outputs [n][2] (host) for host rows x [n][din], standardised */
+vj_status vj_mlp_predict(vj_mlp *m, const float *x, int64_t n, float *out);
+void vj_mlp_free(vj_mlp *m);
+
+/* Predictor features of every query at threshold eps, host [nq][7 + d]:
+ * d1/eps, d2/eps, d1/d2 (Sec. 4.4), dist(q, entry)/eps, dist to the nearest
+ * data neighbour/eps, #data neighbours/R, #data neighbours within eps/R,
+ * then the d coordinates of q. */
+vj_status vj_features(vj_index *ix, float eps, float *out);
+
+/* Use predictor m (din = 7 + d; NULL detaches) for joins with
+ * params.learned = 1: a prologue computes the features, runs m and routes
+ * a query to the brute-force scan when sigmoid(output 1) > route_threshold,
+ * else gives it the hybrid queue size 2^output0 - 1 (0 = BFS below 4,
+ * capped at beam_cap).  The index keeps the pointer; m must outlive it or
+ * be detached. */
+vj_status vj_attach_predictor(vj_index *ix, vj_mlp *m, float route_threshold, int beam_cap);
 
 /* Approximate join (Alg. 1 on the merged index) at threshold eps > 0.
  * budget > 0 overrides hybrid_beam for this call.  The result lives in host

@@ -872,6 +872,36 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
                "work_sharing=hard is not implemented by the GPU join");
     VJ_REQUIRE(ix->p.work_sharing >= 0 && ix->p.work_sharing <= 3, VJ_ERR_ARG, "bad work_sharing");
 
+    // learned prologue (features -> predictor -> per-query plan) in place of
+    // the d1/d2 rule; the plan it sets lives for this join only
+    double ms_pro = 0.0;
+    const bool learned = ix->p.learned != 0;
+    if (learned) {
+        cudaEvent_t p0, p1;
+        VJ_CUDA(cudaEventCreate(&p0));
+        VJ_CUDA(cudaEventCreate(&p1));
+        VJ_CUDA(cudaEventRecord(p0, s));
+        vj_learned_prologue(ix, eps);
+        VJ_CUDA(cudaEventRecord(p1, s));
+        VJ_CUDA(cudaEventSynchronize(p1));
+        float t = 0.f;
+        VJ_CUDA(cudaEventElapsedTime(&t, p0, p1));
+        ms_pro = t;
+        cudaEventDestroy(p0);
+        cudaEventDestroy(p1);
+    }
+    struct PlanReset {
+        vj_index* ix;
+        bool on;
+        ~PlanReset() {
+            if (on) {
+                ix->has_route = false;
+                ix->has_beam = false;
+                ix->nrouted = 0;
+            }
+        }
+    } plan_reset{ix, learned};
+
     ix->cache.ensure(nq, s);
     ix->steps.ensure(nq, s);
     ix->hyb.ensure(nq, s);
@@ -1066,7 +1096,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     st->spill_queries = (int64_t)hc[C_SPILL];
     st->ms_traverse = t_trav;
     st->ms_csr = t_csr;
-    st->ms_total = t_trav + t_csr;
+    st->ms_prologue = ms_pro;
+    st->ms_total = ms_pro + t_trav + t_csr;
     // algorithmic bytes: one vector per distance, one adjacency row per row read
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
     st->kernel_launches = launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort

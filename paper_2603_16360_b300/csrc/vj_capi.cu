@@ -61,8 +61,8 @@ static void check_join_params(const vj_params& p) {
                VJ_ERR_ARG, "work_sharing must be NONE, SOFT or SELF (HARD is not implemented)");
     VJ_REQUIRE(p.hybrid_beam >= 0 && p.hybrid_beam <= (1 << 20), VJ_ERR_ARG, "hybrid_beam out of range");
     VJ_REQUIRE(p.greedy_beam >= 1, VJ_ERR_ARG, "greedy_beam must be >= 1");
-    VJ_REQUIRE(p.learned == 0 && p.route_bruteforce == 0, VJ_ERR_ARG,
-               "learned / route_bruteforce are reserved and must be 0");
+    VJ_REQUIRE(p.learned == 0 || p.learned == 1, VJ_ERR_ARG, "learned must be 0 or 1");
+    VJ_REQUIRE(p.route_bruteforce == 0, VJ_ERR_ARG, "route_bruteforce is reserved and must be 0");
 }
 
 static void free_index(vj_index* ix) {
@@ -78,6 +78,11 @@ static void free_index(vj_index* ix) {
     ix->parent.free_(s);
     ix->order.free_(s);
     ix->depth.free_(s);
+    ix->qstat.free_(s);
+    ix->qdn.free_(s);
+    ix->feat.free_(s);
+    ix->pred_y.free_(s);
+    ix->ctr_plan.free_(s);
     ix->plan_route.free_(s);
     ix->plan_beam.free_(s);
     ix->routed.free_(s);
@@ -180,6 +185,7 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
         ix->p.work_sharing = p->work_sharing;
         ix->p.adapt_hybrid = p->adapt_hybrid;
         ix->p.force_hybrid = p->force_hybrid;
+        ix->p.learned = p->learned;
     });
 }
 

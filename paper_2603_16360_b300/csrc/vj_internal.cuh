@@ -38,6 +38,7 @@ struct VjError {
 
 // ------------------------------------------------------------------ constants
 constexpr int VJ_NUM_SMS_HINT = 148;
+constexpr int VJ_NFEAT = 7;  // scalar features of the learned predictor (before the d coordinates)
 constexpr float VJ_F32_U = 5.9604645e-8f;  // unit roundoff of binary32 (2^-24)
 
 // device error codes (written by kernels into a device word, read by the host)
@@ -123,6 +124,15 @@ struct vj_index {
     int64_t nrouted = 0;
     bool has_route = false, has_beam = false;
     int plan_max_beam = 0;
+    // learned predictor (optional): cached per-query statistics and the model
+    DBuf<float> qstat;         // [nq][5] d1, d2, dist to entry, nearest data neighbour, #data neighbours
+    DBuf<float> qdn;           // [nq][R] distances to data neighbours (+inf otherwise)
+    DBuf<float> feat;          // [nq][VJ_NFEAT + d]
+    DBuf<float> pred_y;        // [nq][2]
+    DBuf<unsigned long long> ctr_plan;
+    struct vj_mlp* predictor = nullptr;
+    float route_threshold = 0.5f;
+    int beam_cap = 256;
     bool bf16_exact = false;   // BF16 Gram keys are exact for these inputs (small integers)
     double maxnorm = 0.0;      // largest vector norm (FP64)
     double last_scan_ms = 0.0; // device time of the last tensor-core scan
@@ -168,6 +178,9 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
 // candidate (query index, data id) pairs, exact after re-check
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
                               DBuf<int32_t>& cx, double* ms_out);
+
+// learned prologue: features -> predictor -> per-query plan; returns #routed
+int64_t vj_learned_prologue(vj_index* ix, float eps);
 
 // utilities
 void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix);

@@ -21,7 +21,9 @@ VJ_WS_NONE, VJ_WS_HARD, VJ_WS_SOFT, VJ_WS_SELF = 0, 1, 2, 3
 VJ_PREC_FP32, VJ_PREC_BF16, VJ_PREC_FP8 = 0, 1, 2
 
 # every function declared in include/vj.h
-EXPORTS = ["vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
+EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_set_params", "vj_mlp_loss_grad",
+           "vj_mlp_train", "vj_mlp_predict", "vj_mlp_free", "vj_features", "vj_attach_predictor",
+           "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_result_free", "vj_free", "vj_last_error"]
 
@@ -50,7 +52,7 @@ class vj_stats(C.Structure):
                 ("hybrid_queries", C.c_int64), ("rechecks", C.c_int64), ("spill_queries", C.c_int64),
                 ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
                 ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
-                ("scan_candidates", C.c_int64)]
+                ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double)]
 
 
 class vj_result(C.Structure):
@@ -82,6 +84,26 @@ def load():
     lib.vj_set_join_params.restype = I
     lib.vj_set_plan.argtypes = [P, P, P]
     lib.vj_set_plan.restype = I
+    lib.vj_mlp_create.argtypes = [I, I, I, C.c_uint64, C.POINTER(P)]
+    lib.vj_mlp_create.restype = I
+    lib.vj_mlp_num_params.argtypes = [P]
+    lib.vj_mlp_num_params.restype = I64
+    lib.vj_mlp_get_params.argtypes = [P, P, P, P]
+    lib.vj_mlp_get_params.restype = I
+    lib.vj_mlp_set_params.argtypes = [P, P, P, P]
+    lib.vj_mlp_set_params.restype = I
+    lib.vj_mlp_loss_grad.argtypes = [P, P, P, P, I64, C.POINTER(C.c_double), P]
+    lib.vj_mlp_loss_grad.restype = I
+    lib.vj_mlp_train.argtypes = [P, P, P, P, I64, I, I, C.c_float, C.c_uint64, C.POINTER(C.c_double)]
+    lib.vj_mlp_train.restype = I
+    lib.vj_mlp_predict.argtypes = [P, P, I64, P]
+    lib.vj_mlp_predict.restype = I
+    lib.vj_mlp_free.argtypes = [P]
+    lib.vj_mlp_free.restype = None
+    lib.vj_features.argtypes = [P, C.c_float, P]
+    lib.vj_features.restype = I
+    lib.vj_attach_predictor.argtypes = [P, P, C.c_float, I]
+    lib.vj_attach_predictor.restype = I
     for fn in ("vj_join", "vj_join_device"):
         getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
         getattr(lib, fn).restype = I
@@ -244,6 +266,87 @@ def vj_set_join_params(ix: Index, params: vj_params | None = None, **kw):
     for k, v in kw.items():
         setattr(p, k, v)
     _check(load().vj_set_join_params(ix.handle, C.byref(p)))
+
+
+NFEAT = 7
+
+
+class MLP:
+    """The learned route / budget predictor (vj_mlp in include/vj.h)."""
+
+    def __init__(self, din: int, h1: int = 256, h2: int = 256, seed: int = 0):
+        h = C.c_void_p()
+        _check(load().vj_mlp_create(din, h1, h2, seed, C.byref(h)))
+        self._h, self.din, self.h1, self.h2 = h, din, h1, h2
+
+    @property
+    def handle(self):
+        return self._h
+
+    def num_params(self) -> int:
+        return int(load().vj_mlp_num_params(self._h))
+
+    def get_params(self):
+        flat = np.zeros(self.num_params(), np.float32)
+        mu = np.zeros(self.din, np.float32)
+        sd = np.zeros(self.din, np.float32)
+        _check(load().vj_mlp_get_params(self._h, flat.ctypes.data, mu.ctypes.data, sd.ctypes.data))
+        return flat, mu, sd
+
+    def set_params(self, flat, mu=None, sd=None):
+        flat = np.ascontiguousarray(flat, np.float32)
+        mu_a = None if mu is None else np.ascontiguousarray(mu, np.float32)
+        sd_a = None if sd is None else np.ascontiguousarray(sd, np.float32)
+        _check(load().vj_mlp_set_params(self._h, flat.ctypes.data, None if mu_a is None else mu_a.ctypes.data,
+                                         None if sd_a is None else sd_a.ctypes.data))
+
+    def loss_grad(self, x, t_reg, t_cls):
+        x = np.ascontiguousarray(x, np.float32)
+        tr = np.ascontiguousarray(t_reg, np.float32)
+        tc = np.ascontiguousarray(t_cls, np.float32)
+        loss = C.c_double()
+        g = np.zeros(self.num_params(), np.float32)
+        _check(load().vj_mlp_loss_grad(self._h, x.ctypes.data, tr.ctypes.data, tc.ctypes.data, len(x),
+                                       C.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, x, t_reg, t_cls, epochs=20, batch=256, lr=1e-3, seed=0) -> float:
+        x = np.ascontiguousarray(x, np.float32)
+        tr = np.ascontiguousarray(t_reg, np.float32)
+        tc = np.ascontiguousarray(t_cls, np.float32)
+        loss = C.c_double()
+        _check(load().vj_mlp_train(self._h, x.ctypes.data, tr.ctypes.data, tc.ctypes.data, len(x), epochs, batch,
+                                   float(lr), seed, C.byref(loss)))
+        return loss.value
+
+    def predict(self, x):
+        x = np.ascontiguousarray(x, np.float32)
+        out = np.zeros((len(x), 2), np.float32)
+        _check(load().vj_mlp_predict(self._h, x.ctypes.data, len(x), out.ctypes.data))
+        return out
+
+    def free(self):
+        if self._h:
+            load().vj_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vj_features(ix: Index, eps: float):
+    inf = ix.info()
+    out = np.zeros((inf["nq"], NFEAT + inf["d"]), np.float32)
+    _check(load().vj_features(ix.handle, float(eps), out.ctypes.data))
+    return out
+
+
+def vj_attach_predictor(ix: Index, mlp, route_threshold: float = 0.5, beam_cap: int = 256):
+    _check(load().vj_attach_predictor(ix.handle, None if mlp is None else mlp.handle, float(route_threshold),
+                                      int(beam_cap)))
 
 
 def vj_set_plan(ix: Index, route=None, beam=None):

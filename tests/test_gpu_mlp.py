@@ -1,0 +1,117 @@
+"""GPU predictor (through the C ABI) against the FP64 MLP oracle, and the
+learned join prologue against the plans it must reduce to."""
+import numpy as np
+import pytest
+
+from paper_2603_16360_b300 import inputs
+from paper_2603_16360_b300 import vj
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16360_b300 import build as b
+    b.build()
+    vj.load()
+
+
+def test_loss_and_gradient_match_fp64_oracle():
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(1)
+    din, h1, h2, n = 20, 48, 40, 70
+    m = vj.MLP(din, h1, h2, seed=3)
+    flat = (rng.standard_normal(m.num_params()) * 0.3).astype(np.float32)
+    m.set_params(flat)
+    x = rng.standard_normal((n, din)).astype(np.float32)
+    tr = rng.standard_normal(n).astype(np.float32)
+    tc = (rng.random(n) < 0.4).astype(np.float32)
+    loss, g = m.loss_grad(x, tr, tc)
+    lref, gref = omlp.loss_grad(flat.astype(np.float64), x.astype(np.float64), tr, tc, din, h1, h2)
+    assert loss == pytest.approx(lref, rel=1e-5)
+    err = np.linalg.norm(g.astype(np.float64) - gref) / np.linalg.norm(gref)
+    assert err < 1e-5, err
+    np.testing.assert_allclose(g, gref, rtol=1e-3, atol=1e-5 * np.abs(gref).max())
+    m.free()
+
+
+def test_training_learns_and_predict_matches_oracle_forward():
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(2)
+    din, n = 12, 4000
+    x = (rng.standard_normal((n, din)) * 3 + 5).astype(np.float32)
+    tc = (x[:, 0] > 5).astype(np.float32)
+    tr = (0.5 * (x[:, 1] - 5)).astype(np.float32)
+    m = vj.MLP(din, 64, 64, seed=4)
+    l0, _ = m.loss_grad((x - x.mean(0)) / x.std(0), tr, tc)
+    lf = m.train(x, tr, tc, epochs=15, batch=128, lr=3e-3, seed=5)
+    assert lf < 0.25 * l0, (l0, lf)
+    flat, mu, sd = m.get_params()
+    y = m.predict(x[:300])
+    yref, _ = omlp.forward(flat.astype(np.float64), (x[:300].astype(np.float64) - mu) / sd, din, 64, 64)
+    np.testing.assert_allclose(y, yref, rtol=1e-4, atol=1e-4)
+    acc = ((y[:, 1] > 0) == (tc[:300] > 0.5)).mean()
+    assert acc > 0.9
+    m.free()
+
+
+def test_features_match_definitions(oracle):
+    w = inputs.gauss_small(seed=31, nx=2000, nq=200, d=16, k=8, ood_frac=0.2, shift=10.0)
+    ix = vj.vj_build(w.X, w.Q, params=vj.default_params(degree=12, knn_k=24))
+    adj, entry, _, _, _ = vj.vj_export_graph(ix)
+    eps = 3.0
+    F = vj.vj_features(ix, eps)
+    assert F.shape == (w.nq, vj.NFEAT + w.d)
+    np.testing.assert_array_equal(F[:, vj.NFEAT:], w.Q)
+    for q in range(0, w.nq, 7):
+        node = w.nx + q
+        flag, d1, d2 = oracle.ood(w.X, w.Q, adj, node)
+        nb = [int(v) for v in adj[node] if 0 <= v < w.nx]
+        dists = [oracle.dist(w.X[v], w.Q[q]) for v in nb]
+        if nb:
+            assert F[q, 0] == pytest.approx(min(d1 / eps, 100), rel=1e-4)
+            assert F[q, 4] == pytest.approx(min(min(dists) / eps, 100), rel=1e-4)
+            if not np.isnan(d2):
+                assert F[q, 1] == pytest.approx(min(d2 / eps, 100), rel=1e-4)
+                assert F[q, 2] == pytest.approx(min(d1 / d2, 100), rel=1e-4)
+        assert F[q, 5] == pytest.approx(len(nb) / 12)
+        assert F[q, 6] == pytest.approx(sum(dd < eps for dd in dists) / 12)
+        de = oracle.dist(w.X[entry] if entry < w.nx else w.Q[entry - w.nx], w.Q[q])
+        assert F[q, 3] == pytest.approx(min(de / eps, 100), rel=1e-4)
+    ix.free()
+
+
+def test_learned_join_reduces_to_route_all_and_bfs():
+    """A predictor whose route logit is +large routes every query (the join
+    then equals the exact join); one whose outputs are all very negative runs
+    BFS everywhere (the join equals the planless join without the rule)."""
+    w = inputs.gauss_small(seed=32, nx=3000, nq=300, d=16, k=8)
+    ix = vj.vj_build(w.X, w.Q, params=vj.default_params(degree=16, knn_k=32))
+    din = vj.NFEAT + w.d
+    m = vj.MLP(din, 16, 16, seed=0)
+    n = m.num_params()
+    eps = 2.5
+    ex = vj.vj_join_exact(ix, eps)
+    vj.vj_attach_predictor(ix, m, 0.5, 64)
+    for route_bias, expect in ((50.0, "exact"), (-50.0, "bfs")):
+        flat = np.zeros(n, np.float32)
+        flat[-2] = -50.0          # budget head -> 2^0 - 1 = 0 (BFS)
+        flat[-1] = route_bias     # route head
+        m.set_params(flat)
+        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1, learned=1)
+        r = vj.vj_join(ix, eps)
+        assert r.stats["ms_prologue"] > 0
+        if expect == "exact":
+            assert np.array_equal(r.offsets, ex.offsets) and np.array_equal(r.ids, ex.ids)
+            assert np.all(r.hybrid == 2)
+        else:
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, learned=0)
+            b = vj.vj_join(ix, eps)
+            assert np.array_equal(r.offsets, b.offsets) and np.array_equal(r.ids, b.ids)
+            assert np.array_equal(r.steps, b.steps)
+    vj.vj_attach_predictor(ix, None, 0.5, 64)
+    ix.free()
+    m.free()
