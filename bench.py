@@ -1,15 +1,23 @@
 """Benchmark of the merged-index vector epsilon-join on one B300.
 
-One step = one vj_join of every query of the workload against the prebuilt
-merged index (Alg. 1 on the merged index with soft work sharing and the
-adaptive hybrid rule; the offline build is timed separately, as the paper
-excludes indexing from join latency).  The default workload is the 1M-data x
-100K-query x 128-d integer Gaussian mixture ("sift_like", graph degree 32,
-eps set for a mean of 20 matches per query).
+Metric: queries/s at recall >= 0.95 against the exact join, learned+BF16 arm
+versus the plain FP32 arm.  One step = one join of every query of the
+workload against the prebuilt merged index (the offline build is timed
+separately, as the paper excludes indexing from join latency).
 
-Prints one JSON line (see the keys below).  --impl reference times the CPU
-oracle's join (FP64, single thread) on whole MST subtrees of the same workload
-instead.
+  plain FP32     MI+SWS (Alg. 1 with soft sharing) in FP32; CheckHybrid by the
+                 d1/d2 rule; when that misses recall 0.95, hybrid search for
+                 every query with the smallest queue size reaching it.
+  learned+BF16   MI+SWS with the learned prologue: a predictor (trained here
+                 on labels from the joins) routes each query to the BF16
+                 tensor-core brute-force scan (exact after re-check) or gives
+                 it a hybrid queue size; the route threshold is the largest
+                 one reaching recall 0.95.
+
+The default workload is 1M data x 100K queries x 128-d integer descriptors
+(sift_like, degree 32, eps for a mean of 20 matches per query).  Prints one
+JSON line.  --impl reference times the CPU oracle's join (FP64, one thread)
+on whole MST subtrees of the same workload instead.
 """
 from __future__ import annotations
 
@@ -34,8 +42,8 @@ def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6400.0), "measured"
-    return 6400.0, "fallback"
+        return d.get("hbm_gbs", 6400.0), d.get("bf16_tflops", 1800.0), "measured"
+    return 6400.0, 1800.0, "fallback"
 
 
 class ClockSampler:
@@ -93,46 +101,47 @@ def make_workload(name, scale):
 
 
 def calibrate_eps(vj, ix, w, target):
-    """eps with mean `target` exact matches per query (exact GPU join)."""
+    """eps with a mean of `target` exact matches per query (exact GPU join)."""
     rng = np.random.default_rng(w.seed + 7)
     qs = w.Q[rng.choice(w.nq, size=min(200, w.nq), replace=False)].astype(np.float64)
     xs = w.X[rng.choice(w.nx, size=min(20000, w.nx), replace=False)].astype(np.float64)
     d2 = (qs ** 2).sum(1)[:, None] + (xs ** 2).sum(1)[None, :] - 2 * qs @ xs.T
     dd = np.sqrt(np.maximum(d2, 0)).ravel()
-    frac = 2.0 * target / w.nx
-    guess = float(np.quantile(dd, min(frac * 4, 0.5)))
+    guess = float(np.quantile(dd, min(8.0 * target / w.nx, 0.5)))
     for _ in range(12):
         ex = vj.vj_join_exact(ix, guess)
         if ex.offsets[-1] >= target * w.nq:
             break
         guess *= 1.25
     k = int(target * w.nq)
-    eps = float(np.partition(ex.dists, k)[k])
-    return float(np.float32(eps))
+    return float(np.float32(np.partition(ex.dists, k)[k]))
 
 
-def recall_of(r, ex):
+def per_query_hits(r, ex, nx):
+    """(hits per query, exact count per query) of result r against ex."""
     nq = len(ex.offsets) - 1
-    tot = int(ex.offsets[-1])
-    hit = 0
-    for q in range(nq):
-        e = ex.ids[ex.offsets[q]:ex.offsets[q + 1]]
-        if len(e) == 0:
-            continue
-        g = r.ids[r.offsets[q]:r.offsets[q + 1]]
-        hit += len(np.intersect1d(e, g, assume_unique=True))
-    return hit / tot if tot else 1.0
+    qa = np.repeat(np.arange(nq, dtype=np.int64), np.diff(ex.offsets))
+    qb = np.repeat(np.arange(nq, dtype=np.int64), np.diff(r.offsets))
+    ka = qa * nx + ex.ids
+    kb = qb * nx + r.ids
+    common = np.intersect1d(ka, kb, assume_unique=True)
+    hits = np.bincount(common // nx, minlength=nq)
+    return hits, np.diff(ex.offsets)
+
+
+def recall_of(r, ex, nx):
+    hits, tot = per_query_hits(r, ex, nx)
+    return float(hits.sum() / max(tot.sum(), 1))
 
 
 def sample_subtrees(parent, order, target=1000):
     """Whole MST subtrees (children of the entry) totalling >= target queries, in order."""
     nq = len(parent)
-    roots = [q for q in order if parent[q] < 0]
     children = {}
     for q in range(nq):
         children.setdefault(int(parent[q]), []).append(q)
     chosen = set()
-    for r0 in roots:
+    for r0 in [q for q in order if parent[q] < 0]:
         stack = [int(r0)]
         while stack:
             a = stack.pop()
@@ -143,17 +152,35 @@ def sample_subtrees(parent, order, target=1000):
     return np.array([q for q in order if int(q) in chosen], np.int32)
 
 
-def run_cpu_oracle(w, vj, ix, eps, sample_q=1000, repeats=1, mode="adapt", budget=256):
+def run_cpu_oracle(w, vj, ix, eps, sample_q=1000, mode="adapt", budget=256):
     import oracle
     adj, entry, parent, order, _ = vj.vj_export_graph(ix)
     sub = sample_subtrees(parent, order, sample_q)
     t0 = time.perf_counter()
-    for _ in range(repeats):
-        oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SOFT, adapt_hybrid=(mode == "adapt"),
-                    force_hybrid=(mode == "force"), hybrid_beam_size=budget, order=sub, parent=parent,
-                    queries=sub)
-    dt = (time.perf_counter() - t0) / repeats
-    return len(sub), dt
+    oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SOFT, adapt_hybrid=(mode == "adapt"),
+                force_hybrid=(mode == "force"), hybrid_beam_size=budget, order=sub, parent=parent, queries=sub)
+    return len(sub), time.perf_counter() - t0
+
+
+def timed(vj, torch, ix, eps, budget, steps, warmup):
+    """Device-resident joins on torch's current stream: (ms per step, per-step stats)."""
+    stream = torch.cuda.current_stream()
+    vj.vj_set_stream(ix, stream.cuda_stream)
+    for _ in range(warmup):
+        vj.vj_join_device(ix, eps, budget).free()
+    torch.cuda.synchronize()
+    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        dr = vj.vj_join_device(ix, eps, budget)
+        s = dict(dr.stats)
+        s["nnz"] = dr.nnz
+        stats.append(s)
+        dr.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, stats
 
 
 def main():
@@ -165,6 +192,7 @@ def main():
     ap.add_argument("--workload", default="sift_like")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-only", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -191,31 +219,27 @@ def main():
     info = ix.info()
     eps = calibrate_eps(vj, ix, w, target)
     ex = vj.vj_join_exact(ix, eps)
+    wl_desc = (f"{w.name}: X={w.nx} Q={w.nq} d={w.d} {'L2' if w.metric == 0 else 'cosine'}, "
+               f"eps for a mean of {target:g} matches/query")
 
-    # operating point: plain FP32 MI+SWS with the adaptive hybrid rule; if its
-    # recall is below 0.95, hybrid search for every query with the smallest
-    # queue size (hybrid_beam_size, the paper's latency-recall knob) that
-    # reaches 0.95
-    op = None
-    ladder = [("adapt", 256)] + [("force", b) for b in (2, 4, 8, 16, 32, 64, 128, 256)]
-    for mode, budget in ladder:
+    # ---- plain FP32 arm: operating point
+    plain = None
+    for mode, budget in [("adapt", 256)] + [("force", b) for b in (2, 4, 8, 16, 32, 64, 128, 256)]:
         vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
-                              force_hybrid=int(mode == "force"), hybrid_beam=budget)
+                              force_hybrid=int(mode == "force"), hybrid_beam=budget, learned=0)
         r = vj.vj_join(ix, eps)
-        rec = recall_of(r, ex)
-        op = (mode, budget, rec, r)
+        rec = recall_of(r, ex, w.nx)
+        plain = (mode, budget, rec, r)
         if rec >= 0.95:
             break
-    mode, budget, rec, r0 = op
-    wl_desc = (f"{w.name}: X={w.nx} Q={w.nq} d={w.d} "
-               f"{'L2' if w.metric == 0 else 'cosine'}, eps for mean {target:g} matches/query")
+    pmode, pbudget, prec, pr = plain
 
     if args.impl == "reference":
         n_s, dt = [], []
         for _ in range(args.warmup):
-            run_cpu_oracle(w, vj, ix, eps, 200, mode=mode, budget=budget)
+            run_cpu_oracle(w, vj, ix, eps, 200, pmode, pbudget)
         for _ in range(args.steps):
-            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, mode=mode, budget=budget)
+            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, pmode, pbudget)
             n_s.append(n)
             dt.append(t)
         v = sum(n_s) / sum(dt)
@@ -223,8 +247,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dt) / len(dt),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS hybrid={mode} (Alg. 1), FP64, 1 thread",
-                           "eps": eps, "hybrid": mode, "budget": budget},
+                "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS hybrid={pmode} beam {pbudget} "
+                                                       "(Alg. 1), FP64, 1 thread", "eps": eps},
                 "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                  "sample": f"whole MST subtrees, {n_s[0]} queries per step, on the GPU-built graph"},
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -234,77 +258,144 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- timed device-resident joins on torch's current stream
-    stream = torch.cuda.current_stream()
-    vj.vj_set_stream(ix, stream.cuda_stream)
-    for _ in range(args.warmup):
-        vj.vj_join_device(ix, eps, budget).free()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    trav_ms, bytes_alg, launches, pairs = [], [], 0, 0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hbm, bf16, peak_kind = _peaks()
+    # ---- time the plain arm
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(pmode == "adapt"),
+                          force_hybrid=int(pmode == "force"), hybrid_beam=pbudget, learned=0)
+    p_ms, p_stats = timed(vj, torch, ix, eps, pbudget, max(2, args.steps // 2), args.warmup)
+    plain_qps = w.nq / (p_ms / 1e3)
+
+    learned = None
+    if not args.plain_only:
+        # ---- labels for the predictor on a seeded 10% training subset
+        rng = np.random.default_rng(w.seed + 99)
+        train = np.sort(rng.choice(w.nq, size=max(1, w.nq // 10), replace=False))
+        ladder = [0, 8, 32]
+        recs, steps_at = {}, {}
+        for b in ladder:
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=int(b > 0),
+                                  hybrid_beam=max(b, 1), learned=0)
+            r = vj.vj_join(ix, eps)
+            h, tot = per_query_hits(r, ex, w.nx)
+            recs[b] = np.where(tot > 0, h / np.maximum(tot, 1), 1.0)
+            steps_at[b] = r.stats, r.steps.astype(np.float64)
+        st0, s0 = steps_at[0]
+        t_step = st0["ms_traverse"] / max(s0.sum(), 1)             # ms per distance evaluation (BFS join)
+        t_bf = ex.stats["ms_scan"] / w.nq                           # ms per query of the full scan
+        budget_lab = np.full(w.nq, ladder[-1], np.int32)
+        ok_any = np.zeros(w.nq, bool)
+        cost = np.full(w.nq, np.inf)
+        for b in reversed(ladder):
+            okb = recs[b] >= 0.95
+            budget_lab = np.where(okb, b, budget_lab)
+            cost = np.where(okb, steps_at[b][1] * t_step, cost)
+            ok_any |= okb
+        route_lab = (~ok_any) | (cost > t_bf)
+        F = vj.vj_features(ix, eps)
+        mlp = vj.MLP(F.shape[1], 256, 256, seed=w.seed)
+        t_tr = time.perf_counter()
+        final_loss = mlp.train(F[train], np.log2(budget_lab[train] + 1.0), route_lab[train].astype(np.float32),
+                               epochs=30, batch=256, lr=1e-3, seed=w.seed)
+        train_s = time.perf_counter() - t_tr
+        pred = mlp.predict(F)
+        held = np.setdiff1d(np.arange(w.nq), train)
+        route_acc = float(((pred[held, 1] > 0) == route_lab[held]).mean())
+        vj.vj_attach_predictor(ix, mlp, 0.5, 64)
+        op = None
+        for thr in (0.5, 0.3, 0.15, 0.05, 0.01):
+            vj.vj_attach_predictor(ix, mlp, thr, 64)
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0, hybrid_beam=64,
+                                  learned=1)
+            r = vj.vj_join(ix, eps)
+            rec = recall_of(r, ex, w.nx)
+            op = (thr, rec, r)
+            if rec >= 0.95:
+                break
+        thr, lrec, lr_ = op
+        l_ms, l_stats = timed(vj, torch, ix, eps, 0, args.steps, args.warmup)
+        learned = {"thr": thr, "recall": lrec, "ms": l_ms, "stats": l_stats, "route_acc": route_acc,
+                   "routed_frac": float((lr_.hybrid == 2).mean()), "train_s": train_s, "final_loss": final_loss,
+                   "labels_route_frac": float(route_lab.mean()), "t_bf_ms": t_bf, "t_step_ms": t_step}
+
+    # ---- headline arm and its rooflines
+    if learned is not None:
+        step_ms, stats, rec = learned["ms"], learned["stats"], learned["recall"]
+        arm = f"learned+BF16: MI+SWS with the learned prologue, route threshold {learned['thr']}"
+        dtype = "bf16"
+    else:
+        step_ms, stats, rec = p_ms, p_stats, prec
+        arm = f"plain FP32 MI+SWS, hybrid={pmode} beam {pbudget}"
+        dtype = "f32"
+    value = world * w.nq / (step_ms / 1e3)
+    t_tr = statistics.mean(s["ms_traverse"] for s in stats)
+    t_sc = statistics.mean(s["ms_scan"] for s in stats)
+    trav = {"kernel": "k_join (traversal)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
+            "achieved": statistics.mean(s["bytes_algorithmic"] for s in stats) / (t_tr / 1e3) / 1e9,
+            "ms_per_launch": t_tr, "algorithmic_bytes_per_launch": statistics.mean(s["bytes_algorithmic"] for s in stats),
+            "peak_kind": f"{peak_kind} hbm_gbs (burst)", "traffic": None}
+    trav["frac"] = trav["achieved"] / hbm
+    rooflines = [trav]
+    if learned is not None and t_sc > 0:
+        nrouted = learned["routed_frac"] * w.nq
+        flops = 2.0 * nrouted * w.nx * w.d
+        scan = {"kernel": "k_tc_scan (tcgen05 BF16 brute-force scan)", "bound": "tensor", "unit": "TFLOP/s",
+                "peak": bf16, "achieved": flops / (t_sc / 1e3) / 1e12, "ms_per_launch": t_sc,
+                "algorithmic_flops_per_launch": flops, "peak_kind": f"{peak_kind} bf16_tflops (burst)",
+                "traffic": None}
+        scan["frac"] = scan["achieved"] / bf16
+        rooflines.append(scan)
+    dominant = max(rooflines, key=lambda k: k["ms_per_launch"])
+
+    # clocks during one more timed run of the headline arm
     with ClockSampler(torch.cuda.current_device()) as cs:
         time.sleep(0.3)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            dr = vj.vj_join_device(ix, eps, budget)
-            trav_ms.append(dr.stats["ms_traverse"])
-            bytes_alg.append(dr.stats["bytes_algorithmic"])
-            launches += dr.stats["kernel_launches"]
-            pairs = dr.nnz
-            dr.free()
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        timed(vj, torch, ix, eps, 0 if learned is not None else pbudget, args.steps, 1)
         time.sleep(0.2)
-    step_ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * w.nq / (step_ms / 1e3)
 
     # ---- end to end through the public call with a host result
     e2e_ms = []
     for _ in range(max(2, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rh = vj.vj_join(ix, eps, budget)
+        rh = vj.vj_join(ix, eps, 0 if learned is not None else pbudget)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     d2h = int(rh.offsets.nbytes + rh.ids.nbytes + rh.dists.nbytes + rh.steps.nbytes + rh.cache.nbytes +
               rh.hybrid.nbytes)
     e2e_v = world * w.nq / (statistics.median(e2e_ms) / 1e3)
 
-    peak, peak_kind = _peaks()
-    t_trav = statistics.mean(trav_ms)
-    achieved = statistics.mean(bytes_alg) / (t_trav / 1e3) / 1e9
-    line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl_desc,
-                   "arm": f"plain FP32 MI+SWS, hybrid={mode} beam {budget} (learned+BF16 arm not built)",
-                   "recall": rec, "eps": eps, "hybrid": mode, "hybrid_budget": budget, "degree": info["degree"],
-                   "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "pairs": int(pairs),
-                   "pairs_per_s": world * pairs / (step_ms / 1e3), "build_s": build_s,
-                   "l2": "inputs larger than L2 (vectors %.0f MB)" % (w.X.nbytes / 1e6 + w.Q.nbytes / 1e6),
-                   "dist_computations": r0.stats["dist_computations"], "seed": w.seed},
-        "roofline": {"kernel": "k_join (traversal)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (burst)",
-                     "traffic": None, "ms_per_launch": t_trav,
-                     "algorithmic_bytes_per_launch": statistics.mean(bytes_alg)},
-        "e2e": {"value": e2e_v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
-        "clocks": cs.summary(),
-        "gpu_launches": int(launches),
-    }
+    if dist:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        value = world * w.nq / (step_ms / 1e3)
+    cfg = {"workload": wl_desc, "arm": arm, "recall": rec, "eps": eps, "degree": info["degree"],
+           "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "build_s": build_s,
+           "pairs": int(stats[-1]["nnz"]), "pairs_per_s": world * stats[-1]["nnz"] / (step_ms / 1e3),
+           "l2": "inputs larger than L2 (vectors %.0f MB)" % ((w.X.nbytes + w.Q.nbytes) / 1e6),
+           "plain_fp32": {"qps": plain_qps, "ms_per_step": p_ms, "recall": prec, "hybrid": pmode,
+                          "hybrid_beam": pbudget},
+           "exact_join_ms": ex.stats["ms_total"], "exact_scan_ms": ex.stats["ms_scan"], "seed": w.seed}
+    if learned is not None:
+        cfg["learned"] = {k: learned[k] for k in ("thr", "recall", "route_acc", "routed_frac", "train_s",
+                                                   "final_loss", "labels_route_frac", "t_bf_ms", "t_step_ms")}
+        cfg["learned"]["ms_prologue"] = statistics.mean(s["ms_prologue"] for s in stats)
+        cfg["learned_vs_plain"] = value / plain_qps
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg, "roofline": dominant,
+            "rooflines": rooflines,
+            "e2e": {"value": e2e_v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+            "clocks": cs.summary(),
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt = run_cpu_oracle(w, vj, ix, eps, 1000, mode=mode, budget=budget)
+        n, dt = run_cpu_oracle(w, vj, ix, eps, 1000, pmode, pbudget)
         line["cpu_baseline"] = {"value": n / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} queries (whole MST subtrees) of the same workload on the GPU-built "
-                                          f"graph, oracle MI+SWS join (hybrid={mode}, beam {budget}), FP64, single thread"}
+                                          f"graph, oracle MI+SWS join (hybrid={pmode}, beam {pbudget}), FP64, "
+                                          "single thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    vj.vj_attach_predictor(ix, None, 0.5, 64)
     ix.free()
     if dist:
         dist.barrier()
