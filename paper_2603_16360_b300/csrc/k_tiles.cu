@@ -429,71 +429,6 @@ __global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ v
 }
 
 // ---------------------------------------------------------------- NLJ
-constexpr int NLJ_COLS = 16;  // column tiles per block
-
-__global__ void __launch_bounds__(TT) k_nlj_tile(const float* __restrict__ vec, const float* __restrict__ sqn,
-                                                  const float* __restrict__ invn, int dp, int64_t nx, int64_t nq,
-                                                  int metric, float key_hi, int32_t* __restrict__ cq,
-                                                  int32_t* __restrict__ cx, unsigned long long* __restrict__ ncand,
-                                                  int64_t cap) {
-    __shared__ GramSmem sm;
-    __shared__ int bq[1024], bx[1024];
-    __shared__ int bn;
-    __shared__ unsigned long long bbase;
-    const int64_t qa = nx + (int64_t)blockIdx.x * TBM;
-    const int64_t qend = nx + nq;
-    float rn[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        int64_t r = qa + tile_row(i);
-        rn[i] = r < qend ? (metric == 0 ? sqn[r] : invn[r]) : 0.f;
-    }
-    for (int tcol = 0; tcol < NLJ_COLS; tcol++) {
-        const int64_t ca = ((int64_t)blockIdx.y * NLJ_COLS + tcol) * TBN;
-        if (ca >= nx) break;
-        if (threadIdx.x == 0) bn = 0;
-        float acc[8][8];
-        gram_tile(vec, dp, qa, qend, ca, nx, acc, sm);
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int64_t c = ca + tile_col(j);
-            if (c >= nx) continue;
-            float cn = metric == 0 ? sqn[c] : invn[c];
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                int64_t r = qa + tile_row(i);
-                if (r >= qend) continue;
-                float key = metric == 0 ? rn[i] + cn - 2.f * acc[i][j] : 1.f - acc[i][j] * rn[i] * cn;
-                if (key < key_hi) {
-                    int slot = atomicAdd(&bn, 1);
-                    if (slot < 1024) {
-                        bq[slot] = (int)(r - nx);
-                        bx[slot] = (int)c;
-                    } else {
-                        unsigned long long g = atomicAdd(ncand, 1ull);
-                        if ((int64_t)g < cap) {
-                            cq[g] = (int)(r - nx);
-                            cx[g] = (int)c;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        int cnt = min(bn, 1024);
-        if (threadIdx.x == 0 && cnt > 0) bbase = atomicAdd(ncand, (unsigned long long)cnt);
-        __syncthreads();
-        for (int e = threadIdx.x; e < cnt; e += TT) {
-            unsigned long long g = bbase + e;
-            if ((int64_t)g < cap) {
-                cq[g] = bq[e];
-                cx[g] = bx[e];
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // warp per 32 candidates: direct-difference key, FP64 near eps; survivors get
 // counted per query and kept (flag)
 __global__ void k_nlj_recheck(const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d,
@@ -669,22 +604,6 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     const float eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
     // Gram-key bound: (2dp+10) u (|a|+|b|)^2 for L2 (norms up to maxnorm),
     // (2dp+10) u * 4 for cosine
-    double maxnorm = 0.0;
-    {
-        DBuf<double> mx;
-        mx.alloc(1, s);
-        VJ_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(double), s));
-        k_norms<<<vj_div_up(ix->n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->n, ix->sqn.p, ix->invn.p,
-                                                            mx.p);
-        VJ_LAUNCH_CHECK();
-        VJ_CUDA(cudaMemcpyAsync(&maxnorm, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-        VJ_CUDA(cudaStreamSynchronize(s));
-        mx.free_(s);
-    }
-    double beta = ix->metric == VJ_L2 ? (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0 * maxnorm * maxnorm
-                                      : (2.0 * ix->dp + 10.0) * VJ_F32_U * 4.0;
-    float key_hi = (float)((double)eps_key + beta) * 1.0001f + 1e-30f;
-    (void)key_hi;
     // candidates from the BF16 tensor-core scan (bounded superset), then the
     // exact FP32 / FP64 re-decision below
     DBuf<int32_t> cq, cx;
