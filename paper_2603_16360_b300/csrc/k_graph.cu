@@ -783,28 +783,6 @@ void vj_build_graph(vj_index* ix) {
         }
         VJ_CUDA(cudaMemcpyAsync(ix->parent.p, hp.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         VJ_CUDA(cudaMemcpyAsync(ix->depth.p, hd.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        // children lists (CSR) and the roots (queries whose parent is the
-        // data entry or none) for the join's ready-queue dispatch
-        std::vector<int32_t> coff(nq + 1, 0), clist(nq), roots;
-        for (int64_t qi = 0; qi < nq; qi++) {
-            if (hp[qi] >= 0) coff[hp[qi] + 1]++;
-            else roots.push_back((int32_t)qi);
-        }
-        for (int64_t qi = 0; qi < nq; qi++) coff[qi + 1] += coff[qi];
-        {
-            std::vector<int32_t> fillp(coff.begin(), coff.end() - 1);
-            for (int64_t qi = 0; qi < nq; qi++)
-                if (hp[qi] >= 0) clist[fillp[hp[qi]]++] = (int32_t)qi;
-        }
-        ix->nroots = (int64_t)roots.size();
-        ix->child_off.ensure(nq + 1, s);
-        ix->child_list.ensure(std::max<int64_t>(nq, 1), s);
-        ix->roots.ensure(std::max<int64_t>(ix->nroots, 1), s);
-        VJ_CUDA(cudaMemcpyAsync(ix->child_off.p, coff.data(), (nq + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        VJ_CUDA(cudaMemcpyAsync(ix->child_list.p, clist.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        if (ix->nroots > 0)
-            VJ_CUDA(cudaMemcpyAsync(ix->roots.p, roots.data(), ix->nroots * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                    s));
         VJ_CUDA(cudaStreamSynchronize(s));
         for (auto* b : {&ea, &eb, &comp, &hook, &deg, &cur, &nbr, &vdepth, &vparent, &fa, &fb}) b->free_(s);
         wb.free_(s);

@@ -26,10 +26,22 @@
 //   UpdateCache (8)    C[q] = closest visited data node, ties by id, FP64
 //                      re-decided among FP32 near-ties.
 //
-// Work sharing: a query is dispatched only once its MST parent is done.  The
-// ready queue starts with the roots; a finished query appends its children
-// (release stores) and warps take slots in order (acquire loads, bounded
-// spin).  A slot is only awaited when no ready query exists.
+// Work sharing (soft): queries are taken in MST BFS order, so a parent is
+// always claimed before its children.  A query does not wait for its parent
+// before starting: its probe, CheckHybrid and (BFS) closure do not depend on
+// the cached seed C[parent] except through set membership, so the warp runs
+// them on the other seeds and merges C[parent] when the parent publishes it
+// (release store of its done flag, bounded acquire spin):
+//   - if C[parent] would have become the greedy front (key 0, a duplicate of
+//     q) the probe would not have run: the query restarts with the seed;
+//   - else if C[parent] is already visited nothing changes (V, I and the
+//     closure are sets; the seed would have been evaluated once either way);
+//   - otherwise it is evaluated and added to V; if it is in range it joins I
+//     and the closure continues from it (the closure of a union is the union
+//     of the closures over the same visited set);
+//   - a hybrid or routed query merges it before its expansion (Q0 = I and V
+//     are sets at that point, the pop order is decided afterwards).
+// The result, visited count and cache equal those of the wait-first order.
 //
 // Visited set: open-addressing hash in shared memory (HCAP slots), moved on
 // overflow to a per-warp global table that grows by 4x (two alternating
@@ -69,7 +81,7 @@ enum {
     C_RECHK = 7,
     C_SPILL = 8,
     C_ABORT = 9,
-    C_TAIL = 10,
+    C_RESTART = 10,
     C_NUM = 11
 };
 
@@ -79,11 +91,10 @@ struct JoinParams {
     const int32_t* adj;
     const float* elen;
     const int32_t* parent;
-    const int32_t* child_off;
-    const int32_t* child_list;
+    int* done;             // per-query publish flag (soft sharing)
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
-    int* ready;
+    const int* order;      // dispatch order (MST BFS order: parents first)
     int64_t nx, nq;
     int dp4, dp, d, R, metric;
     int32_t entry;
@@ -347,38 +358,62 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         if (lane == 0) t = (int)atomicAdd(P.ctr + C_TICKET, 1ull);
         t = __shfl_sync(VJ_FULL, t, 0);
         if (t >= P.nq) break;
-        // ---- dispatch: wait (bounded) until slot t of the ready queue is filled
-        int qi = -1;
-        if (lane == 0) {
-            long long spins = 0;
-            unsigned ns = 32;
-            for (;;) {
-                qi = ld_acquire(P.ready + t);
-                if (qi >= 0) break;
-                if (*((volatile unsigned long long*)(P.ctr + C_ABORT))) break;
-                if (++spins > P.spin_limit) {
-                    raise_err(P, VJ_DERR_WAIT_TIMEOUT);
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 1024) ns <<= 1;
-            }
-        }
-        qi = __shfl_sync(VJ_FULL, qi, 0);
-        if (qi < 0) break;
+        const int qi = P.order[t];
         const int64_t qn = P.nx + qi;
-
-        // ---- Alg. 3 SeedPhase: the parent (if any) finished before q was queued
-        int seedc = -1;
-        if (P.ws == VJ_WS_SOFT) {
-            int par = P.parent[qi];
-            if (par >= 0 && lane == 0) seedc = *((volatile int*)(P.cache + par));
-            seedc = __shfl_sync(VJ_FULL, seedc, 0);
-        }
+        // soft sharing: the parent's cache is a seed (none for children of the entry)
+        const int par = P.ws == VJ_WS_SOFT ? __ldg(P.parent + qi) : -1;
 
         float4 q[NPL];
         load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
         const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
+
+        // C[parent] once the parent has published it; -2 on abort or timeout
+        int scv = -1;
+        auto wait_parent = [&]() -> int {
+            int sc = -1;
+            if (lane == 0) {
+                long long spins = 0;
+                unsigned ns = 32;
+                for (;;) {
+                    if (ld_acquire(P.done + par)) {
+                        sc = *((volatile int*)(P.cache + par));
+                        break;
+                    }
+                    if (*((volatile unsigned long long*)(P.ctr + C_ABORT))) {
+                        sc = -2;
+                        break;
+                    }
+                    if (++spins > P.spin_limit) {
+                        raise_err(P, VJ_DERR_WAIT_TIMEOUT);
+                        sc = -2;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 512) ns <<= 1;
+                }
+            }
+            scv = __shfl_sync(VJ_FULL, sc, 0);
+            return scv;
+        };
+
+        const long long k_exp = c_exp, k_adj = c_adj, k_hyb = c_hyb, k_rechk = c_rechk, k_spill = c_spill;
+        bool quit = false;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; pass++) {
+        // pass 0 runs without C[parent] and merges it late; pass 1 (rare)
+        // restarts with it as a seed from the beginning
+        int seedc = -1;
+        bool pending = par >= 0;
+        if (pass == 1) {
+            seedc = scv;
+            pending = false;
+            c_exp = k_exp;
+            c_adj = k_adj;
+            c_hyb = k_hyb;
+            c_rechk = k_rechk;
+            c_spill = k_spill;
+            if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
+        }
 
         QueryState s;
         s.tab = S->htab;
@@ -400,6 +435,32 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         for (int i = lane; i < HCAP; i += 32) S->htab[i] = -1;
         __syncwarp();
         bool failed = false;
+        bool restart = false;
+        // merge C[parent] = sc into V (and I when in range) after the probe:
+        // 0 merged or nothing to do, 1 restart needed, 2 failed
+        auto merge_seed = [&](int sc, bool probed) -> int {
+            if (sc < 0) return sc == -2 ? 2 : 0;
+            if (lane == 0) S->cand[0] = sc;
+            __syncwarp();
+            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
+            __syncwarp();
+            const float k = S->ckey[0];
+            __syncwarp();
+            // with key 0 the seed would have been the greedy front and the
+            // probe would not have run (whether or not the probe reached it)
+            if (probed && k <= 0.f) return 1;
+            if (!vis_reserve(P, s, 1, W, lane, c_spill)) return 2;
+            int ins = 0;
+            if (lane == 0) ins = hash_insert(s.tab, s.mask, sc);
+            ins = __shfl_sync(VJ_FULL, ins, 0);
+            if (ins != 1) return 0;
+            s.nvis += 1;
+            const bool val = lane == 0;
+            const bool in = inrange_decide(P, val, k, sc, qn, lane, c_rechk);
+            best_update(P, s, val, k, sc, lane);
+            if (!append_results(P, s, in, sc, k, W, lane)) return 2;
+            return 0;
+        };
 
         // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
         int sid = -1;
@@ -504,6 +565,38 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             hbq = P.qbeam[qi];
             hyb = hbq > 0;
         } else if (P.adapt && !failed && !routed) {
+            if (!probe) {
+                // no probe ran (a seed was the greedy front); the rule still
+                // reads q's neighbourhood, evaluated here outside V
+                c_adj++;
+                const int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+                nid_l = v;
+                const bool dv = v >= 0 && v < P.nx;
+                const unsigned dm0 = __ballot_sync(VJ_FULL, dv);
+                const int pos = __popc(dm0 & ((1u << lane) - 1u));
+                if (dv) S->cand[pos] = v;
+                __syncwarp();
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, __popc(dm0), S->ckey,
+                                      lane);
+                __syncwarp();
+                nkey_l = dv ? S->ckey[pos] : FLT_MAX;
+                __syncwarp();
+                if (lane < R) S->cand[lane] = v;  // N(q) for the pair test below
+                __syncwarp();
+            }
+            // w in N(q) U {q}: the visited set after the probe holds N(q) and
+            // the seeds (entry and C[parent] count only if they are in N(q))
+            auto in_nq = [&](int w) -> bool {
+                if (!probe) {
+                    bool f = false;
+                    for (int t = 0; t < R; t++) f |= S->cand[t] == w;
+                    return f;
+                }
+                bool inq = hash_contains(s.tab, s.mask, w);
+                if (inq && w == P.entry && !entry_in_nq) inq = false;
+                if (inq && w == seedc && !seed_in_nq) inq = false;
+                return inq;
+            };
             const bool isd = nid_l >= 0 && nid_l < P.nx;
             float d1s = isd ? key_to_dist(P, nkey_l) : 0.f;
             const unsigned dmask = __ballot_sync(VJ_FULL, isd);
@@ -533,12 +626,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     if (vr[k] >= 0) c_adj += (lane == 0);
                     int w = w4[k];
                     bool ok = w >= 0 && w < P.nx;
-                    if (ok) {
-                        bool inq = hash_contains(s.tab, s.mask, w);
-                        if (inq && w == P.entry && !entry_in_nq) inq = false;
-                        if (inq && w == seedc && !seed_in_nq) inq = false;
-                        ok = !inq;
-                    }
+                    if (ok) ok = !in_nq(w);
                     if (ok) {
                         d2s += e4[k];
                         n2++;
@@ -568,10 +656,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                         for (int j = 0; j < R; j++) {
                             int w = __ldg(P.adj + (int64_t)v * R + j);
                             if (w < 0 || w >= P.nx) continue;
-                            bool inq = hash_contains(s.tab, s.mask, w);
-                            if (inq && w == P.entry && !entry_in_nq) inq = false;
-                            if (inq && w == seedc && !seed_in_nq) inq = false;
-                            if (inq) continue;
+                            if (in_nq(w)) continue;
                             a2 += warp_dist64(P.vec, P.dp, P.d, P.metric, v, w, lane);
                         }
                     }
@@ -581,6 +666,13 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
             hyb = ood;
         }
+        // a hybrid or routed query takes C[parent] before its expansion
+        if (pending && !failed && (routed || hyb)) {
+            const int r = merge_seed(wait_parent(), probe);
+            pending = false;
+            if (r == 1) restart = true;
+            if (r == 2) failed = true;
+        }
         int expansions = 0;
         if (routed) {
             s.nres = 0;  // the scan supplies the row
@@ -588,9 +680,11 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
 
         // ---- Alg. 7 ExpansionPhase
-        if (routed) {
+        if (routed || restart) {
         } else if (!failed && !hyb) {
             int fp = 0;
+#pragma unroll 1
+            for (;;) {
             while (fp < s.nres) {
                 const int nb = min(FB, s.nres - fp);
                 if (!vis_reserve(P, s, nb * R, W, lane, c_spill)) {
@@ -636,7 +730,16 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 __syncwarp();
                 if (failed) break;
             }
-        } else if (!failed && hyb) {
+            // closure done on the other seeds: merge C[parent]; an in-range
+            // seed extends the closure from where it stopped
+            if (failed || !pending) break;
+            const int r = merge_seed(wait_parent(), probe);
+            pending = false;
+            if (r == 1) restart = true;
+            if (r == 2) failed = true;
+            if (failed || restart) break;
+            }
+        } else if (!failed && !restart && hyb) {
             if (lane == 0) c_hyb++;
             int npend = s.nres;  // in-range entries not yet popped (rid >= 0)
             int osz = 0, oqh = 0, cur = 0;
@@ -750,6 +853,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
         }
         c_exp += expansions;
+        if (restart) continue;
 
         // ---- Alg. 8 UpdateCache: FP64 re-decision among near-ties
         int best = (s.bid == INT32_MAX) ? -1 : s.bid;
@@ -773,18 +877,12 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             P.steps[qi] = s.nvis;
             P.hyb[qi] = (uint8_t)hyb;
             c_dist += s.nvis;
-            if (P.ws == VJ_WS_SOFT) {
-                // publish the children: cache[qi] is visible before any slot
-                __threadfence();
-                const int c0 = P.child_off[qi], c1 = P.child_off[qi + 1];
-                if (c1 > c0) {
-                    unsigned long long pos = atomicAdd(P.ctr + C_TAIL, (unsigned long long)(c1 - c0));
-                    for (int c = c0; c < c1; c++) st_release(P.ready + pos + (c - c0), P.child_list[c]);
-                }
-            }
+            // publish: cache[qi] is visible to whoever sees the flag
+            if (P.ws == VJ_WS_SOFT && !failed) st_release(P.done + qi, 1);
         }
         if (failed) {
             if (lane == 0) P.count[qi] = 0;
+            quit = true;
             break;
         }
 
@@ -804,6 +902,9 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
         }
         __syncwarp();
+        break;
+        }  // pass
+        if (quit) break;
     }
     if (lane == 0) {
         atomicAdd(P.ctr + C_DIST, (unsigned long long)c_dist);
@@ -907,7 +1008,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     ix->hyb.ensure(nq, s);
     ix->count.ensure(nq, s);
     ix->seg.ensure(nq, s);
-    ix->ready.ensure(nq, s);
+    ix->done.ensure(nq, s);
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
@@ -939,11 +1040,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.adj = ix->adj.p;
     P.elen = ix->elen.p;
     P.parent = ix->parent.p;
-    P.child_off = ix->child_off.p;
-    P.child_list = ix->child_list.p;
+    P.done = ix->done.p;
+    P.order = ix->order.p;
     P.route = ix->has_route ? ix->plan_route.p : nullptr;
     P.qbeam = ix->has_beam ? ix->plan_beam.p : nullptr;
-    P.ready = ix->ready.p;
     P.nx = ix->nx;
     P.nq = nq;
     P.dp4 = ix->dp / 4;
@@ -988,17 +1088,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         P.pool_id = ix->pool_id.p;
         P.pool_d = ix->pool_d.p;
         P.pool_cap = (int64_t)ix->pool_id.n;
-        // ready queue: the roots (soft sharing) or every query in MST order
         VJ_CUDA(cudaMemsetAsync(ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
-        if (soft) {
-            VJ_CUDA(cudaMemsetAsync(ix->ready.p, 0xff, nq * sizeof(int32_t), s));
-            VJ_CUDA(cudaMemcpyAsync(ix->ready.p, ix->roots.p, ix->nroots * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                                    s));
-            unsigned long long tail = (unsigned long long)ix->nroots;
-            VJ_CUDA(cudaMemcpyAsync(ix->ctr.p + C_TAIL, &tail, sizeof(tail), cudaMemcpyHostToDevice, s));
-        } else {
-            VJ_CUDA(cudaMemcpyAsync(ix->ready.p, ix->order.p, nq * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        }
+        if (soft) VJ_CUDA(cudaMemsetAsync(ix->done.p, 0, nq * sizeof(int32_t), s));
         VJ_CUDA(cudaEventRecord(e0, s));
         jd.launch(P, jd.blocks, s);
         VJ_CUDA(cudaEventRecord(e1, s));
@@ -1019,7 +1110,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         cudaEventDestroy(e2);
         int code = (int)hc[C_ERR];
         if (code == VJ_DERR_WAIT_TIMEOUT) {
-            vj_set_error("join: a wait on the work-sharing ready queue timed out");
+            vj_set_error("join: a wait for a work-sharing parent timed out");
             throw VjError{VJ_ERR_TIMEOUT};
         }
         vj_set_error("join: device error %d (%s)", code,
@@ -1097,6 +1188,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     st->ms_traverse = t_trav;
     st->ms_csr = t_csr;
     st->ms_prologue = ms_pro;
+    st->sws_restarts = (int64_t)hc[C_RESTART];
     st->ms_total = ms_pro + t_trav + t_csr;
     // algorithmic bytes: one vector per distance, one adjacency row per row read
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;

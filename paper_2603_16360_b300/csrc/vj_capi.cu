@@ -87,10 +87,6 @@ static void free_index(vj_index* ix) {
     ix->plan_beam.free_(s);
     ix->routed.free_(s);
     ix->xbf.free_(s);
-    ix->child_off.free_(s);
-    ix->child_list.free_(s);
-    ix->roots.free_(s);
-    ix->ready.free_(s);
     ix->done.free_(s);
     ix->cache.free_(s);
     ix->steps.free_(s);

@@ -111,11 +111,6 @@ struct vj_index {
     DBuf<int32_t> order;  // [nq]
     DBuf<int32_t> depth;  // [nq]
     int max_depth = 0;
-    DBuf<int32_t> child_off;   // [nq+1] MST children CSR
-    DBuf<int32_t> child_list;  // [nq]
-    DBuf<int32_t> roots;       // queries whose MST parent is the data entry (or none)
-    int64_t nroots = 0;
-    DBuf<int32_t> ready;       // [nq] join dispatch queue
     DBuf<__nv_bfloat16> xbf;   // [nx][kp] BF16 copy of the data rows (tensor-core scans)
     // per-query plan (route to the brute-force scan / hybrid budget), optional
     DBuf<uint8_t> plan_route;  // [nq]
@@ -140,8 +135,7 @@ struct vj_index {
     int64_t knn_uncertified = 0;  // rows whose tile candidates needed the exact fallback
 
     // join scratch kept across calls
-    DBuf<int> done;           // [nq] generation stamps of finished queries
-    int gen = 0;
+    DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
     DBuf<int32_t> cache;      // [nq]
     DBuf<int32_t> steps;      // [nq]
     DBuf<uint8_t> hyb;        // [nq]

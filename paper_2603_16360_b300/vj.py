@@ -52,7 +52,8 @@ class vj_stats(C.Structure):
                 ("hybrid_queries", C.c_int64), ("rechecks", C.c_int64), ("spill_queries", C.c_int64),
                 ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
                 ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
-                ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double)]
+                ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double),
+                ("sws_restarts", C.c_int64)]
 
 
 class vj_result(C.Structure):

@@ -181,6 +181,35 @@ def test_single_query_and_duplicates(oracle):
     ix.free()
 
 
+def test_soft_sharing_late_seed_and_restart_match_oracle(oracle):
+    """Soft sharing merges C[parent] after the probe; queries that duplicate a
+    data point (and each other) make that seed the greedy front, which forces
+    the re-run path.  Results, visited counts, caches and hybrid flags must
+    still equal the oracle's wait-first order."""
+    rng = np.random.default_rng(11)
+    X = (rng.standard_normal((2000, 16)) + 3.0 * rng.integers(0, 4, (2000, 1))).astype(np.float32)
+    src = rng.choice(2000, 30, replace=False)
+    Q = np.concatenate([X[src], X[src], X[rng.choice(2000, 140)] + 0.3 * rng.standard_normal((140, 16))])
+    Q = Q.astype(np.float32)
+    ix = vj.vj_build(X, Q, params=vj.default_params(degree=12, knn_k=24))
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    eps = 2.0
+    restarts = 0
+    for kw in (dict(adapt_hybrid=0), dict(adapt_hybrid=1), dict(adapt_hybrid=0, force_hybrid=1, hybrid_beam=8)):
+        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, **kw)
+        r = vj.vj_join(ix, eps)
+        restarts += r.stats["sws_restarts"]
+        o = oracle.join(X, Q, adj, entry, eps, work_sharing=oracle.WS_SOFT,
+                        force_hybrid=bool(kw.get("force_hybrid", 0)), adapt_hybrid=bool(kw["adapt_hybrid"]),
+                        hybrid_beam_size=kw.get("hybrid_beam", 256), order=order, parent=parent)
+        assert _pairs(r.offsets, r.ids) == _pairs(o.offsets, o.ids), kw
+        np.testing.assert_array_equal(r.steps, o.steps)
+        np.testing.assert_array_equal(r.cache, o.cache)
+        np.testing.assert_array_equal(r.hybrid, o.hybrid)
+    assert restarts > 0
+    ix.free()
+
+
 def test_tiny_sets_and_empty_results(oracle):
     rng = np.random.default_rng(8)
     X = rng.standard_normal((5, 4)).astype(np.float32)
