@@ -24,6 +24,9 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <functional>
+
 #include "vj_device.cuh"
 #include "vj_internal.cuh"
 
@@ -127,6 +130,20 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                    "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
                    "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
                    "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld64_issue(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld64(uint32_t (&r)[64]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
                  :
                  : "memory");
 }
@@ -291,13 +308,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int etid = e * 32 + lane;      // threads < TC_BN stage one column each
         // the next tile's column norm and row info are loaded one tile ahead,
         // so their latency overlaps the current tile
+        // (cosine rows are unit-normalised: their norms are 1)
         auto col_norm = [&](int tt) -> float {
             const int64_t c = (int64_t)(tt / P.nrt) * TC_BN + etid;
-            return (etid < TC_BN && tt < ntiles && c < P.ncols) ? P.b_n[c] : -1.f;
+            return (etid < TC_BN && tt < ntiles && c < P.ncols) ? (MODE == 2 ? 1.f : P.b_n[c]) : -1.f;
         };
         auto row_norm = [&](int tt) -> float {
             const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
-            return (tt < ntiles && r < P.nrows) ? P.a_n[r] : -1.f;
+            return (tt < ntiles && r < P.nrows) ? (MODE == 2 ? 1.f : P.a_n[r]) : -1.f;
         };
         auto row_id = [&](int tt) -> int {
             const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
@@ -440,15 +458,370 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// FP32 rows (optionally gathered) -> BF16 rows of kp columns, zero padded
+// ---------------------------------------------------------------- resident-A scan
+// For kp <= 256 a CTA keeps 256 query rows (two 128-row MMA operands, every
+// k-block) in shared memory for a run of 128-row data tiles, so only the data
+// side crosses L2 per tile (K = 128: 32 KB per 8.4 MFLOP instead of 96 KB).
+// The per-column part of the candidate test rides in the GEMM: after the data
+// k-blocks comes a bias k-block whose A side holds (1, 1, 1, 0, ...) and whose
+// data side holds a three-term BF16 split of the column bias, so the
+// accumulator is 2<a,b> + bias_c and the epilogue is a row-wise max against
+// one threshold per query row (one FMNMX per pair).
+constexpr int RS_BN = 128;                     // data rows per tile (MMA N)
+constexpr int RS_EPI = 16;                     // epilogue warps
+constexpr int RS_THREADS = (2 + RS_EPI) * 32;
+constexpr uint32_t RS_BOX = 128 * 64 * 2;      // one 128-row x 64-column BF16 box
+constexpr int RS_MAX_KB = 4;                   // data k-blocks (kp <= 256)
+constexpr int RS_MAX_STAGES = 8;
+constexpr uint32_t RS_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RS_BN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+struct RsBars {
+    uint64_t full[RS_MAX_STAGES];
+    uint64_t empty[RS_MAX_STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t afull;   // the unit's query rows have landed
+    uint64_t aempty;  // the unit's MMAs are done (query rows may be replaced)
+    uint64_t abar;    // the A-side bias block has landed
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+static_assert(sizeof(RsBars) <= 1024, "barrier block");
+
+struct RsParams {
+    int64_t nrows, ncols;
+    int nkb;     // data k-blocks (kp / 64)
+    int bias;    // 1: a bias k-block follows the data k-blocks (L2)
+    int nrp;     // 256-row query blocks
+    int nct;     // data tiles
+    int tpu;     // data tiles per work unit
+    int nunits;  // nrp * ceil(nct / tpu), query block fastest
+    int stages;
+    const float* a_thr;    // per query row: candidate iff accumulator > a_thr
+    const int32_t* a_ids;  // query index of each row
+    int32_t* cq;
+    int32_t* cx;
+    unsigned long long* ncand;
+    int64_t cap;
+    int* err;
+    long long spin_limit;
+};
+
+__global__ void __launch_bounds__(RS_THREADS, 1)
+    k_tc_scan_res(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAb,
+                  const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBb, RsParams P) {
+    extern __shared__ uint8_t rs_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(rs_raw) + 1023) & ~uintptr_t(1023));
+    RsBars& Bb = *reinterpret_cast<RsBars*>(base);
+    uint8_t* sAb = base + 1024;
+    uint8_t* sA = sAb + RS_BOX;                       // [2][nkb] boxes
+    uint8_t* sB = sA + 2 * P.nkb * RS_BOX;            // [stages] boxes
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &Bb.abort;
+    const int nkt = P.nkb + P.bias;  // k-blocks per data tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.stages; s++) {
+            mbar_init(&Bb.full[s], 1);
+            mbar_init(&Bb.empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&Bb.tfull[b], 1);
+            mbar_init(&Bb.tempty[b], RS_EPI);
+        }
+        mbar_init(&Bb.afull, 1);
+        mbar_init(&Bb.aempty, 1);
+        mbar_init(&Bb.abar, 1);
+        mbar_init(&Bb.drain, 1);
+        Bb.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&Bb.tmem_base)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = Bb.tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t issued = 0, last_ph = 0;  // ring stages ever filled, parity of their last fill
+            int a_units = 0;                   // query blocks loaded so far
+            bool ok = true;
+            if (P.bias) {
+                mbar_arrive_tx(&Bb.abar, RS_BOX);
+                tma_load_2d(sAb, &tAb, &Bb.abar, 0, 0);
+            }
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+                const int rp = u % P.nrp, cc = u / P.nrp;
+                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                if (a_units > 0 && !mbar_wait(&Bb.aempty, (uint32_t)((a_units - 1) & 1), abort, P.spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_tx(&Bb.afull, 2u * (uint32_t)P.nkb * RS_BOX);
+                for (int blk = 0; blk < 2; blk++)
+                    for (int kb = 0; kb < P.nkb; kb++)
+                        tma_load_2d(sA + (blk * P.nkb + kb) * RS_BOX, &tA, &Bb.afull, kb * 64, rp * 256 + blk * 128);
+                a_units++;
+                for (int ct = t0; ct < t1 && ok; ct++) {
+                    for (int kb = 0; kb < nkt; kb++) {
+                        if (!mbar_wait(&Bb.empty[s], ph ^ 1u, abort, P.spin_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_tx(&Bb.full[s], RS_BOX);
+                        if (kb < P.nkb) tma_load_2d(sB + s * RS_BOX, &tB, &Bb.full[s], kb * 64, ct * RS_BN);
+                        else tma_load_2d(sB + s * RS_BOX, &tBb, &Bb.full[s], 0, ct * RS_BN);
+                        issued |= 1u << s;
+                        last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                        if (++s == P.stages) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+                // let this CTA's copies land before shared memory goes away
+                for (int st = 0; st < P.stages; st++)
+                    if ((issued >> st) & 1u)
+                        for (long long i = 0; i < P.spin_limit && !mbar_test(&Bb.full[st], (last_ph >> st) & 1u); i++) {
+                        }
+                if (a_units > 0)
+                    for (long long i = 0; i < P.spin_limit && !mbar_test(&Bb.afull, (uint32_t)((a_units - 1) & 1));
+                         i++) {
+                    }
+                if (P.bias)
+                    for (long long i = 0; i < P.spin_limit && !mbar_test(&Bb.abar, 0); i++) {
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: D0 += A0 B^T, D1 += A1 B^T per k-step
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int i = 0, j = 0;
+            bool ok = !P.bias || mbar_wait(&Bb.abar, 0, abort, P.spin_limit);
+            const uint64_t abd = sdesc_sw128(su32(sAb));
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, j++) {
+                const int cc = u / P.nrp;
+                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                if (!mbar_wait(&Bb.afull, (uint32_t)(j & 1), abort, P.spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int ct = t0; ct < t1 && ok; ct++, i++) {
+                    const int acc = i & 1;
+                    if (!mbar_wait(&Bb.tempty[acc], (uint32_t)(((i >> 1) & 1) ^ 1), abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d0 = tmem + (uint32_t)(acc * 256), d1 = d0 + 128u;
+                    for (int kb = 0; kb < nkt; kb++) {
+                        if (!mbar_wait(&Bb.full[s], ph, abort, P.spin_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t bd = sdesc_sw128(su32(sB + s * RS_BOX));
+                        if (kb < P.nkb) {
+                            const uint64_t a0 = sdesc_sw128(su32(sA + kb * RS_BOX));
+                            const uint64_t a1 = sdesc_sw128(su32(sA + (P.nkb + kb) * RS_BOX));
+#pragma unroll
+                            for (int kk = 0; kk < 4; kk++) {
+                                // advance 16 BF16 (32 bytes) along K inside the swizzled rows
+                                const uint32_t accf = (kb | kk) != 0;
+                                tc_mma(d0, a0 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
+                                tc_mma(d1, a1 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
+                            }
+                        } else {
+                            // bias block: its first K=16 step holds the three bias terms
+                            tc_mma(d0, abd, bd, RS_IDESC, 1u);
+                            tc_mma(d1, abd, bd, RS_IDESC, 1u);
+                        }
+                        tc_commit(&Bb.empty[s]);
+                        if (++s == P.stages) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&Bb.tfull[acc]);
+                }
+                if (!ok) break;
+                tc_commit(&Bb.aempty);  // the query rows may be replaced once these MMAs finish
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+            }
+            tc_commit(&Bb.drain);
+            for (long long k = 0; k < P.spin_limit && !mbar_test(&Bb.drain, 0); k++) {
+            }
+        }
+    } else {
+        // ---------------- epilogue: warp e reads TMEM lane quarter (warp & 3),
+        // 64 of the 256 accumulator columns: query block cg >> 1, half cg & 1
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int cg = e >> 2;
+        const int blk = cg >> 1, csub = cg & 1;
+        int i = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+            const int rp = u % P.nrp, cc = u / P.nrp;
+            const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+            const int64_t r = (int64_t)rp * 256 + blk * 128 + quarter * 32 + lane;
+            const float thr = r < P.nrows ? P.a_thr[r] : INFINITY;
+            const int qid = r < P.nrows ? P.a_ids[r] : -1;
+            for (int ct = t0; ct < t1; ct++, i++) {
+                const int acc = i & 1;
+                const bool got = mbar_wait(&Bb.tfull[acc], (uint32_t)((i >> 1) & 1), abort, P.spin_limit);
+                if (!__all_sync(VJ_FULL, got)) {
+                    if (lane == 0) {
+                        *abort = 1;
+                        atomicExch(P.err, 1);
+                    }
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem + (uint32_t)(acc * 256 + blk * 128 + csub * 64) +
+                                       ((uint32_t)(quarter * 32) << 16);
+                uint32_t va[64];
+                tmem_ld64_issue(taddr, va);
+                tmem_wait_ld64(va);
+                float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+#pragma unroll
+                for (int j = 0; j < 64; j += 4) {
+                    m0 = fmaxf(m0, __uint_as_float(va[j + 0]));
+                    m1 = fmaxf(m1, __uint_as_float(va[j + 1]));
+                    m2 = fmaxf(m2, __uint_as_float(va[j + 2]));
+                    m3 = fmaxf(m3, __uint_as_float(va[j + 3]));
+                }
+                const bool maybe = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr;
+                if (__any_sync(VJ_FULL, maybe)) {
+                    const int64_t c0 = (int64_t)ct * RS_BN + csub * 64;
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        uint32_t hit = 0;
+                        if (maybe) {
+#pragma unroll
+                            for (int j = 0; j < 32; j++)
+                                if (__uint_as_float(va[h * 32 + j]) > thr && c0 + h * 32 + j < P.ncols)
+                                    hit |= 1u << j;
+                        }
+                        // warp-aggregated append: one atomic per warp and half
+                        const int mine = __popc(hit);
+                        int incl = mine;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
+                            if (lane >= o) incl += t2;
+                        }
+                        const int total = __shfl_sync(VJ_FULL, incl, 31);
+                        if (total > 0) {
+                            unsigned long long gb = 0;
+                            if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)total);
+                            gb = __shfl_sync(VJ_FULL, gb, 31);
+                            unsigned long long gq = gb + (unsigned long long)(incl - mine);
+                            while (hit) {
+                                const int j = __ffs(hit) - 1;
+                                hit &= hit - 1;
+                                if ((int64_t)gq < P.cap) {
+                                    P.cq[gq] = qid;
+                                    P.cx[gq] = (int)(c0 + h * 32 + j);
+                                }
+                                gq++;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&Bb.tempty[acc]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// FP32 rows (optionally gathered) -> BF16 rows of kp columns, zero padded,
+// each row scaled by `scale` (times rscale[src] when given)
 __global__ void k_to_bf16(const float* __restrict__ vec, int dp, int d, const int32_t* __restrict__ rows,
-                          int64_t row0, int64_t nrows, int kp, __nv_bfloat16* __restrict__ out) {
+                          int64_t row0, int64_t nrows, int kp, float scale, const float* __restrict__ rscale,
+                          __nv_bfloat16* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows * kp) return;
     const int64_t r = i / kp;
     const int k = (int)(i % kp);
     const int64_t src = rows ? (int64_t)rows[r] : row0 + r;
-    out[i] = __float2bfloat16_rn(k < d ? vec[src * dp + k] : 0.f);
+    const float sc = rscale ? scale * rscale[src] : scale;
+    out[i] = __float2bfloat16_rn(k < d ? vec[src * dp + k] * sc : 0.f);
+}
+
+// L2 scan bias of data row c, bias_c = -(1 - c3) |c|^2 + cbmax |c| (FP64),
+// stored as hi + mid + lo BF16 terms in columns 0..2 of a 16-column row
+__global__ void k_bias_split(const float* __restrict__ sqn, int64_t nx, double c3, double cbmax, int w,
+                             __nv_bfloat16* __restrict__ out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nx) return;
+    const double n = (double)sqn[c];
+    double b = -(1.0 - c3) * n + cbmax * sqrt(n);
+    __nv_bfloat16 t[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        t[k] = __double2bfloat16(b);
+        b -= (double)__bfloat162float(t[k]);
+    }
+    __nv_bfloat16* o = out + c * w;
+    for (int k = 0; k < w; k++) o[k] = k < 3 ? t[k] : __float2bfloat16_rn(0.f);
+}
+
+__global__ void k_fill_abias(int w, __nv_bfloat16* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 128 * w) out[i] = __float2bfloat16_rn((i % w) < 3 ? 1.f : 0.f);
+}
+
+// per scanned query row: the accumulator threshold of the resident-A scan.
+//   L2:     2<a',b'> + bias_c > (1 - c3)|a|^2 - eps^2 - margin
+//   cosine: <a',b'> > 1 - eps - cb - margin   (unit rows)
+// margin covers the FP32 accumulation of the kp + 3 products and the BF16
+// split of the bias, (kp + 16) 2^-23 times the sum of their magnitudes
+__global__ void k_row_thr(const float* __restrict__ sqn, const int32_t* __restrict__ node, int64_t n, int metric,
+                          int kp, float eps_key, float cb, float c3, float cbmax, double maxnorm,
+                          float* __restrict__ thr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double g = (double)(kp + 16) * 1.1920928955078125e-7;
+    if (metric == 0) {
+        const double rn = (double)sqn[node[i]];
+        const double mag = 2.1 * sqrt(rn) * maxnorm + 1.1 * maxnorm * maxnorm + (double)cbmax * maxnorm;
+        thr[i] = (float)((1.0 - (double)c3) * rn - (double)eps_key - g * mag - 1e-30);
+    } else {
+        thr[i] = (float)(1.0 - (double)eps_key - (double)cb - 3.0 * g);
+    }
 }
 
 __global__ void k_gather_f(const float* __restrict__ src, const int32_t* __restrict__ rows, int64_t n,
@@ -490,7 +863,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D BF16 tensor map: rows x kp, box (64 x box_rows), 128-byte swizzle
+// 2-D BF16 tensor map: rows x kp, box (64 x box_rows), 128-byte swizzle; a
+// row narrower than the box (kp < 64) reads zeros beyond its end
+bool try_map(CUtensorMap* m, const void* base, int64_t rows, int kp, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return get_encode()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 CUtensorMap make_map(const void* base, int64_t rows, int kp, int box_rows) {
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
@@ -506,13 +890,16 @@ CUtensorMap make_map(const void* base, int64_t rows, int kp, int box_rows) {
 
 }  // namespace
 
-// BF16 copy of the data rows (built once per index, kept for later scans)
+// BF16 copy of the data rows and the scan's bound constants (built once per
+// index, kept for later scans).  Cosine rows are stored unit-normalised.
 static void ensure_data_bf16(vj_index* ix) {
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     if (ix->xbf.n >= (size_t)ix->nx * kp) return;
-    ix->xbf.ensure((size_t)ix->nx * kp, ix->stream);
-    k_to_bf16<<<vj_div_up(ix->nx * kp, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->nx, kp,
-                                                                    ix->xbf.p);
+    cudaStream_t s = ix->stream;
+    ix->xbf.ensure((size_t)ix->nx * kp, s);
+    const bool cosine = ix->metric != VJ_L2;
+    k_to_bf16<<<vj_div_up(ix->nx * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->nx, kp, 1.f,
+                                                           cosine ? ix->invn.p : nullptr, ix->xbf.p);
     VJ_LAUNCH_CHECK();
     // Exact-key test: when every coordinate is an integer of magnitude <= 256
     // it is exact in BF16, every product is an integer below 2^16 and, with
@@ -520,16 +907,47 @@ static void ensure_data_bf16(vj_index* ix) {
     // and the norm expansion stay integers exactly representable in FP32, so
     // the FP32-accumulated key is exact and needs no bound.
     DBuf<unsigned int> flag;
-    flag.alloc(2, ix->stream);
-    VJ_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(unsigned int), ix->stream));
-    k_int_check<<<vj_div_up(ix->n * ix->dp, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->n * ix->dp, flag.p);
+    flag.alloc(2, s);
+    VJ_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(unsigned int), s));
+    k_int_check<<<vj_div_up(ix->n * ix->dp, 256), 256, 0, s>>>(ix->vec.p, ix->n * ix->dp, flag.p);
     VJ_LAUNCH_CHECK();
     unsigned int h[2] = {0, 0};
-    VJ_CUDA(cudaMemcpyAsync(h, flag.p, sizeof(h), cudaMemcpyDeviceToHost, ix->stream));
-    VJ_CUDA(cudaStreamSynchronize(ix->stream));
-    flag.free_(ix->stream);
+    VJ_CUDA(cudaMemcpyAsync(h, flag.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    flag.free_(s);
     const double mx = (double)h[1];
-    ix->bf16_exact = h[0] == 0 && mx <= 256.0 && (double)ix->d * mx * mx <= 8388608.0;
+    ix->bf16_exact = !cosine && h[0] == 0 && mx <= 256.0 && (double)ix->d * mx * mx <= 8388608.0;
+    // |key_bf16 - key| <= cb |a||b| + c3 (|a|^2 + |b|^2) with
+    //   L2:     cb = 4ub + 2ub^2 + 2 kp 2^-23 + 4u, c3 = 3u
+    //   cosine: cb = 2ub + ub^2 + 2 kp 2^-23 + 8u (unit rows), c3 = 0
+    // (ub = 2^-8 BF16, u = 2^-24 FP32), each with a 1.25 margin
+    const double ub = 1.0 / 256.0, u = VJ_F32_U;
+    if (!cosine) {
+        ix->tc_cb = (float)(1.25 * (4 * ub + 2 * ub * ub + 2.0 * kp * 2 * u + 4 * u));
+        ix->tc_c3 = (float)(1.25 * 3 * u);
+        if (ix->bf16_exact) {
+            ix->tc_cb = 0.f;  // exact integer keys (see above)
+            ix->tc_c3 = 0.f;
+        }
+        // row-independent form: cbmax >= cb |a| for every row
+        ix->tc_cbmax = (float)(ix->tc_cb * ix->maxnorm * 1.0001);
+        // bias rows are 16 wide when the driver accepts a 64-wide box over
+        // them (zeros beyond the row), else padded to the box
+        ix->xbias.ensure((size_t)ix->nx * 16, s);
+        CUtensorMap probe;
+        ix->bias_w = try_map(&probe, ix->xbias.p, ix->nx, 16, RS_BN) ? 16 : 64;
+        if (ix->bias_w > 16) ix->xbias.ensure((size_t)ix->nx * ix->bias_w, s);
+        k_bias_split<<<vj_div_up(ix->nx, 256), 256, 0, s>>>(ix->sqn.p, ix->nx, (double)ix->tc_c3,
+                                                              (double)ix->tc_cbmax, ix->bias_w, ix->xbias.p);
+        VJ_LAUNCH_CHECK();
+        ix->abias.ensure(128 * 64, s);
+        k_fill_abias<<<vj_div_up(128 * 64, 256), 256, 0, s>>>(ix->bias_w, ix->abias.p);
+        VJ_LAUNCH_CHECK();
+    } else {
+        ix->tc_cb = (float)(1.25 * (2 * ub + ub * ub + 2.0 * kp * 2 * u + 8 * u));
+        ix->tc_c3 = 0.f;
+        ix->tc_cbmax = 0.f;
+    }
 }
 
 // Candidate pairs (query index, data id) of the BF16 tensor-core scan of the
@@ -541,6 +959,10 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     cudaStream_t s = ix->stream;
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     ensure_data_bf16(ix);
+    const bool cosine = ix->metric != VJ_L2;
+    // kp <= 256: resident query rows and the bias k-block; wider rows stream
+    // both operands through the ring
+    const bool resident = kp <= RS_MAX_KB * TC_BK;
     DBuf<__nv_bfloat16> abf;
     DBuf<int32_t> aid, anode;
     DBuf<float> an;
@@ -551,49 +973,89 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     k_query_rows<<<vj_div_up(nr, 256), 256, 0, s>>>(qrows, nr, (int32_t)ix->nx, aid.p, anode.p);
     VJ_LAUNCH_CHECK();
     const int32_t* arow = anode.p;
-    k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, abf.p);
+    // query rows: L2 scaled by 2 for the resident form (2<a,b> + bias), cosine unit rows
+    const float ascale = (!cosine && resident) ? 2.f : 1.f;
+    k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, ascale,
+                                                      cosine ? ix->invn.p : nullptr, abf.p);
     VJ_LAUNCH_CHECK();
-    const float* nsrc = ix->metric == VJ_L2 ? ix->sqn.p : ix->invn.p;
-    k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(nsrc, arow, nr, an.p);
+    const float eps_key = cosine ? eps : eps * eps;
+    if (resident) {
+        k_row_thr<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, ix->metric, kp, eps_key, ix->tc_cb,
+                                                      ix->tc_c3, ix->tc_cbmax, ix->maxnorm, an.p);
+    } else {
+        k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, an.p);
+    }
     VJ_LAUNCH_CHECK();
 
-    CUtensorMap ta = make_map(abf.p, nr, kp, TC_BM);
-    CUtensorMap tb = make_map(ix->xbf.p, ix->nx, kp, TC_BN);
-    TcScanParams P;
-    P.nrows = nr;
-    P.ncols = ix->nx;
-    P.nkb = kp / TC_BK;
-    P.nrt = vj_div_up(nr, TC_BM);
-    P.nct = vj_div_up(ix->nx, TC_BN);
-    P.metric = ix->metric;
-    P.a_n = an.p;
-    P.b_n = nsrc;  // data rows are the first nx nodes
-    P.a_ids = aid.p;
-    P.eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
-    const double ub = 1.0 / 256.0, u = VJ_F32_U;
-    // |key_bf16 - key| <= (4ub + 2ub^2 + 2 kp 2^-23 + 4u) |a||b| + 3u (|a|^2 + |b|^2), with a 1.25 margin
-    P.cb = (float)(1.25 * (4 * ub + 2 * ub * ub + 2.0 * kp * 2 * u + 4 * u));
-    P.c3 = (float)(1.25 * 3 * u);
-    if (ix->metric != VJ_L2) P.cb = (float)(1.25 * (2 * ub + ub * ub + 2.0 * kp * 2 * u + 8 * u));
-    if (ix->metric == VJ_L2 && ix->bf16_exact) {
-        P.cb = 0.f;  // exact integer keys (see ensure_data_bf16)
-        P.c3 = 0.f;
-    }
-    // row-independent form of the bound (after the exact-key adjustment)
-    P.cbmax = ix->metric == VJ_L2 ? (float)(P.cb * ix->maxnorm * 1.0001) : 0.f;
     DBuf<unsigned long long> ctr;
     DBuf<int> err;
     ctr.alloc(1, s);
     err.alloc(1, s);
-    P.ncand = ctr.p;
-    P.err = err.p;
-    P.spin_limit = 1ll << 22;  // try_wait polls; seconds at most, then an error
-    const int ntiles = P.nrt * P.nct;
-    const int grid = std::min(ntiles, ix->num_sms);
-    const size_t smem = sizeof(TcSmem) + 1024;
-    const int mode = ix->metric != VJ_L2 ? 2 : (ix->bf16_exact ? 0 : 1);
-    auto kern = mode == 0 ? k_tc_scan<0> : (mode == 1 ? k_tc_scan<1> : k_tc_scan<2>);
-    VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long spin_limit = 1ll << 22;  // try_wait polls; seconds at most, then an error
+    std::function<void()> launch;
+    CUtensorMap ta, tb, tab, tbb;
+    RsParams R{};
+    TcScanParams P{};
+    if (resident) {
+        ta = make_map(abf.p, nr, kp, 128);
+        tb = make_map(ix->xbf.p, ix->nx, kp, RS_BN);
+        if (!cosine) {
+            tab = make_map(ix->abias.p, 128, ix->bias_w, 128);
+            tbb = make_map(ix->xbias.p, ix->nx, ix->bias_w, RS_BN);
+        } else {
+            tab = ta;  // unused without the bias block
+            tbb = tb;
+        }
+        R.nrows = nr;
+        R.ncols = ix->nx;
+        R.nkb = kp / TC_BK;
+        R.bias = cosine ? 0 : 1;
+        R.nrp = (int)vj_div_up(nr, 256);
+        R.nct = (int)vj_div_up(ix->nx, RS_BN);
+        // work units: a 256-row query block x a run of data tiles, about 16
+        // per SM; concurrent units share their data tiles through L2
+        const int64_t want = (int64_t)ix->num_sms * 16;
+        int64_t tpu = ((int64_t)R.nrp * R.nct + want - 1) / want;
+        tpu = std::max<int64_t>(tpu, 8);
+        R.tpu = (int)std::min<int64_t>(tpu, R.nct);
+        R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
+        R.stages = std::min(RS_MAX_STAGES, 12 - 2 * R.nkb);
+        R.a_thr = an.p;
+        R.a_ids = aid.p;
+        R.ncand = ctr.p;
+        R.err = err.p;
+        R.spin_limit = spin_limit;
+        const size_t smem = 1024 + (size_t)RS_BOX * (1 + 2 * R.nkb + R.stages) + 1024;
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_scan_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = std::min(R.nunits, ix->num_sms);
+        launch = [&, grid, smem]() { k_tc_scan_res<<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };
+    } else {
+        ta = make_map(abf.p, nr, kp, TC_BM);
+        tb = make_map(ix->xbf.p, ix->nx, kp, TC_BN);
+        P.nrows = nr;
+        P.ncols = ix->nx;
+        P.nkb = kp / TC_BK;
+        P.nrt = (int)vj_div_up(nr, TC_BM);
+        P.nct = (int)vj_div_up(ix->nx, TC_BN);
+        P.metric = ix->metric;
+        P.a_n = an.p;
+        P.b_n = ix->sqn.p;  // data rows are the first nx nodes
+        P.a_ids = aid.p;
+        P.eps_key = eps_key;
+        P.cb = ix->tc_cb;
+        P.c3 = ix->tc_c3;
+        P.cbmax = ix->tc_cbmax;
+        P.ncand = ctr.p;
+        P.err = err.p;
+        P.spin_limit = spin_limit;
+        const int ntiles = P.nrt * P.nct;
+        const int grid = std::min(ntiles, ix->num_sms);
+        const size_t smem = sizeof(TcSmem) + 1024;
+        const int mode = cosine ? 2 : (ix->bf16_exact ? 0 : 1);
+        auto kern = mode == 0 ? k_tc_scan<0> : (mode == 1 ? k_tc_scan<1> : k_tc_scan<2>);
+        VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        launch = [&, grid, smem, kern]() { kern<<<grid, TC_THREADS, smem, s>>>(ta, tb, P); };
+    }
     int64_t cap = std::max<int64_t>(cq.n, std::max<int64_t>(nr * 64, 1 << 20));
     unsigned long long hn = 0;
     int herr = 0;
@@ -604,13 +1066,13 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     for (int attempt = 0; attempt < 2; attempt++) {
         cq.ensure(cap, s);
         cx.ensure(cap, s);
-        P.cq = cq.p;
-        P.cx = cx.p;
-        P.cap = (int64_t)cq.n;
+        P.cq = R.cq = cq.p;
+        P.cx = R.cx = cx.p;
+        P.cap = R.cap = (int64_t)cq.n;
         VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
         VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
         VJ_CUDA(cudaEventRecord(e0, s));
-        kern<<<grid, TC_THREADS, smem, s>>>(ta, tb, P);
+        launch();
         VJ_LAUNCH_CHECK();
         VJ_CUDA(cudaEventRecord(e1, s));
         VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
@@ -618,7 +1080,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         VJ_CUDA(cudaStreamSynchronize(s));
         VJ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core scan: a pipeline wait timed out");
-        if ((int64_t)hn <= P.cap) break;
+        if ((int64_t)hn <= (int64_t)cq.n) break;
         cap = (int64_t)hn + 1024;
     }
     cudaEventDestroy(e0);

@@ -602,10 +602,8 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     VJ_CUDA(cudaEventCreate(&e1));
     VJ_CUDA(cudaEventRecord(e0, s));
     const float eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
-    // Gram-key bound: (2dp+10) u (|a|+|b|)^2 for L2 (norms up to maxnorm),
-    // (2dp+10) u * 4 for cosine
-    // candidates from the BF16 tensor-core scan (bounded superset), then the
-    // exact FP32 / FP64 re-decision below
+    // candidates from the BF16 tensor-core scan (a bounded superset of the
+    // result), then the exact FP32 / FP64 re-decision below
     DBuf<int32_t> cq, cx;
     DBuf<float> cd;
     DBuf<unsigned long long> ctr;

@@ -87,6 +87,8 @@ static void free_index(vj_index* ix) {
     ix->plan_beam.free_(s);
     ix->routed.free_(s);
     ix->xbf.free_(s);
+    ix->xbias.free_(s);
+    ix->abias.free_(s);
     ix->done.free_(s);
     ix->cache.free_(s);
     ix->steps.free_(s);

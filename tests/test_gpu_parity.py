@@ -152,6 +152,21 @@ def test_exact_join_matches_nlj(built, oracle):
         np.testing.assert_allclose(r.dists, dd, rtol=1e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("metric", [0, 1])
+def test_exact_join_wide_rows_matches_nlj(oracle, metric):
+    """Rows wider than 256 columns take the streamed-operand scan kernel."""
+    w = inputs.uniform_small(105 + metric, 1200, 130, 300, metric=metric, degree=12, knn_k=24)
+    ix = _build(w)
+    eps = _calib_eps(oracle, w, 8, w.metric)
+    r = vj.vj_join_exact(ix, eps)
+    off, ids, dd = oracle.nlj(w.X, w.Q, float(np.float32(eps)), w.metric)
+    band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+    diff = (_pairs(r.offsets, r.ids) ^ _pairs(off, ids)) - band
+    assert not diff, f"{len(diff)} pairs differ"
+    assert len(ids) > 0
+    ix.free()
+
+
 def test_recall_of_join_is_reported_against_exact(built, oracle):
     name, w, ix = built
     eps = _calib_eps(oracle, w, 10, w.metric)
