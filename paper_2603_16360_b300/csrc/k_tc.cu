@@ -159,6 +159,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
+// K-major operand, 32-byte swizzle (16 BF16 per row): 8-row groups 256 B apart
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+    d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)6 << 61;                    // 32-byte swizzle
+    return d;
+}
+
 // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
 // K-major, M = 128, N = 256
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
@@ -459,19 +470,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ---------------------------------------------------------------- resident-A scan
-// For kp <= 256 a CTA keeps 256 query rows (two 128-row MMA operands, every
+// For kp <= 128 a CTA keeps 256 query rows (two 128-row MMA operands, every
 // k-block) in shared memory for a run of 128-row data tiles, so only the data
-// side crosses L2 per tile (K = 128: 32 KB per 8.4 MFLOP instead of 96 KB).
+// side crosses L2 per tile (K = 128: 36 KB per 8.4 MFLOP instead of 96 KB).
 // The per-column part of the candidate test rides in the GEMM: after the data
-// k-blocks comes a bias k-block whose A side holds (1, 1, 1, 0, ...) and whose
-// data side holds a three-term BF16 split of the column bias, so the
-// accumulator is 2<a,b> + bias_c and the epilogue is a row-wise max against
-// one threshold per query row (one FMNMX per pair).
+// k-blocks comes one K=16 bias step whose A side holds (1, 1, 1, 0, ...) and
+// whose data side holds a three-term BF16 split of the column bias (16-column
+// boxes with 32-byte swizzle), so the accumulator is 2<a,b> + bias_c and the
+// epilogue is a row-wise max against one threshold per query row (one FMNMX
+// per pair).  A ring stage holds one whole data tile.
 constexpr int RS_BN = 128;                     // data rows per tile (MMA N)
 constexpr int RS_EPI = 16;                     // epilogue warps
 constexpr int RS_THREADS = (2 + RS_EPI) * 32;
 constexpr uint32_t RS_BOX = 128 * 64 * 2;      // one 128-row x 64-column BF16 box
-constexpr int RS_MAX_KB = 4;                   // data k-blocks (kp <= 256)
+constexpr uint32_t RS_BBOX = 128 * 16 * 2;     // one 128-row x 16-column BF16 bias box
+constexpr int RS_MAX_KB = 2;                   // data k-blocks (kp <= 128)
 constexpr int RS_MAX_STAGES = 8;
 constexpr uint32_t RS_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RS_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
@@ -515,12 +528,14 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     extern __shared__ uint8_t rs_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(rs_raw) + 1023) & ~uintptr_t(1023));
     RsBars& Bb = *reinterpret_cast<RsBars*>(base);
-    uint8_t* sAb = base + 1024;
-    uint8_t* sA = sAb + RS_BOX;                       // [2][nkb] boxes
-    uint8_t* sB = sA + 2 * P.nkb * RS_BOX;            // [stages] boxes
+    // bias boxes first: a misread descriptor could only reach later tiles
+    uint8_t* sAb = base + 1024;                          // query-side bias box
+    uint8_t* sBb = sAb + RS_BBOX;                        // [stages] data bias boxes
+    uint8_t* sA = sBb + P.stages * RS_BBOX;              // [2][nkb] query boxes
+    uint8_t* sB = sA + 2 * P.nkb * RS_BOX;               // [stages][nkb] data boxes
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* abort = &Bb.abort;
-    const int nkt = P.nkb + P.bias;  // k-blocks per data tile
+    const uint32_t stage_tx = (uint32_t)P.nkb * RS_BOX + (P.bias ? RS_BBOX : 0u);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.stages; s++) {
@@ -558,7 +573,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             int a_units = 0;                   // query blocks loaded so far
             bool ok = true;
             if (P.bias) {
-                mbar_arrive_tx(&Bb.abar, RS_BOX);
+                mbar_arrive_tx(&Bb.abar, RS_BBOX);
                 tma_load_2d(sAb, &tAb, &Bb.abar, 0, 0);
             }
             for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
@@ -573,21 +588,20 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     for (int kb = 0; kb < P.nkb; kb++)
                         tma_load_2d(sA + (blk * P.nkb + kb) * RS_BOX, &tA, &Bb.afull, kb * 64, rp * 256 + blk * 128);
                 a_units++;
-                for (int ct = t0; ct < t1 && ok; ct++) {
-                    for (int kb = 0; kb < nkt; kb++) {
-                        if (!mbar_wait(&Bb.empty[s], ph ^ 1u, abort, P.spin_limit)) {
-                            ok = false;
-                            break;
-                        }
-                        mbar_arrive_tx(&Bb.full[s], RS_BOX);
-                        if (kb < P.nkb) tma_load_2d(sB + s * RS_BOX, &tB, &Bb.full[s], kb * 64, ct * RS_BN);
-                        else tma_load_2d(sB + s * RS_BOX, &tBb, &Bb.full[s], 0, ct * RS_BN);
-                        issued |= 1u << s;
-                        last_ph = (last_ph & ~(1u << s)) | (ph << s);
-                        if (++s == P.stages) {
-                            s = 0;
-                            ph ^= 1u;
-                        }
+                for (int ct = t0; ct < t1; ct++) {
+                    if (!mbar_wait(&Bb.empty[s], ph ^ 1u, abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(&Bb.full[s], stage_tx);
+                    for (int kb = 0; kb < P.nkb; kb++)
+                        tma_load_2d(sB + (s * P.nkb + kb) * RS_BOX, &tB, &Bb.full[s], kb * 64, ct * RS_BN);
+                    if (P.bias) tma_load_2d(sBb + s * RS_BBOX, &tBb, &Bb.full[s], 0, ct * RS_BN);
+                    issued |= 1u << s;
+                    last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                    if (++s == P.stages) {
+                        s = 0;
+                        ph ^= 1u;
                     }
                 }
             }
@@ -615,7 +629,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             uint32_t ph = 0;
             int i = 0, j = 0;
             bool ok = !P.bias || mbar_wait(&Bb.abar, 0, abort, P.spin_limit);
-            const uint64_t abd = sdesc_sw128(su32(sAb));
+            const uint64_t abd = sdesc_sw32(su32(sAb));
             for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, j++) {
                 const int cc = u / P.nrp;
                 const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
@@ -632,35 +646,34 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t d0 = tmem + (uint32_t)(acc * 256), d1 = d0 + 128u;
-                    for (int kb = 0; kb < nkt; kb++) {
-                        if (!mbar_wait(&Bb.full[s], ph, abort, P.spin_limit)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint64_t bd = sdesc_sw128(su32(sB + s * RS_BOX));
-                        if (kb < P.nkb) {
-                            const uint64_t a0 = sdesc_sw128(su32(sA + kb * RS_BOX));
-                            const uint64_t a1 = sdesc_sw128(su32(sA + (P.nkb + kb) * RS_BOX));
+                    if (!mbar_wait(&Bb.full[s], ph, abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    for (int kb = 0; kb < P.nkb; kb++) {
+                        const uint64_t bd = sdesc_sw128(su32(sB + (s * P.nkb + kb) * RS_BOX));
+                        const uint64_t a0 = sdesc_sw128(su32(sA + kb * RS_BOX));
+                        const uint64_t a1 = sdesc_sw128(su32(sA + (P.nkb + kb) * RS_BOX));
 #pragma unroll
-                            for (int kk = 0; kk < 4; kk++) {
-                                // advance 16 BF16 (32 bytes) along K inside the swizzled rows
-                                const uint32_t accf = (kb | kk) != 0;
-                                tc_mma(d0, a0 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
-                                tc_mma(d1, a1 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
-                            }
-                        } else {
-                            // bias block: its first K=16 step holds the three bias terms
-                            tc_mma(d0, abd, bd, RS_IDESC, 1u);
-                            tc_mma(d1, abd, bd, RS_IDESC, 1u);
-                        }
-                        tc_commit(&Bb.empty[s]);
-                        if (++s == P.stages) {
-                            s = 0;
-                            ph ^= 1u;
+                        for (int kk = 0; kk < 4; kk++) {
+                            // advance 16 BF16 (32 bytes) along K inside the swizzled rows
+                            const uint32_t accf = (kb | kk) != 0;
+                            tc_mma(d0, a0 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
+                            tc_mma(d1, a1 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), RS_IDESC, accf);
                         }
                     }
-                    if (!ok) break;
+                    if (P.bias) {
+                        // the bias step: K = 16 columns holding the three bias terms
+                        const uint64_t bbd = sdesc_sw32(su32(sBb + s * RS_BBOX));
+                        tc_mma(d0, abd, bbd, RS_IDESC, 1u);
+                        tc_mma(d1, abd, bbd, RS_IDESC, 1u);
+                    }
+                    tc_commit(&Bb.empty[s]);
+                    if (++s == P.stages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                     tc_commit(&Bb.tfull[acc]);
                 }
                 if (!ok) break;
@@ -706,6 +719,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 uint32_t va[64];
                 tmem_ld64_issue(taddr, va);
                 tmem_wait_ld64(va);
+                // the accumulator is in registers: hand the TMEM buffer back now
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&Bb.tempty[acc]);
                 float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
 #pragma unroll
                 for (int j = 0; j < 64; j += 4) {
@@ -752,9 +769,6 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         }
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&Bb.tempty[acc]);
             }
         }
     }
@@ -783,7 +797,7 @@ __global__ void k_to_bf16(const float* __restrict__ vec, int dp, int d, const in
 
 // L2 scan bias of data row c, bias_c = -(1 - c3) |c|^2 + cbmax |c| (FP64),
 // stored as hi + mid + lo BF16 terms in columns 0..2 of a 16-column row
-__global__ void k_bias_split(const float* __restrict__ sqn, int64_t nx, double c3, double cbmax, int w,
+__global__ void k_bias_split(const float* __restrict__ sqn, int64_t nx, double c3, double cbmax,
                              __nv_bfloat16* __restrict__ out) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nx) return;
@@ -795,13 +809,14 @@ __global__ void k_bias_split(const float* __restrict__ sqn, int64_t nx, double c
         t[k] = __double2bfloat16(b);
         b -= (double)__bfloat162float(t[k]);
     }
-    __nv_bfloat16* o = out + c * w;
-    for (int k = 0; k < w; k++) o[k] = k < 3 ? t[k] : __float2bfloat16_rn(0.f);
+    __nv_bfloat16* o = out + c * 16;
+#pragma unroll
+    for (int k = 0; k < 16; k++) o[k] = k < 3 ? t[k] : __float2bfloat16_rn(0.f);
 }
 
-__global__ void k_fill_abias(int w, __nv_bfloat16* __restrict__ out) {
+__global__ void k_fill_abias(__nv_bfloat16* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < 128 * w) out[i] = __float2bfloat16_rn((i % w) < 3 ? 1.f : 0.f);
+    if (i < 128 * 16) out[i] = __float2bfloat16_rn((i & 15) < 3 ? 1.f : 0.f);
 }
 
 // per scanned query row: the accumulator threshold of the resident-A scan.
@@ -863,18 +878,21 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// 2-D BF16 tensor map: rows x kp, box (64 x box_rows), 128-byte swizzle; a
-// row narrower than the box (kp < 64) reads zeros beyond its end
-bool try_map(CUtensorMap* m, const void* base, int64_t rows, int kp, int box_rows) {
-    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+// 2-D BF16 tensor map over rows of 16 columns, box (16 x box_rows), 32-byte swizzle
+CUtensorMap make_map16(const void* base, int64_t rows, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {16, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {32};
+    cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    return get_encode()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    VJ_REQUIRE(r == CUDA_SUCCESS, VJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return m;
 }
 
+// 2-D BF16 tensor map: rows x kp, box (64 x box_rows), 128-byte swizzle
 CUtensorMap make_map(const void* base, int64_t rows, int kp, int box_rows) {
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
@@ -931,17 +949,12 @@ static void ensure_data_bf16(vj_index* ix) {
         }
         // row-independent form: cbmax >= cb |a| for every row
         ix->tc_cbmax = (float)(ix->tc_cb * ix->maxnorm * 1.0001);
-        // bias rows are 16 wide when the driver accepts a 64-wide box over
-        // them (zeros beyond the row), else padded to the box
         ix->xbias.ensure((size_t)ix->nx * 16, s);
-        CUtensorMap probe;
-        ix->bias_w = try_map(&probe, ix->xbias.p, ix->nx, 16, RS_BN) ? 16 : 64;
-        if (ix->bias_w > 16) ix->xbias.ensure((size_t)ix->nx * ix->bias_w, s);
         k_bias_split<<<vj_div_up(ix->nx, 256), 256, 0, s>>>(ix->sqn.p, ix->nx, (double)ix->tc_c3,
-                                                              (double)ix->tc_cbmax, ix->bias_w, ix->xbias.p);
+                                                              (double)ix->tc_cbmax, ix->xbias.p);
         VJ_LAUNCH_CHECK();
-        ix->abias.ensure(128 * 64, s);
-        k_fill_abias<<<vj_div_up(128 * 64, 256), 256, 0, s>>>(ix->bias_w, ix->abias.p);
+        ix->abias.ensure(128 * 16, s);
+        k_fill_abias<<<vj_div_up(128 * 16, 256), 256, 0, s>>>(ix->abias.p);
         VJ_LAUNCH_CHECK();
     } else {
         ix->tc_cb = (float)(1.25 * (2 * ub + ub * ub + 2.0 * kp * 2 * u + 8 * u));
@@ -960,7 +973,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
-    // kp <= 256: resident query rows and the bias k-block; wider rows stream
+    // kp <= 128: resident query rows and the bias step; wider rows stream
     // both operands through the ring
     const bool resident = kp <= RS_MAX_KB * TC_BK;
     DBuf<__nv_bfloat16> abf;
@@ -1000,8 +1013,8 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         ta = make_map(abf.p, nr, kp, 128);
         tb = make_map(ix->xbf.p, ix->nx, kp, RS_BN);
         if (!cosine) {
-            tab = make_map(ix->abias.p, 128, ix->bias_w, 128);
-            tbb = make_map(ix->xbias.p, ix->nx, ix->bias_w, RS_BN);
+            tab = make_map16(ix->abias.p, 128, 128);
+            tbb = make_map16(ix->xbias.p, ix->nx, RS_BN);
         } else {
             tab = ta;  // unused without the bias block
             tbb = tb;
@@ -1019,13 +1032,16 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         tpu = std::max<int64_t>(tpu, 8);
         R.tpu = (int)std::min<int64_t>(tpu, R.nct);
         R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
-        R.stages = std::min(RS_MAX_STAGES, 12 - 2 * R.nkb);
+        // ring stages of one data tile each, within 227 KB of shared memory
+        const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
+        const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
+        R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
         R.a_thr = an.p;
         R.a_ids = aid.p;
         R.ncand = ctr.p;
         R.err = err.p;
         R.spin_limit = spin_limit;
-        const size_t smem = 1024 + (size_t)RS_BOX * (1 + 2 * R.nkb + R.stages) + 1024;
+        const size_t smem = fixed + per * (size_t)R.stages;
         VJ_CUDA(cudaFuncSetAttribute(k_tc_scan_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = std::min(R.nunits, ix->num_sms);
         launch = [&, grid, smem]() { k_tc_scan_res<<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };

@@ -112,9 +112,8 @@ struct vj_index {
     DBuf<int32_t> depth;  // [nq]
     int max_depth = 0;
     DBuf<__nv_bfloat16> xbf;   // [nx][kp] BF16 copy of the data rows (tensor-core scans)
-    DBuf<__nv_bfloat16> xbias; // [nx][bias_w] L2: three-term BF16 split of each data row's scan bias
-    DBuf<__nv_bfloat16> abias; // [128][bias_w] (1, 1, 1, 0, ...) rows: the query side of the bias step
-    int bias_w = 16;
+    DBuf<__nv_bfloat16> xbias; // [nx][16] L2: three-term BF16 split of each data row's scan bias
+    DBuf<__nv_bfloat16> abias; // [128][16] (1, 1, 1, 0, ...) rows: the query side of the bias step
     float tc_cb = 0.f, tc_c3 = 0.f, tc_cbmax = 0.f;  // BF16 scan bound constants
     // per-query plan (route to the brute-force scan / hybrid budget), optional
     DBuf<uint8_t> plan_route;  // [nq]
