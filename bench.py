@@ -307,18 +307,17 @@ def main():
         route_acc = float(((pred[held, 1] > 0) == route_lab[held]).mean())
         # operating point: the fastest (route threshold, hybrid-queue cap) whose join reaches recall 0.95
         op, sweep = None, []
-        for cap in (0, 64):
-            for thr in (0.9, 0.7, 0.5, 0.3, 0.15, 0.05):
-                vj.vj_attach_predictor(ix, mlp, thr, cap)
-                vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
-                                      hybrid_beam=max(cap, 1), learned=1)
-                vj.vj_join(ix, eps)
-                r = vj.vj_join(ix, eps)
-                rec = recall_of(r, ex, w.nx)
-                sweep.append({"thr": thr, "beam_cap": cap, "recall": round(rec, 4),
-                              "ms": round(r.stats["ms_total"], 2)})
-                if rec >= 0.95 and (op is None or r.stats["ms_total"] < op[3]):
-                    op = (thr, rec, r, r.stats["ms_total"], cap)
+        grid = [(0, t) for t in (0.99, 0.97, 0.95, 0.9, 0.8, 0.6, 0.4, 0.2)] + [(64, t) for t in (0.9, 0.6, 0.3)]
+        for cap, thr in grid:
+            vj.vj_attach_predictor(ix, mlp, thr, cap)
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
+                                  hybrid_beam=max(cap, 1), learned=1)
+            vj.vj_join(ix, eps)
+            r = vj.vj_join(ix, eps)
+            rec = recall_of(r, ex, w.nx)
+            sweep.append({"thr": thr, "beam_cap": cap, "recall": round(rec, 4), "ms": round(r.stats["ms_total"], 2)})
+            if rec >= 0.95 and (op is None or r.stats["ms_total"] < op[3]):
+                op = (thr, rec, r, r.stats["ms_total"], cap)
         if op is None:  # nothing reached 0.95: route everything that the predictor doubts least
             op = (0.05, rec, r, r.stats["ms_total"], 64)
         thr, lrec, lr_, _, lcap = op

@@ -93,7 +93,8 @@ struct SegSmem {
 __global__ void __launch_bounds__(SS_WPB * 32)
     k_seg_sort_copy(const int64_t* __restrict__ start, const int32_t* __restrict__ counts,
                     const int64_t* __restrict__ offsets, const int32_t* __restrict__ sid,
-                    const float* __restrict__ sd, int32_t* __restrict__ did, float* __restrict__ dd, int64_t nseg) {
+                    const float* __restrict__ sd, int32_t* __restrict__ did, float* __restrict__ dd, int64_t nseg,
+                    int64_t* __restrict__ large, int* __restrict__ nlarge) {
     __shared__ SegSmem sm[SS_WPB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     SegSmem& S = sm[warp];
@@ -157,15 +158,86 @@ __global__ void __launch_bounds__(SS_WPB * 32)
             }
             __syncwarp();
         } else {
-            // large rows: rank = number of smaller ids (ids are distinct)
-            for (int i = lane; i < n; i += 32) {
-                int a = sid[src + i];
-                int rank = 0;
-                for (int j = 0; j < n; j++) rank += sid[src + j] < a;
-                did[dst + rank] = a;
-                dd[dst + rank] = sd[src + i];
-            }
+            // large rows go to the block-wide sort
+            if (lane == 0) large[atomicAdd(nlarge, 1)] = sg;
         }
+    }
+}
+
+// ascending compare-exchange of (id, d) pairs i < p; a partner beyond the row
+// end stands for +infinity and never moves
+__device__ __forceinline__ void cmpx(int32_t* id, float* d, int i, int p, int n) {
+    if (p >= n) return;
+    const int a = id[i], b = id[p];
+    if (a > b) {
+        const float da = d[i], db = d[p];
+        id[i] = b;
+        id[p] = a;
+        d[i] = db;
+        d[p] = da;
+    }
+}
+
+// one row sorted by one block: bitonic network in its all-ascending form (a
+// mirrored compare at the start of each merge, then half-cleaners), so a row
+// of any length sorts as if padded with +infinity.  In shared memory up to
+// SL_CAP entries, in place in the destination beyond that.
+constexpr int SL_T = 1024;
+constexpr int SL_CAP = 16384;
+
+__device__ void block_bitonic(int32_t* id, float* d, int n) {
+    int P2 = 1;
+    while (P2 < n) P2 <<= 1;
+    for (int k = 2; k <= P2; k <<= 1) {
+        const int half = k >> 1;
+        for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+            const int i = (t / half) * k + (t % half);
+            cmpx(id, d, i, i ^ (k - 1), n);
+        }
+        __syncthreads();
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P2 / 2; t += blockDim.x) {
+                const int i = (t / j) * 2 * j + (t % j);
+                cmpx(id, d, i, i + j, n);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SL_T)
+    k_seg_sort_large(const int64_t* __restrict__ start, const int32_t* __restrict__ counts,
+                     const int64_t* __restrict__ offsets, const int32_t* __restrict__ sid,
+                     const float* __restrict__ sd, int32_t* __restrict__ did, float* __restrict__ dd,
+                     const int64_t* __restrict__ large, const int* __restrict__ nlarge) {
+    extern __shared__ uint8_t sl_raw[];
+    int* sid_s = reinterpret_cast<int*>(sl_raw);
+    float* sd_s = reinterpret_cast<float*>(sl_raw + SL_CAP * sizeof(int));
+    const int nl = *nlarge;
+    for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+        const int64_t sg = large[li];
+        const int n = counts[sg];
+        const int64_t src = start[sg], dst = offsets[sg];
+        if (n <= SL_CAP) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                sid_s[i] = sid[src + i];
+                sd_s[i] = sd[src + i];
+            }
+            __syncthreads();
+            block_bitonic(sid_s, sd_s, n);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                did[dst + i] = sid_s[i];
+                dd[dst + i] = sd_s[i];
+            }
+        } else {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                did[dst + i] = sid[src + i];
+                dd[dst + i] = sd[src + i];
+            }
+            __syncthreads();
+            block_bitonic(did + dst, dd + dst, n);
+        }
+        __syncthreads();
     }
 }
 
@@ -192,8 +264,18 @@ void vj_segment_sort_copy(const int64_t* src_start, const int32_t* counts, const
                           const int32_t* src_id, const float* src_d, int32_t* dst_id, float* dst_d, int64_t nseg,
                           vj_index* ix) {
     if (nseg == 0) return;
+    cudaStream_t s = ix->stream;
+    // rows longer than a warp's shared-memory sort are listed for the block-wide sort
+    ix->sort_large.ensure(nseg, s);
+    ix->sort_nlarge.ensure(1, s);
+    VJ_CUDA(cudaMemsetAsync(ix->sort_nlarge.p, 0, sizeof(int), s));
     int blocks = (int)std::min<int64_t>(vj_div_up(nseg, SS_WPB), (int64_t)ix->num_sms * 16);
-    k_seg_sort_copy<<<blocks, SS_WPB * 32, 0, ix->stream>>>(src_start, counts, offsets, src_id, src_d, dst_id, dst_d,
-                                                            nseg);
+    k_seg_sort_copy<<<blocks, SS_WPB * 32, 0, s>>>(src_start, counts, offsets, src_id, src_d, dst_id, dst_d, nseg,
+                                                   ix->sort_large.p, ix->sort_nlarge.p);
+    VJ_LAUNCH_CHECK();
+    const int smem = SL_CAP * (int)(sizeof(int) + sizeof(float));
+    VJ_CUDA(cudaFuncSetAttribute(k_seg_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_seg_sort_large<<<ix->num_sms, SL_T, smem, s>>>(src_start, counts, offsets, src_id, src_d, dst_id, dst_d,
+                                                     ix->sort_large.p, ix->sort_nlarge.p);
     VJ_LAUNCH_CHECK();
 }

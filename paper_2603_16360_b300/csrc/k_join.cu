@@ -165,9 +165,11 @@ __device__ __forceinline__ void raise_err(const JoinParams& P, int code) {
 __device__ bool vis_reserve(const JoinParams& P, QueryState& s, int m, const WarpSpace& W, int lane,
                             long long& c_spill) {
     if (s.nvis + m <= s.vislimit) return true;
+    // grow by 4x, the last step clipped to the region size
     int cap = s.region < 0 ? GCAP0 : (int)(s.mask + 1u) * 4;
-    while (cap / 2 < s.nvis + m && cap <= P.gmax / 4) cap *= 4;
-    if (cap > P.gmax || cap / 2 < s.nvis + m) {
+    while (cap / 2 < s.nvis + m && cap < P.gmax) cap *= 4;
+    if (cap > P.gmax) cap = P.gmax;
+    if (cap <= (int)s.mask + 1 || cap / 2 < s.nvis + m) {
         if (lane == 0) raise_err(P, VJ_DERR_VISITED_OVERFLOW);
         return false;
     }

@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 #include <functional>
 
 #include "vj_device.cuh"
@@ -1025,12 +1026,26 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         R.bias = cosine ? 0 : 1;
         R.nrp = (int)vj_div_up(nr, 256);
         R.nct = (int)vj_div_up(ix->nx, RS_BN);
-        // work units: a 256-row query block x a run of data tiles, about 16
-        // per SM; concurrent units share their data tiles through L2
-        const int64_t want = (int64_t)ix->num_sms * 16;
-        int64_t tpu = ((int64_t)R.nrp * R.nct + want - 1) / want;
-        tpu = std::max<int64_t>(tpu, 8);
-        R.tpu = (int)std::min<int64_t>(tpu, R.nct);
+        // work units: a 256-row query block x a run of data tiles; units run
+        // query block fastest so concurrent units share data tiles in L2.
+        // The run length minimises the busiest SM's load: its units' tiles
+        // plus about 3 tiles of pipeline refill per unit (query rows reload)
+        {
+            const int64_t g = std::max(1, ix->num_sms);
+            int64_t best = INT64_MAX;
+            int best_tpu = R.nct;
+            for (int64_t ncc = 1; ncc <= R.nct; ncc++) {
+                const int64_t tpu = (R.nct + ncc - 1) / ncc;
+                if (ncc > 1 && (R.nct + tpu - 1) / tpu != ncc) continue;  // same split as a smaller ncc
+                const int64_t per = ((int64_t)R.nrp * ncc + g - 1) / g;
+                const int64_t load = per * (tpu + 3);
+                if (load < best) {
+                    best = load;
+                    best_tpu = (int)tpu;
+                }
+            }
+            R.tpu = best_tpu;
+        }
         R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
         // ring stages of one data tile each, within 227 KB of shared memory
         const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;

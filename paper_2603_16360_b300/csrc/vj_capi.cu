@@ -90,6 +90,8 @@ static void free_index(vj_index* ix) {
     ix->xbias.free_(s);
     ix->abias.free_(s);
     ix->done.free_(s);
+    ix->sort_large.free_(s);
+    ix->sort_nlarge.free_(s);
     ix->cache.free_(s);
     ix->steps.free_(s);
     ix->hyb.free_(s);

@@ -139,6 +139,8 @@ struct vj_index {
 
     // join scratch kept across calls
     DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
+    DBuf<int64_t> sort_large;  // result rows handed to the block-wide sort
+    DBuf<int> sort_nlarge;
     DBuf<int32_t> cache;      // [nq]
     DBuf<int32_t> steps;      // [nq]
     DBuf<uint8_t> hyb;        // [nq]

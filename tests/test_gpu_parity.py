@@ -225,6 +225,32 @@ def test_soft_sharing_late_seed_and_restart_match_oracle(oracle):
     ix.free()
 
 
+def test_long_rows_are_sorted_and_complete(oracle):
+    """Rows of thousands of pairs (beyond the warp sorts, and beyond the
+    shared-memory block sort) come back complete and in ascending id order."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((30000, 8)).astype(np.float32)
+    Q = np.array([np.zeros(8), np.full(8, 0.6), np.full(8, 1.2), rng.standard_normal(8)], np.float32)
+    ix = vj.vj_build(X, Q, params=vj.default_params(degree=12, knn_k=24))
+    eps = 3.0
+    off, ids, _ = oracle.nlj(X, Q, eps, 0)
+    lens = np.diff(off)
+    assert lens.max() > 16384 and ((lens > 1024) & (lens <= 16384)).any()
+    band = _band_pairs(oracle, inputs.Workload("t", X, Q, np.zeros(4, bool), 0, 12, 24, eps, 0), eps, 0)
+    ex = vj.vj_join_exact(ix, eps)
+    assert not ((_pairs(ex.offsets, ex.ids) ^ _pairs(off, ids)) - band)
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0)
+    r = vj.vj_join(ix, eps)
+    o = oracle.join(X, Q, adj, entry, eps, work_sharing=oracle.WS_SOFT, order=order, parent=parent)
+    assert not ((_pairs(r.offsets, r.ids) ^ _pairs(o.offsets, o.ids)) - band)
+    for res in (ex, r):
+        for q in range(len(Q)):
+            row = res.row(q)
+            assert np.all(np.diff(row) > 0)
+    ix.free()
+
+
 def test_tiny_sets_and_empty_results(oracle):
     rng = np.random.default_rng(8)
     X = rng.standard_normal((5, 4)).astype(np.float32)
