@@ -81,7 +81,7 @@ typedef struct {
     int64_t rechecks;          /* FP64 re-evaluations near eps or near ties */
     int64_t spill_queries;     /* queries whose visited set left shared memory */
     double ms_traverse;        /* device time of the traversal kernel */
-    double ms_csr;             /* device time of the CSR assembly */
+    double ms_csr;             /* device time of the final CSR assembly */
     double ms_total;           /* device time of the whole join */
     int64_t bytes_algorithmic; /* vector + adjacency bytes the traversal must read */
     int64_t kernel_launches;   /* kernels this call launched */
@@ -90,6 +90,8 @@ typedef struct {
     double ms_prologue;        /* device time of the learned prologue (features + predictor + plan) */
     int64_t sws_restarts;      /* soft-sharing queries re-run because the late-merged cached seed
                                   would have been the greedy front (a duplicate of the query) */
+    double ms_route;           /* device time of the routed queries' rows (scan, exact re-check and
+                                  their CSR); ms_scan is the scan kernel alone */
 } vj_stats;
 
 /* CSR result of a join.  ids are data ids (0..nx-1), ascending within each
@@ -185,6 +187,14 @@ vj_status vj_features(vj_index *ix, float eps, float *out);
  * capped at beam_cap).  The index keeps the pointer; m must outlive it or
  * be detached. */
 vj_status vj_attach_predictor(vj_index *ix, vj_mlp *m, float route_threshold, int beam_cap);
+
+/* Outputs [nq][2] (host) of the attached predictor on the features at eps,
+ * computed exactly as the learned prologue of a join computes them (on the
+ * tensor cores with BF16 inputs and weights when h1 is a multiple of 64 and
+ * h2 a multiple of 16, both at most 256; FP32 otherwise).  No paper
+ * counterpart (the paper has only the d1/d2 rule, Sec. 4.4).  VJ_ERR_STATE
+ * when no predictor is attached. */
+vj_status vj_predictor_outputs(vj_index *ix, float eps, float *out);
 
 /* Approximate join (Alg. 1 on the merged index) at threshold eps > 0.
  * budget > 0 overrides hybrid_beam for this call.  The result lives in host

@@ -193,6 +193,24 @@ extern "C" vj_status vj_features(vj_index* ix, float eps, float* out) {
     }
 }
 
+extern "C" vj_status vj_predictor_outputs(vj_index* ix, float eps, float* out) {
+    try {
+        VJ_REQUIRE(ix != nullptr && out != nullptr && eps > 0.f, VJ_ERR_ARG, "bad argument");
+        VJ_REQUIRE(ix->predictor != nullptr, VJ_ERR_STATE, "no predictor attached");
+        cudaStream_t s = ix->stream;
+        const int64_t nq = ix->nq;
+        ix->feat.ensure((size_t)nq * (VJ_NFEAT + ix->d), s);
+        ix->pred_y.ensure((size_t)nq * 2, s);
+        vj_compute_features(ix, eps, ix->feat.p);
+        vj_mlp_forward_device(ix->predictor, ix->feat.p, nq, ix->pred_y.p, s);
+        VJ_CUDA(cudaMemcpyAsync(out, ix->pred_y.p, (size_t)nq * 2 * sizeof(float), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        return VJ_OK;
+    } catch (const VjError& e) {
+        return e.code;
+    }
+}
+
 extern "C" vj_status vj_attach_predictor(vj_index* ix, vj_mlp* m, float route_threshold, int beam_cap) {
     try {
         VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");

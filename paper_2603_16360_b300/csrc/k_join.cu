@@ -1125,14 +1125,15 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
 
     // ---- brute-force route: rows of the routed queries from the tensor-core
     // scan, appended to the pool behind the traversal's pairs
-    double ms_scan = 0.0;
+    double ms_scan = 0.0, ms_route = 0.0;
     int64_t scand = 0;
     if (ix->has_route && ix->nrouted > 0) {
         DBuf<int64_t> soff;
         DBuf<int32_t> sid;
         DBuf<float> sd;
         int64_t snnz = 0;
-        vj_scan_rows_csr(ix, ix->routed.p, ix->nrouted, eps, soff, sid, sd, &snnz, &ms_scan);
+        vj_scan_rows_csr(ix, ix->routed.p, ix->nrouted, eps, soff, sid, sd, &snnz, &ms_route);
+        ms_scan = ix->last_scan_ms;
         scand = ix->last_scan_cand;
         launches += 8;
         if (nnz + snnz > (int64_t)ix->pool_id.n) {
@@ -1188,7 +1189,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     st->rechecks = (int64_t)hc[C_RECHK];
     st->spill_queries = (int64_t)hc[C_SPILL];
     st->ms_traverse = t_trav;
-    st->ms_csr = t_csr;
+    st->ms_csr = std::max(0.0, (double)t_csr - ms_route);
+    st->ms_route = ms_route;
     st->ms_prologue = ms_pro;
     st->sws_restarts = (int64_t)hc[C_RESTART];
     st->ms_total = ms_pro + t_trav + t_csr;

@@ -16,6 +16,7 @@
 
 #include "vj_device.cuh"
 #include "vj_internal.cuh"
+#include "vj_tc.cuh"
 
 struct vj_mlp {
     int din = 0, h1 = 0, h2 = 0;
@@ -30,6 +31,9 @@ struct vj_mlp {
     DBuf<float> tr, tc;
     DBuf<double> loss;
     int64_t cap = 0;
+    // BF16 operands of the tensor-core inference path
+    DBuf<__nv_bfloat16> xbf, w1bf, w2bf;
+    DBuf<int> err;
 };
 
 namespace {
@@ -242,10 +246,330 @@ void init_params(vj_mlp* m, uint64_t seed) {
     VJ_CUDA(cudaStreamSynchronize(m->stream));
 }
 
+
+// ---------------------------------------------------------------- tensor-core inference
+// Fused forward of 128 rows per CTA on the 5th-generation tensor cores:
+//   D1 = X W1^T           (TMEM columns 0..h1)     X, W1 streamed by TMA
+//   A2 = relu(D1 + b1)    BF16 into shared memory (128-byte swizzled K-major)
+//   D2 = A2 W2^T          (TMEM columns 256..)     W2 streamed by TMA
+//   y  = W3 relu(D2 + b2) + b3                     FP32 in the epilogue
+// Warp 0 issues TMA, warp 1 allocates TMEM and issues tcgen05.mma, warps 2..5
+// (one per TMEM lane quarter, one row per thread) run both epilogues.  Inputs
+// are the standardised features and weights rounded to BF16 (FP32 accumulate).
+using namespace vjtc;
+
+constexpr int ML_EPI = 4;
+constexpr int ML_THREADS = (2 + ML_EPI) * 32;
+constexpr int ML_STAGES = 3;
+constexpr uint32_t ML_ABOX = 128 * 64 * 2;   // 128 rows x 64 BF16
+constexpr uint32_t ML_WBOX = 256 * 64 * 2;   // up to 256 rows x 64 BF16
+constexpr uint32_t ML_STAGE = ML_ABOX + ML_WBOX;
+
+struct MlBars {
+    uint64_t full[ML_STAGES];
+    uint64_t empty[ML_STAGES];
+    uint64_t d1full, a2full, d2full, drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+struct MlParams {
+    int64_t n;
+    int nk1;     // layer-1 k-blocks of 64
+    int h1, h2;  // h1: multiple of 64 up to 256; h2: multiple of 16 up to 256
+    const float* b1;
+    const float* b2;
+    const float* w3;
+    const float* b3;
+    float* y;
+    int* err;
+    long long spin_limit;
+};
+
+__host__ __device__ constexpr uint32_t ml_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(ML_THREADS, 1)
+    k_mlp_fwd_tc(const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tW1,
+                 const __grid_constant__ CUtensorMap tW2, MlParams P) {
+    extern __shared__ uint8_t ml_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ml_raw) + 1023) & ~uintptr_t(1023));
+    MlBars& B = *reinterpret_cast<MlBars*>(base);
+    uint8_t* ring = base + 1024;
+    uint8_t* sA2 = ring + ML_STAGES * ML_STAGE;            // [h1 / 64] boxes of 128 x 64
+    float* sb1 = reinterpret_cast<float*>(sA2 + (P.h1 / 64) * ML_ABOX);
+    float* sb2 = sb1 + 256;
+    float* sw3 = sb2 + 256;                                // [2][256]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* abort = &B.abort;
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const int nk2 = P.h1 / 64;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ML_STAGES; s++) {
+            mbar_init(&B.full[s], 1);
+            mbar_init(&B.empty[s], 1);
+        }
+        mbar_init(&B.d1full, 1);
+        mbar_init(&B.a2full, 1);
+        mbar_init(&B.d2full, 1);
+        mbar_init(&B.drain, 1);
+        B.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&B.tmem_base)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = B.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0, issued = 0, last_ph = 0;
+            bool ok = true;
+            const uint32_t w1b = (uint32_t)P.h1 * 128u, w2b = (uint32_t)P.h2 * 128u;
+            for (int kb = 0; kb < P.nk1 + nk2 && ok; kb++) {
+                if (!mbar_wait(&B.empty[s], ph ^ 1u, abort, P.spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = ring + s * ML_STAGE;
+                if (kb < P.nk1) {
+                    mbar_arrive_tx(&B.full[s], ML_ABOX + w1b);
+                    tma_load_2d(st, &tX, &B.full[s], kb * 64, (int)row0);
+                    tma_load_2d(st + ML_ABOX, &tW1, &B.full[s], kb * 64, 0);
+                } else {
+                    mbar_arrive_tx(&B.full[s], w2b);
+                    tma_load_2d(st + ML_ABOX, &tW2, &B.full[s], (kb - P.nk1) * 64, 0);
+                }
+                issued |= 1u << s;
+                last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                if (++s == ML_STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+                for (int st = 0; st < ML_STAGES; st++)
+                    if ((issued >> st) & 1u)
+                        for (long long i = 0; i < P.spin_limit && !mbar_test(&B.full[st], (last_ph >> st) & 1u); i++) {
+                        }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int kb = 0; kb < P.nk1 + nk2 && ok; kb++) {
+                if (kb == P.nk1) {
+                    // layer 2 reads A2, written by the epilogue warps
+                    tc_commit(&B.d1full);
+                    if (!mbar_wait(&B.a2full, 0, abort, P.spin_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                if (!mbar_wait(&B.full[s], ph, abort, P.spin_limit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint8_t* st = ring + s * ML_STAGE;
+                const bool l1 = kb < P.nk1;
+                const uint64_t ad = sdesc_sw128(su32(l1 ? st : sA2 + (kb - P.nk1) * ML_ABOX));
+                const uint64_t bd = sdesc_sw128(su32(st + ML_ABOX));
+                const uint32_t d = tmem + (l1 ? 0u : 256u);
+                const uint32_t idesc = l1 ? ml_idesc(P.h1) : ml_idesc(P.h2);
+                const int k0 = l1 ? kb : kb - P.nk1;
+#pragma unroll
+                for (int kk = 0; kk < 4; kk++)
+                    tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (uint32_t)((k0 | kk) != 0));
+                tc_commit(&B.empty[s]);
+                if (++s == ML_STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (ok) tc_commit(&B.d2full);
+            else {
+                *abort = 1;
+                atomicExch(P.err, 1);
+            }
+            tc_commit(&B.drain);
+            for (long long k = 0; k < P.spin_limit && !mbar_test(&B.drain, 0); k++) {
+            }
+        }
+    } else {
+        const int et = threadIdx.x - 64;  // 0..127
+        for (int i = et; i < 256; i += 128) {
+            sb1[i] = i < P.h1 ? P.b1[i] : 0.f;
+            sb2[i] = i < P.h2 ? P.b2[i] : 0.f;
+            sw3[i] = i < P.h2 ? P.w3[i] : 0.f;
+            sw3[256 + i] = i < P.h2 ? P.w3[P.h2 + i] : 0.f;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(ML_EPI * 32) : "memory");
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;  // row within the tile = TMEM lane
+        const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+        bool ok = mbar_wait(&B.d1full, 0, abort, P.spin_limit);
+        if (__all_sync(VJ_FULL, ok)) {
+            tc_fence_after();
+            // ---- epilogue 1: A2 = relu(D1 + b1) as BF16, 128-byte swizzled K-major
+            for (int c0 = 0; c0 < P.h1; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32_issue(tmem + lanes + (uint32_t)c0, v);
+                tmem_wait_ld(v);
+                uint32_t pk[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const float a = fmaxf(__uint_as_float(v[2 * j]) + sb1[c0 + 2 * j], 0.f);
+                    const float b = fmaxf(__uint_as_float(v[2 * j + 1]) + sb1[c0 + 2 * j + 1], 0.f);
+                    const __nv_bfloat162 h2v = __floats2bfloat162_rn(a, b);
+                    pk[j] = *reinterpret_cast<const uint32_t*>(&h2v);
+                }
+                uint8_t* line = sA2 + (c0 / 64) * ML_ABOX + r * 128;
+                const int chunk0 = ((c0 % 64) * 2) / 16;
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int phys = (chunk0 + t) ^ (r & 7);
+                    *reinterpret_cast<uint4*>(line + phys * 16) =
+                        make_uint4(pk[4 * t], pk[4 * t + 1], pk[4 * t + 2], pk[4 * t + 3]);
+                }
+            }
+            // generic-proxy stores -> visible to the tensor core's async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            asm volatile("bar.sync 1, %0;" ::"r"(ML_EPI * 32) : "memory");
+            if (threadIdx.x == 64) mbar_arrive(&B.a2full);
+            // ---- epilogue 2: y = W3 relu(D2 + b2) + b3
+            ok = mbar_wait(&B.d2full, 0, abort, P.spin_limit);
+            if (__all_sync(VJ_FULL, ok)) {
+                tc_fence_after();
+                float y0 = P.b3[0], y1 = P.b3[1];
+                for (int c0 = 0; c0 < P.h2; c0 += 16) {
+                    // 16 columns per step: reads stay inside D2's h2 columns
+                    uint32_t v[16];
+                    tmem_ld16_issue(tmem + lanes + 256u + (uint32_t)c0, v);
+                    tmem_wait_ld16(v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const float a = fmaxf(__uint_as_float(v[j]) + sb2[c0 + j], 0.f);
+                        y0 = fmaf(a, sw3[c0 + j], y0);
+                        y1 = fmaf(a, sw3[256 + c0 + j], y1);
+                    }
+                }
+                const int64_t gr = row0 + r;
+                if (gr < P.n) {
+                    P.y[2 * gr] = y0;
+                    P.y[2 * gr + 1] = y1;
+                }
+            } else if (lane == 0) {
+                *abort = 1;
+                atomicExch(P.err, 1);
+            }
+        } else if (lane == 0) {
+            *abort = 1;
+            atomicExch(P.err, 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// standardised features -> BF16 rows of k1 columns (zero padded)
+__global__ void k_feat_bf16(const float* __restrict__ x, int64_t n, int din, int k1, const float* __restrict__ mu,
+                            const float* __restrict__ sd, __nv_bfloat16* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * k1) return;
+    const int64_t r = i / k1;
+    const int f = (int)(i % k1);
+    float v = 0.f;
+    if (f < din) {
+        v = x[r * din + f];
+        if (mu) v = (v - mu[f]) / sd[f];
+    }
+    out[i] = __float2bfloat16_rn(v);
+}
+
+// rows x cols FP32 -> rows x kp BF16 (zero padded)
+__global__ void k_mat_bf16(const float* __restrict__ w, int rows, int cols, int kp, __nv_bfloat16* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * kp) return;
+    const int r = (int)(i / kp), c = (int)(i % kp);
+    out[i] = __float2bfloat16_rn(c < cols ? w[(int64_t)r * cols + c] : 0.f);
+}
+
+bool tc_shape_ok(const vj_mlp* m) {
+    return m->h1 % 64 == 0 && m->h1 >= 64 && m->h1 <= 256 && m->h2 % 16 == 0 && m->h2 >= 16 && m->h2 <= 256;
+}
+
+// tensor-core forward of n standardised-on-the-fly rows (x: n x din FP32)
+void forward_tc(vj_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s) {
+    const Off o = offsets(m);
+    const int k1 = (m->din + 63) / 64 * 64;
+    m->xbf.ensure((size_t)std::max<int64_t>(n, 1) * k1, s);
+    m->w1bf.ensure((size_t)m->h1 * k1, s);
+    m->w2bf.ensure((size_t)m->h2 * m->h1, s);
+    m->err.ensure(1, s);
+    k_feat_bf16<<<vj_div_up(n * k1, 256), 256, 0, s>>>(x, n, m->din, k1, m->has_norm ? m->mu.p : nullptr, m->sd.p,
+                                                       m->xbf.p);
+    VJ_LAUNCH_CHECK();
+    k_mat_bf16<<<vj_div_up((int64_t)m->h1 * k1, 256), 256, 0, s>>>(m->w.p + o.w1, m->h1, m->din, k1, m->w1bf.p);
+    VJ_LAUNCH_CHECK();
+    k_mat_bf16<<<vj_div_up((int64_t)m->h2 * m->h1, 256), 256, 0, s>>>(m->w.p + o.w2, m->h2, m->h1, m->h1, m->w2bf.p);
+    VJ_LAUNCH_CHECK();
+    const CUtensorMap tX = make_map(m->xbf.p, n, k1, 128);
+    const CUtensorMap tW1 = make_map(m->w1bf.p, m->h1, k1, m->h1);
+    const CUtensorMap tW2 = make_map(m->w2bf.p, m->h2, m->h1, m->h2);
+    MlParams P;
+    P.n = n;
+    P.nk1 = k1 / 64;
+    P.h1 = m->h1;
+    P.h2 = m->h2;
+    P.b1 = m->w.p + o.b1;
+    P.b2 = m->w.p + o.b2;
+    P.w3 = m->w.p + o.w3;
+    P.b3 = m->w.p + o.b3;
+    P.y = y;
+    P.err = m->err.p;
+    P.spin_limit = 1ll << 22;
+    const size_t smem = 2048 + (size_t)ML_STAGES * ML_STAGE + (size_t)(m->h1 / 64) * ML_ABOX + 4 * 256 * sizeof(float);
+    VJ_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VJ_CUDA(cudaMemsetAsync(m->err.p, 0, sizeof(int), s));
+    k_mlp_fwd_tc<<<(unsigned)vj_div_up(n, 128), ML_THREADS, smem, s>>>(tX, tW1, tW2, P);
+    VJ_LAUNCH_CHECK();
+    int herr = 0;
+    VJ_CUDA(cudaMemcpyAsync(&herr, m->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "predictor forward: a pipeline wait timed out");
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ internal API
+// the join prologue's forward: BF16 tensor cores when the widths allow
+// (h1 multiple of 64, h2 multiple of 16, both <= 256), else FP32
 void vj_mlp_forward_device(vj_mlp* m, const float* x, int64_t n, float* y_out, cudaStream_t s) {
+    if (n <= 0) return;
+    if (tc_shape_ok(m)) {
+        forward_tc(m, x, n, y_out, s);
+        return;
+    }
     cudaStream_t keep = m->stream;
     m->stream = s;
     forward(m, x, n, true);
@@ -447,6 +771,10 @@ extern "C" vj_status vj_mlp_predict(vj_mlp* m, const float* x, int64_t n, float*
 extern "C" void vj_mlp_free(vj_mlp* m) {
     if (!m) return;
     cudaStream_t s = m->stream;
+    m->xbf.free_(s);
+    m->w1bf.free_(s);
+    m->w2bf.free_(s);
+    m->err.free_(s);
     for (auto* b : {&m->w, &m->m, &m->v, &m->g, &m->mu, &m->sd, &m->xb, &m->z1, &m->a1, &m->z2, &m->a2, &m->y, &m->dy,
                     &m->da2, &m->da1, &m->tr, &m->tc})
         b->free_(s);

@@ -23,6 +23,7 @@ VJ_PREC_FP32, VJ_PREC_BF16, VJ_PREC_FP8 = 0, 1, 2
 # every function declared in include/vj.h
 EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_set_params", "vj_mlp_loss_grad",
            "vj_mlp_train", "vj_mlp_predict", "vj_mlp_free", "vj_features", "vj_attach_predictor",
+           "vj_predictor_outputs",
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_result_free", "vj_free", "vj_last_error"]
@@ -53,7 +54,7 @@ class vj_stats(C.Structure):
                 ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
                 ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
                 ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double),
-                ("sws_restarts", C.c_int64)]
+                ("sws_restarts", C.c_int64), ("ms_route", C.c_double)]
 
 
 class vj_result(C.Structure):
@@ -105,6 +106,8 @@ def load():
     lib.vj_features.restype = I
     lib.vj_attach_predictor.argtypes = [P, P, C.c_float, I]
     lib.vj_attach_predictor.restype = I
+    lib.vj_predictor_outputs.argtypes = [P, C.c_float, P]
+    lib.vj_predictor_outputs.restype = I
     for fn in ("vj_join", "vj_join_device"):
         getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
         getattr(lib, fn).restype = I
@@ -348,6 +351,13 @@ def vj_features(ix: Index, eps: float):
 def vj_attach_predictor(ix: Index, mlp, route_threshold: float = 0.5, beam_cap: int = 256):
     _check(load().vj_attach_predictor(ix.handle, None if mlp is None else mlp.handle, float(route_threshold),
                                       int(beam_cap)))
+
+
+def vj_predictor_outputs(ix: Index, eps: float) -> np.ndarray:
+    """Outputs [nq, 2] of the attached predictor as the learned prologue computes them."""
+    out = np.empty((ix.info()["nq"], 2), np.float32)
+    _check(load().vj_predictor_outputs(ix.handle, float(eps), out.ctypes.data))
+    return out
 
 
 def vj_set_plan(ix: Index, route=None, beam=None):

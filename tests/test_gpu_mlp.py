@@ -9,6 +9,14 @@ from paper_2603_16360_b300 import vj
 pytestmark = pytest.mark.gpu
 
 
+def _bf16(a):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
     import torch
@@ -112,6 +120,49 @@ def test_learned_join_reduces_to_route_all_and_bfs():
             b = vj.vj_join(ix, eps)
             assert np.array_equal(r.offsets, b.offsets) and np.array_equal(r.ids, b.ids)
             assert np.array_equal(r.steps, b.steps)
+    vj.vj_attach_predictor(ix, None, 0.5, 64)
+    ix.free()
+    m.free()
+
+
+@pytest.mark.parametrize("h1,h2", [(256, 256), (64, 48), (16, 16)])
+def test_prologue_forward_matches_fp64_oracle(oracle, h1, h2):
+    """The join prologue's predictor forward (BF16 tensor cores for h1 % 64 ==
+    0 and h2 % 16 == 0, FP32 otherwise) against the FP64 MLP oracle on the
+    same features.  BF16 rounds inputs and weights to 2^-8 relative; with FP32
+    accumulation the outputs stay within a few 2^-8 of the layer scales."""
+    from oracle import mlp as omlp
+    w = inputs.gauss_small(seed=33, nx=3000, nq=700, d=32, k=8, ood_frac=0.1, shift=8.0)
+    ix = vj.vj_build(w.X, w.Q, params=vj.default_params(degree=16, knn_k=32))
+    eps = 2.5
+    F = vj.vj_features(ix, eps)
+    din = F.shape[1]
+    m = vj.MLP(din, h1, h2, seed=7)
+    rng = np.random.default_rng(5)
+    flat, _, _ = m.get_params()
+    flat = flat + (rng.standard_normal(flat.size) * 0.02).astype(np.float32)  # non-zero biases
+    mu = F.mean(0).astype(np.float32)
+    sd = (F.std(0) + 1e-3).astype(np.float32)
+    m.set_params(flat, mu, sd)
+    vj.vj_attach_predictor(ix, m, 0.5, 64)
+    y = vj.vj_predictor_outputs(ix, eps)
+    xs = (F.astype(np.float32) - mu) / sd
+    yref, _ = omlp.forward(flat.astype(np.float64), xs.astype(np.float64), din, h1, h2)
+    scale = np.abs(yref).mean(0) + 1e-3
+    if h1 % 64 == 0 and h2 % 16 == 0:
+        # the same network with BF16-rounded inputs, weights and layer-1
+        # activations (the tensor-core operands), evaluated in FP64: only the
+        # FP32 accumulation order separates it from the GPU
+        W1, b1, W2, b2, W3, b3 = omlp.unpack(flat, din, h1, h2)
+        a1 = np.maximum(_bf16(xs) @ _bf16(W1).T + b1, 0.0)
+        a2 = np.maximum(_bf16(a1) @ _bf16(W2).T + b2, 0.0)
+        ybf = a2 @ W3.T + b3
+        assert (np.abs(y - ybf) / scale).max() < 1e-3
+        # and BF16 rounding itself stays within a few 2^-8 of the FP64 network
+        assert (np.abs(y - yref) / scale).max() < 0.1
+    else:
+        assert (np.abs(y - yref) / scale).max() < 1e-4
+    np.testing.assert_array_equal(y, vj.vj_predictor_outputs(ix, eps))  # deterministic
     vj.vj_attach_predictor(ix, None, 0.5, 64)
     ix.free()
     m.free()
