@@ -88,8 +88,8 @@ typedef struct {
     double ms_scan;            /* device time of the tensor-core brute-force scan (exact join / routed queries) */
     int64_t scan_candidates;   /* pairs the scan passed to the exact re-check */
     double ms_prologue;        /* device time of the learned prologue (features + predictor + plan) */
-    int64_t sws_restarts;      /* soft-sharing queries re-run because the late-merged cached seed
-                                  would have been the greedy front (a duplicate of the query) */
+    int64_t sws_restarts;      /* soft-sharing queries re-run in the parent-ordered second pass
+                                  (hybrid queries, and queries whose result the cached seed changes) */
     double ms_route;           /* device time of the routed queries' rows (scan, exact re-check and
                                   their CSR); ms_scan is the scan kernel alone */
 } vj_stats;

@@ -26,21 +26,22 @@
 //   UpdateCache (8)    C[q] = closest visited data node, ties by id, FP64
 //                      re-decided among FP32 near-ties.
 //
-// Work sharing (soft): queries are taken in MST BFS order, so a parent is
-// always claimed before its children.  A query does not wait for its parent
-// before starting: its probe, CheckHybrid and (BFS) closure do not depend on
-// the cached seed C[parent] except through set membership, so the warp runs
-// them on the other seeds and merges C[parent] when the parent publishes it
-// (release store of its done flag, bounded acquire spin):
-//   - if C[parent] would have become the greedy front (key 0, a duplicate of
-//     q) the probe would not have run: the query restarts with the seed;
-//   - else if C[parent] is already visited nothing changes (V, I and the
-//     closure are sets; the seed would have been evaluated once either way);
-//   - otherwise it is evaluated and added to V; if it is in range it joins I
-//     and the closure continues from it (the closure of a union is the union
-//     of the closures over the same visited set);
-//   - a hybrid or routed query merges it before its expansion (Q0 = I and V
-//     are sets at that point, the pop order is decided afterwards).
+// Work sharing (soft) runs in two launches over the queries in MST BFS order
+// (parents before children):
+//   pass 1  every query runs on the seeds {entry, q} without waiting for its
+//           parent; a hybrid query (OOD, forced or planned) only records that
+//           it needs the cached seed before its expansion;
+//   pass 2  each query waits (bounded acquire spin) for its parent's final
+//           cache C[parent] and decides from pass 1's sets what that seed
+//           changes.  V, I and the BFS closure are sets, and V is
+//           {entry, q} U N(q) U (data neighbours of every result), so:
+//             - C[parent] in V: nothing changes;
+//             - C[parent] new and out of range: one more visited node, the
+//               cache becomes the (dist, id) minimum of the two (FP64);
+//             - C[parent] new and in range, a duplicate of q that would have
+//               been the greedy front, or a hybrid query: the query re-runs
+//               with the seed from the start.
+//           It then publishes C[q] (release store of its done flag).
 // The result, visited count and cache equal those of the wait-first order.
 //
 // Visited set: open-addressing hash in shared memory (HCAP slots), moved on
@@ -81,8 +82,9 @@ enum {
     C_RECHK = 7,
     C_SPILL = 8,
     C_ABORT = 9,
-    C_RESTART = 10,
-    C_NUM = 11
+    C_RESTART = 10,  // pass-2 re-runs
+    C_TICKET2 = 11,  // pass-2 tickets
+    C_NUM = 12
 };
 
 struct JoinParams {
@@ -91,7 +93,10 @@ struct JoinParams {
     const int32_t* adj;
     const float* elen;
     const int32_t* parent;
-    int* done;             // per-query publish flag (soft sharing)
+    int* done;             // per-query publish flag (soft sharing, pass 2)
+    uint8_t* qflag;        // per-query pass-1 record (soft sharing): QF_* bits
+    float* ckey;           // per-query FP32 key of the cache C[q] (soft sharing, pass 1)
+    int mode;              // 0: no soft sharing, 1 / 2: soft-sharing pass 1 / 2
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
     const int* order;      // dispatch order (MST BFS order: parents first)
@@ -119,6 +124,27 @@ struct JoinParams {
     unsigned long long* ctr;
     long long spin_limit;
 };
+
+enum { QF_PROBED = 1, QF_DEFER = 2 };
+
+// does the adjacency row (R ids) contain v?  All loads issued before any test.
+__device__ __forceinline__ bool row_has(const int32_t* __restrict__ row, int R, int v) {
+    bool f = false;
+    if ((R & 3) == 0) {
+        const int4* r4 = reinterpret_cast<const int4*>(row);
+        int4 x[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+            if (c < R / 4) x[c] = __ldg(r4 + c);
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+            if (c < R / 4) f |= (x[c].x == v) | (x[c].y == v) | (x[c].z == v) | (x[c].w == v);
+    } else {
+#pragma unroll 8
+        for (int j = 0; j < R; j++) f |= __ldg(row + j) == v;
+    }
+    return f;
+}
 
 __device__ __forceinline__ float key_band_scale(const JoinParams& P) { return P.metric == 0 ? P.eps_key : 1.0f; }
 
@@ -357,23 +383,22 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
 
     for (;;) {
         int t = 0;
-        if (lane == 0) t = (int)atomicAdd(P.ctr + C_TICKET, 1ull);
+        if (lane == 0) t = (int)atomicAdd(P.ctr + (P.mode == 2 ? C_TICKET2 : C_TICKET), 1ull);
         t = __shfl_sync(VJ_FULL, t, 0);
         if (t >= P.nq) break;
         const int qi = P.order[t];
         const int64_t qn = P.nx + qi;
-        // soft sharing: the parent's cache is a seed (none for children of the entry)
-        const int par = P.ws == VJ_WS_SOFT ? __ldg(P.parent + qi) : -1;
 
         float4 q[NPL];
         load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
         const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
 
-        // C[parent] once the parent has published it; -2 on abort or timeout
-        int scv = -1;
-        auto wait_parent = [&]() -> int {
+        // ---- soft sharing, pass 2: what does C[parent] change?
+        int seedc = -1;
+        if (P.mode == 2) {
+            const int par = __ldg(P.parent + qi);
             int sc = -1;
-            if (lane == 0) {
+            if (par >= 0 && lane == 0) {
                 long long spins = 0;
                 unsigned ns = 32;
                 for (;;) {
@@ -394,26 +419,80 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     if (ns < 512) ns <<= 1;
                 }
             }
-            scv = __shfl_sync(VJ_FULL, sc, 0);
-            return scv;
-        };
-
-        const long long k_exp = c_exp, k_adj = c_adj, k_hyb = c_hyb, k_rechk = c_rechk, k_spill = c_spill;
-        bool quit = false;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {
-        // pass 0 runs without C[parent] and merges it late; pass 1 (rare)
-        // restarts with it as a seed from the beginning
-        int seedc = -1;
-        bool pending = par >= 0;
-        if (pass == 1) {
-            seedc = scv;
-            pending = false;
-            c_exp = k_exp;
-            c_adj = k_adj;
-            c_hyb = k_hyb;
-            c_rechk = k_rechk;
-            c_spill = k_spill;
+            sc = __shfl_sync(VJ_FULL, sc, 0);
+            if (sc == -2) break;
+            const int flags = P.qflag[qi];
+            bool rerun = (flags & QF_DEFER) != 0;
+            bool bump = false;  // one more visited node; the cache may move to sc
+            if (!rerun && sc >= 0 && sc != P.entry) {
+                if (lane == 0) S->cand[0] = sc;
+                __syncwarp();
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
+                __syncwarp();
+                const float k = S->ckey[0];
+                __syncwarp();
+                if ((flags & QF_PROBED) && k <= 0.f) {
+                    rerun = true;  // sc would have been the greedy front: no probe
+                } else {
+                    // sc in pass 1's V?  {entry, q} U N(q) (probed) U N(results) (BFS);
+                    // one result per lane, its whole adjacency row loaded at once
+                    bool seen = false;
+                    if (flags & QF_PROBED) seen = lane < R && __ldg(P.adj + qn * R + lane) == sc;
+                    const int64_t sg = P.seg[qi];
+                    const int cnt = P.count[qi];
+                    // (an overflowed pool is re-run by the host: nothing to read then)
+                    if (P.hyb[qi] == 0 && sg + cnt <= P.pool_cap) {
+                        for (int base = 0; base < cnt && !__any_sync(VJ_FULL, seen); base += 32) {
+                            const int u = base + lane < cnt ? P.pool_id[sg + base + lane] : -1;
+                            if (u == sc) seen = true;
+                            if (u >= 0) seen |= row_has(P.adj + (int64_t)u * R, R, sc);
+                        }
+                    }
+                    if (!__any_sync(VJ_FULL, seen)) {
+                        const bool in = inrange_decide(P, lane == 0, k, sc, qn, lane, c_rechk);
+                        if (__shfl_sync(VJ_FULL, in, 0) && P.hyb[qi] != 2) rerun = true;  // the closure grows
+                        else bump = true;
+                    }
+                }
+            }
+            if (!rerun) {
+                int best = P.cache[qi];
+                if (bump) {
+                    // C[q] = the (dist, id) minimum of pass 1's cache and sc: by
+                    // their FP32 keys when those differ by more than the rounding
+                    // bound, else in FP64
+                    if (best < 0) {
+                        best = sc;
+                    } else {
+                        const float kb = P.ckey[qi];
+                        const float k = S->ckey[0];
+                        // kb is the window's smallest key; the cache itself lies
+                        // within tie_tol above it, hence the wider upper margin
+                        const bool far = P.metric == 0
+                                             ? (k > kb * (1.0f + 2.5f * P.tie_tol) || kb > k * (1.0f + P.tie_tol))
+                                             : (k > kb + 2.5f * P.tie_tol || kb > k + P.tie_tol);
+                        if (far) {
+                            if (k < kb) best = sc;
+                        } else {
+                            const double da = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, best, lane);
+                            const double db = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, sc, lane);
+                            if (db < da || (db == da && sc < best)) best = sc;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (bump) {
+                        P.cache[qi] = best;
+                        P.steps[qi] += 1;
+                        c_dist += 1;
+                    }
+                    st_release(P.done + qi, 1);
+                }
+                __syncwarp();
+                continue;
+            }
+            // re-run from the start with the cached seed
+            seedc = sc;
             if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
         }
 
@@ -437,32 +516,6 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         for (int i = lane; i < HCAP; i += 32) S->htab[i] = -1;
         __syncwarp();
         bool failed = false;
-        bool restart = false;
-        // merge C[parent] = sc into V (and I when in range) after the probe:
-        // 0 merged or nothing to do, 1 restart needed, 2 failed
-        auto merge_seed = [&](int sc, bool probed) -> int {
-            if (sc < 0) return sc == -2 ? 2 : 0;
-            if (lane == 0) S->cand[0] = sc;
-            __syncwarp();
-            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
-            __syncwarp();
-            const float k = S->ckey[0];
-            __syncwarp();
-            // with key 0 the seed would have been the greedy front and the
-            // probe would not have run (whether or not the probe reached it)
-            if (probed && k <= 0.f) return 1;
-            if (!vis_reserve(P, s, 1, W, lane, c_spill)) return 2;
-            int ins = 0;
-            if (lane == 0) ins = hash_insert(s.tab, s.mask, sc);
-            ins = __shfl_sync(VJ_FULL, ins, 0);
-            if (ins != 1) return 0;
-            s.nvis += 1;
-            const bool val = lane == 0;
-            const bool in = inrange_decide(P, val, k, sc, qn, lane, c_rechk);
-            best_update(P, s, val, k, sc, lane);
-            if (!append_results(P, s, in, sc, k, W, lane)) return 2;
-            return 0;
-        };
 
         // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
         int sid = -1;
@@ -668,12 +721,16 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
             hyb = ood;
         }
-        // a hybrid or routed query takes C[parent] before its expansion
-        if (pending && !failed && (routed || hyb)) {
-            const int r = merge_seed(wait_parent(), probe);
-            pending = false;
-            if (r == 1) restart = true;
-            if (r == 2) failed = true;
+        if (P.mode == 1 && !failed && !routed && hyb) {
+            // a hybrid expansion needs the cached seed first: pass 2 runs it
+            if (lane == 0) {
+                P.qflag[qi] = (uint8_t)(QF_DEFER | (probe ? QF_PROBED : 0));
+                P.hyb[qi] = 1;
+                P.count[qi] = 0;
+                P.steps[qi] = 0;
+            }
+            __syncwarp();
+            continue;
         }
         int expansions = 0;
         if (routed) {
@@ -682,11 +739,9 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
 
         // ---- Alg. 7 ExpansionPhase
-        if (routed || restart) {
+        if (routed) {
         } else if (!failed && !hyb) {
             int fp = 0;
-#pragma unroll 1
-            for (;;) {
             while (fp < s.nres) {
                 const int nb = min(FB, s.nres - fp);
                 if (!vis_reserve(P, s, nb * R, W, lane, c_spill)) {
@@ -732,16 +787,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 __syncwarp();
                 if (failed) break;
             }
-            // closure done on the other seeds: merge C[parent]; an in-range
-            // seed extends the closure from where it stopped
-            if (failed || !pending) break;
-            const int r = merge_seed(wait_parent(), probe);
-            pending = false;
-            if (r == 1) restart = true;
-            if (r == 2) failed = true;
-            if (failed || restart) break;
-            }
-        } else if (!failed && !restart && hyb) {
+        } else if (!failed && hyb) {
             if (lane == 0) c_hyb++;
             int npend = s.nres;  // in-range entries not yet popped (rid >= 0)
             int osz = 0, oqh = 0, cur = 0;
@@ -855,7 +901,6 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
         }
         c_exp += expansions;
-        if (restart) continue;
 
         // ---- Alg. 8 UpdateCache: FP64 re-decision among near-ties
         int best = (s.bid == INT32_MAX) ? -1 : s.bid;
@@ -875,16 +920,21 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
 
         if (lane == 0) {
+            // a pass-2 re-run replaces pass 1's count of this query
+            if (P.mode == 2 && !(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
             P.cache[qi] = best;
             P.steps[qi] = s.nvis;
             P.hyb[qi] = (uint8_t)hyb;
             c_dist += s.nvis;
+            if (P.mode == 1) {
+                P.qflag[qi] = (uint8_t)(probe ? QF_PROBED : 0);
+                P.ckey[qi] = s.bk;
+            }
             // publish: cache[qi] is visible to whoever sees the flag
-            if (P.ws == VJ_WS_SOFT && !failed) st_release(P.done + qi, 1);
+            if (P.mode == 2 && !failed) st_release(P.done + qi, 1);
         }
         if (failed) {
             if (lane == 0) P.count[qi] = 0;
-            quit = true;
             break;
         }
 
@@ -904,9 +954,6 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
         }
         __syncwarp();
-        break;
-        }  // pass
-        if (quit) break;
     }
     if (lane == 0) {
         atomicAdd(P.ctr + C_DIST, (unsigned long long)c_dist);
@@ -1011,6 +1058,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     ix->count.ensure(nq, s);
     ix->seg.ensure(nq, s);
     ix->done.ensure(nq, s);
+    ix->qflag.ensure(nq, s);
+    ix->ckey.ensure(nq, s);
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
@@ -1043,6 +1092,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.elen = ix->elen.p;
     P.parent = ix->parent.p;
     P.done = ix->done.p;
+    P.qflag = ix->qflag.p;
+    P.ckey = ix->ckey.p;
     P.order = ix->order.p;
     P.route = ix->has_route ? ix->plan_route.p : nullptr;
     P.qbeam = ix->has_beam ? ix->plan_beam.p : nullptr;
@@ -1093,7 +1144,17 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         VJ_CUDA(cudaMemsetAsync(ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
         if (soft) VJ_CUDA(cudaMemsetAsync(ix->done.p, 0, nq * sizeof(int32_t), s));
         VJ_CUDA(cudaEventRecord(e0, s));
-        jd.launch(P, jd.blocks, s);
+        if (soft) {
+            // two launches: speculative pass, then the parent-ordered fix-up
+            P.mode = 1;
+            jd.launch(P, jd.blocks, s);
+            P.mode = 2;
+            jd.launch(P, jd.blocks, s);
+            launches++;
+        } else {
+            P.mode = 0;
+            jd.launch(P, jd.blocks, s);
+        }
         VJ_CUDA(cudaEventRecord(e1, s));
         VJ_CUDA(cudaMemcpyAsync(hc, ix->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
         VJ_CUDA(cudaStreamSynchronize(s));
@@ -1174,7 +1235,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     vj_segment_sort_copy(ix->seg.p, ix->count.p, ix->offsets.p, ix->pool_id.p, ix->pool_d.p, ix->out_id.p,
                          ix->out_d.p, nq, ix);
     VJ_CUDA(cudaEventRecord(e2, s));
+    // pairs in the result (the pool also holds rows that a pass-2 re-run replaced)
+    VJ_CUDA(cudaMemcpyAsync(&nnz, ix->offsets.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaEventSynchronize(e2));
+    VJ_CUDA(cudaStreamSynchronize(s));
     float t_trav = 0.f, t_csr = 0.f;
     VJ_CUDA(cudaEventElapsedTime(&t_trav, e0, e1));
     VJ_CUDA(cudaEventElapsedTime(&t_csr, e1, e2));

@@ -604,7 +604,10 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     const float eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
     // candidates from the BF16 tensor-core scan (a bounded superset of the
     // result), then the exact FP32 / FP64 re-decision below
-    DBuf<int32_t> cq, cx;
+    // candidate arrays stay with the index: later scans start at the size the
+    // largest earlier one needed instead of re-running the scan to grow them
+    DBuf<int32_t>& cq = ix->scan_cq;
+    DBuf<int32_t>& cx = ix->scan_cx;
     DBuf<float> cd;
     DBuf<unsigned long long> ctr;
     ctr.alloc(2, s);
@@ -654,8 +657,6 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     td.free_(s);
     counts.free_(s);
     cursor.free_(s);
-    cq.free_(s);
-    cx.free_(s);
     cd.free_(s);
     ctr.free_(s);
 }

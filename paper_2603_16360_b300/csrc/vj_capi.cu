@@ -90,6 +90,10 @@ static void free_index(vj_index* ix) {
     ix->xbias.free_(s);
     ix->abias.free_(s);
     ix->done.free_(s);
+    ix->qflag.free_(s);
+    ix->ckey.free_(s);
+    ix->scan_cq.free_(s);
+    ix->scan_cx.free_(s);
     ix->sort_large.free_(s);
     ix->sort_nlarge.free_(s);
     ix->cache.free_(s);

@@ -158,6 +158,10 @@ class Result:
     def row(self, q):
         return self.ids[self.offsets[q]:self.offsets[q + 1]]
 
+    @property
+    def nnz(self) -> int:
+        return len(self.ids)
+
 
 def _stats(s: vj_stats) -> dict:
     return {name: getattr(s, name) for name, _ in vj_stats._fields_}

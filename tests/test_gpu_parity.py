@@ -130,6 +130,7 @@ def test_join_matches_oracle_on_gpu_graph(built, oracle, mode, kw):
     np.testing.assert_array_equal(r.hybrid, o.hybrid)
     np.testing.assert_array_equal(r.cache, o.cache)
     np.testing.assert_array_equal(r.steps, o.steps)
+    assert len(r.ids) == r.offsets[-1] == r.nnz
     # distances of common pairs
     gd = {(q, int(i)): r.dists[r.offsets[q] + j] for q in range(w.nq) for j, i in enumerate(r.row(q))}
     od = {(q, int(i)): o.dists[o.offsets[q] + j] for q in range(w.nq) for j, i in enumerate(o.row(q))}
