@@ -99,7 +99,8 @@ struct JoinParams {
     int mode;              // 0: no soft sharing, 1 / 2: soft-sharing pass 1 / 2
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
-    const int* order;      // dispatch order (MST BFS order: parents first)
+    const int* order;      // dispatch order of pass 2 (MST BFS order: parents first)
+    const int* order1;     // dispatch order without dependencies (mode 0, pass 1)
     int64_t nx, nq;
     int dp4, dp, d, R, metric;
     int32_t entry;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         if (lane == 0) t = (int)atomicAdd(P.ctr + (P.mode == 2 ? C_TICKET2 : C_TICKET), 1ull);
         t = __shfl_sync(VJ_FULL, t, 0);
         if (t >= P.nq) break;
-        const int qi = P.order[t];
+        const int qi = P.mode == 2 ? P.order[t] : P.order1[t];
         const int64_t qn = P.nx + qi;
 
         float4 q[NPL];
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                         break;
                     }
                     __nanosleep(ns);
-                    if (ns < 512) ns <<= 1;
+                    if (ns < 256) ns <<= 1;
                 }
             }
             sc = __shfl_sync(VJ_FULL, sc, 0);
@@ -965,6 +966,44 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
     }
 }
 
+// Dispatch order for passes without dependencies: longest expected work first
+// (the previous join's visited counts, in power-of-two classes), so the long
+// queries start early and the kernel's tail is short.  Counting sort over 32
+// classes; the order within a class is arbitrary (results do not depend on it).
+constexpr int CO_CLASSES = 32;
+
+__device__ __forceinline__ int cost_class(int steps) {
+    return CO_CLASSES - 1 - min(CO_CLASSES - 1, 31 - __clz(max(steps, 0) + 1));
+}
+
+__global__ void k_cost_hist(const int32_t* __restrict__ steps, int64_t n, int* __restrict__ hist) {
+    __shared__ int h[CO_CLASSES];
+    if (threadIdx.x < CO_CLASSES) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[cost_class(steps[i])], 1);
+    __syncthreads();
+    if (threadIdx.x < CO_CLASSES && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// exclusive prefix of the class counts into cursors (one warp)
+__global__ void k_cost_prefix(int* __restrict__ hist) {
+    const int lane = threadIdx.x;
+    const int v = hist[lane];
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(VJ_FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    hist[lane] = x - v;
+}
+
+__global__ void k_cost_scatter(const int32_t* __restrict__ steps, int64_t n, int* __restrict__ cursor,
+                               int32_t* __restrict__ order) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) order[atomicAdd(&cursor[cost_class(steps[i])], 1)] = (int32_t)i;
+}
+
 // rows of routed queries: CSR rows of the scan, placed at `base` in the pool
 __global__ void k_merge_routed(const int32_t* __restrict__ routed, int64_t nr, const int64_t* __restrict__ soff,
                                int64_t base, int64_t* __restrict__ seg, int32_t* __restrict__ count) {
@@ -1095,6 +1134,20 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.qflag = ix->qflag.p;
     P.ckey = ix->ckey.p;
     P.order = ix->order.p;
+    // longest-first order from the previous join's visited counts (MST order on the first join)
+    if (ix->have_costs) {
+        ix->order1.ensure(nq, s);
+        ix->cost_hist.ensure(CO_CLASSES, s);
+        VJ_CUDA(cudaMemsetAsync(ix->cost_hist.p, 0, CO_CLASSES * sizeof(int), s));
+        k_cost_hist<<<std::min<int64_t>(vj_div_up(nq, 256), 4 * (int64_t)ix->num_sms), 256, 0, s>>>(
+            ix->steps.p, nq, ix->cost_hist.p);
+        k_cost_prefix<<<1, 32, 0, s>>>(ix->cost_hist.p);
+        k_cost_scatter<<<vj_div_up(nq, 256), 256, 0, s>>>(ix->steps.p, nq, ix->cost_hist.p, ix->order1.p);
+        VJ_LAUNCH_CHECK();
+        P.order1 = ix->order1.p;
+    } else {
+        P.order1 = ix->order.p;
+    }
     P.route = ix->has_route ? ix->plan_route.p : nullptr;
     P.qbeam = ix->has_beam ? ix->plan_beam.p : nullptr;
     P.nx = ix->nx;
@@ -1258,6 +1311,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     st->ms_prologue = ms_pro;
     st->sws_restarts = (int64_t)hc[C_RESTART];
     st->ms_total = ms_pro + t_trav + t_csr;
+    ix->have_costs = true;  // this join's visited counts order the next one
     // algorithmic bytes: one vector per distance, one adjacency row per row read
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
     st->kernel_launches = launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort

@@ -92,6 +92,8 @@ static void free_index(vj_index* ix) {
     ix->done.free_(s);
     ix->qflag.free_(s);
     ix->ckey.free_(s);
+    ix->order1.free_(s);
+    ix->cost_hist.free_(s);
     ix->scan_cq.free_(s);
     ix->scan_cx.free_(s);
     ix->sort_large.free_(s);

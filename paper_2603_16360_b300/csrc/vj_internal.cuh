@@ -141,6 +141,9 @@ struct vj_index {
     DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
     DBuf<uint8_t> qflag;      // [nq] soft sharing: what pass 1 recorded per query
     DBuf<float> ckey;         // [nq] soft sharing: FP32 key of each query's pass-1 cache
+    DBuf<int32_t> order1;     // [nq] longest-first dispatch order (from the last join's visits)
+    DBuf<int> cost_hist;
+    bool have_costs = false;
     DBuf<int32_t> scan_cq, scan_cx;  // tensor-core scan candidates (query, data id)
     DBuf<int64_t> sort_large;  // result rows handed to the block-wide sort
     DBuf<int> sort_nlarge;
