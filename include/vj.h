@@ -92,6 +92,9 @@ typedef struct {
                                   (hybrid queries, and queries whose result the cached seed changes) */
     double ms_route;           /* device time of the routed queries' rows (scan, exact re-check and
                                   their CSR); ms_scan is the scan kernel alone */
+    double ms_sws[3];          /* soft sharing: device time of the speculative pass, the parallel
+                                  decision pass and the parent-ordered commit pass (of the last
+                                  traversal attempt; the three add up to ms_traverse) */
 } vj_stats;
 
 /* CSR result of a join.  ids are data ids (0..nx-1), ascending within each

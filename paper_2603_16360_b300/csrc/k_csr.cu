@@ -83,7 +83,7 @@ __global__ void k_scan_add(int64_t* __restrict__ out, const int64_t* __restrict_
 
 // ---------------------------------------------------------------- segment sort
 constexpr int SS_WPB = 8;
-constexpr int SS_CAP = 1024;  // per-warp shared-memory sort capacity
+constexpr int SS_CAP = 256;  // per-warp shared-memory sort capacity (longer rows: block sort)
 
 struct SegSmem {
     int id[SS_CAP];

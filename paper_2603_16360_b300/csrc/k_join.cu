@@ -64,6 +64,7 @@ constexpr int FB = 4;       // frontier nodes per BFS batch (FB * 32 <= CCAP)
 constexpr int GCAP0 = 8192; // first global visited table
 
 struct WarpSmem {
+    int nlist;  // bitmap mode: ids listed in the warp's space
     int htab[HCAP];
     int rid[RCAP];
     float rd[RCAP];
@@ -83,8 +84,9 @@ enum {
     C_SPILL = 8,
     C_ABORT = 9,
     C_RESTART = 10,  // pass-2 re-runs
-    C_TICKET2 = 11,  // pass-2 tickets
-    C_NUM = 12
+    C_TICKET2 = 11,  // pass-3 tickets (parent-ordered commit)
+    C_TICKET3 = 12,  // pass-2 tickets (parallel decisions)
+    C_NUM = 13
 };
 
 struct JoinParams {
@@ -96,7 +98,11 @@ struct JoinParams {
     int* done;             // per-query publish flag (soft sharing, pass 2)
     uint8_t* qflag;        // per-query pass-1 record (soft sharing): QF_* bits
     float* ckey;           // per-query FP32 key of the cache C[q] (soft sharing, pass 1)
-    int mode;              // 0: no soft sharing, 1 / 2: soft-sharing pass 1 / 2
+    int32_t* cache1;       // pass 1's C[q] (soft sharing)
+    int32_t* sca;          // pass 2: the seed it decided for
+    uint8_t* outc;         // pass 2: its decision (0 nothing, 1 one more visit, 2 re-run)
+    int32_t* cout;         // pass 2: the cache after a one-more-visit decision
+    int mode;              // 0: no soft sharing; soft sharing: 1 pass 1, 3 pass 2, 2 pass 3
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
     const int* order;      // dispatch order of pass 2 (MST BFS order: parents first)
@@ -119,6 +125,8 @@ struct JoinParams {
     int64_t pool_cap;
     int32_t* wspace;
     int64_t wstride;
+    uint32_t* vbits;  // per-warp visited bitmaps (vwords words each), zero between queries
+    int64_t vwords;
     int gmax;   // slots of each global visited region (power of two)
     int grcap;  // global result slots per warp
     int oqcap;  // out-range queue capacity (per buffer)
@@ -155,8 +163,9 @@ __device__ __forceinline__ float key_to_dist(const JoinParams& P, float k) {
 }
 
 struct WarpSpace {
-    int* hA;
+    int* hA;            // visited list of a query in bitmap mode (gmax ids)
     int* hB;
+    uint32_t* bits;     // this warp's visited bitmap over all nodes (all zero between queries)
     int* grid;
     float* grd;
     float* qk[2];
@@ -168,7 +177,9 @@ struct QueryState {
     unsigned mask;
     int nvis;
     int vislimit;
-    int region;  // -1: shared memory, 0: hA, 1: hB
+    int region;      // -1: shared-memory hash, 0: bitmap (list of set bits in hA)
+    uint32_t* bits;  // bitmap mode: the warp's bitmap, else nullptr
+    int* nlist;      // bitmap mode: entries in the list (shared-memory counter)
     int* rid;
     float* rd;
     int rcap;
@@ -188,34 +199,56 @@ __device__ __forceinline__ void raise_err(const JoinParams& P, int code) {
     atomicExch(P.ctr + C_ABORT, 1ull);
 }
 
-// make room for `m` more visited entries: move to (or grow) the global table
+// make room for `m` more visited entries.  Past the shared-memory hash a
+// query switches to the warp's global bitmap over all nodes (one atomicOr per
+// candidate, no probing); the ids it sets are listed so that the bitmap is
+// cleared when the query ends.
 __device__ bool vis_reserve(const JoinParams& P, QueryState& s, int m, const WarpSpace& W, int lane,
                             long long& c_spill) {
     if (s.nvis + m <= s.vislimit) return true;
-    // grow by 4x, the last step clipped to the region size
-    int cap = s.region < 0 ? GCAP0 : (int)(s.mask + 1u) * 4;
-    while (cap / 2 < s.nvis + m && cap < P.gmax) cap *= 4;
-    if (cap > P.gmax) cap = P.gmax;
-    if (cap <= (int)s.mask + 1 || cap / 2 < s.nvis + m) {
+    if (s.bits || s.nvis + m > P.gmax) {
         if (lane == 0) raise_err(P, VJ_DERR_VISITED_OVERFLOW);
         return false;
     }
-    int* dst = s.region == 0 ? W.hB : W.hA;
-    for (int i = lane; i < cap; i += 32) dst[i] = -1;
+    if (lane == 0) *s.nlist = 0;
     __syncwarp();
-    const unsigned nmask = (unsigned)cap - 1u;
-    const int oldcap = (int)s.mask + 1;
-    for (int i = lane; i < oldcap; i += 32) {
-        int k = s.tab[i];
-        if (k >= 0) hash_insert(dst, nmask, k);
+    for (int i = lane; i < (int)s.mask + 1; i += 32) {
+        const int k = s.tab[i];
+        if (k >= 0) {
+            atomicOr(W.bits + (k >> 5), 1u << (k & 31));
+            W.hA[atomicAdd(s.nlist, 1)] = k;
+        }
     }
     __syncwarp();
-    if (s.region < 0 && lane == 0) c_spill++;
-    s.region = s.region == 0 ? 1 : 0;
-    s.tab = dst;
-    s.mask = nmask;
-    s.vislimit = cap / 2;
+    if (lane == 0) c_spill++;
+    s.region = 0;
+    s.bits = W.bits;
+    s.vislimit = P.gmax;
     return true;
+}
+
+// insert key into the visited set: true when it was not there yet
+__device__ __forceinline__ bool vis_insert(QueryState& s, const WarpSpace& W, int key) {
+    if (!s.bits) return hash_insert(s.tab, s.mask, key) == 1;
+    const uint32_t m = 1u << (key & 31);
+    if (atomicOr(s.bits + (key >> 5), m) & m) return false;
+    W.hA[atomicAdd(s.nlist, 1)] = key;
+    return true;
+}
+
+__device__ __forceinline__ bool vis_contains(const QueryState& s, int key) {
+    if (!s.bits) return hash_contains(s.tab, s.mask, key);
+    return (((volatile const uint32_t*)s.bits)[key >> 5] >> (key & 31)) & 1u;
+}
+
+// bitmap mode: clear the bits this query set
+__device__ __forceinline__ void vis_release(QueryState& s, const WarpSpace& W, int lane) {
+    if (!s.bits) return;
+    __syncwarp();
+    const int n = *s.nlist;
+    for (int i = lane; i < n; i += 32) s.bits[W.hA[i] >> 5] = 0u;
+    __syncwarp();
+    s.bits = nullptr;
 }
 
 __device__ bool res_reserve(const JoinParams& P, QueryState& s, int m, const WarpSpace& W, int lane) {
@@ -371,6 +404,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
     WarpSpace W;
     W.hA = wbase;
     W.hB = wbase + P.gmax;
+    W.bits = P.vbits + gw * P.vwords;
     W.grid = wbase + 2 * (int64_t)P.gmax;
     W.grd = reinterpret_cast<float*>(W.grid + P.grcap);
     int32_t* qbase = wbase + 2 * (int64_t)P.gmax + 2 * (int64_t)P.grcap;
@@ -384,7 +418,8 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
 
     for (;;) {
         int t = 0;
-        if (lane == 0) t = (int)atomicAdd(P.ctr + (P.mode == 2 ? C_TICKET2 : C_TICKET), 1ull);
+        if (lane == 0)
+            t = (int)atomicAdd(P.ctr + (P.mode == 2 ? C_TICKET2 : P.mode == 3 ? C_TICKET3 : C_TICKET), 1ull);
         t = __shfl_sync(VJ_FULL, t, 0);
         if (t >= P.nq) break;
         const int qi = P.mode == 2 ? P.order[t] : P.order1[t];
@@ -394,9 +429,76 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
         const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
 
-        // ---- soft sharing, pass 2: what does C[parent] change?
+        // ---- soft sharing, passes 2 and 3: what does C[parent] change?
+        // decide(sc): 0 nothing, 1 one more visit (cache -> best), 2 re-run
+        auto decide = [&](int sc, int& best) -> int {
+            const int flags = P.qflag[qi];
+            best = P.cache1[qi];
+            if (flags & QF_DEFER) return 2;
+            if (sc < 0 || sc == P.entry) return 0;
+            if (lane == 0) S->cand[0] = sc;
+            __syncwarp();
+            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
+            __syncwarp();
+            const float k = S->ckey[0];
+            __syncwarp();
+            // sc would have been the greedy front: no probe
+            if ((flags & QF_PROBED) && k <= 0.f) return 2;
+            // sc in pass 1's V?  {entry, q} U N(q) (probed) U N(results) (BFS);
+            // one result per lane, its whole adjacency row loaded at once
+            bool seen = false;
+            if (flags & QF_PROBED) seen = lane < R && __ldg(P.adj + qn * R + lane) == sc;
+            const int64_t sg = P.seg[qi];
+            const int cnt = P.count[qi];
+            // (an overflowed pool is re-run by the host: nothing to read then)
+            if (P.hyb[qi] == 0 && sg + cnt <= P.pool_cap) {
+                for (int base = 0; base < cnt && !__any_sync(VJ_FULL, seen); base += 32) {
+                    const int u = base + lane < cnt ? P.pool_id[sg + base + lane] : -1;
+                    if (u == sc) seen = true;
+                    if (u >= 0) seen |= row_has(P.adj + (int64_t)u * R, R, sc);
+                }
+            }
+            if (__any_sync(VJ_FULL, seen)) return 0;
+            const bool in = inrange_decide(P, lane == 0, k, sc, qn, lane, c_rechk);
+            if (__shfl_sync(VJ_FULL, in, 0) && P.hyb[qi] != 2) return 2;  // the closure grows
+            // C[q] = the (dist, id) minimum of pass 1's cache and sc: by their
+            // FP32 keys when those differ by more than the rounding bound, else
+            // in FP64.  kb is the window's smallest key; the cache itself lies
+            // within tie_tol above it, hence the wider upper margin.
+            if (best < 0) {
+                best = sc;
+            } else {
+                const float kb = P.ckey[qi];
+                const bool far = P.metric == 0
+                                     ? (k > kb * (1.0f + 2.5f * P.tie_tol) || kb > k * (1.0f + P.tie_tol))
+                                     : (k > kb + 2.5f * P.tie_tol || kb > k + P.tie_tol);
+                if (far) {
+                    if (k < kb) best = sc;
+                } else {
+                    const double da = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, best, lane);
+                    const double db = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, sc, lane);
+                    if (db < da || (db == da && sc < best)) best = sc;
+                }
+            }
+            return 1;
+        };
         int seedc = -1;
+        if (P.mode == 3) {
+            // pass 2: the decision for C[parent] as pass 1 left it, in parallel
+            const int par = __ldg(P.parent + qi);
+            const int sc = par >= 0 ? P.cache1[par] : -1;
+            int best;
+            const int o = decide(sc, best);
+            if (lane == 0) {
+                P.sca[qi] = sc;
+                P.outc[qi] = (uint8_t)o;
+                P.cout[qi] = best;
+            }
+            __syncwarp();
+            continue;
+        }
         if (P.mode == 2) {
+            // pass 3, parent before child: the final C[parent]
             const int par = __ldg(P.parent + qi);
             int sc = -1;
             if (par >= 0 && lane == 0) {
@@ -422,68 +524,17 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             }
             sc = __shfl_sync(VJ_FULL, sc, 0);
             if (sc == -2) break;
-            const int flags = P.qflag[qi];
-            bool rerun = (flags & QF_DEFER) != 0;
-            bool bump = false;  // one more visited node; the cache may move to sc
-            if (!rerun && sc >= 0 && sc != P.entry) {
-                if (lane == 0) S->cand[0] = sc;
-                __syncwarp();
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
-                __syncwarp();
-                const float k = S->ckey[0];
-                __syncwarp();
-                if ((flags & QF_PROBED) && k <= 0.f) {
-                    rerun = true;  // sc would have been the greedy front: no probe
-                } else {
-                    // sc in pass 1's V?  {entry, q} U N(q) (probed) U N(results) (BFS);
-                    // one result per lane, its whole adjacency row loaded at once
-                    bool seen = false;
-                    if (flags & QF_PROBED) seen = lane < R && __ldg(P.adj + qn * R + lane) == sc;
-                    const int64_t sg = P.seg[qi];
-                    const int cnt = P.count[qi];
-                    // (an overflowed pool is re-run by the host: nothing to read then)
-                    if (P.hyb[qi] == 0 && sg + cnt <= P.pool_cap) {
-                        for (int base = 0; base < cnt && !__any_sync(VJ_FULL, seen); base += 32) {
-                            const int u = base + lane < cnt ? P.pool_id[sg + base + lane] : -1;
-                            if (u == sc) seen = true;
-                            if (u >= 0) seen |= row_has(P.adj + (int64_t)u * R, R, sc);
-                        }
-                    }
-                    if (!__any_sync(VJ_FULL, seen)) {
-                        const bool in = inrange_decide(P, lane == 0, k, sc, qn, lane, c_rechk);
-                        if (__shfl_sync(VJ_FULL, in, 0) && P.hyb[qi] != 2) rerun = true;  // the closure grows
-                        else bump = true;
-                    }
-                }
+            int best, o;
+            if (sc == P.sca[qi]) {  // usually: pass 2 decided for this very seed
+                o = P.outc[qi];
+                best = P.cout[qi];
+            } else {
+                o = decide(sc, best);
             }
-            if (!rerun) {
-                int best = P.cache[qi];
-                if (bump) {
-                    // C[q] = the (dist, id) minimum of pass 1's cache and sc: by
-                    // their FP32 keys when those differ by more than the rounding
-                    // bound, else in FP64
-                    if (best < 0) {
-                        best = sc;
-                    } else {
-                        const float kb = P.ckey[qi];
-                        const float k = S->ckey[0];
-                        // kb is the window's smallest key; the cache itself lies
-                        // within tie_tol above it, hence the wider upper margin
-                        const bool far = P.metric == 0
-                                             ? (k > kb * (1.0f + 2.5f * P.tie_tol) || kb > k * (1.0f + P.tie_tol))
-                                             : (k > kb + 2.5f * P.tie_tol || kb > k + P.tie_tol);
-                        if (far) {
-                            if (k < kb) best = sc;
-                        } else {
-                            const double da = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, best, lane);
-                            const double db = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, sc, lane);
-                            if (db < da || (db == da && sc < best)) best = sc;
-                        }
-                    }
-                }
+            if (o != 2) {
                 if (lane == 0) {
-                    if (bump) {
-                        P.cache[qi] = best;
+                    P.cache[qi] = best;
+                    if (o == 1) {
                         P.steps[qi] += 1;
                         c_dist += 1;
                     }
@@ -503,6 +554,8 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         s.nvis = 0;
         s.vislimit = HCAP / 2;
         s.region = -1;
+        s.bits = nullptr;
+        s.nlist = &S->nlist;
         s.rid = S->rid;
         s.rd = S->rd;
         s.rcap = RCAP;
@@ -528,7 +581,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         for (int src = 0; src < 3; src++) {
             int v = __shfl_sync(VJ_FULL, sid, src);
             int ins = 0;
-            if (lane == 0 && v >= 0) ins = hash_insert(s.tab, s.mask, v);
+            if (lane == 0 && v >= 0) ins = hash_insert(s.tab, s.mask, v);  // seeds: always the shared hash
             ins = __shfl_sync(VJ_FULL, ins, 0);
             if (lane == src) snew = ins == 1;
             __syncwarp();
@@ -580,7 +633,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             unsigned vm = __ballot_sync(VJ_FULL, v >= 0);
             if (!vis_reserve(P, s, __popc(vm), W, lane, c_spill)) failed = true;
             if (!failed) {
-                bool nw = v >= 0 && hash_insert(s.tab, s.mask, v) == 1;
+                bool nw = v >= 0 && vis_insert(s, W, v);
                 unsigned nm = __ballot_sync(VJ_FULL, nw);
                 int nc = __popc(nm);
                 int mypos = __popc(nm & ((1u << lane) - 1u));
@@ -648,7 +701,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     for (int t = 0; t < R; t++) f |= S->cand[t] == w;
                     return f;
                 }
-                bool inq = hash_contains(s.tab, s.mask, w);
+                bool inq = vis_contains(s, w);
                 if (inq && w == P.entry && !entry_in_nq) inq = false;
                 if (inq && w == seedc && !seed_in_nq) inq = false;
                 return inq;
@@ -726,6 +779,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             // a hybrid expansion needs the cached seed first: pass 2 runs it
             if (lane == 0) {
                 P.qflag[qi] = (uint8_t)(QF_DEFER | (probe ? QF_PROBED : 0));
+                P.cache1[qi] = -1;
                 P.hyb[qi] = 1;
                 P.count[qi] = 0;
                 P.steps[qi] = 0;
@@ -760,7 +814,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
 #pragma unroll
                 for (int f = 0; f < FB; f++) {
                     int v = vv[f];
-                    bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
+                    bool nw = v >= 0 && v < P.nx && vis_insert(s, W, v);
                     unsigned nm = __ballot_sync(VJ_FULL, nw);
                     if (nw) S->cand[nc + __popc(nm & ((1u << lane) - 1u))] = v;
                     nc += __popc(nm);
@@ -829,7 +883,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     break;
                 }
                 int v = lane < R ? __ldg(P.adj + (int64_t)u * R + lane) : -1;
-                bool nw = v >= 0 && v < P.nx && hash_insert(s.tab, s.mask, v) == 1;
+                bool nw = v >= 0 && v < P.nx && vis_insert(s, W, v);
                 unsigned nm = __ballot_sync(VJ_FULL, nw);
                 int nc = __popc(nm);
                 if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
@@ -930,10 +984,12 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             if (P.mode == 1) {
                 P.qflag[qi] = (uint8_t)(probe ? QF_PROBED : 0);
                 P.ckey[qi] = s.bk;
+                P.cache1[qi] = best;
             }
             // publish: cache[qi] is visible to whoever sees the flag
             if (P.mode == 2 && !failed) st_release(P.done + qi, 1);
         }
+        vis_release(s, W, lane);
         if (failed) {
             if (lane == 0) P.count[qi] = 0;
             break;
@@ -1099,6 +1155,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     ix->done.ensure(nq, s);
     ix->qflag.ensure(nq, s);
     ix->ckey.ensure(nq, s);
+    ix->cache1.ensure(nq, s);
+    ix->sca.ensure(nq, s);
+    ix->outc.ensure(nq, s);
+    ix->cout.ensure(nq, s);
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
@@ -1118,6 +1178,12 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         ix->wspace.alloc((size_t)(warps * wstride), s);
         ix->wspace_warps = warps;
     }
+    const int64_t vwords = (ix->n + 31) / 32;
+    if (ix->vbits.n < (size_t)(warps * vwords)) {
+        ix->vbits.free_(s);
+        ix->vbits.alloc((size_t)(warps * vwords), s);
+        VJ_CUDA(cudaMemsetAsync(ix->vbits.p, 0, (size_t)(warps * vwords) * sizeof(uint32_t), s));
+    }
     if (ix->pool_id.n == 0) {
         int64_t cap0 = std::max<int64_t>(nq * 64, 1 << 16);
         ix->pool_id.alloc(cap0, s);
@@ -1133,6 +1199,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.done = ix->done.p;
     P.qflag = ix->qflag.p;
     P.ckey = ix->ckey.p;
+    P.cache1 = ix->cache1.p;
+    P.sca = ix->sca.p;
+    P.outc = ix->outc.p;
+    P.cout = ix->cout.p;
     P.order = ix->order.p;
     // longest-first order from the previous join's visited counts (MST order on the first join)
     if (ix->have_costs) {
@@ -1175,6 +1245,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.count = ix->count.p;
     P.seg = ix->seg.p;
     P.wspace = ix->wspace.p;
+    P.vbits = ix->vbits.p;
+    P.vwords = vwords;
     P.wstride = wstride;
     P.gmax = gmax;
     P.grcap = grcap;
@@ -1182,7 +1254,9 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.ctr = ix->ctr.p;
     P.spin_limit = 1ll << 24;  // ~seconds with back-off; then VJ_DERR_WAIT_TIMEOUT
 
-    cudaEvent_t e0, e1, e2;
+    cudaEvent_t e0, e1, e2, ep[2];
+    VJ_CUDA(cudaEventCreate(&ep[0]));
+    VJ_CUDA(cudaEventCreate(&ep[1]));
     VJ_CUDA(cudaEventCreate(&e0));
     VJ_CUDA(cudaEventCreate(&e1));
     VJ_CUDA(cudaEventCreate(&e2));
@@ -1201,9 +1275,13 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
             // two launches: speculative pass, then the parent-ordered fix-up
             P.mode = 1;
             jd.launch(P, jd.blocks, s);
+            VJ_CUDA(cudaEventRecord(ep[0], s));
+            P.mode = 3;
+            jd.launch(P, jd.blocks, s);
+            VJ_CUDA(cudaEventRecord(ep[1], s));
             P.mode = 2;
             jd.launch(P, jd.blocks, s);
-            launches++;
+            launches += 2;
         } else {
             P.mode = 0;
             jd.launch(P, jd.blocks, s);
@@ -1221,6 +1299,8 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         ix->pool_d.alloc(cap, s);
     }
     if (hc[C_ERR] != 0) {
+        cudaEventDestroy(ep[0]);
+        cudaEventDestroy(ep[1]);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaEventDestroy(e2);
@@ -1295,6 +1375,18 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     float t_trav = 0.f, t_csr = 0.f;
     VJ_CUDA(cudaEventElapsedTime(&t_trav, e0, e1));
     VJ_CUDA(cudaEventElapsedTime(&t_csr, e1, e2));
+    st->ms_sws[0] = st->ms_sws[1] = st->ms_sws[2] = 0.0;
+    if (soft) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        VJ_CUDA(cudaEventElapsedTime(&a, e0, ep[0]));
+        VJ_CUDA(cudaEventElapsedTime(&b, ep[0], ep[1]));
+        VJ_CUDA(cudaEventElapsedTime(&c, ep[1], e1));
+        st->ms_sws[0] = a;
+        st->ms_sws[1] = b;
+        st->ms_sws[2] = c;
+    }
+    cudaEventDestroy(ep[0]);
+    cudaEventDestroy(ep[1]);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

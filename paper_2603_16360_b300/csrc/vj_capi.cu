@@ -92,7 +92,12 @@ static void free_index(vj_index* ix) {
     ix->done.free_(s);
     ix->qflag.free_(s);
     ix->ckey.free_(s);
+    ix->cache1.free_(s);
+    ix->sca.free_(s);
+    ix->cout.free_(s);
+    ix->outc.free_(s);
     ix->order1.free_(s);
+    ix->vbits.free_(s);
     ix->cost_hist.free_(s);
     ix->scan_cq.free_(s);
     ix->scan_cx.free_(s);

@@ -141,7 +141,10 @@ struct vj_index {
     DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
     DBuf<uint8_t> qflag;      // [nq] soft sharing: what pass 1 recorded per query
     DBuf<float> ckey;         // [nq] soft sharing: FP32 key of each query's pass-1 cache
+    DBuf<int32_t> cache1, sca, cout;  // [nq] soft sharing: pass-1 cache, pass-2 seed and cache
+    DBuf<uint8_t> outc;       // [nq] soft sharing: pass-2 decision
     DBuf<int32_t> order1;     // [nq] longest-first dispatch order (from the last join's visits)
+    DBuf<uint32_t> vbits;     // per-warp visited bitmaps of the join (zero between queries)
     DBuf<int> cost_hist;
     bool have_costs = false;
     DBuf<int32_t> scan_cq, scan_cx;  // tensor-core scan candidates (query, data id)

@@ -54,7 +54,7 @@ class vj_stats(C.Structure):
                 ("ms_traverse", C.c_double), ("ms_csr", C.c_double), ("ms_total", C.c_double),
                 ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
                 ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double),
-                ("sws_restarts", C.c_int64), ("ms_route", C.c_double)]
+                ("sws_restarts", C.c_int64), ("ms_route", C.c_double), ("ms_sws", C.c_double * 3)]
 
 
 class vj_result(C.Structure):
@@ -164,7 +164,11 @@ class Result:
 
 
 def _stats(s: vj_stats) -> dict:
-    return {name: getattr(s, name) for name, _ in vj_stats._fields_}
+    out = {}
+    for name, _ in vj_stats._fields_:
+        v = getattr(s, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
 
 
 def _host_result(rp) -> Result:
