@@ -318,7 +318,7 @@ def main():
             sweep.append({"thr": thr, "beam_cap": cap, "recall": round(rec, 4), "ms": round(r.stats["ms_total"], 2),
                           "routed": int((r.hybrid == 2).sum()), "ms_traverse": round(r.stats["ms_traverse"], 2),
                           "ms_route": round(r.stats["ms_route"], 2),
-                          "ms_sws": [round(x, 2) for x in r.stats["ms_sws"]]})
+                          "ms_sws": [round(x, 2) for x in r.stats["ms_sws"]], "reruns": r.stats["sws_restarts"]})
             if rec >= 0.95 and (op is None or r.stats["ms_total"] < op[3]):
                 op = (thr, rec, r, r.stats["ms_total"], cap)
         if op is None:  # nothing reached 0.95: route everything that the predictor doubts least

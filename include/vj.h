@@ -101,7 +101,9 @@ typedef struct {
  * query row; dists are the pair distances.  steps/cache/hybrid are per-query
  * (query index order): distance evaluations, the soft cache C[q] of Alg. 8
  * (closest visited data node, -1 if none) and the CheckHybrid outcome.
- * When on_device is 1 every array is a device pointer. */
+ * When on_device is 1 every array is a device pointer; otherwise every array
+ * is page-locked host memory from the library's block cache.  Either way the
+ * result is released with vj_result_free. */
 typedef struct {
     int64_t nq;
     int64_t nnz;
@@ -251,6 +253,7 @@ vj_status vj_export_knn(const vj_index *ix, int32_t *ids, float *dists);
 vj_status vj_index_info(const vj_index *ix, int64_t *nx, int64_t *nq, int *d, int *degree,
                         int *knn_k, int *max_depth);
 
+/* Release a result (its arrays go back to the library's caches). */
 void vj_result_free(vj_result *r);
 void vj_free(vj_index *ix);
 const char *vj_last_error(void);

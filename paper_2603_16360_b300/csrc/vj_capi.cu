@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "vj_internal.cuh"
 
@@ -238,6 +241,52 @@ extern "C" vj_status vj_set_plan(vj_index* ix, const uint8_t* route, const int32
     });
 }
 
+// Host results live in page-locked memory (device-to-host copies at full link
+// speed) from a process-wide cache of blocks in power-of-two size classes, so
+// repeated joins do not pay for cudaMallocHost.  At most 8 GiB stay cached.
+namespace {
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_pin_free;      // class bytes -> cached block
+std::unordered_map<void*, size_t> g_pin_class;  // every live or cached block
+size_t g_pin_cached = 0;
+constexpr size_t PIN_CACHE_MAX = (size_t)8 << 30;
+
+void* pin_alloc(size_t bytes) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_pin_free.find(c);
+    if (it != g_pin_free.end()) {
+        void* p = it->second;
+        g_pin_free.erase(it);
+        g_pin_cached -= c;
+        return p;
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_pin_class[p] = c;
+    return p;
+}
+
+void pin_free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_pin_class.find(p);
+    if (it == g_pin_class.end()) return;
+    const size_t c = it->second;
+    if (g_pin_cached + c <= PIN_CACHE_MAX) {
+        g_pin_free.emplace(c, p);
+        g_pin_cached += c;
+    } else {
+        g_pin_class.erase(it);
+        cudaFreeHost(p);
+    }
+}
+}  // namespace
+
 static vj_result* new_result(int64_t nq, int64_t nnz, bool on_device, cudaStream_t s) {
     vj_result* r = (vj_result*)calloc(1, sizeof(vj_result));
     if (!r) throw std::bad_alloc();
@@ -260,15 +309,16 @@ static vj_result* new_result(int64_t nq, int64_t nnz, bool on_device, cudaStream
             throw VjError{VJ_ERR_OOM};
         }
     } else {
-        r->offsets = (int64_t*)malloc(b_off);
-        r->ids = (int32_t*)malloc(b_id);
-        r->dists = (float*)malloc(b_d);
-        r->steps = (int32_t*)malloc(b_q);
-        r->cache = (int32_t*)malloc(b_q);
-        r->hybrid = (uint8_t*)malloc(b_h);
+        r->offsets = (int64_t*)pin_alloc(b_off);
+        r->ids = (int32_t*)pin_alloc(b_id);
+        r->dists = (float*)pin_alloc(b_d);
+        r->steps = (int32_t*)pin_alloc(b_q);
+        r->cache = (int32_t*)pin_alloc(b_q);
+        r->hybrid = (uint8_t*)pin_alloc(std::max<size_t>(b_h, 1));
         if (!r->offsets || !r->ids || !r->dists || !r->steps || !r->cache || !r->hybrid) {
             vj_result_free(r);
-            throw std::bad_alloc();
+            vj_set_error("page-locked result allocation failed");
+            throw VjError{VJ_ERR_OOM};
         }
     }
     return r;
@@ -400,12 +450,12 @@ extern "C" void vj_result_free(vj_result* r) {
         cudaFree(r->cache);
         cudaFree(r->hybrid);
     } else {
-        free(r->offsets);
-        free(r->ids);
-        free(r->dists);
-        free(r->steps);
-        free(r->cache);
-        free(r->hybrid);
+        pin_free(r->offsets);
+        pin_free(r->ids);
+        pin_free(r->dists);
+        pin_free(r->steps);
+        pin_free(r->cache);
+        pin_free(r->hybrid);
     }
     free(r);
 }

@@ -171,18 +171,35 @@ def _stats(s: vj_stats) -> dict:
     return out
 
 
+class _ResultOwner:
+    """Releases a host vj_result once no array viewing its buffers is left."""
+
+    def __init__(self, rp):
+        self.rp = rp
+
+    def __del__(self):
+        try:
+            load().vj_result_free(self.rp)
+        except Exception:
+            pass
+
+
 def _host_result(rp) -> Result:
+    """Numpy views of the library's page-locked result arrays (no copy)."""
     r = rp.contents
     nq, nnz = r.nq, r.nnz
+    owner = _ResultOwner(rp)
 
-    def arr(ptr, n, dt):
-        return np.ctypeslib.as_array(ptr, shape=(max(n, 1),))[:n].astype(dt, copy=True)
+    def arr(ptr, n, ctype, dt):
+        if n == 0:
+            return np.empty(0, dt)
+        buf = (ctype * n).from_address(C.cast(ptr, C.c_void_p).value)
+        buf._owner = owner  # the buffer lives while any view of it does
+        return np.frombuffer(buf, dtype=dt)
 
-    out = Result(arr(r.offsets, nq + 1, np.int64), arr(r.ids, nnz, np.int32), arr(r.dists, nnz, np.float32),
-                 arr(r.steps, nq, np.int32), arr(r.cache, nq, np.int32), arr(r.hybrid, nq, np.uint8),
-                 _stats(r.stats))
-    load().vj_result_free(rp)
-    return out
+    return Result(arr(r.offsets, nq + 1, C.c_int64, np.int64), arr(r.ids, nnz, C.c_int32, np.int32),
+                  arr(r.dists, nnz, C.c_float, np.float32), arr(r.steps, nq, C.c_int32, np.int32),
+                  arr(r.cache, nq, C.c_int32, np.int32), arr(r.hybrid, nq, C.c_uint8, np.uint8), _stats(r.stats))
 
 
 class DeviceResult:
