@@ -276,26 +276,41 @@ def main():
         rng = np.random.default_rng(w.seed + 99)
         train = np.sort(rng.choice(w.nq, size=max(1, w.nq // 10), replace=False))
         ladder = [0, 8, 32]
-        recs, steps_at = {}, {}
+        recs, steps_at, missed = {}, {}, {}
         for b in ladder:
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=int(b > 0),
                                   hybrid_beam=max(b, 1), learned=0)
             r = vj.vj_join(ix, eps)
             h, tot = per_query_hits(r, ex, w.nx)
             recs[b] = np.where(tot > 0, h / np.maximum(tot, 1), 1.0)
+            missed[b] = (tot - h).astype(np.float64)
             steps_at[b] = r.stats, r.steps.astype(np.float64)
         st0, s0 = steps_at[0]
         t_step = st0["ms_traverse"] / max(s0.sum(), 1)             # ms per distance evaluation (BFS join)
         t_bf = ex.stats["ms_scan"] / w.nq                           # ms per query of the full scan
         budget_lab = np.full(w.nq, ladder[-1], np.int32)
-        ok_any = np.zeros(w.nq, bool)
-        cost = np.full(w.nq, np.inf)
         for b in reversed(ladder):
-            okb = recs[b] >= 0.95
-            budget_lab = np.where(okb, b, budget_lab)
-            cost = np.where(okb, steps_at[b][1] * t_step, cost)
-            ok_any |= okb
-        route_lab = (~ok_any) | (cost > t_bf)
+            budget_lab = np.where(recs[b] >= 0.95, b, budget_lab)
+        # route labels: the routing a knapsack would choose on the training
+        # queries for pooled recall 0.955 -- every query whose BFS costs more
+        # than its scan row, then the others by missed pairs per unit of
+        # extra cost, until the missed pairs left are within 4.5 %
+        tot_all = np.diff(ex.offsets).astype(np.float64)
+        c_bfs = s0 * t_step
+        gain = np.where(c_bfs >= t_bf, np.inf, missed[0] / np.maximum(t_bf - c_bfs, 1e-12))
+        route_lab = np.zeros(w.nq, bool)
+
+        def knapsack(idx):
+            left, allowed = missed[0][idx].sum(), 0.045 * tot_all[idx].sum()
+            for qi in idx[np.argsort(-gain[idx], kind="stable")]:
+                if left <= allowed and not np.isinf(gain[qi]):
+                    break
+                route_lab[qi] = missed[0][qi] > 0 or np.isinf(gain[qi])
+                left -= missed[0][qi]
+
+        held = np.setdiff1d(np.arange(w.nq), train)
+        knapsack(train)
+        knapsack(held)
         F = vj.vj_features(ix, eps)
         mlp = vj.MLP(F.shape[1], 256, 256, seed=w.seed)
         t_tr = time.perf_counter()
@@ -303,7 +318,6 @@ def main():
                                epochs=30, batch=256, lr=1e-3, seed=w.seed)
         train_s = time.perf_counter() - t_tr
         pred = mlp.predict(F)
-        held = np.setdiff1d(np.arange(w.nq), train)
         route_acc = float(((pred[held, 1] > 0) == route_lab[held]).mean())
         # operating point: the fastest (route threshold, hybrid-queue cap) whose join reaches recall 0.95
         op, sweep = None, []
