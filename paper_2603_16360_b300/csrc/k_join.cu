@@ -102,6 +102,11 @@ struct JoinParams {
     int32_t* sca;          // pass 2: the seed it decided for
     uint8_t* outc;         // pass 2: its decision (0 nothing, 1 one more visit, 2 re-run)
     int32_t* cout;         // pass 2: the cache after a one-more-visit decision
+    int32_t* cache2;       // pass 2: a staged re-run's cache, visited count, hybrid flag,
+    int32_t* steps2;       //   result count and pool segment
+    uint8_t* hyb2;
+    int32_t* count2;
+    int64_t* seg2;
     int mode;              // 0: no soft sharing; soft sharing: 1 pass 1, 3 pass 2, 2 pass 3
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
@@ -495,7 +500,11 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 P.cout[qi] = best;
             }
             __syncwarp();
-            continue;
+            if (o != 2) continue;
+            // a re-run for this seed runs here, off the parent chain; its
+            // result is staged and pass 3 commits it if the seed stays
+            seedc = sc;
+            if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
         }
         if (P.mode == 2) {
             // pass 3, parent before child: the final C[parent]
@@ -525,11 +534,27 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
             sc = __shfl_sync(VJ_FULL, sc, 0);
             if (sc == -2) break;
             int best, o;
-            if (sc == P.sca[qi]) {  // usually: pass 2 decided for this very seed
+            const bool same = sc == P.sca[qi];  // usually: pass 2 decided for this very seed
+            if (same) {
                 o = P.outc[qi];
                 best = P.cout[qi];
             } else {
                 o = decide(sc, best);
+            }
+            if (o == 2 && same) {
+                // commit the re-run pass 2 staged
+                if (lane == 0) {
+                    if (!(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
+                    c_dist += P.steps2[qi];
+                    P.cache[qi] = P.cache2[qi];
+                    P.steps[qi] = P.steps2[qi];
+                    P.hyb[qi] = P.hyb2[qi];
+                    P.count[qi] = P.count2[qi];
+                    P.seg[qi] = P.seg2[qi];
+                    st_release(P.done + qi, 1);
+                }
+                __syncwarp();
+                continue;
             }
             if (o != 2) {
                 if (lane == 0) {
@@ -975,12 +1000,19 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
 
         if (lane == 0) {
-            // a pass-2 re-run replaces pass 1's count of this query
-            if (P.mode == 2 && !(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
-            P.cache[qi] = best;
-            P.steps[qi] = s.nvis;
-            P.hyb[qi] = (uint8_t)hyb;
-            c_dist += s.nvis;
+            if (P.mode == 3) {
+                // staged re-run (pass 2): committed by pass 3, counted there
+                P.cache2[qi] = best;
+                P.steps2[qi] = s.nvis;
+                P.hyb2[qi] = (uint8_t)hyb;
+            } else {
+                // a pass-3 re-run replaces pass 1's count of this query
+                if (P.mode == 2 && !(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
+                P.cache[qi] = best;
+                P.steps[qi] = s.nvis;
+                P.hyb[qi] = (uint8_t)hyb;
+                c_dist += s.nvis;
+            }
             if (P.mode == 1) {
                 P.qflag[qi] = (uint8_t)(probe ? QF_PROBED : 0);
                 P.ckey[qi] = s.bk;
@@ -991,7 +1023,10 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
         vis_release(s, W, lane);
         if (failed) {
-            if (lane == 0) P.count[qi] = 0;
+            if (lane == 0) {
+                if (P.mode == 3) P.count2[qi] = 0;
+                else P.count[qi] = 0;
+            }
             break;
         }
 
@@ -1000,8 +1035,13 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         if (lane == 0) off = atomicAdd(P.ctr + C_POOL, (unsigned long long)s.nres);
         off = __shfl_sync(VJ_FULL, off, 0);
         if (lane == 0) {
-            P.count[qi] = s.nres;
-            P.seg[qi] = (int64_t)off;
+            if (P.mode == 3) {
+                P.count2[qi] = s.nres;
+                P.seg2[qi] = (int64_t)off;
+            } else {
+                P.count[qi] = s.nres;
+                P.seg[qi] = (int64_t)off;
+            }
         }
         if ((int64_t)off + s.nres <= P.pool_cap) {
             for (int i = lane; i < s.nres; i += 32) {
@@ -1159,6 +1199,11 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     ix->sca.ensure(nq, s);
     ix->outc.ensure(nq, s);
     ix->cout.ensure(nq, s);
+    ix->cache2.ensure(nq, s);
+    ix->steps2.ensure(nq, s);
+    ix->hyb2.ensure(nq, s);
+    ix->count2.ensure(nq, s);
+    ix->seg2.ensure(nq, s);
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
@@ -1203,6 +1248,11 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.sca = ix->sca.p;
     P.outc = ix->outc.p;
     P.cout = ix->cout.p;
+    P.cache2 = ix->cache2.p;
+    P.steps2 = ix->steps2.p;
+    P.hyb2 = ix->hyb2.p;
+    P.count2 = ix->count2.p;
+    P.seg2 = ix->seg2.p;
     P.order = ix->order.p;
     // longest-first order from the previous join's visited counts (MST order on the first join)
     if (ix->have_costs) {

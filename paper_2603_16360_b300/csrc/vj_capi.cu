@@ -99,6 +99,11 @@ static void free_index(vj_index* ix) {
     ix->sca.free_(s);
     ix->cout.free_(s);
     ix->outc.free_(s);
+    ix->cache2.free_(s);
+    ix->steps2.free_(s);
+    ix->count2.free_(s);
+    ix->hyb2.free_(s);
+    ix->seg2.free_(s);
     ix->order1.free_(s);
     ix->vbits.free_(s);
     ix->cost_hist.free_(s);

@@ -143,6 +143,9 @@ struct vj_index {
     DBuf<float> ckey;         // [nq] soft sharing: FP32 key of each query's pass-1 cache
     DBuf<int32_t> cache1, sca, cout;  // [nq] soft sharing: pass-1 cache, pass-2 seed and cache
     DBuf<uint8_t> outc;       // [nq] soft sharing: pass-2 decision
+    DBuf<int32_t> cache2, steps2, count2;  // [nq] soft sharing: staged pass-2 re-runs
+    DBuf<uint8_t> hyb2;
+    DBuf<int64_t> seg2;
     DBuf<int32_t> order1;     // [nq] longest-first dispatch order (from the last join's visits)
     DBuf<uint32_t> vbits;     // per-warp visited bitmaps of the join (zero between queries)
     DBuf<int> cost_hist;
