@@ -38,6 +38,25 @@ sys.path.insert(0, ROOT)
 METRIC = "queries/s at recall≥0.95 vs exact join: learned+BF16 vs plain FP32, one B300"
 
 
+def _traffic(kernel, scale):
+    """DRAM bytes per step of `kernel` from profiles/traffic.md (an ncu capture of the full-size learned
+    step), or None when the workload is not the full-size one or the kernel's source changed since."""
+    if scale != 1.0:
+        return None
+    import hashlib
+    import re
+    p = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        m = re.match(r"^\| (\S+) \| (\S+) \| ([0-9a-f]{64}) \| ([0-9.eE+]+) \|", line)
+        if m and m.group(1) == kernel:
+            src = os.path.join(ROOT, m.group(2))
+            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == m.group(3):
+                return float(m.group(4))
+    return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -363,7 +382,8 @@ def main():
     trav = {"kernel": "k_join (traversal)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
             "achieved": statistics.mean(s["bytes_algorithmic"] for s in stats) / (t_tr / 1e3) / 1e9,
             "ms_per_launch": t_tr, "algorithmic_bytes_per_launch": statistics.mean(s["bytes_algorithmic"] for s in stats),
-            "peak_kind": f"{peak_kind} hbm_gbs (burst)", "traffic": None}
+            "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+            "traffic": _traffic("k_join", args.scale) if learned is not None else None}
     trav["frac"] = trav["achieved"] / hbm
     rooflines = [trav]
     if learned is not None and t_sc > 0:
@@ -372,7 +392,7 @@ def main():
         scan = {"kernel": "k_tc_scan (tcgen05 BF16 brute-force scan)", "bound": "tensor", "unit": "TFLOP/s",
                 "peak": bf16, "achieved": flops / (t_sc / 1e3) / 1e12, "ms_per_launch": t_sc,
                 "algorithmic_flops_per_launch": flops, "peak_kind": f"{peak_kind} bf16_tflops (burst)",
-                "traffic": None}
+                "traffic": _traffic("k_tc_scan_res", args.scale)}
         scan["frac"] = scan["achieved"] / bf16
         rooflines.append(scan)
     dominant = max(rooflines, key=lambda k: k["ms_per_launch"])
