@@ -65,7 +65,10 @@ typedef struct {
     int work_sharing;     /* VJ_WS_*, default VJ_WS_SOFT (MI+SWS) */
     int adapt_hybrid;     /* cfg.adapt_hybrid (Alg. 6), default 1 */
     int force_hybrid;     /* cfg.force_hybrid (Alg. 6), default 0 */
-    int precision;        /* VJ_PREC_* of the build's distance tiles, default FP32 */
+    int precision;        /* VJ_PREC_* of the kNN build's distance tiles: BF16 (default) sweeps on the
+                             tensor cores, FP32 on the SIMT units; candidates are re-ranked with exact
+                             keys and certified either way, so the lists are the same.  FP8 is not
+                             implemented (VJ_ERR_ARG). */
     int learned;          /* reserved, must be 0 */
     int route_bruteforce; /* reserved, must be 0 */
     int input_on_device;  /* 1: X and Q passed to vj_build are device pointers */
@@ -252,6 +255,12 @@ vj_status vj_export_knn(const vj_index *ix, int32_t *ids, float *dists);
 /* Shape of an index: any pointer may be NULL. */
 vj_status vj_index_info(const vj_index *ix, int64_t *nx, int64_t *nq, int *d, int *degree,
                         int *knn_k, int *max_depth);
+
+/* How the offline build went (any pointer may be NULL): knn_tensor_cores = 1
+ * when the kNN candidates came from the BF16 tensor-core sweep (0: the FP32
+ * SIMT sweep); knn_uncertified = rows whose candidates could not be
+ * certified and were scanned exactly; ms_build = device time of vj_build. */
+vj_status vj_build_info(const vj_index *ix, int *knn_tensor_cores, int64_t *knn_uncertified, double *ms_build);
 
 /* Release a result (its arrays go back to the library's caches). */
 void vj_result_free(vj_result *r);

@@ -411,11 +411,28 @@ struct RsParams {
     int64_t cap;
     int* err;
     long long spin_limit;
+    // kNN epilogue: the rows' node ids equal their row index
+    int kp;               // candidates kept per row
+    int32_t* cand_id;     // [nrows][kp] ids of the kp largest accumulators (-1 padded)
+    float* rej_max;       // [nrows] largest accumulator among nodes not kept
 };
 
-__global__ void __launch_bounds__(RS_THREADS, 1)
-    k_tc_scan_res(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAb,
-                  const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBb, RsParams P) {
+constexpr int KN_EPI = 8;                      // kNN epilogue warps: one per (query block, lane quarter)
+constexpr int KN_MAXKP = 128;
+
+// Resident-query tensor-core kernel with two epilogues:
+//   EPI_SCAN  16 warps; a pair is a candidate when its accumulator exceeds the
+//             row's threshold (the brute-force route and the exact join);
+//   EPI_KNN    8 warps; each thread owns one row and keeps the kp largest
+//             accumulators of its whole sweep (the exact kNN build), plus the
+//             largest one it dropped (the certificate's bound).
+enum { EPI_SCAN = 0, EPI_KNN = 1 };
+
+template <int EPI>
+__global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32, 1)
+    k_tc_res(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAb,
+             const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBb, RsParams P) {
+    constexpr int NEPI = EPI == EPI_KNN ? KN_EPI : RS_EPI;
     extern __shared__ uint8_t rs_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(rs_raw) + 1023) & ~uintptr_t(1023));
     RsBars& Bb = *reinterpret_cast<RsBars*>(base);
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&Bb.tfull[b], 1);
-            mbar_init(&Bb.tempty[b], RS_EPI);
+            mbar_init(&Bb.tempty[b], NEPI);
         }
         mbar_init(&Bb.afull, 1);
         mbar_init(&Bb.aempty, 1);
@@ -576,6 +593,106 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             }
             tc_commit(&Bb.drain);
             for (long long k = 0; k < P.spin_limit && !mbar_test(&Bb.drain, 0); k++) {
+            }
+        }
+    } else if constexpr (EPI == EPI_KNN) {
+        // ---------------- kNN epilogue: warp e owns TMEM lane quarter (warp & 3)
+        // of query block e >> 2, all 128 columns; lane = one row
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int blk = e >> 2;
+        const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+        float lk[KN_MAXKP];
+        int li[KN_MAXKP];
+        int i = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+            const int rp = u % P.nrp, cc = u / P.nrp;
+            const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+            const int64_t r = (int64_t)rp * 256 + blk * 128 + quarter * 32 + lane;
+            const bool rv = r < P.nrows;
+            int cnt = 0, mpos = 0;
+            float mval = -INFINITY;  // smallest kept value once the list is full
+            float rej = -INFINITY;   // largest value not kept
+            for (int ct = t0; ct < t1; ct++, i++) {
+                const int acc = i & 1;
+                const bool got = mbar_wait(&Bb.tfull[acc], (uint32_t)((i >> 1) & 1), abort, P.spin_limit);
+                if (!__all_sync(VJ_FULL, got)) {
+                    if (lane == 0) {
+                        *abort = 1;
+                        atomicExch(P.err, 1);
+                    }
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    uint32_t va[64];
+                    tmem_ld64_issue(tmem + lanes + (uint32_t)(acc * 256 + blk * 128 + h * 64), va);
+                    tmem_wait_ld64(va);
+                    if (h == 1) {
+                        // both halves are in registers: hand the TMEM buffer back
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&Bb.tempty[acc]);
+                    }
+                    if (!rv) continue;
+                    const int64_t c0 = (int64_t)ct * RS_BN + h * 64;
+                    // usual case: the list is full and none of these 64 beats its minimum
+                    if (cnt == P.kp && c0 + 64 <= P.ncols && (r < c0 || r >= c0 + 64)) {
+                        float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+#pragma unroll
+                        for (int j = 0; j < 64; j += 4) {
+                            m0 = fmaxf(m0, __uint_as_float(va[j + 0]));
+                            m1 = fmaxf(m1, __uint_as_float(va[j + 1]));
+                            m2 = fmaxf(m2, __uint_as_float(va[j + 2]));
+                            m3 = fmaxf(m3, __uint_as_float(va[j + 3]));
+                        }
+                        const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+                        if (m <= mval) {
+                            rej = fmaxf(rej, m);
+                            continue;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 64; j++) {
+                        const float o = __uint_as_float(va[j]);
+                        const int64_t c = c0 + j;
+                        if (c >= P.ncols || c == r) continue;
+                        if (cnt < P.kp) {
+                            lk[cnt] = o;
+                            li[cnt] = (int)c;
+                            cnt++;
+                            if (cnt == P.kp) {
+                                mval = lk[0];
+                                mpos = 0;
+                                for (int t = 1; t < P.kp; t++)
+                                    if (lk[t] < mval) {
+                                        mval = lk[t];
+                                        mpos = t;
+                                    }
+                            }
+                        } else if (o > mval) {
+                            rej = fmaxf(rej, mval);
+                            lk[mpos] = o;
+                            li[mpos] = (int)c;
+                            mval = lk[0];
+                            mpos = 0;
+                            for (int t = 1; t < P.kp; t++)
+                                if (lk[t] < mval) {
+                                    mval = lk[t];
+                                    mpos = t;
+                                }
+                        } else {
+                            rej = fmaxf(rej, o);
+                        }
+                    }
+                }
+            }
+            if (ok && rv) {
+                for (int t = 0; t < P.kp; t++) P.cand_id[r * P.kp + t] = t < cnt ? li[t] : -1;
+                P.rej_max[r] = rej;
             }
         }
     } else {
@@ -763,12 +880,13 @@ __global__ void k_query_rows(const int32_t* __restrict__ qrows, int64_t n, int32
 // index, kept for later scans).  Cosine rows are stored unit-normalised.
 static void ensure_data_bf16(vj_index* ix) {
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
-    if (ix->xbf.n >= (size_t)ix->nx * kp) return;
+    if (ix->xbf.n >= (size_t)ix->n * kp) return;
     cudaStream_t s = ix->stream;
-    ix->xbf.ensure((size_t)ix->nx * kp, s);
+    // every node (data rows first): scans read the data rows, the kNN build all
+    ix->xbf.ensure((size_t)ix->n * kp, s);
     const bool cosine = ix->metric != VJ_L2;
-    k_to_bf16<<<vj_div_up(ix->nx * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->nx, kp, 1.f,
-                                                           cosine ? ix->invn.p : nullptr, ix->xbf.p);
+    k_to_bf16<<<vj_div_up(ix->n * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->n, kp, 1.f,
+                                                          cosine ? ix->invn.p : nullptr, ix->xbf.p);
     VJ_LAUNCH_CHECK();
     // Exact-key test: when every coordinate is an integer of magnitude <= 256
     // it is exact in BF16, every product is an integer below 2^16 and, with
@@ -800,9 +918,9 @@ static void ensure_data_bf16(vj_index* ix) {
         }
         // row-independent form: cbmax >= cb |a| for every row
         ix->tc_cbmax = (float)(ix->tc_cb * ix->maxnorm * 1.0001);
-        ix->xbias.ensure((size_t)ix->nx * 16, s);
-        k_bias_split<<<vj_div_up(ix->nx, 256), 256, 0, s>>>(ix->sqn.p, ix->nx, (double)ix->tc_c3,
-                                                              (double)ix->tc_cbmax, ix->xbias.p);
+        ix->xbias.ensure((size_t)ix->n * 16, s);
+        k_bias_split<<<vj_div_up(ix->n, 256), 256, 0, s>>>(ix->sqn.p, ix->n, (double)ix->tc_c3,
+                                                             (double)ix->tc_cbmax, ix->xbias.p);
         VJ_LAUNCH_CHECK();
         ix->abias.ensure(128 * 16, s);
         k_fill_abias<<<vj_div_up(128 * 16, 256), 256, 0, s>>>(ix->abias.p);
@@ -907,9 +1025,9 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         R.err = err.p;
         R.spin_limit = spin_limit;
         const size_t smem = fixed + per * (size_t)R.stages;
-        VJ_CUDA(cudaFuncSetAttribute(k_tc_scan_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = std::min(R.nunits, ix->num_sms);
-        launch = [&, grid, smem]() { k_tc_scan_res<<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };
+        launch = [&, grid, smem]() { k_tc_res<EPI_SCAN><<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };
     } else {
         ta = make_map(abf.p, nr, kp, TC_BM);
         tb = make_map(ix->xbf.p, ix->nx, kp, TC_BN);
@@ -974,4 +1092,88 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     ctr.free_(s);
     err.free_(s);
     return (int64_t)hn;
+}
+
+// ---------------------------------------------------------------- exact kNN build
+// Lower bound, on the true key, of every node a row did not keep: the kept
+// list holds the kp largest accumulators, so every other node's accumulator
+// is at most rej and its key at least (1 - c3)|a|^2 - rej (L2) or 1 - rej - cb
+// (cosine), less the accumulation margin of k_row_thr.
+__global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restrict__ rej, int64_t n, int metric,
+                            int kp, float cb, float c3, float cbmax, double maxnorm, float* __restrict__ thr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float rj = rej[i];
+    if (!(rj > -INFINITY)) {
+        thr[i] = INFINITY;  // the list holds every other node
+        return;
+    }
+    const double g = (double)(kp + 16) * 1.1920928955078125e-7;
+    if (metric == 0) {
+        const double rn = (double)sqn[i];
+        const double mag = 2.1 * sqrt(rn) * maxnorm + 1.1 * maxnorm * maxnorm + (double)cbmax * maxnorm;
+        thr[i] = (float)((1.0 - (double)c3) * rn - (double)rj - g * mag);
+    } else {
+        thr[i] = (float)(1.0 - (double)rj - (double)cb - 3.0 * g);
+    }
+}
+
+// Candidates of the exact kNN over all n nodes on the tensor cores: per row
+// the kp nodes with the largest accumulators (lowest BF16 key lower bounds)
+// and a bound on the true key of every other node.  Returns false when the
+// shape does not suit the resident kernel (the caller uses the SIMT sweep).
+bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr) {
+    const int kpad = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
+    if (kpad > RS_MAX_KB * TC_BK || kp > KN_MAXKP || ix->n < 4096) return false;
+    cudaStream_t s = ix->stream;
+    ensure_data_bf16(ix);
+    const bool cosine = ix->metric != VJ_L2;
+    const int64_t n = ix->n;
+    DBuf<__nv_bfloat16> abf;
+    DBuf<float> rej;
+    DBuf<int> err;
+    abf.alloc((size_t)n * kpad, s);
+    rej.alloc(n, s);
+    err.alloc(1, s);
+    k_to_bf16<<<vj_div_up(n * kpad, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, n, kpad,
+                                                      cosine ? 1.f : 2.f, cosine ? ix->invn.p : nullptr, abf.p);
+    VJ_LAUNCH_CHECK();
+    CUtensorMap ta = make_map(abf.p, n, kpad, 128);
+    CUtensorMap tb = make_map(ix->xbf.p, n, kpad, RS_BN);
+    CUtensorMap tab = cosine ? ta : make_map16(ix->abias.p, 128, 128);
+    CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, n, RS_BN);
+    RsParams R{};
+    R.nrows = n;
+    R.ncols = n;
+    R.nkb = kpad / TC_BK;
+    R.bias = cosine ? 0 : 1;
+    R.nrp = (int)vj_div_up(n, 256);
+    R.nct = (int)vj_div_up(n, RS_BN);
+    R.tpu = R.nct;  // a row's list must see every node: one unit per 256-row block
+    R.nunits = R.nrp;
+    const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
+    const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
+    R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
+    R.err = err.p;
+    R.spin_limit = 1ll << 22;
+    R.kp = kp;
+    R.cand_id = cand_id;
+    R.rej_max = rej.p;
+    const size_t smem = fixed + per * (size_t)R.stages;
+    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    const int grid = std::min(R.nunits, ix->num_sms);
+    k_tc_res<EPI_KNN><<<grid, (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
+    VJ_LAUNCH_CHECK();
+    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, rej.p, n, ix->metric, kpad, ix->tc_cb, ix->tc_c3,
+                                                  ix->tc_cbmax, ix->maxnorm, row_thr);
+    VJ_LAUNCH_CHECK();
+    int herr = 0;
+    VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
+    abf.free_(s);
+    rej.free_(s);
+    err.free_(s);
+    return true;
 }

@@ -259,7 +259,7 @@ template <int G, int NPL>
 __global__ void __launch_bounds__(256) k_knn_rerank(const float* __restrict__ vec, const float* __restrict__ invn,
                                                      const float* __restrict__ sqn, int dp, int d, int64_t n,
                                                      int metric, int KP, int K, const int32_t* __restrict__ cand_id,
-                                                     const float* __restrict__ row_thr, double maxnorm,
+                                                     const float* __restrict__ row_thr, int thr_true, double maxnorm,
                                                      const int32_t* __restrict__ rows, int64_t nrows,
                                                      int32_t* __restrict__ out_id, float* __restrict__ out_key,
                                                      int32_t* __restrict__ bad_rows, int* __restrict__ nbad,
@@ -355,14 +355,15 @@ __global__ void __launch_bounds__(256) k_knn_rerank(const float* __restrict__ ve
         i0 = i1 + 1;
     }
     // certificate: every node outside the candidate list has a Gram key >=
-    // row_thr, hence a true key >= row_thr - beta
+    // row_thr, hence a true key >= row_thr - beta (thr_true: row_thr already
+    // bounds the true key)
     bool full = nvalid >= KP;  // a short list holds every other node
     bool ok = true;
     if (full && K <= nvalid) {
         float kth = keys[K - 1];
         double an = metric == 0 ? sqrt((double)sqn[r]) : 1.0;
         double mx = metric == 0 ? maxnorm : 1.0;
-        double beta = (2.0 * dp + 10.0) * (double)VJ_F32_U * (an + mx) * (an + mx) + 1e-30;
+        double beta = thr_true ? 0.0 : (2.0 * dp + 10.0) * (double)VJ_F32_U * (an + mx) * (an + mx) + 1e-30;
         double kth_hi = (double)kth * (1.0 + tol);
         ok = kth_hi + beta < (double)row_thr[r];
     }
@@ -537,12 +538,18 @@ void vj_build_knn(vj_index* ix) {
     cid.alloc((size_t)n * KP, s);
     ckey.alloc((size_t)n * KP, s);
     thr.alloc(n, s);
-    switch (KP) {
-        case 32: run_sweep<32>(ix, cid.p, ckey.p, thr.p); break;
-        case 64: run_sweep<64>(ix, cid.p, ckey.p, thr.p); break;
-        case 96: run_sweep<96>(ix, cid.p, ckey.p, thr.p); break;
-        default: run_sweep<128>(ix, cid.p, ckey.p, thr.p); break;
+    // tensor cores (BF16 tiles, bound on the true key of every node left out)
+    // when the rows fit the resident kernel; the FP32 SIMT sweep otherwise
+    const bool tc = ix->p.precision == VJ_PREC_BF16 && vj_tc_knn_candidates(ix, KP, cid.p, thr.p);
+    if (!tc) {
+        switch (KP) {
+            case 32: run_sweep<32>(ix, cid.p, ckey.p, thr.p); break;
+            case 64: run_sweep<64>(ix, cid.p, ckey.p, thr.p); break;
+            case 96: run_sweep<96>(ix, cid.p, ckey.p, thr.p); break;
+            default: run_sweep<128>(ix, cid.p, ckey.p, thr.p); break;
+        }
     }
+    ix->knn_tc = tc;
     ix->knn.ensure((size_t)n * K, s);
     ix->knnd.ensure((size_t)n * K, s);
     DBuf<int32_t> bad;
@@ -556,7 +563,7 @@ void vj_build_knn(vj_index* ix) {
     const int dp4 = ix->dp / 4;
     VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(n, 8), 256, 0, s>>>(
                             ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
-                            maxnorm, nullptr, n, ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p)));
+                            tc ? 1 : 0, maxnorm, nullptr, n, ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p)));
     VJ_LAUNCH_CHECK();
     int hb = 0;
     VJ_CUDA(cudaMemcpyAsync(&hb, nbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -573,7 +580,7 @@ void vj_build_knn(vj_index* ix) {
         VJ_CUDA(cudaMemsetAsync(nbad.p, 0, sizeof(int), s));
         VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
                                 ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
-                                maxnorm, bad.p, hb, ix->knn.p, ix->knnd.p, bad2.p, nbad.p, nr.p)));
+                                0, maxnorm, bad.p, hb, ix->knn.p, ix->knnd.p, bad2.p, nbad.p, nr.p)));
         VJ_LAUNCH_CHECK();
         bad2.free_(s);
     }

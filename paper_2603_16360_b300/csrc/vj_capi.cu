@@ -36,7 +36,7 @@ extern "C" void vj_default_params(vj_params* p) {
     p->work_sharing = VJ_WS_SOFT;
     p->adapt_hybrid = 1;
     p->force_hybrid = 0;
-    p->precision = VJ_PREC_FP32;
+    p->precision = VJ_PREC_BF16;
     p->learned = 0;
     p->route_bruteforce = 0;
     p->input_on_device = 0;
@@ -146,7 +146,8 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         VJ_REQUIRE(p.degree >= 1 && p.degree <= 32, VJ_ERR_ARG, "degree must be in [1, 32]");
         if (p.knn_k <= 0) p.knn_k = 2 * p.degree;
         VJ_REQUIRE(p.knn_k >= p.degree && p.knn_k <= 112, VJ_ERR_ARG, "knn_k must be in [degree, 112]");
-        VJ_REQUIRE(p.precision == VJ_PREC_FP32, VJ_ERR_ARG, "only FP32 build tiles are implemented");
+        VJ_REQUIRE(p.precision == VJ_PREC_FP32 || p.precision == VJ_PREC_BF16, VJ_ERR_ARG,
+                   "build tiles: FP32 or BF16 (FP8 is not implemented)");
         check_join_params(p);
 
         ix = new vj_index();
@@ -177,9 +178,19 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
                                   d * sizeof(float), nq, kind, s));
         ix->sqn.alloc(ix->n, s);
         ix->invn.alloc(ix->n, s);
+        cudaEvent_t b0, b1;
+        VJ_CUDA(cudaEventCreate(&b0));
+        VJ_CUDA(cudaEventCreate(&b1));
+        VJ_CUDA(cudaEventRecord(b0, s));
         vj_build_knn(ix);
         vj_build_graph(ix);
+        VJ_CUDA(cudaEventRecord(b1, s));
         VJ_CUDA(cudaStreamSynchronize(s));
+        float mb = 0.f;
+        VJ_CUDA(cudaEventElapsedTime(&mb, b0, b1));
+        ix->ms_build = mb;
+        cudaEventDestroy(b0);
+        cudaEventDestroy(b1);
         *out = ix;
     });
     if (st != VJ_OK && ix) free_index(ix);
@@ -442,6 +453,16 @@ extern "C" vj_status vj_index_info(const vj_index* ix, int64_t* nx, int64_t* nq,
         if (degree) *degree = ix->R;
         if (knn_k) *knn_k = ix->K;
         if (max_depth) *max_depth = ix->max_depth;
+    });
+}
+
+extern "C" vj_status vj_build_info(const vj_index* ix, int* knn_tensor_cores, int64_t* knn_uncertified,
+                                   double* ms_build) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        if (knn_tensor_cores) *knn_tensor_cores = ix->knn_tc ? 1 : 0;
+        if (knn_uncertified) *knn_uncertified = ix->knn_uncertified;
+        if (ms_build) *ms_build = ix->ms_build;
     });
 }
 

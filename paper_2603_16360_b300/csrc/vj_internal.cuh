@@ -111,8 +111,8 @@ struct vj_index {
     DBuf<int32_t> order;  // [nq]
     DBuf<int32_t> depth;  // [nq]
     int max_depth = 0;
-    DBuf<__nv_bfloat16> xbf;   // [nx][kp] BF16 copy of the data rows (tensor-core scans)
-    DBuf<__nv_bfloat16> xbias; // [nx][16] L2: three-term BF16 split of each data row's scan bias
+    DBuf<__nv_bfloat16> xbf;   // [n][kp] BF16 copy of every node, data rows first (tensor-core tiles)
+    DBuf<__nv_bfloat16> xbias; // [n][16] L2: three-term BF16 split of each node's scan bias
     DBuf<__nv_bfloat16> abias; // [128][16] (1, 1, 1, 0, ...) rows: the query side of the bias step
     float tc_cb = 0.f, tc_c3 = 0.f, tc_cbmax = 0.f;  // BF16 scan bound constants
     // per-query plan (route to the brute-force scan / hybrid budget), optional
@@ -136,6 +136,8 @@ struct vj_index {
     double last_scan_ms = 0.0; // device time of the last tensor-core scan
     int64_t last_scan_cand = 0;
     int64_t knn_uncertified = 0;  // rows whose tile candidates needed the exact fallback
+    bool knn_tc = false;          // the kNN candidates came from the tensor cores
+    double ms_build = 0.0;        // device time of vj_build
 
     // join scratch kept across calls
     DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
@@ -187,6 +189,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
 
 // tensor-core (tcgen05) BF16 scan of query rows against all data rows:
 // candidate (query index, data id) pairs, exact after re-check
+bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr);
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
                               DBuf<int32_t>& cx, double* ms_out);
 

@@ -26,7 +26,7 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_predictor_outputs",
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
-           "vj_index_info", "vj_result_free", "vj_free", "vj_last_error"]
+           "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
 
@@ -121,6 +121,8 @@ def load():
     lib.vj_export_knn.restype = I
     lib.vj_index_info.argtypes = [P, P, P, P, P, P, P]
     lib.vj_index_info.restype = I
+    lib.vj_build_info.argtypes = [P, P, P, P]
+    lib.vj_build_info.restype = I
     lib.vj_result_free.argtypes = [C.POINTER(vj_result)]
     lib.vj_result_free.restype = None
     lib.vj_free.argtypes = [P]
@@ -242,6 +244,11 @@ class Index:
                                     C.byref(md)))
         return {"nx": nx.value, "nq": nq.value, "d": d.value, "degree": deg.value, "knn_k": k.value,
                 "max_depth": md.value}
+
+    def build_info(self):
+        tc, unc, ms = C.c_int(), C.c_int64(), C.c_double()
+        _check(load().vj_build_info(self._h, C.byref(tc), C.byref(unc), C.byref(ms)))
+        return {"knn_tensor_cores": bool(tc.value), "knn_uncertified": unc.value, "ms_build": ms.value}
 
     def free(self):
         if self._h:

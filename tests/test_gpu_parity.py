@@ -85,6 +85,42 @@ def test_knn_bit_exact(built, oracle):
     np.testing.assert_allclose(keys, ref, rtol=1e-5, atol=1e-6)
 
 
+TC_KNN_CASES = {
+    "gauss_d32": lambda: inputs.gauss_small(seed=111, nx=6000, nq=600, d=32),
+    "sift_like_ints": lambda: inputs.sift_like(seed=112, scale=0.005),  # 5000 x 128 integers, 500 queries
+    "ragged_d37": lambda: inputs.uniform_small(113, 5000, 400, 37, degree=12, knn_k=24),
+    "cosine_d20": lambda: inputs.uniform_small(114, 5000, 300, 20, metric=1, degree=16, knn_k=32),
+}
+
+
+@pytest.mark.parametrize("case", list(TC_KNN_CASES))
+def test_tensor_core_knn_matches_oracle(oracle, case):
+    """The BF16 tensor-core kNN sweep (kept candidates + a bound on every node
+    left out, then the exact re-rank and certificate) gives the exact lists:
+    ids bit-exact against the FP64 oracle, and the same lists as the FP32 SIMT
+    sweep."""
+    w = TC_KNN_CASES[case]()
+    ix = _build(w)
+    info = ix.build_info()
+    assert info["knn_tensor_cores"], info
+    ids, keys = vj.vj_export_knn(ix)
+    n, K = w.nx + w.nq, ids.shape[1]
+    rows = np.arange(0, n, 3)  # a third of the rows keeps the FP64 oracle quick
+    o_ids, o_d = oracle.knn_rows(w.X, w.Q, K, rows, w.metric)
+    mism = np.nonzero((ids[rows] != o_ids).any(axis=1))[0]
+    assert len(mism) == 0, f"{case}: {len(mism)} rows differ, first {rows[mism[:5]]}"
+    ref = o_d ** 2 if w.metric == 0 else o_d
+    np.testing.assert_allclose(keys[rows], ref, rtol=1e-5, atol=1e-6)
+    p = vj.default_params(degree=w.degree, knn_k=w.knn_k)
+    p.precision = vj.VJ_PREC_FP32
+    ix32 = vj.vj_build(w.X, w.Q, metric=w.metric, params=p)
+    assert not ix32.build_info()["knn_tensor_cores"]
+    ids32, _ = vj.vj_export_knn(ix32)
+    np.testing.assert_array_equal(ids, ids32)
+    ix.free()
+    ix32.free()
+
+
 def test_graph_and_mst_match_oracle_on_same_knn(built, oracle):
     name, w, ix = built
     kn, _ = vj.vj_export_knn(ix)
