@@ -259,8 +259,10 @@ vj_status vj_index_info(const vj_index *ix, int64_t *nx, int64_t *nq, int *d, in
 /* How the offline build went (any pointer may be NULL): knn_tensor_cores = 1
  * when the kNN candidates came from the BF16 tensor-core sweep (0: the FP32
  * SIMT sweep); knn_uncertified = rows whose candidates could not be
- * certified and were scanned exactly; ms_build = device time of vj_build. */
-vj_status vj_build_info(const vj_index *ix, int *knn_tensor_cores, int64_t *knn_uncertified, double *ms_build);
+ * certified and were scanned exactly; ms_build = device time of vj_build,
+ * ms_knn = the part spent on the exact kNN lists. */
+vj_status vj_build_info(const vj_index *ix, int *knn_tensor_cores, int64_t *knn_uncertified, double *ms_build,
+                        double *ms_knn);
 
 /* Release a result (its arrays go back to the library's caches). */
 void vj_result_free(vj_result *r);

@@ -405,6 +405,8 @@ struct RsParams {
     int stages;
     const float* a_thr;    // per query row: candidate iff accumulator > a_thr
     const int32_t* a_ids;  // query index of each row
+    const float* a_rn;     // per query row |a|^2, when keys are written
+    float* ck;             // exact-key inputs: the candidate's key |a|^2 - accumulator (nullptr: none)
     int32_t* cq;
     int32_t* cx;
     unsigned long long* ncand;
@@ -710,6 +712,7 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
             const int64_t r = (int64_t)rp * 256 + blk * 128 + quarter * 32 + lane;
             const float thr = r < P.nrows ? P.a_thr[r] : INFINITY;
             const int qid = r < P.nrows ? P.a_ids[r] : -1;
+            const float rnk = (P.ck && r < P.nrows) ? P.a_rn[r] : 0.f;
             for (int ct = t0; ct < t1; ct++, i++) {
                 const int acc = i & 1;
                 const bool got = mbar_wait(&Bb.tfull[acc], (uint32_t)((i >> 1) & 1), abort, P.spin_limit);
@@ -771,6 +774,8 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
                                 if ((int64_t)gq < P.cap) {
                                     P.cq[gq] = qid;
                                     P.cx[gq] = (int)(c0 + h * 32 + j);
+                                    // integer inputs: the accumulator 2<a,b> - |b|^2 is exact
+                                    if (P.ck) P.ck[gq] = rnk - __uint_as_float(va[h * 32 + j]);
                                 }
                                 gq++;
                             }
@@ -937,7 +942,7 @@ static void ensure_data_bf16(vj_index* ix) {
 // Returns the candidate count (the arrays are grown and the scan re-run when
 // they are too small).
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
-                              DBuf<int32_t>& cx, double* ms_out) {
+                              DBuf<int32_t>& cx, double* ms_out, DBuf<float>* ck) {
     cudaStream_t s = ix->stream;
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     ensure_data_bf16(ix);
@@ -971,6 +976,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
 
     DBuf<unsigned long long> ctr;
     DBuf<int> err;
+    DBuf<float> rn_rows;
     ctr.alloc(1, s);
     err.alloc(1, s);
     const long long spin_limit = 1ll << 22;  // try_wait polls; seconds at most, then an error
@@ -1021,6 +1027,14 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
         R.a_thr = an.p;
         R.a_ids = aid.p;
+        // integer inputs (exact BF16 products and FP32 sums): the scan hands out
+        // each candidate's exact key, and no re-check from the vectors is needed
+        if (ck && !cosine && ix->bf16_exact) {
+            rn_rows.alloc(nr, s);
+            k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, rn_rows.p);
+            VJ_LAUNCH_CHECK();
+            R.a_rn = rn_rows.p;
+        }
         R.ncand = ctr.p;
         R.err = err.p;
         R.spin_limit = spin_limit;
@@ -1067,6 +1081,10 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         cx.ensure(cap, s);
         P.cq = R.cq = cq.p;
         P.cx = R.cx = cx.p;
+        if (R.a_rn) {
+            ck->ensure(cap, s);
+            R.ck = ck->p;
+        }
         P.cap = R.cap = (int64_t)cq.n;
         VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
         VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
@@ -1085,10 +1103,12 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ms_out) *ms_out = ms;
+    ix->last_scan_exact_keys = R.a_rn != nullptr;
     abf.free_(s);
     aid.free_(s);
     an.free_(s);
     anode.free_(s);
+    rn_rows.free_(s);
     ctr.free_(s);
     err.free_(s);
     return (int64_t)hn;

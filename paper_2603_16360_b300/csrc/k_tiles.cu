@@ -485,6 +485,18 @@ __global__ void k_nlj_recheck(const float* __restrict__ vec, const float* __rest
     }
 }
 
+// candidates with exact integer keys K (L2 on integer inputs): a pair is in
+// the join iff sqrt(K) < eps in FP64, exactly the definition's decision
+__global__ void k_exact_decide(const float* __restrict__ ck, const int32_t* __restrict__ cq, int64_t nc, double eps64,
+                               float* __restrict__ cd, int32_t* __restrict__ counts) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nc) return;
+    const double dd = sqrt(fmax((double)ck[e], 0.0));
+    const bool in = dd < eps64;
+    cd[e] = in ? sqrtf(fmaxf(ck[e], 0.f)) : -1.f;  // the traversal's FP32 distance of the same key
+    if (in) atomicAdd(counts + cq[e], 1);
+}
+
 __global__ void k_nlj_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx,
                               const float* __restrict__ cd, int64_t nc, const int64_t* __restrict__ offsets,
                               int32_t* __restrict__ cursor, int32_t* __restrict__ tid, float* __restrict__ td) {
@@ -620,7 +632,8 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     ctr.alloc(2, s);
     VJ_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
     double ms_scan = 0.0;
-    const int64_t nc = nr > 0 ? vj_tc_scan_candidates(ix, qrows, nr, eps, cq, cx, &ms_scan) : 0;
+    const int64_t nc = nr > 0 ? vj_tc_scan_candidates(ix, qrows, nr, eps, cq, cx, &ms_scan, &ix->scan_ck) : 0;
+    const bool exact_keys = nr > 0 && ix->last_scan_exact_keys;
     ix->last_scan_ms = ms_scan;
     ix->last_scan_cand = nc;
     DBuf<int32_t> counts, cursor;
@@ -630,7 +643,11 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
     VJ_CUDA(cudaMemsetAsync(counts.p, 0, nq * sizeof(int32_t), s));
     VJ_CUDA(cudaMemsetAsync(cursor.p, 0, nq * sizeof(int32_t), s));
     const float band = 2.0f * (float)(ix->dp + 4) * VJ_F32_U * (ix->metric == VJ_L2 ? 1.0f : 4.0f) + 1e-6f;
-    if (nc > 0) {
+    if (nc > 0 && exact_keys) {
+        // integer inputs: the scan's keys are exact; decide as the FP64 definition does
+        k_exact_decide<<<vj_div_up(nc, 256), 256, 0, s>>>(ix->scan_ck.p, cq.p, nc, (double)eps, cd.p, counts.p);
+        VJ_LAUNCH_CHECK();
+    } else if (nc > 0) {
         k_nlj_recheck<<<vj_div_up(nc, 256), 256, 0, s>>>(ix->vec.p, ix->invn.p, ix->dp, ix->d, nx, ix->metric,
                                                          eps_key, band, (double)eps, cq.p, cx.p, nc, cd.p, counts.p,
                                                          ctr.p + 1);

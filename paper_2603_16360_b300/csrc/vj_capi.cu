@@ -178,19 +178,24 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
                                   d * sizeof(float), nq, kind, s));
         ix->sqn.alloc(ix->n, s);
         ix->invn.alloc(ix->n, s);
-        cudaEvent_t b0, b1;
+        cudaEvent_t b0, b1, b2;
         VJ_CUDA(cudaEventCreate(&b0));
         VJ_CUDA(cudaEventCreate(&b1));
+        VJ_CUDA(cudaEventCreate(&b2));
         VJ_CUDA(cudaEventRecord(b0, s));
         vj_build_knn(ix);
-        vj_build_graph(ix);
         VJ_CUDA(cudaEventRecord(b1, s));
+        vj_build_graph(ix);
+        VJ_CUDA(cudaEventRecord(b2, s));
         VJ_CUDA(cudaStreamSynchronize(s));
-        float mb = 0.f;
-        VJ_CUDA(cudaEventElapsedTime(&mb, b0, b1));
+        float mb = 0.f, mk = 0.f;
+        VJ_CUDA(cudaEventElapsedTime(&mb, b0, b2));
+        VJ_CUDA(cudaEventElapsedTime(&mk, b0, b1));
         ix->ms_build = mb;
+        ix->ms_knn = mk;
         cudaEventDestroy(b0);
         cudaEventDestroy(b1);
+        cudaEventDestroy(b2);
         *out = ix;
     });
     if (st != VJ_OK && ix) free_index(ix);
@@ -457,12 +462,13 @@ extern "C" vj_status vj_index_info(const vj_index* ix, int64_t* nx, int64_t* nq,
 }
 
 extern "C" vj_status vj_build_info(const vj_index* ix, int* knn_tensor_cores, int64_t* knn_uncertified,
-                                   double* ms_build) {
+                                   double* ms_build, double* ms_knn) {
     return guarded([&] {
         VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
         if (knn_tensor_cores) *knn_tensor_cores = ix->knn_tc ? 1 : 0;
         if (knn_uncertified) *knn_uncertified = ix->knn_uncertified;
         if (ms_build) *ms_build = ix->ms_build;
+        if (ms_knn) *ms_knn = ix->ms_knn;
     });
 }
 

@@ -138,6 +138,7 @@ struct vj_index {
     int64_t knn_uncertified = 0;  // rows whose tile candidates needed the exact fallback
     bool knn_tc = false;          // the kNN candidates came from the tensor cores
     double ms_build = 0.0;        // device time of vj_build
+    double ms_knn = 0.0;          // ... of which the exact kNN lists
 
     // join scratch kept across calls
     DBuf<int> done;           // [nq] publish flags of finished queries (soft sharing)
@@ -153,6 +154,8 @@ struct vj_index {
     DBuf<int> cost_hist;
     bool have_costs = false;
     DBuf<int32_t> scan_cq, scan_cx;  // tensor-core scan candidates (query, data id)
+    DBuf<float> scan_ck;             // ... and their exact keys (integer inputs)
+    bool last_scan_exact_keys = false;
     DBuf<int64_t> sort_large;  // result rows handed to the block-wide sort
     DBuf<int> sort_nlarge;
     DBuf<int32_t> cache;      // [nq]
@@ -191,7 +194,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
 // candidate (query index, data id) pairs, exact after re-check
 bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr);
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
-                              DBuf<int32_t>& cx, double* ms_out);
+                              DBuf<int32_t>& cx, double* ms_out, DBuf<float>* ck = nullptr);
 
 // learned prologue: features -> predictor -> per-query plan; returns #routed
 int64_t vj_learned_prologue(vj_index* ix, float eps);

@@ -121,7 +121,7 @@ def load():
     lib.vj_export_knn.restype = I
     lib.vj_index_info.argtypes = [P, P, P, P, P, P, P]
     lib.vj_index_info.restype = I
-    lib.vj_build_info.argtypes = [P, P, P, P]
+    lib.vj_build_info.argtypes = [P, P, P, P, P]
     lib.vj_build_info.restype = I
     lib.vj_result_free.argtypes = [C.POINTER(vj_result)]
     lib.vj_result_free.restype = None
@@ -246,9 +246,10 @@ class Index:
                 "max_depth": md.value}
 
     def build_info(self):
-        tc, unc, ms = C.c_int(), C.c_int64(), C.c_double()
-        _check(load().vj_build_info(self._h, C.byref(tc), C.byref(unc), C.byref(ms)))
-        return {"knn_tensor_cores": bool(tc.value), "knn_uncertified": unc.value, "ms_build": ms.value}
+        tc, unc, ms, mk = C.c_int(), C.c_int64(), C.c_double(), C.c_double()
+        _check(load().vj_build_info(self._h, C.byref(tc), C.byref(unc), C.byref(ms), C.byref(mk)))
+        return {"knn_tensor_cores": bool(tc.value), "knn_uncertified": unc.value, "ms_build": ms.value,
+                "ms_knn": mk.value}
 
     def free(self):
         if self._h:
