@@ -413,28 +413,27 @@ struct RsParams {
     int64_t cap;
     int* err;
     long long spin_limit;
-    // kNN epilogue: the rows' node ids equal their row index
-    int kp;               // candidates kept per row
-    int32_t* cand_id;     // [nrows][kp] ids of the kp largest accumulators (-1 padded)
-    float* rej_max;       // [nrows] largest accumulator among nodes not kept
+    int tstride;          // data tile t of a unit is tile t * tstride (1: every tile)
+    // sample epilogue: the rows' node ids equal their row index
+    float* top16;         // [nrows] 16th largest accumulator over the sampled tiles (other nodes)
 };
 
-constexpr int KN_EPI = 8;                      // kNN epilogue warps: one per (query block, lane quarter)
-constexpr int KN_MAXKP = 128;
+constexpr int KN_EPI = 8;  // sample epilogue warps: one per (query block, lane quarter)
 
 // Resident-query tensor-core kernel with two epilogues:
-//   EPI_SCAN  16 warps; a pair is a candidate when its accumulator exceeds the
-//             row's threshold (the brute-force route and the exact join);
-//   EPI_KNN    8 warps; each thread owns one row and keeps the kp largest
-//             accumulators of its whole sweep (the exact kNN build), plus the
-//             largest one it dropped (the certificate's bound).
-enum { EPI_SCAN = 0, EPI_KNN = 1 };
+//   EPI_SCAN    16 warps; a pair is a candidate when its accumulator exceeds
+//               the row's threshold (the brute-force route, the exact join and
+//               the kNN build's candidate sweep);
+//   EPI_SAMPLE   8 warps; each thread owns one row and keeps, in registers, the
+//               16 largest accumulators over a sample of the data tiles (the
+//               kNN build's per-row threshold).
+enum { EPI_SCAN = 0, EPI_SAMPLE = 1 };
 
 template <int EPI>
-__global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32, 1)
+__global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 32, 1)
     k_tc_res(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAb,
              const __grid_constant__ CUtensorMap tB, const __grid_constant__ CUtensorMap tBb, RsParams P) {
-    constexpr int NEPI = EPI == EPI_KNN ? KN_EPI : RS_EPI;
+    constexpr int NEPI = EPI == EPI_SAMPLE ? KN_EPI : RS_EPI;
     extern __shared__ uint8_t rs_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(rs_raw) + 1023) & ~uintptr_t(1023));
     RsBars& Bb = *reinterpret_cast<RsBars*>(base);
@@ -505,8 +504,9 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
                     }
                     mbar_arrive_tx(&Bb.full[s], stage_tx);
                     for (int kb = 0; kb < P.nkb; kb++)
-                        tma_load_2d(sB + (s * P.nkb + kb) * RS_BOX, &tB, &Bb.full[s], kb * 64, ct * RS_BN);
-                    if (P.bias) tma_load_2d(sBb + s * RS_BBOX, &tBb, &Bb.full[s], 0, ct * RS_BN);
+                        tma_load_2d(sB + (s * P.nkb + kb) * RS_BOX, &tB, &Bb.full[s], kb * 64,
+                                    ct * P.tstride * RS_BN);
+                    if (P.bias) tma_load_2d(sBb + s * RS_BBOX, &tBb, &Bb.full[s], 0, ct * P.tstride * RS_BN);
                     issued |= 1u << s;
                     last_ph = (last_ph & ~(1u << s)) | (ph << s);
                     if (++s == P.stages) {
@@ -597,15 +597,15 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
             for (long long k = 0; k < P.spin_limit && !mbar_test(&Bb.drain, 0); k++) {
             }
         }
-    } else if constexpr (EPI == EPI_KNN) {
-        // ---------------- kNN epilogue: warp e owns TMEM lane quarter (warp & 3)
-        // of query block e >> 2, all 128 columns; lane = one row
+    } else if constexpr (EPI == EPI_SAMPLE) {
+        // ---------------- sample epilogue: warp e owns TMEM lane quarter (warp & 3)
+        // of query block e >> 2, all 128 columns; lane = one row.  t[] holds
+        // the row's 16 largest accumulators so far, descending (static
+        // indices only: the array stays in registers).
         const int e = warp - 2;
         const int quarter = warp & 3;
         const int blk = e >> 2;
         const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
-        float lk[KN_MAXKP];
-        int li[KN_MAXKP];
         int i = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
@@ -613,9 +613,9 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
             const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
             const int64_t r = (int64_t)rp * 256 + blk * 128 + quarter * 32 + lane;
             const bool rv = r < P.nrows;
-            int cnt = 0, mpos = 0;
-            float mval = -INFINITY;  // smallest kept value once the list is full
-            float rej = -INFINITY;   // largest value not kept
+            float t[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) t[k] = -INFINITY;
             for (int ct = t0; ct < t1; ct++, i++) {
                 const int acc = i & 1;
                 const bool got = mbar_wait(&Bb.tfull[acc], (uint32_t)((i >> 1) & 1), abort, P.spin_limit);
@@ -640,62 +640,33 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
                         if (lane == 0) mbar_arrive(&Bb.tempty[acc]);
                     }
                     if (!rv) continue;
-                    const int64_t c0 = (int64_t)ct * RS_BN + h * 64;
-                    // usual case: the list is full and none of these 64 beats its minimum
-                    if (cnt == P.kp && c0 + 64 <= P.ncols && (r < c0 || r >= c0 + 64)) {
-                        float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+                    const int64_t c0 = (int64_t)ct * P.tstride * RS_BN + h * 64;
+                    float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
 #pragma unroll
-                        for (int j = 0; j < 64; j += 4) {
-                            m0 = fmaxf(m0, __uint_as_float(va[j + 0]));
-                            m1 = fmaxf(m1, __uint_as_float(va[j + 1]));
-                            m2 = fmaxf(m2, __uint_as_float(va[j + 2]));
-                            m3 = fmaxf(m3, __uint_as_float(va[j + 3]));
-                        }
-                        const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-                        if (m <= mval) {
-                            rej = fmaxf(rej, m);
-                            continue;
-                        }
+                    for (int j = 0; j < 64; j += 4) {
+                        m0 = fmaxf(m0, __uint_as_float(va[j + 0]));
+                        m1 = fmaxf(m1, __uint_as_float(va[j + 1]));
+                        m2 = fmaxf(m2, __uint_as_float(va[j + 2]));
+                        m3 = fmaxf(m3, __uint_as_float(va[j + 3]));
                     }
+                    if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) <= t[15]) continue;
+                    const bool edge = c0 + 64 > P.ncols || (r >= c0 && r < c0 + 64);
 #pragma unroll
                     for (int j = 0; j < 64; j++) {
-                        const float o = __uint_as_float(va[j]);
-                        const int64_t c = c0 + j;
-                        if (c >= P.ncols || c == r) continue;
-                        if (cnt < P.kp) {
-                            lk[cnt] = o;
-                            li[cnt] = (int)c;
-                            cnt++;
-                            if (cnt == P.kp) {
-                                mval = lk[0];
-                                mpos = 0;
-                                for (int t = 1; t < P.kp; t++)
-                                    if (lk[t] < mval) {
-                                        mval = lk[t];
-                                        mpos = t;
-                                    }
-                            }
-                        } else if (o > mval) {
-                            rej = fmaxf(rej, mval);
-                            lk[mpos] = o;
-                            li[mpos] = (int)c;
-                            mval = lk[0];
-                            mpos = 0;
-                            for (int t = 1; t < P.kp; t++)
-                                if (lk[t] < mval) {
-                                    mval = lk[t];
-                                    mpos = t;
-                                }
-                        } else {
-                            rej = fmaxf(rej, o);
+                        float x = __uint_as_float(va[j]);
+                        if (x <= t[15]) continue;
+                        if (edge && (c0 + j >= P.ncols || c0 + j == r)) continue;
+                        // insert: x sinks to its place, the 16th value drops out
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            const float hi = fmaxf(t[k], x);
+                            x = fminf(t[k], x);
+                            t[k] = hi;
                         }
                     }
                 }
             }
-            if (ok && rv) {
-                for (int t = 0; t < P.kp; t++) P.cand_id[r * P.kp + t] = t < cnt ? li[t] : -1;
-                P.rej_max[r] = rej;
-            }
+            if (ok && rv) P.top16[r] = t[15];
         }
     } else {
         // ---------------- epilogue: warp e reads TMEM lane quarter (warp & 3),
@@ -744,7 +715,7 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
                 }
                 const bool maybe = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr;
                 if (__any_sync(VJ_FULL, maybe)) {
-                    const int64_t c0 = (int64_t)ct * RS_BN + csub * 64;
+                    const int64_t c0 = (int64_t)ct * P.tstride * RS_BN + csub * 64;
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         uint32_t hit = 0;
@@ -774,8 +745,16 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_KNN ? KN_EPI : RS_EPI)) * 32,
                                 if ((int64_t)gq < P.cap) {
                                     P.cq[gq] = qid;
                                     P.cx[gq] = (int)(c0 + h * 32 + j);
-                                    // integer inputs: the accumulator 2<a,b> - |b|^2 is exact
-                                    if (P.ck) P.ck[gq] = rnk - __uint_as_float(va[h * 32 + j]);
+                                    // integer inputs: the accumulator 2<a,b> - |b|^2 is exact.
+                                    // (select by unrolled compares: a runtime index into va
+                                    // would move the whole array to local memory)
+                                    if (P.ck) {
+                                        float o = 0.f;
+#pragma unroll
+                                        for (int jj = 0; jj < 32; jj++)
+                                            if (jj == j) o = __uint_as_float(va[h * 32 + jj]);
+                                        P.ck[gq] = rnk - o;
+                                    }
                                 }
                                 gq++;
                             }
@@ -1027,6 +1006,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
         R.a_thr = an.p;
         R.a_ids = aid.p;
+        R.tstride = 1;
         // integer inputs (exact BF16 products and FP32 sums): the scan hands out
         // each candidate's exact key, and no re-check from the vectors is needed
         if (ck && !cosine && ix->bf16_exact) {
@@ -1115,48 +1095,85 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
 }
 
 // ---------------------------------------------------------------- exact kNN build
-// Lower bound, on the true key, of every node a row did not keep: the kept
-// list holds the kp largest accumulators, so every other node's accumulator
-// is at most rej and its key at least (1 - c3)|a|^2 - rej (L2) or 1 - rej - cb
-// (cosine), less the accumulation margin of k_row_thr.
-__global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restrict__ rej, int64_t n, int metric,
+// Candidates of the exact kNN over all n nodes, on the tensor cores, in two
+// sweeps of the resident kernel:
+//   1. every KNN_SAMPLE-th data tile: per row the 16th largest accumulator t
+//      (so about 16 * KNN_SAMPLE nodes overall are expected above it);
+//   2. every tile: the nodes whose accumulator exceeds t (a hair below it),
+//      listed per row (CSR).
+// Every node left out has accumulator <= t, so its true key is at least
+// (1 - c3)|a|^2 - t (L2) or 1 - t - cb (cosine) less the accumulation margin;
+// that bound goes to the exact re-rank, whose certificate decides whether the
+// row's top K is proven.
+constexpr int KNN_SAMPLE = 16;
+
+__global__ void k_knn_thr(const float* __restrict__ top, int64_t n, float* __restrict__ thr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = top[i];
+    thr[i] = t > -INFINITY ? t - fabsf(t) * 3.814697265625e-6f - 1e-30f : -INFINITY;
+}
+
+__global__ void k_iota(int32_t* __restrict__ v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)i;
+}
+
+__global__ void k_pair_count(const int32_t* __restrict__ cq, int64_t nc, int32_t* __restrict__ counts) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nc) atomicAdd(counts + cq[e], 1);
+}
+
+__global__ void k_pair_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx, int64_t nc,
+                               const int64_t* __restrict__ off, int32_t* __restrict__ cursor,
+                               int32_t* __restrict__ ids) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nc) return;
+    const int q = cq[e];
+    ids[off[q] + atomicAdd(cursor + q, 1)] = cx[e];
+}
+
+// true-key lower bound of every node a row did not list (accumulator <= thr)
+__global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restrict__ thr_acc, int64_t n, int metric,
                             int kp, float cb, float c3, float cbmax, double maxnorm, float* __restrict__ thr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float rj = rej[i];
-    if (!(rj > -INFINITY)) {
-        thr[i] = INFINITY;  // the list holds every other node
+    const float ta = thr_acc[i];
+    if (!(ta > -INFINITY)) {
+        thr[i] = -INFINITY;  // nothing was left out for a reason: no bound
         return;
     }
     const double g = (double)(kp + 16) * 1.1920928955078125e-7;
     if (metric == 0) {
         const double rn = (double)sqn[i];
         const double mag = 2.1 * sqrt(rn) * maxnorm + 1.1 * maxnorm * maxnorm + (double)cbmax * maxnorm;
-        thr[i] = (float)((1.0 - (double)c3) * rn - (double)rj - g * mag);
+        thr[i] = (float)((1.0 - (double)c3) * rn - (double)ta - g * mag);
     } else {
-        thr[i] = (float)(1.0 - (double)rj - (double)cb - 3.0 * g);
+        thr[i] = (float)(1.0 - (double)ta - (double)cb - 3.0 * g);
     }
 }
 
-// Candidates of the exact kNN over all n nodes on the tensor cores: per row
-// the kp nodes with the largest accumulators (lowest BF16 key lower bounds)
-// and a bound on the true key of every other node.  Returns false when the
-// shape does not suit the resident kernel (the caller uses the SIMT sweep).
-bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr) {
+bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr) {
     const int kpad = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
-    if (kpad > RS_MAX_KB * TC_BK || kp > KN_MAXKP || ix->n < 4096) return false;
+    if (kpad > RS_MAX_KB * TC_BK || ix->n < 4096) return false;
     cudaStream_t s = ix->stream;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
     const int64_t n = ix->n;
     DBuf<__nv_bfloat16> abf;
-    DBuf<float> rej;
+    DBuf<float> top, thr;
+    DBuf<int32_t> iota;
     DBuf<int> err;
+    DBuf<unsigned long long> ctr;
     abf.alloc((size_t)n * kpad, s);
-    rej.alloc(n, s);
+    top.alloc(n, s);
+    thr.alloc(n, s);
+    iota.alloc(n, s);
     err.alloc(1, s);
+    ctr.alloc(1, s);
     k_to_bf16<<<vj_div_up(n * kpad, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, n, kpad,
                                                       cosine ? 1.f : 2.f, cosine ? ix->invn.p : nullptr, abf.p);
+    k_iota<<<vj_div_up(n, 256), 256, 0, s>>>(iota.p, n);
     VJ_LAUNCH_CHECK();
     CUtensorMap ta = make_map(abf.p, n, kpad, 128);
     CUtensorMap tb = make_map(ix->xbf.p, n, kpad, RS_BN);
@@ -1168,32 +1185,97 @@ bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr
     R.nkb = kpad / TC_BK;
     R.bias = cosine ? 0 : 1;
     R.nrp = (int)vj_div_up(n, 256);
-    R.nct = (int)vj_div_up(n, RS_BN);
-    R.tpu = R.nct;  // a row's list must see every node: one unit per 256-row block
-    R.nunits = R.nrp;
+    const int nct_all = (int)vj_div_up(n, RS_BN);
     const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
     const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
     R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
     R.err = err.p;
     R.spin_limit = 1ll << 22;
-    R.kp = kp;
-    R.cand_id = cand_id;
-    R.rej_max = rej.p;
     const size_t smem = fixed + per * (size_t)R.stages;
-    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    const int grid = std::min(R.nunits, ix->num_sms);
-    k_tc_res<EPI_KNN><<<grid, (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
+
+    // 1. sample sweep: one unit per 256-row block over every KNN_SAMPLE-th tile
+    R.tstride = KNN_SAMPLE;
+    R.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
+    R.tpu = R.nct;
+    R.nunits = R.nrp;
+    R.top16 = top.p;
+    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tc_res<EPI_SAMPLE><<<std::min(R.nunits, ix->num_sms), (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
     VJ_LAUNCH_CHECK();
-    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, rej.p, n, ix->metric, kpad, ix->tc_cb, ix->tc_c3,
-                                                  ix->tc_cbmax, ix->maxnorm, row_thr);
+    k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
     VJ_LAUNCH_CHECK();
+
+    // 2. candidate sweep over every tile, rows are node ids
+    R.tstride = 1;
+    R.nct = nct_all;
+    {
+        const int64_t g = std::max(1, ix->num_sms);
+        int64_t best = INT64_MAX;
+        int best_tpu = R.nct;
+        for (int64_t ncc = 1; ncc <= R.nct; ncc++) {
+            const int64_t tpu = (R.nct + ncc - 1) / ncc;
+            if (ncc > 1 && (R.nct + tpu - 1) / tpu != ncc) continue;
+            const int64_t load = (((int64_t)R.nrp * ncc + g - 1) / g) * (tpu + 3);
+            if (load < best) {
+                best = load;
+                best_tpu = (int)tpu;
+            }
+        }
+        R.tpu = best_tpu;
+    }
+    R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
+    R.a_thr = thr.p;
+    R.a_ids = iota.p;
+    R.ncand = ctr.p;
+    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DBuf<int32_t>& cq = ix->scan_cq;
+    DBuf<int32_t>& cx = ix->scan_cx;
+    int64_t cap = std::max<int64_t>(cq.n, n * (int64_t)(20 * KNN_SAMPLE) + (1 << 20));
+    unsigned long long hn = 0;
     int herr = 0;
-    VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    VJ_CUDA(cudaStreamSynchronize(s));
-    VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
+    for (int attempt = 0; attempt < 2; attempt++) {
+        cq.ensure(cap, s);
+        cx.ensure(cap, s);
+        R.cq = cq.p;
+        R.cx = cx.p;
+        R.cap = (int64_t)cq.n;
+        VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
+        k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R);
+        VJ_LAUNCH_CHECK();
+        VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
+        if ((int64_t)hn <= (int64_t)cq.n) break;
+        cap = (int64_t)hn + 1024;
+    }
+    const int64_t nc = (int64_t)hn;
+
+    // 3. candidates grouped by row (CSR) and each row's bound
+    DBuf<int32_t> counts, cursor;
+    counts.alloc(n, s);
+    cursor.alloc(n, s);
+    VJ_CUDA(cudaMemsetAsync(counts.p, 0, n * sizeof(int32_t), s));
+    VJ_CUDA(cudaMemsetAsync(cursor.p, 0, n * sizeof(int32_t), s));
+    if (nc > 0) k_pair_count<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, nc, counts.p);
+    VJ_LAUNCH_CHECK();
+    off.ensure(n + 1, s);
+    vj_exclusive_scan_i32_to_i64(counts.p, off.p, n, ix);
+    ids.ensure(std::max<int64_t>(nc, 1), s);
+    if (nc > 0) k_pair_scatter<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, cx.p, nc, off.p, cursor.p, ids.p);
+    VJ_LAUNCH_CHECK();
+    row_thr.ensure(n, s);
+    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, thr.p, n, ix->metric, kpad, ix->tc_cb, ix->tc_c3,
+                                                  ix->tc_cbmax, ix->maxnorm, row_thr.p);
+    VJ_LAUNCH_CHECK();
+    counts.free_(s);
+    cursor.free_(s);
     abf.free_(s);
-    rej.free_(s);
+    top.free_(s);
+    thr.free_(s);
+    iota.free_(s);
     err.free_(s);
+    ctr.free_(s);
     return true;
 }

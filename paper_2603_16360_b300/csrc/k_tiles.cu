@@ -4,7 +4,9 @@
 // Both evaluate keys through the norm expansion |a|^2 + |b|^2 - 2<a,b> (L2,
 // squared) or 1 - <a,b>/(|a||b|) (cosine) over 128 x 128 tiles of a
 // register-blocked FP32 Gram product, then
-//  - kNN: each block owns 128 rows and sweeps every column tile, keeping per
+//  - kNN (FP32 build tiles; the BF16 default runs on the tensor cores in
+//    k_tc.cu and is re-ranked here by k_knn_rerank_csr): each block owns 128
+//    rows and sweeps every column tile, keeping per
 //    row the KP smallest keys (KP = K + margin); a second pass re-ranks the KP
 //    candidates with direct-difference FP32 keys (FP64 among near-ties) and
 //    certifies that no excluded node can enter the top K given the Gram
@@ -377,6 +379,137 @@ __global__ void __launch_bounds__(256) k_knn_rerank(const float* __restrict__ ve
     }
 }
 
+// warp per row over a CSR candidate list (at most KC_CAP, the row itself
+// dropped): exact keys, sort, FP64 near-tie runs, then the certificate
+// against row_thr, a lower bound on the true key of every node not listed.
+// Rows that cannot be certified (or list more than KC_CAP) go to bad_rows.
+constexpr int KC_CAP = 1024;
+constexpr int KC_WPB = 4;
+
+struct KcSmem {
+    int id[KC_CAP];
+    float key[KC_CAP];
+    double d64[128];
+};
+
+template <int G, int NPL>
+__global__ void __launch_bounds__(KC_WPB * 32)
+    k_knn_rerank_csr(const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d, int64_t n,
+                     int metric, int K, const int64_t* __restrict__ off, const int32_t* __restrict__ cand,
+                     const float* __restrict__ row_thr, int32_t* __restrict__ out_id, float* __restrict__ out_key,
+                     int32_t* __restrict__ bad_rows, int* __restrict__ nbad, unsigned long long* __restrict__ nrechk) {
+    extern __shared__ uint8_t kc_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    KcSmem& S = reinterpret_cast<KcSmem*>(kc_raw)[warp];
+    const int64_t r = (int64_t)blockIdx.x * KC_WPB + warp;
+    if (r >= n) return;
+    const int64_t b = off[r];
+    const int cnt = (int)(off[r + 1] - b);
+    if (cnt > KC_CAP) {
+        if (lane == 0) bad_rows[atomicAdd(nbad, 1)] = (int32_t)r;
+        return;
+    }
+    // compact the list without the row itself
+    int nvalid = 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int v = base + lane < cnt ? cand[b + base + lane] : -1;
+        const bool keep = v >= 0 && v != r;
+        const unsigned m = __ballot_sync(VJ_FULL, keep);
+        if (keep) S.id[nvalid + __popc(m & ((1u << lane) - 1u))] = v;
+        nvalid += __popc(m);
+    }
+    int P2 = 32;
+    while (P2 < nvalid) P2 <<= 1;
+    for (int e = nvalid + lane; e < P2; e += 32) {
+        S.id[e] = INT32_MAX;
+        S.key[e] = FLT_MAX;
+    }
+    __syncwarp();
+    float4 q[NPL];
+    load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
+    const float invq = metric ? invn[r] : 0.f;
+    group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, S.id, nvalid, S.key, lane);
+    __syncwarp();
+    // bitonic sort of P2 (key, id) pairs, ascending
+    for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P2; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = kless(S.key[p], S.id[p], S.key[i], S.id[i]);
+                    if (gt == up) {
+                        const float tk = S.key[i];
+                        const int ti = S.id[i];
+                        S.key[i] = S.key[p];
+                        S.id[i] = S.id[p];
+                        S.key[p] = tk;
+                        S.id[p] = ti;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // near-tie runs among the first K + 1: FP64 re-rank (runs stay below 128)
+    const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
+    const int lim = min(K + 1, nvalid);
+    bool ok = nvalid >= K;
+    int i0 = 0;
+    while (i0 < lim) {
+        int i1 = i0;
+        while (i1 + 1 < nvalid &&
+               (metric == 0 ? S.key[i1 + 1] - S.key[i1] <= tol * S.key[i1 + 1] : S.key[i1 + 1] - S.key[i1] <= tol))
+            i1++;
+        if (i1 > i0) {
+            if (i1 - i0 >= 128) {
+                ok = false;  // a tie run this long is left to the exact row scan
+                break;
+            }
+            for (int e = i0; e <= i1; e++) {
+                const double dd = warp_dist64(vec, dp, d, metric, r, S.id[e], lane);
+                if (lane == 0) S.d64[e - i0] = dd;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                atomicAdd(nrechk, 1ull);
+                for (int a = i0 + 1; a <= i1; a++) {
+                    const double da = S.d64[a - i0];
+                    const int ia = S.id[a];
+                    const float ka = S.key[a];
+                    int c = a - 1;
+                    while (c >= i0 && (S.d64[c - i0] > da || (S.d64[c - i0] == da && S.id[c] > ia))) {
+                        S.d64[c + 1 - i0] = S.d64[c - i0];
+                        S.id[c + 1] = S.id[c];
+                        S.key[c + 1] = S.key[c];
+                        c--;
+                    }
+                    S.d64[c + 1 - i0] = da;
+                    S.id[c + 1] = ia;
+                    S.key[c + 1] = ka;
+                }
+            }
+            __syncwarp();
+        }
+        i0 = i1 + 1;
+    }
+    // certificate: the K-th key, with its rounding margin, below the bound on
+    // every node not listed
+    if (ok) {
+        const double kth = (double)S.key[K - 1];
+        const double hi = metric == 0 ? kth * (1.0 + tol) : kth + tol;
+        ok = hi < (double)row_thr[r];
+    }
+    if (!ok) {
+        if (lane == 0) bad_rows[atomicAdd(nbad, 1)] = (int32_t)r;
+        return;
+    }
+    for (int e = lane; e < K; e += 32) {
+        out_id[r * K + e] = S.id[e];
+        out_key[r * K + e] = S.key[e];
+    }
+}
+
 // ---------------------------------------------------------------- fallback
 // warp per uncertified row: brute-force top-K' over all nodes with
 // direct-difference keys, then the same re-rank (run again on its output)
@@ -545,23 +678,6 @@ void vj_build_knn(vj_index* ix) {
     KP = (KP + 31) / 32 * 32;
     if (KP > 128) KP = 128;
     VJ_REQUIRE(K < KP || K == 128, VJ_ERR_ARG, "knn_k too large");
-    DBuf<int32_t> cid;
-    DBuf<float> ckey, thr;
-    cid.alloc((size_t)n * KP, s);
-    ckey.alloc((size_t)n * KP, s);
-    thr.alloc(n, s);
-    // tensor cores (BF16 tiles, bound on the true key of every node left out)
-    // when the rows fit the resident kernel; the FP32 SIMT sweep otherwise
-    const bool tc = ix->p.precision == VJ_PREC_BF16 && vj_tc_knn_candidates(ix, KP, cid.p, thr.p);
-    if (!tc) {
-        switch (KP) {
-            case 32: run_sweep<32>(ix, cid.p, ckey.p, thr.p); break;
-            case 64: run_sweep<64>(ix, cid.p, ckey.p, thr.p); break;
-            case 96: run_sweep<96>(ix, cid.p, ckey.p, thr.p); break;
-            default: run_sweep<128>(ix, cid.p, ckey.p, thr.p); break;
-        }
-    }
-    ix->knn_tc = tc;
     ix->knn.ensure((size_t)n * K, s);
     ix->knnd.ensure((size_t)n * K, s);
     DBuf<int32_t> bad;
@@ -573,16 +689,53 @@ void vj_build_knn(vj_index* ix) {
     VJ_CUDA(cudaMemsetAsync(nbad.p, 0, sizeof(int), s));
     VJ_CUDA(cudaMemsetAsync(nr.p, 0, sizeof(unsigned long long), s));
     const int dp4 = ix->dp / 4;
-    VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(n, 8), 256, 0, s>>>(
-                            ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
-                            tc ? 1 : 0, maxnorm, nullptr, n, ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p)));
-    VJ_LAUNCH_CHECK();
+    DBuf<int32_t> cid;
+    DBuf<float> ckey, thr;
+    // tensor cores (BF16 tiles; per-row candidate lists with a bound on the
+    // true key of every node left out) when the rows fit the resident kernel,
+    // the FP32 SIMT sweep otherwise; exact re-rank and certificate either way
+    bool tc = false;
+    if (ix->p.precision == VJ_PREC_BF16) {
+        DBuf<int64_t> coff;
+        DBuf<int32_t> cids;
+        DBuf<float> cthr;
+        tc = vj_tc_knn_candidates(ix, coff, cids, cthr);
+        if (tc) {
+            const int smem = KC_WPB * (int)sizeof(KcSmem);
+            VJ_DISPATCH_GN(dp4, VJ_CUDA(cudaFuncSetAttribute(k_knn_rerank_csr<G, NPL>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                           k_knn_rerank_csr<G, NPL><<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
+                               ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p,
+                               ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p));
+            VJ_LAUNCH_CHECK();
+        }
+        coff.free_(s);
+        cids.free_(s);
+        cthr.free_(s);
+    }
+    ix->knn_tc = tc;
+    cid.alloc((size_t)n * KP, s);
+    thr.alloc(n, s);
+    if (!tc) {
+        ckey.alloc((size_t)n * KP, s);
+        switch (KP) {
+            case 32: run_sweep<32>(ix, cid.p, ckey.p, thr.p); break;
+            case 64: run_sweep<64>(ix, cid.p, ckey.p, thr.p); break;
+            case 96: run_sweep<96>(ix, cid.p, ckey.p, thr.p); break;
+            default: run_sweep<128>(ix, cid.p, ckey.p, thr.p); break;
+        }
+        VJ_DISPATCH_GN(dp4, (k_knn_rerank<G, NPL><<<vj_div_up(n, 8), 256, 0, s>>>(
+                                ix->vec.p, ix->invn.p, ix->sqn.p, ix->dp, ix->d, n, ix->metric, KP, K, cid.p, thr.p,
+                                0, maxnorm, nullptr, n, ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p)));
+        VJ_LAUNCH_CHECK();
+    }
     int hb = 0;
     VJ_CUDA(cudaMemcpyAsync(&hb, nbad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaStreamSynchronize(s));
     ix->knn_uncertified = hb;
     if (hb > 0) {
         // exact row scans for the uncertified rows, then re-rank them again
+        // (their scans fill cid / thr at the rows' own positions)
         VJ_DISPATCH_GN(dp4, (k_knn_rowscan<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
                                 ix->vec.p, ix->invn.p, ix->dp, n, ix->metric, KP, bad.p, hb, cid.p, thr.p)));
         VJ_LAUNCH_CHECK();

@@ -192,7 +192,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
 
 // tensor-core (tcgen05) BF16 scan of query rows against all data rows:
 // candidate (query index, data id) pairs, exact after re-check
-bool vj_tc_knn_candidates(vj_index* ix, int kp, int32_t* cand_id, float* row_thr);
+bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr);
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
                               DBuf<int32_t>& cx, double* ms_out, DBuf<float>* ck = nullptr);
 
