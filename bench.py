@@ -207,6 +207,96 @@ def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed"):
     return e0.elapsed_time(e1) / steps, stats
 
 
+def bench_collection(args, vj, torch):
+    """A collection of independent join instances of very different sizes
+    (angular_collection: |X| log-uniform 1e4..2e6 and |Q| 1e3..2e5, both times
+    --scale, d = 100 cosine), joined by vj_join_batch (the traversal passes of
+    all instances fused into one launch per pass) and, for comparison, by one
+    vj_join per instance.  Plain MI+SWS (FP32); the d1/d2 rule, else forced
+    hybrid search with the smallest queue size reaching pooled recall 0.95."""
+    from paper_2603_16360_b300 import inputs
+    lo = lambda v: max(int(v * args.scale), 2000)
+    rng_kw = dict(nx_range=(lo(1e4), max(lo(2e6), lo(1e4) + 1)),
+                  nq_range=(max(int(1e3 * args.scale), 100), max(int(2e5 * args.scale), 101)))
+    ixs, eps, nqs, nxs, targets, exs = [], [], [], [], [], []
+    t0 = time.perf_counter()
+    for w in inputs.angular_collection(n=args.instances, **rng_kw):
+        ix = vj.vj_build(w.X, w.Q, metric=w.metric, params=vj.default_params(degree=w.degree, knn_k=w.knn_k))
+        e = calibrate_eps(vj, ix, w, w.target_matches)
+        ixs.append(ix)
+        eps.append(e)
+        nqs.append(w.nq)
+        nxs.append(w.nx)
+        targets.append(w.target_matches)
+        exs.append(vj.vj_join_exact(ix, e))
+        del w
+    build_s = time.perf_counter() - t0
+    total_q = int(sum(nqs))
+
+    def pooled_recall(rs):
+        hits = tot = 0
+        for r, ex, nx in zip(rs, exs, nxs):
+            h, t = per_query_hits(r, ex, nx)
+            hits += int(h.sum())
+            tot += int(t.sum())
+        return hits / max(tot, 1)
+
+    chosen = None
+    for mode, budget in [("adapt", 256)] + [("force", b) for b in (4, 8, 16, 32, 64, 128, 256)]:
+        for ix in ixs:
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
+                                  force_hybrid=int(mode == "force"), hybrid_beam=budget, learned=0)
+        rs = vj.vj_join_batch(ixs, eps)
+        rec = pooled_recall(rs)
+        chosen = (mode, budget, rec, rs)
+        if rec >= 0.95:
+            break
+    mode, budget, rec, rs = chosen
+    pairs = int(sum(r.nnz for r in rs))
+    for _ in range(args.warmup):
+        vj.vj_join_batch(ixs, eps)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        batch_ms, trav_ms = [], []
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            rb = vj.vj_join_batch(ixs, eps)
+            batch_ms.append(1e3 * (time.perf_counter() - t1))
+            trav_ms.append(rb[0].stats["ms_traverse"])
+        seq_ms, seq_trav = [], []
+        for _ in range(max(2, args.steps // 2)):
+            t1 = time.perf_counter()
+            tt = 0.0
+            for ix, e in zip(ixs, eps):
+                tt += vj.vj_join(ix, e).stats["ms_traverse"]
+            seq_ms.append(1e3 * (time.perf_counter() - t1))
+            seq_trav.append(tt)
+    b_ms = statistics.median(batch_ms)
+    s_ms = statistics.median(seq_ms)
+    d2h = int(sum(r.offsets.nbytes + r.ids.nbytes + r.dists.nbytes + r.steps.nbytes + r.cache.nbytes +
+                  r.hybrid.nbytes for r in rb))
+    line = {"metric": "queries/s of a collection of join instances at pooled recall≥0.95 vs exact join, one B300",
+            "value": total_q / (b_ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"angular_collection: {len(ixs)} instances, |X| {min(nxs)}..{max(nxs)} "
+                                   f"(sum {sum(nxs)}), |Q| {min(nqs)}..{max(nqs)} (sum {total_q}), d=100 cosine, "
+                                   f"eps for a mean of {min(targets):g}..{max(targets):g} matches/query",
+                       "arm": f"vj_join_batch, plain MI+SWS FP32, hybrid={mode} beam {budget}",
+                       "recall": rec, "pairs": pairs, "build_s": build_s,
+                       "fused_traversal_ms": statistics.median(trav_ms),
+                       "one_join_per_instance": {"ms_per_step": s_ms, "queries_per_s": total_q / (s_ms / 1e3),
+                                                 "traversal_ms_sum": statistics.median(seq_trav)},
+                       "batch_vs_one_by_one": s_ms / b_ms,
+                       "timing": "host wall time of the public call (host results, device-to-host copies inside)"},
+            "e2e": {"value": total_q / (b_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": cs.summary()}
+    print(json.dumps(line), flush=True)
+    for ix in ixs:
+        ix.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +307,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-only", action="store_true")
+    ap.add_argument("--instances", type=int, default=64, help="angular_collection: number of join instances")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -235,6 +326,13 @@ def main():
 
     from paper_2603_16360_b300 import vj
     vj.load()
+    if args.workload == "angular_collection":
+        if rank == 0 and args.impl == "ours":
+            bench_collection(args, vj, torch)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     w = make_workload(args.workload, args.scale)
     target = w.target_matches
     t0 = time.perf_counter()

@@ -214,6 +214,24 @@ vj_status vj_join(vj_index *ix, float eps, int budget, vj_result **out);
 /* As vj_join, but the result arrays stay in device memory (on_device = 1). */
 vj_status vj_join_device(vj_index *ix, float eps, int budget, vj_result **out);
 
+/* n independent joins, instance i = vj_join(ixs[i], eps[i], 0) (Def. 1 for
+ * each pair of sets; the scalability study of Sec. 5 runs many instances of
+ * very different sizes).  The traversal passes of all instances run fused,
+ * one launch per pass over up to 64 instances of one kernel class (indexes
+ * whose padded dimensions fall in the same class share a launch); each
+ * result equals what vj_join gives for that instance alone.
+ *   ixs [n]: distinct built indexes (an index listed twice -> VJ_ERR_ARG).  A
+ *   predictor attached to several of them is shared safely (its inference is
+ *   serialised).  The call uses each index's stream and borrows the largest
+ *   index's traversal workspace.
+ *   eps [n] (host): per-instance thresholds, each > 0.
+ *   outs [n] (host): receives n host results, each freed by vj_result_free.
+ *   In each result's stats, ms_traverse is the time of the fused passes
+ *   (shared by all instances) and ms_sws is zero.
+ * All or nothing: on any failure every outs[i] is NULL and vj_last_error
+ * names the first failing instance.  n = 0 is a no-op. */
+vj_status vj_join_batch(vj_index **ixs, const float *eps, int n, vj_result **outs);
+
 /* Exact nested-loop join (Sec. 3.2) of the index's X and Q on the GPU, host
  * result.  Pairs whose FP32 distance lies within the FP32 rounding bound of
  * eps are re-decided in FP64. */

@@ -50,6 +50,8 @@
 // In-range decisions whose FP32 key lies within the FP32 rounding bound of eps
 // are re-decided in FP64.
 #include <float.h>
+#include <stdio.h>
+#include <string.h>
 
 #include "vj_device.cuh"
 #include "vj_internal.cuh"
@@ -399,12 +401,27 @@ __device__ __forceinline__ int lower_rank(const float* Lk, const int* Li, int n,
     return lo;
 }
 
+// per-warp statistics, flushed into the instance's counters
+struct JoinCounters {
+    long long dist = 0, exp = 0, adj = 0, hyb = 0, rechk = 0, spill = 0;
+};
+
+__device__ __forceinline__ void flush_counters(const JoinParams& P, JoinCounters& c) {
+    atomicAdd(P.ctr + C_DIST, (unsigned long long)c.dist);
+    atomicAdd(P.ctr + C_EXP, (unsigned long long)c.exp);
+    atomicAdd(P.ctr + C_ADJ, (unsigned long long)c.adj);
+    atomicAdd(P.ctr + C_HYB, (unsigned long long)c.hyb);
+    atomicAdd(P.ctr + C_RECHK, (unsigned long long)c.rechk);
+    atomicAdd(P.ctr + C_SPILL, (unsigned long long)c.spill);
+    c = JoinCounters();
+}
+
+// One query of one join pass (the pass is P.mode): ticket t of the pass's
+// dispatch order.  Returns true when this warp must stop taking tickets (a
+// device error was raised, or a parent it waits for was abandoned).
 template <int G, int NPL, int U>
-__global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
-    const int64_t gw = (int64_t)blockIdx.x * WPB + warp;
+__device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem* S, int64_t gw, int lane,
+                                           JoinCounters& cnt) {
     int32_t* wbase = P.wspace + gw * P.wstride;
     WarpSpace W;
     W.hA = wbase;
@@ -419,14 +436,9 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
     W.qi[1] = qbase + 3 * P.oqcap;
     const int g = lane & (G - 1);
     const int R = P.R;
-    long long c_dist = 0, c_exp = 0, c_adj = 0, c_hyb = 0, c_rechk = 0, c_spill = 0;
-
-    for (;;) {
-        int t = 0;
-        if (lane == 0)
-            t = (int)atomicAdd(P.ctr + (P.mode == 2 ? C_TICKET2 : P.mode == 3 ? C_TICKET3 : C_TICKET), 1ull);
-        t = __shfl_sync(VJ_FULL, t, 0);
-        if (t >= P.nq) break;
+    long long &c_dist = cnt.dist, &c_exp = cnt.exp, &c_adj = cnt.adj, &c_hyb = cnt.hyb, &c_rechk = cnt.rechk,
+              &c_spill = cnt.spill;
+    {
         const int qi = P.mode == 2 ? P.order[t] : P.order1[t];
         const int64_t qn = P.nx + qi;
 
@@ -500,7 +512,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 P.cout[qi] = best;
             }
             __syncwarp();
-            if (o != 2) continue;
+            if (o != 2) return false;
             // a re-run for this seed runs here, off the parent chain; its
             // result is staged and pass 3 commits it if the seed stays
             seedc = sc;
@@ -532,7 +544,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 }
             }
             sc = __shfl_sync(VJ_FULL, sc, 0);
-            if (sc == -2) break;
+            if (sc == -2) return true;
             int best, o;
             const bool same = sc == P.sca[qi];  // usually: pass 2 decided for this very seed
             if (same) {
@@ -554,7 +566,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     st_release(P.done + qi, 1);
                 }
                 __syncwarp();
-                continue;
+                return false;
             }
             if (o != 2) {
                 if (lane == 0) {
@@ -566,7 +578,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                     st_release(P.done + qi, 1);
                 }
                 __syncwarp();
-                continue;
+                return false;
             }
             // re-run from the start with the cached seed
             seedc = sc;
@@ -810,7 +822,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 P.steps[qi] = 0;
             }
             __syncwarp();
-            continue;
+            return false;
         }
         int expansions = 0;
         if (routed) {
@@ -1027,7 +1039,7 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
                 if (P.mode == 3) P.count2[qi] = 0;
                 else P.count[qi] = 0;
             }
-            break;
+            return true;
         }
 
         // ---- results into the pool
@@ -1052,14 +1064,75 @@ __global__ void __launch_bounds__(WPB * 32) k_join(JoinParams P) {
         }
         __syncwarp();
     }
-    if (lane == 0) {
-        atomicAdd(P.ctr + C_DIST, (unsigned long long)c_dist);
-        atomicAdd(P.ctr + C_EXP, (unsigned long long)c_exp);
-        atomicAdd(P.ctr + C_ADJ, (unsigned long long)c_adj);
-        atomicAdd(P.ctr + C_HYB, (unsigned long long)c_hyb);
-        atomicAdd(P.ctr + C_RECHK, (unsigned long long)c_rechk);
-        atomicAdd(P.ctr + C_SPILL, (unsigned long long)c_spill);
+    return false;
+}
+
+__device__ __forceinline__ int pass_ticket_slot(int mode) {
+    return mode == 2 ? C_TICKET2 : mode == 3 ? C_TICKET3 : C_TICKET;
+}
+
+// one join pass over one index: warps take queries from the pass's ticket
+template <int G, int NPL, int U>
+__global__ void __launch_bounds__(WPB * 32) k_join(const __grid_constant__ JoinParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
+    const int64_t gw = (int64_t)blockIdx.x * WPB + warp;
+    JoinCounters cnt;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(P.ctr + pass_ticket_slot(P.mode), 1ull);
+        t = __shfl_sync(VJ_FULL, t, 0);
+        if (t >= P.nq) break;
+        if (join_query<G, NPL, U>(P, t, S, gw, lane, cnt)) break;
     }
+    if (lane == 0) flush_counters(P, cnt);
+}
+
+// One join pass over up to JB_MAX independent indexes in a single launch (a
+// collection of join instances).  The tickets of all instances form one
+// sequence, instance after instance, each instance's part in its own dispatch
+// order, so a parent's ticket still precedes its children's (pass 3 waits on
+// parents of its own instance only, and a claimed ticket is always being
+// worked on by a running warp).  Each instance keeps its own counters, pool
+// and outputs; all share the warps' workspace.
+constexpr int JB_MAX = 64;
+struct JoinBatch {
+    JoinParams p[JB_MAX];
+    int64_t qstart[JB_MAX + 1];  // ticket offsets: instance i owns [qstart[i], qstart[i+1])
+    int n;
+    unsigned long long* ticket;  // one counter for this launch
+};
+static_assert(sizeof(JoinBatch) <= 32000, "JoinBatch must fit the kernel parameter space");
+
+template <int G, int NPL, int U>
+__global__ void __launch_bounds__(WPB * 32) k_join_multi(const __grid_constant__ JoinBatch B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
+    const int64_t gw = (int64_t)blockIdx.x * WPB + warp;
+    const int64_t total = B.qstart[B.n];
+    JoinCounters cnt;
+    int cur = -1;
+    for (;;) {
+        long long t = 0;
+        if (lane == 0) t = (long long)atomicAdd(B.ticket, 1ull);
+        t = __shfl_sync(VJ_FULL, t, 0);
+        if (t >= total) break;
+        int lo = 0, hi = B.n - 1;  // the instance: last i with qstart[i] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.qstart[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {
+            if (cur >= 0 && lane == 0) flush_counters(B.p[cur], cnt);
+            cnt = JoinCounters();
+            cur = lo;
+        }
+        if (join_query<G, NPL, U>(B.p[lo], (int)(t - B.qstart[lo]), S, gw, lane, cnt)) break;
+    }
+    if (cur >= 0 && lane == 0) flush_counters(B.p[cur], cnt);
 }
 
 // Dispatch order for passes without dependencies: longest expected work first
@@ -1118,9 +1191,15 @@ void launch_join_t(const JoinParams& P, int blocks, cudaStream_t st) {
 }
 
 template <int G, int NPL, int U>
-int blocks_for(int num_sms) {
+void launch_join_multi_t(const JoinBatch& B, int blocks, cudaStream_t st) {
     size_t smem = sizeof(WarpSmem) * WPB;
-    auto kern = k_join<G, NPL, U>;
+    k_join_multi<G, NPL, U><<<blocks, WPB * 32, smem, st>>>(B);
+    VJ_LAUNCH_CHECK();
+}
+
+template <class K>
+int blocks_for(K kern, int num_sms) {
+    size_t smem = sizeof(WarpSmem) * WPB;
     VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
@@ -1130,25 +1209,59 @@ int blocks_for(int num_sms) {
 
 // dispatch on the padded dimension (dp4 = dp / 4 float4 slots per vector)
 struct JoinDispatch {
+    int cls;  // template class: indexes of one class can share a multi-instance launch
     int blocks;
     void (*launch)(const JoinParams&, int, cudaStream_t);
+    int blocks_multi;
+    void (*launch_multi)(const JoinBatch&, int, cudaStream_t);
 };
 
-JoinDispatch pick(int dp4, int num_sms) {
-    if (dp4 <= 8) return {blocks_for<8, 1, 4>(num_sms), launch_join_t<8, 1, 4>};
-    if (dp4 <= 16) return {blocks_for<8, 2, 4>(num_sms), launch_join_t<8, 2, 4>};
-    if (dp4 <= 32) return {blocks_for<8, 4, 2>(num_sms), launch_join_t<8, 4, 2>};
-    if (dp4 <= 64) return {blocks_for<16, 4, 2>(num_sms), launch_join_t<16, 4, 2>};
-    if (dp4 <= 128) return {blocks_for<32, 4, 2>(num_sms), launch_join_t<32, 4, 2>};
-    if (dp4 <= 256) return {blocks_for<32, 8, 1>(num_sms), launch_join_t<32, 8, 1>};
-    if (dp4 <= 512) return {blocks_for<32, 16, 1>(num_sms), launch_join_t<32, 16, 1>};
-    return {blocks_for<32, 32, 1>(num_sms), launch_join_t<32, 32, 1>};
+template <int G, int NPL, int U>
+JoinDispatch dispatch_t(int cls, int num_sms) {
+    return {cls, blocks_for(k_join<G, NPL, U>, num_sms), launch_join_t<G, NPL, U>,
+            blocks_for(k_join_multi<G, NPL, U>, num_sms), launch_join_multi_t<G, NPL, U>};
 }
 
-}  // namespace
+constexpr int JOIN_CLASSES = 8;
 
-// ------------------------------------------------------------------ host
-void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out) {
+JoinDispatch pick(int dp4, int num_sms) {
+    if (dp4 <= 8) return dispatch_t<8, 1, 4>(0, num_sms);
+    if (dp4 <= 16) return dispatch_t<8, 2, 4>(1, num_sms);
+    if (dp4 <= 32) return dispatch_t<8, 4, 2>(2, num_sms);
+    if (dp4 <= 64) return dispatch_t<16, 4, 2>(3, num_sms);
+    if (dp4 <= 128) return dispatch_t<32, 4, 2>(4, num_sms);
+    if (dp4 <= 256) return dispatch_t<32, 8, 1>(5, num_sms);
+    if (dp4 <= 512) return dispatch_t<32, 16, 1>(6, num_sms);
+    return dispatch_t<32, 32, 1>(7, num_sms);
+}
+
+// Host state of one join between its phases: setup (prologue, buffers,
+// parameters), the traversal passes (alone or inside a multi-instance
+// launch), and the finish (brute-force rows, CSR, statistics).
+struct JoinRun {
+    vj_index* ix = nullptr;
+    float eps = 0.f;
+    int budget = 0;
+    bool learned = false, soft = false;
+    double ms_pro = 0.0;
+    JoinParams P;
+    JoinDispatch jd;
+    int64_t wstride = 0, vwords = 0;  // this join's workspace needs per warp
+    unsigned long long hc[16];
+    int64_t launches = 0;
+    float t_trav = 0.f, t_sws[3] = {0.f, 0.f, 0.f};
+    ~JoinRun() {
+        // the plan the learned prologue set lives for this join only
+        if (learned && ix) {
+            ix->has_route = false;
+            ix->has_beam = false;
+            ix->nrouted = 0;
+        }
+    }
+};
+
+void join_setup(JoinRun& r) {
+    vj_index* ix = r.ix;
     cudaStream_t s = ix->stream;
     const int64_t nq = ix->nq;
     VJ_REQUIRE(ix->d <= 4096 && ix->dp / 4 <= 1024, VJ_ERR_ARG, "d too large for the join kernel");
@@ -1158,34 +1271,22 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     VJ_REQUIRE(ix->p.work_sharing >= 0 && ix->p.work_sharing <= 3, VJ_ERR_ARG, "bad work_sharing");
 
     // learned prologue (features -> predictor -> per-query plan) in place of
-    // the d1/d2 rule; the plan it sets lives for this join only
-    double ms_pro = 0.0;
-    const bool learned = ix->p.learned != 0;
-    if (learned) {
+    // the d1/d2 rule
+    r.learned = ix->p.learned != 0;
+    if (r.learned) {
         cudaEvent_t p0, p1;
         VJ_CUDA(cudaEventCreate(&p0));
         VJ_CUDA(cudaEventCreate(&p1));
         VJ_CUDA(cudaEventRecord(p0, s));
-        vj_learned_prologue(ix, eps);
+        vj_learned_prologue(ix, r.eps);
         VJ_CUDA(cudaEventRecord(p1, s));
         VJ_CUDA(cudaEventSynchronize(p1));
         float t = 0.f;
         VJ_CUDA(cudaEventElapsedTime(&t, p0, p1));
-        ms_pro = t;
+        r.ms_pro = t;
         cudaEventDestroy(p0);
         cudaEventDestroy(p1);
     }
-    struct PlanReset {
-        vj_index* ix;
-        bool on;
-        ~PlanReset() {
-            if (on) {
-                ix->has_route = false;
-                ix->has_beam = false;
-                ix->nrouted = 0;
-            }
-        }
-    } plan_reset{ix, learned};
 
     ix->cache.ensure(nq, s);
     ix->steps.ensure(nq, s);
@@ -1207,35 +1308,24 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
-    JoinDispatch jd = pick(ix->dp / 4, ix->num_sms);
-    const int64_t warps = (int64_t)jd.blocks * WPB;
+    r.jd = pick(ix->dp / 4, ix->num_sms);
     // global visited regions: up to 2^17 slots (64K visited nodes per query),
     // no larger than needed for the whole node set
     int gmax = 1 << 17;
     while (gmax > GCAP0 && (int64_t)gmax / 4 >= ix->n) gmax >>= 1;
     if (gmax < GCAP0) gmax = GCAP0;
     const int grcap = gmax / 2;
-    const int hbeam = budget > 0 ? budget : ix->p.hybrid_beam;
+    const int hbeam = r.budget > 0 ? r.budget : ix->p.hybrid_beam;
     const int oqcap = std::max(hbeam, ix->has_beam ? ix->plan_max_beam : 0) + 2;
-    const int64_t wstride = ((int64_t)2 * gmax + 2 * grcap + 4 * oqcap + 31) / 32 * 32;
-    if (ix->wspace_warps < warps || ix->wspace.n < (size_t)(warps * wstride)) {
-        ix->wspace.free_(s);
-        ix->wspace.alloc((size_t)(warps * wstride), s);
-        ix->wspace_warps = warps;
-    }
-    const int64_t vwords = (ix->n + 31) / 32;
-    if (ix->vbits.n < (size_t)(warps * vwords)) {
-        ix->vbits.free_(s);
-        ix->vbits.alloc((size_t)(warps * vwords), s);
-        VJ_CUDA(cudaMemsetAsync(ix->vbits.p, 0, (size_t)(warps * vwords) * sizeof(uint32_t), s));
-    }
+    r.wstride = ((int64_t)2 * gmax + 2 * grcap + 4 * oqcap + 31) / 32 * 32;
+    r.vwords = (ix->n + 31) / 32;
     if (ix->pool_id.n == 0) {
         int64_t cap0 = std::max<int64_t>(nq * 64, 1 << 16);
         ix->pool_id.alloc(cap0, s);
         ix->pool_d.alloc(cap0, s);
     }
 
-    JoinParams P;
+    JoinParams& P = r.P;
     P.vec = ix->vec.p;
     P.invn = ix->invn.p;
     P.adj = ix->adj.p;
@@ -1283,78 +1373,64 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     P.force = ix->p.force_hybrid;
     P.hbeam = hbeam;
     P.conv = ix->p.conv_threshold;
-    P.eps_key = ix->metric == VJ_L2 ? eps * eps : eps;
+    P.eps_key = ix->metric == VJ_L2 ? r.eps * r.eps : r.eps;
     // FP32 keys: L2 squared distance by direct differences has relative error
     // below (dp+2)u; cosine key absolute error below (dp+4)u (unit vectors)
     P.band = 2.0f * (float)(ix->dp + 4) * VJ_F32_U * (ix->metric == VJ_L2 ? 1.0f : 4.0f) + 1e-6f;
     P.tie_tol = P.band;
-    P.eps64 = (double)eps;
+    P.eps64 = (double)r.eps;
     P.cache = ix->cache.p;
     P.steps = ix->steps.p;
     P.hyb = ix->hyb.p;
     P.count = ix->count.p;
     P.seg = ix->seg.p;
-    P.wspace = ix->wspace.p;
-    P.vbits = ix->vbits.p;
-    P.vwords = vwords;
-    P.wstride = wstride;
     P.gmax = gmax;
     P.grcap = grcap;
     P.oqcap = oqcap;
     P.ctr = ix->ctr.p;
     P.spin_limit = 1ll << 24;  // ~seconds with back-off; then VJ_DERR_WAIT_TIMEOUT
+    r.soft = ix->p.work_sharing == VJ_WS_SOFT;
+}
 
-    cudaEvent_t e0, e1, e2, ep[2];
-    VJ_CUDA(cudaEventCreate(&ep[0]));
-    VJ_CUDA(cudaEventCreate(&ep[1]));
-    VJ_CUDA(cudaEventCreate(&e0));
-    VJ_CUDA(cudaEventCreate(&e1));
-    VJ_CUDA(cudaEventCreate(&e2));
-    unsigned long long hc[16];
-    int64_t launches = 0;
-    const bool soft = ix->p.work_sharing == VJ_WS_SOFT;
-    for (int attempt = 0; attempt < 3; attempt++) {
-        launches++;
-        P.pool_id = ix->pool_id.p;
-        P.pool_d = ix->pool_d.p;
-        P.pool_cap = (int64_t)ix->pool_id.n;
-        VJ_CUDA(cudaMemsetAsync(ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
-        if (soft) VJ_CUDA(cudaMemsetAsync(ix->done.p, 0, nq * sizeof(int32_t), s));
-        VJ_CUDA(cudaEventRecord(e0, s));
-        if (soft) {
-            // two launches: speculative pass, then the parent-ordered fix-up
-            P.mode = 1;
-            jd.launch(P, jd.blocks, s);
-            VJ_CUDA(cudaEventRecord(ep[0], s));
-            P.mode = 3;
-            jd.launch(P, jd.blocks, s);
-            VJ_CUDA(cudaEventRecord(ep[1], s));
-            P.mode = 2;
-            jd.launch(P, jd.blocks, s);
-            launches += 2;
-        } else {
-            P.mode = 0;
-            jd.launch(P, jd.blocks, s);
-        }
-        VJ_CUDA(cudaEventRecord(e1, s));
-        VJ_CUDA(cudaMemcpyAsync(hc, ix->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        VJ_CUDA(cudaStreamSynchronize(s));
-        if (hc[C_ERR] != 0) break;
-        if ((int64_t)hc[C_POOL] <= P.pool_cap) break;
-        // pool too small: grow and run again (the join is deterministic)
-        int64_t cap = (int64_t)hc[C_POOL] + hc[C_POOL] / 4 + 1024;
-        ix->pool_id.free_(s);
-        ix->pool_d.free_(s);
-        ix->pool_id.alloc(cap, s);
-        ix->pool_d.alloc(cap, s);
+// the warps' workspace (visited lists, result spill, out-range queues) and
+// visited bitmaps, owned by `owner` and grown to `warps` warps of the given
+// per-warp sizes
+void bind_workspace(vj_index* owner, int64_t warps, int64_t wstride, int64_t vwords, JoinParams& P) {
+    cudaStream_t s = owner->stream;
+    if (owner->wspace_warps < warps || owner->wspace.n < (size_t)(warps * wstride)) {
+        owner->wspace.free_(s);
+        owner->wspace.alloc((size_t)(warps * wstride), s);
+        owner->wspace_warps = warps;
     }
+    if (owner->vbits.n < (size_t)(warps * vwords)) {
+        owner->vbits.free_(s);
+        owner->vbits.alloc((size_t)(warps * vwords), s);
+        VJ_CUDA(cudaMemsetAsync(owner->vbits.p, 0, (size_t)(warps * vwords) * sizeof(uint32_t), s));
+    }
+    P.wspace = owner->wspace.p;
+    P.wstride = wstride;
+    P.vbits = owner->vbits.p;
+    P.vwords = vwords;
+}
+
+void bind_pool(JoinRun& r) {
+    r.P.pool_id = r.ix->pool_id.p;
+    r.P.pool_d = r.ix->pool_d.p;
+    r.P.pool_cap = (int64_t)r.ix->pool_id.n;
+}
+
+// counters and publish flags of one attempt
+void reset_attempt(JoinRun& r, cudaStream_t s) {
+    VJ_CUDA(cudaMemsetAsync(r.ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
+    if (r.soft) VJ_CUDA(cudaMemsetAsync(r.ix->done.p, 0, r.ix->nq * sizeof(int32_t), s));
+}
+
+// after an attempt: true when the pool overflowed (then it is grown: run
+// again, the join is deterministic); throws on a device error
+bool pool_overflowed(JoinRun& r) {
+    const unsigned long long* hc = r.hc;
     if (hc[C_ERR] != 0) {
-        cudaEventDestroy(ep[0]);
-        cudaEventDestroy(ep[1]);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaEventDestroy(e2);
-        int code = (int)hc[C_ERR];
+        const int code = (int)hc[C_ERR];
         if (code == VJ_DERR_WAIT_TIMEOUT) {
             vj_set_error("join: a wait for a work-sharing parent timed out");
             throw VjError{VJ_ERR_TIMEOUT};
@@ -1365,6 +1441,36 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
                                                         : "queue overflow");
         throw VjError{VJ_ERR_STATE};
     }
+    if ((int64_t)hc[C_POOL] <= r.P.pool_cap) return false;
+    vj_index* ix = r.ix;
+    const int64_t cap = (int64_t)hc[C_POOL] + hc[C_POOL] / 4 + 1024;
+    ix->pool_id.free_(ix->stream);
+    ix->pool_d.free_(ix->stream);
+    ix->pool_id.alloc(cap, ix->stream);
+    ix->pool_d.alloc(cap, ix->stream);
+    return true;
+}
+
+struct Events {
+    cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    Events() {
+        for (auto& x : e) VJ_CUDA(cudaEventCreate(&x));
+    }
+    ~Events() {
+        for (auto& x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+// the brute-force rows of routed queries, the CSR and the statistics; the
+// traversal's counters are in r.hc and its times in r.t_trav / r.t_sws
+void join_finish(JoinRun& r, vj_stats* st, int64_t* nnz_out) {
+    vj_index* ix = r.ix;
+    cudaStream_t s = ix->stream;
+    const int64_t nq = ix->nq;
+    const unsigned long long* hc = r.hc;
+    Events ev;
+    VJ_CUDA(cudaEventRecord(ev.e[0], s));
     int64_t nnz = (int64_t)hc[C_POOL];
 
     // ---- brute-force route: rows of the routed queries from the tensor-core
@@ -1376,10 +1482,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         DBuf<int32_t> sid;
         DBuf<float> sd;
         int64_t snnz = 0;
-        vj_scan_rows_csr(ix, ix->routed.p, ix->nrouted, eps, soff, sid, sd, &snnz, &ms_route);
+        vj_scan_rows_csr(ix, ix->routed.p, ix->nrouted, r.eps, soff, sid, sd, &snnz, &ms_route);
         ms_scan = ix->last_scan_ms;
         scand = ix->last_scan_cand;
-        launches += 8;
+        r.launches += 8;
         if (nnz + snnz > (int64_t)ix->pool_id.n) {
             DBuf<int32_t> nid;
             DBuf<float> nd;
@@ -1417,47 +1523,191 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     vj_exclusive_scan_i32_to_i64(ix->count.p, ix->offsets.p, nq, ix);
     vj_segment_sort_copy(ix->seg.p, ix->count.p, ix->offsets.p, ix->pool_id.p, ix->pool_d.p, ix->out_id.p,
                          ix->out_d.p, nq, ix);
-    VJ_CUDA(cudaEventRecord(e2, s));
+    VJ_CUDA(cudaEventRecord(ev.e[1], s));
     // pairs in the result (the pool also holds rows that a pass-2 re-run replaced)
     VJ_CUDA(cudaMemcpyAsync(&nnz, ix->offsets.p + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    VJ_CUDA(cudaEventSynchronize(e2));
     VJ_CUDA(cudaStreamSynchronize(s));
-    float t_trav = 0.f, t_csr = 0.f;
-    VJ_CUDA(cudaEventElapsedTime(&t_trav, e0, e1));
-    VJ_CUDA(cudaEventElapsedTime(&t_csr, e1, e2));
-    st->ms_sws[0] = st->ms_sws[1] = st->ms_sws[2] = 0.0;
-    if (soft) {
-        float a = 0.f, b = 0.f, c = 0.f;
-        VJ_CUDA(cudaEventElapsedTime(&a, e0, ep[0]));
-        VJ_CUDA(cudaEventElapsedTime(&b, ep[0], ep[1]));
-        VJ_CUDA(cudaEventElapsedTime(&c, ep[1], e1));
-        st->ms_sws[0] = a;
-        st->ms_sws[1] = b;
-        st->ms_sws[2] = c;
-    }
-    cudaEventDestroy(ep[0]);
-    cudaEventDestroy(ep[1]);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
+    float t_csr = 0.f;
+    VJ_CUDA(cudaEventElapsedTime(&t_csr, ev.e[0], ev.e[1]));
 
+    st->ms_sws[0] = r.t_sws[0];
+    st->ms_sws[1] = r.t_sws[1];
+    st->ms_sws[2] = r.t_sws[2];
     st->dist_computations = (int64_t)hc[C_DIST];
     st->expansions = (int64_t)hc[C_EXP];
     st->adj_rows_read = (int64_t)hc[C_ADJ];
     st->hybrid_queries = (int64_t)hc[C_HYB];
     st->rechecks = (int64_t)hc[C_RECHK];
     st->spill_queries = (int64_t)hc[C_SPILL];
-    st->ms_traverse = t_trav;
+    st->ms_traverse = r.t_trav;
     st->ms_csr = std::max(0.0, (double)t_csr - ms_route);
     st->ms_route = ms_route;
-    st->ms_prologue = ms_pro;
+    st->ms_prologue = r.ms_pro;
     st->sws_restarts = (int64_t)hc[C_RESTART];
-    st->ms_total = ms_pro + t_trav + t_csr;
+    st->ms_total = r.ms_pro + r.t_trav + t_csr;
     ix->have_costs = true;  // this join's visited counts order the next one
     // algorithmic bytes: one vector per distance, one adjacency row per row read
     st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
-    st->kernel_launches = launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort
+    st->kernel_launches = r.launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort
     st->ms_scan = ms_scan;
     st->scan_candidates = scand;
     *nnz_out = nnz;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out) {
+    JoinRun r;
+    r.ix = ix;
+    r.eps = eps;
+    r.budget = budget;
+    join_setup(r);
+    cudaStream_t s = ix->stream;
+    JoinParams& P = r.P;
+    bind_workspace(ix, (int64_t)r.jd.blocks * WPB, r.wstride, r.vwords, P);
+
+    Events ev;  // e[0] start, e[1] after pass 1, e[2] after pass 2, e[3] end
+    for (int attempt = 0; attempt < 3; attempt++) {
+        r.launches++;
+        bind_pool(r);
+        reset_attempt(r, s);
+        VJ_CUDA(cudaEventRecord(ev.e[0], s));
+        if (r.soft) {
+            // speculative pass, parallel seed decisions, parent-ordered commit
+            P.mode = 1;
+            r.jd.launch(P, r.jd.blocks, s);
+            VJ_CUDA(cudaEventRecord(ev.e[1], s));
+            P.mode = 3;
+            r.jd.launch(P, r.jd.blocks, s);
+            VJ_CUDA(cudaEventRecord(ev.e[2], s));
+            P.mode = 2;
+            r.jd.launch(P, r.jd.blocks, s);
+            r.launches += 2;
+        } else {
+            P.mode = 0;
+            r.jd.launch(P, r.jd.blocks, s);
+        }
+        VJ_CUDA(cudaEventRecord(ev.e[3], s));
+        VJ_CUDA(cudaMemcpyAsync(r.hc, ix->ctr.p, sizeof(r.hc), cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        if (!pool_overflowed(r)) break;
+    }
+    VJ_REQUIRE((int64_t)r.hc[C_POOL] <= r.P.pool_cap, VJ_ERR_STATE, "join: result pool still too small");
+    VJ_CUDA(cudaEventElapsedTime(&r.t_trav, ev.e[0], ev.e[3]));
+    if (r.soft) {
+        VJ_CUDA(cudaEventElapsedTime(&r.t_sws[0], ev.e[0], ev.e[1]));
+        VJ_CUDA(cudaEventElapsedTime(&r.t_sws[1], ev.e[1], ev.e[2]));
+        VJ_CUDA(cudaEventElapsedTime(&r.t_sws[2], ev.e[2], ev.e[3]));
+    }
+    join_finish(r, st, nnz_out);
+}
+
+// Joins of several indexes with their traversal passes fused: every pass runs
+// as one launch over all instances of one kernel class (k_join_multi), so
+// that small instances fill the GPU together.  Setup and finish run per
+// instance, each on its own index's stream, through `par_for`.
+void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* st, int64_t* nnz_out,
+                       const vj_par_for& par_for) {
+    if (n <= 0) return;
+    std::vector<JoinRun> runs(n);
+    for (int i = 0; i < n; i++) {
+        runs[i].ix = ixs[i];
+        runs[i].eps = eps[i];
+        runs[i].budget = 0;
+    }
+    par_for(n, [&](int i) { join_setup(runs[i]); });
+
+    // the workspace is the largest instance's, sized for the widest needs of all
+    int owner = 0;
+    int64_t warps = 0, wstride = 0, vwords = 0;
+    for (int i = 0; i < n; i++) {
+        warps = std::max<int64_t>(warps, (int64_t)runs[i].jd.blocks_multi * WPB);
+        wstride = std::max(wstride, runs[i].wstride);
+        vwords = std::max(vwords, runs[i].vwords);
+        if (ixs[i]->n > ixs[owner]->n) owner = i;
+    }
+    cudaStream_t s = ixs[owner]->stream;
+    for (int i = 0; i < n; i++) VJ_CUDA(cudaStreamSynchronize(ixs[i]->stream));
+    for (int i = 0; i < n; i++) bind_workspace(ixs[owner], warps, wstride, vwords, runs[i].P);
+    DBuf<unsigned long long> ticket;
+    ticket.alloc(1, s);
+    std::vector<unsigned long long> hc((size_t)n * 16);
+    std::vector<char> pending(n, 1);
+    Events ev;
+    static const int soft_modes[3] = {1, 3, 2};  // speculative pass, decisions, commit
+    for (int attempt = 0; attempt < 3; attempt++) {
+        std::vector<int> todo;
+        for (int i = 0; i < n; i++)
+            if (pending[i]) todo.push_back(i);
+        if (todo.empty()) break;
+        VJ_CUDA(cudaEventRecord(ev.e[0], s));
+        for (int cls = 0; cls < JOIN_CLASSES; cls++) {
+            std::vector<int> members;  // largest first: their long queries start early
+            for (int i : todo)
+                if (runs[i].jd.cls == cls) members.push_back(i);
+            std::stable_sort(members.begin(), members.end(),
+                             [&](int a, int b) { return ixs[a]->nq > ixs[b]->nq; });
+            for (size_t c0 = 0; c0 < members.size(); c0 += JB_MAX) {
+                const int nb = (int)std::min<size_t>(JB_MAX, members.size() - c0);
+                JoinBatch B;
+                B.n = nb;
+                B.ticket = ticket.p;
+                bool soft = false;
+                for (int k = 0; k < nb; k++) {
+                    JoinRun& r = runs[members[c0 + k]];
+                    r.launches++;
+                    bind_pool(r);
+                    reset_attempt(r, s);
+                    B.p[k] = r.P;
+                    soft |= r.soft;
+                }
+                // soft-sharing instances run passes 1, 2 and 3; the others run
+                // their single pass in the first launch and have no tickets in
+                // the later ones
+                const int npass = soft ? 3 : 1;
+                const JoinDispatch& jd = runs[members[c0]].jd;
+                for (int ps = 0; ps < npass; ps++) {
+                    B.qstart[0] = 0;
+                    for (int k = 0; k < nb; k++) {
+                        JoinRun& r = runs[members[c0 + k]];
+                        B.p[k].mode = r.soft ? soft_modes[ps] : 0;
+                        const int64_t qk = (r.soft || ps == 0) ? r.ix->nq : 0;
+                        B.qstart[k + 1] = B.qstart[k] + qk;
+                        if (ps > 0 && r.soft) r.launches++;
+                    }
+                    VJ_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned long long), s));
+                    jd.launch_multi(B, jd.blocks_multi, s);
+                }
+            }
+        }
+        VJ_CUDA(cudaEventRecord(ev.e[3], s));
+        for (int i : todo)
+            VJ_CUDA(cudaMemcpyAsync(&hc[(size_t)i * 16], ixs[i]->ctr.p, 16 * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        float t = 0.f;
+        VJ_CUDA(cudaEventElapsedTime(&t, ev.e[0], ev.e[3]));
+        for (int i : todo) {
+            JoinRun& r = runs[i];
+            memcpy(r.hc, &hc[(size_t)i * 16], sizeof(r.hc));
+            r.t_trav += t;
+            try {
+                pending[i] = pool_overflowed(r) ? 1 : 0;
+            } catch (const VjError&) {
+                char msg[900];
+                snprintf(msg, sizeof(msg), "%s", vj_last_error());
+                vj_set_error("instance %d: %s", i, msg);
+                ticket.free_(s);
+                throw;
+            }
+        }
+    }
+    ticket.free_(s);
+    for (int i = 0; i < n; i++)
+        VJ_REQUIRE(!pending[i], VJ_ERR_STATE, "instance %d: join result pool still too small", i);
+    // the instances' streams continue after the fused passes
+    VJ_CUDA(cudaEventRecord(ev.e[4], s));
+    for (int i = 0; i < n; i++) VJ_CUDA(cudaStreamWaitEvent(ixs[i]->stream, ev.e[4], 0));
+    par_for(n, [&](int i) { join_finish(runs[i], st + i, nnz_out + i); });
 }

@@ -11,6 +11,7 @@
 // inputs before the first layer (kept with the weights).
 #include <float.h>
 
+#include <mutex>
 #include <numeric>
 #include <random>
 
@@ -34,6 +35,9 @@ struct vj_mlp {
     // BF16 operands of the tensor-core inference path
     DBuf<__nv_bfloat16> xbf, w1bf, w2bf;
     DBuf<int> err;
+    // Serialises inference when one predictor serves indexes joined on
+    // concurrent host threads (the scratch above is per predictor).
+    std::mutex fwd_mu;
 };
 
 namespace {
@@ -566,8 +570,9 @@ void forward_tc(vj_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s) 
 // (h1 multiple of 64, h2 multiple of 16, both <= 256), else FP32
 void vj_mlp_forward_device(vj_mlp* m, const float* x, int64_t n, float* y_out, cudaStream_t s) {
     if (n <= 0) return;
+    std::lock_guard<std::mutex> lk(m->fwd_mu);
     if (tc_shape_ok(m)) {
-        forward_tc(m, x, n, y_out, s);
+        forward_tc(m, x, n, y_out, s);  // ends with a stream synchronize
         return;
     }
     cudaStream_t keep = m->stream;
@@ -575,6 +580,7 @@ void vj_mlp_forward_device(vj_mlp* m, const float* x, int64_t n, float* y_out, c
     forward(m, x, n, true);
     VJ_CUDA(cudaMemcpyAsync(y_out, m->y.p, (size_t)n * 2 * sizeof(float), cudaMemcpyDeviceToDevice, s));
     m->stream = keep;
+    VJ_CUDA(cudaStreamSynchronize(s));  // the scratch is free for the next caller
 }
 int vj_mlp_din(const vj_mlp* m) { return m->din; }
 

@@ -7,10 +7,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
+#include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "vj_internal.cuh"
 
@@ -383,6 +388,93 @@ extern "C" vj_status vj_join(vj_index* ix, float eps, int budget, vj_result** ou
 
 extern "C" vj_status vj_join_device(vj_index* ix, float eps, int budget, vj_result** out) {
     return join_impl(ix, eps, budget, out, true);
+}
+
+// Many independent joins (a collection of instances of very different
+// sizes).  One instance rarely fills 148 SMs, so the traversal passes of all
+// instances run fused, one launch per pass over every instance
+// (vj_run_join_multi); the per-instance setup (prologue, buffers) and finish
+// (brute-force rows, CSR, result copy) run on up to BATCH_WORKERS host
+// threads, each instance on its own index's stream.  Each instance's result
+// is the one vj_join gives for it alone.
+static constexpr int BATCH_WORKERS = 8;
+
+// fn(0..n-1) on up to BATCH_WORKERS threads; rethrows the lowest failing
+// index's error (as "instance i: ...") after all calls ended
+static void batch_par_for(int n, const std::function<void(int)>& fn) {
+    int dev = 0;
+    VJ_CUDA(cudaGetDevice(&dev));
+    std::vector<vj_status> st(n, VJ_OK);
+    std::vector<std::string> msg(n);
+    std::atomic<int> next{0};
+    auto work = [&] {
+        const bool dev_ok = cudaSetDevice(dev) == cudaSuccess;
+        for (int i; (i = next.fetch_add(1)) < n;) {
+            if (!dev_ok) {
+                st[i] = VJ_ERR_CUDA;
+                msg[i] = "cudaSetDevice failed on a worker thread";
+                continue;
+            }
+            st[i] = guarded([&] { fn(i); });
+            if (st[i] != VJ_OK) msg[i] = vj_last_error();
+        }
+    };
+    const int nw = std::min(n, BATCH_WORKERS);
+    std::vector<std::thread> pool;
+    pool.reserve(std::max(nw - 1, 0));
+    for (int t = 1; t < nw; t++) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < n; i++)
+        if (st[i] != VJ_OK) {
+            vj_set_error("instance %d: %s", i, msg[i].c_str());
+            throw VjError{st[i]};
+        }
+}
+
+extern "C" vj_status vj_join_batch(vj_index** ixs, const float* eps, int n, vj_result** outs) {
+    return guarded([&] {
+        VJ_REQUIRE(n >= 0, VJ_ERR_ARG, "n must be >= 0");
+        if (n == 0) return;
+        VJ_REQUIRE(ixs != nullptr && eps != nullptr && outs != nullptr, VJ_ERR_ARG, "NULL argument");
+        for (int i = 0; i < n; i++) outs[i] = nullptr;
+        for (int i = 0; i < n; i++) {
+            VJ_REQUIRE(ixs[i] != nullptr, VJ_ERR_ARG, "index %d is NULL", i);
+            VJ_REQUIRE(eps[i] > 0.f && eps[i] == eps[i], VJ_ERR_ARG, "eps[%d] must be > 0", i);
+        }
+        std::vector<vj_index*> uniq(ixs, ixs + n);
+        std::sort(uniq.begin(), uniq.end());
+        VJ_REQUIRE(std::adjacent_find(uniq.begin(), uniq.end()) == uniq.end(), VJ_ERR_ARG,
+                   "an index appears twice in the batch");
+        std::vector<vj_stats> st(n);
+        memset(st.data(), 0, sizeof(vj_stats) * n);
+        std::vector<int64_t> nnz(n, 0);
+        std::vector<vj_result*> res(n, nullptr);
+        try {
+            vj_run_join_multi(ixs, eps, n, st.data(), nnz.data(), batch_par_for);
+            batch_par_for(n, [&](int i) {
+                vj_index* ix = ixs[i];
+                cudaStream_t s = ix->stream;
+                vj_result* r = new_result(ix->nq, nnz[i], false, s);
+                res[i] = r;
+                const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+                VJ_CUDA(cudaMemcpyAsync(r->offsets, ix->offsets.p, (ix->nq + 1) * sizeof(int64_t), k, s));
+                if (nnz[i] > 0) {
+                    VJ_CUDA(cudaMemcpyAsync(r->ids, ix->out_id.p, nnz[i] * sizeof(int32_t), k, s));
+                    VJ_CUDA(cudaMemcpyAsync(r->dists, ix->out_d.p, nnz[i] * sizeof(float), k, s));
+                }
+                VJ_CUDA(cudaMemcpyAsync(r->steps, ix->steps.p, ix->nq * sizeof(int32_t), k, s));
+                VJ_CUDA(cudaMemcpyAsync(r->cache, ix->cache.p, ix->nq * sizeof(int32_t), k, s));
+                VJ_CUDA(cudaMemcpyAsync(r->hybrid, ix->hyb.p, ix->nq, k, s));
+                VJ_CUDA(cudaStreamSynchronize(s));
+                r->stats = st[i];
+            });
+        } catch (...) {
+            for (auto* r : res) vj_result_free(r);
+            throw;
+        }
+        for (int i = 0; i < n; i++) outs[i] = res[i];
+    });
 }
 
 extern "C" vj_status vj_join_exact(vj_index* ix, float eps, vj_result** out) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -189,6 +190,12 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
                       DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
+// joins of n distinct indexes (default budget) with fused traversal launches;
+// par(n, fn) runs fn(0..n-1), possibly on several host threads, and throws if
+// any call threw
+using vj_par_for = std::function<void(int, const std::function<void(int)>&)>;
+void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* st, int64_t* nnz_out,
+                       const vj_par_for& par);
 
 // tensor-core (tcgen05) BF16 scan of query rows against all data rows:
 // candidate (query index, data id) pairs, exact after re-check

@@ -137,15 +137,16 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
 
 
 // ---------------------------------------------------------------- host
+// Looked up once per process; the function-local static makes the first call
+// thread-safe (joins of several indexes run on concurrent host threads).
 inline PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
         VJ_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
         VJ_REQUIRE(q == cudaDriverEntryPointSuccess && p, VJ_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
     return fn;
 }
 

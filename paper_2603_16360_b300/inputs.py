@@ -16,6 +16,16 @@ project's benchmark configurations):
                     0, 255)); 100,000 queries, 90 % from the same mixture, 10 %
                     from 256 fresh centres shifted by +64 (then clipped).
                     ``scale`` shrinks both counts (same recipe) for tests.
+* ``angular_instance`` / ``angular_collection``
+                    a collection of independent join instances of very
+                    different sizes (the scalability study's shape): |X|
+                    log-uniform in [1e4, 2e6], |Q| log-uniform in [1e3, 2e5]
+                    clipped to |X|, d = 100 unit vectors (cosine), 64 clusters
+                    per instance (centres uniform on the sphere, points
+                    normalise(mu + N(0, 0.07^2 I))), 10 % of the queries from 64
+                    fresh centres; a target of U{5..50} matches per query.
+                    The size ranges are parameters, so tests draw small
+                    collections from the same recipe.
 """
 from __future__ import annotations
 
@@ -105,3 +115,34 @@ def uniform_small(seed: int, nx: int, nq: int, d: int, metric: int = 0, degree: 
         X /= np.linalg.norm(X, axis=1, keepdims=True)
         Q /= np.linalg.norm(Q, axis=1, keepdims=True)
     return Workload("uniform_small", X, Q, np.zeros(nq, bool), metric, degree, knn_k, 5.0, seed)
+
+
+def _unit(a):
+    return (a / np.linalg.norm(a, axis=1, keepdims=True)).astype(np.float32)
+
+
+def angular_instance(seed: int, i: int, nx_range=(1e4, 2e6), nq_range=(1e3, 2e5), d: int = 100,
+                     k: int = 64, sigma: float = 0.07, ood_frac: float = 0.10) -> Workload:
+    """Instance i of an angular collection (a pure function of seed and i)."""
+    rng = np.random.default_rng([seed, i])
+    lx = rng.uniform(np.log(nx_range[0]), np.log(nx_range[1]))
+    lq = rng.uniform(np.log(nq_range[0]), np.log(nq_range[1]))
+    nx = int(round(np.exp(lx)))
+    nq = min(int(round(np.exp(lq))), nx)
+    target = float(rng.integers(5, 51))
+    centres = _unit(rng.standard_normal((k, d)))
+    X = _unit(_mixture(rng, nx, centres, sigma))
+    n_ood = int(round(nq * ood_frac))
+    Qi = _unit(_mixture(rng, nq - n_ood, centres, sigma))
+    Qo = _unit(_mixture(rng, n_ood, _unit(rng.standard_normal((k, d))), sigma))
+    Q = np.concatenate([Qi, Qo]).astype(np.float32)
+    ood = np.zeros(nq, bool)
+    ood[nq - n_ood:] = True
+    perm = rng.permutation(nq)
+    return Workload(f"angular_{i}", X, Q[perm].copy(), ood[perm].copy(), 1, 32, 64, target, seed)
+
+
+def angular_collection(seed: int = 1239, n: int = 64, **kw):
+    """The n instances of an angular collection, generated one at a time."""
+    for i in range(n):
+        yield angular_instance(seed, i, **kw)

@@ -25,7 +25,7 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_mlp_train", "vj_mlp_predict", "vj_mlp_free", "vj_features", "vj_attach_predictor",
            "vj_predictor_outputs",
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
-           "vj_join_device", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
+           "vj_join_device", "vj_join_batch", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
@@ -111,6 +111,8 @@ def load():
     for fn in ("vj_join", "vj_join_device"):
         getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
         getattr(lib, fn).restype = I
+    lib.vj_join_batch.argtypes = [P, P, I, P]
+    lib.vj_join_batch.restype = I
     lib.vj_join_exact.argtypes = [P, C.c_float, C.POINTER(C.POINTER(vj_result))]
     lib.vj_join_exact.restype = I
     lib.vj_join_exact_noalloc.argtypes = [P, I64, P, I64, I, I, C.c_float, P, P, P, I64, C.POINTER(C.c_int64), P]
@@ -410,6 +412,18 @@ def vj_join_device(ix: Index, eps: float, budget: int = 0) -> DeviceResult:
     rp = C.POINTER(vj_result)()
     _check(load().vj_join_device(ix.handle, float(eps), int(budget), C.byref(rp)))
     return DeviceResult(rp)
+
+
+def vj_join_batch(ixs, eps) -> list:
+    """Independent joins of several indexes with fused traversal launches; result i = vj_join(ixs[i], eps[i])."""
+    n = len(ixs)
+    e = np.ascontiguousarray(eps, dtype=np.float32)
+    if e.shape != (n,):
+        raise ValueError("eps needs one threshold per index")
+    hs = (C.c_void_p * max(n, 1))(*[ix.handle for ix in ixs])
+    outs = (C.POINTER(vj_result) * max(n, 1))()
+    _check(load().vj_join_batch(C.cast(hs, C.c_void_p), e.ctypes.data, n, C.cast(outs, C.c_void_p)))
+    return [_host_result(outs[i]) for i in range(n)]
 
 
 def vj_join_exact(ix: Index, eps: float) -> Result:

@@ -64,6 +64,17 @@ def test_join_and_free_reject_null():
     assert lib.vj_join_device(None, 1.0, 0, C.byref(rp)) == vj.VJ_ERR_ARG
     assert lib.vj_join_exact(None, 1.0, C.byref(rp)) == vj.VJ_ERR_ARG
     assert lib.vj_export_graph(None, None, None, None, None, None) == vj.VJ_ERR_ARG
+    # batch: negative count, NULL arrays, NULL index, n = 0 (a no-op)
+    assert lib.vj_join_batch(None, None, -1, None) == vj.VJ_ERR_ARG
+    assert lib.vj_join_batch(None, None, 2, None) == vj.VJ_ERR_ARG
+    hs = (C.c_void_p * 2)(None, None)
+    outs = (C.POINTER(vj.vj_result) * 2)()
+    import numpy as np
+    eps = np.ones(2, np.float32)
+    assert lib.vj_join_batch(C.cast(hs, C.c_void_p), eps.ctypes.data, 2, C.cast(outs, C.c_void_p)) == vj.VJ_ERR_ARG
+    assert b"NULL" in lib.vj_last_error()
+    assert not outs[0] and not outs[1]
+    assert lib.vj_join_batch(None, None, 0, None) == vj.VJ_OK
     lib.vj_result_free(None)
     lib.vj_free(None)
 
