@@ -50,6 +50,7 @@
 // In-range decisions whose FP32 key lies within the FP32 rounding bound of eps
 // are re-decided in FP64.
 #include <float.h>
+#include <mutex>
 #include <stdio.h>
 #include <string.h>
 
@@ -1392,26 +1393,108 @@ void join_setup(JoinRun& r) {
     r.soft = ix->p.work_sharing == VJ_WS_SOFT;
 }
 
-// the warps' workspace (visited lists, result spill, out-range queues) and
-// visited bitmaps, owned by `owner` and grown to `warps` warps of the given
-// per-warp sizes
-void bind_workspace(vj_index* owner, int64_t warps, int64_t wstride, int64_t vwords, JoinParams& P) {
-    cudaStream_t s = owner->stream;
-    if (owner->wspace_warps < warps || owner->wspace.n < (size_t)(warps * wstride)) {
-        owner->wspace.free_(s);
-        owner->wspace.alloc((size_t)(warps * wstride), s);
-        owner->wspace_warps = warps;
+// Traversal workspaces -- the warps' spill space (visited lists, result
+// spill, out-range queues) and their visited bitmaps -- are large (up to 2^17
+// visited slots per warp: GBs for a persistent grid) and only a running join
+// needs one.  A process-wide cache lends them out per join, so memory grows
+// with the number of joins running at once, not with the number of indexes.
+// The cache is emptied when the last index is freed.
+struct TravSpace {
+    int dev = 0;
+    bool busy = false;
+    DBuf<int32_t> ws;
+    DBuf<uint32_t> bits;  // all zero between queries
+};
+std::mutex g_ts_mu;
+std::vector<TravSpace*> g_ts;
+
+// free the idle spaces of this process (all devices); the caller holds g_ts_mu
+void trim_idle_locked() {
+    for (auto it = g_ts.begin(); it != g_ts.end();) {
+        TravSpace* t = *it;
+        if (t->busy) {
+            ++it;
+            continue;
+        }
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(t->dev);
+        if (t->ws.p) cudaFree(t->ws.p);
+        if (t->bits.p) cudaFree(t->bits.p);
+        cudaSetDevice(cur);
+        delete t;
+        it = g_ts.erase(it);
     }
-    if (owner->vbits.n < (size_t)(warps * vwords)) {
-        owner->vbits.free_(s);
-        owner->vbits.alloc((size_t)(warps * vwords), s);
-        VJ_CUDA(cudaMemsetAsync(owner->vbits.p, 0, (size_t)(warps * vwords) * sizeof(uint32_t), s));
-    }
-    P.wspace = owner->wspace.p;
-    P.wstride = wstride;
-    P.vbits = owner->vbits.p;
-    P.vwords = vwords;
 }
+
+class TravLease {
+  public:
+    TravLease(size_t ws_need, size_t bits_need, cudaStream_t s) : s_(s) {
+        int dev = 0;
+        VJ_CUDA(cudaGetDevice(&dev));
+        {
+            std::lock_guard<std::mutex> lk(g_ts_mu);
+            for (TravSpace* t : g_ts)
+                if (!t->busy && t->dev == dev && (!t_ || t->ws.n + t->bits.n > t_->ws.n + t_->bits.n)) t_ = t;
+            if (!t_) {
+                t_ = new TravSpace();
+                t_->dev = dev;
+                g_ts.push_back(t_);
+            }
+            t_->busy = true;
+        }
+        try {
+            grow(ws_need, bits_need);
+        } catch (const VjError&) {
+            // out of memory: free the other idle spaces and try once more
+            cudaGetLastError();
+            {
+                std::lock_guard<std::mutex> lk(g_ts_mu);
+                trim_idle_locked();
+            }
+            try {
+                grow(ws_need, bits_need);
+            } catch (...) {
+                std::lock_guard<std::mutex> lk(g_ts_mu);
+                t_->busy = false;
+                throw;
+            }
+        }
+    }
+    ~TravLease() {
+        // after a failed join the bitmaps may hold an abandoned query's bits;
+        // the stream is done with the space before another join takes it
+        if (dirty_ && t_->bits.p) cudaMemsetAsync(t_->bits.p, 0, t_->bits.n * sizeof(uint32_t), s_);
+        cudaStreamSynchronize(s_);
+        std::lock_guard<std::mutex> lk(g_ts_mu);
+        t_->busy = false;
+    }
+    TravLease(const TravLease&) = delete;
+    TravLease& operator=(const TravLease&) = delete;
+    void bind(int64_t wstride, int64_t vwords, JoinParams& P) const {
+        P.wspace = t_->ws.p;
+        P.wstride = wstride;
+        P.vbits = t_->bits.p;
+        P.vwords = vwords;
+    }
+    void clean() { dirty_ = false; }
+
+  private:
+    void grow(size_t ws_need, size_t bits_need) {
+        if (t_->ws.n < ws_need) {
+            t_->ws.free_(s_);
+            t_->ws.alloc(ws_need, s_);
+        }
+        if (t_->bits.n < bits_need) {
+            t_->bits.free_(s_);
+            t_->bits.alloc(bits_need, s_);
+            VJ_CUDA(cudaMemsetAsync(t_->bits.p, 0, bits_need * sizeof(uint32_t), s_));
+        }
+    }
+    TravSpace* t_ = nullptr;
+    cudaStream_t s_;
+    bool dirty_ = true;
+};
 
 void bind_pool(JoinRun& r) {
     r.P.pool_id = r.ix->pool_id.p;
@@ -1557,6 +1640,11 @@ void join_finish(JoinRun& r, vj_stats* st, int64_t* nnz_out) {
 }  // namespace
 
 // ------------------------------------------------------------------ host
+void vj_trav_space_trim() {
+    std::lock_guard<std::mutex> lk(g_ts_mu);
+    trim_idle_locked();
+}
+
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out) {
     JoinRun r;
     r.ix = ix;
@@ -1565,7 +1653,9 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
     join_setup(r);
     cudaStream_t s = ix->stream;
     JoinParams& P = r.P;
-    bind_workspace(ix, (int64_t)r.jd.blocks * WPB, r.wstride, r.vwords, P);
+    const int64_t warps = (int64_t)r.jd.blocks * WPB;
+    TravLease lease((size_t)(warps * r.wstride), (size_t)(warps * r.vwords), s);
+    lease.bind(r.wstride, r.vwords, P);
 
     Events ev;  // e[0] start, e[1] after pass 1, e[2] after pass 2, e[3] end
     for (int attempt = 0; attempt < 3; attempt++) {
@@ -1593,6 +1683,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         VJ_CUDA(cudaStreamSynchronize(s));
         if (!pool_overflowed(r)) break;
     }
+    lease.clean();  // no device error: every query cleared its bitmap bits
     VJ_REQUIRE((int64_t)r.hc[C_POOL] <= r.P.pool_cap, VJ_ERR_STATE, "join: result pool still too small");
     VJ_CUDA(cudaEventElapsedTime(&r.t_trav, ev.e[0], ev.e[3]));
     if (r.soft) {
@@ -1618,7 +1709,8 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
     }
     par_for(n, [&](int i) { join_setup(runs[i]); });
 
-    // the workspace is the largest instance's, sized for the widest needs of all
+    // one workspace for all, sized for the widest needs; the fused passes run
+    // on the largest instance's stream
     int owner = 0;
     int64_t warps = 0, wstride = 0, vwords = 0;
     for (int i = 0; i < n; i++) {
@@ -1629,7 +1721,8 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
     }
     cudaStream_t s = ixs[owner]->stream;
     for (int i = 0; i < n; i++) VJ_CUDA(cudaStreamSynchronize(ixs[i]->stream));
-    for (int i = 0; i < n; i++) bind_workspace(ixs[owner], warps, wstride, vwords, runs[i].P);
+    TravLease lease((size_t)(warps * wstride), (size_t)(warps * vwords), s);
+    for (int i = 0; i < n; i++) lease.bind(wstride, vwords, runs[i].P);
     DBuf<unsigned long long> ticket;
     ticket.alloc(1, s);
     std::vector<unsigned long long> hc((size_t)n * 16);
@@ -1704,6 +1797,7 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
         }
     }
     ticket.free_(s);
+    lease.clean();  // no device error in any instance
     for (int i = 0; i < n; i++)
         VJ_REQUIRE(!pending[i], VJ_ERR_STATE, "instance %d: join result pool still too small", i);
     // the instances' streams continue after the fused passes

@@ -73,6 +73,8 @@ static void check_join_params(const vj_params& p) {
     VJ_REQUIRE(p.route_bruteforce == 0, VJ_ERR_ARG, "route_bruteforce is reserved and must be 0");
 }
 
+static std::atomic<int64_t> g_live_indexes{0};
+
 static void free_index(vj_index* ix) {
     if (!ix) return;
     cudaStream_t s = ix->stream;
@@ -110,10 +112,10 @@ static void free_index(vj_index* ix) {
     ix->hyb2.free_(s);
     ix->seg2.free_(s);
     ix->order1.free_(s);
-    ix->vbits.free_(s);
     ix->cost_hist.free_(s);
     ix->scan_cq.free_(s);
     ix->scan_cx.free_(s);
+    ix->scan_ck.free_(s);
     ix->sort_large.free_(s);
     ix->sort_nlarge.free_(s);
     ix->cache.free_(s);
@@ -123,7 +125,6 @@ static void free_index(vj_index* ix) {
     ix->seg.free_(s);
     ix->pool_id.free_(s);
     ix->pool_d.free_(s);
-    ix->wspace.free_(s);
     ix->ctr.free_(s);
     ix->offsets.free_(s);
     ix->out_id.free_(s);
@@ -132,6 +133,8 @@ static void free_index(vj_index* ix) {
     cudaStreamSynchronize(s);
     if (ix->own_stream) cudaStreamDestroy(ix->own_stream);
     delete ix;
+    // the last index gone: nothing will join soon, release the join workspaces
+    if (g_live_indexes.fetch_sub(1) == 1) vj_trav_space_trim();
 }
 
 extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_t nq, int d, vj_metric metric,
@@ -156,6 +159,7 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         check_join_params(p);
 
         ix = new vj_index();
+        g_live_indexes.fetch_add(1);
         VJ_CUDA(cudaGetDevice(&ix->dev));
         int sms = 0;
         VJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->dev));

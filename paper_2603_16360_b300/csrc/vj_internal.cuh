@@ -151,7 +151,6 @@ struct vj_index {
     DBuf<uint8_t> hyb2;
     DBuf<int64_t> seg2;
     DBuf<int32_t> order1;     // [nq] longest-first dispatch order (from the last join's visits)
-    DBuf<uint32_t> vbits;     // per-warp visited bitmaps of the join (zero between queries)
     DBuf<int> cost_hist;
     bool have_costs = false;
     DBuf<int32_t> scan_cq, scan_cx;  // tensor-core scan candidates (query, data id)
@@ -166,8 +165,6 @@ struct vj_index {
     DBuf<int64_t> seg;        // [nq] start of each query's results in the pool
     DBuf<int32_t> pool_id;    // result pool
     DBuf<float> pool_d;
-    DBuf<int32_t> wspace;     // per-warp spill space
-    int64_t wspace_warps = 0;
     DBuf<unsigned long long> ctr;  // counters + ticket + error word
     DBuf<int64_t> offsets;    // [nq+1]
     DBuf<int32_t> out_id;
@@ -190,6 +187,8 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
                       DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
+// free the idle traversal workspaces of the process-wide cache
+void vj_trav_space_trim();
 // joins of n distinct indexes (default budget) with fused traversal launches;
 // par(n, fn) runs fn(0..n-1), possibly on several host threads, and throws if
 // any call threw
