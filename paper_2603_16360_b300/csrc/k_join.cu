@@ -26,27 +26,30 @@
 //   UpdateCache (8)    C[q] = closest visited data node, ties by id, FP64
 //                      re-decided among FP32 near-ties.
 //
-// Work sharing (soft) runs in two launches over the queries in MST BFS order
-// (parents before children):
-//   pass 1  every query runs on the seeds {entry, q} without waiting for its
-//           parent; a hybrid query (OOD, forced or planned) only records that
-//           it needs the cached seed before its expansion;
-//   pass 2  each query waits (bounded acquire spin) for its parent's final
-//           cache C[parent] and decides from pass 1's sets what that seed
+// Work sharing (soft) runs in three launches over the queries:
+//   pass 1  every query, hybrid ones included, runs on the seeds {entry, q}
+//           without waiting for its parent (longest-first order);
+//   pass 2  in parallel, each query decides what C[parent] as pass 1 left it
 //           changes.  V, I and the BFS closure are sets, and V is
 //           {entry, q} U N(q) U (data neighbours of every result), so:
 //             - C[parent] in V: nothing changes;
 //             - C[parent] new and out of range: one more visited node, the
 //               cache becomes the (dist, id) minimum of the two (FP64);
 //             - C[parent] new and in range, a duplicate of q that would have
-//               been the greedy front, or a hybrid query: the query re-runs
-//               with the seed from the start.
-//           It then publishes C[q] (release store of its done flag).
+//               been the greedy front, or a hybrid query (its expansion
+//               depends on the order of its seeds): the query re-runs with
+//               the seed from the start; the re-run is staged.
+//   pass 3  in MST BFS order (parents first), each query waits (bounded
+//           acquire spin) for its parent's final cache; when that is the seed
+//           pass 2 decided for, pass 2's outcome is committed, otherwise the
+//           query decides again.  It then publishes C[q] (release store of
+//           its done flag).
 // The result, visited count and cache equal those of the wait-first order.
 //
-// Visited set: open-addressing hash in shared memory (HCAP slots), moved on
-// overflow to a per-warp global table that grows by 4x (two alternating
-// regions).  Results: shared-memory list (RCAP) spilling to global memory.
+// Visited set: open-addressing hash in shared memory (HCAP slots); past half
+// of it a query switches to its warp's global bitmap over all nodes (cleared
+// from the list of set ids when the query ends).  Results: shared-memory
+// list (RCAP) spilling to global memory.
 // In-range decisions whose FP32 key lies within the FP32 rounding bound of eps
 // are re-decided in FP64.
 #include <float.h>
@@ -142,7 +145,7 @@ struct JoinParams {
     long long spin_limit;
 };
 
-enum { QF_PROBED = 1, QF_DEFER = 2 };
+enum { QF_PROBED = 1 };
 
 // does the adjacency row (R ids) contain v?  All loads issued before any test.
 __device__ __forceinline__ bool row_has(const int32_t* __restrict__ row, int R, int v) {
@@ -452,8 +455,10 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         auto decide = [&](int sc, int& best) -> int {
             const int flags = P.qflag[qi];
             best = P.cache1[qi];
-            if (flags & QF_DEFER) return 2;
             if (sc < 0 || sc == P.entry) return 0;
+            // a hybrid expansion depends on the order its seeds enter the
+            // queue: any real seed means a re-run
+            if (P.hyb[qi] == 1) return 2;
             if (lane == 0) S->cand[0] = sc;
             __syncwarp();
             group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
@@ -557,8 +562,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (o == 2 && same) {
                 // commit the re-run pass 2 staged
                 if (lane == 0) {
-                    if (!(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
-                    c_dist += P.steps2[qi];
+                    c_dist += P.steps2[qi] - P.steps[qi];
                     P.cache[qi] = P.cache2[qi];
                     P.steps[qi] = P.steps2[qi];
                     P.hyb[qi] = P.hyb2[qi];
@@ -813,18 +817,6 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             }
             hyb = ood;
         }
-        if (P.mode == 1 && !failed && !routed && hyb) {
-            // a hybrid expansion needs the cached seed first: pass 2 runs it
-            if (lane == 0) {
-                P.qflag[qi] = (uint8_t)(QF_DEFER | (probe ? QF_PROBED : 0));
-                P.cache1[qi] = -1;
-                P.hyb[qi] = 1;
-                P.count[qi] = 0;
-                P.steps[qi] = 0;
-            }
-            __syncwarp();
-            return false;
-        }
         int expansions = 0;
         if (routed) {
             s.nres = 0;  // the scan supplies the row
@@ -1020,7 +1012,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 P.hyb2[qi] = (uint8_t)hyb;
             } else {
                 // a pass-3 re-run replaces pass 1's count of this query
-                if (P.mode == 2 && !(P.qflag[qi] & QF_DEFER)) c_dist -= P.steps[qi];
+                if (P.mode == 2) c_dist -= P.steps[qi];
                 P.cache[qi] = best;
                 P.steps[qi] = s.nvis;
                 P.hyb[qi] = (uint8_t)hyb;
