@@ -220,8 +220,11 @@ def bench_collection(args, vj, torch):
                   nq_range=(max(int(1e3 * args.scale), 100), max(int(2e5 * args.scale), 101)))
     ixs, eps, nqs, nxs, targets, exs = [], [], [], [], [], []
     t0 = time.perf_counter()
+    build_total = 0.0
     for w in inputs.angular_collection(n=args.instances, **rng_kw):
+        tb = time.perf_counter()
         ix = vj.vj_build(w.X, w.Q, metric=w.metric, params=vj.default_params(degree=w.degree, knn_k=w.knn_k))
+        build_total += time.perf_counter() - tb
         e = calibrate_eps(vj, ix, w, w.target_matches)
         ixs.append(ix)
         eps.append(e)
@@ -242,12 +245,16 @@ def bench_collection(args, vj, torch):
         return hits / max(tot, 1)
 
     chosen = None
+    sweep = []
     for mode, budget in [("adapt", 256)] + [("force", b) for b in (4, 8, 16, 32, 64, 128, 256)]:
         for ix in ixs:
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
                                   force_hybrid=int(mode == "force"), hybrid_beam=budget, learned=0)
+        t1 = time.perf_counter()
         rs = vj.vj_join_batch(ixs, eps)
+        t1 = time.perf_counter() - t1
         rec = pooled_recall(rs)
+        sweep.append({"hybrid": mode, "beam": budget, "recall": round(rec, 4), "ms": round(1e3 * t1, 1)})
         chosen = (mode, budget, rec, rs)
         if rec >= 0.95:
             break
@@ -267,8 +274,16 @@ def bench_collection(args, vj, torch):
         for _ in range(max(2, args.steps // 2)):
             t1 = time.perf_counter()
             tt = 0.0
-            for ix, e in zip(ixs, eps):
-                tt += vj.vj_join(ix, e).stats["ms_traverse"]
+            per_inst = []
+            for k, (ix, e) in enumerate(zip(ixs, eps)):
+                r1 = vj.vj_join(ix, e)
+                st1 = r1.stats
+                tt += st1["ms_traverse"]
+                per_inst.append({"i": k, "nx": nxs[k], "nq": nqs[k], "ms_traverse": round(st1["ms_traverse"], 3),
+                                 "ms_sws": [round(x, 3) for x in st1["ms_sws"]],
+                                 "dist_per_query": round(st1["dist_computations"] / nqs[k], 1),
+                                 "max_visited": int(r1.steps.max()), "restarts": st1["sws_restarts"],
+                                 "spill_queries": st1["spill_queries"]})
             seq_ms.append(1e3 * (time.perf_counter() - t1))
             seq_trav.append(tt)
     b_ms = statistics.median(batch_ms)
@@ -283,11 +298,14 @@ def bench_collection(args, vj, torch):
                                    f"(sum {sum(nxs)}), |Q| {min(nqs)}..{max(nqs)} (sum {total_q}), d=100 cosine, "
                                    f"eps for a mean of {min(targets):g}..{max(targets):g} matches/query",
                        "arm": f"vj_join_batch, plain MI+SWS FP32, hybrid={mode} beam {budget}",
-                       "recall": rec, "pairs": pairs, "build_s": build_s,
+                       "recall": rec, "pairs": pairs, "sweep": sweep,
+                       "prep_s": round(build_s, 1), "build_s": round(build_total, 2),
                        "fused_traversal_ms": statistics.median(trav_ms),
                        "one_join_per_instance": {"ms_per_step": s_ms, "queries_per_s": total_q / (s_ms / 1e3),
                                                  "traversal_ms_sum": statistics.median(seq_trav)},
                        "batch_vs_one_by_one": s_ms / b_ms,
+                       "dist_computations": int(sum(r.stats["dist_computations"] for r in rb)),
+                       "slowest_instances": sorted(per_inst, key=lambda x: -x["ms_traverse"])[:6],
                        "timing": "host wall time of the public call (host results, device-to-host copies inside)"},
             "e2e": {"value": total_q / (b_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
