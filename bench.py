@@ -116,6 +116,10 @@ def make_workload(name, scale):
         return inputs.sift_like(scale=scale)
     if name == "gauss_small":
         return inputs.gauss_small()
+    if name == "angular_one":
+        # one instance of the angular collection's recipe: 300K x 30K (times scale), d = 100 cosine
+        nx, nq = int(3e5 * scale), int(3e4 * scale)
+        return inputs.angular_instance(1239, 0, nx_range=(nx, nx + 1), nq_range=(nq, nq + 1))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -499,7 +503,7 @@ def main():
             "achieved": statistics.mean(s["bytes_algorithmic"] for s in stats) / (t_tr / 1e3) / 1e9,
             "ms_per_launch": t_tr, "algorithmic_bytes_per_launch": statistics.mean(s["bytes_algorithmic"] for s in stats),
             "peak_kind": f"{peak_kind} hbm_gbs (burst)",
-            "traffic": _traffic("k_join", args.scale) if learned is not None else None}
+            "traffic": _traffic("k_join", args.scale) if learned is not None and args.workload == "sift_like" else None}
     trav["frac"] = trav["achieved"] / hbm
     rooflines = [trav]
     if learned is not None and t_sc > 0:
@@ -508,7 +512,7 @@ def main():
         scan = {"kernel": "k_tc_scan (tcgen05 BF16 brute-force scan)", "bound": "tensor", "unit": "TFLOP/s",
                 "peak": bf16, "achieved": flops / (t_sc / 1e3) / 1e12, "ms_per_launch": t_sc,
                 "algorithmic_flops_per_launch": flops, "peak_kind": f"{peak_kind} bf16_tflops (burst)",
-                "traffic": _traffic("k_tc_scan_res", args.scale)}
+                "traffic": _traffic("k_tc_scan_res", args.scale) if args.workload == "sift_like" else None}
         scan["frac"] = scan["achieved"] / bf16
         rooflines.append(scan)
     dominant = max(rooflines, key=lambda k: k["ms_per_launch"])

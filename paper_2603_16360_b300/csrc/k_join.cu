@@ -68,6 +68,7 @@ constexpr int RCAP = 256;   // shared-memory result slots per warp
 constexpr int CCAP = 128;   // candidate slots per batch
 constexpr int FB = 4;       // frontier nodes per BFS batch (FB * 32 <= CCAP)
 constexpr int GCAP0 = 8192; // first global visited table
+constexpr int OQS = 64;     // out-range queue slots per buffer kept in shared memory
 
 struct WarpSmem {
     int nlist;  // bitmap mode: ids listed in the warp's space
@@ -76,6 +77,10 @@ struct WarpSmem {
     float rd[RCAP];
     int cand[CCAP];
     float ckey[CCAP];
+    // the hybrid out-range queue (two alternating buffers) when its capacity
+    // fits: every pop reads it, so it stays off global memory
+    float oqk[2][OQS];
+    int oqi[2][OQS];
 };
 
 enum {
@@ -358,6 +363,13 @@ __device__ __forceinline__ bool inrange_decide(const JoinParams& P, bool valid, 
 }
 
 // append in-range candidates (one per lane) to the result list (keys stored)
+// bring a node's adjacency row toward L2 ahead of its expansion (a hint only)
+__device__ __forceinline__ void prefetch_row(const JoinParams& P, int node) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)node * P.R));
+}
+
+// Every result is expanded later (closure or hybrid queue): its adjacency row
+// is prefetched here, off the critical path of that expansion.
 __device__ __forceinline__ bool append_results(const JoinParams& P, QueryState& s, bool in, int node, float k,
                                                const WarpSpace& W, int lane) {
     unsigned m = __ballot_sync(VJ_FULL, in);
@@ -368,6 +380,7 @@ __device__ __forceinline__ bool append_results(const JoinParams& P, QueryState& 
         int pos = s.nres + __popc(m & ((1u << lane) - 1u));
         s.rid[pos] = node;
         s.rd[pos] = k;
+        if (node >= 0 && node < P.nx) prefetch_row(P, node);
     }
     s.nres += cnt;
     __syncwarp();
@@ -434,10 +447,17 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
     W.grid = wbase + 2 * (int64_t)P.gmax;
     W.grd = reinterpret_cast<float*>(W.grid + P.grcap);
     int32_t* qbase = wbase + 2 * (int64_t)P.gmax + 2 * (int64_t)P.grcap;
-    W.qk[0] = reinterpret_cast<float*>(qbase);
-    W.qi[0] = qbase + P.oqcap;
-    W.qk[1] = reinterpret_cast<float*>(qbase + 2 * P.oqcap);
-    W.qi[1] = qbase + 3 * P.oqcap;
+    if (P.oqcap <= OQS) {
+        W.qk[0] = S->oqk[0];
+        W.qi[0] = S->oqi[0];
+        W.qk[1] = S->oqk[1];
+        W.qi[1] = S->oqi[1];
+    } else {
+        W.qk[0] = reinterpret_cast<float*>(qbase);
+        W.qi[0] = qbase + P.oqcap;
+        W.qk[1] = reinterpret_cast<float*>(qbase + 2 * P.oqcap);
+        W.qi[1] = qbase + 3 * P.oqcap;
+    }
     const int g = lane & (G - 1);
     const int R = P.R;
     long long &c_dist = cnt.dist, &c_exp = cnt.exp, &c_adj = cnt.adj, &c_hyb = cnt.hyb, &c_rechk = cnt.rechk,
@@ -930,6 +950,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 const bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
                 best_update(P, s, val, ck, cv, lane);
                 const bool isout = val && !in;
+                if (isout) prefetch_row(P, cv);  // it may be popped from the out-range queue
                 const unsigned inm = __ballot_sync(VJ_FULL, in);
                 const unsigned outm = __ballot_sync(VJ_FULL, isout);
                 // queue size after the per-insert rule, in adjacency order

@@ -141,3 +141,60 @@ def test_batch_shared_predictor_and_errors(collection):
         vj.vj_join_batch([ixs[0], ixs[1]], [eps[0], -1.0])
     assert e.value.status == vj.VJ_ERR_ARG
     assert vj.vj_join_batch([], []) == []
+
+
+def test_batch_beyond_one_launch():
+    """More instances than one fused launch takes (64): the batch is split
+    into several launches per pass and still equals the single joins."""
+    rng = np.random.default_rng(77)
+    ixs, eps, single = [], [], []
+    for k in range(70):
+        nx, nq = int(rng.integers(300, 900)), int(rng.integers(20, 120))
+        X = rng.standard_normal((nx, 16)).astype(np.float32)
+        Q = (X[rng.integers(0, nx, nq)] + 0.3 * rng.standard_normal((nq, 16))).astype(np.float32)
+        ix = vj.vj_build(X, Q, params=vj.default_params(degree=8, knn_k=16))
+        ixs.append(ix)
+        eps.append(2.0 + 0.01 * k)
+    single = [vj.vj_join(ix, e) for ix, e in zip(ixs, eps)]
+    batch = vj.vj_join_batch(ixs, eps)
+    for i, (a, b) in enumerate(zip(batch, single)):
+        _same(a, b, f"instance {i}")
+    assert sum(r.nnz for r in batch) > 0
+    for ix in ixs:
+        ix.free()
+
+
+def test_concurrent_joins_on_host_threads():
+    """Joins of different indexes from concurrent host threads each borrow
+    their own traversal workspace and give the single-thread results."""
+    import threading
+    ws = [inputs.angular_instance(601, k, nx_range=(3000, 6000), nq_range=(300, 600)) for k in range(4)]
+    ixs = [_build(w) for w in ws]
+    eps = [_eps(w) for w in ws]
+    ref = [vj.vj_join(ix, e) for ix, e in zip(ixs, eps)]
+    out = [None] * len(ixs)
+    errs = []
+
+    def run(k):
+        try:
+            for _ in range(3):
+                out[k] = vj.vj_join(ixs[k], eps[k])
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(len(ixs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for k in range(len(ixs)):
+        _same(out[k], ref[k], f"thread {k}")
+    for ix in ixs:
+        ix.free()
+    # a rebuilt index borrows a cached workspace and joins the same
+    w = ws[0]
+    ix = _build(w)
+    r = vj.vj_join(ix, eps[0])
+    _same(r, ref[0], "after the cache was emptied")
+    ix.free()
