@@ -250,7 +250,7 @@ def bench_collection(args, vj, torch):
 
     chosen = None
     sweep = []
-    for mode, budget in [("adapt", 256)] + [("force", b) for b in (4, 8, 16, 32, 64, 128, 256)]:
+    for mode, budget in [("adapt", 256)] + [("force", b) for b in (2, 4, 8, 16, 32, 64, 128, 256)]:
         for ix in ixs:
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
                                   force_hybrid=int(mode == "force"), hybrid_beam=budget, learned=0)
