@@ -211,6 +211,16 @@ def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed"):
     return e0.elapsed_time(e1) / steps, stats
 
 
+def slowest_rank_ms(ms, dist, device):
+    """The largest of the ranks' times (ms itself without a process group)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def bench_collection(args, vj, torch):
     """A collection of independent join instances of very different sizes
     (angular_collection: |X| log-uniform 1e4..2e6 and |Q| 1e3..2e5, both times
@@ -532,12 +542,10 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     d2h = int(rh.offsets.nbytes + rh.ids.nbytes + rh.dists.nbytes + rh.steps.nbytes + rh.cache.nbytes +
               rh.hybrid.nbytes)
-    e2e_v = world * w.nq / (statistics.median(e2e_ms) / 1e3)
-
+    # replicas: every rank joins the same workload; the job's time is the slowest rank's
+    e2e_v = world * w.nq / (slowest_rank_ms(statistics.median(e2e_ms), dist, "cuda") / 1e3)
     if dist:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+        step_ms = slowest_rank_ms(step_ms, dist, "cuda")
         value = world * w.nq / (step_ms / 1e3)
     cfg = {"workload": wl_desc, "arm": arm, "recall": rec, "eps": eps, "degree": info["degree"],
            "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "build_s": build_s,
