@@ -377,6 +377,14 @@ constexpr uint32_t RS_BOX = 128 * 64 * 2;      // one 128-row x 64-column BF16 b
 constexpr uint32_t RS_BBOX = 128 * 16 * 2;     // one 128-row x 16-column BF16 bias box
 constexpr int RS_MAX_KB = 2;                   // data k-blocks (kp <= 128)
 constexpr int RS_MAX_STAGES = 8;
+// Candidates are appended through per-warp chunks of the output: one global
+// atomic reserves RS_CHUNK slots (more if one append needs more), and the
+// slots a warp leaves unused are holes (query index -1).  A counter shared by
+// every warp of the grid made same-address atomics the bottleneck once the
+// scanned rows had about a hundred pairs each.
+constexpr int RS_CHUNK = 128;
+// holes one launch can leave: a part-filled chunk per epilogue warp at its end
+constexpr int64_t RS_HOLE_SLACK = (int64_t)RS_CHUNK * 32 * 160;
 constexpr uint32_t RS_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RS_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
 
@@ -677,6 +685,8 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
         const int blk = cg >> 1, csub = cg & 1;
         int i = 0;
         bool ok = true;
+        unsigned long long cbase = 0;  // this warp's output chunk: next slot, slots left
+        int cleft = 0;
         for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
             const int rp = u % P.nrp, cc = u / P.nrp;
             const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
@@ -735,10 +745,20 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
                         }
                         const int total = __shfl_sync(VJ_FULL, incl, 31);
                         if (total > 0) {
-                            unsigned long long gb = 0;
-                            if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)total);
-                            gb = __shfl_sync(VJ_FULL, gb, 31);
-                            unsigned long long gq = gb + (unsigned long long)(incl - mine);
+                            if (total > cleft) {
+                                // close the chunk (its unused slots become holes) and
+                                // reserve the next one
+                                for (int k = lane; k < cleft; k += 32)
+                                    if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
+                                const int want = max(total, RS_CHUNK);
+                                unsigned long long gb = 0;
+                                if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
+                                cbase = __shfl_sync(VJ_FULL, gb, 31);
+                                cleft = want;
+                            }
+                            unsigned long long gq = cbase + (unsigned long long)(incl - mine);
+                            cbase += (unsigned long long)total;
+                            cleft -= total;
                             while (hit) {
                                 const int j = __ffs(hit) - 1;
                                 hit &= hit - 1;
@@ -763,6 +783,8 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
                 }
             }
         }
+        for (int k = lane; k < cleft; k += 32)
+            if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
     }
     tc_fence_before();
     __syncthreads();
@@ -1078,8 +1100,9 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         VJ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core scan: a pipeline wait timed out");
         if ((int64_t)hn <= (int64_t)cq.n) break;
-        cap = (int64_t)hn + 1024;
+        cap = (int64_t)hn + RS_HOLE_SLACK;  // the next launch may leave other holes
     }
+    VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core scan: candidate list still too small");
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ms_out) *ms_out = ms;
@@ -1121,7 +1144,7 @@ __global__ void k_iota(int32_t* __restrict__ v, int64_t n) {
 
 __global__ void k_pair_count(const int32_t* __restrict__ cq, int64_t nc, int32_t* __restrict__ counts) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nc) atomicAdd(counts + cq[e], 1);
+    if (e < nc && cq[e] >= 0) atomicAdd(counts + cq[e], 1);  // -1: a hole
 }
 
 __global__ void k_pair_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx, int64_t nc,
@@ -1130,6 +1153,7 @@ __global__ void k_pair_scatter(const int32_t* __restrict__ cq, const int32_t* __
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nc) return;
     const int q = cq[e];
+    if (q < 0) return;  // a hole
     ids[off[q] + atomicAdd(cursor + q, 1)] = cx[e];
 }
 
@@ -1248,8 +1272,9 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         VJ_CUDA(cudaStreamSynchronize(s));
         VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
         if ((int64_t)hn <= (int64_t)cq.n) break;
-        cap = (int64_t)hn + 1024;
+        cap = (int64_t)hn + RS_HOLE_SLACK;  // the next launch may leave other holes
     }
+    VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core kNN: candidate list still too small");
     const int64_t nc = (int64_t)hn;
 
     // 3. candidates grouped by row (CSR) and each row's bound

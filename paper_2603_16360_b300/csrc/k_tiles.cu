@@ -574,7 +574,8 @@ __global__ void k_nlj_recheck(const float* __restrict__ vec, const float* __rest
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t e = w * 32 + lane;
     // each lane computes its own pair's key sequentially (vectors are short-lived in L2)
-    bool valid = e < nc;
+    const bool inb = e < nc;
+    bool valid = inb && cq[e] >= 0;  // -1: a hole in the candidate list
     float key = FLT_MAX;
     int64_t qn = 0, xn = 0;
     if (valid) {
@@ -615,6 +616,8 @@ __global__ void k_nlj_recheck(const float* __restrict__ vec, const float* __rest
     if (valid) {
         cd[e] = in ? (metric == 0 ? sqrtf(fmaxf(key, 0.f)) : key) : -1.f;
         if (in) atomicAdd(counts + cq[e], 1);
+    } else if (inb) {
+        cd[e] = -1.f;
     }
 }
 
@@ -624,6 +627,10 @@ __global__ void k_exact_decide(const float* __restrict__ ck, const int32_t* __re
                                float* __restrict__ cd, int32_t* __restrict__ counts) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nc) return;
+    if (cq[e] < 0) {  // a hole in the candidate list
+        cd[e] = -1.f;
+        return;
+    }
     const double dd = sqrt(fmax((double)ck[e], 0.0));
     const bool in = dd < eps64;
     cd[e] = in ? sqrtf(fmaxf(ck[e], 0.f)) : -1.f;  // the traversal's FP32 distance of the same key
