@@ -726,39 +726,47 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
                 const bool maybe = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr;
                 if (__any_sync(VJ_FULL, maybe)) {
                     const int64_t c0 = (int64_t)ct * P.tstride * RS_BN + csub * 64;
+                    // columns past the last data row (last tile only), as masks of each half
+                    const int64_t room = P.ncols - c0;
+                    const uint32_t cm0 = room >= 32 ? ~0u : (room <= 0 ? 0u : ((1u << room) - 1u));
+                    const uint32_t cm1 = room >= 64 ? ~0u : (room <= 32 ? 0u : ((1u << (room - 32)) - 1u));
+                    uint32_t hit0 = 0, hit1 = 0;
+                    if (maybe) {
 #pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        uint32_t hit = 0;
-                        if (maybe) {
-#pragma unroll
-                            for (int j = 0; j < 32; j++)
-                                if (__uint_as_float(va[h * 32 + j]) > thr && c0 + h * 32 + j < P.ncols)
-                                    hit |= 1u << j;
+                        for (int j = 0; j < 32; j++) {
+                            hit0 |= (uint32_t)(__uint_as_float(va[j]) > thr) << j;
+                            hit1 |= (uint32_t)(__uint_as_float(va[32 + j]) > thr) << j;
                         }
-                        // warp-aggregated append: one atomic per warp and half
-                        const int mine = __popc(hit);
-                        int incl = mine;
+                        hit0 &= cm0;
+                        hit1 &= cm1;
+                    }
+                    // warp-aggregated append of both halves
+                    const int mine = __popc(hit0) + __popc(hit1);
+                    int incl = mine;
 #pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
-                            if (lane >= o) incl += t2;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
+                        if (lane >= o) incl += t2;
+                    }
+                    const int total = __shfl_sync(VJ_FULL, incl, 31);
+                    if (total > 0) {
+                        if (total > cleft) {
+                            // close the chunk (its unused slots become holes) and
+                            // reserve the next one
+                            for (int k = lane; k < cleft; k += 32)
+                                if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
+                            const int want = max(total, RS_CHUNK);
+                            unsigned long long gb = 0;
+                            if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
+                            cbase = __shfl_sync(VJ_FULL, gb, 31);
+                            cleft = want;
                         }
-                        const int total = __shfl_sync(VJ_FULL, incl, 31);
-                        if (total > 0) {
-                            if (total > cleft) {
-                                // close the chunk (its unused slots become holes) and
-                                // reserve the next one
-                                for (int k = lane; k < cleft; k += 32)
-                                    if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
-                                const int want = max(total, RS_CHUNK);
-                                unsigned long long gb = 0;
-                                if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
-                                cbase = __shfl_sync(VJ_FULL, gb, 31);
-                                cleft = want;
-                            }
-                            unsigned long long gq = cbase + (unsigned long long)(incl - mine);
-                            cbase += (unsigned long long)total;
-                            cleft -= total;
+                        unsigned long long gq = cbase + (unsigned long long)(incl - mine);
+                        cbase += (unsigned long long)total;
+                        cleft -= total;
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            uint32_t hit = h ? hit1 : hit0;
                             while (hit) {
                                 const int j = __ffs(hit) - 1;
                                 hit &= hit - 1;
