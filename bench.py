@@ -470,7 +470,7 @@ def main():
         route_acc = float(((pred[held, 1] > 0) == route_lab[held]).mean())
         # operating point: the fastest (route threshold, hybrid-queue cap) whose join reaches recall 0.95
         op, sweep = None, []
-        grid = [(0, t) for t in (0.99, 0.97, 0.95, 0.9, 0.8, 0.6, 0.4, 0.2)] + [(64, t) for t in (0.9, 0.6, 0.3)]
+        grid = [(0, t) for t in (0.99, 0.97, 0.95, 0.9, 0.85, 0.8, 0.7, 0.6, 0.5, 0.4, 0.2)] + [(64, t) for t in (0.9, 0.6, 0.3)]
         for cap, thr in grid:
             vj.vj_attach_predictor(ix, mlp, thr, cap)
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
