@@ -383,8 +383,10 @@ constexpr int RS_MAX_STAGES = 8;
 // every warp of the grid made same-address atomics the bottleneck once the
 // scanned rows had about a hundred pairs each.
 constexpr int RS_CHUNK = 128;
-// holes one launch can leave: a part-filled chunk per epilogue warp at its end
-constexpr int64_t RS_HOLE_SLACK = (int64_t)RS_CHUNK * 32 * 160;
+// room for holes when a list is sized from a previous launch's count: a
+// part-filled chunk per epilogue warp at the end (RS_EPI warps per CTA, one CTA
+// per SM, up to 256 SMs); the chunk switches add a quarter of the count on top
+constexpr int64_t RS_HOLE_SLACK = (int64_t)RS_CHUNK * 16 * 256;
 constexpr uint32_t RS_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RS_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);
 
@@ -1086,7 +1088,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     VJ_CUDA(cudaEventCreate(&e0));
     VJ_CUDA(cudaEventCreate(&e1));
     float ms = 0.f;
-    for (int attempt = 0; attempt < 2; attempt++) {
+    for (int attempt = 0; attempt < 3; attempt++) {
         cq.ensure(cap, s);
         cx.ensure(cap, s);
         P.cq = R.cq = cq.p;
@@ -1108,7 +1110,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         VJ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core scan: a pipeline wait timed out");
         if ((int64_t)hn <= (int64_t)cq.n) break;
-        cap = (int64_t)hn + RS_HOLE_SLACK;  // the next launch may leave other holes
+        cap = (int64_t)hn + (int64_t)hn / 4 + RS_HOLE_SLACK;  // the next launch may leave other holes
     }
     VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core scan: candidate list still too small");
     cudaEventDestroy(e0);
@@ -1266,7 +1268,7 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     int64_t cap = std::max<int64_t>(cq.n, n * (int64_t)(20 * KNN_SAMPLE) + (1 << 20));
     unsigned long long hn = 0;
     int herr = 0;
-    for (int attempt = 0; attempt < 2; attempt++) {
+    for (int attempt = 0; attempt < 3; attempt++) {
         cq.ensure(cap, s);
         cx.ensure(cap, s);
         R.cq = cq.p;
@@ -1280,7 +1282,7 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         VJ_CUDA(cudaStreamSynchronize(s));
         VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
         if ((int64_t)hn <= (int64_t)cq.n) break;
-        cap = (int64_t)hn + RS_HOLE_SLACK;  // the next launch may leave other holes
+        cap = (int64_t)hn + (int64_t)hn / 4 + RS_HOLE_SLACK;  // the next launch may leave other holes
     }
     VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core kNN: candidate list still too small");
     const int64_t nc = (int64_t)hn;
