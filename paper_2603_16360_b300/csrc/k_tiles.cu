@@ -766,14 +766,14 @@ void vj_build_knn(vj_index* ix) {
 
 void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids, DBuf<float>& dists,
                           int64_t* nnz_out, double* ms_out) {
-    vj_scan_rows_csr(ix, nullptr, ix->nq, eps, offsets, ids, dists, nnz_out, ms_out);
+    vj_scan_rows_csr(ix, nullptr, ix->nq, eps, offsets, ids, dists, nnz_out, ms_out, true);
 }
 
 // Exact join rows of the queries `qrows` (nullptr: all queries) by the
 // tensor-core scan and the exact re-check; CSR over all nq queries, rows of
 // queries not listed are empty.
 void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int64_t>& offsets,
-                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out) {
+                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out, bool sort_rows) {
     cudaStream_t s = ix->stream;
     const int64_t nx = ix->nx, nq = ix->nq;
     cudaEvent_t e0, e1;
@@ -826,9 +826,19 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
         k_nlj_scatter<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, cx.p, cd.p, nc, offsets.p, cursor.p, tid.p, td.p);
         VJ_LAUNCH_CHECK();
     }
-    ids.ensure(std::max<int64_t>(nnz, 1), s);
-    dists.ensure(std::max<int64_t>(nnz, 1), s);
-    vj_segment_sort_copy(offsets.p, counts.p, offsets.p, tid.p, td.p, ids.p, dists.p, nq, ix);
+    if (sort_rows) {
+        ids.ensure(std::max<int64_t>(nnz, 1), s);
+        dists.ensure(std::max<int64_t>(nnz, 1), s);
+        vj_segment_sort_copy(offsets.p, counts.p, offsets.p, tid.p, td.p, ids.p, dists.p, nq, ix);
+    } else {
+        // rows in scatter order: the caller sorts them with the rest of its result
+        ids.free_(s);
+        dists.free_(s);
+        ids = tid;
+        dists = td;
+        tid = DBuf<int32_t>();
+        td = DBuf<float>();
+    }
     VJ_CUDA(cudaEventRecord(e1, s));
     VJ_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;

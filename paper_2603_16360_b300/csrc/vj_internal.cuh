@@ -183,8 +183,12 @@ struct CsrOut {
 };
 void vj_exact_join_device(vj_index* ix, float eps, DBuf<int64_t>& offsets, DBuf<int32_t>& ids,
                           DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
+// exact rows of the queries qrows (all queries when NULL) from the tensor-core
+// scan, as a CSR over all nq queries; each row sorted by data id when
+// sort_rows, else in scatter order (the join sorts the routed rows later)
 void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int64_t>& offsets,
-                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out);
+                      DBuf<int32_t>& ids, DBuf<float>& dists, int64_t* nnz_out, double* ms_out,
+                      bool sort_rows = false);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
 // free the idle traversal workspaces of the process-wide cache
