@@ -85,27 +85,33 @@ __global__ void __launch_bounds__(256) k_query_stats(const float* __restrict__ v
     }
 }
 
+// warp per query: the seven features from lane 0, the query's coordinates
+// copied by all lanes (coalesced rows)
 __global__ void k_features(const float* __restrict__ vec, int dp, int d, int64_t nx, int64_t nq, int R,
                            const float* __restrict__ stat, const float* __restrict__ dn, float eps,
                            float* __restrict__ feat) {
-    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= nq) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qi >= nq) return;  // whole warps
     const int din = VJ_NFEAT + d;
     float* f = feat + qi * din;
-    const float d1 = stat[qi * NSTAT + 0], d2 = stat[qi * NSTAT + 1], de = stat[qi * NSTAT + 2];
-    const float dnn = stat[qi * NSTAT + 3], n1 = stat[qi * NSTAT + 4];
-    auto cap = [](float x) { return fminf(x, 100.f); };
     int nin = 0;
-    for (int j = 0; j < R; j++) nin += dn[qi * R + j] < eps;
-    f[0] = cap(d1 / eps);
-    f[1] = cap(d2 / eps);
-    f[2] = d2 > 0.f ? cap(d1 / d2) : 100.f;
-    f[3] = cap(de / eps);
-    f[4] = cap(dnn / eps);
-    f[5] = n1 / (float)R;
-    f[6] = (float)nin / (float)R;
+    for (int j = lane; j < R; j += 32) nin += dn[qi * R + j] < eps;
+    nin = __reduce_add_sync(VJ_FULL, nin);
+    if (lane == 0) {
+        const float d1 = stat[qi * NSTAT + 0], d2 = stat[qi * NSTAT + 1], de = stat[qi * NSTAT + 2];
+        const float dnn = stat[qi * NSTAT + 3], n1 = stat[qi * NSTAT + 4];
+        auto cap = [](float x) { return fminf(x, 100.f); };
+        f[0] = cap(d1 / eps);
+        f[1] = cap(d2 / eps);
+        f[2] = d2 > 0.f ? cap(d1 / d2) : 100.f;
+        f[3] = cap(de / eps);
+        f[4] = cap(dnn / eps);
+        f[5] = n1 / (float)R;
+        f[6] = (float)nin / (float)R;
+    }
     const float* q = vec + (nx + qi) * dp;
-    for (int i = 0; i < d; i++) f[VJ_NFEAT + i] = q[i];
+    for (int i = lane; i < d; i += 32) f[VJ_NFEAT + i] = q[i];
 }
 
 // plan from predictor outputs: route when the route logit exceeds lthr;
@@ -138,8 +144,8 @@ static void ensure_query_stats(vj_index* ix) {
 
 void vj_compute_features(vj_index* ix, float eps, float* feat_dev) {
     ensure_query_stats(ix);
-    k_features<<<vj_div_up(ix->nq, 128), 128, 0, ix->stream>>>(ix->vec.p, ix->dp, ix->d, ix->nx, ix->nq, ix->R,
-                                                               ix->qstat.p, ix->qdn.p, eps, feat_dev);
+    k_features<<<vj_div_up(ix->nq * 32, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->dp, ix->d, ix->nx, ix->nq,
+                                                                     ix->R, ix->qstat.p, ix->qdn.p, eps, feat_dev);
     VJ_LAUNCH_CHECK();
 }
 
