@@ -222,8 +222,9 @@ vj_status vj_join_device(vj_index *ix, float eps, int budget, vj_result **out);
  * result equals what vj_join gives for that instance alone.
  *   ixs [n]: distinct built indexes (an index listed twice -> VJ_ERR_ARG).  A
  *   predictor attached to several of them is shared safely (its inference is
- *   serialised).  The call uses each index's stream and borrows the largest
- *   index's traversal workspace.
+ *   serialised).  The call uses each index's stream; the fused passes run on
+ *   the largest index's stream with one traversal workspace from the
+ *   library's cache.
  *   eps [n] (host): per-instance thresholds, each > 0.
  *   outs [n] (host): receives n host results, each freed by vj_result_free.
  *   In each result's stats, ms_traverse is the time of the fused passes
@@ -284,6 +285,9 @@ vj_status vj_build_info(const vj_index *ix, int *knn_tensor_cores, int64_t *knn_
 
 /* Release a result (its arrays go back to the library's caches). */
 void vj_result_free(vj_result *r);
+/* Release an index.  Joins borrow their traversal workspace (GBs: visited
+ * lists and bitmaps per resident warp) from a process-wide cache, one per join
+ * running at once; freeing the last live index empties that cache. */
 void vj_free(vj_index *ix);
 const char *vj_last_error(void);
 
