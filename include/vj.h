@@ -208,7 +208,9 @@ vj_status vj_predictor_outputs(vj_index *ix, float eps, float *out);
  * budget > 0 overrides hybrid_beam for this call.  The result lives in host
  * memory (the device->host copy is part of the call).
  * Errors: VJ_ERR_ARG, VJ_ERR_OOM, VJ_ERR_CUDA, VJ_ERR_TIMEOUT (a work-sharing
- * dependency wait ran out; the index stays usable). */
+ * dependency wait ran out; the index stays usable).
+ * Threads: calls on one index must not overlap; joins of different indexes may
+ * run at the same time from different host threads. */
 vj_status vj_join(vj_index *ix, float eps, int budget, vj_result **out);
 
 /* As vj_join, but the result arrays stay in device memory (on_device = 1). */
