@@ -97,6 +97,7 @@ def test_full_size_exact_and_routed_rows_match_nlj(full, oracle):
     vj.vj_set_plan(ix, route=np.zeros(w.nq, np.uint8))
     assert int((r.hybrid == 2).sum()) == int(route.sum())
     nonempty = 0
+    worst = 0.0
     for k, q in enumerate(sample):
         exp = ids[off[k]:off[k + 1]]
         nonempty += len(exp) > 0
@@ -105,4 +106,11 @@ def test_full_size_exact_and_routed_rows_match_nlj(full, oracle):
         bad = _row_diff_outside_band(w, int(q), r.row(q), exp, eps)
         assert not bad, f"routed row, query {q}: pairs {bad[:5]} differ"
         assert np.all(np.diff(r.row(q)) > 0)  # ascending data ids
+        # returned distances against FP64
+        for res in (ex, r):
+            lo, hi = res.offsets[q], res.offsets[q + 1]
+            for x, dv in zip(res.ids[lo:hi], res.dists[lo:hi]):
+                ref = _d64(w, int(q), int(x))
+                worst = max(worst, abs(float(dv) - ref) / max(ref, 1e-30))
     assert nonempty >= 20
+    assert worst <= 1e-5, worst
