@@ -221,6 +221,79 @@ def slowest_rank_ms(ms, dist, device):
     return float(t.item())
 
 
+def collection_learned_arm(vj, ixs, eps, exs, nxs, nqs, pooled_recall, steps):
+    """One predictor for the whole collection: trained on the labels of the
+    six cheapest instances (per query: the smallest hybrid queue size on the
+    ladder {0, 8, 32} reaching recall 0.95, and the route to the scan when none
+    does or when the BFS costs more than a scan row), attached to every index,
+    then the largest route threshold whose batched join reaches pooled recall
+    0.95 (non-routed queries run the BFS closure)."""
+    order = np.argsort([nq * nx for nq, nx in zip(nqs, nxs)], kind="stable")
+    train_ids = [int(i) for i in order[:6]]
+    Fs, yb, yr = [], [], []
+    ladder = [0, 8, 32]
+    for i in train_ids:
+        ix, e, ex, nx = ixs[i], eps[i], exs[i], nxs[i]
+        recs = {}
+        for b in ladder:
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=int(b > 0),
+                                  hybrid_beam=max(b, 1), learned=0)
+            r = vj.vj_join(ix, e)
+            h, tot = per_query_hits(r, ex, nx)
+            recs[b] = np.where(tot > 0, h / np.maximum(tot, 1), 1.0)
+            if b == 0:
+                s0, st0 = r.steps.astype(np.float64), r.stats
+        t_step = st0["ms_traverse"] / max(s0.sum(), 1.0)
+        t_bf = ex.stats["ms_scan"] / len(s0)
+        budget = np.full(len(s0), ladder[-1], np.int32)
+        for b in reversed(ladder):
+            budget = np.where(recs[b] >= 0.95, b, budget)
+        route = (recs[ladder[-1]] < 0.95) | (s0 * t_step >= t_bf)
+        Fs.append(vj.vj_features(ix, e))
+        yb.append(np.log2(budget + 1.0))
+        yr.append(route.astype(np.float32))
+    F = np.concatenate(Fs)
+    mlp = vj.MLP(F.shape[1], 256, 256, seed=7)
+    t0 = time.perf_counter()
+    loss = mlp.train(F, np.concatenate(yb).astype(np.float32), np.concatenate(yr), epochs=30, batch=256, lr=1e-3,
+                     seed=7)
+    train_s = time.perf_counter() - t0
+    sweep, best = [], None
+    for thr in (0.9, 0.7, 0.5, 0.3, 0.15, 0.05):
+        for ix in ixs:
+            vj.vj_attach_predictor(ix, mlp, thr, 0)
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0, hybrid_beam=1,
+                                  learned=1)
+        vj.vj_join_batch(ixs, eps)
+        t0 = time.perf_counter()
+        rs = vj.vj_join_batch(ixs, eps)
+        ms = 1e3 * (time.perf_counter() - t0)
+        rec = pooled_recall(rs)
+        routed = int(sum(int((r.hybrid == 2).sum()) for r in rs))
+        sweep.append({"thr": thr, "recall": round(rec, 4), "ms": round(ms, 1), "routed": routed})
+        if rec >= 0.95 and (best is None or ms < best[1]):
+            best = (thr, ms)
+    out = {"train_instances": train_ids, "train_queries": int(F.shape[0]), "train_s": round(train_s, 1),
+           "final_loss": loss, "sweep": sweep}
+    if best is not None:
+        thr = best[0]
+        for ix in ixs:
+            vj.vj_attach_predictor(ix, mlp, thr, 0)
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            rs = vj.vj_join_batch(ixs, eps)
+            ts.append(1e3 * (time.perf_counter() - t0))
+        ms = statistics.median(ts)
+        out.update({"thr": thr, "ms_per_step": ms, "queries_per_s": int(sum(nqs)) / (ms / 1e3),
+                    "recall": pooled_recall(rs), "routed_frac": sum(int((r.hybrid == 2).sum()) for r in rs) / sum(nqs)})
+    for ix in ixs:
+        vj.vj_set_join_params(ix, learned=0)
+        vj.vj_attach_predictor(ix, None, 0.5, 0)
+    mlp.free()
+    return out
+
+
 def bench_collection(args, vj, torch):
     """A collection of independent join instances of very different sizes
     (angular_collection: |X| log-uniform 1e4..2e6 and |Q| 1e3..2e5, both times
@@ -324,6 +397,9 @@ def bench_collection(args, vj, torch):
             "e2e": {"value": total_q / (b_ms / 1e3), "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": d2h},
             "clocks": cs.summary()}
+    if args.collection_learned:
+        line["config"]["learned"] = collection_learned_arm(vj, ixs, eps, exs, nxs, nqs, pooled_recall,
+                                                           max(3, args.steps))
     print(json.dumps(line), flush=True)
     for ix in ixs:
         ix.free()
@@ -340,6 +416,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-only", action="store_true")
     ap.add_argument("--instances", type=int, default=64, help="angular_collection: number of join instances")
+    ap.add_argument("--collection-learned", action="store_true",
+                    help="angular_collection: also time one shared predictor's learned route")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
