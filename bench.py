@@ -259,7 +259,7 @@ def collection_learned_arm(vj, ixs, eps, exs, nxs, nqs, pooled_recall, steps):
                      seed=7)
     train_s = time.perf_counter() - t0
     sweep, best = [], None
-    for thr in (0.9, 0.7, 0.5, 0.3, 0.15, 0.05):
+    for thr in (0.999, 0.99, 0.97, 0.9, 0.7, 0.5, 0.3):
         for ix in ixs:
             vj.vj_attach_predictor(ix, mlp, thr, 0)
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0, hybrid_beam=1,
