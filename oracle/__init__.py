@@ -5,6 +5,8 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 its Python binding) never imports, links or calls it, and it shares no code
 with that path: the arithmetic lives in ``vj_oracle.c`` (plain single-threaded
 loops, FP64 accumulation) and this module only marshals numpy arrays into it.
+``nnmap.py`` holds the oracle of the NN-Map design in plain Python (small
+inputs only).
 
 Naming follows the build's convention: ``X`` = data vectors (node ids
 ``0..nx-1``), ``Q`` = query vectors (node ids ``nx..nx+nq-1``); the paper
