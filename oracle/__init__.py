@@ -82,6 +82,7 @@ class _Cfg(C.Structure):
         ("hybrid_beam_size", C.c_int),
         ("route", C.c_void_p),
         ("beam", C.c_void_p),
+        ("separate", C.c_int),
     ]
 
 
@@ -160,6 +161,21 @@ def mst(X, Q, adj, entry: int, metric: int = L2):
     return parent, order, depth, w
 
 
+def separate_mst(X, Q, adj_q, entry: int, metric: int = L2):
+    """Order and parents of separate-index work sharing (Sec. 3.2 WS, Alg. 2):
+    the MST over the query graph G_X (adj_q: [nq][R] query ids, -1 padded)
+    plus an edge from the data entry s_Y to every query, rooted at s_Y.
+    Returns (parent, order, depth, total_weight) as `mst` does."""
+    X, Q = _f32(X), _f32(Q)
+    nx, nq = X.shape[0], Q.shape[0]
+    adj_q = np.asarray(adj_q, np.int32)
+    R = adj_q.shape[1]
+    # the same Prim routine, on a node set whose query rows hold G_X's edges
+    adj_m = np.full((nx + nq, R), -1, np.int32)
+    adj_m[nx:] = np.where(adj_q >= 0, adj_q + nx, -1)
+    return mst(X, Q, adj_m, entry, metric)
+
+
 def ood(X, Q, adj, node: int, metric: int = L2):
     """OOD predictor of Sec. 4.4 for merged node id `node`: (flag, d1, d2)."""
     X, Q = _f32(X), _f32(Q)
@@ -188,7 +204,7 @@ class JoinResult:
 def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: int = WS_SELF,
          force_hybrid: bool = False, adapt_hybrid: bool = False, greedy_beam_size: int = 256,
          conv_threshold: int = 10, hybrid_beam_size: int = 256, order=None, parent=None,
-         queries=None, route=None, beam=None) -> JoinResult:
+         queries=None, route=None, beam=None, separate: bool = False) -> JoinResult:
     """Alg. 1 VectorJoin on the merged index.
 
     route/beam (optional, per query) replace Alg. 6's rule with a plan:
@@ -197,7 +213,11 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
     size, beam[q] = 0 the BFS expansion.
 
     order/parent default to the MST of `mst()` when work sharing is hard/soft,
-    else to index order.  `queries` (optional) restricts the run to that list of
+    else to index order.
+
+    separate=True runs the separate-index execution (Sec. 3.2 INLJ, HWS/SWS on
+    a per-set index): adj is the data graph G_Y ([nx][R]) with entry s_Y, and
+    with hard/soft sharing order/parent must be given (`separate_mst`).  `queries` (optional) restricts the run to that list of
     query indices, processed in the given order; it must be closed under MST
     parents when sharing is on (a set of whole subtrees).
     """
@@ -206,6 +226,8 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
     nq = Q.shape[0]
     adj = np.ascontiguousarray(adj, dtype=np.int32)
     R = adj.shape[1]
+    if separate and work_sharing in (WS_HARD, WS_SOFT) and (order is None or parent is None):
+        raise ValueError("separate-index sharing needs the order and parents of separate_mst()")
     if work_sharing in (WS_HARD, WS_SOFT) and (order is None or parent is None):
         p, o, _, _ = mst(X, Q, adj, entry, metric)
         parent = p if parent is None else parent
@@ -215,7 +237,7 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
     route_a = None if route is None else np.ascontiguousarray(route, dtype=np.uint8)
     beam_a = None if beam is None else np.ascontiguousarray(beam, dtype=np.int32)
     cfg = _Cfg(work_sharing, int(force_hybrid), int(adapt_hybrid), greedy_beam_size, conv_threshold, hybrid_beam_size,
-               _ptr(route_a), _ptr(beam_a))
+               _ptr(route_a), _ptr(beam_a), int(separate))
     lib = _load()
     order_a = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     parent_a = None if parent is None else np.ascontiguousarray(parent, dtype=np.int32)

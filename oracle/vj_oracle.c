@@ -552,6 +552,13 @@ typedef struct {
      * beam[qi] > 0, the plain BFS expansion when beam[qi] == 0.  NULL: unused. */
     const uint8_t *route;
     const int32_t *beam;
+    /* 1: separate-index execution (cfg.merged = false, Sec. 3.2 INLJ and its
+     * work sharing): `adj` is the data graph G_Y ([nx][R], data ids only),
+     * `entry` its entry s_Y, the query is not a graph node, StopGreedy's
+     * third rule is off and CheckHybrid ignores adapt_hybrid (Alg. 6).  With
+     * hard/soft sharing the order and parents come from the MST over the
+     * query graph G_X (Alg. 2).  0: the merged index. */
+    int separate;
 } vjo_cfg;
 
 /* per-query outputs of vjo_join */
@@ -646,6 +653,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
         /* parent's cache; self adds q.  Reading: under the merged index, soft  */
         /* sharing seeds with q as well (otherwise StopGreedy's third rule ends */
         /* the walk before any neighbourhood is probed).                        */
+        const int merged = !cfg->separate;
         int32_t S[2 + 1];
         int nS = 0;
         S[nS++] = entry;
@@ -654,15 +662,15 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
         int64_t par = parent ? parent[qi] : -1;
         if (cfg->work_sharing == VJO_WS_SOFT) {
             if (par >= 0 && cache[par] >= 0) S[nS++] = cache[par];
-            S[nS++] = qn;
+            if (merged) S[nS++] = qn;
         } else if (cfg->work_sharing == VJO_WS_HARD) {
             if (par >= 0) {
                 hseed = hard[par];
                 nhseed = hard_n[par];
             }
-            S[nS++] = qn;
+            if (merged) S[nS++] = qn;
         } else if (cfg->work_sharing == VJO_WS_SELF) {
-            S[nS++] = qn;
+            if (merged) S[nS++] = qn; /* self seeding exists only on the merged index */
         }
 
         /* --- Alg. 4 GreedySearchPhase */
@@ -696,7 +704,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
                 }
                 if (no_improve >= cfg->conv_threshold) stop = 1;
             }
-            if (!stop && f.id != qn) stop = 1; /* merged index: only q's neighbourhood */
+            if (merged && !stop && f.id != qn) stop = 1; /* merged index: only q's neighbourhood */
             if (stop) break;
             /* pop front */
             int32_t u = f.id;
@@ -722,7 +730,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
         if (cfg->beam) {
             beam = cfg->beam[qi];
             hyb = beam > 0;
-        } else if (cfg->adapt_hybrid) {
+        } else if (cfg->adapt_hybrid && merged) {
             hyb = vjo_ood(X, nx, Q, d, metric, adj, R, qn, NULL, NULL);
         } else {
             hyb = cfg->force_hybrid;

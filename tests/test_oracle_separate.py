@@ -1,0 +1,93 @@
+"""Pins of the oracle's separate-index execution (Sec. 3.2: INLJ on a per-set
+index G_Y, and its hard / soft work sharing in MST order), the base of the
+paper's INLJ, HWS and SWS comparisons.  Hand-traced cases on a chain of data
+points, the complete graph against the nested-loop join, and precision on a
+random graph."""
+import numpy as np
+import pytest
+
+
+def _chain(n):
+    """Data points 0..n-1 on a line, each adjacent to its two neighbours."""
+    X = np.arange(n, dtype=np.float32)[:, None]
+    adj = np.array([[i - 1 if i > 0 else -1, i + 1 if i < n - 1 else -1] for i in range(n)], np.int32)
+    return X, adj
+
+
+def test_inlj_hand_traced_on_a_chain(oracle):
+    """Entry 0, query at 50.3, eps 2: the greedy walks 0, 1, ..., 49 and stops
+    at the in-range front 49 before popping it (50 visited nodes); the BFS from
+    49 then visits 50, 51, 52, 53 and keeps 49..52."""
+    X, adj = _chain(100)
+    Q = np.array([[50.3]], np.float32)
+    r = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_NONE, conv_threshold=1000, separate=True)
+    assert r.row(0).tolist() == [49, 50, 51, 52]
+    assert r.steps[0] == 54
+    q64 = float(np.float32(50.3))  # the FP32 input, evaluated in FP64
+    np.testing.assert_allclose(r.dists, [abs(q64 - v) for v in (49, 50, 51, 52)], rtol=1e-12)
+
+
+def test_inlj_convergence_rule_stops_the_walk(oracle):
+    """conv_threshold 0 stops at the first check: only the entry is evaluated,
+    and an out-of-range entry gives an empty row."""
+    X, adj = _chain(100)
+    Q = np.array([[50.3]], np.float32)
+    r = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_NONE, conv_threshold=0, separate=True)
+    assert len(r.row(0)) == 0 and r.steps[0] == 1
+
+
+def test_hard_and_soft_sharing_hand_traced(oracle):
+    """Queries at 50.3 and 50.6; the query-graph MST makes the first the parent
+    of the second.  Hard sharing seeds the child with the parent's whole row,
+    soft sharing with the parent's closest visited data node (50)."""
+    X, adj = _chain(100)
+    Q = np.array([[50.3], [50.6]], np.float32)
+    adj_q = np.array([[1], [0]], np.int32)
+    parent, order, _, _ = oracle.separate_mst(X, Q, adj_q, 0)
+    assert parent.tolist() == [-1, 0] and order.tolist() == [0, 1]
+    kw = dict(conv_threshold=1000, separate=True, order=order, parent=parent)
+    h = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_HARD, **kw)
+    s = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_SOFT, **kw)
+    for r in (h, s):
+        assert r.row(0).tolist() == [49, 50, 51, 52] and r.steps[0] == 54
+        assert r.row(1).tolist() == [49, 50, 51, 52]
+    # hard: seeds 0, 49..52 (5), then 48 and 53; soft: seeds 0, 50, then 49, 51, 48, 52, 53
+    assert h.steps[1] == 7 and s.steps[1] == 7
+    assert s.cache[0] == 50 and s.cache[1] == 51
+
+
+def test_inlj_on_the_complete_graph_is_the_nested_loop_join(oracle):
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((80, 5)).astype(np.float32)
+    Q = rng.standard_normal((20, 5)).astype(np.float32)
+    adj = np.array([[v for v in range(80) if v != u] for u in range(80)], np.int32)
+    eps = 1.6
+    r = oracle.join(X, Q, adj, 0, eps, work_sharing=oracle.WS_NONE, separate=True)
+    off, ids, dd = oracle.nlj(X, Q, eps)
+    np.testing.assert_array_equal(r.offsets, off)
+    np.testing.assert_array_equal(r.ids, ids)
+    np.testing.assert_allclose(r.dists, dd, rtol=1e-12)
+
+
+@pytest.mark.parametrize("ws", ["none", "hard", "soft"])
+def test_separate_joins_return_only_true_pairs(oracle, ws):
+    rng = np.random.default_rng(32)
+    centres = rng.standard_normal((5, 8)) * 3
+    X = (centres[rng.integers(0, 5, 500)] + rng.standard_normal((500, 8))).astype(np.float32)
+    Q = (centres[rng.integers(0, 5, 60)] + rng.standard_normal((60, 8))).astype(np.float32)
+    empty = np.zeros((0, 8), np.float32)
+    adj_x, entry, _ = oracle.build_graph(X, empty, 8, 16)
+    adj_q, _, _ = oracle.build_graph(Q, empty, 6, 12)
+    parent, order, _, _ = oracle.separate_mst(X, Q, adj_q, entry)
+    eps = 2.5
+    mode = {"none": oracle.WS_NONE, "hard": oracle.WS_HARD, "soft": oracle.WS_SOFT}[ws]
+    r = oracle.join(X, Q, adj_x, entry, eps, work_sharing=mode, separate=True, order=order, parent=parent)
+    off, ids, _ = oracle.nlj(X, Q, eps)
+    found = tot = 0
+    for q in range(len(Q)):
+        exact = set(ids[off[q]:off[q + 1]].tolist())
+        got = set(r.row(q).tolist())
+        assert got <= exact
+        found += len(got)
+        tot += len(exact)
+    assert tot > 0 and found > 0  # recall may be low: INLJ's greedy can miss in-range regions
