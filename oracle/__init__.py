@@ -83,6 +83,7 @@ class _Cfg(C.Structure):
         ("route", C.c_void_p),
         ("beam", C.c_void_p),
         ("separate", C.c_int),
+        ("hybrid_seed_best", C.c_int),
     ]
 
 
@@ -204,7 +205,8 @@ class JoinResult:
 def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: int = WS_SELF,
          force_hybrid: bool = False, adapt_hybrid: bool = False, greedy_beam_size: int = 256,
          conv_threshold: int = 10, hybrid_beam_size: int = 256, order=None, parent=None,
-         queries=None, route=None, beam=None, separate: bool = False) -> JoinResult:
+         queries=None, route=None, beam=None, separate: bool = False,
+         hybrid_seed_best: bool = False) -> JoinResult:
     """Alg. 1 VectorJoin on the merged index.
 
     route/beam (optional, per query) replace Alg. 6's rule with a plan:
@@ -214,6 +216,10 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
 
     order/parent default to the MST of `mst()` when work sharing is hard/soft,
     else to index order.
+
+    hybrid_seed_best=True starts a hybrid expansion whose greedy phase found no
+    in-range point from the closest visited data node (a variant; the literal
+    reading returns an empty row).
 
     separate=True runs the separate-index execution (Sec. 3.2 INLJ, HWS/SWS on
     a per-set index): adj is the data graph G_Y ([nx][R]) with entry s_Y, and
@@ -237,7 +243,7 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
     route_a = None if route is None else np.ascontiguousarray(route, dtype=np.uint8)
     beam_a = None if beam is None else np.ascontiguousarray(beam, dtype=np.int32)
     cfg = _Cfg(work_sharing, int(force_hybrid), int(adapt_hybrid), greedy_beam_size, conv_threshold, hybrid_beam_size,
-               _ptr(route_a), _ptr(beam_a), int(separate))
+               _ptr(route_a), _ptr(beam_a), int(separate), int(hybrid_seed_best))
     lib = _load()
     order_a = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     parent_a = None if parent is None else np.ascontiguousarray(parent, dtype=np.int32)

@@ -559,6 +559,10 @@ typedef struct {
      * hard/soft sharing the order and parents come from the MST over the
      * query graph G_X (Alg. 2).  0: the merged index. */
     int separate;
+    /* 1: a hybrid expansion whose greedy phase found no in-range point starts
+     * from the closest visited data node instead of returning an empty row
+     * (the "seed with the best" variant; the paper's literal reading is 0). */
+    int hybrid_seed_best;
 } vjo_cfg;
 
 /* per-query outputs of vjo_join */
@@ -741,6 +745,23 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
         for (int64_t j = 0; j < nI && !routed; j++) {
             cand_t c = {dv[I[j]], I[j]};
             PQ_PUSH(c);
+        }
+        if (cfg->hybrid_seed_best && hyb && nI == 0 && !routed) {
+            /* no in-range point: start from the closest visited data node */
+            int32_t bid = -1;
+            double bd = INFINITY;
+            for (int64_t j = 0; j < nvis; j++) {
+                int32_t v = vis[j];
+                if (v >= nx) continue;
+                if (dv[v] < bd || (dv[v] == bd && v < bid)) {
+                    bd = dv[v];
+                    bid = v;
+                }
+            }
+            if (bid >= 0) {
+                cand_t c = {bd, bid};
+                PQ_PUSH(c);
+            }
         }
         int64_t expansions = 0;
         while (npq > 0) {

@@ -91,3 +91,26 @@ def test_separate_joins_return_only_true_pairs(oracle, ws):
         found += len(got)
         tot += len(exact)
     assert tot > 0 and found > 0  # recall may be low: INLJ's greedy can miss in-range regions
+
+
+def test_hybrid_seed_best_variant(oracle):
+    """With the walk stopped at the entry (conv_threshold 0) the greedy phase
+    finds nothing in range.  The literal hybrid expansion then has nothing to
+    expand; the seed-with-the-best variant walks from the entry along the
+    chain and reaches the in-range points, visiting 0..53 like the full INLJ
+    walk."""
+    X, adj = _chain(100)
+    Q = np.array([[50.3]], np.float32)
+    kw = dict(work_sharing=oracle.WS_NONE, conv_threshold=0, separate=True, force_hybrid=True,
+              hybrid_beam_size=4)
+    lit = oracle.join(X, Q, adj, 0, 2.0, **kw)
+    best = oracle.join(X, Q, adj, 0, 2.0, hybrid_seed_best=True, **kw)
+    assert len(lit.row(0)) == 0 and lit.steps[0] == 1
+    assert best.row(0).tolist() == [49, 50, 51, 52]
+    assert best.steps[0] == 100  # the hybrid queue keeps out-range nodes: the walk runs to the chain's end
+    # the variant only changes queries with an empty greedy result
+    on = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_NONE, conv_threshold=1000, separate=True,
+                     force_hybrid=True, hybrid_beam_size=4, hybrid_seed_best=True)
+    off = oracle.join(X, Q, adj, 0, 2.0, work_sharing=oracle.WS_NONE, conv_threshold=1000, separate=True,
+                      force_hybrid=True, hybrid_beam_size=4)
+    assert on.row(0).tolist() == off.row(0).tolist() and on.steps[0] == off.steps[0]
