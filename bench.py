@@ -157,6 +157,12 @@ def recall_of(r, ex, nx):
     return float(hits.sum() / max(tot.sum(), 1))
 
 
+def per_query_recall_mean(r, ex, nx):
+    """Mean over queries of |R n E| / |E|; a query with an empty exact row counts 1."""
+    hits, tot = per_query_hits(r, ex, nx)
+    return float(np.where(tot > 0, hits / np.maximum(tot, 1), 1.0).mean())
+
+
 def sample_subtrees(parent, order, target=1000):
     """Whole MST subtrees (children of the entry) totalling >= target queries, in order."""
     nq = len(parent)
@@ -572,7 +578,8 @@ def main():
         learned = {"thr": thr, "beam_cap": lcap, "sweep": sweep, "recall": lrec, "ms": l_ms, "stats": l_stats,
                    "route_acc": route_acc,
                    "routed_frac": float((lr_.hybrid == 2).mean()), "train_s": train_s, "final_loss": final_loss,
-                   "labels_route_frac": float(route_lab.mean()), "t_bf_ms": t_bf, "t_step_ms": t_step}
+                   "labels_route_frac": float(route_lab.mean()), "t_bf_ms": t_bf, "t_step_ms": t_step,
+                   "recall_per_query_mean": per_query_recall_mean(lr_, ex, w.nx)}
 
     # ---- headline arm and its rooflines
     if learned is not None:
@@ -629,7 +636,9 @@ def main():
     if dist:
         step_ms = slowest_rank_ms(step_ms, dist, "cuda")
         value = world * w.nq / (step_ms / 1e3)
-    cfg = {"workload": wl_desc, "arm": arm, "recall": rec, "eps": eps, "degree": info["degree"],
+    rec_q = learned["recall_per_query_mean"] if learned is not None else per_query_recall_mean(pr, ex, w.nx)
+    cfg = {"workload": wl_desc, "arm": arm, "recall": rec, "recall_per_query_mean": rec_q, "eps": eps,
+           "degree": info["degree"],
            "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "build_s": build_s,
            "pairs": int(stats[-1]["nnz"]), "pairs_per_s": world * stats[-1]["nnz"] / (step_ms / 1e3),
            "l2": "inputs larger than L2 (vectors %.0f MB)" % ((w.X.nbytes + w.Q.nbytes) / 1e6),

@@ -81,3 +81,11 @@ def test_clock_summary_flags_throttle_reasons():
 
 def test_slowest_rank_without_process_group():
     assert bench.slowest_rank_ms(3.5, None, "cpu") == 3.5
+
+
+def test_per_query_recall_mean_counts_empty_rows_as_one():
+    ex = _R([[1, 2, 3, 4], [], [7]])
+    got = _R([[1, 2], [5], []])
+    # 2/4, empty exact row -> 1, 0/1
+    assert abs(bench.per_query_recall_mean(got, ex, 10) - (0.5 + 1.0 + 0.0) / 3) < 1e-12
+    assert abs(bench.recall_of(got, ex, 10) - 2 / 5) < 1e-12
