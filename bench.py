@@ -660,7 +660,8 @@ def main():
             "clocks": cs.summary(),
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt = run_cpu_oracle(w, vj, ix, eps, 1000, pmode, pbudget)
+        # a bounded sample: whole MST subtrees of about 15,000 queries, some seconds of one core
+        n, dt = run_cpu_oracle(w, vj, ix, eps, 15000, pmode, pbudget)
         line["cpu_baseline"] = {"value": n / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} queries (whole MST subtrees) of the same workload on the GPU-built "
                                           f"graph, oracle MI+SWS join (hybrid={pmode}, beam {pbudget}), FP64, "
