@@ -20,7 +20,8 @@ Readings (the design is sketched, not fully specified):
   * OOD bit: the d1/d2 rule of Alg. 6 with N1 = the query's R nearest data
     vectors (the neighbourhood a merged-index insertion would start from),
     d2 = mean length of the G_X edges from N1 to data nodes outside N1;
-    OOD iff d1/d2 > 1.5, and no such edge means not OOD;
+    OOD iff d1/d2 > 1.5, and no such edge means not OOD (parity unpinned
+    against the paper beyond the far-query trend);
   * distance computations ("steps"): the witness distance is stored, so the
     seed costs none; every other node the expansion evaluates costs one.
 """

@@ -28,7 +28,10 @@
  *                     beyond the App. C invariant)
  *   vjo_mst           Prim MST over query nodes plus star edges from the entry
  *                     (Sec. 3.2 WS, Alg. 2)
- *   vjo_ood           d1/d2 > 1.5 OOD predictor (Sec. 4.4)
+ *   vjo_ood           d1/d2 > 1.5 OOD predictor (Sec. 4.4; the pair set is this
+ *                     project's reading of "2-hop neighbours": parity unpinned
+ *                     against the paper beyond hand-computed cases and the
+ *                     far-query trend, the paper prints no per-query values)
  *   vjo_join          Alg. 1 VectorJoin with Alg. 2-8 in the paper's order
  */
 #include <math.h>
