@@ -60,6 +60,10 @@ def _load():
         lib.vjo_ood.argtypes = [p, i64, p, i32, i32, p, i32, i64, p, p]
         lib.vjo_join.restype = i64
         lib.vjo_join.argtypes = [p, i64, p, i64, i32, i32, p, i32, C.c_int32, p, i64, p, p, dbl, p]
+        lib.vjo_nnmap_build.restype = None
+        lib.vjo_nnmap_build.argtypes = [p, i64, p, i64, i32, i32, p, i32, p, p, p]
+        lib.vjo_nnmap_join.restype = i64
+        lib.vjo_nnmap_join.argtypes = [p, i64, p, i64, i32, i32, p, i32, p, p, p, i32, i32, dbl, p, p, p, i64, p, p]
         _lib = lib
     return _lib
 
@@ -285,3 +289,47 @@ def recall(offsets, ids, ex_offsets, ex_ids):
         per[q] = h / len(e)
     tot = int(ex_offsets[-1])
     return (hit / tot if tot else 1.0), float(per.mean())
+
+
+def nnmap_build_c(X, Q, adj_x, metric: int = L2):
+    """NN-Map witnesses, witness distances and OOD bits (Sec. NN-Map), in C;
+    the same readings as ``nnmap.nnmap_build``."""
+    from .nnmap import NNMap
+    X, Q = _f32(X), _f32(Q)
+    nx, d = X.shape
+    nq = Q.shape[0]
+    adj_x = np.ascontiguousarray(adj_x, dtype=np.int32)
+    w = np.zeros(nq, np.int32)
+    wd = np.zeros(nq, np.float64)
+    ood = np.zeros(nq, np.uint8)
+    _load().vjo_nnmap_build(_ptr(X), nx, _ptr(Q), nq, d, metric, _ptr(adj_x), adj_x.shape[1], _ptr(w), _ptr(wd),
+                            _ptr(ood))
+    return NNMap(w, wd, ood)
+
+
+def nnmap_join_c(X, Q, adj_x, nm, eps: float, *, metric: int = L2, hybrid: str = "adapt",
+                 hybrid_beam_size: int = 256):
+    """The NN-Map join (Sec. NN-Map) in C; the same semantics as ``nnmap.nnmap_join``."""
+    from .nnmap import NNMapResult
+    X, Q = _f32(X), _f32(Q)
+    nx, d = X.shape
+    nq = Q.shape[0]
+    adj_x = np.ascontiguousarray(adj_x, dtype=np.int32)
+    mode = {"off": 0, "adapt": 1, "force": 2}[hybrid]
+    w = np.ascontiguousarray(nm.witness, np.int32)
+    wd = np.ascontiguousarray(nm.wdist, np.float64)
+    ood = np.ascontiguousarray(nm.ood, np.uint8)
+    offsets = np.zeros(nq + 1, np.int64)
+    steps = np.zeros(nq, np.int64)
+    hyb = np.zeros(nq, np.uint8)
+    cap = 1 << 16
+    while True:
+        ids = np.zeros(cap, np.int32)
+        dists = np.zeros(cap, np.float64)
+        total = _load().vjo_nnmap_join(_ptr(X), nx, _ptr(Q), nq, d, metric, _ptr(adj_x), adj_x.shape[1], _ptr(w),
+                                       _ptr(wd), _ptr(ood), mode, int(hybrid_beam_size), float(eps), _ptr(offsets),
+                                       _ptr(ids), _ptr(dists), cap, _ptr(steps), _ptr(hyb))
+        if total <= cap:
+            break
+        cap = int(total)
+    return NNMapResult(offsets, ids[:total], dists[:total], steps, hyb)

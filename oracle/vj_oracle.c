@@ -33,6 +33,8 @@
  *                     against the paper beyond hand-computed cases and the
  *                     far-query trend, the paper prints no per-query values)
  *   vjo_join          Alg. 1 VectorJoin with Alg. 2-8 in the paper's order
+ *   vjo_nnmap_build   NN-Map witnesses and OOD bits (Sec. NN-Map)
+ *   vjo_nnmap_join    the join from the witnesses on the data graph (Sec. NN-Map)
  */
 #include <math.h>
 #include <stdint.h>
@@ -875,4 +877,132 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
 #undef VISITED
 #undef PQ_PUSH
 #undef I_PUSH
+}
+
+/* ------------------------------------------------------------------ */
+/* NN-Map (Sec. NN-Map): a materialised top-1 join index from the       */
+/* queries to the data, and the join that expands from it on the data's */
+/* own graph G_X (adj: [nx][R] data ids).  Readings as in nnmap.py.     */
+/* ------------------------------------------------------------------ */
+
+/* witness[q]: the nearest data vector (ties by id), wdist[q] its distance;
+ * ood[q]: d1/d2 > 1.5 with N1 = the R nearest data vectors of q, d1 = their
+ * mean distance to q, d2 = the mean length of the G_X edges from N1 to data
+ * vectors outside N1 (no such edge: not OOD) */
+void vjo_nnmap_build(const float *X, int64_t nx, const float *Q, int64_t nq, int d, int metric,
+                     const int32_t *adj, int R, int32_t *witness, double *wdist, uint8_t *ood)
+{
+    cand_t *nb = (cand_t *)malloc((size_t)(R + 1) * sizeof(cand_t));
+    for (int64_t q = 0; q < nq; q++) {
+        const float *qv = Q + (size_t)q * d;
+        int64_t n1 = 0;
+        for (int64_t x = 0; x < nx; x++) {
+            cand_t c = {vjo_dist(X + (size_t)x * d, qv, d, metric), (int32_t)x};
+            if (n1 < R) {
+                sorted_insert(nb, &n1, c);
+            } else if (cand_less(c, nb[R - 1])) {
+                n1--;
+                sorted_insert(nb, &n1, c);
+            }
+        }
+        witness[q] = nb[0].id;
+        wdist[q] = nb[0].d;
+        double d1 = 0.0, s2 = 0.0;
+        int64_t c2 = 0;
+        for (int64_t j = 0; j < n1; j++) d1 += nb[j].d;
+        d1 /= (double)n1;
+        for (int64_t j = 0; j < n1; j++) {
+            int32_t v = nb[j].id;
+            for (int k = 0; k < R; k++) {
+                int32_t u = adj[(int64_t)v * R + k];
+                if (u < 0) continue;
+                int inside = 0;
+                for (int64_t t = 0; t < n1; t++) inside |= nb[t].id == u;
+                if (inside) continue;
+                s2 += vjo_dist(X + (size_t)v * d, X + (size_t)u * d, d, metric);
+                c2++;
+            }
+        }
+        ood[q] = (uint8_t)(c2 > 0 && s2 > 0.0 && d1 / (s2 / (double)c2) > 1.5);
+    }
+    free(nb);
+}
+
+/* hybrid_mode: 0 BFS closure for every query, 1 the OOD bit, 2 hybrid for
+ * every query.  A query with wdist >= eps is certainly empty and computes no
+ * distance; otherwise Alg. 7 runs from its witness on G_X (min-queue by
+ * (dist, id); hybrid: out-range nodes queued, the largest dropped once the
+ * queue holds more than `beam`).  steps[q] counts distance computations (the
+ * stored witness distance costs none).  Returns the total pair count. */
+int64_t vjo_nnmap_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, int metric,
+                       const int32_t *adj, int R, const int32_t *witness, const double *wdist,
+                       const uint8_t *ood, int hybrid_mode, int beam, double eps, int64_t *offsets,
+                       int32_t *ids, double *dists, int64_t cap, int64_t *steps, uint8_t *hyb_out)
+{
+    int64_t *stamp = (int64_t *)malloc((size_t)nx * sizeof(int64_t));
+    double *dv = (double *)malloc((size_t)nx * sizeof(double));
+    for (int64_t u = 0; u < nx; u++) stamp[u] = -1;
+    int64_t qcap = 1024, rcap = 1024;
+    cand_t *pq = (cand_t *)malloc((size_t)qcap * sizeof(cand_t));
+    int32_t *res = (int32_t *)malloc((size_t)rcap * sizeof(int32_t));
+    int64_t total = 0;
+    for (int64_t q = 0; q < nq; q++) {
+        offsets[q] = total;
+        steps[q] = 0;
+        hyb_out[q] = 0;
+        if (wdist[q] >= eps) continue; /* certified empty */
+        const float *qv = Q + (size_t)q * d;
+        const int hyb = hybrid_mode == 2 || (hybrid_mode == 1 && ood[q]);
+        hyb_out[q] = (uint8_t)hyb;
+        int64_t npq = 0, nres = 0;
+        int32_t s = witness[q];
+        stamp[s] = q;
+        dv[s] = wdist[q];
+        res[nres++] = s;
+        cand_t c0 = {wdist[q], s};
+        sorted_insert(pq, &npq, c0);
+        while (npq > 0) {
+            int32_t u = pq[0].id;
+            memmove(pq, pq + 1, (size_t)(npq - 1) * sizeof(cand_t));
+            npq--;
+            for (int k = 0; k < R; k++) {
+                int32_t v = adj[(int64_t)u * R + k];
+                if (v < 0 || stamp[v] == q) continue;
+                double dd = vjo_dist(X + (size_t)v * d, qv, d, metric);
+                steps[q]++;
+                stamp[v] = q;
+                dv[v] = dd;
+                if (dd >= eps && !hyb) continue;
+                if (npq + 1 > qcap) {
+                    qcap *= 2;
+                    pq = (cand_t *)realloc(pq, (size_t)qcap * sizeof(cand_t));
+                }
+                cand_t c = {dd, v};
+                sorted_insert(pq, &npq, c);
+                if (dd < eps) {
+                    if (nres + 1 > rcap) {
+                        rcap *= 2;
+                        res = (int32_t *)realloc(res, (size_t)rcap * sizeof(int32_t));
+                    }
+                    res[nres++] = v;
+                } else if (npq > beam) {
+                    npq--; /* the largest key is out of range */
+                }
+            }
+        }
+        qsort(res, (size_t)nres, sizeof(int32_t), cmp_i32);
+        for (int64_t j = 0; j < nres; j++) {
+            if (total + j < cap) {
+                ids[total + j] = res[j];
+                dists[total + j] = dv[res[j]];
+            }
+        }
+        total += nres;
+    }
+    offsets[nq] = total;
+    free(res);
+    free(pq);
+    free(dv);
+    free(stamp);
+    return total;
 }

@@ -1,13 +1,21 @@
 """Pins of the NN-Map oracle (the next design of the paper, Sec. NN-Map) against
 facts it must satisfy, each computed by independent code: the C oracle's
 nested-loop join, connected components of the in-range subgraph (scipy), and
-the complete graph."""
+the complete graph.  Both the plain Python oracle and its C twin (for larger
+inputs) are pinned, and they agree on every output."""
 import numpy as np
 import pytest
 
 from oracle import nnmap
 
 scipy_sparse = pytest.importorskip("scipy.sparse")
+
+
+@pytest.fixture(params=["py", "c"])
+def impl(request, oracle):
+    if request.param == "py":
+        return nnmap.nnmap_build, nnmap.nnmap_join
+    return oracle.nnmap_build_c, oracle.nnmap_join_c
 
 
 @pytest.fixture(scope="module")
@@ -39,23 +47,23 @@ def test_witness_property_for_every_threshold(case, oracle):
                 assert nm.witness[q] == min(int(row[j]) for j in range(len(row)) if rd[j] == rd[k])
 
 
-def test_certified_empty_queries_compute_nothing(case):
+def test_certified_empty_queries_compute_nothing(case, impl):
     X, Q, adj_x, nm = case
     eps = float(np.quantile(nm.wdist, 0.5))
-    r = nnmap.nnmap_join(X, Q, adj_x, nm, eps)
+    r = impl[1](X, Q, adj_x, nm, eps)
     empty = nm.wdist >= eps
     assert empty.any() and (~empty).any()
     assert np.all(r.steps[empty] == 0)
     assert all(len(r.row(q)) == 0 for q in np.nonzero(empty)[0])
 
 
-def test_bfs_join_is_the_in_range_component_of_the_witness(case):
+def test_bfs_join_is_the_in_range_component_of_the_witness(case, impl):
     """Non-hybrid: the result is the connected component of w[q] in the
     subgraph of G_X induced by the in-range data nodes (order-independent)."""
     from scipy.sparse.csgraph import connected_components
     X, Q, adj_x, nm = case
     eps = float(np.quantile(nm.wdist, 0.6)) * 1.6
-    r = nnmap.nnmap_join(X, Q, adj_x, nm, eps, hybrid="off")
+    r = impl[1](X, Q, adj_x, nm, eps, hybrid="off")
     nx, R = adj_x.shape
     src = np.repeat(np.arange(nx), R)
     dst = adj_x.ravel()
@@ -84,27 +92,27 @@ def test_bfs_join_is_the_in_range_component_of_the_witness(case):
         assert reach <= set(int(v) for v in comp)
 
 
-def test_complete_graph_join_equals_nested_loop_join(oracle):
+def test_complete_graph_join_equals_nested_loop_join(oracle, impl):
     rng = np.random.default_rng(22)
     X = rng.standard_normal((60, 6)).astype(np.float32)
     Q = rng.standard_normal((15, 6)).astype(np.float32)
     adj = np.array([[v for v in range(60) if v != u] for u in range(60)], np.int32)
-    nm = nnmap.nnmap_build(X, Q, adj)
+    nm = impl[0](X, Q, adj)
     eps = float(np.quantile(nm.wdist, 0.8)) * 1.3
-    r = nnmap.nnmap_join(X, Q, adj, nm, eps, hybrid="off")
+    r = impl[1](X, Q, adj, nm, eps, hybrid="off")
     off, ids, dd = oracle.nlj(X, Q, eps)
     for q in range(len(Q)):
         assert set(r.row(q).tolist()) == set(ids[off[q]:off[q + 1]].tolist())
     np.testing.assert_allclose(r.dists, dd, rtol=1e-12)
 
 
-def test_hybrid_contains_bfs_and_rows_grow_with_eps(case):
+def test_hybrid_contains_bfs_and_rows_grow_with_eps(case, impl):
     X, Q, adj_x, nm = case
     e1 = float(np.quantile(nm.wdist, 0.5))
     e2 = e1 * 1.3
-    b1 = nnmap.nnmap_join(X, Q, adj_x, nm, e1, hybrid="off")
-    b2 = nnmap.nnmap_join(X, Q, adj_x, nm, e2, hybrid="off")
-    h1 = nnmap.nnmap_join(X, Q, adj_x, nm, e1, hybrid="force", hybrid_beam_size=16)
+    b1 = impl[1](X, Q, adj_x, nm, e1, hybrid="off")
+    b2 = impl[1](X, Q, adj_x, nm, e2, hybrid="off")
+    h1 = impl[1](X, Q, adj_x, nm, e1, hybrid="force", hybrid_beam_size=16)
     for q in range(len(Q)):
         assert set(b1.row(q).tolist()) <= set(h1.row(q).tolist())
         assert set(b1.row(q).tolist()) <= set(b2.row(q).tolist())  # one build serves every threshold
@@ -122,3 +130,30 @@ def test_ood_bit_flags_far_queries(case):
     pairs = [np.sqrt(((X[v].astype(np.float64) - X[u].astype(np.float64)) ** 2).sum())
              for v in n1 for u in adj_x[v] if u >= 0 and u not in n1]
     assert nm.ood[q] == int(d1 / np.mean(pairs) > 1.5)
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_python_and_c_oracles_agree(oracle, metric):
+    rng = np.random.default_rng(23 + metric)
+    centres = rng.standard_normal((5, 10)) * 2.5
+    X = (centres[rng.integers(0, 5, 400)] + rng.standard_normal((400, 10))).astype(np.float32)
+    Q = np.concatenate([centres[rng.integers(0, 5, 40)] + rng.standard_normal((40, 10)),
+                        centres[rng.integers(0, 5, 8)] + 5.0 + rng.standard_normal((8, 10))]).astype(np.float32)
+    if metric == 1:
+        X /= np.linalg.norm(X, axis=1, keepdims=True)
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    adj_x, _, _ = oracle.build_graph(X, np.zeros((0, 10), np.float32), 8, 16, metric)
+    a = nnmap.nnmap_build(X, Q, adj_x, metric)
+    b = oracle.nnmap_build_c(X, Q, adj_x, metric)
+    np.testing.assert_array_equal(a.witness, b.witness)
+    np.testing.assert_allclose(a.wdist, b.wdist, rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(a.ood, b.ood)
+    eps = float(np.quantile(a.wdist, 0.7)) * 1.4
+    for hyb, beam in (("off", 256), ("adapt", 256), ("force", 8)):
+        ra = nnmap.nnmap_join(X, Q, adj_x, a, eps, metric=metric, hybrid=hyb, hybrid_beam_size=beam)
+        rb = oracle.nnmap_join_c(X, Q, adj_x, b, eps, metric=metric, hybrid=hyb, hybrid_beam_size=beam)
+        np.testing.assert_array_equal(ra.offsets, rb.offsets)
+        np.testing.assert_array_equal(ra.ids, rb.ids)
+        np.testing.assert_allclose(ra.dists, rb.dists, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(ra.steps, rb.steps)
+        np.testing.assert_array_equal(ra.hybrid, rb.hybrid)
