@@ -333,3 +333,26 @@ def nnmap_join_c(X, Q, adj_x, nm, eps: float, *, metric: int = L2, hybrid: str =
             break
         cap = int(total)
     return NNMapResult(offsets, ids[:total], dists[:total], steps, hyb)
+
+
+def transpose_csr(offsets, ids, dists, n_cols: int):
+    """Rows <-> columns of a CSR pair list (pairs ascending by column id per row)."""
+    offsets = np.asarray(offsets, np.int64)
+    rows = np.repeat(np.arange(len(offsets) - 1, dtype=np.int64), np.diff(offsets))
+    cols = np.asarray(ids, np.int64)
+    order = np.lexsort((rows, cols))  # by new row (old column), then new column (old row)
+    t_off = np.zeros(n_cols + 1, np.int64)
+    np.add.at(t_off, cols + 1, 1)
+    return np.cumsum(t_off), rows[order].astype(np.int32), np.asarray(dists, np.float64)[order]
+
+
+def join_switched(X, Q, eps: float, *, degree: int, knn_k: int, metric: int = L2, **kw):
+    """Query-data switching (the large-threshold discussion after Sec. 5): the
+    join X |><| Q equals Q |><| X, so the merged-index join runs with the roles
+    swapped (Q as data, X as queries, on the merged graph of both) and its
+    pair list is transposed back to one row per query of Q.  Returns
+    (offsets, ids, dists) over Q's queries.  kw: the options of `join`."""
+    X, Q = _f32(X), _f32(Q)
+    adj, entry, _ = build_graph(Q, X, degree, knn_k, metric)
+    r = join(Q, X, adj, entry, eps, metric=metric, **kw)
+    return transpose_csr(r.offsets, r.ids, r.dists, Q.shape[0])
