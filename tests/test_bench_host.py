@@ -89,3 +89,15 @@ def test_per_query_recall_mean_counts_empty_rows_as_one():
     # 2/4, empty exact row -> 1, 0/1
     assert abs(bench.per_query_recall_mean(got, ex, 10) - (0.5 + 1.0 + 0.0) / 3) < 1e-12
     assert abs(bench.recall_of(got, ex, 10) - 2 / 5) < 1e-12
+
+
+def test_profile_commands_run_committed_files_only():
+    """Every profile summary gives its command, and the command runs files of
+    this repository (bench.py), never a scratch script."""
+    pdir = os.path.join(ROOT, "profiles")
+    for f in sorted(os.listdir(pdir)):
+        text = open(os.path.join(pdir, f)).read()
+        assert "_work" not in text, f
+        for block in re.findall(r"```(.*?)```", text, re.S):
+            for script in re.findall(r"python\S*\s+(\S+\.py)", block):
+                assert os.path.exists(os.path.join(ROOT, script)), (f, script)
