@@ -88,3 +88,20 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "vj_oracle" not in txt and "vjo_" not in txt, f
+
+
+def test_sources_name_no_build_notes_or_machine_paths():
+    """Code and comments stand on their own: no references to the planning
+    notes, the benchmark's config file, or paths of a particular machine."""
+    banned = ["BASELINE.json", "north_star", "SURVEY", "VERDICT", "ADVICE", "DESIGN.md", "/root/", "gpurun"]
+    roots = [os.path.join(ROOT, d) for d in ("paper_2603_16360_b300", "oracle", "include", "tests")]
+    files = [os.path.join(ROOT, f) for f in ("bench.py", "__graft_entry__.py")]
+    for r in roots:
+        for dirpath, _, names in os.walk(r):
+            files += [os.path.join(dirpath, n) for n in names if n.endswith((".py", ".cu", ".cuh", ".h", ".c"))]
+    for f in files:
+        if os.path.basename(f) == "test_abi.py":
+            continue
+        txt = open(f, errors="replace").read()
+        for b in banned:
+            assert b not in txt, (f, b)
