@@ -251,11 +251,17 @@ vj_status vj_join_exact(vj_index *ix, float eps, vj_result **out);
  *   ascending data id per query; pairs beyond cap are not written.
  *   nnz (host): total number of pairs.  stream: a cudaStream_t or NULL.
  * Scratch is a fixed 4 MiB device array inside the library, which limits nq
- * to 1,048,576 (larger nq -> VJ_ERR_ARG) and is held by every GPU that loads
- * the library until exit.  All calls share that array: calls that overlap on
- * the GPU race and give wrong results.  The first call on a device looks up
- * the array's address (cudaGetSymbolAddress) and should come before any
- * stream capture on that device.  Returns VJ_ERR_STATE when nnz > cap.
+ * to 1,048,576 (larger nq -> VJ_ERR_ARG).  A GPU holds the array, until the
+ * process exits, from the moment the library's device code is loaded on it.
+ * Under CUDA's lazy module loading (the default) that is the first call into
+ * the library on that device, so a first call of this entry point can take
+ * those 4 MiB implicitly: make one warm-up call (or any other vj call) before
+ * entering a budgeted phase, or set CUDA_MODULE_LOADING=EAGER.  All calls
+ * share the array: calls that overlap on the GPU race and give wrong results.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture on that
+ * device.  Every call copies nnz to the host and waits for `stream` to finish
+ * before it returns.  Returns VJ_ERR_STATE when nnz > cap.
  * Decisions: FP32 keys, re-decided in FP64 within the FP32 rounding bound
  * of eps (same rule as vj_join_exact). */
 vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int64_t nq, int d,

@@ -5,7 +5,8 @@ Loss over n rows: mean_i [ (y_i0 - t_reg_i)^2 + softplus(y_i1) - t_cls_i y_i1 ]
 (squared error on the budget head, binary cross-entropy with logits on the
 route head).  Parameters are one flat vector W1[h1][din] b1 W2[h2][h1] b2
 W3[2][h2] b3, the layout of the library's predictor.  Plain numpy in float64;
-the backward pass is the chain rule written out layer by layer.
+the backward pass is the chain rule written out layer by layer.  Training is
+Adam on standardised inputs; `standardise` and `adam_step` state both steps.
 """
 from __future__ import annotations
 
@@ -69,3 +70,25 @@ def loss_grad(flat, x, t_reg, t_cls, din, h1, h2):
 
 def num_params(din, h1, h2):
     return h1 * din + h1 + h2 * h1 + h2 + 2 * h2 + 2
+
+
+def standardise(x):
+    """Per-feature mean and population standard deviation of the training rows
+    (floored at 1e-6), and the rows standardised with them, in float64."""
+    x = np.asarray(x, np.float64)
+    mu = x.mean(0)
+    sd = np.maximum(np.sqrt(np.maximum((x * x).mean(0) - mu * mu, 0.0)), 1e-6)
+    return mu, sd, (x - mu) / sd
+
+
+def adam_step(flat, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, "Adam: A Method for Stochastic
+    Optimization", Algorithm 1) at step t >= 1, float64: first and second
+    moment estimates, their bias corrections, then the parameter step.
+    Returns (new parameters, new m, new v)."""
+    flat, m, v, g = (np.asarray(a, np.float64) for a in (flat, m, v, g))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return flat - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

@@ -10,8 +10,11 @@
 //
 // Scratch: g_na_scratch, a static __device__ array of VJ_NOALLOC_SCRATCH_BYTES
 // (4 MiB + 256 B: one int32 match count per query, up to
-// VJ_NOALLOC_MAX_QUERIES queries).  Every GPU that loads the library holds it
-// until the process exits.  All calls share it and it keeps the last call's
+// VJ_NOALLOC_MAX_QUERIES queries).  A GPU holds it from the moment the
+// library's device code is loaded there until the process exits; with lazy
+// module loading (CUDA's default) that is the first call into the library on
+// that device, so callers with a fixed budget should make one call before the
+// budgeted phase (or set CUDA_MODULE_LOADING=EAGER).  All calls share it and it keeps the last call's
 // contents; every call overwrites each count it reads before reading it, so
 // nothing needs clearing, but two calls whose work overlaps on the GPU race on
 // it and produce wrong results.
@@ -19,7 +22,8 @@
 // Host code cannot use the array's name as a device address (it names a host
 // shadow), so the first call on each device, with that device current, looks
 // the address up with cudaGetSymbolAddress and caches it.  That first call on a
-// device should therefore come before any stream capture on it.
+// device should therefore come before any stream capture on it.  Every call
+// reads the pair count back to the host and waits for its stream.
 #include <float.h>
 #include <mutex>
 

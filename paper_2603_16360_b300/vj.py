@@ -441,8 +441,27 @@ def vj_join_exact_noalloc(X, Q, eps: float, offsets, ids, dists, metric: int = V
     caller owns; returns the pair count.  Raises VjError (VJ_ERR_STATE) when the
     pairs exceed len(ids); offsets are complete even then.
     """
+    import torch
+    ts = {"X": X, "Q": Q, "offsets": offsets, "ids": ids, "dists": dists}
+    for name, t in ts.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    devs = {t.device for t in ts.values()}
+    if len(devs) != 1 or next(iter(devs)).index != torch.cuda.current_device():
+        raise ValueError("every tensor must live on the current CUDA device")
+    want = {"X": torch.float32, "Q": torch.float32, "offsets": torch.int64, "ids": torch.int32,
+            "dists": torch.float32}
+    for name, dt in want.items():
+        if ts[name].dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {ts[name].dtype}")
+    if X.dim() != 2 or Q.dim() != 2 or X.shape[1] != Q.shape[1]:
+        raise ValueError("X and Q must be 2-D with the same number of columns")
     nx, d = X.shape
     nq = Q.shape[0]
+    if offsets.dim() != 1 or offsets.numel() < nq + 1:
+        raise ValueError(f"offsets needs at least nq + 1 = {nq + 1} entries")
     nnz = C.c_int64(0)
     cap = min(ids.numel(), dists.numel())
     _check(load().vj_join_exact_noalloc(X.data_ptr(), nx, Q.data_ptr(), nq, d, metric, float(eps),

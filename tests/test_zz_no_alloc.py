@@ -4,10 +4,11 @@ paths that cannot take cudaMalloc/cudaFree's locks and device syncs).
 
 The test calls it through the C ABI twice in a row on caller-owned device
 buffers and checks both outputs against vj_join_exact, the allocating entry
-point, with the tolerances of the other parity tests: pair ids equal outside
-the |dist - eps| <= 1e-4 eps band, distances within 1e-5 relative.  This file
-sorts last so that a run stopping at its first failure has already run every
-other test.
+point, and against the CPU oracle's nested-loop join (FP64), with the
+tolerances of the other parity tests: pair ids equal outside the
+|dist - eps| <= 1e-4 eps band, distances within 1e-5 relative on every pair
+the two results share.  This file sorts last so that a run stopping at its
+first failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -35,8 +36,20 @@ def _pairs(off, ids):
     return {(q, int(i)) for q in range(len(off) - 1) for i in ids[off[q]:off[q + 1]]}
 
 
+def _dist_map(off, ids, dists):
+    return {(q, int(ids[k])): float(dists[k]) for q in range(len(off) - 1) for k in range(off[q], off[q + 1])}
+
+
+def _check_shared_dists(got, want, what):
+    shared = got.keys() & want.keys()
+    assert shared, f"{what}: no shared pair to compare distances on"
+    a = np.array([got[k] for k in sorted(shared)])
+    b = np.array([want[k] for k in sorted(shared)])
+    np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6, err_msg=what)
+
+
 @pytest.mark.parametrize("metric", [vj.VJ_L2, vj.VJ_COSINE])
-def test_noalloc_matches_allocating_exact_join_twice(torch_cuda, metric):
+def test_noalloc_matches_allocating_exact_join_twice(torch_cuda, oracle, metric):
     torch = torch_cuda
     w = inputs.uniform_small(201 + metric, 2000, 300, 37, metric=metric)
     from scipy.spatial.distance import cdist
@@ -47,6 +60,7 @@ def test_noalloc_matches_allocating_exact_join_twice(torch_cuda, metric):
     ix = vj.vj_build(w.X, w.Q, metric=metric, params=vj.default_params(degree=12, knn_k=24))
     ref = vj.vj_join_exact(ix, eps)
     ix.free()
+    o_off, o_ids, o_d = oracle.nlj(w.X, w.Q, eps, metric)
 
     X = torch.from_numpy(w.X).cuda()
     Q = torch.from_numpy(w.Q).cuda()
@@ -62,12 +76,15 @@ def test_noalloc_matches_allocating_exact_join_twice(torch_cuda, metric):
         dv = dd.cpu().numpy()[:nnz]
         assert o[-1] == nnz
         diff = (_pairs(o, i) ^ _pairs(ref.offsets, ref.ids)) - band
-        assert not diff, f"call {call}: {len(diff)} pairs differ"
+        assert not diff, f"call {call}: {len(diff)} pairs differ from vj_join_exact"
+        diff = (_pairs(o, i) ^ _pairs(o_off, o_ids)) - band
+        assert not diff, f"call {call}: {len(diff)} pairs differ from the oracle"
         for q in range(w.nq):
             r = i[o[q]:o[q + 1]]
             assert np.all(np.diff(r) > 0)
-        if np.array_equal(o, ref.offsets) and np.array_equal(i, ref.ids):
-            np.testing.assert_allclose(dv, ref.dists, rtol=1e-5, atol=1e-6)
+        got = _dist_map(o, i, dv)
+        _check_shared_dists(got, _dist_map(ref.offsets, ref.ids, ref.dists), f"call {call} vs vj_join_exact")
+        _check_shared_dists(got, _dist_map(o_off, o_ids, o_d), f"call {call} vs the oracle")
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(torch_cuda):
