@@ -202,6 +202,173 @@ __global__ void k_fill_in(const int32_t* __restrict__ pid, const float* __restri
     inlk[inoff[v] + pos] = pkey[e];
 }
 
+// ---------------------------------------------------------------- tiled RNG prune (wide rows)
+// Block per node: the RNG prune of a sorted candidate list, in rounds of up to
+// 32 candidates.  A round stages the vectors of the nodes kept so far (<= 32)
+// and of its candidates (<= 32) in shared memory, 64 dimensions at a time and
+// dimension-major (a thread reads 4 consecutive rows per load), and every
+// thread accumulates a 4 x 4 block of the 64 x 64 pair keys with FP32 direct
+// differences (cosine: dot products, then 1 - dot/(|a||b|)).  Warp 0 then
+// takes the round's decisions in list order with the rule and the FP64
+// near-tie re-decision of rng_prune_warp.  Rows of d floats are read once per
+// round instead of once per (candidate, kept node) pair.
+constexpr int TP_THREADS = 256;
+constexpr int TP_ROWS = 64;
+constexpr int TP_CH = 64;  // dimensions per staged chunk
+
+struct TpSmem {
+    __align__(16) float T[TP_CH][TP_ROWS];
+    float M[TP_ROWS][TP_ROWS + 1];
+    int rid[TP_ROWS];  // node id of each tile row: kept nodes, then the round's candidates
+    int kid[32];
+    float kkey[32];
+    int krow[32];
+    int cid[32];
+    float ckey[32];
+    int nk;
+};
+
+// lists: row u's candidates are lid/lkey[base .. base + cnt), base = loff[u]
+// (u * K when loff is null), cnt = lcnt[u] (when null: the entries of the K
+// before the first -1).  rows: the nodes to prune (null: all nrows).
+__global__ void __launch_bounds__(TP_THREADS) k_rng_tile(
+    const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d, int metric, float tol, int R,
+    const int32_t* __restrict__ lid, const float* __restrict__ lkey, const int64_t* __restrict__ loff,
+    const int32_t* __restrict__ lcnt, int K, const int32_t* __restrict__ rows, int64_t nrows,
+    int32_t* __restrict__ out_id, float* __restrict__ out_key, int32_t* __restrict__ out_cnt,
+    unsigned long long* __restrict__ nrechk) {
+    __shared__ TpSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t ri = blockIdx.x; ri < nrows; ri += gridDim.x) {
+        const int64_t u = rows ? (int64_t)rows[ri] : ri;
+        const int64_t base = loff ? loff[u] : u * K;
+        int cnt;
+        if (lcnt) {
+            cnt = lcnt[u];
+        } else {
+            // the K-list is sorted with -1 only at the tail
+            int c = 0;
+            for (int e0 = 0; e0 < K; e0 += 32)
+                c += __popc(__ballot_sync(VJ_FULL, e0 + lane < K && lid[base + e0 + lane] >= 0));
+            cnt = c;
+        }
+        int nk = 0;
+        for (int r0 = 0; r0 < cnt && nk < R; r0 += 32) {
+            const int m = min(32, cnt - r0);
+            const int nk0 = nk;
+            if (tid < m) {
+                const int v = lid[base + r0 + tid];
+                S.cid[tid] = v;
+                S.ckey[tid] = lkey[base + r0 + tid];
+                S.rid[nk0 + tid] = v;
+            }
+            if (tid < nk0) {
+                S.rid[tid] = S.kid[tid];
+                S.krow[tid] = tid;
+            }
+            const int nt = nk0 + m;
+            const int bi = tid >> 4, bj = tid & 15;  // this thread's rows bi*4.., columns bj*4..
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+            for (int k0 = 0; k0 < dp; k0 += TP_CH) {
+                __syncthreads();  // tile rows known; the previous chunk consumed
+                {
+                    const int r = tid & (TP_ROWS - 1);
+                    for (int f = tid / TP_ROWS; f < TP_CH / 4; f += TP_THREADS / TP_ROWS) {
+                        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < nt && k0 + f * 4 < dp)
+                            x = __ldg(reinterpret_cast<const float4*>(vec + (int64_t)S.rid[r] * dp + k0 + f * 4));
+                        S.T[f * 4 + 0][r] = x.x;
+                        S.T[f * 4 + 1][r] = x.y;
+                        S.T[f * 4 + 2][r] = x.z;
+                        S.T[f * 4 + 3][r] = x.w;
+                    }
+                }
+                __syncthreads();
+                if (bi * 4 < nt && bj * 4 < nt) {
+#pragma unroll 8
+                    for (int k = 0; k < TP_CH; k++) {
+                        const float4 a = *reinterpret_cast<const float4*>(&S.T[k][bi * 4]);
+                        const float4 b = *reinterpret_cast<const float4*>(&S.T[k][bj * 4]);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                if (metric == 0) {
+                                    const float t = av[i] - bv[j];
+                                    acc[i][j] = fmaf(t, t, acc[i][j]);
+                                } else {
+                                    acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                                }
+                            }
+                    }
+                }
+            }
+            if (bi * 4 < nt && bj * 4 < nt) {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int ti = bi * 4 + i, tj = bj * 4 + j;
+                        if (ti < nt && tj < nt)
+                            S.M[ti][tj] = metric == 0 ? acc[i][j]
+                                                      : 1.f - acc[i][j] * __ldg(invn + S.rid[ti]) *
+                                                                  __ldg(invn + S.rid[tj]);
+                    }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                for (int i = 0; i < m && nk < R; i++) {
+                    const int v = S.cid[i];
+                    const float kuv = S.ckey[i];
+                    const int trow = nk0 + i;
+                    bool keep = true;
+                    if (nk > 0) {
+                        const float kw = lane < nk ? S.M[trow][S.krow[lane]] : FLT_MAX;
+                        bool rej = lane < nk && kw < kuv;
+                        const bool nr = lane < nk && near_equal(kw, kuv, tol, metric);
+                        unsigned nm = __ballot_sync(VJ_FULL, nr);
+                        if (nm) {
+                            const double duv = warp_dist64(vec, dp, d, metric, u, v, lane);
+                            while (nm) {
+                                const int src = __ffs(nm) - 1;
+                                nm &= nm - 1;
+                                const int w = S.kid[src];
+                                const double dwv = warp_dist64(vec, dp, d, metric, w, v, lane);
+                                if (lane == src) rej = dwv < duv;
+                                if (lane == 0) atomicAdd(nrechk, 1ull);
+                            }
+                        }
+                        keep = !__any_sync(VJ_FULL, rej);
+                    }
+                    if (keep) {
+                        if (lane == 0) {
+                            S.kid[nk] = v;
+                            S.kkey[nk] = kuv;
+                            S.krow[nk] = trow;
+                        }
+                        nk++;
+                        __syncwarp();
+                    }
+                }
+                if (lane == 0) S.nk = nk;
+            }
+            __syncthreads();
+            nk = S.nk;
+        }
+        if (tid < R) {
+            out_id[u * R + tid] = tid < nk ? S.kid[tid] : -1;
+            out_key[u * R + tid] = tid < nk ? S.kkey[tid] : FLT_MAX;
+        }
+        if (tid == 0 && out_cnt) out_cnt[u] = nk;
+        __syncthreads();  // the next row overwrites the shared lists
+    }
+}
+
 struct MergeSmem {
     int uid[UCAP];
     float uk[UCAP];
@@ -219,7 +386,10 @@ __global__ void __launch_bounds__(4 * 32) k_merge(const float* __restrict__ vec,
                                                    const int64_t* __restrict__ inoff, const int32_t* __restrict__ inl,
                                                    const float* __restrict__ inlk, int32_t* __restrict__ adj,
                                                    float* __restrict__ adjk, int32_t* __restrict__ big_rows,
-                                                   int* __restrict__ nbig, unsigned long long* __restrict__ nrechk) {
+                                                   int* __restrict__ nbig, unsigned long long* __restrict__ nrechk,
+                                                   int32_t* __restrict__ stage_rows, int* __restrict__ nstage,
+                                                   int32_t* __restrict__ uid_out, float* __restrict__ uk_out,
+                                                   int32_t* __restrict__ ucnt) {
     extern __shared__ __align__(16) unsigned char mraw[];
     MergeSmem* sms = reinterpret_cast<MergeSmem*>(mraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -280,6 +450,20 @@ __global__ void __launch_bounds__(4 * 32) k_merge(const float* __restrict__ vec,
         __syncwarp();
     } else {
         fix_tie_runs(vec, dp, d, metric, tol, v, S.uk, S.uid, nu, S.s64, lane, nrechk);
+        if (stage_rows) {
+            // wide rows: the sorted union goes to the tiled prune (its slot:
+            // v * R + inoff[v] holds the R own entries plus the offers)
+            const int64_t ub = v * R + i0;
+            for (int e = lane; e < nu; e += 32) {
+                uid_out[ub + e] = S.uid[e];
+                uk_out[ub + e] = S.uk[e];
+            }
+            if (lane == 0) {
+                ucnt[v] = nu;
+                stage_rows[atomicAdd(nstage, 1)] = (int32_t)v;
+            }
+            return;
+        }
         nk = rng_prune_warp<G, NPL>(vec, invn, dp, d, metric, tol, v, S.uid, S.uk, nu, R, S.kid, S.kkey, S.tmpk,
                                     lane, nrechk);
     }
@@ -559,6 +743,11 @@ __global__ void k_tree_level(const int32_t* __restrict__ front, int nf, const in
     }
 }
 
+__global__ void k_union_off(const int64_t* __restrict__ inoff, int64_t n, int R, int64_t* __restrict__ uoff) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) uoff[v] = v * R + inoff[v];
+}
+
 }  // namespace
 
 
@@ -578,9 +767,19 @@ void vj_build_graph(vj_index* ix) {
     pid.alloc((size_t)n * R, s);
     pkey.alloc((size_t)n * R, s);
     pcount.alloc(n, s);
-    VJ_DISPATCH_GN(dp4, (k_prune<G, NPL><<<vj_div_up(n, PWPB), PWPB * 32, 0, s>>>(
-                            ix->vec.p, ix->invn.p, dp, d, n, metric, tol, K, R, ix->knn.p, ix->knnd.p, pid.p, pkey.p,
-                            pcount.p, nr.p)));
+    // rows wider than 256 floats: the tiled prune (a warp per node would
+    // gather every kept vector once per candidate)
+    const bool tiled = dp4 > 64;
+    const int tp_grid = (int)std::min<int64_t>(n, (int64_t)ix->num_sms * 32);
+    if (tiled) {
+        k_rng_tile<<<tp_grid, TP_THREADS, 0, s>>>(ix->vec.p, ix->invn.p, dp, d, metric, tol, R, ix->knn.p,
+                                                  ix->knnd.p, nullptr, nullptr, K, nullptr, n, pid.p, pkey.p,
+                                                  pcount.p, nr.p);
+    } else {
+        VJ_DISPATCH_GN(dp4, (k_prune<G, NPL><<<vj_div_up(n, PWPB), PWPB * 32, 0, s>>>(
+                                ix->vec.p, ix->invn.p, dp, d, n, metric, tol, K, R, ix->knn.p, ix->knnd.p, pid.p,
+                                pkey.p, pcount.p, nr.p)));
+    }
     VJ_LAUNCH_CHECK();
 
     // ---- 2. reverse edges
@@ -605,26 +804,49 @@ void vj_build_graph(vj_index* ix) {
     ix->adj.ensure((size_t)n * R, s);
     DBuf<float> adjk;
     adjk.alloc((size_t)n * R, s);
-    DBuf<int32_t> big;
+    DBuf<int32_t> big, stage, uid, ucnt;
+    DBuf<float> uk;
     DBuf<int> nbig;
     big.alloc(n, s);
-    nbig.alloc(1, s);
-    VJ_CUDA(cudaMemsetAsync(nbig.p, 0, sizeof(int), s));
+    nbig.alloc(2, s);
+    VJ_CUDA(cudaMemsetAsync(nbig.p, 0, 2 * sizeof(int), s));
+    if (tiled) {
+        stage.alloc(n, s);
+        ucnt.alloc(n, s);
+        uid.alloc((size_t)n * R + std::max<int64_t>(nin, 1), s);
+        uk.alloc((size_t)n * R + std::max<int64_t>(nin, 1), s);
+    }
     {
         size_t smem = sizeof(MergeSmem) * 4;
         VJ_DISPATCH_GN(dp4, {
             VJ_CUDA(cudaFuncSetAttribute(k_merge<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_merge<G, NPL><<<vj_div_up(n, 4), 4 * 32, smem, s>>>(ix->vec.p, ix->invn.p, dp, d, n, metric, tol, R,
-                                                                  pid.p, pkey.p, inoff.p, inl.p, inlk.p, ix->adj.p,
-                                                                  adjk.p, big.p, nbig.p, nr.p);
+            k_merge<G, NPL><<<vj_div_up(n, 4), 4 * 32, smem, s>>>(
+                ix->vec.p, ix->invn.p, dp, d, n, metric, tol, R, pid.p, pkey.p, inoff.p, inl.p, inlk.p, ix->adj.p,
+                adjk.p, big.p, nbig.p, nr.p, tiled ? stage.p : nullptr, nbig.p + 1, uid.p, uk.p, ucnt.p);
         });
         VJ_LAUNCH_CHECK();
     }
-    int hbig = 0;
-    VJ_CUDA(cudaMemcpyAsync(&hbig, nbig.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hbig[2] = {0, 0};
+    VJ_CUDA(cudaMemcpyAsync(hbig, nbig.p, sizeof(hbig), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaStreamSynchronize(s));
-    VJ_REQUIRE(hbig == 0, VJ_ERR_STATE, "graph build: %d nodes have more than %d reverse-edge offers", hbig,
+    VJ_REQUIRE(hbig[0] == 0, VJ_ERR_STATE, "graph build: %d nodes have more than %d reverse-edge offers", hbig[0],
                UCAP - R);
+    if (tiled && hbig[1] > 0) {
+        // over-full unions of wide rows: their RNG prune, into adj / adjk
+        DBuf<int64_t> uoff;
+        uoff.alloc(n, s);
+        k_union_off<<<vj_div_up(n, 256), 256, 0, s>>>(inoff.p, n, R, uoff.p);
+        VJ_LAUNCH_CHECK();
+        k_rng_tile<<<(int)std::min<int64_t>(hbig[1], (int64_t)ix->num_sms * 32), TP_THREADS, 0, s>>>(
+            ix->vec.p, ix->invn.p, dp, d, metric, tol, R, uid.p, uk.p, uoff.p, ucnt.p, 0, stage.p, hbig[1],
+            ix->adj.p, adjk.p, nullptr, nr.p);
+        VJ_LAUNCH_CHECK();
+        uoff.free_(s);
+    }
+    stage.free_(s);
+    ucnt.free_(s);
+    uid.free_(s);
+    uk.free_(s);
 
     // ---- 3. entry point
     {

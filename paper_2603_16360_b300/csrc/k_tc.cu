@@ -36,73 +36,96 @@ namespace {
 
 using namespace vjtc;
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
-constexpr int TC_EPI_WARPS = 16;
-constexpr int TC_CG = TC_EPI_WARPS / 4;    // column groups: warps sharing a TMEM lane quarter
-constexpr int TC_CW = TC_BN / TC_CG;       // columns per epilogue warp
-constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;
-constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
-constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
-constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr int TC_BK = 64;                 // K columns per TMA box (128 bytes of BF16: one swizzle row)
+constexpr uint32_t TC_TMEM_COLS = 512;    // two 256-column FP32 accumulators
 
-struct __align__(1024) TcSmem {
-    uint8_t A[TC_STAGES][TC_A_BYTES];
-    uint8_t B[TC_STAGES][TC_B_BYTES];
-    uint64_t full[TC_STAGES];
-    uint64_t empty[TC_STAGES];
+// ---------------------------------------------------------------- streamed tiles (kp > 128)
+// For rows wider than the resident kernel holds, both operands stream through
+// a ring of K blocks: a 128-row A box and a 256-row B box of 64 BF16 columns
+// per stage, tcgen05.mma M=128 N=256 into one of two TMEM accumulators while
+// the epilogue drains the other.  A work unit is one 128-row tile of A against
+// a run of B tiles (every tstride-th tile), so a CTA keeps its A rows hot in L2
+// and the units running at the same time walk the same B tiles.
+//
+// The epilogue works on v = acc * cs[c] + cb[c] with per-B-row scale and bias
+// (L2: cs = 2 and cb = the scan bias -(1 - c3)|b|^2 + cbmax |b|, so v is the
+// value the resident kernel accumulates; cosine: cs = 1/|b| for raw rows or 1
+// for unit rows, cb = 0):
+//   EPI_SCAN    a pair is a candidate when v > thr[row]; candidates are
+//               appended through per-warp chunks as (row id, column, acc * cs);
+//   EPI_SAMPLE  each row keeps the 16 largest v over the unit's tiles (its own
+//               column excluded) and writes the 16th to top16[row].
+// Warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..9 are the
+// epilogue (two per TMEM lane quarter, 128 columns each).  Every wait is
+// bounded; an epilogue warp that gives up keeps walking its tiles (without
+// touching TMEM) so that the epilogue's named barriers always fill.
+enum { EPI_SCAN = 0, EPI_SAMPLE = 1 };
+
+constexpr int WD_BM = 128, WD_BN = 256, WD_STAGES = 4;
+constexpr int WD_EPI = 8;
+constexpr int WD_THREADS = (2 + WD_EPI) * 32;
+constexpr uint32_t WD_A_BYTES = WD_BM * TC_BK * 2;  // 16 KB
+constexpr uint32_t WD_B_BYTES = WD_BN * TC_BK * 2;  // 32 KB
+constexpr int WD_CHUNK = 128;                       // candidate slots reserved per warp at a time
+
+struct __align__(1024) WdSmem {
+    uint8_t A[WD_STAGES][WD_A_BYTES];
+    uint8_t B[WD_STAGES][WD_B_BYTES];
+    uint64_t full[WD_STAGES];
+    uint64_t empty[WD_STAGES];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
-    float cn[2][TC_BN];   // column squared norms (L2) / inverse norms (cosine)
-    float cnr[2][TC_BN];  // column norms
-    __align__(16) float g[2][TC_BN];  // per-column filter thresholds
-    uint8_t cvalid[2][TC_BN];
+    __align__(16) float cs[2][WD_BN];
+    __align__(16) float cb[2][WD_BN];
+    float part[WD_BM][17];  // sample: the second column half's top 16 per row
 };
 
 // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
 // K-major, M = 128, N = 256
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                              ((uint32_t)(TC_BM >> 4) << 24);
+constexpr uint32_t WD_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WD_BN >> 3) << 17) |
+                              ((uint32_t)(WD_BM >> 4) << 24);
 
-struct TcScanParams {
-    int64_t nrows, ncols;  // A rows (queries), B rows (data)
-    int nkb;               // K blocks of 64
-    int nrt, nct;          // row / column tiles
-    int metric;
-    const float* a_n;      // per A row: squared norm (L2) or inverse norm (cosine)
-    const float* b_n;      // per B row: same
-    const int32_t* a_ids;  // query index of each A row
-    float eps_key;
-    float cb, c3;          // candidate bound: key - cb*|a||b| - c3*(|a|^2+|b|^2) < eps_key
-    float cbmax;           // cb * (largest row norm): row-independent form of the bound
+struct WdParams {
+    int64_t nrows, ncols;  // A rows, B rows
+    int nkb;               // K blocks of 64 columns
+    int nrt;               // A row tiles
+    int nct;               // B tiles a sweep visits (tile k of the sweep is B tile k * tstride)
+    int tstride;
+    int tpu;               // B tiles per work unit (EPI_SAMPLE: all of them)
+    int nunits;            // nrt * ceil(nct / tpu), row tile fastest
+    const float* cs;       // [ncols] per B row: scale of the accumulator
+    const float* cb;       // [ncols] per B row: bias added before the row test
+    const float* thr;      // [nrows] EPI_SCAN: candidate iff acc * cs + cb > thr
+    const int32_t* a_ids;  // [nrows] id written for the row's candidates (nullptr: the row index)
     int32_t* cq;
     int32_t* cx;
+    float* cw;             // acc * cs of each candidate (nullptr: not written)
     unsigned long long* ncand;
     int64_t cap;
+    float* top16;          // [nrows] EPI_SAMPLE output (rows are node ids: the row's own column is skipped)
     int* err;
     long long spin_limit;
 };
 
-// MODE 0: exact L2 keys, 1: L2 keys with the BF16 rounding bound, 2: cosine
-template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_scan(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, TcScanParams P) {
-    extern __shared__ uint8_t tc_raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+template <int EPI>
+__global__ void __launch_bounds__(WD_THREADS, 1)
+    k_tc_wide(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, WdParams P) {
+    extern __shared__ uint8_t wd_raw[];
+    WdSmem& S = *reinterpret_cast<WdSmem*>((reinterpret_cast<uintptr_t>(wd_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* abort = &S.abort;
-    const int ntiles = P.nrt * P.nct;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; s++) {
+        for (int s = 0; s < WD_STAGES; s++) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&S.tfull[b], 1);
-            mbar_init(&S.tempty[b], TC_EPI_WARPS);
+            mbar_init(&S.tempty[b], WD_EPI);
         }
         mbar_init(&S.drain, 1);
         S.abort = 0;
@@ -126,21 +149,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0;
             uint32_t issued = 0, last_ph = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int rt = t % P.nrt, ct = t / P.nrt;
-                for (int kb = 0; kb < P.nkb; kb++) {
-                    if (!mbar_wait(&S.empty[s], ph ^ 1u, abort, P.spin_limit)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_tx(&S.full[s], TC_A_BYTES + TC_B_BYTES);
-                    tma_load_2d(S.A[s], &tA, &S.full[s], kb * TC_BK, rt * TC_BM);
-                    tma_load_2d(S.B[s], &tB, &S.full[s], kb * TC_BK, ct * TC_BN);
-                    issued |= 1u << s;
-                    last_ph = (last_ph & ~(1u << s)) | (ph << s);
-                    if (++s == TC_STAGES) {
-                        s = 0;
-                        ph ^= 1u;
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+                const int rt = u % P.nrt, cc = u / P.nrt;
+                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                for (int ct = t0; ct < t1 && ok; ct++) {
+                    for (int kb = 0; kb < P.nkb; kb++) {
+                        if (!mbar_wait(&S.empty[s], ph ^ 1u, abort, P.spin_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_tx(&S.full[s], WD_A_BYTES + WD_B_BYTES);
+                        tma_load_2d(S.A[s], &tA, &S.full[s], kb * TC_BK, rt * WD_BM);
+                        tma_load_2d(S.B[s], &tB, &S.full[s], kb * TC_BK, ct * P.tstride * WD_BN);
+                        issued |= 1u << s;
+                        last_ph = (last_ph & ~(1u << s)) | (ph << s);
+                        if (++s == WD_STAGES) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                 }
             }
@@ -148,12 +174,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 *abort = 1;
                 atomicExch(P.err, 1);
                 // let this CTA's copies land before shared memory goes away
-                for (int st = 0; st < TC_STAGES; st++)
-                    if ((issued >> st) & 1u) {
+                for (int st = 0; st < WD_STAGES; st++)
+                    if ((issued >> st) & 1u)
                         for (long long i = 0; i < P.spin_limit && !mbar_test(&S.full[st], (last_ph >> st) & 1u);
                              i++) {
                         }
-                    }
             }
         }
     } else if (warp == 1) {
@@ -163,35 +188,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0;
             int i = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, i++) {
-                const int acc = i & 1;
-                if (!mbar_wait(&S.tempty[acc], ((i >> 1) & 1) ^ 1u, abort, P.spin_limit)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * TC_BN);
-                for (int kb = 0; kb < P.nkb; kb++) {
-                    if (!mbar_wait(&S.full[s], ph, abort, P.spin_limit)) {
+            for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+                const int cc = u / P.nrt;
+                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                for (int ct = t0; ct < t1 && ok; ct++, i++) {
+                    const int acc = i & 1;
+                    if (!mbar_wait(&S.tempty[acc], (uint32_t)(((i >> 1) & 1) ^ 1), abort, P.spin_limit)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ad = sdesc_sw128(su32(S.A[s]));
-                    const uint64_t bd = sdesc_sw128(su32(S.B[s]));
+                    const uint32_t d = tmem + (uint32_t)(acc * WD_BN);
+                    for (int kb = 0; kb < P.nkb; kb++) {
+                        if (!mbar_wait(&S.full[s], ph, abort, P.spin_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(su32(S.A[s]));
+                        const uint64_t bd = sdesc_sw128(su32(S.B[s]));
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; kk++) {
-                        // advance 16 BF16 (32 bytes) along K inside the swizzled rows
-                        tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), TC_IDESC, (kb | kk) != 0);
+                        for (int kk = 0; kk < TC_BK / 16; kk++) {
+                            // advance 16 BF16 (32 bytes) along K inside the swizzled rows
+                            tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC, (kb | kk) != 0);
+                        }
+                        tc_commit(&S.empty[s]);
+                        if (++s == WD_STAGES) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
-                    tc_commit(&S.empty[s]);
-                    if (++s == TC_STAGES) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
+                    if (!ok) break;
+                    tc_commit(&S.tfull[acc]);
                 }
-                if (!ok) break;
-                tc_commit(&S.tfull[acc]);
             }
             if (!ok) {
                 *abort = 1;
@@ -203,152 +232,183 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue
-        const int e = warp - 2;              // 0..TC_EPI_WARPS-1
-        const int quarter = warp & 3;        // TMEM lane quarter this warp may access
-        const int cg = e >> 2;               // column group
-        const int etid = e * 32 + lane;      // threads < TC_BN stage one column each
-        // the next tile's column norm and row info are loaded one tile ahead,
-        // so their latency overlaps the current tile
-        // (cosine rows are unit-normalised: their norms are 1)
-        auto col_norm = [&](int tt) -> float {
-            const int64_t c = (int64_t)(tt / P.nrt) * TC_BN + etid;
-            return (etid < TC_BN && tt < ntiles && c < P.ncols) ? (MODE == 2 ? 1.f : P.b_n[c]) : -1.f;
-        };
-        auto row_norm = [&](int tt) -> float {
-            const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
-            return (tt < ntiles && r < P.nrows) ? (MODE == 2 ? 1.f : P.a_n[r]) : -1.f;
-        };
-        auto row_id = [&](int tt) -> int {
-            const int64_t r = (int64_t)(tt % P.nrt) * TC_BM + quarter * 32 + lane;
-            return (tt < ntiles && r < P.nrows) ? P.a_ids[r] : -1;
-        };
-        float nc_next = col_norm(blockIdx.x), rn_next = row_norm(blockIdx.x);
-        int qid_next = row_id(blockIdx.x);
+        // ---------------- epilogue: warp e reads TMEM lane quarter (warp & 3),
+        // columns cg * 128 .. cg * 128 + 127 of each accumulator
+        const int e = warp - 2;
+        const int quarter = warp & 3;
+        const int cg = e >> 2;
+        const int etid = e * 32 + lane;  // one B column of each tile to stage
+        bool dead = false;
         int i = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
-            const int acc = i & 1;
-            const int ct = t / P.nrt;
-            // ---- per-tile staging (overlaps the MMA of this tile)
-            // filter: a pair can only be a candidate when v - g[c] > h[r]
-            //   L2:     v > ((1-c3)(|r|^2 + |c|^2) - eps^2 - cbmax |c|)/2, with
-            //           cbmax >= cb |r| for every row (a conservative bound)
-            //   cosine: v * cinv > (1 - cb - eps) |r|
-            if (etid < TC_BN) {
-                const float n = nc_next;
-                const bool cvld = n >= 0.f;
-                float g;
-                if (MODE == 2) g = cvld ? n : 0.f;
-                else g = cvld ? 0.5f * ((1.f - P.c3) * n - P.eps_key - P.cbmax * sqrtf(n)) : INFINITY;
-                S.g[acc][etid] = g;
-                S.cn[acc][etid] = cvld ? n : FLT_MAX;
-                S.cnr[acc][etid] = cvld ? (MODE == 2 ? 1.f : sqrtf(n)) : 0.f;
-                S.cvalid[acc][etid] = cvld;
-            }
-            const bool rv = rn_next >= 0.f;
-            const float rn = rv ? rn_next : 0.f;
-            const int qid = qid_next;
-            if (t + (int)gridDim.x < ntiles) {
-                nc_next = col_norm(t + gridDim.x);
-                rn_next = row_norm(t + gridDim.x);
-                qid_next = row_id(t + gridDim.x);
-            }
-            asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
-            const float cbr = MODE == 1 ? P.cb * sqrtf(rn) : 0.f;
-            float hr, marg;
-            if (MODE == 2) {
-                hr = (1.f - P.cb - P.eps_key) * (rn > 0.f ? 1.f / rn : 0.f);
-                marg = 1e-5f * (fabsf(hr) + 1.f);
-            } else {
-                hr = 0.5f * (1.f - P.c3) * rn;
-                marg = 1e-5f * (rn + P.eps_key) + 1e-30f;
-            }
-            const float thr = hr - marg;
-            bool ok = mbar_wait(&S.tfull[acc], (i >> 1) & 1, abort, P.spin_limit);
-            if (!__all_sync(VJ_FULL, ok)) {
-                if (lane == 0) {
-                    *abort = 1;
-                    atomicExch(P.err, 1);
+        unsigned long long cbase = 0;  // EPI_SCAN: this warp's output chunk (next slot, slots left)
+        int cleft = 0;
+        for (int u = blockIdx.x; u < P.nunits; u += gridDim.x) {
+            const int rt = u % P.nrt, cc = u / P.nrt;
+            const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+            const int64_t r = (int64_t)rt * WD_BM + quarter * 32 + lane;
+            const bool rv = r < P.nrows;
+            const float thr = (EPI == EPI_SCAN && rv) ? P.thr[r] : INFINITY;
+            const int qid = rv ? (P.a_ids ? P.a_ids[r] : (int)r) : -1;
+            float t[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) t[k] = -INFINITY;
+            for (int ct = t0; ct < t1; ct++, i++) {
+                const int acc = i & 1;
+                const int64_t cbase_col = (int64_t)ct * P.tstride * WD_BN;
+                // stage this tile's column scale and bias (a column past the last
+                // B row gets bias -inf: it never passes a test)
+                {
+                    const int64_t c = cbase_col + etid;
+                    const bool cv = c < P.ncols;
+                    S.cs[acc][etid] = cv ? P.cs[c] : 0.f;
+                    S.cb[acc][etid] = cv ? P.cb[c] : -INFINITY;
                 }
-                break;
-            }
-            tc_fence_after();
-            const float eps_k = P.eps_key;
-            const uint32_t tbase = tmem + (uint32_t)(acc * TC_BN + cg * TC_CW) + ((uint32_t)(quarter * 32) << 16);
+                asm volatile("bar.sync 1, %0;" ::"r"(WD_EPI * 32) : "memory");
+                if (!dead) {
+                    const bool got = mbar_wait(&S.tfull[acc], (uint32_t)((i >> 1) & 1), abort, P.spin_limit);
+                    if (!__all_sync(VJ_FULL, got)) {
+                        if (lane == 0) {
+                            *abort = 1;
+                            atomicExch(P.err, 1);
+                        }
+                        dead = true;
+                    }
+                }
+                if (!dead) {
+                    tc_fence_after();
 #pragma unroll 1
-            for (int ch = 0; ch < TC_CW / 32; ch++) {
-                const int col0 = cg * TC_CW + ch * 32;
-                uint32_t va[32];
-                tmem_ld32_issue(tbase + (uint32_t)(ch * 32), va);
-                tmem_wait_ld(va);
-                // fast filter: two instructions per pair, four independent chains
-                float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
-                const float4* g4 = reinterpret_cast<const float4*>(&S.g[acc][col0]);
+                    for (int h = 0; h < 2; h++) {
+                        const int col0 = cg * 128 + h * 64;  // column within the tile
+                        uint32_t va[64];
+                        __syncwarp();  // lanes that skipped the last half's work rejoin before the aligned load
+                        tmem_ld64_issue(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * WD_BN + col0), va);
+                        tmem_wait_ld64(va);
+                        if (h == 1) {
+                            // both halves have been read: hand the TMEM buffer back
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&S.tempty[acc]);
+                        }
+                        const float4* cs4 = reinterpret_cast<const float4*>(&S.cs[acc][col0]);
+                        const float4* cb4 = reinterpret_cast<const float4*>(&S.cb[acc][col0]);
+                        float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
 #pragma unroll
-                for (int j4 = 0; j4 < 8; j4++) {
-                    const float4 g = g4[j4];
-                    if (MODE == 2) {
-                        m0 = fmaxf(m0, __uint_as_float(va[4 * j4 + 0]) * g.x);
-                        m1 = fmaxf(m1, __uint_as_float(va[4 * j4 + 1]) * g.y);
-                        m2 = fmaxf(m2, __uint_as_float(va[4 * j4 + 2]) * g.z);
-                        m3 = fmaxf(m3, __uint_as_float(va[4 * j4 + 3]) * g.w);
-                    } else {
-                        m0 = fmaxf(m0, __uint_as_float(va[4 * j4 + 0]) - g.x);
-                        m1 = fmaxf(m1, __uint_as_float(va[4 * j4 + 1]) - g.y);
-                        m2 = fmaxf(m2, __uint_as_float(va[4 * j4 + 2]) - g.z);
-                        m3 = fmaxf(m3, __uint_as_float(va[4 * j4 + 3]) - g.w);
-                    }
-                }
-                const bool maybe = rv && fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) > thr;
-                if (!__any_sync(VJ_FULL, maybe)) continue;
-                uint32_t hit = 0;
-                if (maybe) {
-                    // exact candidate test for this row's 32 columns (unrolled:
-                    // the TMEM registers must stay registers)
+                        for (int j4 = 0; j4 < 16; j4++) {
+                            const float4 a = cs4[j4], b = cb4[j4];
+                            m0 = fmaxf(m0, fmaf(__uint_as_float(va[4 * j4 + 0]), a.x, b.x));
+                            m1 = fmaxf(m1, fmaf(__uint_as_float(va[4 * j4 + 1]), a.y, b.y));
+                            m2 = fmaxf(m2, fmaf(__uint_as_float(va[4 * j4 + 2]), a.z, b.z));
+                            m3 = fmaxf(m3, fmaf(__uint_as_float(va[4 * j4 + 3]), a.w, b.w));
+                        }
+                        const float mx = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+                        if constexpr (EPI == EPI_SAMPLE) {
+                            if (!rv || !(mx > t[15])) continue;
+                            const int64_t c0 = cbase_col + col0;
+                            const bool self_here = r >= c0 && r < c0 + 64;
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const float v = __uint_as_float(va[j]);
-                        const float cn = S.cn[acc][col0 + j];
-                        bool h;
-                        if (MODE == 0) {
-                            h = fmaf(-2.f, v, rn + cn) < eps_k;
-                        } else if (MODE == 1) {
-                            const float t = rn + cn;
-                            h = fmaf(-2.f, v, t) - fmaf(cbr, S.cnr[acc][col0 + j], P.c3 * t) < eps_k;
+                            for (int j = 0; j < 64; j++) {
+                                float x = fmaf(__uint_as_float(va[j]), S.cs[acc][col0 + j], S.cb[acc][col0 + j]);
+                                if (!(x > t[15])) continue;
+                                if (self_here && c0 + j == r) continue;
+                                // insert: x sinks to its place, the 16th value drops out
+#pragma unroll
+                                for (int k = 0; k < 16; k++) {
+                                    const float hi = fmaxf(t[k], x);
+                                    x = fminf(t[k], x);
+                                    t[k] = hi;
+                                }
+                            }
                         } else {
-                            h = 1.f - v * rn * cn - P.cb < eps_k;
-                        }
-                        if (h && S.cvalid[acc][col0 + j]) hit |= 1u << j;
-                    }
-                }
-                // warp-aggregated append: one atomic per warp and chunk
-                const int mine = __popc(hit);
-                int incl = mine;
+                            const bool maybe = rv && mx > thr;
+                            if (!__any_sync(VJ_FULL, maybe)) continue;
+                            uint32_t hit0 = 0, hit1 = 0;
+                            if (maybe) {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int t2 = __shfl_up_sync(VJ_FULL, incl, o);
-                    if (lane >= o) incl += t2;
-                }
-                const int total = __shfl_sync(VJ_FULL, incl, 31);
-                if (total > 0) {
-                    unsigned long long base = 0;
-                    if (lane == 31) base = atomicAdd(P.ncand, (unsigned long long)total);
-                    base = __shfl_sync(VJ_FULL, base, 31);
-                    unsigned long long gq = base + (unsigned long long)(incl - mine);
-                    while (hit) {
-                        const int j = __ffs(hit) - 1;
-                        hit &= hit - 1;
-                        if ((int64_t)gq < P.cap) {
-                            P.cq[gq] = qid;
-                            P.cx[gq] = (int)((int64_t)ct * TC_BN + col0 + j);
+                                for (int j = 0; j < 32; j++) {
+                                    hit0 |= (uint32_t)(fmaf(__uint_as_float(va[j]), S.cs[acc][col0 + j],
+                                                            S.cb[acc][col0 + j]) > thr) << j;
+                                    hit1 |= (uint32_t)(fmaf(__uint_as_float(va[32 + j]), S.cs[acc][col0 + 32 + j],
+                                                            S.cb[acc][col0 + 32 + j]) > thr) << j;
+                                }
+                            }
+                            // warp-aggregated append of both halves
+                            const int mine = __popc(hit0) + __popc(hit1);
+                            int incl = mine;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
+                                if (lane >= o) incl += t2;
+                            }
+                            const int total = __shfl_sync(VJ_FULL, incl, 31);
+                            if (total == 0) continue;
+                            if (total > cleft) {
+                                // close the chunk (its unused slots become holes) and reserve the next
+                                for (int k = lane; k < cleft; k += 32)
+                                    if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
+                                const int want = max(total, WD_CHUNK);
+                                unsigned long long gb = 0;
+                                if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
+                                cbase = __shfl_sync(VJ_FULL, gb, 31);
+                                cleft = want;
+                            }
+                            unsigned long long gq = cbase + (unsigned long long)(incl - mine);
+                            cbase += (unsigned long long)total;
+                            cleft -= total;
+                            const int64_t c0 = cbase_col + col0;
+#pragma unroll
+                            for (int hh = 0; hh < 2; hh++) {
+                                uint32_t hit = hh ? hit1 : hit0;
+                                while (hit) {
+                                    const int j = __ffs(hit) - 1;
+                                    hit &= hit - 1;
+                                    if ((int64_t)gq < P.cap) {
+                                        P.cq[gq] = qid;
+                                        P.cx[gq] = (int)(c0 + hh * 32 + j);
+                                        if (P.cw) {
+                                            // select by unrolled compares: a runtime index into va
+                                            // would move the whole array to local memory
+                                            float o = 0.f;
+#pragma unroll
+                                            for (int jj = 0; jj < 32; jj++)
+                                                if (jj == j) o = __uint_as_float(va[hh * 32 + jj]);
+                                            P.cw[gq] = o * S.cs[acc][col0 + hh * 32 + j];
+                                        }
+                                    }
+                                    gq++;
+                                }
+                            }
                         }
-                        gq++;
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.tempty[acc]);
+            if constexpr (EPI == EPI_SAMPLE) {
+                // merge the two column halves' lists of each row
+                const int rl = quarter * 32 + lane;
+                if (cg == 1) {
+#pragma unroll
+                    for (int k = 0; k < 16; k++) S.part[rl][k] = t[k];
+                }
+                asm volatile("bar.sync 2, %0;" ::"r"(WD_EPI * 32) : "memory");
+                if (cg == 0 && rv && !dead) {
+#pragma unroll 1
+                    for (int k2 = 0; k2 < 16; k2++) {
+                        float x = S.part[rl][k2];
+                        if (!(x > t[15])) break;  // the partner's list is descending
+#pragma unroll
+                        for (int k = 0; k < 16; k++) {
+                            const float hi = fmaxf(t[k], x);
+                            x = fminf(t[k], x);
+                            t[k] = hi;
+                        }
+                    }
+                    P.top16[r] = t[15];
+                }
+                asm volatile("bar.sync 2, %0;" ::"r"(WD_EPI * 32) : "memory");
+            }
+        }
+        if constexpr (EPI == EPI_SCAN) {
+            for (int k = lane; k < cleft; k += 32)
+                if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
         }
     }
     tc_fence_before();
@@ -359,7 +419,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      : "memory");
     }
 }
-
 // ---------------------------------------------------------------- resident-A scan
 // For kp <= 128 a CTA keeps 256 query rows (two 128-row MMA operands, every
 // k-block) in shared memory for a run of 128-row data tiles, so only the data
@@ -437,7 +496,6 @@ constexpr int KN_EPI = 8;  // sample epilogue warps: one per (query block, lane 
 //   EPI_SAMPLE   8 warps; each thread owns one row and keeps, in registers, the
 //               16 largest accumulators over a sample of the data tiles (the
 //               kNN build's per-row threshold).
-enum { EPI_SCAN = 0, EPI_SAMPLE = 1 };
 
 template <int EPI>
 __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 32, 1)
@@ -641,6 +699,7 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
 #pragma unroll 1
                 for (int h = 0; h < 2; h++) {
                     uint32_t va[64];
+                    __syncwarp();  // lanes that skipped the last half's work rejoin before the aligned load
                     tmem_ld64_issue(tmem + lanes + (uint32_t)(acc * 256 + blk * 128 + h * 64), va);
                     tmem_wait_ld64(va);
                     if (h == 1) {
@@ -869,15 +928,25 @@ __global__ void k_gather_f(const float* __restrict__ src, const int32_t* __restr
     if (i < n) dst[i] = src[rows[i]];
 }
 
-// flag[0] |= any non-integer coordinate; flag[1] = max |coordinate| (integer part)
+// flag[0] |= any non-integer coordinate; flag[1] = max |coordinate| (integer
+// part); flag[2] |= any coordinate that is not exactly a BF16 value.  Grid
+// stride with one atomic per warp and flag (the vectors can be GBs).
 __global__ void k_int_check(const float* __restrict__ v, int64_t n, unsigned int* __restrict__ flag) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float x = v[i];
-    const bool nonint = !(x == rintf(x)) || fabsf(x) > 1e9f;
-    if (__any_sync(__activemask(), nonint) && nonint) atomicOr(flag, 1u);
-    const unsigned int m = (unsigned int)fminf(fabsf(x), 4e9f);
-    atomicMax(flag + 1, m);
+    unsigned int nonint = 0u, nonbf = 0u, mx = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = v[i];
+        nonint |= (unsigned int)(!(x == rintf(x)) || fabsf(x) > 1e9f);
+        nonbf |= (unsigned int)((__float_as_uint(x) & 0xFFFFu) != 0u);
+        mx = max(mx, (unsigned int)fminf(fabsf(x), 4e9f));
+    }
+    nonint = __reduce_or_sync(VJ_FULL, nonint);
+    nonbf = __reduce_or_sync(VJ_FULL, nonbf);
+    mx = __reduce_max_sync(VJ_FULL, mx);
+    if ((threadIdx.x & 31) == 0) {
+        if (nonint) atomicOr(flag, 1u);
+        if (nonbf) atomicOr(flag + 2, 1u);
+        atomicMax(flag + 1, mx);
+    }
 }
 
 // query index and merged node id of each scanned row
@@ -890,43 +959,94 @@ __global__ void k_query_rows(const int32_t* __restrict__ qrows, int64_t n, int32
     node[i] = nx + q;
 }
 
+// per node, the streamed kernel's column scale and bias (v = acc * cs + cb)
+//   mode 0, L2:          cs = 2, cb = -(1 - c3)|b|^2 + cbmax |b|, so v is the
+//                        resident kernel's accumulator 2<a,b> + bias_b
+//   mode 1, cosine raw:  cs = 1/|b| (0 for a zero row), cb = 0
+//   mode 2, cosine unit: cs = 1, cb = 0
+__global__ void k_wide_cols(const float* __restrict__ sqn, const float* __restrict__ invn, int64_t n, int mode,
+                            double c3, double cbmax, float* __restrict__ cs, float* __restrict__ cb) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (mode == 0) {
+        const double nn = (double)sqn[c];
+        cs[c] = 2.f;
+        cb[c] = (float)(-(1.0 - c3) * nn + cbmax * sqrt(nn));
+    } else {
+        cs[c] = mode == 1 ? invn[c] : 1.f;
+        cb[c] = 0.f;
+    }
+}
+
+// cosine on raw rows: a pair is a candidate iff acc / |b| > (1 - eps - cb - margin) |a|
+// (margin as in k_row_thr); a zero query row has cosine distance 1 to everything
+__global__ void k_row_thr_raw(const float* __restrict__ invn, const int32_t* __restrict__ node, int64_t n, int kp,
+                              float eps_key, float cb, float* __restrict__ thr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double g = (double)(kp + 16) * 1.1920928955078125e-7;
+    const double t = 1.0 - (double)eps_key - (double)cb - 3.0 * g;
+    const double iv = (double)invn[node ? node[i] : i];
+    thr[i] = iv > 0.0 ? (float)(t / iv) : (t < 0.0 ? -INFINITY : INFINITY);
+}
+
+// exact keys of the streamed scan's candidates (integer inputs): |a|^2 + |b|^2 - 2<a,b>
+__global__ void k_key_from_w(const float* __restrict__ sqn, const int32_t* __restrict__ cq,
+                             const int32_t* __restrict__ cx, const float* __restrict__ cw, int64_t nc, int64_t nx,
+                             float* __restrict__ ck) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nc || cq[e] < 0) return;
+    ck[e] = sqn[nx + cq[e]] + sqn[cx[e]] - cw[e];
+}
+
 }  // namespace
 
-// BF16 copy of the data rows and the scan's bound constants (built once per
-// index, kept for later scans).  Cosine rows are stored unit-normalised.
+// BF16 copy of every node and the bound constants of the tensor-core tiles
+// (built once per index, kept for later scans).
+//   kp <= 128 (resident kernel): cosine rows are stored unit-normalised.
+//   kp >  128 (streamed kernel): also the per-node column scale and bias; when
+//   every coordinate is exactly a BF16 value, cosine rows are stored raw (the
+//   epilogue divides by |b|), so the tiles' only error is the accumulation.
 static void ensure_data_bf16(vj_index* ix) {
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     if (ix->xbf.n >= (size_t)ix->n * kp) return;
     cudaStream_t s = ix->stream;
-    // every node (data rows first): scans read the data rows, the kNN build all
-    ix->xbf.ensure((size_t)ix->n * kp, s);
     const bool cosine = ix->metric != VJ_L2;
-    k_to_bf16<<<vj_div_up(ix->n * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->n, kp, 1.f,
-                                                          cosine ? ix->invn.p : nullptr, ix->xbf.p);
-    VJ_LAUNCH_CHECK();
+    const bool wide = kp > RS_MAX_KB * TC_BK;
     // Exact-key test: when every coordinate is an integer of magnitude <= 256
     // it is exact in BF16, every product is an integer below 2^16 and, with
     // d * max^2 <= 2^23, every partial sum, both norms, their sum (<= 2^24)
     // and the norm expansion stay integers exactly representable in FP32, so
     // the FP32-accumulated key is exact and needs no bound.
     DBuf<unsigned int> flag;
-    flag.alloc(2, s);
-    VJ_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(unsigned int), s));
-    k_int_check<<<vj_div_up(ix->n * ix->dp, 256), 256, 0, s>>>(ix->vec.p, ix->n * ix->dp, flag.p);
+    flag.alloc(3, s);
+    VJ_CUDA(cudaMemsetAsync(flag.p, 0, 3 * sizeof(unsigned int), s));
+    k_int_check<<<std::max(1, std::min(vj_div_up(ix->n * ix->dp, 256), 16 * ix->num_sms)), 256, 0, s>>>(
+        ix->vec.p, ix->n * ix->dp, flag.p);
     VJ_LAUNCH_CHECK();
-    unsigned int h[2] = {0, 0};
+    unsigned int h[3] = {0, 0, 0};
     VJ_CUDA(cudaMemcpyAsync(h, flag.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaStreamSynchronize(s));
     flag.free_(s);
     const double mx = (double)h[1];
     ix->bf16_exact = !cosine && h[0] == 0 && mx <= 256.0 && (double)ix->d * mx * mx <= 8388608.0;
+    ix->bf16_lossless = h[2] == 0;
+    ix->cos_raw = cosine && wide && ix->bf16_lossless;
+    // every node (data rows first): scans read the data rows, the kNN build all
+    ix->xbf.ensure((size_t)ix->n * kp, s);
+    k_to_bf16<<<vj_div_up(ix->n * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, ix->n, kp, 1.f,
+                                                          (cosine && !ix->cos_raw) ? ix->invn.p : nullptr, ix->xbf.p);
+    VJ_LAUNCH_CHECK();
     // |key_bf16 - key| <= cb |a||b| + c3 (|a|^2 + |b|^2) with
     //   L2:     cb = 4ub + 2ub^2 + 2 kp 2^-23 + 4u, c3 = 3u
     //   cosine: cb = 2ub + ub^2 + 2 kp 2^-23 + 8u (unit rows), c3 = 0
-    // (ub = 2^-8 BF16, u = 2^-24 FP32), each with a 1.25 margin
+    // (ub = 2^-8 BF16, u = 2^-24 FP32), each with a 1.25 margin.  Inputs that
+    // are exactly BF16 drop the ub terms (L2 rows, and cosine raw rows whose
+    // norms are applied in FP32 after the accumulation).
     const double ub = 1.0 / 256.0, u = VJ_F32_U;
     if (!cosine) {
-        ix->tc_cb = (float)(1.25 * (4 * ub + 2 * ub * ub + 2.0 * kp * 2 * u + 4 * u));
+        const double in_round = ix->bf16_lossless ? 0.0 : 4 * ub + 2 * ub * ub;
+        ix->tc_cb = (float)(1.25 * (in_round + 2.0 * kp * 2 * u + 4 * u));
         ix->tc_c3 = (float)(1.25 * 3 * u);
         if (ix->bf16_exact) {
             ix->tc_cb = 0.f;  // exact integer keys (see above)
@@ -934,19 +1054,51 @@ static void ensure_data_bf16(vj_index* ix) {
         }
         // row-independent form: cbmax >= cb |a| for every row
         ix->tc_cbmax = (float)(ix->tc_cb * ix->maxnorm * 1.0001);
-        ix->xbias.ensure((size_t)ix->n * 16, s);
-        k_bias_split<<<vj_div_up(ix->n, 256), 256, 0, s>>>(ix->sqn.p, ix->n, (double)ix->tc_c3,
-                                                             (double)ix->tc_cbmax, ix->xbias.p);
-        VJ_LAUNCH_CHECK();
-        ix->abias.ensure(128 * 16, s);
-        k_fill_abias<<<vj_div_up(128 * 16, 256), 256, 0, s>>>(ix->abias.p);
-        VJ_LAUNCH_CHECK();
+        if (!wide) {
+            ix->xbias.ensure((size_t)ix->n * 16, s);
+            k_bias_split<<<vj_div_up(ix->n, 256), 256, 0, s>>>(ix->sqn.p, ix->n, (double)ix->tc_c3,
+                                                                 (double)ix->tc_cbmax, ix->xbias.p);
+            VJ_LAUNCH_CHECK();
+            ix->abias.ensure(128 * 16, s);
+            k_fill_abias<<<vj_div_up(128 * 16, 256), 256, 0, s>>>(ix->abias.p);
+            VJ_LAUNCH_CHECK();
+        }
     } else {
-        ix->tc_cb = (float)(1.25 * (2 * ub + ub * ub + 2.0 * kp * 2 * u + 8 * u));
+        const double in_round = ix->cos_raw ? 0.0 : 2 * ub + ub * ub;
+        ix->tc_cb = (float)(1.25 * (in_round + 2.0 * kp * 2 * u + 8 * u));
         ix->tc_c3 = 0.f;
         ix->tc_cbmax = 0.f;
     }
+    if (wide) {
+        ix->wcs.ensure(ix->n, s);
+        ix->wcb.ensure(ix->n, s);
+        k_wide_cols<<<vj_div_up(ix->n, 256), 256, 0, s>>>(ix->sqn.p, ix->invn.p, ix->n,
+                                                            !cosine ? 0 : (ix->cos_raw ? 1 : 2), (double)ix->tc_c3,
+                                                            (double)ix->tc_cbmax, ix->wcs.p, ix->wcb.p);
+        VJ_LAUNCH_CHECK();
+    }
 }
+
+// Work split of a sweep of nrt row tiles over nct tiles: the tiles per unit
+// that minimise the busiest SM's load (its units' tiles plus `refill` tiles of
+// pipeline restart per unit)
+static int best_tiles_per_unit(int64_t nrt, int64_t nct, int num_sms, int64_t refill) {
+    const int64_t g = std::max(1, num_sms);
+    int64_t best = INT64_MAX;
+    int best_tpu = (int)nct;
+    for (int64_t ncc = 1; ncc <= nct; ncc++) {
+        const int64_t tpu = (nct + ncc - 1) / ncc;
+        if (ncc > 1 && (nct + tpu - 1) / tpu != ncc) continue;  // same split as a smaller ncc
+        const int64_t load = ((nrt * ncc + g - 1) / g) * (tpu + refill);
+        if (load < best) {
+            best = load;
+            best_tpu = (int)tpu;
+        }
+    }
+    return best_tpu;
+}
+
+static size_t wide_smem() { return sizeof(WdSmem) + 1024; }
 
 // Candidate pairs (query index, data id) of the BF16 tensor-core scan of the
 // queries `qrows` (query indices; nullptr = all) against every data row.
@@ -971,30 +1123,34 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     k_query_rows<<<vj_div_up(nr, 256), 256, 0, s>>>(qrows, nr, (int32_t)ix->nx, aid.p, anode.p);
     VJ_LAUNCH_CHECK();
     const int32_t* arow = anode.p;
-    // query rows: L2 scaled by 2 for the resident form (2<a,b> + bias), cosine unit rows
+    // query rows: L2 scaled by 2 for the resident form (2<a,b> + bias), cosine
+    // unit rows (raw rows for the streamed kernel on BF16-exact inputs)
     const float ascale = (!cosine && resident) ? 2.f : 1.f;
     k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, ascale,
-                                                      cosine ? ix->invn.p : nullptr, abf.p);
+                                                      (cosine && !ix->cos_raw) ? ix->invn.p : nullptr, abf.p);
     VJ_LAUNCH_CHECK();
     const float eps_key = cosine ? eps : eps * eps;
-    if (resident) {
+    if (ix->cos_raw) {
+        k_row_thr_raw<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->invn.p, arow, nr, kp, eps_key, ix->tc_cb, an.p);
+    } else {
         k_row_thr<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, ix->metric, kp, eps_key, ix->tc_cb,
                                                       ix->tc_c3, ix->tc_cbmax, ix->maxnorm, an.p);
-    } else {
-        k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, an.p);
     }
     VJ_LAUNCH_CHECK();
 
     DBuf<unsigned long long> ctr;
     DBuf<int> err;
-    DBuf<float> rn_rows;
+    DBuf<float> rn_rows, cw;
     ctr.alloc(1, s);
     err.alloc(1, s);
     const long long spin_limit = 1ll << 22;  // try_wait polls; seconds at most, then an error
     std::function<void()> launch;
     CUtensorMap ta, tb, tab, tbb;
     RsParams R{};
-    TcScanParams P{};
+    WdParams W{};
+    // integer inputs (exact BF16 products and FP32 sums): the scan hands out
+    // each candidate's exact key, and no re-check from the vectors is needed
+    const bool want_keys = ck && !cosine && ix->bf16_exact;
     if (resident) {
         ta = make_map(abf.p, nr, kp, 128);
         tb = make_map(ix->xbf.p, ix->nx, kp, RS_BN);
@@ -1015,22 +1171,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         // query block fastest so concurrent units share data tiles in L2.
         // The run length minimises the busiest SM's load: its units' tiles
         // plus about 3 tiles of pipeline refill per unit (query rows reload)
-        {
-            const int64_t g = std::max(1, ix->num_sms);
-            int64_t best = INT64_MAX;
-            int best_tpu = R.nct;
-            for (int64_t ncc = 1; ncc <= R.nct; ncc++) {
-                const int64_t tpu = (R.nct + ncc - 1) / ncc;
-                if (ncc > 1 && (R.nct + tpu - 1) / tpu != ncc) continue;  // same split as a smaller ncc
-                const int64_t per = ((int64_t)R.nrp * ncc + g - 1) / g;
-                const int64_t load = per * (tpu + 3);
-                if (load < best) {
-                    best = load;
-                    best_tpu = (int)tpu;
-                }
-            }
-            R.tpu = best_tpu;
-        }
+        R.tpu = best_tiles_per_unit(R.nrp, R.nct, ix->num_sms, 3);
         R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
         // ring stages of one data tile each, within 227 KB of shared memory
         const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
@@ -1039,9 +1180,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         R.a_thr = an.p;
         R.a_ids = aid.p;
         R.tstride = 1;
-        // integer inputs (exact BF16 products and FP32 sums): the scan hands out
-        // each candidate's exact key, and no re-check from the vectors is needed
-        if (ck && !cosine && ix->bf16_exact) {
+        if (want_keys) {
             rn_rows.alloc(nr, s);
             k_gather_f<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, rn_rows.p);
             VJ_LAUNCH_CHECK();
@@ -1055,31 +1194,27 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         const int grid = std::min(R.nunits, ix->num_sms);
         launch = [&, grid, smem]() { k_tc_res<EPI_SCAN><<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };
     } else {
-        ta = make_map(abf.p, nr, kp, TC_BM);
-        tb = make_map(ix->xbf.p, ix->nx, kp, TC_BN);
-        P.nrows = nr;
-        P.ncols = ix->nx;
-        P.nkb = kp / TC_BK;
-        P.nrt = (int)vj_div_up(nr, TC_BM);
-        P.nct = (int)vj_div_up(ix->nx, TC_BN);
-        P.metric = ix->metric;
-        P.a_n = an.p;
-        P.b_n = ix->sqn.p;  // data rows are the first nx nodes
-        P.a_ids = aid.p;
-        P.eps_key = eps_key;
-        P.cb = ix->tc_cb;
-        P.c3 = ix->tc_c3;
-        P.cbmax = ix->tc_cbmax;
-        P.ncand = ctr.p;
-        P.err = err.p;
-        P.spin_limit = spin_limit;
-        const int ntiles = P.nrt * P.nct;
-        const int grid = std::min(ntiles, ix->num_sms);
-        const size_t smem = sizeof(TcSmem) + 1024;
-        const int mode = cosine ? 2 : (ix->bf16_exact ? 0 : 1);
-        auto kern = mode == 0 ? k_tc_scan<0> : (mode == 1 ? k_tc_scan<1> : k_tc_scan<2>);
-        VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        launch = [&, grid, smem, kern]() { kern<<<grid, TC_THREADS, smem, s>>>(ta, tb, P); };
+        ta = make_map(abf.p, nr, kp, WD_BM);
+        tb = make_map(ix->xbf.p, ix->nx, kp, WD_BN);
+        W.nrows = nr;
+        W.ncols = ix->nx;
+        W.nkb = kp / TC_BK;
+        W.nrt = (int)vj_div_up(nr, WD_BM);
+        W.nct = (int)vj_div_up(ix->nx, WD_BN);
+        W.tstride = 1;
+        W.tpu = best_tiles_per_unit(W.nrt, W.nct, ix->num_sms, 1);
+        W.nunits = W.nrt * (int)vj_div_up(W.nct, W.tpu);
+        W.cs = ix->wcs.p;  // data rows are the first nx nodes
+        W.cb = ix->wcb.p;
+        W.thr = an.p;
+        W.a_ids = aid.p;
+        W.ncand = ctr.p;
+        W.err = err.p;
+        W.spin_limit = spin_limit;
+        const size_t smem = wide_smem();
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = std::min(W.nunits, ix->num_sms);
+        launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
     }
     int64_t cap = std::max<int64_t>(cq.n, std::max<int64_t>(nr * 64, 1 << 20));
     unsigned long long hn = 0;
@@ -1091,13 +1226,17 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     for (int attempt = 0; attempt < 3; attempt++) {
         cq.ensure(cap, s);
         cx.ensure(cap, s);
-        P.cq = R.cq = cq.p;
-        P.cx = R.cx = cx.p;
-        if (R.a_rn) {
+        W.cq = R.cq = cq.p;
+        W.cx = R.cx = cx.p;
+        if (want_keys) {
             ck->ensure(cap, s);
-            R.ck = ck->p;
+            if (resident) R.ck = ck->p;
+            else {
+                cw.ensure(cap, s);
+                W.cw = cw.p;
+            }
         }
-        P.cap = R.cap = (int64_t)cq.n;
+        W.cap = R.cap = (int64_t)cq.n;
         VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
         VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
         VJ_CUDA(cudaEventRecord(e0, s));
@@ -1113,20 +1252,25 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         cap = (int64_t)hn + (int64_t)hn / 4 + RS_HOLE_SLACK;  // the next launch may leave other holes
     }
     VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core scan: candidate list still too small");
+    if (want_keys && !resident && hn > 0) {
+        k_key_from_w<<<vj_div_up((int64_t)hn, 256), 256, 0, s>>>(ix->sqn.p, cq.p, cx.p, cw.p, (int64_t)hn, ix->nx,
+                                                                ck->p);
+        VJ_LAUNCH_CHECK();
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ms_out) *ms_out = ms;
-    ix->last_scan_exact_keys = R.a_rn != nullptr;
+    ix->last_scan_exact_keys = want_keys;
     abf.free_(s);
     aid.free_(s);
     an.free_(s);
     anode.free_(s);
     rn_rows.free_(s);
+    cw.free_(s);
     ctr.free_(s);
     err.free_(s);
     return (int64_t)hn;
 }
-
 // ---------------------------------------------------------------- exact kNN build
 // Candidates of the exact kNN over all n nodes, on the tensor cores, in two
 // sweeps of the resident kernel:
@@ -1157,19 +1301,23 @@ __global__ void k_pair_count(const int32_t* __restrict__ cq, int64_t nc, int32_t
     if (e < nc && cq[e] >= 0) atomicAdd(counts + cq[e], 1);  // -1: a hole
 }
 
-__global__ void k_pair_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx, int64_t nc,
-                               const int64_t* __restrict__ off, int32_t* __restrict__ cursor,
-                               int32_t* __restrict__ ids) {
+__global__ void k_pair_scatter(const int32_t* __restrict__ cq, const int32_t* __restrict__ cx,
+                               const float* __restrict__ cw, int64_t nc, const int64_t* __restrict__ off,
+                               int32_t* __restrict__ cursor, int32_t* __restrict__ ids, float* __restrict__ wv) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nc) return;
     const int q = cq[e];
     if (q < 0) return;  // a hole
-    ids[off[q] + atomicAdd(cursor + q, 1)] = cx[e];
+    const int64_t pos = off[q] + atomicAdd(cursor + q, 1);
+    ids[pos] = cx[e];
+    if (wv) wv[pos] = cw[e];
 }
 
-// true-key lower bound of every node a row did not list (accumulator <= thr)
-__global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restrict__ thr_acc, int64_t n, int metric,
-                            int kp, float cb, float c3, float cbmax, double maxnorm, float* __restrict__ thr) {
+// true-key lower bound of every node a row did not list (accumulator <= thr;
+// for cosine raw rows the tile value is acc / |b|)
+__global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restrict__ invn,
+                            const float* __restrict__ thr_acc, int64_t n, int metric, int raw, int kp, float cb,
+                            float c3, float cbmax, double maxnorm, float* __restrict__ thr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float ta = thr_acc[i];
@@ -1182,109 +1330,152 @@ __global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restri
         const double rn = (double)sqn[i];
         const double mag = 2.1 * sqrt(rn) * maxnorm + 1.1 * maxnorm * maxnorm + (double)cbmax * maxnorm;
         thr[i] = (float)((1.0 - (double)c3) * rn - (double)ta - g * mag);
+    } else if (raw) {
+        thr[i] = (float)(1.0 - (double)ta * (double)invn[i] - (double)cb - 3.0 * g);
     } else {
         thr[i] = (float)(1.0 - (double)ta - (double)cb - 3.0 * g);
     }
 }
 
-bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr) {
+bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr,
+                          DBuf<float>* cw_out) {
     const int kpad = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
-    if (kpad > RS_MAX_KB * TC_BK || ix->n < 4096) return false;
+    if (ix->n < 4096) return false;
+    const bool wide = kpad > RS_MAX_KB * TC_BK;
     cudaStream_t s = ix->stream;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
     const int64_t n = ix->n;
     DBuf<__nv_bfloat16> abf;
-    DBuf<float> top, thr;
+    DBuf<float> top, thr, cw;
     DBuf<int32_t> iota;
     DBuf<int> err;
     DBuf<unsigned long long> ctr;
-    abf.alloc((size_t)n * kpad, s);
     top.alloc(n, s);
     thr.alloc(n, s);
-    iota.alloc(n, s);
     err.alloc(1, s);
     ctr.alloc(1, s);
-    k_to_bf16<<<vj_div_up(n * kpad, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, n, kpad,
-                                                      cosine ? 1.f : 2.f, cosine ? ix->invn.p : nullptr, abf.p);
-    k_iota<<<vj_div_up(n, 256), 256, 0, s>>>(iota.p, n);
-    VJ_LAUNCH_CHECK();
-    CUtensorMap ta = make_map(abf.p, n, kpad, 128);
-    CUtensorMap tb = make_map(ix->xbf.p, n, kpad, RS_BN);
-    CUtensorMap tab = cosine ? ta : make_map16(ix->abias.p, 128, 128);
-    CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, n, RS_BN);
-    RsParams R{};
-    R.nrows = n;
-    R.ncols = n;
-    R.nkb = kpad / TC_BK;
-    R.bias = cosine ? 0 : 1;
-    R.nrp = (int)vj_div_up(n, 256);
-    const int nct_all = (int)vj_div_up(n, RS_BN);
-    const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
-    const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
-    R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
-    R.err = err.p;
-    R.spin_limit = 1ll << 22;
-    const size_t smem = fixed + per * (size_t)R.stages;
     VJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-
-    // 1. sample sweep: one unit per 256-row block over every KNN_SAMPLE-th tile
-    R.tstride = KNN_SAMPLE;
-    R.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
-    R.tpu = R.nct;
-    R.nunits = R.nrp;
-    R.top16 = top.p;
-    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tc_res<EPI_SAMPLE><<<std::min(R.nunits, ix->num_sms), (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
-    VJ_LAUNCH_CHECK();
-    k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
-    VJ_LAUNCH_CHECK();
-
-    // 2. candidate sweep over every tile, rows are node ids
-    R.tstride = 1;
-    R.nct = nct_all;
-    {
-        const int64_t g = std::max(1, ix->num_sms);
-        int64_t best = INT64_MAX;
-        int best_tpu = R.nct;
-        for (int64_t ncc = 1; ncc <= R.nct; ncc++) {
-            const int64_t tpu = (R.nct + ncc - 1) / ncc;
-            if (ncc > 1 && (R.nct + tpu - 1) / tpu != ncc) continue;
-            const int64_t load = (((int64_t)R.nrp * ncc + g - 1) / g) * (tpu + 3);
-            if (load < best) {
-                best = load;
-                best_tpu = (int)tpu;
-            }
-        }
-        R.tpu = best_tpu;
-    }
-    R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
-    R.a_thr = thr.p;
-    R.a_ids = iota.p;
-    R.ncand = ctr.p;
-    VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long spin_limit = 1ll << 22;
     DBuf<int32_t>& cq = ix->scan_cq;
     DBuf<int32_t>& cx = ix->scan_cx;
     int64_t cap = std::max<int64_t>(cq.n, n * (int64_t)(20 * KNN_SAMPLE) + (1 << 20));
     unsigned long long hn = 0;
     int herr = 0;
-    for (int attempt = 0; attempt < 3; attempt++) {
-        cq.ensure(cap, s);
-        cx.ensure(cap, s);
-        R.cq = cq.p;
-        R.cx = cx.p;
-        R.cap = (int64_t)cq.n;
-        VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
-        k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R);
+    // the candidate sweep, re-run with larger lists when they overflow
+    auto sweep = [&](const std::function<void(int32_t*, int32_t*, float*, int64_t)>& launch) {
+        for (int attempt = 0; attempt < 3; attempt++) {
+            cq.ensure(cap, s);
+            cx.ensure(cap, s);
+            if (wide && cw_out) cw.ensure(cap, s);
+            VJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
+            launch(cq.p, cx.p, (wide && cw_out) ? cw.p : nullptr, (int64_t)cq.n);
+            VJ_LAUNCH_CHECK();
+            VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
+            VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+            VJ_CUDA(cudaStreamSynchronize(s));
+            VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
+            if ((int64_t)hn <= (int64_t)cq.n) break;
+            cap = (int64_t)hn + (int64_t)hn / 4 + RS_HOLE_SLACK;  // the next launch may leave other holes
+        }
+        VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core kNN: candidate list still too small");
+    };
+
+    if (!wide) {
+        abf.alloc((size_t)n * kpad, s);
+        iota.alloc(n, s);
+        k_to_bf16<<<vj_div_up(n * kpad, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, nullptr, 0, n, kpad,
+                                                          cosine ? 1.f : 2.f, cosine ? ix->invn.p : nullptr, abf.p);
+        k_iota<<<vj_div_up(n, 256), 256, 0, s>>>(iota.p, n);
         VJ_LAUNCH_CHECK();
-        VJ_CUDA(cudaMemcpyAsync(&hn, ctr.p, sizeof(hn), cudaMemcpyDeviceToHost, s));
-        VJ_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        VJ_CUDA(cudaStreamSynchronize(s));
-        VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "tensor-core kNN: a pipeline wait timed out");
-        if ((int64_t)hn <= (int64_t)cq.n) break;
-        cap = (int64_t)hn + (int64_t)hn / 4 + RS_HOLE_SLACK;  // the next launch may leave other holes
+        CUtensorMap ta = make_map(abf.p, n, kpad, 128);
+        CUtensorMap tb = make_map(ix->xbf.p, n, kpad, RS_BN);
+        CUtensorMap tab = cosine ? ta : make_map16(ix->abias.p, 128, 128);
+        CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, n, RS_BN);
+        RsParams R{};
+        R.nrows = n;
+        R.ncols = n;
+        R.nkb = kpad / TC_BK;
+        R.bias = cosine ? 0 : 1;
+        R.nrp = (int)vj_div_up(n, 256);
+        const int nct_all = (int)vj_div_up(n, RS_BN);
+        const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
+        const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
+        R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
+        R.err = err.p;
+        R.spin_limit = spin_limit;
+        const size_t smem = fixed + per * (size_t)R.stages;
+
+        // 1. sample sweep: one unit per 256-row block over every KNN_SAMPLE-th tile
+        R.tstride = KNN_SAMPLE;
+        R.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
+        R.tpu = R.nct;
+        R.nunits = R.nrp;
+        R.top16 = top.p;
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tc_res<EPI_SAMPLE><<<std::min(R.nunits, ix->num_sms), (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
+        VJ_LAUNCH_CHECK();
+        k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
+        VJ_LAUNCH_CHECK();
+
+        // 2. candidate sweep over every tile, rows are node ids
+        R.tstride = 1;
+        R.nct = nct_all;
+        R.tpu = best_tiles_per_unit(R.nrp, R.nct, ix->num_sms, 3);
+        R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
+        R.a_thr = thr.p;
+        R.a_ids = iota.p;
+        R.ncand = ctr.p;
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sweep([&](int32_t* pq, int32_t* px, float*, int64_t c) {
+            R.cq = pq;
+            R.cx = px;
+            R.cap = c;
+            k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R);
+        });
+    } else {
+        // streamed tiles: A and B are both the BF16 copy of every node
+        CUtensorMap ta = make_map(ix->xbf.p, n, kpad, WD_BM);
+        CUtensorMap tb = make_map(ix->xbf.p, n, kpad, WD_BN);
+        WdParams W{};
+        W.nrows = n;
+        W.ncols = n;
+        W.nkb = kpad / TC_BK;
+        W.nrt = (int)vj_div_up(n, WD_BM);
+        W.cs = ix->wcs.p;
+        W.cb = ix->wcb.p;
+        W.err = err.p;
+        W.spin_limit = spin_limit;
+        const int nct_all = (int)vj_div_up(n, WD_BN);
+        const size_t smem = wide_smem();
+        // 1. sample sweep: one unit per 128-row tile over every KNN_SAMPLE-th tile
+        W.tstride = KNN_SAMPLE;
+        W.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
+        W.tpu = W.nct;
+        W.nunits = W.nrt;
+        W.top16 = top.p;
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tc_wide<EPI_SAMPLE><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta, tb, W);
+        VJ_LAUNCH_CHECK();
+        k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
+        VJ_LAUNCH_CHECK();
+        // 2. candidate sweep over every tile, rows are node ids
+        W.tstride = 1;
+        W.nct = nct_all;
+        W.tpu = best_tiles_per_unit(W.nrt, W.nct, ix->num_sms, 1);
+        W.nunits = W.nrt * (int)vj_div_up(W.nct, W.tpu);
+        W.thr = thr.p;
+        W.a_ids = nullptr;
+        W.ncand = ctr.p;
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sweep([&](int32_t* pq, int32_t* px, float* pw, int64_t c) {
+            W.cq = pq;
+            W.cx = px;
+            W.cw = pw;
+            W.cap = c;
+            k_tc_wide<EPI_SCAN><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta, tb, W);
+        });
     }
-    VJ_REQUIRE((int64_t)hn <= (int64_t)cq.n, VJ_ERR_STATE, "tensor-core kNN: candidate list still too small");
     const int64_t nc = (int64_t)hn;
 
     // 3. candidates grouped by row (CSR) and each row's bound
@@ -1298,17 +1489,27 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     off.ensure(n + 1, s);
     vj_exclusive_scan_i32_to_i64(counts.p, off.p, n, ix);
     ids.ensure(std::max<int64_t>(nc, 1), s);
-    if (nc > 0) k_pair_scatter<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, cx.p, nc, off.p, cursor.p, ids.p);
+    const bool with_w = wide && cw_out;
+    if (with_w) cw_out->ensure(std::max<int64_t>(nc, 1), s);
+    if (nc > 0)
+        k_pair_scatter<<<vj_div_up(nc, 256), 256, 0, s>>>(cq.p, cx.p, with_w ? cw.p : nullptr, nc, off.p, cursor.p,
+                                                          ids.p, with_w ? cw_out->p : nullptr);
     VJ_LAUNCH_CHECK();
     row_thr.ensure(n, s);
-    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, thr.p, n, ix->metric, kpad, ix->tc_cb, ix->tc_c3,
-                                                  ix->tc_cbmax, ix->maxnorm, row_thr.p);
+    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, ix->invn.p, thr.p, n, ix->metric, ix->cos_raw ? 1 : 0,
+                                                  kpad, ix->tc_cb, ix->tc_c3, ix->tc_cbmax, ix->maxnorm, row_thr.p);
     VJ_LAUNCH_CHECK();
+    if (wide) {
+        // build-sized lists (hundreds of candidates per node) are not kept for later scans
+        cq.free_(s);
+        cx.free_(s);
+    }
     counts.free_(s);
     cursor.free_(s);
     abf.free_(s);
     top.free_(s);
     thr.free_(s);
+    cw.free_(s);
     iota.free_(s);
     err.free_(s);
     ctr.free_(s);

@@ -383,8 +383,40 @@ __global__ void __launch_bounds__(256) k_knn_rerank(const float* __restrict__ ve
 // dropped): exact keys, sort, FP64 near-tie runs, then the certificate
 // against row_thr, a lower bound on the true key of every node not listed.
 // Rows that cannot be certified (or list more than KC_CAP) go to bad_rows.
+//
+// With the streamed kernel's tile values cw (acc * cs per candidate), an
+// approximate key k~ = |a|^2 + |b|^2 - cw (L2), 1 - cw / |a| (cosine, raw
+// rows) or 1 - cw (cosine, unit rows) comes first, within beta of the true
+// key (beta = cb |a||b| + (c3 + 4u)(|a|^2 + |b|^2), or cb + 4u for cosine,
+// bounded with the largest norm).  Only the prefix with k~ <= k~_K + 2 beta
+// can hold the top K; it alone gets exact keys, and every candidate after it
+// has a true key above k~_min_out - beta, which joins the certificate.
 constexpr int KC_CAP = 1024;
 constexpr int KC_WPB = 4;
+
+// bitonic sort of P2 (key, id) pairs in shared memory, ascending (one warp)
+__device__ void bitonic_pairs(float* key, int* id, int P2, int lane) {
+    for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P2; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = kless(key[p], id[p], key[i], id[i]);
+                    if (gt == up) {
+                        const float tk = key[i];
+                        const int ti = id[i];
+                        key[i] = key[p];
+                        id[i] = id[p];
+                        key[p] = tk;
+                        id[p] = ti;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
 
 struct KcSmem {
     int id[KC_CAP];
@@ -397,7 +429,9 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     k_knn_rerank_csr(const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d, int64_t n,
                      int metric, int K, const int64_t* __restrict__ off, const int32_t* __restrict__ cand,
                      const float* __restrict__ row_thr, int32_t* __restrict__ out_id, float* __restrict__ out_key,
-                     int32_t* __restrict__ bad_rows, int* __restrict__ nbad, unsigned long long* __restrict__ nrechk) {
+                     int32_t* __restrict__ bad_rows, int* __restrict__ nbad, unsigned long long* __restrict__ nrechk,
+                     const float* __restrict__ cw, const float* __restrict__ sqn, int raw, float cb, float c3,
+                     float maxnorm) {
     extern __shared__ uint8_t kc_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     KcSmem& S = reinterpret_cast<KcSmem*>(kc_raw)[warp];
@@ -409,13 +443,22 @@ __global__ void __launch_bounds__(KC_WPB * 32)
         if (lane == 0) bad_rows[atomicAdd(nbad, 1)] = (int32_t)r;
         return;
     }
-    // compact the list without the row itself
+    // compact the list without the row itself (with its approximate keys)
+    const float rn2 = cw && metric == 0 ? sqn[r] : 0.f;
+    const float rinv = cw && metric != 0 && raw ? invn[r] : 1.f;
     int nvalid = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int v = base + lane < cnt ? cand[b + base + lane] : -1;
         const bool keep = v >= 0 && v != r;
         const unsigned m = __ballot_sync(VJ_FULL, keep);
-        if (keep) S.id[nvalid + __popc(m & ((1u << lane) - 1u))] = v;
+        if (keep) {
+            const int pos = nvalid + __popc(m & ((1u << lane) - 1u));
+            S.id[pos] = v;
+            if (cw) {
+                const float w = cw[b + base + lane];
+                S.key[pos] = metric == 0 ? (rn2 + sqn[v]) - w : 1.f - w * rinv;
+            }
+        }
         nvalid += __popc(m);
     }
     int P2 = 32;
@@ -425,32 +468,35 @@ __global__ void __launch_bounds__(KC_WPB * 32)
         S.key[e] = FLT_MAX;
     }
     __syncwarp();
+    float out_lo = FLT_MAX;  // approximate-key prefilter: lower bound on every dropped candidate
+    if (cw && nvalid > K) {
+        bitonic_pairs(S.key, S.id, P2, lane);
+        const double mx = (double)maxnorm;
+        const double beta = metric == 0
+                                ? (double)cb * sqrt((double)rn2) * mx + ((double)c3 + 4.0 * VJ_F32_U) * ((double)rn2 + mx * mx)
+                                : (double)cb + 4.0 * VJ_F32_U;
+        const double lim = (double)S.key[K - 1] + 2.0 * beta;
+        int ne = 0;
+        for (int base = 0; base < nvalid; base += 32) {
+            const bool in = base + lane < nvalid && (double)S.key[base + lane] <= lim;
+            ne += __popc(__ballot_sync(VJ_FULL, in));
+        }
+        if (ne < nvalid) out_lo = (float)((double)S.key[ne] - beta);
+        nvalid = ne;
+        P2 = 32;
+        while (P2 < nvalid) P2 <<= 1;
+        for (int e = nvalid + lane; e < P2; e += 32) {
+            S.id[e] = INT32_MAX;
+            S.key[e] = FLT_MAX;
+        }
+        __syncwarp();
+    }
     float4 q[NPL];
     load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
     const float invq = metric ? invn[r] : 0.f;
     group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, S.id, nvalid, S.key, lane);
     __syncwarp();
-    // bitonic sort of P2 (key, id) pairs, ascending
-    for (int k = 2; k <= P2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < P2; i += 32) {
-                const int p = i ^ j;
-                if (p > i) {
-                    const bool up = (i & k) == 0;
-                    const bool gt = kless(S.key[p], S.id[p], S.key[i], S.id[i]);
-                    if (gt == up) {
-                        const float tk = S.key[i];
-                        const int ti = S.id[i];
-                        S.key[i] = S.key[p];
-                        S.id[i] = S.id[p];
-                        S.key[p] = tk;
-                        S.id[p] = ti;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
+    bitonic_pairs(S.key, S.id, P2, lane);
     // near-tie runs among the first K + 1: FP64 re-rank (runs stay below 128)
     const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
     const int lim = min(K + 1, nvalid);
@@ -498,7 +544,7 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     if (ok) {
         const double kth = (double)S.key[K - 1];
         const double hi = metric == 0 ? kth * (1.0 + tol) : kth + tol;
-        ok = hi < (double)row_thr[r];
+        ok = hi < (double)row_thr[r] && hi < (double)out_lo;
     }
     if (!ok) {
         if (lane == 0) bad_rows[atomicAdd(nbad, 1)] = (int32_t)r;
@@ -705,20 +751,23 @@ void vj_build_knn(vj_index* ix) {
     if (ix->p.precision == VJ_PREC_BF16) {
         DBuf<int64_t> coff;
         DBuf<int32_t> cids;
-        DBuf<float> cthr;
-        tc = vj_tc_knn_candidates(ix, coff, cids, cthr);
+        DBuf<float> cthr, cw;
+        tc = vj_tc_knn_candidates(ix, coff, cids, cthr, &cw);
         if (tc) {
             const int smem = KC_WPB * (int)sizeof(KcSmem);
+            const float* w = cw.n > 0 ? cw.p : nullptr;  // tile values: streamed kernel only
             VJ_DISPATCH_GN(dp4, VJ_CUDA(cudaFuncSetAttribute(k_knn_rerank_csr<G, NPL>,
                                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
                            k_knn_rerank_csr<G, NPL><<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
                                ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p,
-                               ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p));
+                               ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->cos_raw ? 1 : 0,
+                               ix->tc_cb, ix->tc_c3, (float)(ix->maxnorm * 1.0001)));
             VJ_LAUNCH_CHECK();
         }
         coff.free_(s);
         cids.free_(s);
         cthr.free_(s);
+        cw.free_(s);
     }
     ix->knn_tc = tc;
     cid.alloc((size_t)n * KP, s);

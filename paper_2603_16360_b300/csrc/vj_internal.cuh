@@ -133,6 +133,9 @@ struct vj_index {
     float route_threshold = 0.5f;
     int beam_cap = 256;
     bool bf16_exact = false;   // BF16 Gram keys are exact for these inputs (small integers)
+    bool bf16_lossless = false;  // every coordinate is exactly a BF16 value
+    bool cos_raw = false;      // cosine, streamed tiles: xbf holds the raw (not unit) rows, scaled in the epilogue
+    DBuf<float> wcs, wcb;      // [n] streamed tiles: per-column scale and bias of the accumulator
     double maxnorm = 0.0;      // largest vector norm (FP64)
     double last_scan_ms = 0.0; // device time of the last tensor-core scan
     int64_t last_scan_cand = 0;
@@ -202,7 +205,11 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
 
 // tensor-core (tcgen05) BF16 scan of query rows against all data rows:
 // candidate (query index, data id) pairs, exact after re-check
-bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr);
+// cw (optional): per candidate, the low-precision Gram value acc * cs of the
+// streamed kernel (kp > 128; left empty otherwise), for the approximate-key
+// prefilter of the re-rank
+bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr,
+                          DBuf<float>* cw = nullptr);
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
                               DBuf<int32_t>& cx, double* ms_out, DBuf<float>* ck = nullptr);
 

@@ -26,6 +26,18 @@ project's benchmark configurations):
                     fresh centres; a target of U{5..50} matches per query.
                     The size ranges are parameters, so tests draw small
                     collections from the same recipe.
+* ``vmf_like``      X 10,000,000 x 768 unit vectors rounded to BF16 (cosine),
+                    a 4,096-component von Mises-Fisher mixture with
+                    concentration kappa = 50 (mean directions uniform on the
+                    sphere, Wood's rejection sampler for the component along
+                    the mean); 1,000,000 queries, 80 % from the same mixture
+                    and 20 % from 1,024 unseen mean directions; plus a
+                    held-out set of 100,000 queries drawn the same way for
+                    training the learned predictor.  ``scale`` shrinks the
+                    counts and the number of mixture components together.
+* ``gauss_wide``    X = Q = 1,000,000 x 960 float32, a 512-component Gaussian
+                    mixture (centres ~ N(0, I), sigma 0.3), the equal-size
+                    GIST-shaped precision case.
 """
 from __future__ import annotations
 
@@ -146,3 +158,102 @@ def angular_collection(seed: int = 1239, n: int = 64, **kw):
     """The n instances of an angular collection, generated one at a time."""
     for i in range(n):
         yield angular_instance(seed, i, **kw)
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 value (ties to even), kept as float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+def wood_w(rng, n: int, d: int, kappa: float) -> np.ndarray:
+    """Component along the mean direction of n draws from vMF(kappa) on the unit
+    sphere of R^d, by Wood's rejection sampler ("Simulation of the von
+    Mises Fisher distribution", 1994): a Beta((d-1)/2, (d-1)/2) proposal mapped
+    through a Moebius transform, accepted by the log-density test."""
+    m = d - 1.0
+    b = (-2.0 * kappa + np.sqrt(4.0 * kappa * kappa + m * m)) / m
+    x0 = (1.0 - b) / (1.0 + b)
+    c = kappa * x0 + m * np.log(1.0 - x0 * x0)
+    w = np.empty(n)
+    todo = np.arange(n)
+    while todo.size:
+        z = rng.beta(m / 2.0, m / 2.0, size=todo.size)
+        wt = (1.0 - (1.0 + b) * z) / (1.0 - (1.0 - b) * z)
+        u = rng.uniform(size=todo.size)
+        ok = kappa * wt + m * np.log(1.0 - x0 * wt) - c >= np.log(u)
+        w[todo[ok]] = wt[ok]
+        todo = todo[~ok]
+    return w
+
+
+def _vmf_rows(rng, mus, lab, w):
+    """Unit vectors w * mu + sqrt(1 - w^2) * v, v uniform on the sphere of the
+    directions orthogonal to mu (numpy, float64 arithmetic)."""
+    mu = mus[lab].astype(np.float64)
+    g = rng.standard_normal(mu.shape)
+    v = g - (g * mu).sum(1, keepdims=True) * mu
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return (w[:, None] * mu + np.sqrt(np.maximum(1.0 - w * w, 0.0))[:, None] * v).astype(np.float32)
+
+
+def vmf_like(seed: int = 1238, scale: float = 1.0, nx: int = 10_000_000, nq: int = 1_000_000,
+             nh: int = 100_000, d: int = 768, k: int = 4096, k_unseen: int = 1024, kappa: float = 50.0,
+             unseen_frac: float = 0.20, device=None) -> Workload:
+    """The learned-predictor workload.  Q holds the nq queries followed by the nh
+    held-out queries (``ood`` marks queries of unseen components).  With a
+    torch CUDA ``device`` the bulk (the Gaussian draws, the projections and the
+    BF16 rounding) runs there with a seeded torch generator and X, Q are CUDA
+    tensors; the mean directions, labels and Wood draws come from numpy either
+    way."""
+    nx = max(1, int(round(nx * scale)))
+    nq = max(1, int(round(nq * scale)))
+    nh = int(round(nh * scale))
+    k = max(1, int(round(k * scale)))
+    k_unseen = max(1, int(round(k_unseen * scale)))
+    rng = np.random.default_rng(seed)
+    mus = _unit(rng.standard_normal((k, d)))
+    fresh = _unit(rng.standard_normal((k_unseen, d)))
+    nqa = nq + nh
+    unseen = rng.random(nqa) < unseen_frac
+    lab_x = rng.integers(0, k, size=nx)
+    lab_q = np.where(unseen, k + rng.integers(0, k_unseen, size=nqa), rng.integers(0, k, size=nqa))
+    allmu = np.concatenate([mus, fresh])
+    w_x = wood_w(rng, nx, d, kappa)
+    w_q = wood_w(rng, nqa, d, kappa)
+    if device is None:
+        X = bf16_round(_vmf_rows(rng, allmu, lab_x, w_x))
+        Q = bf16_round(_vmf_rows(rng, allmu, lab_q, w_q))
+    else:
+        import torch
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+        mu_t = torch.from_numpy(allmu).to(device)
+
+        def rows(lab, w):
+            out = torch.empty((len(lab), d), dtype=torch.float32, device=device)
+            for a in range(0, len(lab), 1 << 20):
+                b = min(len(lab), a + (1 << 20))
+                mu = mu_t[torch.from_numpy(lab[a:b]).to(device)]
+                g = torch.randn((b - a, d), generator=gen, device=device, dtype=torch.float32)
+                v = g - (g * mu).sum(1, keepdim=True) * mu
+                v = v / v.norm(dim=1, keepdim=True)
+                wt = torch.from_numpy(w[a:b]).to(device=device, dtype=torch.float32)[:, None]
+                out[a:b] = (wt * mu + torch.sqrt(torch.clamp(1.0 - wt * wt, min=0.0)) * v).to(torch.bfloat16).float()
+            return out
+
+        X = rows(lab_x, w_x)
+        Q = rows(lab_q, w_q)
+    return Workload("vmf_like", X, Q, unseen, 1, 32, 64, 10.0, seed)
+
+
+def gauss_wide(seed: int = 1237, scale: float = 1.0, nx: int = 1_000_000, nq: int = 1_000_000, d: int = 960,
+               k: int = 512, sigma: float = 0.3) -> Workload:
+    nx = max(1, int(round(nx * scale)))
+    nq = max(1, int(round(nq * scale)))
+    rng = np.random.default_rng(seed)
+    centres = rng.standard_normal((k, d)).astype(np.float32)
+    X = _mixture(rng, nx, centres, sigma)
+    Q = _mixture(rng, nq, centres, sigma)
+    return Workload("gauss_wide", X, Q, np.zeros(nq, bool), 0, 32, 64, 10.0, seed)
