@@ -1,23 +1,30 @@
 """Benchmark of the merged-index vector epsilon-join on one B300.
 
 Metric: queries/s at recall >= 0.95 against the exact join, learned+BF16 arm
-versus the plain FP32 arm.  One step = one join of every query of the
-workload against the prebuilt merged index (the offline build is timed
-separately, as the paper excludes indexing from join latency).
+versus the plain FP32 arm.  One step = one join of every query of the index
+(the offline build is timed separately, as the paper excludes indexing from
+join latency).
 
-  plain FP32     MI+SWS (Alg. 1 with soft sharing) in FP32; CheckHybrid by the
-                 d1/d2 rule; when that misses recall 0.95, hybrid search for
-                 every query with the smallest queue size reaching it.
-  learned+BF16   MI+SWS with the learned prologue: a predictor (trained here
-                 on labels from the joins) routes each query to the BF16
-                 tensor-core brute-force scan (exact after re-check) or gives
-                 it a hybrid queue size; the route threshold is the largest
-                 one reaching recall 0.95.
+Default workload: 10M data x 1M evaluated queries x 768-d unit vectors rounded
+to BF16 (vmf_like: a 4,096-component von Mises-Fisher mixture, kappa 50, 20 %
+of the queries from unseen components; cosine distance; eps for a mean of 10
+matches per query; degree 32).  A further 100K held-out queries of the same
+recipe are built into the same merged index: the learned arm trains on them
+and picks its operating point on them; recall and queries/s count only the
+evaluated queries (the held-out rows are joined in every step too).
 
-The default workload is 1M data x 100K queries x 128-d integer descriptors
-(sift_like, degree 32, eps for a mean of 20 matches per query).  Prints one
-JSON line.  --impl reference times the CPU oracle's join (FP64, one thread)
-on whole MST subtrees of the same workload instead.
+  plain FP32     MI+SWS (Alg. 1 with soft sharing) with FP32 gathers: the
+                 d1/d2 rule at several hybrid queue sizes, the rule with its
+                 OOD queries routed to the tensor-core brute-force scan, and
+                 forced hybrid search when none of those reaches 0.95; the
+                 fastest setting reaching recall 0.95 is timed.
+  learned+BF16   MI+SWS with the predictor's per-query plan (route to the
+                 scan, no expansion, BFS or a hybrid queue size), trained by
+                 the library on the held-out queries (vj_train_predictor), and
+                 BF16 gathers (exact here: every coordinate is a BF16 value).
+
+Prints one JSON line.  --impl reference times the CPU oracle's join (FP64,
+one thread) on whole MST subtrees of the same workload instead.
 """
 from __future__ import annotations
 
@@ -38,22 +45,20 @@ sys.path.insert(0, ROOT)
 METRIC = "queries/s at recall≥0.95 vs exact join: learned+BF16 vs plain FP32, one B300"
 
 
-def _traffic(kernel, scale):
-    """DRAM bytes per step of `kernel` from profiles/traffic.md (an ncu capture of the full-size learned
-    step), or None when the workload is not the full-size one or the kernel's source changed since."""
-    if scale != 1.0:
-        return None
+def _traffic(kernel, workload):
+    """DRAM bytes per step of `kernel` on `workload` ("name@scale") from profiles/traffic.md, or None when
+    no capture of that workload is recorded or the kernel's source changed since."""
     import hashlib
     import re
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
     for line in open(p):
-        m = re.match(r"^\| (\S+) \| (\S+) \| ([0-9a-f]{64}) \| ([0-9.eE+]+) \|", line)
-        if m and m.group(1) == kernel:
-            src = os.path.join(ROOT, m.group(2))
-            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == m.group(3):
-                return float(m.group(4))
+        m = re.match(r"^\| (\S+) \| (\S+) \| (\S+) \| ([0-9a-f]{64}) \| ([0-9.eE+]+) \|", line)
+        if m and m.group(1) == kernel and m.group(2) == workload:
+            src = os.path.join(ROOT, m.group(3))
+            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == m.group(4):
+                return float(m.group(5))
     return None
 
 
@@ -110,10 +115,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_workload(name, scale):
+def make_workload(name, scale, replica=0):
+    """The workload `name` (replica r > 0: the same recipe with seed + 1000 r)."""
     from paper_2603_16360_b300 import inputs
+    if name == "vmf_like":
+        return inputs.vmf_like(seed=1238 + 1000 * replica, scale=scale, device="cuda")
     if name == "sift_like":
-        return inputs.sift_like(scale=scale)
+        return inputs.sift_like(seed=1236 + 1000 * replica, scale=scale, nh=10_000)
     if name == "gauss_small":
         return inputs.gauss_small()
     if name == "angular_one":
@@ -123,79 +131,113 @@ def make_workload(name, scale):
     raise SystemExit(f"unknown workload {name}")
 
 
+def host(a):
+    """numpy copy of a workload array (host arrays pass through)."""
+    return a.detach().cpu().numpy() if hasattr(a, "detach") else a
+
+
+def n_eval(w):
+    """Evaluated queries: the rows of Q before the held-out ones."""
+    return w.nq - getattr(w, "nh", 0)
+
+
 def calibrate_eps(vj, ix, w, target):
-    """eps with a mean of `target` exact matches per query (exact GPU join)."""
+    """eps with a mean of `target` exact matches per evaluated query: an
+    overestimate from a 200 x 20,000 sample, then the k-th distance of the
+    exact GPU join."""
     rng = np.random.default_rng(w.seed + 7)
-    qs = w.Q[rng.choice(w.nq, size=min(200, w.nq), replace=False)].astype(np.float64)
-    xs = w.X[rng.choice(w.nx, size=min(20000, w.nx), replace=False)].astype(np.float64)
-    d2 = (qs ** 2).sum(1)[:, None] + (xs ** 2).sum(1)[None, :] - 2 * qs @ xs.T
-    dd = np.sqrt(np.maximum(d2, 0)).ravel()
+    ne = n_eval(w)
+    qi = np.sort(rng.choice(ne, size=min(200, ne), replace=False))
+    xi = np.sort(rng.choice(w.nx, size=min(20000, w.nx), replace=False))
+    if hasattr(w.X, "detach"):
+        import torch
+        qs = w.Q[torch.from_numpy(qi).to(w.Q.device)].double().cpu().numpy()
+        xs = w.X[torch.from_numpy(xi).to(w.X.device)].double().cpu().numpy()
+    else:
+        qs, xs = w.Q[qi].astype(np.float64), w.X[xi].astype(np.float64)
+    if w.metric == 0:
+        d2 = (qs ** 2).sum(1)[:, None] + (xs ** 2).sum(1)[None, :] - 2 * qs @ xs.T
+        dd = np.sqrt(np.maximum(d2, 0)).ravel()
+    else:
+        qn = qs / np.linalg.norm(qs, axis=1, keepdims=True)
+        xn = xs / np.linalg.norm(xs, axis=1, keepdims=True)
+        dd = (1.0 - qn @ xn.T).ravel()
     guess = float(np.quantile(dd, min(8.0 * target / w.nx, 0.5)))
     for _ in range(12):
         ex = vj.vj_join_exact(ix, guess)
-        if ex.offsets[-1] >= target * w.nq:
+        if ex.offsets[ne] >= target * ne:
             break
-        guess *= 1.25
-    k = int(target * w.nq)
-    return float(np.float32(np.partition(ex.dists, k)[k]))
+        # grow: L2 by a factor, cosine by shrinking the similarity bound
+        guess = guess * 1.25 if w.metric == 0 else 1.0 - (1.0 - guess) * 0.9
+    k = int(target * ne)
+    return float(np.float32(np.partition(ex.dists[:ex.offsets[ne]], k)[k]))
 
 
-def per_query_hits(r, ex, nx):
-    """(hits per query, exact count per query) of result r against ex."""
-    nq = len(ex.offsets) - 1
-    qa = np.repeat(np.arange(nq, dtype=np.int64), np.diff(ex.offsets))
-    qb = np.repeat(np.arange(nq, dtype=np.int64), np.diff(r.offsets))
-    ka = qa * nx + ex.ids
-    kb = qb * nx + r.ids
+def per_query_hits(r, ex, nx, rows=None):
+    """(hits, exact count) per query of result r against ex, over the query
+    index range rows = (lo, hi) (all queries when None)."""
+    lo, hi = (0, len(ex.offsets) - 1) if rows is None else rows
+    qa = np.repeat(np.arange(lo, hi, dtype=np.int64), np.diff(ex.offsets[lo:hi + 1]))
+    qb = np.repeat(np.arange(lo, hi, dtype=np.int64), np.diff(r.offsets[lo:hi + 1]))
+    ka = qa * nx + ex.ids[ex.offsets[lo]:ex.offsets[hi]]
+    kb = qb * nx + r.ids[r.offsets[lo]:r.offsets[hi]]
     common = np.intersect1d(ka, kb, assume_unique=True)
-    hits = np.bincount(common // nx, minlength=nq)
-    return hits, np.diff(ex.offsets)
+    hits = np.bincount(common // nx - lo, minlength=hi - lo)
+    return hits, np.diff(ex.offsets[lo:hi + 1])
 
 
-def recall_of(r, ex, nx):
-    hits, tot = per_query_hits(r, ex, nx)
+def recall_of(r, ex, nx, rows=None):
+    hits, tot = per_query_hits(r, ex, nx, rows)
     return float(hits.sum() / max(tot.sum(), 1))
 
 
-def per_query_recall_mean(r, ex, nx):
+def per_query_recall_mean(r, ex, nx, rows=None):
     """Mean over queries of |R n E| / |E|; a query with an empty exact row counts 1."""
-    hits, tot = per_query_hits(r, ex, nx)
+    hits, tot = per_query_hits(r, ex, nx, rows)
     return float(np.where(tot > 0, hits / np.maximum(tot, 1), 1.0).mean())
 
 
-def sample_subtrees(parent, order, target=1000):
-    """Whole MST subtrees (children of the entry) totalling >= target queries, in order."""
+def sample_subtrees(parent, order, target=1000, limit=None):
+    """Whole MST subtrees (children of the entry) totalling >= target queries,
+    in processing order; with `limit`, only queries below it (their
+    subtrees contain no other query)."""
     nq = len(parent)
     children = {}
     for q in range(nq):
         children.setdefault(int(parent[q]), []).append(q)
     chosen = set()
     for r0 in [q for q in order if parent[q] < 0]:
-        stack = [int(r0)]
+        stack, sub = [int(r0)], []
         while stack:
             a = stack.pop()
-            chosen.add(a)
+            sub.append(a)
             stack.extend(children.get(a, []))
+        if limit is not None and max(sub) >= limit:
+            continue
+        chosen.update(sub)
         if len(chosen) >= target:
             break
     return np.array([q for q in order if int(q) in chosen], np.int32)
 
 
-def run_cpu_oracle(w, vj, ix, eps, sample_q=1000, mode="adapt", budget=256):
+def run_cpu_oracle(w, vj, ix, eps, sample_q, mode, budget, Xh, Qh):
+    """The oracle's MI+SWS join (FP64, one thread) on whole MST subtrees of
+    evaluated queries of the GPU-built graph: (queries, seconds)."""
     import oracle
     adj, entry, parent, order, _ = vj.vj_export_graph(ix)
-    sub = sample_subtrees(parent, order, sample_q)
+    sub = sample_subtrees(parent, order, sample_q, limit=n_eval(w))
     t0 = time.perf_counter()
-    oracle.join(w.X, w.Q, adj, entry, eps, work_sharing=oracle.WS_SOFT, adapt_hybrid=(mode == "adapt"),
-                force_hybrid=(mode == "force"), hybrid_beam_size=budget, order=sub, parent=parent, queries=sub)
+    oracle.join(Xh, Qh, adj, entry, eps, metric=w.metric, work_sharing=oracle.WS_SOFT,
+                adapt_hybrid=(mode == "adapt"), force_hybrid=(mode == "force"), hybrid_beam_size=budget,
+                order=sub, parent=parent, queries=sub)
     return len(sub), time.perf_counter() - t0
 
 
-def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed"):
-    """Device-resident joins on torch's current stream: (ms per step, per-step stats).
-
-    The timed steps run inside an NVTX range named `tag`, so a profiler can
-    select exactly their kernels (ncu --nvtx --nvtx-include "<tag>/")."""
+def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed", clocks=False):
+    """Device-resident joins on torch's current stream: (ms per step, per-step
+    stats, clock summary or None).  The timed steps run inside an NVTX range
+    named `tag` (ncu --nvtx --nvtx-include "<tag>/" selects their kernels);
+    with clocks, nvidia-smi samples the SM clock during them."""
     stream = torch.cuda.current_stream()
     vj.vj_set_stream(ix, stream.cuda_stream)
     for _ in range(warmup):
@@ -203,6 +245,10 @@ def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed"):
     torch.cuda.synchronize()
     stats = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cs = ClockSampler(torch.cuda.current_device()) if clocks else None
+    if cs:
+        cs.__enter__()
+        time.sleep(0.3)  # the sampler's first rows before the timed region
     torch.cuda.nvtx.range_push(tag)
     e0.record(stream)
     for _ in range(steps):
@@ -214,7 +260,9 @@ def timed(vj, torch, ix, eps, budget, steps, warmup, tag="timed"):
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps, stats
+    if cs:
+        cs.__exit__()
+    return e0.elapsed_time(e1) / steps, stats, (cs.summary() if cs else None)
 
 
 def slowest_rank_ms(ms, dist, device):
@@ -411,19 +459,122 @@ def bench_collection(args, vj, torch):
         ix.free()
 
 
+
+def plain_arm(vj, ix, eps, ex, w, log):
+    """The paper's method in FP32 (MI+SWS): the d1/d2 rule at several hybrid
+    queue sizes, the rule with its OOD queries sent to the brute-force scan,
+    and, when none of those reaches recall 0.95 on the evaluated queries,
+    forced hybrid search at growing queue sizes.  Returns the fastest setting
+    that reaches 0.95 (else the one with the best recall) and the sweep."""
+    ne = n_eval(w)
+    sweep, best, best_any = [], None, None
+
+    def consider(name, setup):
+        nonlocal best, best_any
+        try:
+            setup()
+            vj.vj_join(ix, eps)
+            r = vj.vj_join(ix, eps)
+        except vj.VjError as e:
+            sweep.append({"setting": name, "error": str(e)[:120]})
+            vj.vj_set_plan(ix, None, None)
+            return None
+        rec = recall_of(r, ex, w.nx, (0, ne))
+        ent = {"setting": name, "recall": round(rec, 4), "ms": round(r.stats["ms_total"], 3),
+               "hybrid_queries": r.stats["hybrid_queries"], "routed": int((r.hybrid == 2).sum())}
+        sweep.append(ent)
+        log(f"plain {name}: recall {rec:.4f} ms {r.stats['ms_total']:.2f}")
+        cand = (r.stats["ms_total"], name, setup, rec, r)
+        if rec >= 0.95 and (best is None or cand[0] < best[0]):
+            best = cand
+        if best_any is None or rec > best_any[3]:
+            best_any = cand
+        return rec
+
+    def rule(beam):
+        return lambda: (vj.vj_set_plan(ix, None, None),
+                        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1, force_hybrid=0,
+                                              hybrid_beam=beam, learned=0, gather=vj.VJ_PREC_FP32))
+
+    for beam in (256, 32, 4):
+        consider(f"rule, hybrid queue {beam}", rule(beam))
+    # the rule's OOD queries (hybrid flag 1 under the rule) routed to the exact scan
+    rule(256)()
+    flags = vj.vj_join(ix, eps).hybrid
+    route = (flags == 1).astype(np.uint8)
+
+    def rule_route():
+        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0, hybrid_beam=1,
+                              learned=0, gather=vj.VJ_PREC_FP32)
+        vj.vj_set_plan(ix, route, np.zeros(w.nq, np.int32))
+
+    consider(f"rule, its {int(route.sum())} OOD queries routed to the scan", rule_route)
+    if best is None:
+        for beam in (2, 4, 8, 16, 32, 64, 128, 256):
+            rec = consider(f"forced hybrid, queue {beam}",
+                           lambda beam=beam: (vj.vj_set_plan(ix, None, None),
+                                              vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0,
+                                                                    force_hybrid=1, hybrid_beam=beam, learned=0,
+                                                                    gather=vj.VJ_PREC_FP32)))
+            if rec is not None and rec >= 0.95:
+                break
+    return (best or best_any), sweep
+
+
+def learned_arm(vj, ix, eps, ex, w, log, caps):
+    """The learned route with BF16 gathers: a predictor trained by the library
+    on the held-out queries' labels (vj_train_predictor), then the fastest
+    (route threshold, hybrid-queue cap) whose join reaches recall 0.955 on
+    the held-out queries.  The evaluated queries' recall is measured after."""
+    ne = n_eval(w)
+    rows = np.arange(ne, w.nq, dtype=np.int32)
+    t0 = time.perf_counter()
+    m, rep = vj.vj_train_predictor(ix, eps, rows, ladder=[-1, 0, 8], query_recall=0.95, pooled_recall=0.955,
+                                   h1=256, h2=256, epochs=30, batch=256, lr=1e-3, seed=w.seed)
+    train_s = time.perf_counter() - t0
+    log(f"trained on {len(rows)} held-out queries in {train_s:.1f}s: {rep}")
+    sweep, op = [], None
+    for cap in caps:
+        for thr in (0.99, 0.95, 0.9, 0.8, 0.7, 0.5, 0.3, 0.1):
+            vj.vj_attach_predictor(ix, m, thr, cap)
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
+                                  hybrid_beam=max(cap, 1), learned=1, gather=vj.VJ_PREC_BF16)
+            try:
+                vj.vj_join(ix, eps)
+                r = vj.vj_join(ix, eps)
+            except vj.VjError as e:
+                sweep.append({"thr": thr, "beam_cap": cap, "error": str(e)[:120]})
+                continue
+            rh = recall_of(r, ex, w.nx, (ne, w.nq))
+            ent = {"thr": thr, "beam_cap": cap, "heldout_recall": round(rh, 4), "ms": round(r.stats["ms_total"], 3),
+                   "routed": int((r.hybrid == 2).sum()), "no_expansion": int((r.hybrid == 3).sum()),
+                   "ms_traverse": round(r.stats["ms_traverse"], 3), "ms_route": round(r.stats["ms_route"], 3)}
+            sweep.append(ent)
+            log(f"learned {ent}")
+            if rh >= 0.955 and (op is None or r.stats["ms_total"] < op[2]):
+                op = (thr, cap, r.stats["ms_total"])
+    if op is None:  # nothing reached the target on the held-out queries: route the most
+        op = (0.01, caps[0], None)
+    vj.vj_attach_predictor(ix, m, op[0], op[1])
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0, hybrid_beam=max(op[1], 1),
+                          learned=1, gather=vj.VJ_PREC_BF16)
+    return m, {"thr": op[0], "beam_cap": op[1], "sweep": sweep, "train_s": train_s, "train_report": rep}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sift_like")
+    ap.add_argument("--workload", default="vmf_like")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-only", action="store_true")
     ap.add_argument("--instances", type=int, default=64, help="angular_collection: number of join instances")
     ap.add_argument("--collection-learned", action="store_true",
                     help="angular_collection: also time one shared predictor's learned route")
+    ap.add_argument("--quiet", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -440,6 +591,10 @@ def main():
             dist.destroy_process_group()
         return
 
+    def log(msg):
+        if not args.quiet and rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
     from paper_2603_16360_b300 import vj
     vj.load()
     if args.workload == "angular_collection":
@@ -449,35 +604,37 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
-    w = make_workload(args.workload, args.scale)
+    t0 = time.perf_counter()
+    # ranks run independent replicas: the same recipe, each rank its own seed
+    w = make_workload(args.workload, args.scale, rank)
+    gen_s = time.perf_counter() - t0
+    ne = n_eval(w)
     target = w.target_matches
+    log(f"workload {w.name}: X {w.nx} x {w.d}, Q {ne} evaluated + {w.nq - ne} held out ({gen_s:.1f}s)")
     t0 = time.perf_counter()
     ix = vj.vj_build(w.X, w.Q, metric=w.metric, params=vj.default_params(degree=w.degree, knn_k=w.knn_k))
     build_s = time.perf_counter() - t0
-    info = ix.info()
+    info, binfo = ix.info(), ix.build_info()
+    log(f"build {build_s:.1f}s {binfo}")
     eps = calibrate_eps(vj, ix, w, target)
     ex = vj.vj_join_exact(ix, eps)
-    wl_desc = (f"{w.name}: X={w.nx} Q={w.nq} d={w.d} {'L2' if w.metric == 0 else 'cosine'}, "
-               f"eps for a mean of {target:g} matches/query")
+    log(f"eps {eps}: exact pairs {ex.offsets[ne]} over {ne} evaluated queries, scan {ex.stats['ms_scan']:.1f} ms")
+    wl_desc = (f"{w.name}: X={w.nx} Q={ne} (+{w.nq - ne} held-out queries in the index) d={w.d} "
+               f"{'L2' if w.metric == 0 else 'cosine'}, eps for a mean of {target:g} matches/query")
 
-    # ---- plain FP32 arm: operating point
-    plain = None
-    for mode, budget in [("adapt", 256)] + [("force", b) for b in (2, 4, 8, 16, 32, 64, 128, 256)]:
-        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(mode == "adapt"),
-                              force_hybrid=int(mode == "force"), hybrid_beam=budget, learned=0)
-        r = vj.vj_join(ix, eps)
-        rec = recall_of(r, ex, w.nx)
-        plain = (mode, budget, rec, r)
-        if rec >= 0.95:
-            break
-    pmode, pbudget, prec, pr = plain
+    plain, psweep = plain_arm(vj, ix, eps, ex, w, log)
+    p_ms_sweep, pname, psetup, prec, pr = plain
 
     if args.impl == "reference":
+        Xh, Qh = host(w.X), host(w.Q)
+        mode = "adapt" if pname.startswith("rule") else "force"
+        pbeam = int(pname.split()[-1]) if "queue" in pname else 256
         n_s, dt = [], []
-        for _ in range(args.warmup):
-            run_cpu_oracle(w, vj, ix, eps, 200, pmode, pbudget)
+        run_cpu_oracle(w, vj, ix, eps, 200, mode, pbeam, Xh, Qh)
+        for _ in range(max(args.warmup - 1, 0)):
+            run_cpu_oracle(w, vj, ix, eps, 200, mode, pbeam, Xh, Qh)
         for _ in range(args.steps):
-            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, pmode, pbudget)
+            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, mode, pbeam, Xh, Qh)
             n_s.append(n)
             dt.append(t)
         v = sum(n_s) / sum(dt)
@@ -485,171 +642,114 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dt) / len(dt),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS hybrid={pmode} beam {pbudget} "
-                                                       "(Alg. 1), FP64, 1 thread", "eps": eps},
+                "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS ({pname}), Alg. 1, FP64, 1 thread",
+                           "eps": eps},
                 "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"whole MST subtrees, {n_s[0]} queries per step, on the GPU-built graph"},
+                                 "sample": f"whole MST subtrees of evaluated queries, {n_s[0]} queries per step, "
+                                           "on the GPU-built graph"},
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
+        ix.free()
         if dist:
             dist.barrier()
             dist.destroy_process_group()
         return
 
     hbm, bf16, peak_kind = _peaks()
-    # ---- time the plain arm
-    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(pmode == "adapt"),
-                          force_hybrid=int(pmode == "force"), hybrid_beam=pbudget, learned=0)
-    p_ms, p_stats = timed(vj, torch, ix, eps, pbudget, max(2, args.steps // 2), args.warmup, "plain_timed")
-    plain_qps = w.nq / (p_ms / 1e3)
+    # ---- time the plain arm (its setting re-applied)
+    psetup()
+    p_ms, p_stats, _ = timed(vj, torch, ix, eps, 0, max(2, args.steps // 2), args.warmup, "plain_timed")
+    plain_qps = ne / (p_ms / 1e3)
+    vj.vj_set_plan(ix, None, None)
 
-    learned = None
+    learned, m = None, None
     if not args.plain_only:
-        # ---- labels for the predictor on a seeded 10% training subset
-        rng = np.random.default_rng(w.seed + 99)
-        train = np.sort(rng.choice(w.nq, size=max(1, w.nq // 10), replace=False))
-        ladder = [0, 8, 32]
-        recs, steps_at, missed = {}, {}, {}
-        for b in ladder:
-            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=int(b > 0),
-                                  hybrid_beam=max(b, 1), learned=0)
-            r = vj.vj_join(ix, eps)
-            h, tot = per_query_hits(r, ex, w.nx)
-            recs[b] = np.where(tot > 0, h / np.maximum(tot, 1), 1.0)
-            missed[b] = (tot - h).astype(np.float64)
-            steps_at[b] = r.stats, r.steps.astype(np.float64)
-        st0, s0 = steps_at[0]
-        t_step = st0["ms_traverse"] / max(s0.sum(), 1)             # ms per distance evaluation (BFS join)
-        t_bf = ex.stats["ms_scan"] / w.nq                           # ms per query of the full scan
-        budget_lab = np.full(w.nq, ladder[-1], np.int32)
-        for b in reversed(ladder):
-            budget_lab = np.where(recs[b] >= 0.95, b, budget_lab)
-        # route labels: the routing a knapsack would choose on the training
-        # queries for pooled recall 0.955 -- every query whose BFS costs more
-        # than its scan row, then the others by missed pairs per unit of
-        # extra cost, until the missed pairs left are within 4.5 %
-        tot_all = np.diff(ex.offsets).astype(np.float64)
-        c_bfs = s0 * t_step
-        gain = np.where(c_bfs >= t_bf, np.inf, missed[0] / np.maximum(t_bf - c_bfs, 1e-12))
-        route_lab = np.zeros(w.nq, bool)
-
-        def knapsack(idx):
-            left, allowed = missed[0][idx].sum(), 0.045 * tot_all[idx].sum()
-            for qi in idx[np.argsort(-gain[idx], kind="stable")]:
-                if left <= allowed and not np.isinf(gain[qi]):
-                    break
-                route_lab[qi] = missed[0][qi] > 0 or np.isinf(gain[qi])
-                left -= missed[0][qi]
-
-        held = np.setdiff1d(np.arange(w.nq), train)
-        knapsack(train)
-        knapsack(held)
-        F = vj.vj_features(ix, eps)
-        mlp = vj.MLP(F.shape[1], 256, 256, seed=w.seed)
-        t_tr = time.perf_counter()
-        final_loss = mlp.train(F[train], np.log2(budget_lab[train] + 1.0), route_lab[train].astype(np.float32),
-                               epochs=30, batch=256, lr=1e-3, seed=w.seed)
-        train_s = time.perf_counter() - t_tr
-        pred = mlp.predict(F)
-        route_acc = float(((pred[held, 1] > 0) == route_lab[held]).mean())
-        # operating point: the fastest (route threshold, hybrid-queue cap) whose join reaches recall 0.95
-        op, sweep = None, []
-        grid = [(0, t) for t in (0.99, 0.97, 0.95, 0.9, 0.85, 0.8, 0.7, 0.6, 0.5, 0.4, 0.2)] + [(64, t) for t in (0.9, 0.6, 0.3)]
-        for cap, thr in grid:
-            vj.vj_attach_predictor(ix, mlp, thr, cap)
-            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
-                                  hybrid_beam=max(cap, 1), learned=1)
-            vj.vj_join(ix, eps)
-            r = vj.vj_join(ix, eps)
-            rec = recall_of(r, ex, w.nx)
-            sweep.append({"thr": thr, "beam_cap": cap, "recall": round(rec, 4), "ms": round(r.stats["ms_total"], 2),
-                          "routed": int((r.hybrid == 2).sum()), "ms_traverse": round(r.stats["ms_traverse"], 2),
-                          "ms_route": round(r.stats["ms_route"], 2),
-                          "ms_sws": [round(x, 2) for x in r.stats["ms_sws"]], "reruns": r.stats["sws_restarts"]})
-            if rec >= 0.95 and (op is None or r.stats["ms_total"] < op[3]):
-                op = (thr, rec, r, r.stats["ms_total"], cap)
-        if op is None:  # nothing reached 0.95: route everything that the predictor doubts least
-            op = (0.05, rec, r, r.stats["ms_total"], 64)
-        thr, lrec, lr_, _, lcap = op
-        vj.vj_attach_predictor(ix, mlp, thr, lcap)
-        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, force_hybrid=0,
-                              hybrid_beam=max(lcap, 1), learned=1)
-        l_ms, l_stats = timed(vj, torch, ix, eps, 0, args.steps, args.warmup, "learned_timed")
-        learned = {"thr": thr, "beam_cap": lcap, "sweep": sweep, "recall": lrec, "ms": l_ms, "stats": l_stats,
-                   "route_acc": route_acc,
-                   "routed_frac": float((lr_.hybrid == 2).mean()), "train_s": train_s, "final_loss": final_loss,
-                   "labels_route_frac": float(route_lab.mean()), "t_bf_ms": t_bf, "t_step_ms": t_step,
-                   "recall_per_query_mean": per_query_recall_mean(lr_, ex, w.nx)}
+        m, learned = learned_arm(vj, ix, eps, ex, w, log, caps=(0,) if w.d > 256 else (0, 64))
+        l_ms, l_stats, clk = timed(vj, torch, ix, eps, 0, args.steps, args.warmup, "learned_timed", clocks=True)
+        r = vj.vj_join(ix, eps)
+        learned.update({"ms": l_ms, "stats": l_stats, "clocks": clk, "recall": recall_of(r, ex, w.nx, (0, ne)),
+                        "recall_per_query_mean": per_query_recall_mean(r, ex, w.nx, (0, ne)),
+                        "routed_frac": float((r.hybrid[:ne] == 2).mean()),
+                        "no_expansion_frac": float((r.hybrid[:ne] == 3).mean())})
 
     # ---- headline arm and its rooflines
     if learned is not None:
-        step_ms, stats, rec = learned["ms"], learned["stats"], learned["recall"]
-        arm = (f"learned+BF16: MI+SWS with the learned prologue, route threshold {learned['thr']}, "
-               f"hybrid-queue cap {learned['beam_cap']}")
+        step_ms, stats, rec, clk = learned["ms"], learned["stats"], learned["recall"], learned["clocks"]
+        arm = (f"learned+BF16: MI+SWS with the predictor's plan (route threshold {learned['thr']}, hybrid-queue cap "
+               f"{learned['beam_cap']}), BF16 gathers")
         dtype = "bf16"
     else:
-        step_ms, stats, rec = p_ms, p_stats, prec
-        arm = f"plain FP32 MI+SWS, hybrid={pmode} beam {pbudget}"
+        psetup()
+        step_ms, stats, clk = timed(vj, torch, ix, eps, 0, args.steps, 1, "plain_clock", clocks=True)
+        rec = prec
+        arm = f"plain FP32 MI+SWS, {pname}"
         dtype = "f32"
-    value = world * w.nq / (step_ms / 1e3)
+    value = ne / (step_ms / 1e3)
     t_tr = statistics.mean(s["ms_traverse"] for s in stats)
     t_sc = statistics.mean(s["ms_scan"] for s in stats)
     trav = {"kernel": "k_join (traversal)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
             "achieved": statistics.mean(s["bytes_algorithmic"] for s in stats) / (t_tr / 1e3) / 1e9,
             "ms_per_launch": t_tr, "algorithmic_bytes_per_launch": statistics.mean(s["bytes_algorithmic"] for s in stats),
             "peak_kind": f"{peak_kind} hbm_gbs (burst)",
-            "traffic": _traffic("k_join", args.scale) if learned is not None and args.workload == "sift_like" else None}
+            "traffic": _traffic("k_join", f"{args.workload}@{args.scale}")}
     trav["frac"] = trav["achieved"] / hbm
     rooflines = [trav]
     if learned is not None and t_sc > 0:
-        nrouted = learned["routed_frac"] * w.nq
+        nrouted = learned["routed_frac"] * ne + float((r.hybrid[ne:] == 2).sum())
         flops = 2.0 * nrouted * w.nx * w.d
-        scan = {"kernel": "k_tc_scan (tcgen05 BF16 brute-force scan)", "bound": "tensor", "unit": "TFLOP/s",
-                "peak": bf16, "achieved": flops / (t_sc / 1e3) / 1e12, "ms_per_launch": t_sc,
+        scan = {"kernel": "k_tc_res / k_tc_wide (tcgen05 BF16 brute-force scan)", "bound": "tensor",
+                "unit": "TFLOP/s", "peak": bf16, "achieved": flops / (t_sc / 1e3) / 1e12, "ms_per_launch": t_sc,
                 "algorithmic_flops_per_launch": flops, "peak_kind": f"{peak_kind} bf16_tflops (burst)",
-                "traffic": _traffic("k_tc_scan_res", args.scale) if args.workload == "sift_like" else None}
+                "traffic": _traffic("k_tc_scan", f"{args.workload}@{args.scale}")}
         scan["frac"] = scan["achieved"] / bf16
         rooflines.append(scan)
     dominant = max(rooflines, key=lambda k: k["ms_per_launch"])
-
-    # clocks during one more timed run of the headline arm
-    with ClockSampler(torch.cuda.current_device()) as cs:
-        time.sleep(0.3)
-        timed(vj, torch, ix, eps, 0 if learned is not None else pbudget, args.steps, 1, "clock_run")
-        time.sleep(0.2)
+    n_all = w.nx + w.nq
+    kp = (w.d + 63) // 64 * 64
+    knn_flops = 2.0 * n_all * n_all * kp * (1.0 + 1.0 / 16)
+    exact_flops = 2.0 * w.nq * w.nx * w.d
 
     # ---- end to end through the public call with a host result
     e2e_ms, e2e_gpu = [], []
     rh = None
     for _ in range(max(2, args.warmup)):  # untimed: page-locked result blocks enter the cache
-        rh = vj.vj_join(ix, eps, 0 if learned is not None else pbudget)  # (two results alive at a time)
+        rh = vj.vj_join(ix, eps, 0)
     for _ in range(max(3, args.steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rh = vj.vj_join(ix, eps, 0 if learned is not None else pbudget)
+        rh = vj.vj_join(ix, eps, 0)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_gpu.append(rh.stats["ms_total"])
     d2h = int(rh.offsets.nbytes + rh.ids.nbytes + rh.dists.nbytes + rh.steps.nbytes + rh.cache.nbytes +
               rh.hybrid.nbytes)
-    # replicas: every rank joins the same workload; the job's time is the slowest rank's
-    e2e_v = world * w.nq / (slowest_rank_ms(statistics.median(e2e_ms), dist, "cuda") / 1e3)
+    e2e_v = world * ne / (slowest_rank_ms(statistics.median(e2e_ms), dist, "cuda") / 1e3)
     if dist:
         step_ms = slowest_rank_ms(step_ms, dist, "cuda")
-        value = world * w.nq / (step_ms / 1e3)
-    rec_q = learned["recall_per_query_mean"] if learned is not None else per_query_recall_mean(pr, ex, w.nx)
+        value = world * ne / (step_ms / 1e3)
+    rec_q = learned["recall_per_query_mean"] if learned is not None else per_query_recall_mean(pr, ex, w.nx, (0, ne))
+    pairs = int(ex.offsets[ne])
     cfg = {"workload": wl_desc, "arm": arm, "recall": rec, "recall_per_query_mean": rec_q, "eps": eps,
-           "degree": info["degree"],
-           "knn_k": info["knn_k"], "mst_depth": info["max_depth"], "build_s": build_s,
-           "pairs": int(stats[-1]["nnz"]), "pairs_per_s": world * stats[-1]["nnz"] / (step_ms / 1e3),
-           "l2": "inputs larger than L2 (vectors %.0f MB)" % ((w.X.nbytes + w.Q.nbytes) / 1e6),
-           "plain_fp32": {"qps": plain_qps, "ms_per_step": p_ms, "recall": prec, "hybrid": pmode,
-                          "hybrid_beam": pbudget},
-           "exact_join_ms": ex.stats["ms_total"], "exact_scan_ms": ex.stats["ms_scan"], "seed": w.seed,
+           "degree": info["degree"], "knn_k": info["knn_k"], "mst_depth": info["max_depth"],
+           "queries_evaluated": ne, "queries_held_out": w.nq - ne,
+           "build": {"wall_s": round(build_s, 2), "ms_device": binfo["ms_build"], "ms_knn": binfo["ms_knn"],
+                     "knn_tensor_cores": binfo["knn_tensor_cores"], "knn_uncertified": binfo["knn_uncertified"],
+                     "knn_tflops": knn_flops / (binfo["ms_knn"] / 1e3) / 1e12,
+                     "knn_frac_of_bf16_peak": knn_flops / (binfo["ms_knn"] / 1e3) / 1e12 / bf16,
+                     "knn_flops": knn_flops},
+           "generate_s": round(gen_s, 2),
+           "pairs_per_s": world * pairs / (step_ms / 1e3),
+           "l2": "inputs larger than L2 (FP32 vectors %.1f GB, BF16 copy %.1f GB)" % (
+               (w.nx + w.nq) * w.d * 4 / 1e9, (w.nx + w.nq) * kp * 2 / 1e9),
+           "plain_fp32": {"qps": plain_qps, "ms_per_step": p_ms, "recall": prec, "setting": pname,
+                          "sweep": psweep},
+           "exact_join": {"ms": ex.stats["ms_total"], "ms_scan": ex.stats["ms_scan"],
+                          "tflops": exact_flops / (ex.stats["ms_scan"] / 1e3) / 1e12},
+           "seed": w.seed,
            "e2e_detail": {"wall_ms": [round(x, 3) for x in e2e_ms], "join_stats_ms": [round(x, 3) for x in e2e_gpu],
                           "timed_step_join_stats_ms": round(statistics.mean(s["ms_total"] for s in stats), 3)}}
     if learned is not None:
-        cfg["learned"] = {k: learned[k] for k in ("thr", "beam_cap", "sweep", "recall", "route_acc", "routed_frac",
-                                                   "train_s", "final_loss", "labels_route_frac", "t_bf_ms", "t_step_ms")}
+        cfg["learned"] = {k: learned[k] for k in ("thr", "beam_cap", "sweep", "recall", "routed_frac",
+                                                   "no_expansion_frac", "train_s", "train_report")}
         cfg["learned"]["ms_prologue"] = statistics.mean(s["ms_prologue"] for s in stats)
         cfg["learned_vs_plain"] = value / plain_qps
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -657,18 +757,23 @@ def main():
             "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg, "roofline": dominant,
             "rooflines": rooflines,
             "e2e": {"value": e2e_v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
-            "clocks": cs.summary(),
+            "clocks": clk,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
     if rank == 0 and not args.no_cpu_baseline:
-        # a bounded sample: whole MST subtrees of about 15,000 queries, some seconds of one core
-        n, dt = run_cpu_oracle(w, vj, ix, eps, 15000, pmode, pbudget)
+        # a bounded sample: whole MST subtrees of about 10,000 evaluated queries
+        Xh, Qh = host(w.X), host(w.Q)
+        mode = "adapt" if pname.startswith("rule") else "force"
+        pbeam = int(pname.split()[-1]) if "queue" in pname else 256
+        n, dt = run_cpu_oracle(w, vj, ix, eps, 10000, mode, pbeam, Xh, Qh)
         line["cpu_baseline"] = {"value": n / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{n} queries (whole MST subtrees) of the same workload on the GPU-built "
-                                          f"graph, oracle MI+SWS join (hybrid={pmode}, beam {pbudget}), FP64, "
-                                          "single thread"}
+                                "sample": f"{n} evaluated queries (whole MST subtrees) of the same workload on the "
+                                          f"GPU-built graph, oracle MI+SWS join ({pname}), FP64, single thread"}
+        del Xh, Qh
     if rank == 0:
         print(json.dumps(line), flush=True)
     vj.vj_attach_predictor(ix, None, 0.5, 64)
+    if m is not None:
+        m.free()
     ix.free()
     if dist:
         dist.barrier()

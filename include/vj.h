@@ -69,10 +69,15 @@ typedef struct {
                              tensor cores, FP32 on the SIMT units; candidates are re-ranked with exact
                              keys and certified either way, so the lists are the same.  FP8 is not
                              implemented (VJ_ERR_ARG). */
-    int learned;          /* reserved, must be 0 */
+    int learned;          /* joins: 1 = plan every query with the attached predictor
+                             (vj_attach_predictor) in place of Alg. 6's rule; default 0 */
     int route_bruteforce; /* reserved, must be 0 */
     int input_on_device;  /* 1: X and Q passed to vj_build are device pointers */
     uint64_t seed;        /* reserved for randomised steps; recorded only */
+    int gather;           /* joins: VJ_PREC_* of the traversal's vector gathers.  BF16 reads the BF16
+                             copy of the vectors (half the bytes) when every coordinate is exactly a
+                             BF16 value, so every key equals the FP32 one; otherwise, and by default
+                             (FP32), the FP32 rows.  A join-time field. */
 } vj_params;
 
 /* Per-call counters and device timings of a join. */
@@ -103,7 +108,9 @@ typedef struct {
 /* CSR result of a join.  ids are data ids (0..nx-1), ascending within each
  * query row; dists are the pair distances.  steps/cache/hybrid are per-query
  * (query index order): distance evaluations, the soft cache C[q] of Alg. 8
- * (closest visited data node, -1 if none) and the CheckHybrid outcome.
+ * (closest visited data node, -1 if none) and the expansion the query ran:
+ * 0 BFS, 1 hybrid (the CheckHybrid outcome), 2 routed to the brute-force
+ * scan, 3 none (a plan of -1).
  * When on_device is 1 every array is a device pointer; otherwise every array
  * is page-locked host memory from the library's block cache.  Either way the
  * result is released with vj_result_free. */
@@ -141,7 +148,8 @@ vj_status vj_build(const float *X, int64_t nx, const float *Q, int64_t nq, int d
 vj_status vj_set_stream(vj_index *ix, void *stream);
 
 /* Replace the join-time fields (greedy_beam, conv_threshold, hybrid_beam,
- * work_sharing, adapt_hybrid, force_hybrid) used by later joins. */
+ * work_sharing, adapt_hybrid, force_hybrid, learned, gather) used by later
+ * joins. */
 vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
 
 /* Per-query plan used by later joins in place of Alg. 6's CheckHybrid rule
@@ -152,14 +160,17 @@ vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
  *     exact nested-loop-join row, computed by the tensor-core brute-force scan
  *     with exact re-check; hybrid flag 2 in the result.
  *   beam[q] > 0: hybrid expansion with hybrid_beam_size = beam[q];
- *   beam[q] == 0: the BFS expansion.
- * Errors: VJ_ERR_ARG (beam outside [0, 2^20]). */
+ *   beam[q] == 0: the BFS expansion;
+ *   beam[q] == -1: no expansion phase: the row is the probe's in-range data
+ *     points (hybrid flag 3 in the result).  An expansion budget of zero,
+ *     not in the paper (a knob for the learned predictor).
+ * Errors: VJ_ERR_ARG (beam outside [-1, 2^20]). */
 vj_status vj_set_plan(vj_index *ix, const uint8_t *route, const int32_t *beam);
 
 /* ---- Learned route / budget predictor (not in the paper, which decides with
  * the d1/d2 > 1.5 rule of Sec. 4.4 only; that rule stays the default).
  * A 3-layer MLP din -> h1 -> h2 -> 2 (ReLU): output 0 regresses
- * log2(budget + 1), output 1 is the route logit.  Loss = mean squared error on
+ * log2(budget + 2), output 1 is the route logit.  Loss = mean squared error on
  * output 0 + binary cross-entropy with logits on output 1, averaged over rows.
  * Parameters: one flat FP32 array W1[h1][din] b1 W2[h2][h1] b2 W3[2][h2] b3.
  * Inputs are standardised per feature with the training rows' mean / std. */
@@ -191,9 +202,11 @@ vj_status vj_features(vj_index *ix, float eps, float *out);
 /* Use predictor m (din = 7 + d; NULL detaches) for joins with
  * params.learned = 1: a prologue computes the features, runs m and routes
  * a query to the brute-force scan when sigmoid(output 1) > route_threshold,
- * else gives it the hybrid queue size 2^output0 - 1 (0 = BFS below 4,
- * capped at beam_cap).  The index keeps the pointer; m must outlive it or
- * be detached. */
+ * else reads the budget b = 2^output0 - 2: b < -1/2 no expansion phase (plan
+ * -1), b < 4 the BFS expansion, else the hybrid queue size b capped at
+ * beam_cap (a cap below 4: BFS).  Output 0 therefore regresses
+ * log2(budget + 2) with budget -1 (none), 0 (BFS) or a queue size.  The index
+ * keeps the pointer; m must outlive it or be detached. */
 vj_status vj_attach_predictor(vj_index *ix, vj_mlp *m, float route_threshold, int beam_cap);
 
 /* Outputs [nq][2] (host) of the attached predictor on the features at eps,
@@ -203,6 +216,67 @@ vj_status vj_attach_predictor(vj_index *ix, vj_mlp *m, float route_threshold, in
  * counterpart (the paper has only the d1/d2 rule, Sec. 4.4).  VJ_ERR_STATE
  * when no predictor is attached. */
 vj_status vj_predictor_outputs(vj_index *ix, float eps, float *out);
+
+/* ---- Training the predictor inside the library (no paper counterpart: the
+ * paper's route is the d1/d2 rule of Sec. 4.4).  The training queries are
+ * rows of the index's own query set, which the caller keeps apart from the
+ * queries it evaluates on (a held-out set built into the same merged index).
+ * Labels, per training query q at threshold eps:
+ *   - the exact row of q (tensor-core scan with the exact re-check, Sec. 3.2);
+ *   - for each ladder budget in order (-1 no expansion, 0 BFS, > 0 hybrid
+ *     queue size) one join of every query planned with that budget, giving
+ *     q's row recall against its exact row and q's cost (its distance
+ *     evaluations); a join that fails (a hybrid search outgrowing its visited
+ *     set) ends the ladder, the first must succeed;
+ *   - budget = the first ladder budget whose recall reaches query_recall,
+ *     else the last budget that ran;
+ *   - route = 1 when q's cost at its budget is at least scan_row_cost; then,
+ *     while the training queries' pooled recall (pairs found / exact pairs)
+ *     is below pooled_recall, the query with the most missed pairs per unit of
+ *     extra cost, missed / (scan_row_cost - cost), ties by smaller query
+ *     index, is routed too.
+ * scan_row_cost is the cost of one brute-force row in distance evaluations;
+ * <= 0 measures it (scan time per training query over the BFS join's time
+ * per distance evaluation).  The index's plan is cleared and its join
+ * parameters restored afterwards. */
+typedef struct {
+    int n_ladder;        /* 1..8 entries of ladder used, in order of increasing cost */
+    int ladder[8];       /* default -1, 0, 8 */
+    float query_recall;  /* default 0.95 */
+    float pooled_recall; /* default 0.955 */
+    float scan_row_cost; /* default 0 (measured) */
+    int h1, h2;          /* hidden widths, default 256, 256 */
+    int epochs, batch;   /* default 30, 256 */
+    float lr;            /* default 1e-3 */
+    uint64_t seed;       /* weight init and batch shuffle, default 7 */
+} vj_train_params;
+
+typedef struct {
+    int64_t n;              /* training queries */
+    int64_t routed;         /* route labels set */
+    int64_t per_budget[8];  /* budget labels per ladder entry */
+    int ladder_run;         /* ladder entries whose join completed */
+    double scan_row_cost;   /* the cost the route labels used */
+    double final_loss;      /* vj_train_predictor: last epoch's mean loss */
+    double ms_labels;       /* host wall time of the labels (joins included) */
+    double ms_train;        /* host wall time of features + training */
+} vj_train_report;
+
+void vj_default_train_params(vj_train_params *tp);
+
+/* The labels above for the n training queries rows[] (query indices, host):
+ * budget[n] (int32) and route[n] (uint8, 0/1), host buffers.  rep may be NULL.
+ * Errors: VJ_ERR_ARG (bad rows or parameters), and those of vj_join. */
+vj_status vj_predictor_labels(vj_index *ix, float eps, const int32_t *rows, int64_t n,
+                              const vj_train_params *tp, int32_t *budget, uint8_t *route,
+                              vj_train_report *rep);
+
+/* Labels as above, features of the training queries (vj_features), then a
+ * new predictor din = 7 + d -> h1 -> h2 -> 2 trained with vj_mlp_train on
+ * targets log2(budget + 2) and route.  *out receives it (free with
+ * vj_mlp_free; attach with vj_attach_predictor).  rep may be NULL. */
+vj_status vj_train_predictor(vj_index *ix, float eps, const int32_t *rows, int64_t n,
+                             const vj_train_params *tp, vj_mlp **out, vj_train_report *rep);
 
 /* Approximate join (Alg. 1 on the merged index) at threshold eps > 0.
  * budget > 0 overrides hybrid_beam for this call.  The result lives in host
@@ -267,6 +341,15 @@ vj_status vj_join_exact(vj_index *ix, float eps, vj_result **out);
 vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int64_t nq, int d,
                                 vj_metric metric, float eps, int64_t *offsets, int32_t *ids,
                                 float *dists, int64_t cap, int64_t *nnz, void *stream);
+
+/* Bounded dependency wait of soft work sharing (for tests of its failure
+ * path; no paper counterpart).  max_polls > 0 limits the polls of a query's
+ * wait for its MST parent's cache before the join gives up with
+ * VJ_ERR_TIMEOUT (0 restores the default of 2^24 polls with back-off, about
+ * seconds).  hold_q >= 0 makes that query never publish its cache, so its
+ * children's waits run out (-1: none).  The index stays usable after a
+ * timeout. */
+vj_status vj_set_wait_test(vj_index *ix, long long max_polls, int64_t hold_q);
 
 /* Copy the built graph to host buffers (any may be NULL):
  *   adj [(nx+nq) * R] int32 (-1 padded), entry (1 value),

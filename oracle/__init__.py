@@ -216,7 +216,8 @@ def join(X, Q, adj, entry: int, eps: float, *, metric: int = L2, work_sharing: i
     route/beam (optional, per query) replace Alg. 6's rule with a plan:
     route[q] = 1 sends q to the brute-force scan after its greedy phase
     (hybrid flag 2), beam[q] > 0 runs the hybrid expansion with that queue
-    size, beam[q] = 0 the BFS expansion.
+    size, beam[q] = 0 the BFS expansion, beam[q] = -1 no expansion phase
+    (an expansion budget of zero: the row is I after the greedy phase, flag 3).
 
     order/parent default to the MST of `mst()` when work sharing is hard/soft,
     else to index order.

@@ -554,7 +554,10 @@ typedef struct {
      * is its exact NLJ row (brute-force scan) and no expansion runs; the soft
      * cache is taken over the nodes the greedy phase visited.  beam[qi]: the
      * query runs the hybrid expansion with hybrid_beam_size = beam[qi] when
-     * beam[qi] > 0, the plain BFS expansion when beam[qi] == 0.  NULL: unused. */
+     * beam[qi] > 0, the plain BFS expansion when beam[qi] == 0, and skips the
+     * expansion phase of Alg. 1 when beam[qi] < 0 (an expansion budget of
+     * zero: the result is I after the greedy phase; reported as hybrid flag
+     * 3).  NULL: unused. */
     const uint8_t *route;
     const int32_t *beam;
     /* 1: separate-index execution (cfg.merged = false, Sec. 3.2 INLJ and its
@@ -736,6 +739,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
         int hyb;
         int beam = cfg->hybrid_beam_size;
         const int routed = cfg->route && cfg->route[qi];
+        const int no_expansion = cfg->beam && cfg->beam[qi] < 0 && !routed;
         if (cfg->beam) {
             beam = cfg->beam[qi];
             hyb = beam > 0;
@@ -747,7 +751,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
 
         /* --- Alg. 7 ExpansionPhase (merged index: min-priority queue by dist) */
         npq = 0;
-        for (int64_t j = 0; j < nI && !routed; j++) {
+        for (int64_t j = 0; j < nI && !routed && !no_expansion; j++) {
             cand_t c = {dv[I[j]], I[j]};
             PQ_PUSH(c);
         }
@@ -827,6 +831,7 @@ int64_t vjo_join(const float *X, int64_t nx, const float *Q, int64_t nq, int d, 
             }
             hyb = 2;
         }
+        if (no_expansion) hyb = 3;
 
         /* R <- R U I (sorted by data id for the CSR) */
         qsort(I, (size_t)nI, sizeof(int32_t), cmp_i32);

@@ -115,7 +115,8 @@ __global__ void k_features(const float* __restrict__ vec, int dp, int d, int64_t
 }
 
 // plan from predictor outputs: route when the route logit exceeds lthr;
-// otherwise the budget 2^y0 - 1 rounded to the nearest ladder value
+// otherwise the budget b = 2^y0 - 2: below -1/2 no expansion (plan -1), below
+// 4 the BFS expansion (plan 0), else the hybrid queue size b (capped)
 __global__ void k_plan(const float* __restrict__ y, int64_t nq, float lthr, int beam_cap,
                        uint8_t* __restrict__ route, int32_t* __restrict__ beam, int32_t* __restrict__ routed,
                        unsigned long long* __restrict__ nrouted) {
@@ -123,8 +124,9 @@ __global__ void k_plan(const float* __restrict__ y, int64_t nq, float lthr, int 
     if (qi >= nq) return;
     const bool r = y[2 * qi + 1] > lthr;
     route[qi] = r ? 1 : 0;
-    float b = exp2f(fminf(fmaxf(y[2 * qi], 0.f), 20.f)) - 1.f;
-    int bi = b < 4.f ? 0 : (int)fminf(b + 0.5f, (float)beam_cap);
+    float b = exp2f(fminf(fmaxf(y[2 * qi], 0.f), 20.f)) - 2.f;
+    int bi = b < -0.5f ? -1 : (b < 4.f ? 0 : (int)fminf(b + 0.5f, (float)beam_cap));
+    if (bi > 0 && beam_cap < 4) bi = 0;  // a cap below 4 allows no hybrid search
     beam[qi] = bi;
     if (r) routed[atomicAdd(nrouted, 1ull)] = (int32_t)qi;
 }

@@ -102,6 +102,9 @@ enum {
 
 struct JoinParams {
     const float* vec;
+    const __nv_bfloat16* xb;  // BF16 copy of the vectors for the candidate gathers (nullptr: FP32 rows)
+    int kpb;                  // its row stride in BF16 values
+    int hold_q;               // test knob: this query never publishes in pass 3 (-1: none)
     const float* invn;
     const int32_t* adj;
     const float* elen;
@@ -481,13 +484,14 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (P.hyb[qi] == 1) return 2;
             if (lane == 0) S->cand[0] = sc;
             __syncwarp();
-            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane);
+            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane, P.xb, P.kpb);
             __syncwarp();
             const float k = S->ckey[0];
             __syncwarp();
             // sc would have been the greedy front: no probe
             if ((flags & QF_PROBED) && k <= 0.f) return 2;
-            // sc in pass 1's V?  {entry, q} U N(q) (probed) U N(results) (BFS);
+            // sc in pass 1's V?  {entry, q} U N(q) (probed) U N(results) (BFS;
+            // a query without expansion, flag 3, never read N(results));
             // one result per lane, its whole adjacency row loaded at once
             bool seen = false;
             if (flags & QF_PROBED) seen = lane < R && __ldg(P.adj + qn * R + lane) == sc;
@@ -588,7 +592,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                     P.hyb[qi] = P.hyb2[qi];
                     P.count[qi] = P.count2[qi];
                     P.seg[qi] = P.seg2[qi];
-                    st_release(P.done + qi, 1);
+                    if (qi != P.hold_q) st_release(P.done + qi, 1);
                 }
                 __syncwarp();
                 return false;
@@ -600,7 +604,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                         P.steps[qi] += 1;
                         c_dist += 1;
                     }
-                    st_release(P.done + qi, 1);
+                    if (qi != P.hold_q) st_release(P.done + qi, 1);
                 }
                 __syncwarp();
                 return false;
@@ -652,7 +656,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         if (snew) S->cand[__popc(sm & ((1u << lane) - 1u))] = sid;
         __syncwarp();
         int ns = __popc(sm);
-        group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane);
+        group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane, P.xb, P.kpb);
         __syncwarp();
         s.nvis += ns;
         float skey = FLT_MAX;
@@ -701,7 +705,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 int mypos = __popc(nm & ((1u << lane) - 1u));
                 if (nw) S->cand[mypos] = v;
                 __syncwarp();
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane);
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
                 __syncwarp();
                 s.nvis += nc;
                 int cv = lane < nc ? S->cand[lane] : -1;
@@ -728,13 +732,14 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         // otherwise), or the per-query plan when one is set: a routed query
         // stops after its greedy phase (its row comes from the brute-force
         // scan); a planned beam > 0 selects the hybrid expansion with that
-        // queue size, 0 the BFS expansion
+        // queue size, 0 the BFS expansion, and a negative beam no expansion
+        // at all (the result is the probe's in-range points; flag 3)
         const bool routed = P.route != nullptr && P.route[qi] != 0;
         int hbq = P.hbeam;
         int hyb = P.force;
         if (P.qbeam) {
             hbq = P.qbeam[qi];
-            hyb = hbq > 0;
+            hyb = hbq > 0 ? 1 : (hbq < 0 ? 3 : 0);
         } else if (P.adapt && !failed && !routed) {
             if (!probe) {
                 // no probe ran (a seed was the greedy front); the rule still
@@ -747,8 +752,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 const int pos = __popc(dm0 & ((1u << lane) - 1u));
                 if (dv) S->cand[pos] = v;
                 __syncwarp();
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, __popc(dm0), S->ckey,
-                                      lane);
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, __popc(dm0), S->ckey, lane, P.xb, P.kpb);
                 __syncwarp();
                 nkey_l = dv ? S->ckey[pos] : FLT_MAX;
                 __syncwarp();
@@ -844,7 +848,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         }
 
         // ---- Alg. 7 ExpansionPhase
-        if (routed) {
+        if (routed || hyb == 3) {
         } else if (!failed && !hyb) {
             int fp = 0;
             while (fp < s.nres) {
@@ -874,7 +878,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 expansions += nb;
                 fp += nb;
                 if (nc == 0) continue;
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane);
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
                 __syncwarp();
                 s.nvis += nc;
                 for (int base = 0; base < nc; base += 32) {
@@ -939,7 +943,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
                 __syncwarp();
                 if (nc == 0) continue;
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane);
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
                 __syncwarp();
                 s.nvis += nc;
                 // one candidate per lane, in adjacency order (nc <= 32)
@@ -1045,7 +1049,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 P.cache1[qi] = best;
             }
             // publish: cache[qi] is visible to whoever sees the flag
-            if (P.mode == 2 && !failed) st_release(P.done + qi, 1);
+            if (P.mode == 2 && !failed) if (qi != P.hold_q) st_release(P.done + qi, 1);
         }
         vis_release(s, W, lane);
         if (failed) {
@@ -1264,6 +1268,7 @@ struct JoinRun {
     unsigned long long hc[16];
     int64_t launches = 0;
     float t_trav = 0.f, t_sws[3] = {0.f, 0.f, 0.f};
+    int gather_bytes = 4;  // bytes per coordinate the traversal gathers (4 FP32, 2 BF16)
     ~JoinRun() {
         // the plan the learned prologue set lives for this join only
         if (learned && ix) {
@@ -1402,7 +1407,20 @@ void join_setup(JoinRun& r) {
     P.grcap = grcap;
     P.oqcap = oqcap;
     P.ctr = ix->ctr.p;
-    P.spin_limit = 1ll << 24;  // ~seconds with back-off; then VJ_DERR_WAIT_TIMEOUT
+    P.spin_limit = ix->wait_polls > 0 ? ix->wait_polls : (1ll << 24);  // ~seconds with back-off; then VJ_DERR_WAIT_TIMEOUT
+    P.hold_q = ix->hold_q;
+    // BF16 gathers when asked for and exact: every coordinate is a BF16 value
+    // and the BF16 copy holds the raw rows (L2, or cosine rows kept raw)
+    P.xb = nullptr;
+    P.kpb = 0;
+    if (ix->p.gather == VJ_PREC_BF16) {
+        vj_ensure_bf16(ix);
+        if (ix->bf16_lossless && (ix->metric == VJ_L2 || ix->cos_raw)) {
+            P.xb = ix->xbf.p;
+            P.kpb = (ix->d + 63) / 64 * 64;
+        }
+    }
+    r.gather_bytes = P.xb ? 2 : 4;
     r.soft = ix->p.work_sharing == VJ_WS_SOFT;
 }
 
@@ -1643,7 +1661,7 @@ void join_finish(JoinRun& r, vj_stats* st, int64_t* nnz_out) {
     st->ms_total = r.ms_pro + r.t_trav + t_csr;
     ix->have_costs = true;  // this join's visited counts order the next one
     // algorithmic bytes: one vector per distance, one adjacency row per row read
-    st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * 4 + (int64_t)hc[C_ADJ] * ix->R * 4;
+    st->bytes_algorithmic = (int64_t)hc[C_DIST] * ix->d * r.gather_bytes + (int64_t)hc[C_ADJ] * ix->R * 4;
     st->kernel_launches = r.launches + (nq > 0 ? 4 : 3);  // traversal attempts + 3-kernel scan + row sort
     st->ms_scan = ms_scan;
     st->scan_candidates = scand;

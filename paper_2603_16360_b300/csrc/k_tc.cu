@@ -1079,6 +1079,8 @@ static void ensure_data_bf16(vj_index* ix) {
     }
 }
 
+void vj_ensure_bf16(vj_index* ix) { ensure_data_bf16(ix); }
+
 // Work split of a sweep of nrt row tiles over nct tiles: the tiles per unit
 // that minimise the busiest SM's load (its units' tiles plus `refill` tiles of
 // pipeline restart per unit)

@@ -468,6 +468,8 @@ __global__ void __launch_bounds__(KC_WPB * 32)
         S.key[e] = FLT_MAX;
     }
     __syncwarp();
+    // tolerance of the FP32 direct-difference keys (relative for L2)
+    const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
     float out_lo = FLT_MAX;  // approximate-key prefilter: lower bound on every dropped candidate
     if (cw && nvalid > K) {
         bitonic_pairs(S.key, S.id, P2, lane);
@@ -475,7 +477,12 @@ __global__ void __launch_bounds__(KC_WPB * 32)
         const double beta = metric == 0
                                 ? (double)cb * sqrt((double)rn2) * mx + ((double)c3 + 4.0 * VJ_F32_U) * ((double)rn2 + mx * mx)
                                 : (double)cb + 4.0 * VJ_F32_U;
-        const double lim = (double)S.key[K - 1] + 2.0 * beta;
+        // the true K-th key is at most k~_K + beta, and the certificate below
+        // needs its FP32 key with margin (at most (k~_K + beta)(1 + tol) + tol
+        // before rounding slack) under every dropped candidate's lower bound
+        // k~ - beta: cut at k~_K + 3 beta plus twice the margin
+        const double kk = (double)S.key[K - 1] + beta;
+        const double lim = metric == 0 ? kk * (1.0 + 2.0 * (double)tol) + 2.0 * beta : kk + 2.0 * beta + 2.0 * (double)tol;
         int ne = 0;
         for (int base = 0; base < nvalid; base += 32) {
             const bool in = base + lane < nvalid && (double)S.key[base + lane] <= lim;
@@ -498,7 +505,6 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     __syncwarp();
     bitonic_pairs(S.key, S.id, P2, lane);
     // near-tie runs among the first K + 1: FP64 re-rank (runs stay below 128)
-    const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
     const int lim = min(K + 1, nvalid);
     bool ok = nvalid >= K;
     int i0 = 0;

@@ -46,6 +46,7 @@ extern "C" void vj_default_params(vj_params* p) {
     p->route_bruteforce = 0;
     p->input_on_device = 0;
     p->seed = 0;
+    p->gather = VJ_PREC_FP32;
 }
 
 template <class F>
@@ -71,6 +72,7 @@ static void check_join_params(const vj_params& p) {
     VJ_REQUIRE(p.greedy_beam >= 1, VJ_ERR_ARG, "greedy_beam must be >= 1");
     VJ_REQUIRE(p.learned == 0 || p.learned == 1, VJ_ERR_ARG, "learned must be 0 or 1");
     VJ_REQUIRE(p.route_bruteforce == 0, VJ_ERR_ARG, "route_bruteforce is reserved and must be 0");
+    VJ_REQUIRE(p.gather == VJ_PREC_FP32 || p.gather == VJ_PREC_BF16, VJ_ERR_ARG, "gather must be FP32 or BF16");
 }
 
 static std::atomic<int64_t> g_live_indexes{0};
@@ -230,6 +232,17 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
         ix->p.adapt_hybrid = p->adapt_hybrid;
         ix->p.force_hybrid = p->force_hybrid;
         ix->p.learned = p->learned;
+        ix->p.gather = p->gather;
+    });
+}
+
+extern "C" vj_status vj_set_wait_test(vj_index* ix, long long max_polls, int64_t hold_q) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        VJ_REQUIRE(max_polls >= 0, VJ_ERR_ARG, "max_polls must be >= 0");
+        VJ_REQUIRE(hold_q >= -1 && hold_q < ix->nq, VJ_ERR_ARG, "hold_q out of range");
+        ix->wait_polls = max_polls;
+        ix->hold_q = (int)hold_q;
     });
 }
 
@@ -258,7 +271,7 @@ extern "C" vj_status vj_set_plan(vj_index* ix, const uint8_t* route, const int32
         if (beam) {
             int mx = 0;
             for (int64_t q = 0; q < nq; q++) {
-                VJ_REQUIRE(beam[q] >= 0 && beam[q] <= (1 << 20), VJ_ERR_ARG, "beam[%lld] out of range",
+                VJ_REQUIRE(beam[q] >= -1 && beam[q] <= (1 << 20), VJ_ERR_ARG, "beam[%lld] out of range",
                            (long long)q);
                 mx = std::max(mx, (int)beam[q]);
             }

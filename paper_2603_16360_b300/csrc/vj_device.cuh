@@ -10,6 +10,7 @@
 // group are in flight at once (their loads are issued before any arithmetic),
 // which keeps U*NPL 16-byte gathers outstanding per lane.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +29,27 @@ __device__ __forceinline__ void load_slots(const float* __restrict__ vec, int64_
     for (int k = 0; k < NPL; k++) {
         int idx = g + k * G;
         r[k] = (idx < dp4) ? ldv(row + idx) : f4zero();
+    }
+}
+
+// The same slots from the BF16 copy of the vectors (rows of kpb BF16 values,
+// zero padded): slot idx holds BF16 values 4 idx .. 4 idx + 3, one 8-byte
+// load, converted exactly to FP32.  When every coordinate is a BF16 value the
+// slots, and so every key, equal those of the FP32 rows at half the bytes.
+template <int G, int NPL>
+__device__ __forceinline__ void load_slots_bf16(const __nv_bfloat16* __restrict__ xb, int64_t node, int kpb,
+                                                int dp4, int g, float4 (&r)[NPL]) {
+    const uint2* row = reinterpret_cast<const uint2*>(xb + node * (int64_t)kpb);
+#pragma unroll
+    for (int k = 0; k < NPL; k++) {
+        int idx = g + k * G;
+        if (idx < dp4) {
+            const uint2 v = __ldg(row + idx);
+            r[k] = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
+                               __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+        } else {
+            r[k] = f4zero();
+        }
     }
 }
 
@@ -64,11 +86,13 @@ __device__ __forceinline__ float group_sum(float a) {
 }
 
 // Distance keys of q to cand[0..nc) written to key[0..nc) (shared memory).
-// L2: squared distance; cosine: 1 - <x,q> * invx * invq.
+// L2: squared distance; cosine: 1 - <x,q> * invx * invq.  With xb, the
+// candidates' vectors are read from the BF16 copy (see load_slots_bf16).
 template <int G, int NPL, int U>
 __device__ __forceinline__ void group_keys(const float* __restrict__ vec, const float* __restrict__ invn,
                                            int dp4, int metric, const float4 (&q)[NPL], float invq,
-                                           const int32_t* cand, int nc, float* key, int lane) {
+                                           const int32_t* cand, int nc, float* key, int lane,
+                                           const __nv_bfloat16* __restrict__ xb = nullptr, int kpb = 0) {
     constexpr int NG = 32 / G;
     const int grp = lane / G, g = lane & (G - 1);
     for (int base = 0; base < nc; base += NG * U) {
@@ -79,7 +103,8 @@ __device__ __forceinline__ void group_keys(const float* __restrict__ vec, const 
             int ci = base + u * NG + grp;
             node[u] = ci < nc ? cand[ci] : -1;
             if (node[u] >= 0) {
-                load_slots<G, NPL>(vec, node[u], dp4, g, x[u]);
+                if (xb) load_slots_bf16<G, NPL>(xb, node[u], kpb, dp4, g, x[u]);
+                else load_slots<G, NPL>(vec, node[u], dp4, g, x[u]);
             } else {
 #pragma unroll
                 for (int k = 0; k < NPL; k++) x[u][k] = f4zero();

@@ -136,6 +136,8 @@ struct vj_index {
     bool bf16_lossless = false;  // every coordinate is exactly a BF16 value
     bool cos_raw = false;      // cosine, streamed tiles: xbf holds the raw (not unit) rows, scaled in the epilogue
     DBuf<float> wcs, wcb;      // [n] streamed tiles: per-column scale and bias of the accumulator
+    long long wait_polls = 0;  // dependency-wait limit of the traversal (0: the default)
+    int hold_q = -1;           // test knob: a query that never publishes its cache (-1: none)
     double maxnorm = 0.0;      // largest vector norm (FP64)
     double last_scan_ms = 0.0; // device time of the last tensor-core scan
     int64_t last_scan_cand = 0;
@@ -210,9 +212,13 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
 // prefilter of the re-rank
 bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr,
                           DBuf<float>* cw = nullptr);
+// BF16 copy of every node and the tiles' bound constants (built once)
+void vj_ensure_bf16(vj_index* ix);
 int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, float eps, DBuf<int32_t>& cq,
                               DBuf<int32_t>& cx, double* ms_out, DBuf<float>* ck = nullptr);
 
+// predictor features of every query at eps, [nq][VJ_NFEAT + d] in device memory
+void vj_compute_features(vj_index* ix, float eps, float* feat_dev);
 // learned prologue: features -> predictor -> per-query plan; returns #routed
 int64_t vj_learned_prologue(vj_index* ix, float eps);
 

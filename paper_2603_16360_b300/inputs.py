@@ -57,6 +57,7 @@ class Workload:
     knn_k: int             # kNN candidates per node for the graph build
     target_matches: float  # mean matches per query used to set eps
     seed: int
+    nh: int = 0            # the last nh rows of Q are held out (training the predictor), not evaluated
 
     @property
     def nx(self):
@@ -96,7 +97,7 @@ def gauss_small(seed: int = 1235, nx: int = 10_000, nq: int = 1_000, d: int = 32
 
 def sift_like(seed: int = 1236, scale: float = 1.0, nx: int = 1_000_000, nq: int = 100_000,
               d: int = 128, k: int = 256, ood_frac: float = 0.10, sigma: float = 20.0,
-              shift: float = 64.0) -> Workload:
+              shift: float = 64.0, nh: int = 0) -> Workload:
     nx = max(1, int(round(nx * scale)))
     nq = max(1, int(round(nq * scale)))
     rng = np.random.default_rng(seed)
@@ -114,7 +115,15 @@ def sift_like(seed: int = 1236, scale: float = 1.0, nx: int = 1_000_000, nq: int
     ood = np.zeros(nq, bool)
     ood[nq - n_ood:] = True
     perm = rng.permutation(nq)
-    return Workload("sift_like", X, Q[perm].copy(), ood[perm].copy(), 0, 32, 64, 20.0, seed)
+    Q, ood = Q[perm].copy(), ood[perm].copy()
+    nh = int(round(nh * scale))
+    if nh > 0:
+        # held-out queries drawn after the evaluated ones, same recipe
+        h_ood = rng.random(nh) < ood_frac
+        H = np.where(h_ood[:, None], ints(_mixture(rng, nh, fresh, sigma)), ints(_mixture(rng, nh, centres, sigma)))
+        Q = np.concatenate([Q, H.astype(np.float32)])
+        ood = np.concatenate([ood, h_ood])
+    return Workload("sift_like", X, Q, ood, 0, 32, 64, 20.0, seed, nh)
 
 
 def uniform_small(seed: int, nx: int, nq: int, d: int, metric: int = 0, degree: int = 8,
@@ -245,7 +254,7 @@ def vmf_like(seed: int = 1238, scale: float = 1.0, nx: int = 10_000_000, nq: int
 
         X = rows(lab_x, w_x)
         Q = rows(lab_q, w_q)
-    return Workload("vmf_like", X, Q, unseen, 1, 32, 64, 10.0, seed)
+    return Workload("vmf_like", X, Q, unseen, 1, 32, 64, 10.0, seed, nh)
 
 
 def gauss_wide(seed: int = 1237, scale: float = 1.0, nx: int = 1_000_000, nq: int = 1_000_000, d: int = 960,

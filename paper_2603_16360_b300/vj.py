@@ -26,7 +26,8 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_predictor_outputs",
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_batch", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
-           "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error"]
+           "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error", "vj_set_wait_test",
+           "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
 
@@ -45,7 +46,8 @@ class vj_params(C.Structure):
     _fields_ = [("degree", C.c_int), ("knn_k", C.c_int), ("greedy_beam", C.c_int), ("conv_threshold", C.c_int),
                 ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
                 ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
-                ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64)]
+                ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64),
+                ("gather", C.c_int)]
 
 
 class vj_stats(C.Structure):
@@ -55,6 +57,18 @@ class vj_stats(C.Structure):
                 ("bytes_algorithmic", C.c_int64), ("kernel_launches", C.c_int64), ("ms_scan", C.c_double),
                 ("scan_candidates", C.c_int64), ("ms_prologue", C.c_double),
                 ("sws_restarts", C.c_int64), ("ms_route", C.c_double), ("ms_sws", C.c_double * 3)]
+
+
+class vj_train_params(C.Structure):
+    _fields_ = [("n_ladder", C.c_int), ("ladder", C.c_int * 8), ("query_recall", C.c_float),
+                ("pooled_recall", C.c_float), ("scan_row_cost", C.c_float), ("h1", C.c_int), ("h2", C.c_int),
+                ("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64)]
+
+
+class vj_train_report(C.Structure):
+    _fields_ = [("n", C.c_int64), ("routed", C.c_int64), ("per_budget", C.c_int64 * 8), ("ladder_run", C.c_int),
+                ("scan_row_cost", C.c_double), ("final_loss", C.c_double), ("ms_labels", C.c_double),
+                ("ms_train", C.c_double)]
 
 
 class vj_result(C.Structure):
@@ -129,6 +143,16 @@ def load():
     lib.vj_result_free.restype = None
     lib.vj_free.argtypes = [P]
     lib.vj_free.restype = None
+    lib.vj_default_train_params.argtypes = [C.POINTER(vj_train_params)]
+    lib.vj_default_train_params.restype = None
+    lib.vj_predictor_labels.argtypes = [P, C.c_float, P, I64, C.POINTER(vj_train_params), P, P,
+                                        C.POINTER(vj_train_report)]
+    lib.vj_predictor_labels.restype = I
+    lib.vj_train_predictor.argtypes = [P, C.c_float, P, I64, C.POINTER(vj_train_params), C.POINTER(P),
+                                       C.POINTER(vj_train_report)]
+    lib.vj_train_predictor.restype = I
+    lib.vj_set_wait_test.argtypes = [P, C.c_longlong, I64]
+    lib.vj_set_wait_test.restype = I
     lib.vj_last_error.argtypes = []
     lib.vj_last_error.restype = C.c_char_p
     _lib = lib
@@ -322,6 +346,13 @@ class MLP:
     def handle(self):
         return self._h
 
+    @classmethod
+    def _adopt(cls, handle, din: int, h1: int, h2: int):
+        """Wrap a predictor the library created (vj_train_predictor)."""
+        m = cls.__new__(cls)
+        m._h, m.din, m.h1, m.h2 = handle, din, h1, h2
+        return m
+
     def num_params(self) -> int:
         return int(load().vj_mlp_num_params(self._h))
 
@@ -393,6 +424,59 @@ def vj_predictor_outputs(ix: Index, eps: float) -> np.ndarray:
     out = np.empty((ix.info()["nq"], 2), np.float32)
     _check(load().vj_predictor_outputs(ix.handle, float(eps), out.ctypes.data))
     return out
+
+
+def train_params(**kw) -> vj_train_params:
+    """vj_train_params with the library's defaults, fields overridden by kw
+    (ladder may be a sequence: it also sets n_ladder)."""
+    tp = vj_train_params()
+    load().vj_default_train_params(C.byref(tp))
+    for k, v in kw.items():
+        if k == "ladder":
+            v = list(v)
+            if not 1 <= len(v) <= 8:
+                raise ValueError("ladder needs 1..8 budgets")
+            tp.n_ladder = len(v)
+            for i, b in enumerate(v):
+                tp.ladder[i] = int(b)
+        else:
+            setattr(tp, k, v)
+    return tp
+
+
+def _report(rep: vj_train_report) -> dict:
+    d = {name: getattr(rep, name) for name, _ in vj_train_report._fields_}
+    d["per_budget"] = list(rep.per_budget)
+    return d
+
+
+def vj_predictor_labels(ix: Index, eps: float, rows, **kw):
+    """(budget [n] int32, route [n] uint8, report) of the training queries rows."""
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    tp = train_params(**kw)
+    budget = np.zeros(len(r), np.int32)
+    route = np.zeros(len(r), np.uint8)
+    rep = vj_train_report()
+    _check(load().vj_predictor_labels(ix.handle, float(eps), r.ctypes.data, len(r), C.byref(tp), budget.ctypes.data,
+                                      route.ctypes.data, C.byref(rep)))
+    return budget, route, _report(rep)
+
+
+def vj_train_predictor(ix: Index, eps: float, rows, **kw):
+    """(MLP, report): labels of the training queries rows, then a trained predictor."""
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    tp = train_params(**kw)
+    h = C.c_void_p()
+    rep = vj_train_report()
+    _check(load().vj_train_predictor(ix.handle, float(eps), r.ctypes.data, len(r), C.byref(tp), C.byref(h),
+                                     C.byref(rep)))
+    inf = ix.info()
+    return MLP._adopt(h, NFEAT + inf["d"], tp.h1, tp.h2), _report(rep)
+
+
+def vj_set_wait_test(ix: Index, max_polls: int = 0, hold_q: int = -1):
+    """Limit the soft-sharing dependency wait (0: default) and hold one query's publication (-1: none)."""
+    _check(load().vj_set_wait_test(ix.handle, int(max_polls), int(hold_q)))
 
 
 def vj_set_plan(ix: Index, route=None, beam=None):

@@ -59,13 +59,13 @@ def test_sample_subtrees_are_closed_under_parents():
 
 def test_stored_traffic_is_keyed_to_the_kernel_sources():
     text = open(os.path.join(ROOT, "profiles", "traffic.md")).read()
-    rows = re.findall(r"^\| (\S+) \| (\S+) \| ([0-9a-f]{64}) \| ([0-9.eE+]+) \|", text, re.M)
-    assert {r[0] for r in rows} == {"k_join", "k_tc_scan_res"}
-    for kernel, src, sha, val in rows:
+    rows = re.findall(r"^\| (\S+) \| (\S+) \| (\S+) \| ([0-9a-f]{64}) \| ([0-9.eE+]+) \|", text, re.M)
+    assert rows and {r[0] for r in rows} <= {"k_join", "k_tc_scan"}
+    for kernel, wl, src, sha, val in rows:
         cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
-        got = bench._traffic(kernel, 1.0)
+        got = bench._traffic(kernel, wl)
         assert got == (float(val) if cur == sha else None)
-        assert bench._traffic(kernel, 0.5) is None  # only the full-size workload was captured
+        assert bench._traffic(kernel, wl + "0") is None  # only the captured workload
 
 
 def test_clock_summary_flags_throttle_reasons():

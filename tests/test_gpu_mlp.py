@@ -94,8 +94,11 @@ def test_features_match_definitions(oracle):
 
 def test_learned_join_reduces_to_route_all_and_bfs():
     """A predictor whose route logit is +large routes every query (the join
-    then equals the exact join); one whose outputs are all very negative runs
-    BFS everywhere (the join equals the planless join without the rule)."""
+    then equals the exact join); one with a very negative route logit and a
+    budget output of 1 (b = 2^1 - 2 = 0) runs BFS everywhere (the join equals
+    the planless join without the rule); with a very negative budget output
+    (b clamps to 2^0 - 2 = -1) no query expands (the join equals a plan of -1
+    for every query)."""
     w = inputs.gauss_small(seed=32, nx=3000, nq=300, d=16, k=8)
     ix = vj.vj_build(w.X, w.Q, params=vj.default_params(degree=16, knn_k=32))
     din = vj.NFEAT + w.d
@@ -104,9 +107,9 @@ def test_learned_join_reduces_to_route_all_and_bfs():
     eps = 2.5
     ex = vj.vj_join_exact(ix, eps)
     vj.vj_attach_predictor(ix, m, 0.5, 64)
-    for route_bias, expect in ((50.0, "exact"), (-50.0, "bfs")):
+    for route_bias, budget_head, expect in ((50.0, 1.0, "exact"), (-50.0, 1.0, "bfs"), (-50.0, -50.0, "none")):
         flat = np.zeros(n, np.float32)
-        flat[-2] = -50.0          # budget head -> 2^0 - 1 = 0 (BFS)
+        flat[-2] = budget_head    # 2^1 - 2 = 0: BFS; 2^0 - 2 = -1 (clamped): no expansion
         flat[-1] = route_bias     # route head
         m.set_params(flat)
         vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1, learned=1)
@@ -115,6 +118,14 @@ def test_learned_join_reduces_to_route_all_and_bfs():
         if expect == "exact":
             assert np.array_equal(r.offsets, ex.offsets) and np.array_equal(r.ids, ex.ids)
             assert np.all(r.hybrid == 2)
+        elif expect == "none":
+            assert np.all(r.hybrid == 3)
+            vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, learned=0)
+            vj.vj_set_plan(ix, None, np.full(w.nq, -1, np.int32))
+            b = vj.vj_join(ix, eps)
+            vj.vj_set_plan(ix, None, None)
+            assert np.array_equal(r.offsets, b.offsets) and np.array_equal(r.ids, b.ids)
+            assert np.array_equal(r.steps, b.steps)
         else:
             vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, learned=0)
             b = vj.vj_join(ix, eps)

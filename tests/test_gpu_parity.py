@@ -352,12 +352,14 @@ def test_plan_route_and_beams_match_oracle(built, oracle, ws):
     """Routed queries take their rows from the tensor-core scan (exact after
     re-check), others run BFS or hybrid with their planned queue size; every
     row, visited count, soft cache and route/hybrid flag equals the oracle's
-    run of the same plan on the same graph."""
+    run of the same plan on the same graph.  A plan of -1 skips the
+    expansion phase (hybrid flag 3)."""
     name, w, ix = built
     eps = _calib_eps(oracle, w, 10, w.metric)
     rng = np.random.default_rng(11)
     route = (rng.random(w.nq) < 0.25).astype(np.uint8)
-    beam = np.where(rng.random(w.nq) < 0.4, 8, 0).astype(np.int32)
+    u = rng.random(w.nq)
+    beam = np.where(u < 0.4, 8, np.where(u < 0.7, -1, 0)).astype(np.int32)
     vj.vj_set_join_params(ix, work_sharing=ws, adapt_hybrid=1)
     vj.vj_set_plan(ix, route, beam)
     try:

@@ -301,6 +301,40 @@ def test_mi_self_join_equals_closed_form(oracle, metric):
         assert int(r.cache[q]) == best
 
 
+@pytest.mark.parametrize("metric", [0, 1])
+def test_no_expansion_plan_equals_probe_closed_form(oracle, metric):
+    """Plan -1 (an expansion budget of zero): the row is I after the greedy
+    phase, i.e. the in-range data nodes among {entry, q} U N(q), the visited
+    count is |{entry, q} U N(q)| and the cache the closest of those data
+    nodes; plan 0 queries in the same join keep the full closure."""
+    w = inputs.uniform_small(15, 400, 60, 5, metric=metric) if metric else inputs.gauss_small(seed=15, nx=400, nq=60, d=5, k=4)
+    adj, entry, _ = oracle.build_graph(w.X, w.Q, 8, 16, metric=metric)
+    V = np.concatenate([w.X, w.Q]).astype(np.float64)
+    D = cdist(w.Q.astype(np.float64), V, "euclidean" if metric == 0 else "cosine")
+    eps = float(np.quantile(D[:, :w.nx], 0.03))
+    beam = np.where(np.arange(w.nq) % 2 == 0, -1, 0).astype(np.int32)
+    r = oracle.join(w.X, w.Q, adj, entry, eps, metric=metric, work_sharing=oracle.WS_SELF, beam=beam)
+    full = _closure_expected(w, adj, entry, eps, D, [(q, [entry]) for q in range(w.nq)])
+    grew = 0
+    for q in range(w.nq):
+        if beam[q] == 0:
+            res, nvis, best = full[q]
+            assert int(r.hybrid[q]) == 0
+        else:
+            u = w.nx + q
+            probe = {entry, u} | {int(v) for v in adj[u] if v >= 0}
+            res = {v for v in probe if v < w.nx and D[q][v] < eps}
+            nvis = len(probe)
+            data = [v for v in probe if v < w.nx]
+            best = min(data, key=lambda v: (D[q][v], v)) if data else -1
+            assert int(r.hybrid[q]) == 3
+            grew += len(full[q][0]) > len(res)
+        assert set(int(i) for i in r.row(q)) == res
+        assert int(r.steps[q]) == nvis
+        assert int(r.cache[q]) == best
+    assert grew > 0  # the closure adds points on some of these queries
+
+
 def test_mi_sws_join_equals_closed_form(oracle):
     w = inputs.gauss_small(seed=14, nx=500, nq=80, d=5, k=4)
     adj, entry, _ = oracle.build_graph(w.X, w.Q, 8, 16)
