@@ -1240,7 +1240,7 @@ JoinDispatch dispatch_t(int cls, int num_sms) {
             blocks_for(k_join_multi<G, NPL, U>, num_sms), launch_join_multi_t<G, NPL, U>};
 }
 
-constexpr int JOIN_CLASSES = 8;
+constexpr int JOIN_CLASSES = 9;
 
 JoinDispatch pick(int dp4, int num_sms) {
     if (dp4 <= 8) return dispatch_t<8, 1, 4>(0, num_sms);
@@ -1248,6 +1248,9 @@ JoinDispatch pick(int dp4, int num_sms) {
     if (dp4 <= 32) return dispatch_t<8, 4, 2>(2, num_sms);
     if (dp4 <= 64) return dispatch_t<16, 4, 2>(3, num_sms);
     if (dp4 <= 128) return dispatch_t<32, 4, 2>(4, num_sms);
+    // up to 768 floats: two 16-lane groups with two candidates each, so four
+    // rows' gathers are in flight per warp (one 32-lane group waited on one)
+    if (dp4 <= 192) return dispatch_t<16, 12, 2>(8, num_sms);
     if (dp4 <= 256) return dispatch_t<32, 8, 1>(5, num_sms);
     if (dp4 <= 512) return dispatch_t<32, 16, 1>(6, num_sms);
     return dispatch_t<32, 32, 1>(7, num_sms);

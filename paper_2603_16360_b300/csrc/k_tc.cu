@@ -53,8 +53,9 @@ constexpr uint32_t TC_TMEM_COLS = 512;    // two 256-column FP32 accumulators
 // for unit rows, cb = 0):
 //   EPI_SCAN    a pair is a candidate when v > thr[row]; candidates are
 //               appended through per-warp chunks as (row id, column, acc * cs);
-//   EPI_SAMPLE  each row keeps the 16 largest v over the unit's tiles (its own
-//               column excluded) and writes the 16th to top16[row].
+//   EPI_SAMPLE  each row keeps the WD_TOP largest v over the unit's tiles (its
+//               own column excluded) and writes the smallest of them to
+//               top16[row].
 // Warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..9 are the
 // epilogue (two per TMEM lane quarter, 128 columns each).  Every wait is
 // bounded; an epilogue warp that gives up keeps walking its tiles (without
@@ -67,6 +68,12 @@ constexpr int WD_THREADS = (2 + WD_EPI) * 32;
 constexpr uint32_t WD_A_BYTES = WD_BM * TC_BK * 2;  // 16 KB
 constexpr uint32_t WD_B_BYTES = WD_BN * TC_BK * 2;  // 32 KB
 constexpr int WD_CHUNK = 128;                       // candidate slots reserved per warp at a time
+// EPI_SAMPLE keeps the WD_TOP largest values per row.  With every 16th tile
+// sampled, the WD_TOP-th sampled value lies near the row's 16 WD_TOP-th
+// largest overall; a row's K = 64 nearest all stay above it unless at least
+// WD_TOP of them fall in the 1/16 sample (binomial tail: about 1e-5 per row
+// for 16, 1.5e-8 for 20), which is what leaves a row uncertified.
+constexpr int WD_TOP = 20;
 
 struct __align__(1024) WdSmem {
     uint8_t A[WD_STAGES][WD_A_BYTES];
@@ -80,7 +87,8 @@ struct __align__(1024) WdSmem {
     int abort;
     __align__(16) float cs[2][WD_BN];
     __align__(16) float cb[2][WD_BN];
-    float part[WD_BM][17];  // sample: the second column half's top 16 per row
+    __align__(16) float th[2][WD_BN];  // symmetric sweep: the columns' row thresholds
+    float part[WD_BM][WD_TOP + 1];  // sample: the second column half's list per row
 };
 
 // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both
@@ -108,7 +116,80 @@ struct WdParams {
     float* top16;          // [nrows] EPI_SAMPLE output (rows are node ids: the row's own column is skipped)
     int* err;
     long long spin_limit;
+    // symmetric sweep (A = B, EPI_SCAN, tstride 1): units[u] = (row tile, first
+    // B tile, end B tile); a tile strictly above its row tile's 256-row block
+    // (ct > rt / 2) also tests the transposed pairs (c, r): acc * cs[r] + cb[r]
+    // > thr[c], so each unordered pair is computed once
+    const int4* units;
 };
+
+// (row tile, first tile, end tile) of work unit u
+__device__ __forceinline__ void wd_unit(const WdParams& P, int u, int& rt, int& t0, int& t1) {
+    if (P.units) {
+        const int4 v = P.units[u];
+        rt = v.x;
+        t0 = v.y;
+        t1 = v.z;
+    } else {
+        rt = u % P.nrt;
+        const int cc = u / P.nrt;
+        t0 = cc * P.tpu;
+        t1 = min(P.nct, t0 + P.tpu);
+    }
+}
+
+// warp-aggregated append of the pairs marked in (h0, h1) over 64 accumulator
+// columns c0 .. c0 + 63: as (row, column) pairs, or, transposed, as (column,
+// row) pairs; w = acc times the B row's scale (cs[j], or rs when transposed)
+__device__ __forceinline__ void wd_append(const WdParams& P, const uint32_t (&va)[64], uint32_t h0, uint32_t h1,
+                                          int64_t c0, int rowid, bool transposed, const float* cs, float rs,
+                                          unsigned long long& cbase, int& cleft, int lane) {
+    const int mine = __popc(h0) + __popc(h1);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
+        if (lane >= o) incl += t2;
+    }
+    const int total = __shfl_sync(VJ_FULL, incl, 31);
+    if (total == 0) return;
+    if (total > cleft) {
+        // close the chunk (its unused slots become holes) and reserve the next
+        for (int k = lane; k < cleft; k += 32)
+            if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
+        const int want = max(total, WD_CHUNK);
+        unsigned long long gb = 0;
+        if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
+        cbase = __shfl_sync(VJ_FULL, gb, 31);
+        cleft = want;
+    }
+    unsigned long long gq = cbase + (unsigned long long)(incl - mine);
+    cbase += (unsigned long long)total;
+    cleft -= total;
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+        uint32_t hit = hh ? h1 : h0;
+        while (hit) {
+            const int j = __ffs(hit) - 1;
+            hit &= hit - 1;
+            if ((int64_t)gq < P.cap) {
+                const int col = (int)(c0 + hh * 32 + j);
+                P.cq[gq] = transposed ? col : rowid;
+                P.cx[gq] = transposed ? rowid : col;
+                if (P.cw) {
+                    // select by unrolled compares: a runtime index into va
+                    // would move the whole array to local memory
+                    float o = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < 32; jj++)
+                        if (jj == j) o = __uint_as_float(va[hh * 32 + jj]);
+                    P.cw[gq] = o * (transposed ? rs : cs[hh * 32 + j]);
+                }
+            }
+            gq++;
+        }
+    }
+}
 
 template <int EPI>
 __global__ void __launch_bounds__(WD_THREADS, 1)
@@ -150,8 +231,8 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
             uint32_t issued = 0, last_ph = 0;  // stages ever filled, parity of their last fill
             bool ok = true;
             for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
-                const int rt = u % P.nrt, cc = u / P.nrt;
-                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                int rt, t0, t1;
+                wd_unit(P, u, rt, t0, t1);
                 for (int ct = t0; ct < t1 && ok; ct++) {
                     for (int kb = 0; kb < P.nkb; kb++) {
                         if (!mbar_wait(&S.empty[s], ph ^ 1u, abort, P.spin_limit)) {
@@ -189,8 +270,8 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
             int i = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
-                const int cc = u / P.nrt;
-                const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+                int rt, t0, t1;
+                wd_unit(P, u, rt, t0, t1);
                 for (int ct = t0; ct < t1 && ok; ct++, i++) {
                     const int acc = i & 1;
                     if (!mbar_wait(&S.tempty[acc], (uint32_t)(((i >> 1) & 1) ^ 1), abort, P.spin_limit)) {
@@ -243,25 +324,30 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
         unsigned long long cbase = 0;  // EPI_SCAN: this warp's output chunk (next slot, slots left)
         int cleft = 0;
         for (int u = blockIdx.x; u < P.nunits; u += gridDim.x) {
-            const int rt = u % P.nrt, cc = u / P.nrt;
-            const int t0 = cc * P.tpu, t1 = min(P.nct, t0 + P.tpu);
+            int rt, t0, t1;
+            wd_unit(P, u, rt, t0, t1);
             const int64_t r = (int64_t)rt * WD_BM + quarter * 32 + lane;
             const bool rv = r < P.nrows;
             const float thr = (EPI == EPI_SCAN && rv) ? P.thr[r] : INFINITY;
             const int qid = rv ? (P.a_ids ? P.a_ids[r] : (int)r) : -1;
-            float t[16];
+            // symmetric sweep: this row as a B row (scale and bias of the transposed test)
+            const float rcs = (P.units && rv) ? P.cs[r] : 0.f;
+            const float rcb = (P.units && rv) ? P.cb[r] : -INFINITY;
+            float t[WD_TOP];
 #pragma unroll
-            for (int k = 0; k < 16; k++) t[k] = -INFINITY;
+            for (int k = 0; k < WD_TOP; k++) t[k] = -INFINITY;
             for (int ct = t0; ct < t1; ct++, i++) {
                 const int acc = i & 1;
                 const int64_t cbase_col = (int64_t)ct * P.tstride * WD_BN;
                 // stage this tile's column scale and bias (a column past the last
                 // B row gets bias -inf: it never passes a test)
+                const bool sym_t = P.units != nullptr && ct > (rt >> 1);  // both directions in this tile
                 {
                     const int64_t c = cbase_col + etid;
                     const bool cv = c < P.ncols;
                     S.cs[acc][etid] = cv ? P.cs[c] : 0.f;
                     S.cb[acc][etid] = cv ? P.cb[c] : -INFINITY;
+                    if (EPI == EPI_SCAN && sym_t) S.th[acc][etid] = cv ? P.thr[c] : INFINITY;
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(WD_EPI * 32) : "memory");
                 if (!dead) {
@@ -302,17 +388,17 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                         }
                         const float mx = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
                         if constexpr (EPI == EPI_SAMPLE) {
-                            if (!rv || !(mx > t[15])) continue;
+                            if (!rv || !(mx > t[WD_TOP - 1])) continue;
                             const int64_t c0 = cbase_col + col0;
                             const bool self_here = r >= c0 && r < c0 + 64;
 #pragma unroll
                             for (int j = 0; j < 64; j++) {
                                 float x = fmaf(__uint_as_float(va[j]), S.cs[acc][col0 + j], S.cb[acc][col0 + j]);
-                                if (!(x > t[15])) continue;
+                                if (!(x > t[WD_TOP - 1])) continue;
                                 if (self_here && c0 + j == r) continue;
-                                // insert: x sinks to its place, the 16th value drops out
+                                // insert: x sinks to its place, the last value drops out
 #pragma unroll
-                                for (int k = 0; k < 16; k++) {
+                                for (int k = 0; k < WD_TOP; k++) {
                                     const float hi = fmaxf(t[k], x);
                                     x = fminf(t[k], x);
                                     t[k] = hi;
@@ -320,7 +406,23 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                             }
                         } else {
                             const bool maybe = rv && mx > thr;
-                            if (!__any_sync(VJ_FULL, maybe)) continue;
+                            // the transposed test: this row's value against each column's threshold
+                            bool maybe_t = false;
+                            if (sym_t) {
+                                const float4* th4 = reinterpret_cast<const float4*>(&S.th[acc][col0]);
+                                float n0 = -INFINITY, n1 = -INFINITY, n2 = -INFINITY, n3 = -INFINITY;
+#pragma unroll
+                                for (int j4 = 0; j4 < 16; j4++) {
+                                    const float4 th = th4[j4];
+                                    n0 = fmaxf(n0, fmaf(__uint_as_float(va[4 * j4 + 0]), rcs, rcb) - th.x);
+                                    n1 = fmaxf(n1, fmaf(__uint_as_float(va[4 * j4 + 1]), rcs, rcb) - th.y);
+                                    n2 = fmaxf(n2, fmaf(__uint_as_float(va[4 * j4 + 2]), rcs, rcb) - th.z);
+                                    n3 = fmaxf(n3, fmaf(__uint_as_float(va[4 * j4 + 3]), rcs, rcb) - th.w);
+                                }
+                                maybe_t = rv && fmaxf(fmaxf(n0, n1), fmaxf(n2, n3)) > 0.f;
+                            }
+                            if (!__any_sync(VJ_FULL, maybe || maybe_t)) continue;
+                            const int64_t c0 = cbase_col + col0;
                             uint32_t hit0 = 0, hit1 = 0;
                             if (maybe) {
 #pragma unroll
@@ -331,51 +433,20 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                                                             S.cb[acc][col0 + 32 + j]) > thr) << j;
                                 }
                             }
-                            // warp-aggregated append of both halves
-                            const int mine = __popc(hit0) + __popc(hit1);
-                            int incl = mine;
+                            wd_append(P, va, hit0, hit1, c0, qid, false, &S.cs[acc][col0], 0.f, cbase, cleft, lane);
+                            if (__any_sync(VJ_FULL, maybe_t)) {
+                                uint32_t th0 = 0, th1 = 0;
+                                if (maybe_t) {
 #pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int t2 = __shfl_up_sync(VJ_FULL, incl, o);
-                                if (lane >= o) incl += t2;
-                            }
-                            const int total = __shfl_sync(VJ_FULL, incl, 31);
-                            if (total == 0) continue;
-                            if (total > cleft) {
-                                // close the chunk (its unused slots become holes) and reserve the next
-                                for (int k = lane; k < cleft; k += 32)
-                                    if ((int64_t)(cbase + k) < P.cap) P.cq[cbase + k] = -1;
-                                const int want = max(total, WD_CHUNK);
-                                unsigned long long gb = 0;
-                                if (lane == 31) gb = atomicAdd(P.ncand, (unsigned long long)want);
-                                cbase = __shfl_sync(VJ_FULL, gb, 31);
-                                cleft = want;
-                            }
-                            unsigned long long gq = cbase + (unsigned long long)(incl - mine);
-                            cbase += (unsigned long long)total;
-                            cleft -= total;
-                            const int64_t c0 = cbase_col + col0;
-#pragma unroll
-                            for (int hh = 0; hh < 2; hh++) {
-                                uint32_t hit = hh ? hit1 : hit0;
-                                while (hit) {
-                                    const int j = __ffs(hit) - 1;
-                                    hit &= hit - 1;
-                                    if ((int64_t)gq < P.cap) {
-                                        P.cq[gq] = qid;
-                                        P.cx[gq] = (int)(c0 + hh * 32 + j);
-                                        if (P.cw) {
-                                            // select by unrolled compares: a runtime index into va
-                                            // would move the whole array to local memory
-                                            float o = 0.f;
-#pragma unroll
-                                            for (int jj = 0; jj < 32; jj++)
-                                                if (jj == j) o = __uint_as_float(va[hh * 32 + jj]);
-                                            P.cw[gq] = o * S.cs[acc][col0 + hh * 32 + j];
-                                        }
+                                    for (int j = 0; j < 32; j++) {
+                                        th0 |= (uint32_t)(fmaf(__uint_as_float(va[j]), rcs, rcb) > S.th[acc][col0 + j])
+                                               << j;
+                                        th1 |= (uint32_t)(fmaf(__uint_as_float(va[32 + j]), rcs, rcb) >
+                                                          S.th[acc][col0 + 32 + j])
+                                               << j;
                                     }
-                                    gq++;
                                 }
+                                wd_append(P, va, th0, th1, c0, qid, true, nullptr, rcs, cbase, cleft, lane);
                             }
                         }
                     }
@@ -386,22 +457,22 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                 const int rl = quarter * 32 + lane;
                 if (cg == 1) {
 #pragma unroll
-                    for (int k = 0; k < 16; k++) S.part[rl][k] = t[k];
+                    for (int k = 0; k < WD_TOP; k++) S.part[rl][k] = t[k];
                 }
                 asm volatile("bar.sync 2, %0;" ::"r"(WD_EPI * 32) : "memory");
                 if (cg == 0 && rv && !dead) {
 #pragma unroll 1
-                    for (int k2 = 0; k2 < 16; k2++) {
+                    for (int k2 = 0; k2 < WD_TOP; k2++) {
                         float x = S.part[rl][k2];
-                        if (!(x > t[15])) break;  // the partner's list is descending
+                        if (!(x > t[WD_TOP - 1])) break;  // the partner's list is descending
 #pragma unroll
-                        for (int k = 0; k < 16; k++) {
+                        for (int k = 0; k < WD_TOP; k++) {
                             const float hi = fmaxf(t[k], x);
                             x = fminf(t[k], x);
                             t[k] = hi;
                         }
                     }
-                    P.top16[r] = t[15];
+                    P.top16[r] = t[WD_TOP - 1];
                 }
                 asm volatile("bar.sync 2, %0;" ::"r"(WD_EPI * 32) : "memory");
             }
@@ -1351,6 +1422,7 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     DBuf<__nv_bfloat16> abf;
     DBuf<float> top, thr, cw;
     DBuf<int32_t> iota;
+    DBuf<int4> units;
     DBuf<int> err;
     DBuf<unsigned long long> ctr;
     top.alloc(n, s);
@@ -1361,7 +1433,9 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     const long long spin_limit = 1ll << 22;
     DBuf<int32_t>& cq = ix->scan_cq;
     DBuf<int32_t>& cx = ix->scan_cx;
-    int64_t cap = std::max<int64_t>(cq.n, n * (int64_t)(20 * KNN_SAMPLE) + (1 << 20));
+    // expected candidates per row: the sample list length times the sampling stride
+    const int64_t per_row = (int64_t)(wide ? WD_TOP : 16) * KNN_SAMPLE;
+    int64_t cap = std::max<int64_t>(cq.n, n * (per_row + per_row / 4) + (1 << 20));
     unsigned long long hn = 0;
     int herr = 0;
     // the candidate sweep, re-run with larger lists when they overflow
@@ -1461,11 +1535,26 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         VJ_LAUNCH_CHECK();
         k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
         VJ_LAUNCH_CHECK();
-        // 2. candidate sweep over every tile, rows are node ids
+        // 2. candidate sweep, rows are node ids.  A = B, so the Gram tiles are
+        // symmetric: row tile rt visits the B tiles from its own 256-row block
+        // on (ct >= rt / 2), and tiles past that block test both directions.
+        // Units: a row tile's run of tpu tiles, ordered by first tile so the
+        // units running together walk the same B tiles (and the longest runs,
+        // of the first row tiles, start first).
         W.tstride = 1;
         W.nct = nct_all;
-        W.tpu = best_tiles_per_unit(W.nrt, W.nct, ix->num_sms, 1);
-        W.nunits = W.nrt * (int)vj_div_up(W.nct, W.tpu);
+        int64_t tiles = 0;
+        for (int rt = 0; rt < W.nrt; rt++) tiles += nct_all - (rt >> 1);
+        const int64_t tpu = std::min<int64_t>(nct_all, std::max<int64_t>(64, tiles / (8 * (int64_t)ix->num_sms)));
+        std::vector<int4> hu;
+        for (int rt = 0; rt < W.nrt; rt++)
+            for (int64_t t0 = rt >> 1; t0 < nct_all; t0 += tpu)
+                hu.push_back(make_int4(rt, (int)t0, (int)std::min<int64_t>(nct_all, t0 + tpu), 0));
+        std::stable_sort(hu.begin(), hu.end(), [](const int4& a, const int4& b) { return a.y < b.y; });
+        units.alloc(hu.size(), s);
+        VJ_CUDA(cudaMemcpyAsync(units.p, hu.data(), hu.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        W.units = units.p;
+        W.nunits = (int)hu.size();
         W.thr = thr.p;
         W.a_ids = nullptr;
         W.ncand = ctr.p;
@@ -1513,6 +1602,7 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     thr.free_(s);
     cw.free_(s);
     iota.free_(s);
+    units.free_(s);
     err.free_(s);
     ctr.free_(s);
     return true;

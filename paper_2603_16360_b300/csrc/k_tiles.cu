@@ -424,7 +424,7 @@ struct KcSmem {
     double d64[128];
 };
 
-template <int G, int NPL>
+template <int G, int NPL, int U>
 __global__ void __launch_bounds__(KC_WPB * 32)
     k_knn_rerank_csr(const float* __restrict__ vec, const float* __restrict__ invn, int dp, int d, int64_t n,
                      int metric, int K, const int64_t* __restrict__ off, const int32_t* __restrict__ cand,
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     float4 q[NPL];
     load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
     const float invq = metric ? invn[r] : 0.f;
-    group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, S.id, nvalid, S.key, lane);
+    group_keys<G, NPL, U>(vec, invn, dp / 4, metric, q, invq, S.id, nvalid, S.key, lane);
     __syncwarp();
     bitonic_pairs(S.key, S.id, P2, lane);
     // near-tie runs among the first K + 1: FP64 re-rank (runs stay below 128)
@@ -762,12 +762,18 @@ void vj_build_knn(vj_index* ix) {
         if (tc) {
             const int smem = KC_WPB * (int)sizeof(KcSmem);
             const float* w = cw.n > 0 ? cw.p : nullptr;  // tile values: streamed kernel only
-            VJ_DISPATCH_GN(dp4, VJ_CUDA(cudaFuncSetAttribute(k_knn_rerank_csr<G, NPL>,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-                           k_knn_rerank_csr<G, NPL><<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
-                               ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p,
-                               ix->knn.p, ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->cos_raw ? 1 : 0,
-                               ix->tc_cb, ix->tc_c3, (float)(ix->maxnorm * 1.0001)));
+            // rows wider than 512 floats keep four candidates' gathers in flight per warp
+            auto launch = [&](auto kern) {
+                VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                kern<<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
+                    ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p, ix->knn.p,
+                    ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->cos_raw ? 1 : 0, ix->tc_cb, ix->tc_c3,
+                    (float)(ix->maxnorm * 1.0001));
+            };
+            VJ_DISPATCH_GN(dp4, {
+                if (dp4 > 128) launch(k_knn_rerank_csr<G, NPL, 4>);
+                else launch(k_knn_rerank_csr<G, NPL, 1>);
+            });
             VJ_LAUNCH_CHECK();
         }
         coff.free_(s);
