@@ -561,6 +561,28 @@ def learned_arm(vj, ix, eps, ex, w, log, caps):
     return m, {"thr": op[0], "beam_cap": op[1], "sweep": sweep, "train_s": train_s, "train_report": rep}
 
 
+def profile_modes(args, vj, ix, w, build_s, binfo):
+    """--mode build / join: one JSON line per build or join, for profiling runs."""
+    print(json.dumps({"mode": "build", "workload": w.name, "nx": w.nx, "nq": w.nq, "d": w.d, "build_s": build_s,
+                      **binfo}), flush=True)
+    if args.mode != "join":
+        return
+    # a threshold near the workload's: the exact join's calibration is not needed to time a traversal
+    eps = calibrate_eps(vj, ix, w, w.target_matches)
+    plan = {"none": -1, "bfs": 0}.get(args.plan)
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=int(plan is None), learned=0,
+                          gather=vj.VJ_PREC_BF16)
+    if plan is not None:
+        vj.vj_set_plan(ix, None, np.full(w.nq, plan, np.int32))
+    for i in range(args.reps):
+        st = vj.vj_join(ix, eps).stats
+        print(json.dumps({"mode": "join", "plan": args.plan, "rep": i, "eps": eps, "ms_total": st["ms_total"],
+                          "ms_traverse": st["ms_traverse"], "ms_sws": st["ms_sws"],
+                          "dist_per_query": st["dist_computations"] / w.nq,
+                          "gbs_algorithmic": st["bytes_algorithmic"] / st["ms_traverse"] / 1e6}), flush=True)
+    vj.vj_set_plan(ix, None, None)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,6 +597,12 @@ def main():
     ap.add_argument("--collection-learned", action="store_true",
                     help="angular_collection: also time one shared predictor's learned route")
     ap.add_argument("--quiet", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "build", "join"],
+                    help="build: generate the workload and build the index only (profiling the build); join: "
+                         "also run --reps joins with every query planned --plan (profiling the traversal)")
+    ap.add_argument("--plan", default="none", choices=["none", "bfs", "rule"],
+                    help="--mode join: none = no expansion (the learned step's plan here), bfs, or the d1/d2 rule")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -616,6 +644,10 @@ def main():
     build_s = time.perf_counter() - t0
     info, binfo = ix.info(), ix.build_info()
     log(f"build {build_s:.1f}s {binfo}")
+    if args.mode != "bench":
+        profile_modes(args, vj, ix, w, build_s, binfo)
+        ix.free()
+        return
     eps = calibrate_eps(vj, ix, w, target)
     ex = vj.vj_join_exact(ix, eps)
     log(f"eps {eps}: exact pairs {ex.offsets[ne]} over {ne} evaluated queries, scan {ex.stats['ms_scan']:.1f} ms")

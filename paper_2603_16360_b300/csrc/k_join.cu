@@ -69,6 +69,10 @@ constexpr int CCAP = 128;   // candidate slots per batch
 constexpr int FB = 4;       // frontier nodes per BFS batch (FB * 32 <= CCAP)
 constexpr int GCAP0 = 8192; // first global visited table
 constexpr int OQS = 64;     // out-range queue slots per buffer kept in shared memory
+// wide rows: two blocks (16 warps) per SM, registers capped at 128 -- the
+// gathers are latency-bound, so resident warps matter more than the few
+// registers spilled; narrow rows fit two blocks uncapped
+#define JOIN_MIN_BLOCKS(NPL, U) ((NPL) * (U) >= 12 ? 2 : 1)
 
 struct WarpSmem {
     int nlist;  // bitmap mode: ids listed in the warp's space
@@ -1091,7 +1095,7 @@ __device__ __forceinline__ int pass_ticket_slot(int mode) {
 
 // one join pass over one index: warps take queries from the pass's ticket
 template <int G, int NPL, int U>
-__global__ void __launch_bounds__(WPB * 32) k_join(const __grid_constant__ JoinParams P) {
+__global__ void __launch_bounds__(WPB * 32, JOIN_MIN_BLOCKS(NPL, U)) k_join(const __grid_constant__ JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
@@ -1124,7 +1128,7 @@ struct JoinBatch {
 static_assert(sizeof(JoinBatch) <= 32000, "JoinBatch must fit the kernel parameter space");
 
 template <int G, int NPL, int U>
-__global__ void __launch_bounds__(WPB * 32) k_join_multi(const __grid_constant__ JoinBatch B) {
+__global__ void __launch_bounds__(WPB * 32, JOIN_MIN_BLOCKS(NPL, U)) k_join_multi(const __grid_constant__ JoinBatch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem* S = reinterpret_cast<WarpSmem*>(smem_raw) + warp;
@@ -1219,6 +1223,9 @@ template <class K>
 int blocks_for(K kern, int num_sms) {
     size_t smem = sizeof(WarpSmem) * WPB;
     VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the largest shared-memory carveout, so two blocks' warp state fits an SM
+    VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
     VJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1248,9 +1255,10 @@ JoinDispatch pick(int dp4, int num_sms) {
     if (dp4 <= 32) return dispatch_t<8, 4, 2>(2, num_sms);
     if (dp4 <= 64) return dispatch_t<16, 4, 2>(3, num_sms);
     if (dp4 <= 128) return dispatch_t<32, 4, 2>(4, num_sms);
-    // up to 768 floats: two 16-lane groups with two candidates each, so four
-    // rows' gathers are in flight per warp (one 32-lane group waited on one)
-    if (dp4 <= 192) return dispatch_t<16, 12, 2>(8, num_sms);
+    // up to 768 floats: six 16-byte slots per lane and two candidates in
+    // flight per warp (eight slots and one candidate left the warp waiting
+    // on one row's gathers at a time)
+    if (dp4 <= 192) return dispatch_t<32, 6, 2>(8, num_sms);
     if (dp4 <= 256) return dispatch_t<32, 8, 1>(5, num_sms);
     if (dp4 <= 512) return dispatch_t<32, 16, 1>(6, num_sms);
     return dispatch_t<32, 32, 1>(7, num_sms);

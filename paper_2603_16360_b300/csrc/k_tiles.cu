@@ -96,7 +96,7 @@ __device__ __forceinline__ int tile_col(int j) { return (threadIdx.x & 15) * 4 +
 
 // ---------------------------------------------------------------- norms
 __global__ void k_norms(const float* __restrict__ vec, int dp, int d, int64_t n, float* __restrict__ sqn,
-                        float* __restrict__ invn, double* __restrict__ maxn) {
+                        float* __restrict__ invn, double* __restrict__ sqn64, double* __restrict__ maxn) {
     const int lane = threadIdx.x & 31;
     int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (u >= n) return;
@@ -108,6 +108,7 @@ __global__ void k_norms(const float* __restrict__ vec, int dp, int d, int64_t n,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(VJ_FULL, s, o);
     if (lane == 0) {
+        sqn64[u] = s;
         sqn[u] = (float)s;
         invn[u] = s > 0.0 ? (float)(1.0 / sqrt(s)) : 0.f;
         // max norm (non-negative doubles order like their bit patterns)
@@ -418,11 +419,94 @@ __device__ void bitonic_pairs(float* key, int* id, int P2, int lane) {
     }
 }
 
+constexpr int KC_E64 = 256;  // prefix lengths ranked directly in FP64
+
 struct KcSmem {
     int id[KC_CAP];
     float key[KC_CAP];
     double d64[128];
+    double e64[KC_E64];
 };
+
+// bitonic sort of P2 (FP64 key, id) pairs in shared memory, ascending (one warp)
+__device__ void bitonic_pairs64(double* key, int* id, int P2, int lane) {
+    for (int k = 2; k <= P2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P2; i += 32) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = key[p] < key[i] || (key[p] == key[i] && id[p] < id[i]);
+                    if (gt == up) {
+                        const double tk = key[i];
+                        const int ti = id[i];
+                        key[i] = key[p];
+                        id[i] = id[p];
+                        key[p] = tk;
+                        id[p] = ti;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// FP64 keys of q (FP32 slots in registers, |q|^2 = qq in FP64) to cand[0..nc):
+// L2 the squared distance, cosine 1 - <x,q> / (|x||q|) with |x|^2 from sqn64;
+// FP32 inputs make every product exact in FP64, so these equal the
+// definition's keys up to FP64 summation order.  U candidates per lane group
+// in flight, as group_keys.
+template <int G, int NPL, int U>
+__device__ void group_keys64(const float* __restrict__ vec, const double* __restrict__ sqn64, int dp4, int metric,
+                             const float4 (&q)[NPL], double qq, const int32_t* cand, int nc, double* key, int lane) {
+    constexpr int NG = 32 / G;
+    const int grp = lane / G, g = lane & (G - 1);
+    for (int base = 0; base < nc; base += NG * U) {
+        float4 x[U][NPL];
+        int node[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int ci = base + u * NG + grp;
+            node[u] = ci < nc ? cand[ci] : -1;
+            if (node[u] >= 0) {
+                load_slots<G, NPL>(vec, node[u], dp4, g, x[u]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NPL; k++) x[u][k] = f4zero();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            double a = 0.0;
+#pragma unroll
+            for (int k = 0; k < NPL; k++) {
+                const double xs[4] = {x[u][k].x, x[u][k].y, x[u][k].z, x[u][k].w};
+                const double qs[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    if (metric == 0) {
+                        const double t = xs[c] - qs[c];
+                        a = fma(t, t, a);
+                    } else {
+                        a = fma(xs[c], qs[c], a);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(VJ_FULL, a, o);
+            const int ci = base + u * NG + grp;
+            if (g == 0 && ci < nc) {
+                if (metric == 0) {
+                    key[ci] = a;
+                } else {
+                    const double xx = sqn64[node[u]];
+                    key[ci] = (xx == 0.0 || qq == 0.0) ? 1.0 : 1.0 - a / (sqrt(xx) * sqrt(qq));
+                }
+            }
+        }
+    }
+}
 
 template <int G, int NPL, int U>
 __global__ void __launch_bounds__(KC_WPB * 32)
@@ -431,7 +515,7 @@ __global__ void __launch_bounds__(KC_WPB * 32)
                      const float* __restrict__ row_thr, int32_t* __restrict__ out_id, float* __restrict__ out_key,
                      int32_t* __restrict__ bad_rows, int* __restrict__ nbad, unsigned long long* __restrict__ nrechk,
                      const float* __restrict__ cw, const float* __restrict__ sqn, int raw, float cb, float c3,
-                     float maxnorm) {
+                     float maxnorm, const double* __restrict__ sqn64) {
     extern __shared__ uint8_t kc_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     KcSmem& S = reinterpret_cast<KcSmem*>(kc_raw)[warp];
@@ -471,7 +555,9 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     // tolerance of the FP32 direct-difference keys (relative for L2)
     const float tol = 2.0f * (float)(dp + 4) * VJ_F32_U * (metric == 0 ? 1.0f : 4.0f) + 1e-7f;
     float out_lo = FLT_MAX;  // approximate-key prefilter: lower bound on every dropped candidate
+    bool pref = false;       // the prefilter ran
     if (cw && nvalid > K) {
+        pref = true;
         bitonic_pairs(S.key, S.id, P2, lane);
         const double mx = (double)maxnorm;
         const double beta = metric == 0
@@ -501,6 +587,34 @@ __global__ void __launch_bounds__(KC_WPB * 32)
     float4 q[NPL];
     load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
     const float invq = metric ? invn[r] : 0.f;
+    if (pref && nvalid <= KC_E64) {
+        // the prefix in FP64: its order is the definition's (ties by id), no
+        // FP32 near-tie runs to resolve
+        int Q2 = 32;
+        while (Q2 < nvalid) Q2 <<= 1;
+        group_keys64<G, NPL, U>(vec, sqn64, dp / 4, metric, q, sqn64[r], S.id, nvalid, S.e64, lane);
+        for (int e = nvalid + lane; e < Q2; e += 32) {
+            S.e64[e] = DBL_MAX;
+            S.id[e] = INT32_MAX;
+        }
+        __syncwarp();
+        bitonic_pairs64(S.e64, S.id, Q2, lane);
+        bool ok = nvalid >= K;
+        if (ok) {
+            const double kth = S.e64[K - 1];
+            const double hi = kth + 1e-12 * (1.0 + fabs(kth));
+            ok = hi < (double)row_thr[r] && hi < (double)out_lo;
+        }
+        if (!ok) {
+            if (lane == 0) bad_rows[atomicAdd(nbad, 1)] = (int32_t)r;
+            return;
+        }
+        for (int e = lane; e < K; e += 32) {
+            out_id[r * K + e] = S.id[e];
+            out_key[r * K + e] = (float)S.e64[e];
+        }
+        return;
+    }
     group_keys<G, NPL, U>(vec, invn, dp / 4, metric, q, invq, S.id, nvalid, S.key, lane);
     __syncwarp();
     bitonic_pairs(S.key, S.id, P2, lane);
@@ -709,7 +823,9 @@ void vj_compute_norms(vj_index* ix, double* maxnorm_out) {
     DBuf<double> mx;
     mx.alloc(1, s);
     VJ_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(double), s));
-    k_norms<<<vj_div_up(ix->n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->n, ix->sqn.p, ix->invn.p, mx.p);
+    ix->sqn64.ensure(ix->n, s);
+    k_norms<<<vj_div_up(ix->n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->n, ix->sqn.p, ix->invn.p,
+                                                         ix->sqn64.p, mx.p);
     VJ_LAUNCH_CHECK();
     VJ_CUDA(cudaMemcpyAsync(maxnorm_out, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaStreamSynchronize(s));
@@ -768,7 +884,7 @@ void vj_build_knn(vj_index* ix) {
                 kern<<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
                     ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p, ix->knn.p,
                     ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->cos_raw ? 1 : 0, ix->tc_cb, ix->tc_c3,
-                    (float)(ix->maxnorm * 1.0001));
+                    (float)(ix->maxnorm * 1.0001), ix->sqn64.p);
             };
             VJ_DISPATCH_GN(dp4, {
                 if (dp4 > 128) launch(k_knn_rerank_csr<G, NPL, 4>);

@@ -83,6 +83,7 @@ static void free_index(vj_index* ix) {
     ix->vec.free_(s);
     ix->sqn.free_(s);
     ix->invn.free_(s);
+    ix->sqn64.free_(s);
     ix->knn.free_(s);
     ix->knnd.free_(s);
     ix->adj.free_(s);
@@ -99,6 +100,8 @@ static void free_index(vj_index* ix) {
     ix->plan_beam.free_(s);
     ix->routed.free_(s);
     ix->xbf.free_(s);
+    ix->wcs.free_(s);
+    ix->wcb.free_(s);
     ix->xbias.free_(s);
     ix->abias.free_(s);
     ix->done.free_(s);

@@ -103,6 +103,7 @@ struct vj_index {
     DBuf<float> vec;      // [n][dp] FP32, zero padded
     DBuf<float> sqn;      // [n] squared norm (FP32 of the FP64 value)
     DBuf<float> invn;     // [n] 1/|v| (cosine), 0 for a zero vector
+    DBuf<double> sqn64;   // [n] squared norm in FP64
     DBuf<int32_t> knn;    // [n][K] exact kNN ids
     DBuf<float> knnd;     // [n][K] their distance keys (L2: squared distance; cosine: distance)
     DBuf<int32_t> adj;    // [n][R] -1 padded
