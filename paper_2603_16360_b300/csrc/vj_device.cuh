@@ -32,25 +32,46 @@ __device__ __forceinline__ void load_slots(const float* __restrict__ vec, int64_
     }
 }
 
-// The same slots from the BF16 copy of the vectors (rows of kpb BF16 values,
-// zero padded): slot idx holds BF16 values 4 idx .. 4 idx + 3, one 8-byte
-// load, converted exactly to FP32.  When every coordinate is a BF16 value the
-// slots, and so every key, equal those of the FP32 rows at half the bytes.
+// Slots from the BF16 copy of the vectors (rows of kpb BF16 values, zero
+// padded): slot idx holds BF16 values 4 idx .. 4 idx + 3, one 8-byte load,
+// kept raw (two uint32) until converted exactly to FP32 at use.  When every
+// coordinate is a BF16 value these equal the FP32 rows' slots, and so every
+// key, at half the bytes.
 template <int G, int NPL>
-__device__ __forceinline__ void load_slots_bf16(const __nv_bfloat16* __restrict__ xb, int64_t node, int kpb,
-                                                int dp4, int g, float4 (&r)[NPL]) {
+__device__ __forceinline__ void load_raw_bf16(const __nv_bfloat16* __restrict__ xb, int64_t node, int kpb, int dp4,
+                                              int g, uint2 (&r)[NPL]) {
     const uint2* row = reinterpret_cast<const uint2*>(xb + node * (int64_t)kpb);
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
         int idx = g + k * G;
-        if (idx < dp4) {
-            const uint2 v = __ldg(row + idx);
-            r[k] = make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xFFFF0000u),
-                               __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xFFFF0000u));
+        r[k] = (idx < dp4) ? __ldg(row + idx) : make_uint2(0u, 0u);
+    }
+}
+
+// metric 0: squared L2 distance; metric 1: dot product (raw BF16 slots, each
+// converted exactly to FP32 right before its four products: the same values
+// and order as slot_accum on the converted slots)
+template <int NPL>
+__device__ __forceinline__ float slot_accum_bf16(const uint2 (&xr)[NPL], const float4 (&q)[NPL], int metric) {
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < NPL; k++) {
+        const float x0 = __uint_as_float(xr[k].x << 16), x1 = __uint_as_float(xr[k].x & 0xFFFF0000u);
+        const float x2 = __uint_as_float(xr[k].y << 16), x3 = __uint_as_float(xr[k].y & 0xFFFF0000u);
+        if (metric == 0) {
+            float t0 = x0 - q[k].x, t1 = x1 - q[k].y, t2 = x2 - q[k].z, t3 = x3 - q[k].w;
+            a = fmaf(t0, t0, a);
+            a = fmaf(t1, t1, a);
+            a = fmaf(t2, t2, a);
+            a = fmaf(t3, t3, a);
         } else {
-            r[k] = f4zero();
+            a = fmaf(x0, q[k].x, a);
+            a = fmaf(x1, q[k].y, a);
+            a = fmaf(x2, q[k].z, a);
+            a = fmaf(x3, q[k].w, a);
         }
     }
+    return a;
 }
 
 // metric 0: squared L2 distance; metric 1: dot product
@@ -87,7 +108,7 @@ __device__ __forceinline__ float group_sum(float a) {
 
 // Distance keys of q to cand[0..nc) written to key[0..nc) (shared memory).
 // L2: squared distance; cosine: 1 - <x,q> * invx * invq.  With xb, the
-// candidates' vectors are read from the BF16 copy (see load_slots_bf16).
+// candidates' vectors are read from the BF16 copy (see load_raw_bf16).
 template <int G, int NPL, int U>
 __device__ __forceinline__ void group_keys(const float* __restrict__ vec, const float* __restrict__ invn,
                                            int dp4, int metric, const float4 (&q)[NPL], float invq,
@@ -95,6 +116,33 @@ __device__ __forceinline__ void group_keys(const float* __restrict__ vec, const 
                                            const __nv_bfloat16* __restrict__ xb = nullptr, int kpb = 0) {
     constexpr int NG = 32 / G;
     const int grp = lane / G, g = lane & (G - 1);
+    if (xb) {
+        // BF16 rows: raw 8-byte slots take half the registers of converted
+        // ones, so twice the candidates' gathers are in flight
+        constexpr int UB = 2 * U;
+        for (int base = 0; base < nc; base += NG * UB) {
+            uint2 xr[UB][NPL];
+            int node[UB];
+#pragma unroll
+            for (int u = 0; u < UB; u++) {
+                int ci = base + u * NG + grp;
+                node[u] = ci < nc ? cand[ci] : -1;
+                if (node[u] >= 0) {
+                    load_raw_bf16<G, NPL>(xb, node[u], kpb, dp4, g, xr[u]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NPL; k++) xr[u][k] = make_uint2(0u, 0u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UB; u++) {
+                float a = group_sum<G>(slot_accum_bf16<NPL>(xr[u], q, metric));
+                int ci = base + u * NG + grp;
+                if (g == 0 && ci < nc) key[ci] = metric == 0 ? a : 1.0f - a * __ldg(invn + node[u]) * invq;
+            }
+        }
+        return;
+    }
     for (int base = 0; base < nc; base += NG * U) {
         float4 x[U][NPL];
         int node[U];
@@ -103,8 +151,7 @@ __device__ __forceinline__ void group_keys(const float* __restrict__ vec, const 
             int ci = base + u * NG + grp;
             node[u] = ci < nc ? cand[ci] : -1;
             if (node[u] >= 0) {
-                if (xb) load_slots_bf16<G, NPL>(xb, node[u], kpb, dp4, g, x[u]);
-                else load_slots<G, NPL>(vec, node[u], dp4, g, x[u]);
+                load_slots<G, NPL>(vec, node[u], dp4, g, x[u]);
             } else {
 #pragma unroll
                 for (int k = 0; k < NPL; k++) x[u][k] = f4zero();
