@@ -43,6 +43,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "queries/s at recall≥0.95 vs exact join: learned+BF16 vs plain FP32, one B300"
+# queries (whole MST subtrees) in the CPU oracle's timed sample: the cpu_baseline and each step of the
+# reference arm time the same subtrees
+CPU_SAMPLE = 3000
 
 
 def _traffic(kernel, workload):
@@ -666,7 +669,7 @@ def main():
         for _ in range(max(args.warmup - 1, 0)):
             run_cpu_oracle(w, vj, ix, eps, 200, mode, pbeam, Xh, Qh)
         for _ in range(args.steps):
-            n, t = run_cpu_oracle(w, vj, ix, eps, 1000, mode, pbeam, Xh, Qh)
+            n, t = run_cpu_oracle(w, vj, ix, eps, CPU_SAMPLE, mode, pbeam, Xh, Qh)
             n_s.append(n)
             dt.append(t)
         v = sum(n_s) / sum(dt)
@@ -677,8 +680,8 @@ def main():
                 "config": {"workload": wl_desc, "arm": f"CPU oracle MI+SWS ({pname}), Alg. 1, FP64, 1 thread",
                            "eps": eps},
                 "cpu_baseline": {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"whole MST subtrees of evaluated queries, {n_s[0]} queries per step, "
-                                           "on the GPU-built graph"},
+                                 "sample": f"whole MST subtrees of evaluated queries, {n_s[0]} queries per step (the "
+                                           f"cpu_baseline's sample), on the GPU-built graph, {pname}"},
                 "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         ix.free()
@@ -792,11 +795,12 @@ def main():
             "clocks": clk,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
     if rank == 0 and not args.no_cpu_baseline:
-        # a bounded sample: whole MST subtrees of about 10,000 evaluated queries
+        # a bounded sample: the reference arm's per-step sample (whole MST
+        # subtrees of about CPU_SAMPLE evaluated queries), in the plain arm's mode
         Xh, Qh = host(w.X), host(w.Q)
         mode = "adapt" if pname.startswith("rule") else "force"
         pbeam = int(pname.split()[-1]) if "queue" in pname else 256
-        n, dt = run_cpu_oracle(w, vj, ix, eps, 10000, mode, pbeam, Xh, Qh)
+        n, dt = run_cpu_oracle(w, vj, ix, eps, CPU_SAMPLE, mode, pbeam, Xh, Qh)
         line["cpu_baseline"] = {"value": n / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{n} evaluated queries (whole MST subtrees) of the same workload on the "
                                           f"GPU-built graph, oracle MI+SWS join ({pname}), FP64, single thread"}

@@ -106,3 +106,56 @@ def test_dependency_wait_times_out_and_index_stays_usable():
     with pytest.raises(vj.VjError):
         vj.vj_set_wait_test(ix, 0, w.nq)  # out of range
     ix.free()
+
+
+def _recall_rows(r, ex, lo, hi):
+    hit = tot = 0
+    for q in range(lo, hi):
+        a = set(r.row(q).tolist())
+        b = set(ex.row(q).tolist())
+        hit += len(a & b)
+        tot += len(b)
+    return hit / max(tot, 1)
+
+
+def test_learned_route_gains_over_the_rule():
+    """What the trained network gains over the method without it.  On the
+    learned-predictor recipe (vMF embeddings, BF16, cosine), a predictor trained
+    on held-out queries of the index (vj_train_predictor) plans the evaluated
+    queries.  It must reach recall 0.95 against the exact join, and cost at most
+    half as much as the paper's d1/d2 rule (Sec. 4.4), alone or with its OOD
+    queries sent to the brute-force scan.  Cost: distance evaluations plus
+    routed queries times the cost of a scan row in distance evaluations."""
+    w = inputs.vmf_like(seed=44, scale=0.01)  # 100K x 768 data, 10K evaluated + 1K held-out queries
+    ne = w.nq - w.nh
+    ix = vj.vj_build(w.X, w.Q, metric=w.metric, params=vj.default_params(degree=32, knn_k=64))
+    from scipy.spatial.distance import cdist
+    D = cdist(w.Q[:200].astype(np.float64), w.X.astype(np.float64), "cosine")
+    eps = float(np.float32(np.partition(D.ravel(), 2000)[2000]))
+    ex = vj.vj_join_exact(ix, eps)
+    rows = np.arange(ne, w.nq, dtype=np.int32)
+    m, rep = vj.vj_train_predictor(ix, eps, rows, ladder=[-1, 0], h1=64, h2=64, epochs=20, batch=64)
+    c_scan = rep["scan_row_cost"]
+
+    def cost(r):
+        s = r.steps[:ne].astype(np.float64)
+        return float(s.sum() + (r.hybrid[:ne] == 2).sum() * c_scan)
+
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1, learned=0)
+    rule = vj.vj_join(ix, eps)
+    route = (rule.hybrid == 1).astype(np.uint8)
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, learned=0)
+    vj.vj_set_plan(ix, route, np.zeros(w.nq, np.int32))
+    rule_routed = vj.vj_join(ix, eps)
+    vj.vj_set_plan(ix, None, None)
+    vj.vj_attach_predictor(ix, m, 0.5, 0)
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=0, learned=1, gather=vj.VJ_PREC_BF16)
+    lr = vj.vj_join(ix, eps)
+    rec = {k: _recall_rows(r, ex, 0, ne) for k, r in (("rule", rule), ("rule_routed", rule_routed), ("learned", lr))}
+    c = {k: cost(r) for k, r in (("rule", rule), ("rule_routed", rule_routed), ("learned", lr))}
+    assert rec["learned"] >= 0.95, (rec, c)
+    assert c["learned"] <= 0.5 * min(c["rule"], c["rule_routed"]), (rec, c)
+    vj.vj_set_join_params(ix, learned=0, gather=vj.VJ_PREC_FP32)
+    vj.vj_attach_predictor(ix, None, 0.5, 64)
+    m.free()
+    ix.free()
