@@ -78,6 +78,9 @@ typedef struct {
                              copy of the vectors (half the bytes) when every coordinate is exactly a
                              BF16 value, so every key equals the FP32 one; otherwise, and by default
                              (FP32), the FP32 rows.  A join-time field. */
+    int hybrid_seed_best; /* joins: 1 = a hybrid expansion whose greedy phase found no in-range point
+                             starts from the closest visited data node (the paper's Alg. 7 as
+                             written starts nowhere and returns nothing); default 0 */
 } vj_params;
 
 /* Per-call counters and device timings of a join. */
@@ -148,8 +151,8 @@ vj_status vj_build(const float *X, int64_t nx, const float *Q, int64_t nq, int d
 vj_status vj_set_stream(vj_index *ix, void *stream);
 
 /* Replace the join-time fields (greedy_beam, conv_threshold, hybrid_beam,
- * work_sharing, adapt_hybrid, force_hybrid, learned, gather) used by later
- * joins. */
+ * work_sharing, adapt_hybrid, force_hybrid, learned, gather,
+ * hybrid_seed_best) used by later joins. */
 vj_status vj_set_join_params(vj_index *ix, const vj_params *p);
 
 /* Per-query plan used by later joins in place of Alg. 6's CheckHybrid rule
@@ -308,6 +311,18 @@ vj_status vj_join_device(vj_index *ix, float eps, int budget, vj_result **out);
  * All or nothing: on any failure every outs[i] is NULL and vj_last_error
  * names the first failing instance.  n = 0 is a no-op. */
 vj_status vj_join_batch(vj_index **ixs, const float *eps, int n, vj_result **outs);
+
+/* Query-data switching (the paper's large-threshold discussion, App. E):
+ * the join X |><| Q equals Q |><| X transposed, so for large eps the roles may
+ * be swapped.  ix must be built with them swapped (vj_build(Q, nq, X, nx,
+ * ...): the original queries as the index's data).  The call runs Alg. 1 on
+ * it (the original data vectors as queries) and transposes the pair list
+ * back: one row per original query (the index's data row), ids the original
+ * data ids (the index's query indices) ascending, dists the pair distances.
+ * Host result with nq = the index's nx; steps and hybrid are 0 and cache -1
+ * (the swapped join's per-query outputs describe the other set); stats are
+ * the swapped join's.  Errors: as vj_join. */
+vj_status vj_join_switched(vj_index *ix, float eps, vj_result **out);
 
 /* Exact nested-loop join (Sec. 3.2) of the index's X and Q on the GPU, host
  * result.  Pairs whose FP32 distance lies within the FP32 rounding bound of

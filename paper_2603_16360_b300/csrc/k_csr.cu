@@ -241,7 +241,60 @@ __global__ void __launch_bounds__(SL_T)
     }
 }
 
+// column counts of a pair list
+__global__ void k_col_count(const int32_t* __restrict__ ids, int64_t nnz, int32_t* __restrict__ counts) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) atomicAdd(counts + ids[e], 1);
+}
+
+// warp per row: each pair (row r, column c) goes to c's transposed row as r
+__global__ void k_transpose_scatter(const int64_t* __restrict__ off, int64_t nrows, const int32_t* __restrict__ ids,
+                                    const float* __restrict__ d, const int64_t* __restrict__ toff,
+                                    int32_t* __restrict__ cursor, int32_t* __restrict__ tid, float* __restrict__ td) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nrows) return;
+    for (int64_t e = off[r] + lane; e < off[r + 1]; e += 32) {
+        const int c = ids[e];
+        const int64_t pos = toff[c] + atomicAdd(cursor + c, 1);
+        tid[pos] = (int32_t)r;
+        td[pos] = d[e];
+    }
+}
+
 }  // namespace
+
+void vj_csr_transpose(vj_index* ix, const int64_t* off, int64_t nrows, const int32_t* ids, const float* d,
+                      int64_t nnz, int64_t ncols, DBuf<int64_t>& toff, DBuf<int32_t>& tids, DBuf<float>& tds) {
+    cudaStream_t s = ix->stream;
+    DBuf<int32_t> counts, cursor, uid;
+    DBuf<float> ud;
+    counts.alloc(std::max<int64_t>(ncols, 1), s);
+    cursor.alloc(std::max<int64_t>(ncols, 1), s);
+    VJ_CUDA(cudaMemsetAsync(counts.p, 0, std::max<int64_t>(ncols, 1) * sizeof(int32_t), s));
+    VJ_CUDA(cudaMemsetAsync(cursor.p, 0, std::max<int64_t>(ncols, 1) * sizeof(int32_t), s));
+    if (nnz > 0) {
+        k_col_count<<<vj_div_up(nnz, 256), 256, 0, s>>>(ids, nnz, counts.p);
+        VJ_LAUNCH_CHECK();
+    }
+    toff.ensure(ncols + 1, s);
+    vj_exclusive_scan_i32_to_i64(counts.p, toff.p, ncols, ix);
+    uid.alloc(std::max<int64_t>(nnz, 1), s);
+    ud.alloc(std::max<int64_t>(nnz, 1), s);
+    if (nnz > 0 && nrows > 0) {
+        k_transpose_scatter<<<vj_div_up(nrows * 32, 256), 256, 0, s>>>(off, nrows, ids, d, toff.p, cursor.p, uid.p,
+                                                                     ud.p);
+        VJ_LAUNCH_CHECK();
+    }
+    // the scatter order within a row is arbitrary: sort each row by id
+    tids.ensure(std::max<int64_t>(nnz, 1), s);
+    tds.ensure(std::max<int64_t>(nnz, 1), s);
+    vj_segment_sort_copy(toff.p, counts.p, toff.p, uid.p, ud.p, tids.p, tds.p, ncols, ix);
+    counts.free_(s);
+    cursor.free_(s);
+    uid.free_(s);
+    ud.free_(s);
+}
 
 void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix) {
     // out has n + 1 entries; out[n] = total

@@ -134,6 +134,7 @@ struct JoinParams {
     int dp4, dp, d, R, metric;
     int32_t entry;
     int ws, adapt, force, hbeam, conv;
+    int seed_best;  // hybrid expansion with nothing in range starts from the closest visited data node
     float eps_key;  // L2: eps^2, cosine: eps
     float band;     // |key - eps_key| <= band * scale -> FP64 re-decision
     float tie_tol;  // keys closer than this (relative / absolute) are re-decided in FP64
@@ -904,6 +905,37 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (lane == 0) c_hyb++;
             int npend = s.nres;  // in-range entries not yet popped (rid >= 0)
             int osz = 0, oqh = 0, cur = 0;
+            if (P.seed_best && s.nres == 0 && s.bid != INT32_MAX) {
+                // seed-with-the-best variant: with nothing in range after the
+                // greedy phase, the queue starts from the closest visited data
+                // node ((dist, id) minimum, FP64 among FP32 near-ties)
+                int b = s.bid;
+                float bk = s.bk;
+                if (s.nt > 1) {
+                    double bd = 1e300;
+                    int bi = INT32_MAX;
+                    float bkk = s.bk;
+                    for (int src = 0; src < s.nt; src++) {
+                        const int v = __shfl_sync(VJ_FULL, s.tid, src);
+                        const float kv = __shfl_sync(VJ_FULL, s.tk, src);
+                        const double d64 = warp_dist64(P.vec, P.dp, P.d, P.metric, qn, v, lane);
+                        if (d64 < bd || (d64 == bd && v < bi)) {
+                            bd = d64;
+                            bi = v;
+                            bkk = kv;
+                        }
+                    }
+                    b = bi;
+                    bk = bkk;
+                    if (lane == 0) c_rechk++;
+                }
+                if (lane == 0) {
+                    W.qk[cur][0] = bk;
+                    W.qi[cur][0] = b;
+                }
+                __syncwarp();
+                osz = 1;
+            }
             for (;;) {
                 int u;
                 if (npend > 0) {
@@ -1401,6 +1433,7 @@ void join_setup(JoinRun& r) {
     P.ws = ix->p.work_sharing;
     P.adapt = ix->p.adapt_hybrid;
     P.force = ix->p.force_hybrid;
+    P.seed_best = ix->p.hybrid_seed_best;
     P.hbeam = hbeam;
     P.conv = ix->p.conv_threshold;
     P.eps_key = ix->metric == VJ_L2 ? r.eps * r.eps : r.eps;

@@ -73,6 +73,7 @@ static void check_join_params(const vj_params& p) {
     VJ_REQUIRE(p.learned == 0 || p.learned == 1, VJ_ERR_ARG, "learned must be 0 or 1");
     VJ_REQUIRE(p.route_bruteforce == 0, VJ_ERR_ARG, "route_bruteforce is reserved and must be 0");
     VJ_REQUIRE(p.gather == VJ_PREC_FP32 || p.gather == VJ_PREC_BF16, VJ_ERR_ARG, "gather must be FP32 or BF16");
+    VJ_REQUIRE(p.hybrid_seed_best == 0 || p.hybrid_seed_best == 1, VJ_ERR_ARG, "hybrid_seed_best must be 0 or 1");
 }
 
 static std::atomic<int64_t> g_live_indexes{0};
@@ -236,6 +237,7 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
         ix->p.force_hybrid = p->force_hybrid;
         ix->p.learned = p->learned;
         ix->p.gather = p->gather;
+        ix->p.hybrid_seed_best = p->hybrid_seed_best;
     });
 }
 
@@ -397,6 +399,46 @@ static vj_status join_impl(vj_index* ix, float eps, int budget, vj_result** out,
             vj_set_error("result copy failed: %s", cudaGetErrorString(e));
             throw VjError{VJ_ERR_CUDA};
         }
+        r->stats = st;
+        *out = r;
+    });
+}
+
+// Query-data switching: the join on an index built with the sets' roles
+// swapped, transposed back to one row per original query
+extern "C" vj_status vj_join_switched(vj_index* ix, float eps, vj_result** out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr && out != nullptr, VJ_ERR_ARG, "NULL argument");
+        VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
+        cudaStream_t s = ix->stream;
+        vj_stats st;
+        memset(&st, 0, sizeof(st));
+        int64_t nnz = 0;
+        vj_run_join(ix, eps, 0, &st, &nnz);
+        DBuf<int64_t> toff;
+        DBuf<int32_t> tid;
+        DBuf<float> td;
+        vj_csr_transpose(ix, ix->offsets.p, ix->nq, ix->out_id.p, ix->out_d.p, nnz, ix->nx, toff, tid, td);
+        vj_result* r = new_result(ix->nx, nnz, false, s);
+        cudaError_t e = cudaMemcpyAsync(r->offsets, toff.p, (ix->nx + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (nnz > 0) {
+            e = e ? e : cudaMemcpyAsync(r->ids, tid.p, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            e = e ? e : cudaMemcpyAsync(r->dists, td.p, nnz * sizeof(float), cudaMemcpyDeviceToHost, s);
+        }
+        e = e ? e : cudaStreamSynchronize(s);
+        toff.free_(s);
+        tid.free_(s);
+        td.free_(s);
+        if (e != cudaSuccess) {
+            vj_result_free(r);
+            vj_set_error("result copy failed: %s", cudaGetErrorString(e));
+            throw VjError{VJ_ERR_CUDA};
+        }
+        // per-query outputs of the swapped join belong to the other set
+        memset(r->steps, 0, ix->nx * sizeof(int32_t));
+        memset(r->cache, 0xff, ix->nx * sizeof(int32_t));
+        memset(r->hybrid, 0, ix->nx);
         r->stats = st;
         *out = r;
     });

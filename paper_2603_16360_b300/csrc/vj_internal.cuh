@@ -225,6 +225,10 @@ int64_t vj_learned_prologue(vj_index* ix, float eps);
 
 // utilities
 void vj_exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, vj_index* ix);
+// rows <-> columns of a device CSR pair list (nrows rows over ncols columns);
+// every transposed row ascending by id
+void vj_csr_transpose(vj_index* ix, const int64_t* off, int64_t nrows, const int32_t* ids, const float* d,
+                      int64_t nnz, int64_t ncols, DBuf<int64_t>& toff, DBuf<int32_t>& tids, DBuf<float>& tds);
 void vj_segment_sort_copy(const int64_t* src_start, const int32_t* counts, const int64_t* offsets,
                           const int32_t* src_id, const float* src_d, int32_t* dst_id, float* dst_d,
                           int64_t nseg, vj_index* ix);

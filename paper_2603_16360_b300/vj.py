@@ -27,7 +27,7 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_batch", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error", "vj_set_wait_test",
-           "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor"]
+           "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor", "vj_join_switched"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
 
@@ -47,7 +47,7 @@ class vj_params(C.Structure):
                 ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
                 ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
                 ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64),
-                ("gather", C.c_int)]
+                ("gather", C.c_int), ("hybrid_seed_best", C.c_int)]
 
 
 class vj_stats(C.Structure):
@@ -122,6 +122,8 @@ def load():
     lib.vj_attach_predictor.restype = I
     lib.vj_predictor_outputs.argtypes = [P, C.c_float, P]
     lib.vj_predictor_outputs.restype = I
+    lib.vj_join_switched.argtypes = [P, C.c_float, C.POINTER(C.POINTER(vj_result))]
+    lib.vj_join_switched.restype = I
     for fn in ("vj_join", "vj_join_device"):
         getattr(lib, fn).argtypes = [P, C.c_float, I, C.POINTER(C.POINTER(vj_result))]
         getattr(lib, fn).restype = I
@@ -489,6 +491,14 @@ def vj_set_plan(ix: Index, route=None, beam=None):
 def vj_join(ix: Index, eps: float, budget: int = 0) -> Result:
     rp = C.POINTER(vj_result)()
     _check(load().vj_join(ix.handle, float(eps), int(budget), C.byref(rp)))
+    return _host_result(rp)
+
+
+def vj_join_switched(ix: Index, eps: float) -> Result:
+    """Join on an index built with the roles swapped (vj_build(Q, X)), transposed
+    back to one row per original query."""
+    rp = C.POINTER(vj_result)()
+    _check(load().vj_join_switched(ix.handle, float(eps), C.byref(rp)))
     return _host_result(rp)
 
 

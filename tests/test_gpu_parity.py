@@ -383,3 +383,62 @@ def test_plan_route_and_beams_match_oracle(built, oracle, ws):
     exp = {(int(rq[i]), int(x)) for i in range(len(rq)) for x in ids[off[i]:off[i + 1]]}
     assert not ((got ^ exp) - band)
     assert r.stats["scan_candidates"] >= len(exp) - len(band)
+
+
+@pytest.mark.parametrize("ws", [vj.VJ_WS_SELF, vj.VJ_WS_SOFT], ids=["self", "sws"])
+def test_hybrid_seed_best_matches_oracle(oracle, ws):
+    """The seed-with-the-best variant of the hybrid expansion (a hybrid query
+    whose greedy phase found nothing in range starts from the closest visited
+    data node) equals the oracle's run of the same variant: rows, visited
+    counts, caches and flags; and it finds pairs the literal reading misses."""
+    w = inputs.gauss_small(seed=121, nx=3000, nq=400, d=16, k=8, ood_frac=0.25, shift=6.0)
+    ix = _build(w)
+    eps = _calib_eps(oracle, w, 4, w.metric)
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    owss = {vj.VJ_WS_SELF: oracle.WS_SELF, vj.VJ_WS_SOFT: oracle.WS_SOFT}[ws]
+    res = {}
+    for sb in (0, 1):
+        vj.vj_set_join_params(ix, work_sharing=ws, adapt_hybrid=0, force_hybrid=1, hybrid_beam=16,
+                              hybrid_seed_best=sb)
+        r = vj.vj_join(ix, eps)
+        o = oracle.join(w.X, w.Q, adj, entry, np.float32(eps), metric=w.metric, work_sharing=owss,
+                        force_hybrid=True, hybrid_beam_size=16, order=order, parent=parent,
+                        hybrid_seed_best=bool(sb))
+        band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)
+        diff = (_pairs(r.offsets, r.ids) ^ _pairs(o.offsets, o.ids)) - band
+        assert not diff, f"seed_best={sb}: {len(diff)} pairs differ"
+        np.testing.assert_array_equal(r.steps, o.steps)
+        np.testing.assert_array_equal(r.cache, o.cache)
+        np.testing.assert_array_equal(r.hybrid, o.hybrid)
+        res[sb] = _pairs(r.offsets, r.ids)
+    assert res[1] > res[0] or len(res[1] - res[0]) > 0  # the variant reaches more points
+    ix.free()
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_switched_join_matches_oracle(oracle, metric):
+    """Query-data switching: the join on the index built with the roles swapped
+    (the queries as data), transposed back on the GPU, equals the oracle's join
+    on the same swapped graph transposed by the oracle (pairs, ascending rows,
+    distances)."""
+    w = inputs.uniform_small(131 + metric, 1500, 400, 12, metric=metric, degree=12, knn_k=24)
+    eps = _calib_eps(oracle, w, 40, w.metric)
+    ix = vj.vj_build(w.Q, w.X, metric=w.metric, params=vj.default_params(degree=w.degree, knn_k=w.knn_k))
+    vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_SOFT, adapt_hybrid=1)
+    r = vj.vj_join_switched(ix, eps)
+    assert len(r.offsets) == w.nq + 1
+    adj, entry, parent, order, _ = vj.vj_export_graph(ix)
+    o = oracle.join(w.Q, w.X, adj, entry, np.float32(eps), metric=w.metric, work_sharing=oracle.WS_SOFT,
+                    adapt_hybrid=True, order=order, parent=parent)
+    t_off, t_ids, t_d = oracle.transpose_csr(o.offsets, o.ids, o.dists, w.nq)
+    band = _band_pairs(oracle, w, float(np.float32(eps)), w.metric)  # dist is symmetric
+    diff = (_pairs(r.offsets, r.ids) ^ _pairs(t_off, t_ids)) - band
+    assert not diff, f"{len(diff)} pairs differ"
+    for q in range(w.nq):
+        assert np.all(np.diff(r.row(q)) > 0)
+    gd = {(q, int(i)): float(r.dists[r.offsets[q] + j]) for q in range(w.nq) for j, i in enumerate(r.row(q))}
+    od = {(q, int(i)): float(t_d[t_off[q] + j]) for q in range(w.nq) for j, i in enumerate(t_ids[t_off[q]:t_off[q + 1]])}
+    com = sorted(set(gd) & set(od))
+    assert com
+    np.testing.assert_allclose([gd[k] for k in com], [od[k] for k in com], rtol=1e-5, atol=1e-6)
+    ix.free()
