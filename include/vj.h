@@ -81,6 +81,18 @@ typedef struct {
     int hybrid_seed_best; /* joins: 1 = a hybrid expansion whose greedy phase found no in-range point
                              starts from the closest visited data node (the paper's Alg. 7 as
                              written starts nowhere and returns nothing); default 0 */
+    int nnmap;            /* build: 1 = an NN-Map index (the paper's closing design, "NN-Map"):
+                             the data set's own graph G_X (kNN among data only, pruned over data
+                             rows only) and, per query, its witness (nearest data vector, ties by
+                             id), the witness's FP64 distance and an OOD bit (the d1/d2 > 1.5 rule
+                             with N1 = the query's R nearest data vectors and d2 = the mean length
+                             of the G_X edges from N1 to data outside N1; no such edge: not OOD).
+                             vj_join on it has no greedy phase: a query whose witness distance is
+                             >= eps has an empty row and computes nothing; the others run the
+                             expansion of Alg. 7 on G_X from the witness (BFS; hybrid when
+                             force_hybrid, or adapt_hybrid and the OOD bit), with no work
+                             sharing.  steps counts distance evaluations (the stored witness
+                             distance costs none); default 0 */
 } vj_params;
 
 /* Per-call counters and device timings of a join. */
@@ -376,6 +388,11 @@ vj_status vj_export_graph(const vj_index *ix, int32_t *adj, int32_t *entry, int3
 /* Copy the exact kNN lists computed by the build: ids [(nx+nq) * K] and
  * dists [(nx+nq) * K] (ascending by (dist, id)). */
 vj_status vj_export_knn(const vj_index *ix, int32_t *ids, float *dists);
+
+/* The NN-Map outputs of an index built with nnmap = 1 (any pointer may be
+ * NULL): witness [nq] int32 data ids, wdist [nq] FP64 distances, ood [nq].
+ * VJ_ERR_STATE for an index built without nnmap. */
+vj_status vj_export_nnmap(const vj_index *ix, int32_t *witness, double *wdist, uint8_t *ood);
 
 /* Shape of an index: any pointer may be NULL. */
 vj_status vj_index_info(const vj_index *ix, int64_t *nx, int64_t *nq, int *d, int *degree,

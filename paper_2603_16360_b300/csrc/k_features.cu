@@ -145,6 +145,9 @@ static void ensure_query_stats(vj_index* ix) {
 }
 
 void vj_compute_features(vj_index* ix, float eps, float* feat_dev) {
+    // the features read each query's merged-graph neighbourhood, which an
+    // NN-Map index does not build
+    VJ_REQUIRE(!ix->nnmap, VJ_ERR_STATE, "an NN-Map index has no query neighbourhoods for the predictor features");
     ensure_query_stats(ix);
     k_features<<<vj_div_up(ix->nq * 32, 256), 256, 0, ix->stream>>>(ix->vec.p, ix->dp, ix->d, ix->nx, ix->nq,
                                                                      ix->R, ix->qstat.p, ix->qdn.p, eps, feat_dev);

@@ -761,23 +761,27 @@ void vj_build_graph(vj_index* ix) {
     nr.alloc(1, s);
     VJ_CUDA(cudaMemsetAsync(nr.p, 0, sizeof(unsigned long long), s));
 
+    // nodes with a graph row: every node, or the data nodes only (G_X of an
+    // NN-Map index, whose kNN lists hold data nodes only)
+    const int64_t gr = ix->graph_rows;
+
     // ---- 1. prune
     DBuf<int32_t> pid, pcount;
     DBuf<float> pkey;
-    pid.alloc((size_t)n * R, s);
-    pkey.alloc((size_t)n * R, s);
-    pcount.alloc(n, s);
+    pid.alloc((size_t)gr * R, s);
+    pkey.alloc((size_t)gr * R, s);
+    pcount.alloc(gr, s);
     // rows wider than 256 floats: the tiled prune (a warp per node would
     // gather every kept vector once per candidate)
     const bool tiled = dp4 > 64;
-    const int tp_grid = (int)std::min<int64_t>(n, (int64_t)ix->num_sms * 32);
+    const int tp_grid = (int)std::min<int64_t>(gr, (int64_t)ix->num_sms * 32);
     if (tiled) {
         k_rng_tile<<<tp_grid, TP_THREADS, 0, s>>>(ix->vec.p, ix->invn.p, dp, d, metric, tol, R, ix->knn.p,
-                                                  ix->knnd.p, nullptr, nullptr, K, nullptr, n, pid.p, pkey.p,
+                                                  ix->knnd.p, nullptr, nullptr, K, nullptr, gr, pid.p, pkey.p,
                                                   pcount.p, nr.p);
     } else {
-        VJ_DISPATCH_GN(dp4, (k_prune<G, NPL><<<vj_div_up(n, PWPB), PWPB * 32, 0, s>>>(
-                                ix->vec.p, ix->invn.p, dp, d, n, metric, tol, K, R, ix->knn.p, ix->knnd.p, pid.p,
+        VJ_DISPATCH_GN(dp4, (k_prune<G, NPL><<<vj_div_up(gr, PWPB), PWPB * 32, 0, s>>>(
+                                ix->vec.p, ix->invn.p, dp, d, gr, metric, tol, K, R, ix->knn.p, ix->knnd.p, pid.p,
                                 pkey.p, pcount.p, nr.p)));
     }
     VJ_LAUNCH_CHECK();
@@ -786,42 +790,47 @@ void vj_build_graph(vj_index* ix) {
     DBuf<int32_t> indeg, cursor, inl;
     DBuf<int64_t> inoff;
     DBuf<float> inlk;
-    indeg.alloc(n, s);
-    cursor.alloc(n, s);
-    inoff.alloc(n + 1, s);
-    VJ_CUDA(cudaMemsetAsync(indeg.p, 0, n * sizeof(int32_t), s));
-    VJ_CUDA(cudaMemsetAsync(cursor.p, 0, n * sizeof(int32_t), s));
-    k_indeg<<<vj_div_up(n * R, 256), 256, 0, s>>>(pid.p, n, R, indeg.p);
+    indeg.alloc(gr, s);
+    cursor.alloc(gr, s);
+    inoff.alloc(gr + 1, s);
+    VJ_CUDA(cudaMemsetAsync(indeg.p, 0, gr * sizeof(int32_t), s));
+    VJ_CUDA(cudaMemsetAsync(cursor.p, 0, gr * sizeof(int32_t), s));
+    k_indeg<<<vj_div_up(gr * R, 256), 256, 0, s>>>(pid.p, gr, R, indeg.p);
     VJ_LAUNCH_CHECK();
-    vj_exclusive_scan_i32_to_i64(indeg.p, inoff.p, n, ix);
+    vj_exclusive_scan_i32_to_i64(indeg.p, inoff.p, gr, ix);
     int64_t nin = 0;
-    VJ_CUDA(cudaMemcpyAsync(&nin, inoff.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaMemcpyAsync(&nin, inoff.p + gr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     VJ_CUDA(cudaStreamSynchronize(s));
     inl.alloc(std::max<int64_t>(nin, 1), s);
     inlk.alloc(std::max<int64_t>(nin, 1), s);
-    k_fill_in<<<vj_div_up(n * R, 256), 256, 0, s>>>(pid.p, pkey.p, n, R, inoff.p, cursor.p, inl.p, inlk.p);
+    k_fill_in<<<vj_div_up(gr * R, 256), 256, 0, s>>>(pid.p, pkey.p, gr, R, inoff.p, cursor.p, inl.p, inlk.p);
     VJ_LAUNCH_CHECK();
     ix->adj.ensure((size_t)n * R, s);
     DBuf<float> adjk;
     adjk.alloc((size_t)n * R, s);
+    if (gr < n) {
+        // rows without a graph row (the queries of an NN-Map index): no edges
+        VJ_CUDA(cudaMemsetAsync(ix->adj.p + gr * R, 0xff, (size_t)(n - gr) * R * sizeof(int32_t), s));
+        VJ_CUDA(cudaMemsetAsync(adjk.p + gr * R, 0, (size_t)(n - gr) * R * sizeof(float), s));
+    }
     DBuf<int32_t> big, stage, uid, ucnt;
     DBuf<float> uk;
     DBuf<int> nbig;
-    big.alloc(n, s);
+    big.alloc(gr, s);
     nbig.alloc(2, s);
     VJ_CUDA(cudaMemsetAsync(nbig.p, 0, 2 * sizeof(int), s));
     if (tiled) {
-        stage.alloc(n, s);
-        ucnt.alloc(n, s);
-        uid.alloc((size_t)n * R + std::max<int64_t>(nin, 1), s);
-        uk.alloc((size_t)n * R + std::max<int64_t>(nin, 1), s);
+        stage.alloc(gr, s);
+        ucnt.alloc(gr, s);
+        uid.alloc((size_t)gr * R + std::max<int64_t>(nin, 1), s);
+        uk.alloc((size_t)gr * R + std::max<int64_t>(nin, 1), s);
     }
     {
         size_t smem = sizeof(MergeSmem) * 4;
         VJ_DISPATCH_GN(dp4, {
             VJ_CUDA(cudaFuncSetAttribute(k_merge<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_merge<G, NPL><<<vj_div_up(n, 4), 4 * 32, smem, s>>>(
-                ix->vec.p, ix->invn.p, dp, d, n, metric, tol, R, pid.p, pkey.p, inoff.p, inl.p, inlk.p, ix->adj.p,
+            k_merge<G, NPL><<<vj_div_up(gr, 4), 4 * 32, smem, s>>>(
+                ix->vec.p, ix->invn.p, dp, d, gr, metric, tol, R, pid.p, pkey.p, inoff.p, inl.p, inlk.p, ix->adj.p,
                 adjk.p, big.p, nbig.p, nr.p, tiled ? stage.p : nullptr, nbig.p + 1, uid.p, uk.p, ucnt.p);
         });
         VJ_LAUNCH_CHECK();
@@ -834,8 +843,8 @@ void vj_build_graph(vj_index* ix) {
     if (tiled && hbig[1] > 0) {
         // over-full unions of wide rows: their RNG prune, into adj / adjk
         DBuf<int64_t> uoff;
-        uoff.alloc(n, s);
-        k_union_off<<<vj_div_up(n, 256), 256, 0, s>>>(inoff.p, n, R, uoff.p);
+        uoff.alloc(gr, s);
+        k_union_off<<<vj_div_up(gr, 256), 256, 0, s>>>(inoff.p, gr, R, uoff.p);
         VJ_LAUNCH_CHECK();
         k_rng_tile<<<(int)std::min<int64_t>(hbig[1], (int64_t)ix->num_sms * 32), TP_THREADS, 0, s>>>(
             ix->vec.p, ix->invn.p, dp, d, metric, tol, R, uid.p, uk.p, uoff.p, ucnt.p, 0, stage.p, hbig[1],
@@ -848,23 +857,23 @@ void vj_build_graph(vj_index* ix) {
     uid.free_(s);
     uk.free_(s);
 
-    // ---- 3. entry point
+    // ---- 3. entry point (over the nodes with a graph row)
     {
-        const int nblk = (int)std::min<int64_t>(1024, std::max<int64_t>(1, n / 256));
-        const int64_t rpb = (n + nblk - 1) / nblk;
+        const int nblk = (int)std::min<int64_t>(1024, std::max<int64_t>(1, gr / 256));
+        const int64_t rpb = (gr + nblk - 1) / nblk;
         DBuf<double> part, cen, bd;
         DBuf<int32_t> bi, ent;
         part.alloc((size_t)nblk * d, s);
         cen.alloc(d, s);
-        k_centroid_part<<<nblk, 128, 0, s>>>(ix->vec.p, dp, d, n, rpb, part.p);
+        k_centroid_part<<<nblk, 128, 0, s>>>(ix->vec.p, dp, d, gr, rpb, part.p);
         VJ_LAUNCH_CHECK();
-        k_centroid_final<<<1, 256, 0, s>>>(part.p, nblk, d, n, cen.p);
+        k_centroid_final<<<1, 256, 0, s>>>(part.p, nblk, d, gr, cen.p);
         VJ_LAUNCH_CHECK();
         const int eb = 512;
         bd.alloc(eb, s);
         bi.alloc(eb, s);
         ent.alloc(1, s);
-        k_entry_part<<<eb, CB, 0, s>>>(ix->vec.p, dp, d, n, metric, cen.p, bd.p, bi.p);
+        k_entry_part<<<eb, CB, 0, s>>>(ix->vec.p, dp, d, gr, metric, cen.p, bd.p, bi.p);
         VJ_LAUNCH_CHECK();
         k_entry_final<<<1, 1, 0, s>>>(bd.p, bi.p, eb, ent.p);
         VJ_LAUNCH_CHECK();
@@ -882,8 +891,20 @@ void vj_build_graph(vj_index* ix) {
     k_elen<<<vj_div_up(n * R, 256), 256, 0, s>>>(ix->adj.p, adjk.p, n, nx, R, metric, ix->elen.p);
     VJ_LAUNCH_CHECK();
 
-    // ---- 5. MST + BFS order
-    {
+    // ---- 5. MST + BFS order (an NN-Map index has no query graph: every
+    // query hangs off the data side, in id order)
+    if (ix->nnmap) {
+        std::vector<int32_t> ho(nq), hp(nq, -1), hd(nq, 1);
+        for (int64_t qi = 0; qi < nq; qi++) ho[qi] = (int32_t)qi;
+        ix->order.ensure(nq, s);
+        ix->parent.ensure(nq, s);
+        ix->depth.ensure(nq, s);
+        VJ_CUDA(cudaMemcpyAsync(ix->order.p, ho.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        VJ_CUDA(cudaMemcpyAsync(ix->parent.p, hp.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        VJ_CUDA(cudaMemcpyAsync(ix->depth.p, hd.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
+        ix->max_depth = 1;
+    } else {
         const int64_t ne = nq * (R + 1);
         const int nv = (int)nq + 1;  // queries + (possibly unused) data-entry vertex
         const bool entry_is_query = ix->entry >= nx;

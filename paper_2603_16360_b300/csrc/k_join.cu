@@ -156,6 +156,11 @@ struct JoinParams {
     int oqcap;  // out-range queue capacity (per buffer)
     unsigned long long* ctr;
     long long spin_limit;
+    // NN-Map index: per query the witness, its FP64 distance and the OOD bit
+    // (nullptr: the merged-index join)
+    const int32_t* nm_w;
+    const double* nm_wd;
+    const uint8_t* nm_ood;
 };
 
 enum { QF_PROBED = 1 };
@@ -642,91 +647,113 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         __syncwarp();
         bool failed = false;
 
-        // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
-        int sid = -1;
-        if (lane == 0) sid = P.entry;
-        if (lane == 1 && seedc >= 0) sid = seedc;
-        if (lane == 2 && (P.ws == VJ_WS_SELF || P.ws == VJ_WS_SOFT)) sid = (int)qn;
-        bool snew = false;
-#pragma unroll 1
-        for (int src = 0; src < 3; src++) {
-            int v = __shfl_sync(VJ_FULL, sid, src);
-            int ins = 0;
-            if (lane == 0 && v >= 0) ins = hash_insert(s.tab, s.mask, v);  // seeds: always the shared hash
-            ins = __shfl_sync(VJ_FULL, ins, 0);
-            if (lane == src) snew = ins == 1;
-            __syncwarp();
-        }
-        unsigned sm = __ballot_sync(VJ_FULL, snew);
-        if (snew) S->cand[__popc(sm & ((1u << lane) - 1u))] = sid;
-        __syncwarp();
-        int ns = __popc(sm);
-        group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane, P.xb, P.kpb);
-        __syncwarp();
-        s.nvis += ns;
-        float skey = FLT_MAX;
-        int snode = -1;
-        if (lane < ns) {
-            snode = S->cand[lane];
-            skey = (snode == (int)qn) ? 0.f : S->ckey[lane];
-        }
-        __syncwarp();
-        bool sdata = lane < ns && snode < P.nx;
-        bool sin = inrange_decide(P, sdata, skey, snode, qn, lane, c_rechk);
-        best_update(P, s, sdata, skey, snode, lane);
-        if (!append_results(P, s, sin, snode, skey, W, lane)) failed = true;
-
-        // StopGreedy on the front = argmin (key, id) over the seeds
-        float fk = lane < ns ? skey : FLT_MAX;
-        int fi = lane < ns ? snode : INT32_MAX;
-        bool fin = sin;
-        {
-            float mk = fk;
-            int mi = fi;
-            warp_argmin(mk, mi);
-            unsigned who = __ballot_sync(VJ_FULL, fi == mi && lane < ns);
-            int src = who ? __ffs(who) - 1 : 0;
-            fin = __shfl_sync(VJ_FULL, sin, src);
-            fi = mi;
-        }
-        bool probe = !failed && ns > 0 && !(fi < P.nx && fin) && P.conv > 0 && fi == (int)qn;
-
-        // ---- probe N(q); lane j keeps slot j of q's list and that neighbour's key
+        bool probe = false;
         float nkey_l = FLT_MAX;
         int nid_l = -1;
         int entry_in_nq = 0, seed_in_nq = 0;
-        if (probe) {
-            c_adj++;
-            int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
-            nid_l = v;
-            if (v == P.entry) entry_in_nq = 1;
-            if (v >= 0 && v == seedc) seed_in_nq = 1;
-            unsigned vm = __ballot_sync(VJ_FULL, v >= 0);
-            if (!vis_reserve(P, s, __popc(vm), W, lane, c_spill)) failed = true;
-            if (!failed) {
-                bool nw = v >= 0 && vis_insert(s, W, v);
-                unsigned nm = __ballot_sync(VJ_FULL, nw);
-                int nc = __popc(nm);
-                int mypos = __popc(nm & ((1u << lane) - 1u));
-                if (nw) S->cand[mypos] = v;
+        bool nm_empty = false;  // NN-Map: the row is certified empty
+        int nm_hyb = 0;         // NN-Map: the expansion's hybrid flag
+        if (P.nm_w) {
+            // ---- NN-Map seeding (no greedy phase): the witness w (nearest
+            // data vector) and its stored FP64 distance.  Out of range: no
+            // data vector is in range, and nothing is computed.  Otherwise w
+            // is the one in-range seed of the expansion, visited at no cost.
+            const int w = __ldg(P.nm_w + qi);
+            const double wd = __ldg(P.nm_wd + qi);
+            if (!(wd < P.eps64)) {
+                nm_empty = true;
+            } else {
+                nm_hyb = P.force ? 1 : (P.adapt ? (int)__ldg(P.nm_ood + qi) : 0);
+                if (lane == 0) hash_insert(s.tab, s.mask, w);
                 __syncwarp();
-                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
+                const float wk = P.metric == 0 ? (float)(wd * wd) : (float)wd;
+                best_update(P, s, lane == 0, wk, w, lane);
+                if (!append_results(P, s, lane == 0, w, wk, W, lane)) failed = true;
+            }
+        } else {
+            // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
+            int sid = -1;
+            if (lane == 0) sid = P.entry;
+            if (lane == 1 && seedc >= 0) sid = seedc;
+            if (lane == 2 && (P.ws == VJ_WS_SELF || P.ws == VJ_WS_SOFT)) sid = (int)qn;
+            bool snew = false;
+    #pragma unroll 1
+            for (int src = 0; src < 3; src++) {
+                int v = __shfl_sync(VJ_FULL, sid, src);
+                int ins = 0;
+                if (lane == 0 && v >= 0) ins = hash_insert(s.tab, s.mask, v);  // seeds: always the shared hash
+                ins = __shfl_sync(VJ_FULL, ins, 0);
+                if (lane == src) snew = ins == 1;
                 __syncwarp();
-                s.nvis += nc;
-                int cv = lane < nc ? S->cand[lane] : -1;
-                float ck = lane < nc ? S->ckey[lane] : FLT_MAX;
-                float kk = S->ckey[nw ? mypos : 0];
-                __syncwarp();
-                bool dat = lane < nc && cv < P.nx;
-                bool in = inrange_decide(P, dat, ck, cv, qn, lane, c_rechk);
-                best_update(P, s, dat, ck, cv, lane);
-                if (!append_results(P, s, in, cv, ck, W, lane)) failed = true;
-                if (nw) nkey_l = kk;
-                // a neighbour that was a seed keeps the seed's key
-                for (int src = 0; src < ns; src++) {
-                    int sn = __shfl_sync(VJ_FULL, snode, src);
-                    float sk2 = __shfl_sync(VJ_FULL, skey, src);
-                    if (!nw && v == sn) nkey_l = sk2;
+            }
+            unsigned sm = __ballot_sync(VJ_FULL, snew);
+            if (snew) S->cand[__popc(sm & ((1u << lane) - 1u))] = sid;
+            __syncwarp();
+            int ns = __popc(sm);
+            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane, P.xb, P.kpb);
+            __syncwarp();
+            s.nvis += ns;
+            float skey = FLT_MAX;
+            int snode = -1;
+            if (lane < ns) {
+                snode = S->cand[lane];
+                skey = (snode == (int)qn) ? 0.f : S->ckey[lane];
+            }
+            __syncwarp();
+            bool sdata = lane < ns && snode < P.nx;
+            bool sin = inrange_decide(P, sdata, skey, snode, qn, lane, c_rechk);
+            best_update(P, s, sdata, skey, snode, lane);
+            if (!append_results(P, s, sin, snode, skey, W, lane)) failed = true;
+
+            // StopGreedy on the front = argmin (key, id) over the seeds
+            float fk = lane < ns ? skey : FLT_MAX;
+            int fi = lane < ns ? snode : INT32_MAX;
+            bool fin = sin;
+            {
+                float mk = fk;
+                int mi = fi;
+                warp_argmin(mk, mi);
+                unsigned who = __ballot_sync(VJ_FULL, fi == mi && lane < ns);
+                int src = who ? __ffs(who) - 1 : 0;
+                fin = __shfl_sync(VJ_FULL, sin, src);
+                fi = mi;
+            }
+            probe = !failed && ns > 0 && !(fi < P.nx && fin) && P.conv > 0 && fi == (int)qn;
+
+            // ---- probe N(q); lane j keeps slot j of q's list and that neighbour's key
+            if (probe) {
+                c_adj++;
+                int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+                nid_l = v;
+                if (v == P.entry) entry_in_nq = 1;
+                if (v >= 0 && v == seedc) seed_in_nq = 1;
+                unsigned vm = __ballot_sync(VJ_FULL, v >= 0);
+                if (!vis_reserve(P, s, __popc(vm), W, lane, c_spill)) failed = true;
+                if (!failed) {
+                    bool nw = v >= 0 && vis_insert(s, W, v);
+                    unsigned nm = __ballot_sync(VJ_FULL, nw);
+                    int nc = __popc(nm);
+                    int mypos = __popc(nm & ((1u << lane) - 1u));
+                    if (nw) S->cand[mypos] = v;
+                    __syncwarp();
+                    group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
+                    __syncwarp();
+                    s.nvis += nc;
+                    int cv = lane < nc ? S->cand[lane] : -1;
+                    float ck = lane < nc ? S->ckey[lane] : FLT_MAX;
+                    float kk = S->ckey[nw ? mypos : 0];
+                    __syncwarp();
+                    bool dat = lane < nc && cv < P.nx;
+                    bool in = inrange_decide(P, dat, ck, cv, qn, lane, c_rechk);
+                    best_update(P, s, dat, ck, cv, lane);
+                    if (!append_results(P, s, in, cv, ck, W, lane)) failed = true;
+                    if (nw) nkey_l = kk;
+                    // a neighbour that was a seed keeps the seed's key
+                    for (int src = 0; src < ns; src++) {
+                        int sn = __shfl_sync(VJ_FULL, snode, src);
+                        float sk2 = __shfl_sync(VJ_FULL, skey, src);
+                        if (!nw && v == sn) nkey_l = sk2;
+                    }
                 }
             }
         }
@@ -742,7 +769,9 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         const bool routed = P.route != nullptr && P.route[qi] != 0;
         int hbq = P.hbeam;
         int hyb = P.force;
-        if (P.qbeam) {
+        if (P.nm_w) {
+            hyb = nm_hyb;
+        } else if (P.qbeam) {
             hbq = P.qbeam[qi];
             hyb = hbq > 0 ? 1 : (hbq < 0 ? 3 : 0);
         } else if (P.adapt && !failed && !routed) {
@@ -853,7 +882,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         }
 
         // ---- Alg. 7 ExpansionPhase
-        if (routed || hyb == 3) {
+        if (routed || hyb == 3 || nm_empty) {
         } else if (!failed && !hyb) {
             int fp = 0;
             while (fp < s.nres) {
@@ -1332,6 +1361,9 @@ void join_setup(JoinRun& r) {
                "work_sharing=hard is not implemented by the GPU join");
     VJ_REQUIRE(ix->p.work_sharing >= 0 && ix->p.work_sharing <= 3, VJ_ERR_ARG, "bad work_sharing");
 
+    VJ_REQUIRE(!ix->nnmap || (ix->p.learned == 0 && !ix->has_route && !ix->has_beam), VJ_ERR_STATE,
+               "an NN-Map index joins from its witnesses: no learned route or per-query plan");
+
     // learned prologue (features -> predictor -> per-query plan) in place of
     // the d1/d2 rule
     r.learned = ix->p.learned != 0;
@@ -1466,6 +1498,17 @@ void join_setup(JoinRun& r) {
     }
     r.gather_bytes = P.xb ? 2 : 4;
     r.soft = ix->p.work_sharing == VJ_WS_SOFT;
+    // NN-Map index: the join expands from the stored witnesses on G_X, with
+    // no greedy phase and no work sharing
+    P.nm_w = nullptr;
+    P.nm_wd = nullptr;
+    P.nm_ood = nullptr;
+    if (ix->nnmap) {
+        P.nm_w = ix->nm_w.p;
+        P.nm_wd = ix->nm_wd.p;
+        P.nm_ood = ix->nm_ood.p;
+        r.soft = false;
+    }
 }
 
 // Traversal workspaces -- the warps' spill space (visited lists, result

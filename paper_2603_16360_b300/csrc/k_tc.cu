@@ -1364,9 +1364,9 @@ __global__ void k_knn_thr(const float* __restrict__ top, int64_t n, float* __res
     thr[i] = t > -INFINITY ? t - fabsf(t) * 3.814697265625e-6f - 1e-30f : -INFINITY;
 }
 
-__global__ void k_iota(int32_t* __restrict__ v, int64_t n) {
+__global__ void k_iota(int32_t* __restrict__ v, int64_t n, int64_t base = 0) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = (int32_t)i;
+    if (i < n) v[i] = (int32_t)(base + i);
 }
 
 __global__ void k_pair_count(const int32_t* __restrict__ cq, int64_t nc, int32_t* __restrict__ counts) {
@@ -1413,12 +1413,14 @@ __global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restri
 bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr,
                           DBuf<float>* cw_out) {
     const int kpad = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
-    if (ix->n < 4096) return false;
+    if (ix->n < 4096 || ix->knn_cols < 4096) return false;
     const bool wide = kpad > RS_MAX_KB * TC_BK;
     cudaStream_t s = ix->stream;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
     const int64_t n = ix->n;
+    // candidate columns: every node, or the data nodes only (NN-Map index)
+    const int64_t ncols = ix->knn_cols;
     DBuf<__nv_bfloat16> abf;
     DBuf<float> top, thr, cw;
     DBuf<int32_t> iota;
@@ -1465,16 +1467,16 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         k_iota<<<vj_div_up(n, 256), 256, 0, s>>>(iota.p, n);
         VJ_LAUNCH_CHECK();
         CUtensorMap ta = make_map(abf.p, n, kpad, 128);
-        CUtensorMap tb = make_map(ix->xbf.p, n, kpad, RS_BN);
+        CUtensorMap tb = make_map(ix->xbf.p, ncols, kpad, RS_BN);
         CUtensorMap tab = cosine ? ta : make_map16(ix->abias.p, 128, 128);
-        CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, n, RS_BN);
+        CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, ncols, RS_BN);
         RsParams R{};
         R.nrows = n;
-        R.ncols = n;
+        R.ncols = ncols;
         R.nkb = kpad / TC_BK;
         R.bias = cosine ? 0 : 1;
         R.nrp = (int)vj_div_up(n, 256);
-        const int nct_all = (int)vj_div_up(n, RS_BN);
+        const int nct_all = (int)vj_div_up(ncols, RS_BN);
         const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
         const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
         R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
@@ -1510,19 +1512,19 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
             k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R);
         });
     } else {
-        // streamed tiles: A and B are both the BF16 copy of every node
+        // streamed tiles: A is the BF16 copy of every node, B of the candidate nodes
         CUtensorMap ta = make_map(ix->xbf.p, n, kpad, WD_BM);
-        CUtensorMap tb = make_map(ix->xbf.p, n, kpad, WD_BN);
+        CUtensorMap tb = make_map(ix->xbf.p, ncols, kpad, WD_BN);
         WdParams W{};
         W.nrows = n;
-        W.ncols = n;
+        W.ncols = ncols;
         W.nkb = kpad / TC_BK;
         W.nrt = (int)vj_div_up(n, WD_BM);
         W.cs = ix->wcs.p;
         W.cb = ix->wcb.p;
         W.err = err.p;
         W.spin_limit = spin_limit;
-        const int nct_all = (int)vj_div_up(n, WD_BN);
+        const int nct_all = (int)vj_div_up(ncols, WD_BN);
         const size_t smem = wide_smem();
         // 1. sample sweep: one unit per 128-row tile over every KNN_SAMPLE-th tile
         W.tstride = KNN_SAMPLE;
@@ -1535,14 +1537,18 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         VJ_LAUNCH_CHECK();
         k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
         VJ_LAUNCH_CHECK();
-        // 2. candidate sweep, rows are node ids.  A = B, so the Gram tiles are
-        // symmetric: row tile rt visits the B tiles from its own 256-row block
-        // on (ct >= rt / 2), and tiles past that block test both directions.
-        // Units: a row tile's run of tpu tiles, ordered by first tile so the
-        // units running together walk the same B tiles (and the longest runs,
-        // of the first row tiles, start first).
+        // 2. candidate sweep, rows are node ids.  Over the candidate rows A = B,
+        // so the Gram tiles are symmetric: row tile rt visits the B tiles from
+        // its own 256-row block on (ct >= rt / 2), and tiles past that block
+        // test both directions.  Units: a row tile's run of tpu tiles, ordered
+        // by first tile so the units running together walk the same B tiles
+        // (and the longest runs, of the first row tiles, start first).  Rows
+        // past the candidate nodes (the queries of an NN-Map index) sweep every
+        // B tile in a second launch.
         W.tstride = 1;
         W.nct = nct_all;
+        W.nrows = ncols;
+        W.nrt = (int)vj_div_up(ncols, WD_BM);
         int64_t tiles = 0;
         for (int rt = 0; rt < W.nrt; rt++) tiles += nct_all - (rt >> 1);
         const int64_t tpu = std::min<int64_t>(nct_all, std::max<int64_t>(64, tiles / (8 * (int64_t)ix->num_sms)));
@@ -1558,13 +1564,32 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         W.thr = thr.p;
         W.a_ids = nullptr;
         W.ncand = ctr.p;
+        // the remaining rows: A starts at row ncols, their ids are ncols + row
+        const int64_t nrest = n - ncols;
+        WdParams W2 = W;
+        CUtensorMap ta2 = ta;
+        if (nrest > 0) {
+            iota.alloc(nrest, s);
+            k_iota<<<vj_div_up(nrest, 256), 256, 0, s>>>(iota.p, nrest, ncols);
+            VJ_LAUNCH_CHECK();
+            ta2 = make_map(ix->xbf.p + (size_t)ncols * kpad, nrest, kpad, WD_BM);
+            W2.nrows = nrest;
+            W2.nrt = (int)vj_div_up(nrest, WD_BM);
+            W2.units = nullptr;
+            W2.tpu = (int)std::min<int64_t>(
+                nct_all, std::max<int64_t>(64, (int64_t)W2.nrt * nct_all / (8 * (int64_t)ix->num_sms)));
+            W2.nunits = W2.nrt * (int)vj_div_up(nct_all, W2.tpu);
+            W2.thr = thr.p + ncols;
+            W2.a_ids = iota.p;
+        }
         VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         sweep([&](int32_t* pq, int32_t* px, float* pw, int64_t c) {
-            W.cq = pq;
-            W.cx = px;
-            W.cw = pw;
-            W.cap = c;
+            W.cq = W2.cq = pq;
+            W.cx = W2.cx = px;
+            W.cw = W2.cw = pw;
+            W.cap = W2.cap = c;
             k_tc_wide<EPI_SCAN><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta, tb, W);
+            if (nrest > 0) k_tc_wide<EPI_SCAN><<<std::min(W2.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta2, tb, W2);
         });
     }
     const int64_t nc = (int64_t)hn;

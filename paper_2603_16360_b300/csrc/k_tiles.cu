@@ -185,9 +185,9 @@ __device__ __forceinline__ void list_insert(float* Lk, int* Li, float k, int id,
 
 template <int KP>
 __global__ void __launch_bounds__(TT) k_knn_sweep(const float* __restrict__ vec, const float* __restrict__ sqn,
-                                                   const float* __restrict__ invn, int dp, int64_t n, int metric,
-                                                   int32_t* __restrict__ cand_id, float* __restrict__ cand_key,
-                                                   float* __restrict__ row_thr) {
+                                                   const float* __restrict__ invn, int dp, int64_t n, int64_t ncols,
+                                                   int metric, int32_t* __restrict__ cand_id,
+                                                   float* __restrict__ cand_key, float* __restrict__ row_thr) {
     extern __shared__ __align__(16) unsigned char sraw[];
     KnnSmem<KP>& S = *reinterpret_cast<KnnSmem<KP>*>(sraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -203,19 +203,20 @@ __global__ void __launch_bounds__(TT) k_knn_sweep(const float* __restrict__ vec,
         int64_t r = ra + tile_row(i);
         rn[i] = r < n ? (metric == 0 ? sqn[r] : invn[r]) : 0.f;
     }
-    for (int64_t ca = 0; ca < n; ca += TBN) {
+    // candidates: nodes 0 .. ncols-1 (every node, or the data nodes only)
+    for (int64_t ca = 0; ca < ncols; ca += TBN) {
         float acc[8][8];
-        gram_tile(vec, dp, ra, n, ca, n, acc, S.u.g);
+        gram_tile(vec, dp, ra, n, ca, ncols, acc, S.u.g);
         // keys into the tile (the gram buffers are dead after the last sync)
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             int64_t c = ca + tile_col(j);
-            float cn = c < n ? (metric == 0 ? sqn[c] : invn[c]) : 0.f;
+            float cn = c < ncols ? (metric == 0 ? sqn[c] : invn[c]) : 0.f;
 #pragma unroll
             for (int i = 0; i < 8; i++) {
                 int64_t r = ra + tile_row(i);
                 float key;
-                if (c >= n || r >= n || c == r) key = FLT_MAX;
+                if (c >= ncols || r >= n || c == r) key = FLT_MAX;
                 else if (metric == 0) key = fmaxf(rn[i] + cn - 2.f * acc[i][j], 0.f);
                 else key = 1.f - acc[i][j] * rn[i] * cn;
                 S.u.D[tile_row(i)][tile_col(j)] = key;
@@ -677,11 +678,11 @@ __global__ void __launch_bounds__(KC_WPB * 32)
 }
 
 // ---------------------------------------------------------------- fallback
-// warp per uncertified row: brute-force top-K' over all nodes with
+// warp per uncertified row: brute-force top-K' over all candidate nodes with
 // direct-difference keys, then the same re-rank (run again on its output)
 template <int G, int NPL>
 __global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ vec, const float* __restrict__ invn,
-                                                      int dp, int64_t n, int metric, int KP,
+                                                      int dp, int64_t ncols, int metric, int KP,
                                                       const int32_t* __restrict__ rows, int nrows,
                                                       int32_t* __restrict__ cand_id, float* __restrict__ row_thr) {
     __shared__ int cid[8][128];
@@ -700,8 +701,8 @@ __global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ v
     float4 q[NPL];
     load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
     const float invq = metric ? invn[r] : 0.f;
-    for (int64_t c0 = 0; c0 < n; c0 += 128) {
-        int nc = (n - c0) < 128 ? (int)(n - c0) : 128;
+    for (int64_t c0 = 0; c0 < ncols; c0 += 128) {
+        int nc = (ncols - c0) < 128 ? (int)(ncols - c0) : 128;
         for (int e = lane; e < 128; e += 32) cid[warp][e] = (int)(c0 + e);
         __syncwarp();
         group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, cid[warp], nc, ckey[warp], lane);
@@ -837,7 +838,7 @@ static void run_sweep(vj_index* ix, int32_t* cid, float* ckey, float* thr) {
     size_t smem = sizeof(KnnSmem<KP>);
     VJ_CUDA(cudaFuncSetAttribute(k_knn_sweep<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_knn_sweep<KP><<<vj_div_up(ix->n, TBM), TT, smem, ix->stream>>>(ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, ix->n,
-                                                                     ix->metric, cid, ckey, thr);
+                                                                     ix->knn_cols, ix->metric, cid, ckey, thr);
     VJ_LAUNCH_CHECK();
 }
 
@@ -921,7 +922,7 @@ void vj_build_knn(vj_index* ix) {
         // exact row scans for the uncertified rows, then re-rank them again
         // (their scans fill cid / thr at the rows' own positions)
         VJ_DISPATCH_GN(dp4, (k_knn_rowscan<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
-                                ix->vec.p, ix->invn.p, ix->dp, n, ix->metric, KP, bad.p, hb, cid.p, thr.p)));
+                                ix->vec.p, ix->invn.p, ix->dp, ix->knn_cols, ix->metric, KP, bad.p, hb, cid.p, thr.p)));
         VJ_LAUNCH_CHECK();
         // the row scans saw every node, so these rows certify on re-rank
         DBuf<int32_t> bad2;

@@ -103,6 +103,9 @@ static void free_index(vj_index* ix) {
     ix->xbf.free_(s);
     ix->wcs.free_(s);
     ix->wcb.free_(s);
+    ix->nm_w.free_(s);
+    ix->nm_wd.free_(s);
+    ix->nm_ood.free_(s);
     ix->xbias.free_(s);
     ix->abias.free_(s);
     ix->done.free_(s);
@@ -162,6 +165,7 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         VJ_REQUIRE(p.knn_k >= p.degree && p.knn_k <= 112, VJ_ERR_ARG, "knn_k must be in [degree, 112]");
         VJ_REQUIRE(p.precision == VJ_PREC_FP32 || p.precision == VJ_PREC_BF16, VJ_ERR_ARG,
                    "build tiles: FP32 or BF16 (FP8 is not implemented)");
+        VJ_REQUIRE(p.nnmap == 0 || p.nnmap == 1, VJ_ERR_ARG, "nnmap must be 0 or 1");
         check_join_params(p);
 
         ix = new vj_index();
@@ -183,6 +187,15 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         ix->R = std::min(ix->R, ix->K);
         ix->metric = metric;
         ix->p = p;
+        ix->nnmap = p.nnmap != 0;
+        // an NN-Map index lists data candidates only, and only data rows enter the graph
+        ix->knn_cols = ix->nnmap ? nx : ix->n;
+        ix->graph_rows = ix->nnmap ? nx : ix->n;
+        if (ix->nnmap) {
+            VJ_REQUIRE(nx >= 2, VJ_ERR_ARG, "an NN-Map index needs nx >= 2");
+            ix->K = (int)std::min<int64_t>(ix->K, nx - 1);
+            ix->R = std::min(ix->R, ix->K);
+        }
         cudaStream_t s = ix->stream;
         ix->vec.alloc((size_t)ix->n * ix->dp, s);
         if (ix->dp != d) VJ_CUDA(cudaMemsetAsync(ix->vec.p, 0, (size_t)ix->n * ix->dp * sizeof(float), s));
@@ -201,6 +214,7 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         vj_build_knn(ix);
         VJ_CUDA(cudaEventRecord(b1, s));
         vj_build_graph(ix);
+        if (ix->nnmap) vj_build_nnmap(ix);
         VJ_CUDA(cudaEventRecord(b2, s));
         VJ_CUDA(cudaStreamSynchronize(s));
         float mb = 0.f, mk = 0.f;
@@ -254,6 +268,8 @@ extern "C" vj_status vj_set_wait_test(vj_index* ix, long long max_polls, int64_t
 extern "C" vj_status vj_set_plan(vj_index* ix, const uint8_t* route, const int32_t* beam) {
     return guarded([&] {
         VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        VJ_REQUIRE(!ix->nnmap || (route == nullptr && beam == nullptr), VJ_ERR_STATE,
+                   "an NN-Map index joins from its witnesses: no per-query plan");
         cudaStream_t s = ix->stream;
         const int64_t nq = ix->nq;
         ix->has_route = false;
@@ -401,6 +417,19 @@ static vj_status join_impl(vj_index* ix, float eps, int budget, vj_result** out,
         }
         r->stats = st;
         *out = r;
+    });
+}
+
+extern "C" vj_status vj_export_nnmap(const vj_index* ix, int32_t* witness, double* wdist, uint8_t* ood) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        VJ_REQUIRE(ix->nnmap, VJ_ERR_STATE, "the index was built without nnmap");
+        cudaStream_t s = ix->stream;
+        if (witness)
+            VJ_CUDA(cudaMemcpyAsync(witness, ix->nm_w.p, ix->nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (wdist) VJ_CUDA(cudaMemcpyAsync(wdist, ix->nm_wd.p, ix->nq * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (ood) VJ_CUDA(cudaMemcpyAsync(ood, ix->nm_ood.p, ix->nq, cudaMemcpyDeviceToHost, s));
+        VJ_CUDA(cudaStreamSynchronize(s));
     });
 }
 

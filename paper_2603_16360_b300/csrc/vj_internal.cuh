@@ -137,6 +137,15 @@ struct vj_index {
     bool bf16_lossless = false;  // every coordinate is exactly a BF16 value
     bool cos_raw = false;      // cosine, streamed tiles: xbf holds the raw (not unit) rows, scaled in the epilogue
     DBuf<float> wcs, wcb;      // [n] streamed tiles: per-column scale and bias of the accumulator
+    // NN-Map index (the paper's closing design): kNN lists over data columns
+    // only, the graph G_X over data rows only, and per query its witness
+    // (nearest data vector), the witness's FP64 distance and the OOD bit
+    bool nnmap = false;
+    int64_t knn_cols = 0;      // kNN candidates are nodes 0..knn_cols-1 (n, or nx for an NN-Map index)
+    int64_t graph_rows = 0;    // nodes with a graph row (n, or nx for an NN-Map index)
+    DBuf<int32_t> nm_w;        // [nq] witness
+    DBuf<double> nm_wd;        // [nq] its distance (FP64)
+    DBuf<uint8_t> nm_ood;      // [nq] OOD bit
     long long wait_polls = 0;  // dependency-wait limit of the traversal (0: the default)
     int hold_q = -1;           // test knob: a query that never publishes its cache (-1: none)
     double maxnorm = 0.0;      // largest vector norm (FP64)
@@ -183,6 +192,8 @@ struct vj_index {
 void vj_build_knn(vj_index* ix);
 // graph: prune + reverse edges + entry + edge lengths + MST order
 void vj_build_graph(vj_index* ix);
+// NN-Map: witness, FP64 witness distance and OOD bit of every query
+void vj_build_nnmap(vj_index* ix);
 // exact join pairs into CSR (device arrays owned by the caller-provided buffers)
 struct CsrOut {
     int64_t nnz;

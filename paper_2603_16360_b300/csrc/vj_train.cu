@@ -94,6 +94,7 @@ struct PlanGuard {
 
 void check_train_args(vj_index* ix, float eps, const int32_t* rows, int64_t n, const vj_train_params* tp) {
     VJ_REQUIRE(ix && rows && tp && n >= 1, VJ_ERR_ARG, "NULL argument or no training rows");
+    VJ_REQUIRE(!ix->nnmap, VJ_ERR_STATE, "an NN-Map index joins from its witnesses: nothing to plan or train");
     VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
     VJ_REQUIRE(tp->n_ladder >= 1 && tp->n_ladder <= 8, VJ_ERR_ARG, "n_ladder must be 1..8");
     for (int k = 0; k < tp->n_ladder; k++)

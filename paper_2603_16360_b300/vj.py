@@ -27,7 +27,8 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_default_params", "vj_build", "vj_set_stream", "vj_set_join_params", "vj_set_plan", "vj_join",
            "vj_join_device", "vj_join_batch", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error", "vj_set_wait_test",
-           "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor", "vj_join_switched"]
+           "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor", "vj_join_switched",
+           "vj_export_nnmap"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
 
@@ -47,7 +48,7 @@ class vj_params(C.Structure):
                 ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
                 ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
                 ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64),
-                ("gather", C.c_int), ("hybrid_seed_best", C.c_int)]
+                ("gather", C.c_int), ("hybrid_seed_best", C.c_int), ("nnmap", C.c_int)]
 
 
 class vj_stats(C.Structure):
@@ -137,6 +138,8 @@ def load():
     lib.vj_export_graph.restype = I
     lib.vj_export_knn.argtypes = [P, P, P]
     lib.vj_export_knn.restype = I
+    lib.vj_export_nnmap.argtypes = [P, P, P, P]
+    lib.vj_export_nnmap.restype = I
     lib.vj_index_info.argtypes = [P, P, P, P, P, P, P]
     lib.vj_index_info.restype = I
     lib.vj_build_info.argtypes = [P, P, P, P, P]
@@ -586,3 +589,14 @@ def vj_export_knn(ix: Index):
     keys = np.zeros((n, inf["knn_k"]), np.float32)
     _check(load().vj_export_knn(ix.handle, ids.ctypes.data, keys.ctypes.data))
     return ids, keys
+
+
+def vj_export_nnmap(ix: Index):
+    """(witness [nq] int32, wdist [nq] float64, ood [nq] uint8) of an index
+    built with nnmap=1."""
+    nq = ix.info()["nq"]
+    w = np.zeros(nq, np.int32)
+    wd = np.zeros(nq, np.float64)
+    ood = np.zeros(nq, np.uint8)
+    _check(load().vj_export_nnmap(ix.handle, w.ctypes.data, wd.ctypes.data, ood.ctypes.data))
+    return w, wd, ood
