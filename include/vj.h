@@ -50,7 +50,9 @@ typedef enum {
 
 /* cfg.work_sharing of Tab. cfg (Sec. 4.1).  Under the merged index, SOFT also
  * seeds the query node itself (S = {entry, q} U C[parent]); SELF is the
- * paper's default merged mode (S = {entry, q}). */
+ * paper's default merged mode (S = {entry, q}).  HARD (HWS: the parent's result
+ * row as seeds) runs on separate indexes only (vj_params.separate); a join of
+ * a merged index with HARD returns VJ_ERR_ARG. */
 enum { VJ_WS_NONE = 0, VJ_WS_HARD = 1, VJ_WS_SOFT = 2, VJ_WS_SELF = 3 };
 
 enum { VJ_PREC_FP32 = 0, VJ_PREC_BF16 = 1, VJ_PREC_FP8 = 2 };
@@ -93,6 +95,18 @@ typedef struct {
                              force_hybrid, or adapt_hybrid and the OOD bit), with no work
                              sharing.  steps counts distance evaluations (the stored witness
                              distance costs none); default 0 */
+    int separate;         /* build: 1 = separate (per-set) indexes (Sec. 3.2): the data graph G_Y
+                             over the data rows and the query graph over the query rows (each
+                             row's kNN list ranks its own set only), the entry s_Y nearest the
+                             data centroid, and the MST over the query graph plus a star edge
+                             (s_Y, q) per query.  vj_join on it runs Alg. 1 with Alg. 4-5's
+                             best-first greedy search on G_Y (queue trimmed to greedy_beam after
+                             each expansion, stopped by an in-range front or conv_threshold
+                             checks without a smaller front key) from S = {s_Y} (INLJ:
+                             work_sharing NONE or SELF), {s_Y, C[parent]} (SOFT) or {s_Y} plus
+                             the parent's result row (HARD); with sharing, queries run parents
+                             first.  adapt_hybrid does not apply (the rule reads the merged
+                             graph); force_hybrid does.  Exclusive with nnmap; default 0 */
 } vj_params;
 
 /* Per-call counters and device timings of a join. */

@@ -762,7 +762,9 @@ void vj_build_graph(vj_index* ix) {
     VJ_CUDA(cudaMemsetAsync(nr.p, 0, sizeof(unsigned long long), s));
 
     // nodes with a graph row: every node, or the data nodes only (G_X of an
-    // NN-Map index, whose kNN lists hold data nodes only)
+    // NN-Map index, whose kNN lists hold data nodes only).  Separate indexes
+    // keep both sets' rows: their lists never cross sets, so neither do the
+    // pruned and reverse edges
     const int64_t gr = ix->graph_rows;
 
     // ---- 1. prune
@@ -857,23 +859,25 @@ void vj_build_graph(vj_index* ix) {
     uid.free_(s);
     uk.free_(s);
 
-    // ---- 3. entry point (over the nodes with a graph row)
+    // ---- 3. entry point: the node nearest the centroid of nodes 0 .. entry_rows-1
+    // (every node of a merged index; the data set of NN-Map and separate indexes)
     {
-        const int nblk = (int)std::min<int64_t>(1024, std::max<int64_t>(1, gr / 256));
-        const int64_t rpb = (gr + nblk - 1) / nblk;
+        const int64_t er = ix->entry_rows;
+        const int nblk = (int)std::min<int64_t>(1024, std::max<int64_t>(1, er / 256));
+        const int64_t rpb = (er + nblk - 1) / nblk;
         DBuf<double> part, cen, bd;
         DBuf<int32_t> bi, ent;
         part.alloc((size_t)nblk * d, s);
         cen.alloc(d, s);
-        k_centroid_part<<<nblk, 128, 0, s>>>(ix->vec.p, dp, d, gr, rpb, part.p);
+        k_centroid_part<<<nblk, 128, 0, s>>>(ix->vec.p, dp, d, er, rpb, part.p);
         VJ_LAUNCH_CHECK();
-        k_centroid_final<<<1, 256, 0, s>>>(part.p, nblk, d, gr, cen.p);
+        k_centroid_final<<<1, 256, 0, s>>>(part.p, nblk, d, er, cen.p);
         VJ_LAUNCH_CHECK();
         const int eb = 512;
         bd.alloc(eb, s);
         bi.alloc(eb, s);
         ent.alloc(1, s);
-        k_entry_part<<<eb, CB, 0, s>>>(ix->vec.p, dp, d, gr, metric, cen.p, bd.p, bi.p);
+        k_entry_part<<<eb, CB, 0, s>>>(ix->vec.p, dp, d, er, metric, cen.p, bd.p, bi.p);
         VJ_LAUNCH_CHECK();
         k_entry_final<<<1, 1, 0, s>>>(bd.p, bi.p, eb, ent.p);
         VJ_LAUNCH_CHECK();

@@ -125,7 +125,8 @@ struct JoinParams {
     uint8_t* hyb2;
     int32_t* count2;
     int64_t* seg2;
-    int mode;              // 0: no soft sharing; soft sharing: 1 pass 1, 3 pass 2, 2 pass 3
+    int mode;              // 0: no soft sharing; soft sharing: 1 pass 1, 3 pass 2, 2 pass 3;
+                           // 4: separate indexes with sharing, one pass in MST order
     const uint8_t* route;  // per-query plan (nullptr: none)
     const int32_t* qbeam;
     const int* order;      // dispatch order of pass 2 (MST BFS order: parents first)
@@ -161,6 +162,11 @@ struct JoinParams {
     const int32_t* nm_w;
     const double* nm_wd;
     const uint8_t* nm_ood;
+    // separate (per-set) indexes: the greedy phase is Alg. 4-5's best-first
+    // search on G_Y from s_Y (plus the parent's cache or result row), its
+    // queue trimmed to gbeam after each expansion
+    int separate;
+    int gbeam;
 };
 
 enum { QF_PROBED = 1 };
@@ -431,6 +437,50 @@ __device__ __forceinline__ int lower_rank(const float* Lk, const int* Li, int n,
     return lo;
 }
 
+// The separate-index greedy queue: fold one candidate per lane (`valid`)
+// into the ascending queue W.qk/qi[cur][head .. head + np), keeping the
+// `cap` smallest (key, id); the result lands at the start of the other
+// buffer.  Keys are distinct pairs (every node is queued once).
+__device__ __forceinline__ void pq_merge(WarpSpace& W, WarpSmem* S, int& cur, int& head, int& np, bool valid, float k,
+                                         int id, int cap, int lane) {
+    float nk = valid ? k : FLT_MAX;
+    int ni = valid ? id : INT32_MAX;
+    const int m = __popc(__ballot_sync(VJ_FULL, valid));
+    if (m == 0) return;
+    warp_sort_pairs(nk, ni, lane);
+    __syncwarp();
+    if (lane < m) {
+        S->ckey[lane] = nk;
+        S->cand[lane] = ni;
+    }
+    __syncwarp();
+    const float* ok_ = W.qk[cur] + head;
+    const int* oi_ = W.qi[cur] + head;
+    float* dk = W.qk[cur ^ 1];
+    int* di = W.qi[cur ^ 1];
+    const int kfin = min(np + m, cap);
+    for (int i = lane; i < np; i += 32) {
+        const float a = ok_[i];
+        const int b = oi_[i];
+        const int pos = i + lower_rank(S->ckey, S->cand, m, a, b);
+        if (pos < kfin) {
+            dk[pos] = a;
+            di[pos] = b;
+        }
+    }
+    if (lane < m) {
+        const int pos = lane + lower_rank(ok_, oi_, np, nk, ni);
+        if (pos < kfin) {
+            dk[pos] = nk;
+            di[pos] = ni;
+        }
+    }
+    __syncwarp();
+    cur ^= 1;
+    head = 0;
+    np = kfin;
+}
+
 // per-warp statistics, flushed into the instance's counters
 struct JoinCounters {
     long long dist = 0, exp = 0, adj = 0, hyb = 0, rechk = 0, spill = 0;
@@ -476,7 +526,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
     long long &c_dist = cnt.dist, &c_exp = cnt.exp, &c_adj = cnt.adj, &c_hyb = cnt.hyb, &c_rechk = cnt.rechk,
               &c_spill = cnt.spill;
     {
-        const int qi = P.mode == 2 ? P.order[t] : P.order1[t];
+        const int qi = (P.mode == 2 || P.mode == 4) ? P.order[t] : P.order1[t];
         const int64_t qn = P.nx + qi;
 
         float4 q[NPL];
@@ -624,6 +674,49 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
         }
 
+        // ---- separate indexes with hard or soft sharing (mode 4): one pass in
+        // MST order, each query waiting (bounded acquire spin) for its
+        // parent's final cache (soft) or result row (hard) before it starts
+        int hcnt = 0;
+        int64_t hseg = 0;
+        if (P.mode == 4) {
+            const int par = __ldg(P.parent + qi);
+            int ok = 1;
+            if (par >= 0 && lane == 0) {
+                long long spins = 0;
+                unsigned ns = 32;
+                for (;;) {
+                    if (ld_acquire(P.done + par)) {
+                        if (P.ws == VJ_WS_SOFT) {
+                            seedc = *((volatile int*)(P.cache + par));
+                        } else {
+                            hseg = *((volatile int64_t*)(P.seg + par));
+                            hcnt = *((volatile int*)(P.count + par));
+                            // an overflowed pool holds no row (the host re-runs the join)
+                            if (hseg + hcnt > P.pool_cap || hcnt < 0) hcnt = 0;
+                        }
+                        break;
+                    }
+                    if (*((volatile unsigned long long*)(P.ctr + C_ABORT))) {
+                        ok = 0;
+                        break;
+                    }
+                    if (++spins > P.spin_limit) {
+                        raise_err(P, VJ_DERR_WAIT_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 256) ns <<= 1;
+                }
+            }
+            ok = __shfl_sync(VJ_FULL, ok, 0);
+            if (!ok) return true;
+            seedc = __shfl_sync(VJ_FULL, seedc, 0);
+            hcnt = __shfl_sync(VJ_FULL, hcnt, 0);
+            hseg = __shfl_sync(VJ_FULL, hseg, 0);
+        }
+
         QueryState s;
         s.tab = S->htab;
         s.mask = HCAP - 1;
@@ -669,6 +762,96 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 const float wk = P.metric == 0 ? (float)(wd * wd) : (float)wd;
                 best_update(P, s, lane == 0, wk, w, lane);
                 if (!append_results(P, s, lane == 0, w, wk, W, lane)) failed = true;
+            }
+        } else if (P.separate) {
+            // ---- Alg. 3 seeds on the per-set index G_Y: s_Y, then C[parent]
+            // (soft) or the parent's result row (hard); Alg. 4 evaluates them
+            // all (the visited set drops repeats) and queues them.  Only the
+            // gbeam + 1 smallest queued seeds can survive the first trim (one
+            // pop, then the queue keeps gbeam), so the queue keeps those.
+            const int nsc = seedc >= 0 ? 1 : 0;
+            const int nseed = 1 + nsc + hcnt;
+            int cur = 0, head = 0, np = 0;  // the queue: W.qk/qi[cur][head .. head + np), ascending
+            for (int base = 0; base < nseed && !failed; base += 32) {
+                const int j = base + lane;
+                int v = -1;
+                if (j == 0) v = P.entry;
+                else if (j == 1 && nsc) v = seedc;
+                else if (j < nseed) v = __ldcg(P.pool_id + hseg + (j - 1 - nsc));
+                if (v >= P.nx) v = -1;
+                if (!vis_reserve(P, s, 32, W, lane, c_spill)) {
+                    failed = true;
+                    break;
+                }
+                const bool nw = v >= 0 && vis_insert(s, W, v);
+                const unsigned nm = __ballot_sync(VJ_FULL, nw);
+                const int nc = __popc(nm);
+                if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
+                __syncwarp();
+                if (nc == 0) continue;
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb,
+                                      P.kpb);
+                __syncwarp();
+                s.nvis += nc;
+                const bool val = lane < nc;
+                const int cv = val ? S->cand[lane] : -1;
+                const float ck = val ? S->ckey[lane] : FLT_MAX;
+                __syncwarp();
+                const bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
+                best_update(P, s, val, ck, cv, lane);
+                if (!append_results(P, s, in, cv, ck, W, lane)) {
+                    failed = true;
+                    break;
+                }
+                pq_merge(W, S, cur, head, np, val, ck, cv, P.gbeam + 1, lane);
+            }
+            // ---- Alg. 4-5: pop the front and evaluate its G_Y neighbours until
+            // StopGreedy: the front is an in-range data node (on G_Y: some
+            // in-range node has been found, since every in-range key is below
+            // every out-range one), or the front key has not decreased for
+            // conv_threshold consecutive checks
+            float best_front = INFINITY;
+            int noimp = 0;
+            while (!failed && np > 0) {
+                if (s.nres > 0) break;
+                const float fk = W.qk[cur][head];
+                const int u = W.qi[cur][head];
+                if (fk < best_front) {
+                    best_front = fk;
+                    noimp = 0;
+                } else {
+                    noimp++;
+                }
+                if (noimp >= P.conv) break;
+                head++;
+                np--;
+                c_adj++;
+                if (!vis_reserve(P, s, R, W, lane, c_spill)) {
+                    failed = true;
+                    break;
+                }
+                const int v = lane < R ? __ldg(P.adj + (int64_t)u * R + lane) : -1;
+                const bool nw = v >= 0 && v < P.nx && vis_insert(s, W, v);
+                const unsigned nm = __ballot_sync(VJ_FULL, nw);
+                const int nc = __popc(nm);
+                if (nw) S->cand[__popc(nm & ((1u << lane) - 1u))] = v;
+                __syncwarp();
+                if (nc == 0) continue;
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb,
+                                      P.kpb);
+                __syncwarp();
+                s.nvis += nc;
+                const bool val = lane < nc;
+                const int cv = val ? S->cand[lane] : -1;
+                const float ck = val ? S->ckey[lane] : FLT_MAX;
+                __syncwarp();
+                const bool in = inrange_decide(P, val, ck, cv, qn, lane, c_rechk);
+                best_update(P, s, val, ck, cv, lane);
+                if (!append_results(P, s, in, cv, ck, W, lane)) {
+                    failed = true;
+                    break;
+                }
+                pq_merge(W, S, cur, head, np, val, ck, cv, P.gbeam, lane);
             }
         } else {
             // ---- Alg. 4 greedy: the seeds (lanes 0..2: entry, cached seed, q)
@@ -774,7 +957,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         } else if (P.qbeam) {
             hbq = P.qbeam[qi];
             hyb = hbq > 0 ? 1 : (hbq < 0 ? 3 : 0);
-        } else if (P.adapt && !failed && !routed) {
+        } else if (P.adapt && !P.separate && !failed && !routed) {
             if (!probe) {
                 // no probe ran (a seed was the greedy front); the rule still
                 // reads q's neighbourhood, evaluated here outside V
@@ -1146,12 +1329,19 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             }
         }
         __syncwarp();
+        if (P.mode == 4) {
+            // publish: the cache, count, segment and pooled row are visible
+            // to whoever sees the flag
+            __threadfence();
+            __syncwarp();
+            if (lane == 0 && qi != P.hold_q) st_release(P.done + qi, 1);
+        }
     }
     return false;
 }
 
 __device__ __forceinline__ int pass_ticket_slot(int mode) {
-    return mode == 2 ? C_TICKET2 : mode == 3 ? C_TICKET3 : C_TICKET;
+    return (mode == 2 || mode == 4) ? C_TICKET2 : mode == 3 ? C_TICKET3 : C_TICKET;
 }
 
 // one join pass over one index: warps take queries from the pass's ticket
@@ -1333,6 +1523,7 @@ struct JoinRun {
     float eps = 0.f;
     int budget = 0;
     bool learned = false, soft = false;
+    bool wait_first = false;  // separate indexes with sharing: one pass, parents first (mode 4)
     double ms_pro = 0.0;
     JoinParams P;
     JoinDispatch jd;
@@ -1357,8 +1548,8 @@ void join_setup(JoinRun& r) {
     const int64_t nq = ix->nq;
     VJ_REQUIRE(ix->d <= 4096 && ix->dp / 4 <= 1024, VJ_ERR_ARG, "d too large for the join kernel");
     VJ_REQUIRE(ix->R <= 32, VJ_ERR_ARG, "the GPU join supports degree <= 32");
-    VJ_REQUIRE(ix->p.work_sharing != VJ_WS_HARD, VJ_ERR_ARG,
-               "work_sharing=hard is not implemented by the GPU join");
+    VJ_REQUIRE(ix->p.work_sharing != VJ_WS_HARD || ix->separate, VJ_ERR_ARG,
+               "work_sharing=hard runs on separate indexes only (the merged index's hard sharing is not built)");
     VJ_REQUIRE(ix->p.work_sharing >= 0 && ix->p.work_sharing <= 3, VJ_ERR_ARG, "bad work_sharing");
 
     VJ_REQUIRE(!ix->nnmap || (ix->p.learned == 0 && !ix->has_route && !ix->has_beam), VJ_ERR_STATE,
@@ -1410,7 +1601,9 @@ void join_setup(JoinRun& r) {
     if (gmax < GCAP0) gmax = GCAP0;
     const int grcap = gmax / 2;
     const int hbeam = r.budget > 0 ? r.budget : ix->p.hybrid_beam;
-    const int oqcap = std::max(hbeam, ix->has_beam ? ix->plan_max_beam : 0) + 2;
+    // the out-range queue; on separate indexes also the greedy queue (gbeam + 1 seeds)
+    const int oqcap = std::max(std::max(hbeam, ix->has_beam ? ix->plan_max_beam : 0),
+                               ix->separate ? ix->p.greedy_beam + 1 : 0) + 2;
     r.wstride = ((int64_t)2 * gmax + 2 * grcap + 4 * oqcap + 31) / 32 * 32;
     r.vwords = (ix->n + 31) / 32;
     if (ix->pool_id.n == 0) {
@@ -1503,6 +1696,12 @@ void join_setup(JoinRun& r) {
     P.nm_w = nullptr;
     P.nm_wd = nullptr;
     P.nm_ood = nullptr;
+    P.separate = ix->separate ? 1 : 0;
+    P.gbeam = ix->p.greedy_beam;
+    if (ix->separate) {
+        r.soft = false;
+        r.wait_first = ix->p.work_sharing == VJ_WS_SOFT || ix->p.work_sharing == VJ_WS_HARD;
+    }
     if (ix->nnmap) {
         P.nm_w = ix->nm_w.p;
         P.nm_wd = ix->nm_wd.p;
@@ -1623,7 +1822,7 @@ void bind_pool(JoinRun& r) {
 // counters and publish flags of one attempt
 void reset_attempt(JoinRun& r, cudaStream_t s) {
     VJ_CUDA(cudaMemsetAsync(r.ix->ctr.p, 0, 16 * sizeof(unsigned long long), s));
-    if (r.soft) VJ_CUDA(cudaMemsetAsync(r.ix->done.p, 0, r.ix->nq * sizeof(int32_t), s));
+    if (r.soft || r.wait_first) VJ_CUDA(cudaMemsetAsync(r.ix->done.p, 0, r.ix->nq * sizeof(int32_t), s));
 }
 
 // after an attempt: true when the pool overflowed (then it is grown: run
@@ -1793,7 +1992,7 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
             r.jd.launch(P, r.jd.blocks, s);
             r.launches += 2;
         } else {
-            P.mode = 0;
+            P.mode = r.wait_first ? 4 : 0;
             r.jd.launch(P, r.jd.blocks, s);
         }
         VJ_CUDA(cudaEventRecord(ev.e[3], s));
@@ -1882,7 +2081,7 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
                     B.qstart[0] = 0;
                     for (int k = 0; k < nb; k++) {
                         JoinRun& r = runs[members[c0 + k]];
-                        B.p[k].mode = r.soft ? soft_modes[ps] : 0;
+                        B.p[k].mode = r.soft ? soft_modes[ps] : (r.wait_first ? 4 : 0);
                         const int64_t qk = (r.soft || ps == 0) ? r.ix->nq : 0;
                         B.qstart[k + 1] = B.qstart[k] + qk;
                         if (ps > 0 && r.soft) r.launches++;

@@ -121,6 +121,8 @@ struct WdParams {
     // (ct > rt / 2) also tests the transposed pairs (c, r): acc * cs[r] + cb[r]
     // > thr[c], so each unordered pair is computed once
     const int4* units;
+    // node ids of A row 0 (when a_ids is nullptr) and of B row 0
+    int64_t row_base, col_base;
 };
 
 // (row tile, first tile, end tile) of work unit u
@@ -173,7 +175,7 @@ __device__ __forceinline__ void wd_append(const WdParams& P, const uint32_t (&va
             const int j = __ffs(hit) - 1;
             hit &= hit - 1;
             if ((int64_t)gq < P.cap) {
-                const int col = (int)(c0 + hh * 32 + j);
+                const int col = (int)(P.col_base + c0 + hh * 32 + j);
                 P.cq[gq] = transposed ? col : rowid;
                 P.cx[gq] = transposed ? rowid : col;
                 if (P.cw) {
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
             const int64_t r = (int64_t)rt * WD_BM + quarter * 32 + lane;
             const bool rv = r < P.nrows;
             const float thr = (EPI == EPI_SCAN && rv) ? P.thr[r] : INFINITY;
-            const int qid = rv ? (P.a_ids ? P.a_ids[r] : (int)r) : -1;
+            const int qid = rv ? (P.a_ids ? P.a_ids[r] : (int)(P.row_base + r)) : -1;
             // symmetric sweep: this row as a B row (scale and bias of the transposed test)
             const float rcs = (P.units && rv) ? P.cs[r] : 0.f;
             const float rcb = (P.units && rv) ? P.cb[r] : -INFINITY;
@@ -389,13 +391,13 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                         const float mx = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
                         if constexpr (EPI == EPI_SAMPLE) {
                             if (!rv || !(mx > t[WD_TOP - 1])) continue;
-                            const int64_t c0 = cbase_col + col0;
-                            const bool self_here = r >= c0 && r < c0 + 64;
+                            const int64_t c0 = P.col_base + cbase_col + col0;  // node id of the first column
+                            const bool self_here = qid >= c0 && qid < c0 + 64;
 #pragma unroll
                             for (int j = 0; j < 64; j++) {
                                 float x = fmaf(__uint_as_float(va[j]), S.cs[acc][col0 + j], S.cb[acc][col0 + j]);
                                 if (!(x > t[WD_TOP - 1])) continue;
-                                if (self_here && c0 + j == r) continue;
+                                if (self_here && c0 + j == qid) continue;
                                 // insert: x sinks to its place, the last value drops out
 #pragma unroll
                                 for (int k = 0; k < WD_TOP; k++) {
@@ -554,8 +556,9 @@ struct RsParams {
     int* err;
     long long spin_limit;
     int tstride;          // data tile t of a unit is tile t * tstride (1: every tile)
-    // sample epilogue: the rows' node ids equal their row index
+    // sample epilogue: the rows' node ids are row_base + row, the columns' col_base + column
     float* top16;         // [nrows] 16th largest accumulator over the sampled tiles (other nodes)
+    int64_t row_base, col_base;
 };
 
 constexpr int KN_EPI = 8;  // sample epilogue warps: one per (query block, lane quarter)
@@ -790,12 +793,13 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
                         m3 = fmaxf(m3, __uint_as_float(va[j + 3]));
                     }
                     if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) <= t[15]) continue;
-                    const bool edge = c0 + 64 > P.ncols || (r >= c0 && r < c0 + 64);
+                    const int64_t rg = P.row_base + r, cg = P.col_base + c0;  // node ids
+                    const bool edge = c0 + 64 > P.ncols || (rg >= cg && rg < cg + 64);
 #pragma unroll
                     for (int j = 0; j < 64; j++) {
                         float x = __uint_as_float(va[j]);
                         if (x <= t[15]) continue;
-                        if (edge && (c0 + j >= P.ncols || c0 + j == r)) continue;
+                        if (edge && (c0 + j >= P.ncols || cg + j == rg)) continue;
                         // insert: x sinks to its place, the 16th value drops out
 #pragma unroll
                         for (int k = 0; k < 16; k++) {
@@ -904,7 +908,7 @@ __global__ void __launch_bounds__((2 + (EPI == EPI_SAMPLE ? KN_EPI : RS_EPI)) * 
                                 hit &= hit - 1;
                                 if ((int64_t)gq < P.cap) {
                                     P.cq[gq] = qid;
-                                    P.cx[gq] = (int)(c0 + h * 32 + j);
+                                    P.cx[gq] = (int)(P.col_base + c0 + h * 32 + j);
                                     // integer inputs: the accumulator 2<a,b> - |b|^2 is exact.
                                     // (select by unrolled compares: a runtime index into va
                                     // would move the whole array to local memory)
@@ -1413,18 +1417,30 @@ __global__ void k_knn_bound(const float* __restrict__ sqn, const float* __restri
 bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, DBuf<float>& row_thr,
                           DBuf<float>* cw_out) {
     const int kpad = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
-    if (ix->n < 4096 || ix->knn_cols < 4096) return false;
+    const int64_t n = ix->n, nx = ix->nx;
+    // blocks of (rows, candidate columns) by the index's kNN mode; a block
+    // whose rows are its columns is symmetric
+    struct Blk {
+        int64_t r0, nr, c0, nc;
+    };
+    std::vector<Blk> blks;
+    if (ix->knn_mode == VJ_KNN_ALL) {
+        blks.push_back(Blk{0, n, 0, n});
+    } else {
+        blks.push_back(Blk{0, nx, 0, nx});
+        if (ix->knn_mode == VJ_KNN_DATA) blks.push_back(Blk{nx, n - nx, 0, nx});
+        else blks.push_back(Blk{nx, n - nx, nx, n - nx});
+    }
+    for (const Blk& b : blks)
+        if (b.nr > 0 && b.nc < 4096) return false;  // too few tiles to sample: the SIMT sweep
     const bool wide = kpad > RS_MAX_KB * TC_BK;
     cudaStream_t s = ix->stream;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
-    const int64_t n = ix->n;
-    // candidate columns: every node, or the data nodes only (NN-Map index)
-    const int64_t ncols = ix->knn_cols;
     DBuf<__nv_bfloat16> abf;
     DBuf<float> top, thr, cw;
     DBuf<int32_t> iota;
-    DBuf<int4> units;
+    std::vector<DBuf<int4>> units(blks.size());
     DBuf<int> err;
     DBuf<unsigned long long> ctr;
     top.alloc(n, s);
@@ -1466,130 +1482,168 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
                                                           cosine ? 1.f : 2.f, cosine ? ix->invn.p : nullptr, abf.p);
         k_iota<<<vj_div_up(n, 256), 256, 0, s>>>(iota.p, n);
         VJ_LAUNCH_CHECK();
-        CUtensorMap ta = make_map(abf.p, n, kpad, 128);
-        CUtensorMap tb = make_map(ix->xbf.p, ncols, kpad, RS_BN);
-        CUtensorMap tab = cosine ? ta : make_map16(ix->abias.p, 128, 128);
-        CUtensorMap tbb = cosine ? tb : make_map16(ix->xbias.p, ncols, RS_BN);
-        RsParams R{};
-        R.nrows = n;
-        R.ncols = ncols;
-        R.nkb = kpad / TC_BK;
-        R.bias = cosine ? 0 : 1;
-        R.nrp = (int)vj_div_up(n, 256);
-        const int nct_all = (int)vj_div_up(ncols, RS_BN);
-        const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)R.nkb * RS_BOX;
-        const size_t per = (size_t)R.nkb * RS_BOX + RS_BBOX;
-        R.stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
-        R.err = err.p;
-        R.spin_limit = spin_limit;
-        const size_t smem = fixed + per * (size_t)R.stages;
-
+        const int nkb = kpad / TC_BK;
+        const size_t fixed = 2048 + RS_BBOX + 2 * (size_t)nkb * RS_BOX;
+        const size_t per = (size_t)nkb * RS_BOX + RS_BBOX;
+        const int stages = (int)std::min<size_t>(RS_MAX_STAGES, (232448 - fixed) / per);
+        const size_t smem = fixed + per * (size_t)stages;
+        // the block's A rows (node ids r0 ..) against its B rows (node ids c0 ..)
+        struct RsBlk {
+            CUtensorMap ta, tab, tb, tbb;
+            RsParams R;
+            int nct_all;
+        };
+        std::vector<RsBlk> rb;
+        for (const Blk& b : blks) {
+            if (b.nr <= 0) continue;
+            RsBlk x;
+            x.ta = make_map(abf.p + (size_t)b.r0 * kpad, b.nr, kpad, 128);
+            x.tb = make_map(ix->xbf.p + (size_t)b.c0 * kpad, b.nc, kpad, RS_BN);
+            x.tab = cosine ? x.ta : make_map16(ix->abias.p, 128, 128);
+            x.tbb = cosine ? x.tb : make_map16(ix->xbias.p + (size_t)b.c0 * 16, b.nc, RS_BN);
+            RsParams& R = x.R;
+            R = RsParams{};
+            R.nrows = b.nr;
+            R.ncols = b.nc;
+            R.nkb = nkb;
+            R.bias = cosine ? 0 : 1;
+            R.nrp = (int)vj_div_up(b.nr, 256);
+            R.stages = stages;
+            R.err = err.p;
+            R.spin_limit = spin_limit;
+            R.row_base = b.r0;
+            R.col_base = b.c0;
+            R.a_ids = iota.p + b.r0;
+            x.nct_all = (int)vj_div_up(b.nc, RS_BN);
+            rb.push_back(x);
+        }
         // 1. sample sweep: one unit per 256-row block over every KNN_SAMPLE-th tile
-        R.tstride = KNN_SAMPLE;
-        R.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
-        R.tpu = R.nct;
-        R.nunits = R.nrp;
-        R.top16 = top.p;
         VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tc_res<EPI_SAMPLE><<<std::min(R.nunits, ix->num_sms), (2 + KN_EPI) * 32, smem, s>>>(ta, tab, tb, tbb, R);
-        VJ_LAUNCH_CHECK();
+        for (RsBlk& x : rb) {
+            RsParams R = x.R;
+            R.tstride = KNN_SAMPLE;
+            R.nct = (x.nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
+            R.tpu = R.nct;
+            R.nunits = R.nrp;
+            R.top16 = top.p + R.row_base;
+            k_tc_res<EPI_SAMPLE><<<std::min(R.nunits, ix->num_sms), (2 + KN_EPI) * 32, smem, s>>>(x.ta, x.tab, x.tb,
+                                                                                              x.tbb, R);
+            VJ_LAUNCH_CHECK();
+        }
         k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
         VJ_LAUNCH_CHECK();
 
         // 2. candidate sweep over every tile, rows are node ids
-        R.tstride = 1;
-        R.nct = nct_all;
-        R.tpu = best_tiles_per_unit(R.nrp, R.nct, ix->num_sms, 3);
-        R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
-        R.a_thr = thr.p;
-        R.a_ids = iota.p;
-        R.ncand = ctr.p;
+        for (RsBlk& x : rb) {
+            RsParams& R = x.R;
+            R.tstride = 1;
+            R.nct = x.nct_all;
+            R.tpu = best_tiles_per_unit(R.nrp, R.nct, ix->num_sms, 3);
+            R.nunits = R.nrp * (int)vj_div_up(R.nct, R.tpu);
+            R.a_thr = thr.p + R.row_base;
+            R.ncand = ctr.p;
+        }
         VJ_CUDA(cudaFuncSetAttribute(k_tc_res<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         sweep([&](int32_t* pq, int32_t* px, float*, int64_t c) {
-            R.cq = pq;
-            R.cx = px;
-            R.cap = c;
-            k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R);
+            for (RsBlk& x : rb) {
+                RsParams R = x.R;
+                R.cq = pq;
+                R.cx = px;
+                R.cap = c;
+                k_tc_res<EPI_SCAN><<<std::min(R.nunits, ix->num_sms), RS_THREADS, smem, s>>>(x.ta, x.tab, x.tb,
+                                                                                          x.tbb, R);
+            }
         });
     } else {
-        // streamed tiles: A is the BF16 copy of every node, B of the candidate nodes
-        CUtensorMap ta = make_map(ix->xbf.p, n, kpad, WD_BM);
-        CUtensorMap tb = make_map(ix->xbf.p, ncols, kpad, WD_BN);
-        WdParams W{};
-        W.nrows = n;
-        W.ncols = ncols;
-        W.nkb = kpad / TC_BK;
-        W.nrt = (int)vj_div_up(n, WD_BM);
-        W.cs = ix->wcs.p;
-        W.cb = ix->wcb.p;
-        W.err = err.p;
-        W.spin_limit = spin_limit;
-        const int nct_all = (int)vj_div_up(ncols, WD_BN);
+        // streamed tiles: A and B are the BF16 copies of the block's rows and columns
         const size_t smem = wide_smem();
+        struct WdBlk {
+            CUtensorMap ta, tb;
+            WdParams W;
+            int nct_all;
+        };
+        std::vector<WdBlk> wb;
+        for (const Blk& b : blks) {
+            if (b.nr <= 0) continue;
+            WdBlk x;
+            x.ta = make_map(ix->xbf.p + (size_t)b.r0 * kpad, b.nr, kpad, WD_BM);
+            x.tb = make_map(ix->xbf.p + (size_t)b.c0 * kpad, b.nc, kpad, WD_BN);
+            WdParams& W = x.W;
+            W = WdParams{};
+            W.nrows = b.nr;
+            W.ncols = b.nc;
+            W.nkb = kpad / TC_BK;
+            W.nrt = (int)vj_div_up(b.nr, WD_BM);
+            W.cs = ix->wcs.p + b.c0;
+            W.cb = ix->wcb.p + b.c0;
+            W.err = err.p;
+            W.spin_limit = spin_limit;
+            W.row_base = b.r0;
+            W.col_base = b.c0;
+            x.nct_all = (int)vj_div_up(b.nc, WD_BN);
+            wb.push_back(x);
+        }
         // 1. sample sweep: one unit per 128-row tile over every KNN_SAMPLE-th tile
-        W.tstride = KNN_SAMPLE;
-        W.nct = (nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
-        W.tpu = W.nct;
-        W.nunits = W.nrt;
-        W.top16 = top.p;
         VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tc_wide<EPI_SAMPLE><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta, tb, W);
-        VJ_LAUNCH_CHECK();
+        for (WdBlk& x : wb) {
+            WdParams W = x.W;
+            W.tstride = KNN_SAMPLE;
+            W.nct = (x.nct_all + KNN_SAMPLE - 1) / KNN_SAMPLE;
+            W.tpu = W.nct;
+            W.nunits = W.nrt;
+            W.top16 = top.p + W.row_base;
+            k_tc_wide<EPI_SAMPLE><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+            VJ_LAUNCH_CHECK();
+        }
         k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
         VJ_LAUNCH_CHECK();
-        // 2. candidate sweep, rows are node ids.  Over the candidate rows A = B,
-        // so the Gram tiles are symmetric: row tile rt visits the B tiles from
-        // its own 256-row block on (ct >= rt / 2), and tiles past that block
-        // test both directions.  Units: a row tile's run of tpu tiles, ordered
-        // by first tile so the units running together walk the same B tiles
-        // (and the longest runs, of the first row tiles, start first).  Rows
-        // past the candidate nodes (the queries of an NN-Map index) sweep every
-        // B tile in a second launch.
-        W.tstride = 1;
-        W.nct = nct_all;
-        W.nrows = ncols;
-        W.nrt = (int)vj_div_up(ncols, WD_BM);
-        int64_t tiles = 0;
-        for (int rt = 0; rt < W.nrt; rt++) tiles += nct_all - (rt >> 1);
-        const int64_t tpu = std::min<int64_t>(nct_all, std::max<int64_t>(64, tiles / (8 * (int64_t)ix->num_sms)));
-        std::vector<int4> hu;
-        for (int rt = 0; rt < W.nrt; rt++)
-            for (int64_t t0 = rt >> 1; t0 < nct_all; t0 += tpu)
-                hu.push_back(make_int4(rt, (int)t0, (int)std::min<int64_t>(nct_all, t0 + tpu), 0));
-        std::stable_sort(hu.begin(), hu.end(), [](const int4& a, const int4& b) { return a.y < b.y; });
-        units.alloc(hu.size(), s);
-        VJ_CUDA(cudaMemcpyAsync(units.p, hu.data(), hu.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-        W.units = units.p;
-        W.nunits = (int)hu.size();
-        W.thr = thr.p;
-        W.a_ids = nullptr;
-        W.ncand = ctr.p;
-        // the remaining rows: A starts at row ncols, their ids are ncols + row
-        const int64_t nrest = n - ncols;
-        WdParams W2 = W;
-        CUtensorMap ta2 = ta;
-        if (nrest > 0) {
-            iota.alloc(nrest, s);
-            k_iota<<<vj_div_up(nrest, 256), 256, 0, s>>>(iota.p, nrest, ncols);
-            VJ_LAUNCH_CHECK();
-            ta2 = make_map(ix->xbf.p + (size_t)ncols * kpad, nrest, kpad, WD_BM);
-            W2.nrows = nrest;
-            W2.nrt = (int)vj_div_up(nrest, WD_BM);
-            W2.units = nullptr;
-            W2.tpu = (int)std::min<int64_t>(
-                nct_all, std::max<int64_t>(64, (int64_t)W2.nrt * nct_all / (8 * (int64_t)ix->num_sms)));
-            W2.nunits = W2.nrt * (int)vj_div_up(nct_all, W2.tpu);
-            W2.thr = thr.p + ncols;
-            W2.a_ids = iota.p;
+        // 2. candidate sweep, rows are node ids.  A symmetric block (its rows
+        // are its columns) has symmetric Gram tiles: row tile rt visits the B
+        // tiles from its own 256-row block on (ct >= rt / 2), and tiles past
+        // that block test both directions.  Units: a row tile's run of tpu
+        // tiles, ordered by first tile so the units running together walk the
+        // same B tiles (and the longest runs, of the first row tiles, start
+        // first).  Other blocks sweep every B tile, row tile fastest.
+        for (size_t k = 0; k < wb.size(); k++) {
+            WdBlk& x = wb[k];
+            WdParams& W = x.W;
+            const int nct_all = x.nct_all;
+            W.tstride = 1;
+            W.nct = nct_all;
+            W.thr = thr.p + W.row_base;
+            W.a_ids = nullptr;
+            W.ncand = ctr.p;
+            if (W.row_base == W.col_base && W.nrows == W.ncols) {
+                int64_t tiles = 0;
+                for (int rt = 0; rt < W.nrt; rt++) tiles += nct_all - (rt >> 1);
+                const int64_t tpu =
+                    std::min<int64_t>(nct_all, std::max<int64_t>(64, tiles / (8 * (int64_t)ix->num_sms)));
+                std::vector<int4> hu;
+                for (int rt = 0; rt < W.nrt; rt++)
+                    for (int64_t t0 = rt >> 1; t0 < nct_all; t0 += tpu)
+                        hu.push_back(make_int4(rt, (int)t0, (int)std::min<int64_t>(nct_all, t0 + tpu), 0));
+                std::stable_sort(hu.begin(), hu.end(), [](const int4& a, const int4& b) { return a.y < b.y; });
+                units[k].alloc(hu.size(), s);
+                VJ_CUDA(cudaMemcpyAsync(units[k].p, hu.data(), hu.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+                W.units = units[k].p;
+                W.nunits = (int)hu.size();
+            } else {
+                W.units = nullptr;
+                W.tpu = (int)std::min<int64_t>(
+                    nct_all, std::max<int64_t>(64, (int64_t)W.nrt * nct_all / (8 * (int64_t)ix->num_sms)));
+                W.nunits = W.nrt * (int)vj_div_up(nct_all, W.tpu);
+            }
         }
         VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         sweep([&](int32_t* pq, int32_t* px, float* pw, int64_t c) {
-            W.cq = W2.cq = pq;
-            W.cx = W2.cx = px;
-            W.cw = W2.cw = pw;
-            W.cap = W2.cap = c;
-            k_tc_wide<EPI_SCAN><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta, tb, W);
-            if (nrest > 0) k_tc_wide<EPI_SCAN><<<std::min(W2.nunits, ix->num_sms), WD_THREADS, smem, s>>>(ta2, tb, W2);
+            for (WdBlk& x : wb) {
+                WdParams W = x.W;
+                W.cq = pq;
+                W.cx = px;
+                W.cw = pw;
+                W.cap = c;
+                k_tc_wide<EPI_SCAN><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+            }
         });
     }
     const int64_t nc = (int64_t)hn;
@@ -1627,7 +1681,7 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
     thr.free_(s);
     cw.free_(s);
     iota.free_(s);
-    units.free_(s);
+    for (auto& u : units) u.free_(s);
     err.free_(s);
     ctr.free_(s);
     return true;

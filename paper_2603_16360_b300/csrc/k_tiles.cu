@@ -185,13 +185,15 @@ __device__ __forceinline__ void list_insert(float* Lk, int* Li, float k, int id,
 
 template <int KP>
 __global__ void __launch_bounds__(TT) k_knn_sweep(const float* __restrict__ vec, const float* __restrict__ sqn,
-                                                   const float* __restrict__ invn, int dp, int64_t n, int64_t ncols,
-                                                   int metric, int32_t* __restrict__ cand_id,
+                                                   const float* __restrict__ invn, int dp, int64_t r0, int64_t r1,
+                                                   int64_t c0, int64_t c1, int metric, int32_t* __restrict__ cand_id,
                                                    float* __restrict__ cand_key, float* __restrict__ row_thr) {
     extern __shared__ __align__(16) unsigned char sraw[];
     KnnSmem<KP>& S = *reinterpret_cast<KnnSmem<KP>*>(sraw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t ra = (int64_t)blockIdx.x * TBM;
+    // rows r0 .. r1-1 against the candidate nodes c0 .. c1-1
+    const int64_t ra = r0 + (int64_t)blockIdx.x * TBM;
+    const int64_t n = r1;
     for (int i = threadIdx.x; i < TBM * KP; i += TT) {
         (&S.lk[0][0])[i] = FLT_MAX;
         (&S.li[0][0])[i] = INT32_MAX;
@@ -203,20 +205,19 @@ __global__ void __launch_bounds__(TT) k_knn_sweep(const float* __restrict__ vec,
         int64_t r = ra + tile_row(i);
         rn[i] = r < n ? (metric == 0 ? sqn[r] : invn[r]) : 0.f;
     }
-    // candidates: nodes 0 .. ncols-1 (every node, or the data nodes only)
-    for (int64_t ca = 0; ca < ncols; ca += TBN) {
+    for (int64_t ca = c0; ca < c1; ca += TBN) {
         float acc[8][8];
-        gram_tile(vec, dp, ra, n, ca, ncols, acc, S.u.g);
+        gram_tile(vec, dp, ra, n, ca, c1, acc, S.u.g);
         // keys into the tile (the gram buffers are dead after the last sync)
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             int64_t c = ca + tile_col(j);
-            float cn = c < ncols ? (metric == 0 ? sqn[c] : invn[c]) : 0.f;
+            float cn = c < c1 ? (metric == 0 ? sqn[c] : invn[c]) : 0.f;
 #pragma unroll
             for (int i = 0; i < 8; i++) {
                 int64_t r = ra + tile_row(i);
                 float key;
-                if (c >= ncols || r >= n || c == r) key = FLT_MAX;
+                if (c >= c1 || r >= n || c == r) key = FLT_MAX;
                 else if (metric == 0) key = fmaxf(rn[i] + cn - 2.f * acc[i][j], 0.f);
                 else key = 1.f - acc[i][j] * rn[i] * cn;
                 S.u.D[tile_row(i)][tile_col(j)] = key;
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(KC_WPB * 32)
 // direct-difference keys, then the same re-rank (run again on its output)
 template <int G, int NPL>
 __global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ vec, const float* __restrict__ invn,
-                                                      int dp, int64_t ncols, int metric, int KP,
+                                                      int dp, int64_t nx, int64_t n, int knn_mode, int metric, int KP,
                                                       const int32_t* __restrict__ rows, int nrows,
                                                       int32_t* __restrict__ cand_id, float* __restrict__ row_thr) {
     __shared__ int cid[8][128];
@@ -701,8 +702,11 @@ __global__ void __launch_bounds__(256) k_knn_rowscan(const float* __restrict__ v
     float4 q[NPL];
     load_slots<G, NPL>(vec, r, dp / 4, lane & (G - 1), q);
     const float invq = metric ? invn[r] : 0.f;
-    for (int64_t c0 = 0; c0 < ncols; c0 += 128) {
-        int nc = (ncols - c0) < 128 ? (int)(ncols - c0) : 128;
+    // the row's candidate nodes [lo, hi)
+    const int64_t lo = (knn_mode == VJ_KNN_GROUPS && r >= nx) ? nx : 0;
+    const int64_t hi = knn_mode == VJ_KNN_DATA || (knn_mode == VJ_KNN_GROUPS && r < nx) ? nx : n;
+    for (int64_t c0 = lo; c0 < hi; c0 += 128) {
+        int nc = (hi - c0) < 128 ? (int)(hi - c0) : 128;
         for (int e = lane; e < 128; e += 32) cid[warp][e] = (int)(c0 + e);
         __syncwarp();
         group_keys<G, NPL, 1>(vec, invn, dp / 4, metric, q, invq, cid[warp], nc, ckey[warp], lane);
@@ -837,9 +841,24 @@ template <int KP>
 static void run_sweep(vj_index* ix, int32_t* cid, float* ckey, float* thr) {
     size_t smem = sizeof(KnnSmem<KP>);
     VJ_CUDA(cudaFuncSetAttribute(k_knn_sweep<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_knn_sweep<KP><<<vj_div_up(ix->n, TBM), TT, smem, ix->stream>>>(ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, ix->n,
-                                                                     ix->knn_cols, ix->metric, cid, ckey, thr);
-    VJ_LAUNCH_CHECK();
+    // (row range, candidate range) blocks of the index's kNN mode
+    const int64_t n = ix->n, nx = ix->nx;
+    int64_t blk[2][4] = {{0, n, 0, n}, {0, 0, 0, 0}};
+    if (ix->knn_mode == VJ_KNN_DATA) blk[0][3] = nx;
+    if (ix->knn_mode == VJ_KNN_GROUPS) {
+        blk[0][1] = nx;
+        blk[0][3] = nx;
+        blk[1][0] = nx;
+        blk[1][1] = n;
+        blk[1][2] = nx;
+        blk[1][3] = n;
+    }
+    for (auto& b : blk) {
+        if (b[1] <= b[0]) continue;
+        k_knn_sweep<KP><<<vj_div_up(b[1] - b[0], TBM), TT, smem, ix->stream>>>(
+            ix->vec.p, ix->sqn.p, ix->invn.p, ix->dp, b[0], b[1], b[2], b[3], ix->metric, cid, ckey, thr);
+        VJ_LAUNCH_CHECK();
+    }
 }
 
 void vj_build_knn(vj_index* ix) {
@@ -922,7 +941,8 @@ void vj_build_knn(vj_index* ix) {
         // exact row scans for the uncertified rows, then re-rank them again
         // (their scans fill cid / thr at the rows' own positions)
         VJ_DISPATCH_GN(dp4, (k_knn_rowscan<G, NPL><<<vj_div_up(hb, 8), 256, 0, s>>>(
-                                ix->vec.p, ix->invn.p, ix->dp, ix->knn_cols, ix->metric, KP, bad.p, hb, cid.p, thr.p)));
+                                ix->vec.p, ix->invn.p, ix->dp, ix->nx, n, ix->knn_mode, ix->metric, KP, bad.p, hb,
+                                cid.p, thr.p)));
         VJ_LAUNCH_CHECK();
         // the row scans saw every node, so these rows certify on re-rank
         DBuf<int32_t> bad2;

@@ -66,8 +66,8 @@ static vj_status guarded(F&& f) {
 }
 
 static void check_join_params(const vj_params& p) {
-    VJ_REQUIRE(p.work_sharing == VJ_WS_NONE || p.work_sharing == VJ_WS_SOFT || p.work_sharing == VJ_WS_SELF,
-               VJ_ERR_ARG, "work_sharing must be NONE, SOFT or SELF (HARD is not implemented)");
+    VJ_REQUIRE(p.work_sharing >= VJ_WS_NONE && p.work_sharing <= VJ_WS_SELF, VJ_ERR_ARG,
+               "work_sharing must be NONE, HARD, SOFT or SELF");
     VJ_REQUIRE(p.hybrid_beam >= 0 && p.hybrid_beam <= (1 << 20), VJ_ERR_ARG, "hybrid_beam out of range");
     VJ_REQUIRE(p.greedy_beam >= 1, VJ_ERR_ARG, "greedy_beam must be >= 1");
     VJ_REQUIRE(p.learned == 0 || p.learned == 1, VJ_ERR_ARG, "learned must be 0 or 1");
@@ -166,6 +166,10 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         VJ_REQUIRE(p.precision == VJ_PREC_FP32 || p.precision == VJ_PREC_BF16, VJ_ERR_ARG,
                    "build tiles: FP32 or BF16 (FP8 is not implemented)");
         VJ_REQUIRE(p.nnmap == 0 || p.nnmap == 1, VJ_ERR_ARG, "nnmap must be 0 or 1");
+        VJ_REQUIRE(p.separate == 0 || p.separate == 1, VJ_ERR_ARG, "separate must be 0 or 1");
+        VJ_REQUIRE(!(p.nnmap && p.separate), VJ_ERR_ARG, "nnmap and separate are exclusive");
+        VJ_REQUIRE(p.work_sharing != VJ_WS_HARD || p.separate, VJ_ERR_ARG,
+                   "work_sharing HARD runs on separate indexes only (vj_params.separate = 1)");
         check_join_params(p);
 
         ix = new vj_index();
@@ -188,12 +192,20 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         ix->metric = metric;
         ix->p = p;
         ix->nnmap = p.nnmap != 0;
-        // an NN-Map index lists data candidates only, and only data rows enter the graph
-        ix->knn_cols = ix->nnmap ? nx : ix->n;
+        ix->separate = p.separate != 0;
+        // an NN-Map index lists data candidates only, and only data rows enter
+        // the graph; separate indexes list each row's own set
+        ix->knn_mode = ix->nnmap ? VJ_KNN_DATA : (ix->separate ? VJ_KNN_GROUPS : VJ_KNN_ALL);
         ix->graph_rows = ix->nnmap ? nx : ix->n;
+        ix->entry_rows = (ix->nnmap || ix->separate) ? nx : ix->n;
         if (ix->nnmap) {
             VJ_REQUIRE(nx >= 2, VJ_ERR_ARG, "an NN-Map index needs nx >= 2");
             ix->K = (int)std::min<int64_t>(ix->K, nx - 1);
+            ix->R = std::min(ix->R, ix->K);
+        }
+        if (ix->separate) {
+            VJ_REQUIRE(nx >= 2 && nq >= 2, VJ_ERR_ARG, "separate indexes need nx >= 2 and nq >= 2");
+            ix->K = (int)std::min<int64_t>(ix->K, std::min(nx, nq) - 1);
             ix->R = std::min(ix->R, ix->K);
         }
         cudaStream_t s = ix->stream;
@@ -243,6 +255,8 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
     return guarded([&] {
         VJ_REQUIRE(ix != nullptr && p != nullptr, VJ_ERR_ARG, "NULL argument");
         check_join_params(*p);
+        VJ_REQUIRE(p->work_sharing != VJ_WS_HARD || ix->separate, VJ_ERR_ARG,
+                   "work_sharing HARD runs on separate indexes only (vj_params.separate = 1)");
         ix->p.greedy_beam = p->greedy_beam;
         ix->p.conv_threshold = p->conv_threshold;
         ix->p.hybrid_beam = p->hybrid_beam;

@@ -89,6 +89,13 @@ void DBuf<T>::free_(cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ the index
+// candidate columns of a node's kNN list
+enum {
+    VJ_KNN_ALL = 0,    // every other node (merged index)
+    VJ_KNN_DATA = 1,   // data nodes only (NN-Map index)
+    VJ_KNN_GROUPS = 2  // nodes of its own set (separate indexes)
+};
+
 struct vj_index {
     int dev = 0;
     int64_t nx = 0, nq = 0, n = 0;
@@ -141,8 +148,13 @@ struct vj_index {
     // only, the graph G_X over data rows only, and per query its witness
     // (nearest data vector), the witness's FP64 distance and the OOD bit
     bool nnmap = false;
-    int64_t knn_cols = 0;      // kNN candidates are nodes 0..knn_cols-1 (n, or nx for an NN-Map index)
-    int64_t graph_rows = 0;    // nodes with a graph row (n, or nx for an NN-Map index)
+    // separate (per-set) indexes (Sec. 3.2): the data graph G_Y over the data
+    // rows and the query graph over the query rows, in one adjacency array;
+    // the entry s_Y is a data node and the MST runs over the query graph
+    bool separate = false;
+    int knn_mode = VJ_KNN_ALL;  // which nodes a row's kNN list ranks (VJ_KNN_*)
+    int64_t graph_rows = 0;     // nodes with a graph row (n, or nx for an NN-Map index)
+    int64_t entry_rows = 0;     // the entry is the node nearest the centroid of nodes 0..entry_rows-1
     DBuf<int32_t> nm_w;        // [nq] witness
     DBuf<double> nm_wd;        // [nq] its distance (FP64)
     DBuf<uint8_t> nm_ood;      // [nq] OOD bit

@@ -48,7 +48,7 @@ class vj_params(C.Structure):
                 ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
                 ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
                 ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64),
-                ("gather", C.c_int), ("hybrid_seed_best", C.c_int), ("nnmap", C.c_int)]
+                ("gather", C.c_int), ("hybrid_seed_best", C.c_int), ("nnmap", C.c_int), ("separate", C.c_int)]
 
 
 class vj_stats(C.Structure):
