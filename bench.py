@@ -586,29 +586,38 @@ def profile_modes(args, vj, ix, w, build_s, binfo):
     vj.vj_set_plan(ix, None, None)
 
 
-def nnmap_mode(args, vj, torch, ix, w, build_s, binfo, log):
-    """--mode nnmap: the NN-Map index's joins at the workload's eps, one JSON
-    line.  Each setting runs `steps` device-resident joins (CUDA events on the
-    launching stream); recall is against the exact join over the evaluated
-    queries.  `value` is the fastest setting reaching recall 0.95 (else the
-    most accurate)."""
+VARIANT_SETTINGS = {
+    "nnmap": [("BFS expansion", dict(work_sharing=0, adapt_hybrid=0, force_hybrid=0, hybrid_beam=256)),
+              ("adaptive hybrid, queue 64", dict(work_sharing=0, adapt_hybrid=1, force_hybrid=0, hybrid_beam=64)),
+              ("adaptive hybrid, queue 256", dict(work_sharing=0, adapt_hybrid=1, force_hybrid=0, hybrid_beam=256)),
+              ("forced hybrid, queue 64", dict(work_sharing=0, adapt_hybrid=0, force_hybrid=1, hybrid_beam=64))],
+    # Sec. 3.2's separate-index executions (the paper's INLJ / HWS / SWS baselines)
+    "separate": [("INLJ (greedy from s_Y), BFS expansion", dict(work_sharing=0, force_hybrid=0)),
+                 ("HWS (parent's row as seeds), BFS expansion", dict(work_sharing=1, force_hybrid=0)),
+                 ("SWS (parent's cache as seed), BFS expansion", dict(work_sharing=2, force_hybrid=0)),
+                 ("SWS, forced hybrid, queue 8", dict(work_sharing=2, force_hybrid=1, hybrid_beam=8))],
+}
+
+
+def variant_mode(args, vj, torch, ix, w, build_s, binfo, log):
+    """--mode nnmap / separate: the joins of an NN-Map or a separate-index
+    build at the workload's eps, one JSON line.  Each setting runs `steps`
+    device-resident joins (CUDA events on the launching stream); recall is
+    against the exact join over the evaluated queries.  `value` is the fastest
+    setting reaching recall 0.95 (else the most accurate)."""
     ne = n_eval(w)
     eps = calibrate_eps(vj, ix, w, w.target_matches)
     ex = vj.vj_join_exact(ix, eps)
-    _, wd, ood = vj.vj_export_nnmap(ix)
     hbm, _, peak_kind = _peaks()
-    settings = [("BFS expansion", dict(adapt_hybrid=0, force_hybrid=0, hybrid_beam=256)),
-                ("adaptive hybrid, queue 64", dict(adapt_hybrid=1, force_hybrid=0, hybrid_beam=64)),
-                ("adaptive hybrid, queue 256", dict(adapt_hybrid=1, force_hybrid=0, hybrid_beam=256)),
-                ("forced hybrid, queue 64", dict(adapt_hybrid=0, force_hybrid=1, hybrid_beam=64))]
+    settings = VARIANT_SETTINGS[args.mode]
     arms, best = [], None
     for k, (name, kw) in enumerate(settings):
-        vj.vj_set_join_params(ix, work_sharing=vj.VJ_WS_NONE, learned=0, gather=vj.VJ_PREC_BF16, **kw)
+        vj.vj_set_join_params(ix, learned=0, gather=vj.VJ_PREC_BF16, **kw)
         try:
             r = vj.vj_join(ix, eps)
         except vj.VjError as e:  # e.g. a hybrid search that outgrows the per-query visited capacity
             arms.append({"setting": name, "error": str(e)[:160]})
-            log(f"nnmap {name}: {e}")
+            log(f"{args.mode} {name}: {e}")
             continue
         rec = recall_of(r, ex, w.nx, (0, ne))
         ms, stats, clk = timed(vj, torch, ix, eps, 0, args.steps, args.warmup, "nnmap_timed", clocks=(k == 0))
@@ -619,14 +628,14 @@ def nnmap_mode(args, vj, torch, ix, w, build_s, binfo, log):
                "ms_per_step": ms, "qps": ne / (ms / 1e3), "ms_traverse": t_tr,
                "dist_per_query": statistics.mean(s["dist_computations"] for s in stats) / w.nq,
                "hybrid_queries": int((r.hybrid[:ne] == 1).sum()),
-               "roofline": {"kernel": "k_join (NN-Map expansion)", "bound": "hbm", "unit": "GB/s", "peak": hbm,
+               "roofline": {"kernel": f"k_join ({args.mode})", "bound": "hbm", "unit": "GB/s", "peak": hbm,
                             "achieved": byts / (t_tr / 1e3) / 1e9, "frac": byts / (t_tr / 1e3) / 1e9 / hbm,
                             "algorithmic_bytes_per_launch": byts, "peak_kind": f"{peak_kind} hbm_gbs (burst)",
                             "traffic": None},
                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
         if clk is not None:
             arm["clocks"] = clk
-        log(f"nnmap {name}: recall {rec:.4f} {arm['qps']:.3e} q/s")
+        log(f"{args.mode} {name}: recall {rec:.4f} {arm['qps']:.3e} q/s")
         arms.append(arm)
         if best is None:
             best = arm
@@ -637,23 +646,29 @@ def nnmap_mode(args, vj, torch, ix, w, build_s, binfo, log):
         else:
             best = arm if arm["recall"] > best["recall"] else best
     if best is None:
-        raise SystemExit(f"nnmap: no setting ran: {arms}")
-    line = {"mode": "nnmap", "metric": METRIC, "value": best["qps"], "unit": "queries/s", "n_gpus": 1,
+        raise SystemExit(f"{args.mode}: no setting ran: {arms}")
+    line = {"mode": args.mode, "metric": METRIC, "value": best["qps"], "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"], "higher_is_better": True,
             "dtype": "bf16", "data": "synthetic", "roofline": best["roofline"], "clocks": arms[0].get("clocks"),
             "gpu_launches": best["gpu_launches"],
             "config": {"workload": f"{w.name}: X={w.nx} Q={ne} (+{w.nq - ne} held out) d={w.d} "
                                    f"{'L2' if w.metric == 0 else 'cosine'}, eps for a mean of "
                                    f"{w.target_matches:g} matches/query",
-                       "arm": f"NN-Map: {best['setting']}, BF16 gathers", "eps": eps,
+                       "arm": f"{'NN-Map' if args.mode == 'nnmap' else 'separate indexes'}: {best['setting']}, "
+                              f"BF16 gathers", "eps": eps,
                        "build": {"wall_s": round(build_s, 2), "ms_device": binfo["ms_build"],
                                  "ms_knn": binfo["ms_knn"], "knn_tensor_cores": binfo["knn_tensor_cores"],
                                  "knn_uncertified": binfo["knn_uncertified"]},
-                       "certified_empty_frac": float((wd[:ne] >= eps).mean()),
-                       # the witness property: a row is certified empty exactly when the exact row is empty
-                       "certified_empty_equals_exact_empty": bool(np.array_equal(
-                           wd[:ne] >= eps, np.diff(ex.offsets[:ne + 1]) == 0)),
-                       "ood_frac": float(ood[:ne].mean()), "settings": arms}}
+                       "settings": arms}}
+    if args.mode == "nnmap":
+        _, wd, ood = vj.vj_export_nnmap(ix)
+        line["config"]["certified_empty_frac"] = float((wd[:ne] >= eps).mean())
+        # the witness property: a row is certified empty exactly when the exact row is empty
+        line["config"]["certified_empty_equals_exact_empty"] = bool(np.array_equal(
+            wd[:ne] >= eps, np.diff(ex.offsets[:ne + 1]) == 0))
+        line["config"]["ood_frac"] = float(ood[:ne].mean())
+    else:
+        line["config"]["mst_depth"] = ix.info()["max_depth"]
     print(json.dumps(line), flush=True)
 
 
@@ -671,11 +686,12 @@ def main():
     ap.add_argument("--collection-learned", action="store_true",
                     help="angular_collection: also time one shared predictor's learned route")
     ap.add_argument("--quiet", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "build", "join", "nnmap"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "build", "join", "nnmap", "separate"],
                     help="build: generate the workload and build the index only (profiling the build); join: "
                          "also run --reps joins with every query planned --plan (profiling the traversal); "
                          "nnmap: build an NN-Map index instead and time its joins (BFS, adaptive and forced "
-                         "hybrid expansion from the witnesses)")
+                         "hybrid expansion from the witnesses); separate: build separate per-set indexes and time "
+                         "INLJ, HWS and SWS")
     ap.add_argument("--plan", default="none", choices=["none", "bfs", "rule"],
                     help="--mode join: none = no expansion (the learned step's plan here), bfs, or the d1/d2 rule")
     ap.add_argument("--reps", type=int, default=3)
@@ -717,12 +733,12 @@ def main():
     log(f"workload {w.name}: X {w.nx} x {w.d}, Q {ne} evaluated + {w.nq - ne} held out ({gen_s:.1f}s)")
     t0 = time.perf_counter()
     ix = vj.vj_build(w.X, w.Q, metric=w.metric, params=vj.default_params(degree=w.degree, knn_k=w.knn_k),
-                     nnmap=int(args.mode == "nnmap"))
+                     nnmap=int(args.mode == "nnmap"), separate=int(args.mode == "separate"))
     build_s = time.perf_counter() - t0
     info, binfo = ix.info(), ix.build_info()
     log(f"build {build_s:.1f}s {binfo}")
-    if args.mode == "nnmap":
-        nnmap_mode(args, vj, torch, ix, w, build_s, binfo, log)
+    if args.mode in VARIANT_SETTINGS:
+        variant_mode(args, vj, torch, ix, w, build_s, binfo, log)
         ix.free()
         return
     if args.mode != "bench":
