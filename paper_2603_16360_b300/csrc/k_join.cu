@@ -167,6 +167,10 @@ struct JoinParams {
     // queue trimmed to gbeam after each expansion
     int separate;
     int gbeam;
+    // probe keys from k_probe ([nq][R + 1]: slot j of q's adjacency row, then
+    // the entry), bit-identical to the traversal's own (nullptr: computed in
+    // the traversal)
+    const float* pkeys;
 };
 
 enum { QF_PROBED = 1 };
@@ -484,7 +488,14 @@ __device__ __forceinline__ void pq_merge(WarpSpace& W, WarpSmem* S, int& cur, in
 // per-warp statistics, flushed into the instance's counters
 struct JoinCounters {
     long long dist = 0, exp = 0, adj = 0, hyb = 0, rechk = 0, spill = 0;
+    // this warp's chunk of the instance's result pool: next slot, slots left
+    // (one pool atomic per chunk instead of one per query; unused tails are
+    // holes, never read: rows are located by count and segment)
+    unsigned long long pbase = 0;
+    int pleft = 0;
 };
+
+constexpr int POOL_CHUNK = 256;  // result-pool slots a warp reserves at a time
 
 __device__ __forceinline__ void flush_counters(const JoinParams& P, JoinCounters& c) {
     atomicAdd(P.ctr + C_DIST, (unsigned long long)c.dist);
@@ -532,6 +543,13 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         float4 q[NPL];
         load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
         const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
+        // everything else the query reads by its index, issued together: its
+        // plan, its adjacency row and the probe kernel's keys
+        const uint8_t route_q = P.route ? __ldg(P.route + qi) : (uint8_t)0;
+        const int beam_q = P.qbeam ? __ldg(P.qbeam + qi) : 0;
+        const int adj_l = lane < P.R ? __ldg(P.adj + qn * P.R + lane) : -1;
+        const float pk_l = (P.pkeys && lane < P.R) ? __ldg(P.pkeys + (int64_t)qi * (P.R + 1) + lane) : 0.f;
+        const float pk_entry = P.pkeys ? __ldg(P.pkeys + (int64_t)qi * (P.R + 1) + P.R) : 0.f;
 
         // ---- soft sharing, passes 2 and 3: what does C[parent] change?
         // decide(sc): 0 nothing, 1 one more visit (cache -> best), 2 re-run
@@ -554,7 +572,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             // a query without expansion, flag 3, never read N(results));
             // one result per lane, its whole adjacency row loaded at once
             bool seen = false;
-            if (flags & QF_PROBED) seen = lane < R && __ldg(P.adj + qn * R + lane) == sc;
+            if (flags & QF_PROBED) seen = lane < R && adj_l == sc;
             const int64_t sg = P.seg[qi];
             const int cnt = P.count[qi];
             // (an overflowed pool is re-run by the host: nothing to read then)
@@ -873,7 +891,16 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (snew) S->cand[__popc(sm & ((1u << lane) - 1u))] = sid;
             __syncwarp();
             int ns = __popc(sm);
-            group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane, P.xb, P.kpb);
+            if (P.pkeys && seedc < 0) {
+                // the entry's key is the probe kernel's; q's own key is never read
+                if (snew) {
+                    const int pos = __popc(sm & ((1u << lane) - 1u));
+                    S->ckey[pos] = sid == P.entry ? pk_entry : 0.f;
+                }
+            } else {
+                group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, ns, S->ckey, lane, P.xb,
+                                      P.kpb);
+            }
             __syncwarp();
             s.nvis += ns;
             float skey = FLT_MAX;
@@ -906,7 +933,8 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             // ---- probe N(q); lane j keeps slot j of q's list and that neighbour's key
             if (probe) {
                 c_adj++;
-                int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+                int v = adj_l;
+                const float pk = pk_l;  // its key from the probe kernel
                 nid_l = v;
                 if (v == P.entry) entry_in_nq = 1;
                 if (v >= 0 && v == seedc) seed_in_nq = 1;
@@ -918,8 +946,14 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                     int nc = __popc(nm);
                     int mypos = __popc(nm & ((1u << lane) - 1u));
                     if (nw) S->cand[mypos] = v;
-                    __syncwarp();
-                    group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane, P.xb, P.kpb);
+                    if (P.pkeys) {
+                        // slot `lane` of q's row: its key from the probe kernel
+                        if (nw) S->ckey[mypos] = pk;
+                    } else {
+                        __syncwarp();
+                        group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, nc, S->ckey, lane,
+                                              P.xb, P.kpb);
+                    }
                     __syncwarp();
                     s.nvis += nc;
                     int cv = lane < nc ? S->cand[lane] : -1;
@@ -949,20 +983,20 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         // scan); a planned beam > 0 selects the hybrid expansion with that
         // queue size, 0 the BFS expansion, and a negative beam no expansion
         // at all (the result is the probe's in-range points; flag 3)
-        const bool routed = P.route != nullptr && P.route[qi] != 0;
+        const bool routed = route_q != 0;
         int hbq = P.hbeam;
         int hyb = P.force;
         if (P.nm_w) {
             hyb = nm_hyb;
         } else if (P.qbeam) {
-            hbq = P.qbeam[qi];
+            hbq = beam_q;
             hyb = hbq > 0 ? 1 : (hbq < 0 ? 3 : 0);
         } else if (P.adapt && !P.separate && !failed && !routed) {
             if (!probe) {
                 // no probe ran (a seed was the greedy front); the rule still
                 // reads q's neighbourhood, evaluated here outside V
                 c_adj++;
-                const int v = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+                const int v = adj_l;
                 nid_l = v;
                 const bool dv = v >= 0 && v < P.nx;
                 const unsigned dm0 = __ballot_sync(VJ_FULL, dv);
@@ -1308,10 +1342,17 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             return true;
         }
 
-        // ---- results into the pool
-        unsigned long long off = 0;
-        if (lane == 0) off = atomicAdd(P.ctr + C_POOL, (unsigned long long)s.nres);
-        off = __shfl_sync(VJ_FULL, off, 0);
+        // ---- results into the pool (the warp's chunk; a new one when it runs out)
+        if (s.nres > cnt.pleft) {
+            const int want = max(s.nres, POOL_CHUNK);
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(P.ctr + C_POOL, (unsigned long long)want);
+            cnt.pbase = __shfl_sync(VJ_FULL, b, 0);
+            cnt.pleft = want;
+        }
+        const unsigned long long off = cnt.pbase;
+        cnt.pbase += (unsigned long long)s.nres;
+        cnt.pleft -= s.nres;
         if (lane == 0) {
             if (P.mode == 3) {
                 P.count2[qi] = s.nres;
@@ -1345,6 +1386,143 @@ __device__ __forceinline__ int pass_ticket_slot(int mode) {
 }
 
 // one join pass over one index: warps take queries from the pass's ticket
+// ---------------------------------------------------------------- probe keys
+// The greedy phase of the merged index probes N(q), the query's own
+// adjacency row (Alg. 4 under the merged rule), and every query's first
+// seeds are the entry and q itself.  k_probe evaluates those keys for all
+// queries ahead of the traversal: a warp per query streams the rows of N(q)
+// and the entry through a shared-memory ring (cp.async, PB_RING stages in
+// flight), so the gathers are bandwidth-bound instead of a chain of
+// dependent round trips per query.  The arithmetic is group_keys'
+// (the same lane slots, FMA order and group reduction), so every key equals
+// the one the traversal would compute.
+constexpr int PB_WARPS = 8;
+constexpr int PB_RING = 8;           // stages in flight per warp
+constexpr int PB_STAGE_MAX = 12288;  // bytes of one warp's ring at most
+
+struct PbParams {
+    const float* vec;
+    const float* invn;
+    const __nv_bfloat16* xb;  // BF16 copy (the traversal's gathers), or nullptr: FP32 rows
+    int kpb;
+    int dp4;
+    int metric;
+    const int32_t* adj;
+    int R;
+    int32_t entry;
+    int64_t nx, nq;
+    int ring;      // stages per warp (<= PB_RING)
+    int rowbytes;  // bytes copied per row (16-byte multiple)
+    int rowpitch;  // bytes between rows in the ring
+    float* pkeys;  // [nq][R + 1]
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// wait until at most n (0 .. PB_RING - 1) of this thread's groups are pending
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+    switch (n) {
+        case 0: cp_async_wait<0>(); break;
+        case 1: cp_async_wait<1>(); break;
+        case 2: cp_async_wait<2>(); break;
+        case 3: cp_async_wait<3>(); break;
+        case 4: cp_async_wait<4>(); break;
+        case 5: cp_async_wait<5>(); break;
+        case 6: cp_async_wait<6>(); break;
+        default: cp_async_wait<7>(); break;
+    }
+}
+
+template <int G, int NPL>
+__global__ void __launch_bounds__(PB_WARPS * 32) k_probe(const __grid_constant__ PbParams P) {
+    extern __shared__ __align__(16) unsigned char pb_raw[];
+    constexpr int NG = 32 / G;  // rows per stage (one per lane group)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / G, g = lane & (G - 1);
+    const int64_t qi = (int64_t)blockIdx.x * PB_WARPS + warp;
+    if (qi >= P.nq) return;
+    unsigned char* ring = pb_raw + (size_t)warp * P.ring * NG * P.rowpitch;
+    const int64_t qn = P.nx + qi;
+    const int R = P.R;
+    // slot j < R: adjacency slot j of q (held by lane j); slot R: the entry
+    const int vl = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+    float4 q[NPL];
+    load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
+    const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
+    const float invl = (P.metric && vl >= 0) ? __ldg(P.invn + vl) : 0.f;
+    const float inve = P.metric ? __ldg(P.invn + P.entry) : 0.f;
+    const int nstage = (R + 1 + NG - 1) / NG;
+    const int chunks = P.rowbytes >> 4;
+    auto issue = [&](int st) {
+        if (st < nstage) {
+            unsigned char* dst = ring + (size_t)(st % P.ring) * NG * P.rowpitch;
+            for (int r = 0; r < NG; r++) {
+                const int slot = st * NG + r;
+                const int vs = __shfl_sync(VJ_FULL, vl, slot & 31);
+                const int v = slot < R ? vs : (slot == R ? P.entry : -1);
+                if (v < 0) continue;
+                const unsigned char* src =
+                    P.xb ? reinterpret_cast<const unsigned char*>(P.xb + (int64_t)v * P.kpb)
+                         : reinterpret_cast<const unsigned char*>(P.vec + (int64_t)v * P.dp4 * 4);
+                for (int c = lane; c < chunks; c += 32) cp_async16(dst + (size_t)r * P.rowpitch + c * 16, src + c * 16);
+            }
+        }
+        cp_async_commit();  // an empty group past the last stage keeps the count
+    };
+    // group k of this thread carries stage k: after `ring` groups are issued
+    // ahead, waiting until ring - 1 are pending completes stage st
+    for (int st = 0; st < P.ring; st++) issue(st);
+    for (int st = 0; st < nstage; st++) {
+        cp_async_wait_dyn(P.ring - 1);
+        __syncwarp();
+        const int slot = st * NG + grp;
+        const int vs = __shfl_sync(VJ_FULL, vl, slot & 31);
+        const float ils = __shfl_sync(VJ_FULL, invl, slot & 31);
+        const int v = slot < R ? vs : (slot == R ? P.entry : -1);
+        const float il = slot < R ? ils : inve;
+        const unsigned char* row = ring + (size_t)(st % P.ring) * NG * P.rowpitch + (size_t)grp * P.rowpitch;
+        float a;
+        if (P.xb) {
+            uint2 xr[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; k++) {
+                const int idx = g + k * G;
+                xr[k] = idx < P.dp4 ? reinterpret_cast<const uint2*>(row)[idx] : make_uint2(0u, 0u);
+            }
+            a = group_sum<G>(slot_accum_bf16<NPL>(xr, q, P.metric));
+        } else {
+            float4 x[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; k++) {
+                const int idx = g + k * G;
+                x[k] = idx < P.dp4 ? reinterpret_cast<const float4*>(row)[idx] : f4zero();
+            }
+            a = group_sum<G>(slot_accum<NPL>(x, q, P.metric));
+        }
+        if (g == 0 && slot <= R)
+            P.pkeys[qi * (R + 1) + slot] = v < 0 ? FLT_MAX : (P.metric == 0 ? a : 1.0f - a * il * invq);
+        __syncwarp();  // the stage's buffer is read before the next issue overwrites it
+        issue(st + P.ring);
+    }
+    cp_async_wait<0>();
+}
+
+template <int G, int NPL>
+void launch_probe_t(const PbParams& P, cudaStream_t st) {
+    constexpr int NG = 32 / G;
+    const size_t smem = (size_t)PB_WARPS * P.ring * NG * P.rowpitch;
+    VJ_CUDA(cudaFuncSetAttribute(k_probe<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_probe<G, NPL><<<(unsigned)vj_div_up(P.nq, PB_WARPS), PB_WARPS * 32, smem, st>>>(P);
+    VJ_LAUNCH_CHECK();
+}
+
 template <int G, int NPL, int U>
 __global__ void __launch_bounds__(WPB * 32, JOIN_MIN_BLOCKS(NPL, U)) k_join(const __grid_constant__ JoinParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1490,12 +1668,16 @@ struct JoinDispatch {
     void (*launch)(const JoinParams&, int, cudaStream_t);
     int blocks_multi;
     void (*launch_multi)(const JoinBatch&, int, cudaStream_t);
+    int G;    // lanes per candidate of the class (the probe kernel's rows per stage: 32 / G)
+    int NPL;  // 16-byte slots per lane
+    void (*launch_probe)(const PbParams&, cudaStream_t);
 };
 
 template <int G, int NPL, int U>
 JoinDispatch dispatch_t(int cls, int num_sms) {
     return {cls, blocks_for(k_join<G, NPL, U>, num_sms), launch_join_t<G, NPL, U>,
-            blocks_for(k_join_multi<G, NPL, U>, num_sms), launch_join_multi_t<G, NPL, U>};
+            blocks_for(k_join_multi<G, NPL, U>, num_sms), launch_join_multi_t<G, NPL, U>, G, NPL,
+            launch_probe_t<G, NPL>};
 }
 
 constexpr int JOIN_CLASSES = 9;
@@ -1524,6 +1706,8 @@ struct JoinRun {
     int budget = 0;
     bool learned = false, soft = false;
     bool wait_first = false;  // separate indexes with sharing: one pass, parents first (mode 4)
+    bool probe = false;       // probe keys from k_probe before the first pass
+    PbParams pb;
     double ms_pro = 0.0;
     JoinParams P;
     JoinDispatch jd;
@@ -1662,9 +1846,24 @@ void join_setup(JoinRun& r) {
     P.hbeam = hbeam;
     P.conv = ix->p.conv_threshold;
     P.eps_key = ix->metric == VJ_L2 ? r.eps * r.eps : r.eps;
-    // FP32 keys: L2 squared distance by direct differences has relative error
-    // below (dp+2)u; cosine key absolute error below (dp+4)u (unit vectors)
-    P.band = 2.0f * (float)(ix->dp + 4) * VJ_F32_U * (ix->metric == VJ_L2 ? 1.0f : 4.0f) + 1e-6f;
+    // Rounding bound of the traversal's FP32 keys.  A lane sums its 4 NPL
+    // products (or squared differences) in one FMA chain, then log2(G) levels
+    // of a pairwise tree join the lanes: the dot product's error is at most
+    // gamma_m sum|x_i q_i| with m = 4 NPL + log2 G (gamma_m = m u / (1 - m u)).
+    //   L2: each difference adds one rounding, squared: relative error of the
+    //       key below (m + 2) u (1 + O(u));
+    //   cosine: 1 - <x,q> ix iq with ix, iq the reciprocal norms rounded once
+    //       from FP64: absolute error below gamma_m (Cauchy-Schwarz bounds
+    //       sum|x_i q_i| by |x||q|) + 4u (the norms and two products) + 2u
+    //       (the final subtraction).
+    // The band adds 25 % and a few u of slack; keys within it of eps (or of
+    // another key, for the FP64 tie decisions) are re-decided in FP64.
+    {
+        int lg = 0;
+        while ((1 << lg) < r.jd.G) lg++;
+        const int m = 4 * r.jd.NPL + lg;
+        P.band = (float)((double)(m + 8) * VJ_F32_U * 1.25) + 1e-9f;
+    }
     P.tie_tol = P.band;
     P.eps64 = (double)r.eps;
     P.cache = ix->cache.p;
@@ -1698,6 +1897,35 @@ void join_setup(JoinRun& r) {
     P.nm_ood = nullptr;
     P.separate = ix->separate ? 1 : 0;
     P.gbeam = ix->p.greedy_beam;
+    // probe keys ahead of the traversal (merged index: every query probes N(q))
+    P.pkeys = nullptr;
+    r.probe = false;
+    if (!ix->separate && !ix->nnmap) {
+        const int ng = 32 / r.jd.G;
+        const int rowbytes = P.xb ? ((ix->d * 2 + 15) / 16) * 16 : ix->dp * 4;
+        const int ring = std::min(PB_RING, PB_STAGE_MAX / (ng * rowbytes));
+        if (ring >= 2) {
+            ix->pkeys.ensure((size_t)nq * (ix->R + 1), s);
+            PbParams& B = r.pb;
+            B.vec = ix->vec.p;
+            B.invn = ix->invn.p;
+            B.xb = P.xb;
+            B.kpb = P.kpb;
+            B.dp4 = ix->dp / 4;
+            B.metric = ix->metric;
+            B.adj = ix->adj.p;
+            B.R = ix->R;
+            B.entry = ix->entry;
+            B.nx = ix->nx;
+            B.nq = nq;
+            B.ring = ring;
+            B.rowbytes = rowbytes;
+            B.rowpitch = rowbytes;
+            B.pkeys = ix->pkeys.p;
+            P.pkeys = ix->pkeys.p;
+            r.probe = true;
+        }
+    }
     if (ix->separate) {
         r.soft = false;
         r.wait_first = ix->p.work_sharing == VJ_WS_SOFT || ix->p.work_sharing == VJ_WS_HARD;
@@ -1980,6 +2208,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
         bind_pool(r);
         reset_attempt(r, s);
         VJ_CUDA(cudaEventRecord(ev.e[0], s));
+        if (r.probe && attempt == 0) {
+            r.jd.launch_probe(r.pb, s);
+            r.launches++;
+        }
         if (r.soft) {
             // speculative pass, parallel seed decisions, parent-ordered commit
             P.mode = 1;
@@ -2052,6 +2284,13 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
             if (pending[i]) todo.push_back(i);
         if (todo.empty()) break;
         VJ_CUDA(cudaEventRecord(ev.e[0], s));
+        if (attempt == 0) {
+            for (int i : todo) {
+                if (!runs[i].probe) continue;
+                runs[i].jd.launch_probe(runs[i].pb, s);
+                runs[i].launches++;
+            }
+        }
         for (int cls = 0; cls < JOIN_CLASSES; cls++) {
             std::vector<int> members;  // largest first: their long queries start early
             for (int i : todo)

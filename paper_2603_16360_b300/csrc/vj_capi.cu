@@ -103,6 +103,7 @@ static void free_index(vj_index* ix) {
     ix->xbf.free_(s);
     ix->wcs.free_(s);
     ix->wcb.free_(s);
+    ix->pkeys.free_(s);
     ix->nm_w.free_(s);
     ix->nm_wd.free_(s);
     ix->nm_ood.free_(s);

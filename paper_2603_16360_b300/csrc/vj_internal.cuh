@@ -155,6 +155,7 @@ struct vj_index {
     int knn_mode = VJ_KNN_ALL;  // which nodes a row's kNN list ranks (VJ_KNN_*)
     int64_t graph_rows = 0;     // nodes with a graph row (n, or nx for an NN-Map index)
     int64_t entry_rows = 0;     // the entry is the node nearest the centroid of nodes 0..entry_rows-1
+    DBuf<float> pkeys;         // [nq][R + 1] the probe kernel's keys (N(q), then the entry)
     DBuf<int32_t> nm_w;        // [nq] witness
     DBuf<double> nm_wd;        // [nq] its distance (FP64)
     DBuf<uint8_t> nm_ood;      // [nq] OOD bit
