@@ -17,8 +17,12 @@
 #include "vj_device.cuh"
 #include "vj_internal.cuh"
 
+#include <functional>
+
 struct vj_mlp;
 void vj_mlp_forward_device(vj_mlp* m, const float* x, int64_t n, float* y_out, cudaStream_t s);
+bool vj_mlp_forward_filled(vj_mlp* m, int64_t n, float* y_out, cudaStream_t s,
+                           const std::function<void(__nv_bfloat16*, int, const float*, const float*)>& fill);
 int vj_mlp_din(const vj_mlp* m);
 
 namespace {
@@ -85,8 +89,26 @@ __global__ void __launch_bounds__(256) k_query_stats(const float* __restrict__ v
     }
 }
 
-// warp per query: the seven features from lane 0, the query's coordinates
-// copied by all lanes (coalesced rows)
+// the seven features of query qi (every lane of the warp gets them)
+__device__ __forceinline__ void query_features(const float* __restrict__ stat, const float* __restrict__ dn,
+                                               int64_t qi, int R, float eps, int lane, float (&f)[VJ_NFEAT]) {
+    int nin = 0;
+    for (int j = lane; j < R; j += 32) nin += dn[qi * R + j] < eps;
+    nin = __reduce_add_sync(VJ_FULL, nin);
+    const float d1 = stat[qi * NSTAT + 0], d2 = stat[qi * NSTAT + 1], de = stat[qi * NSTAT + 2];
+    const float dnn = stat[qi * NSTAT + 3], n1 = stat[qi * NSTAT + 4];
+    auto cap = [](float x) { return fminf(x, 100.f); };
+    f[0] = cap(d1 / eps);
+    f[1] = cap(d2 / eps);
+    f[2] = d2 > 0.f ? cap(d1 / d2) : 100.f;
+    f[3] = cap(de / eps);
+    f[4] = cap(dnn / eps);
+    f[5] = n1 / (float)R;
+    f[6] = (float)nin / (float)R;
+}
+
+// warp per query: the seven features, then the query's coordinates copied by
+// all lanes (coalesced rows)
 __global__ void k_features(const float* __restrict__ vec, int dp, int d, int64_t nx, int64_t nq, int R,
                            const float* __restrict__ stat, const float* __restrict__ dn, float eps,
                            float* __restrict__ feat) {
@@ -95,23 +117,47 @@ __global__ void k_features(const float* __restrict__ vec, int dp, int d, int64_t
     if (qi >= nq) return;  // whole warps
     const int din = VJ_NFEAT + d;
     float* f = feat + qi * din;
-    int nin = 0;
-    for (int j = lane; j < R; j += 32) nin += dn[qi * R + j] < eps;
-    nin = __reduce_add_sync(VJ_FULL, nin);
+    float fv[VJ_NFEAT];
+    query_features(stat, dn, qi, R, eps, lane, fv);
     if (lane == 0) {
-        const float d1 = stat[qi * NSTAT + 0], d2 = stat[qi * NSTAT + 1], de = stat[qi * NSTAT + 2];
-        const float dnn = stat[qi * NSTAT + 3], n1 = stat[qi * NSTAT + 4];
-        auto cap = [](float x) { return fminf(x, 100.f); };
-        f[0] = cap(d1 / eps);
-        f[1] = cap(d2 / eps);
-        f[2] = d2 > 0.f ? cap(d1 / d2) : 100.f;
-        f[3] = cap(de / eps);
-        f[4] = cap(dnn / eps);
-        f[5] = n1 / (float)R;
-        f[6] = (float)nin / (float)R;
+#pragma unroll
+        for (int j = 0; j < VJ_NFEAT; j++) f[j] = fv[j];
     }
     const float* q = vec + (nx + qi) * dp;
     for (int i = lane; i < d; i += 32) f[VJ_NFEAT + i] = q[i];
+}
+
+// The predictor's input rows written directly: warp per query, the features
+// and coordinates standardised ((v - mu) / sd) and rounded to BF16 into rows
+// of k1 columns (zero padded), two columns per lane store.  The same values
+// and operations as k_features followed by the predictor's own conversion.
+__global__ void k_features_bf16(const float* __restrict__ vec, int dp, int d, int64_t nx, int64_t nq, int R,
+                                const float* __restrict__ stat, const float* __restrict__ dn, float eps, int k1,
+                                const float* __restrict__ mu, const float* __restrict__ sd,
+                                __nv_bfloat16* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (qi >= nq) return;  // whole warps
+    const int din = VJ_NFEAT + d;
+    float fv[VJ_NFEAT];
+    query_features(stat, dn, qi, R, eps, lane, fv);
+    const float* q = vec + (nx + qi) * dp;
+    auto value = [&](int j) -> float {
+        float v = 0.f;
+        if (j < din) {
+            v = j == 0 ? fv[0] : j == 1 ? fv[1] : j == 2 ? fv[2] : j == 3 ? fv[3] : j == 4 ? fv[4] : j == 5 ? fv[5]
+                : j == 6 ? fv[6] : q[j - VJ_NFEAT];
+            if (mu) v = (v - mu[j]) / sd[j];
+        }
+        return v;
+    };
+    __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(out + qi * k1);
+    for (int j2 = lane; j2 < k1 / 2; j2 += 32) {
+        __nv_bfloat162 w;
+        w.x = __float2bfloat16_rn(value(2 * j2));
+        w.y = __float2bfloat16_rn(value(2 * j2 + 1));
+        o2[j2] = w;
+    }
 }
 
 // plan from predictor outputs: route when the route logit exceeds lthr;
@@ -154,19 +200,39 @@ void vj_compute_features(vj_index* ix, float eps, float* feat_dev) {
     VJ_LAUNCH_CHECK();
 }
 
+// predictor outputs of every query at threshold eps into ix->pred_y
+static void predictor_forward(vj_index* ix, float eps) {
+    cudaStream_t s = ix->stream;
+    const int64_t nq = ix->nq;
+    const int din = VJ_NFEAT + ix->d;
+    VJ_REQUIRE(vj_mlp_din(ix->predictor) == din, VJ_ERR_ARG, "predictor input size %d != %d features",
+               vj_mlp_din(ix->predictor), din);
+    ix->pred_y.ensure((size_t)nq * 2, s);
+    // the tensor-core forward reads BF16 rows the features kernel writes
+    // directly; other predictor shapes take the FP32 features
+    VJ_REQUIRE(!ix->nnmap, VJ_ERR_STATE, "an NN-Map index has no query neighbourhoods for the predictor features");
+    ensure_query_stats(ix);
+    const bool fused = vj_mlp_forward_filled(
+        ix->predictor, nq, ix->pred_y.p, s,
+        [&](__nv_bfloat16* xbf, int k1, const float* mu, const float* sd) {
+            k_features_bf16<<<vj_div_up(nq * 32, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, ix->nx, nq, ix->R,
+                                                                    ix->qstat.p, ix->qdn.p, eps, k1, mu, sd, xbf);
+            VJ_LAUNCH_CHECK();
+        });
+    if (!fused) {
+        ix->feat.ensure((size_t)nq * din, s);
+        vj_compute_features(ix, eps, ix->feat.p);
+        vj_mlp_forward_device(ix->predictor, ix->feat.p, nq, ix->pred_y.p, s);
+    }
+}
+
 // the learned prologue: features -> predictor -> device plan (route flags,
 // beams, routed list); returns the number of routed queries
 int64_t vj_learned_prologue(vj_index* ix, float eps) {
     cudaStream_t s = ix->stream;
     const int64_t nq = ix->nq;
-    const int din = VJ_NFEAT + ix->d;
     VJ_REQUIRE(ix->predictor != nullptr, VJ_ERR_STATE, "learned join requested but no predictor is attached");
-    VJ_REQUIRE(vj_mlp_din(ix->predictor) == din, VJ_ERR_ARG, "predictor input size %d != %d features",
-               vj_mlp_din(ix->predictor), din);
-    ix->feat.ensure((size_t)nq * din, s);
-    ix->pred_y.ensure((size_t)nq * 2, s);
-    vj_compute_features(ix, eps, ix->feat.p);
-    vj_mlp_forward_device(ix->predictor, ix->feat.p, nq, ix->pred_y.p, s);
+    predictor_forward(ix, eps);
     ix->plan_route.ensure(nq, s);
     ix->plan_beam.ensure(nq, s);
     ix->routed.ensure(nq, s);
@@ -210,10 +276,7 @@ extern "C" vj_status vj_predictor_outputs(vj_index* ix, float eps, float* out) {
         VJ_REQUIRE(ix->predictor != nullptr, VJ_ERR_STATE, "no predictor attached");
         cudaStream_t s = ix->stream;
         const int64_t nq = ix->nq;
-        ix->feat.ensure((size_t)nq * (VJ_NFEAT + ix->d), s);
-        ix->pred_y.ensure((size_t)nq * 2, s);
-        vj_compute_features(ix, eps, ix->feat.p);
-        vj_mlp_forward_device(ix->predictor, ix->feat.p, nq, ix->pred_y.p, s);
+        predictor_forward(ix, eps);  // the learned prologue's own forward
         VJ_CUDA(cudaMemcpyAsync(out, ix->pred_y.p, (size_t)nq * 2 * sizeof(float), cudaMemcpyDeviceToHost, s));
         VJ_CUDA(cudaStreamSynchronize(s));
         return VJ_OK;

@@ -11,6 +11,8 @@
 // inputs before the first layer (kept with the weights).
 #include <float.h>
 
+#include <functional>
+
 #include <mutex>
 #include <numeric>
 #include <random>
@@ -522,17 +524,14 @@ bool tc_shape_ok(const vj_mlp* m) {
     return m->h1 % 64 == 0 && m->h1 >= 64 && m->h1 <= 256 && m->h2 % 16 == 0 && m->h2 >= 16 && m->h2 <= 256;
 }
 
-// tensor-core forward of n standardised-on-the-fly rows (x: n x din FP32)
-void forward_tc(vj_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s) {
+// tensor-core forward of the n BF16 input rows in m->xbf (standardised, k1
+// columns)
+void forward_tc_rows(vj_mlp* m, int64_t n, float* y, cudaStream_t s) {
     const Off o = offsets(m);
     const int k1 = (m->din + 63) / 64 * 64;
-    m->xbf.ensure((size_t)std::max<int64_t>(n, 1) * k1, s);
     m->w1bf.ensure((size_t)m->h1 * k1, s);
     m->w2bf.ensure((size_t)m->h2 * m->h1, s);
     m->err.ensure(1, s);
-    k_feat_bf16<<<vj_div_up(n * k1, 256), 256, 0, s>>>(x, n, m->din, k1, m->has_norm ? m->mu.p : nullptr, m->sd.p,
-                                                       m->xbf.p);
-    VJ_LAUNCH_CHECK();
     k_mat_bf16<<<vj_div_up((int64_t)m->h1 * k1, 256), 256, 0, s>>>(m->w.p + o.w1, m->h1, m->din, k1, m->w1bf.p);
     VJ_LAUNCH_CHECK();
     k_mat_bf16<<<vj_div_up((int64_t)m->h2 * m->h1, 256), 256, 0, s>>>(m->w.p + o.w2, m->h2, m->h1, m->h1, m->w2bf.p);
@@ -563,6 +562,16 @@ void forward_tc(vj_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s) 
     VJ_REQUIRE(herr == 0, VJ_ERR_TIMEOUT, "predictor forward: a pipeline wait timed out");
 }
 
+// tensor-core forward of n standardised-on-the-fly rows (x: n x din FP32)
+void forward_tc(vj_mlp* m, const float* x, int64_t n, float* y, cudaStream_t s) {
+    const int k1 = (m->din + 63) / 64 * 64;
+    m->xbf.ensure((size_t)std::max<int64_t>(n, 1) * k1, s);
+    k_feat_bf16<<<vj_div_up(n * k1, 256), 256, 0, s>>>(x, n, m->din, k1, m->has_norm ? m->mu.p : nullptr, m->sd.p,
+                                                       m->xbf.p);
+    VJ_LAUNCH_CHECK();
+    forward_tc_rows(m, n, y, s);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ internal API
@@ -583,6 +592,21 @@ void vj_mlp_forward_device(vj_mlp* m, const float* x, int64_t n, float* y_out, c
     VJ_CUDA(cudaStreamSynchronize(s));  // the scratch is free for the next caller
 }
 int vj_mlp_din(const vj_mlp* m) { return m->din; }
+
+// the tensor-core forward with its BF16 input rows written by `fill` (the
+// predictor's buffer, k1 columns, and the standardisation to apply: mu and
+// sd, or nullptr); false when the shape has no tensor-core path
+bool vj_mlp_forward_filled(vj_mlp* m, int64_t n, float* y_out, cudaStream_t s,
+                           const std::function<void(__nv_bfloat16*, int, const float*, const float*)>& fill) {
+    if (n <= 0) return true;
+    if (!tc_shape_ok(m)) return false;
+    std::lock_guard<std::mutex> lk(m->fwd_mu);
+    const int k1 = (m->din + 63) / 64 * 64;
+    m->xbf.ensure((size_t)n * k1, s);
+    fill(m->xbf.p, k1, m->has_norm ? m->mu.p : nullptr, m->sd.p);
+    forward_tc_rows(m, n, y_out, s);  // ends with a stream synchronize
+    return true;
+}
 
 // ------------------------------------------------------------------ C ABI
 template <class F>
