@@ -540,8 +540,15 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
         const int qi = (P.mode == 2 || P.mode == 4) ? P.order[t] : P.order1[t];
         const int64_t qn = P.nx + qi;
 
+        // q's slots: loaded at once for a full run; the decision passes (2, 3)
+        // load them only when they evaluate a seed or re-run the query
         float4 q[NPL];
-        load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
+        bool have_q = false;
+        auto need_q = [&]() {
+            if (!have_q) load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
+            have_q = true;
+        };
+        if (P.mode != 2 && P.mode != 3) need_q();
         const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
         // everything else the query reads by its index, issued together: its
         // plan, its adjacency row and the probe kernel's keys
@@ -560,6 +567,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             // a hybrid expansion depends on the order its seeds enter the
             // queue: any real seed means a re-run
             if (P.hyb[qi] == 1) return 2;
+            need_q();
             if (lane == 0) S->cand[0] = sc;
             __syncwarp();
             group_keys<G, NPL, U>(P.vec, P.invn, P.dp4, P.metric, q, invq, S->cand, 1, S->ckey, lane, P.xb, P.kpb);
@@ -623,12 +631,17 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             if (o != 2) return false;
             // a re-run for this seed runs here, off the parent chain; its
             // result is staged and pass 3 commits it if the seed stays
+            need_q();
             seedc = sc;
             if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
         }
         if (P.mode == 2) {
-            // pass 3, parent before child: the final C[parent]
+            // pass 3, parent before child: the final C[parent].  What pass 2
+            // decided is read before the wait, so that only the commit follows it.
             const int par = __ldg(P.parent + qi);
+            const int sca_q = P.sca[qi];
+            const int outc_q = P.outc[qi];
+            const int cout_q = P.cout[qi];
             int sc = -1;
             if (par >= 0 && lane == 0) {
                 long long spins = 0;
@@ -648,16 +661,16 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                         break;
                     }
                     __nanosleep(ns);
-                    if (ns < 256) ns <<= 1;
+                    if (ns < 64) ns <<= 1;  // a short poll: the chain's latency is the pass's time
                 }
             }
             sc = __shfl_sync(VJ_FULL, sc, 0);
             if (sc == -2) return true;
             int best, o;
-            const bool same = sc == P.sca[qi];  // usually: pass 2 decided for this very seed
+            const bool same = sc == sca_q;  // usually: pass 2 decided for this very seed
             if (same) {
-                o = P.outc[qi];
-                best = P.cout[qi];
+                o = outc_q;
+                best = cout_q;
             } else {
                 o = decide(sc, best);
             }
@@ -688,6 +701,7 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
                 return false;
             }
             // re-run from the start with the cached seed
+            need_q();
             seedc = sc;
             if (lane == 0) atomicAdd(P.ctr + C_RESTART, 1ull);
         }
@@ -1903,7 +1917,8 @@ void join_setup(JoinRun& r) {
     if (!ix->separate && !ix->nnmap) {
         const int ng = 32 / r.jd.G;
         const int rowbytes = P.xb ? ((ix->d * 2 + 15) / 16) * 16 : ix->dp * 4;
-        const int ring = std::min(PB_RING, PB_STAGE_MAX / (ng * rowbytes));
+        const int rowpitch = (rowbytes + 127) / 128 * 128;
+        const int ring = std::min(PB_RING, PB_STAGE_MAX / (ng * rowpitch));
         if (ring >= 2) {
             ix->pkeys.ensure((size_t)nq * (ix->R + 1), s);
             PbParams& B = r.pb;
@@ -1920,7 +1935,7 @@ void join_setup(JoinRun& r) {
             B.nq = nq;
             B.ring = ring;
             B.rowbytes = rowbytes;
-            B.rowpitch = rowbytes;
+            B.rowpitch = rowpitch;
             B.pkeys = ix->pkeys.p;
             P.pkeys = ix->pkeys.p;
             r.probe = true;
