@@ -127,6 +127,8 @@ def make_workload(name, scale, replica=0):
         return inputs.sift_like(seed=1236 + 1000 * replica, scale=scale, nh=10_000)
     if name == "gauss_small":
         return inputs.gauss_small()
+    if name == "gauss_wide":
+        return inputs.gauss_wide(seed=1237 + 1000 * replica, scale=scale)
     if name == "angular_one":
         # one instance of the angular collection's recipe: 300K x 30K (times scale), d = 100 cosine
         nx, nq = int(3e5 * scale), int(3e4 * scale)
@@ -586,6 +588,108 @@ def profile_modes(args, vj, ix, w, build_s, binfo):
     vj.vj_set_plan(ix, None, None)
 
 
+def fp8_gemm_peak(torch):
+    """Dense E4M3 GEMM throughput (TFLOP/s) of the library path (torch._scaled_mm, 8192^3, best of 10 by CUDA
+    events): the measured FP8 denominator beside the nominal ratio (2x the measured BF16 peak)."""
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda")
+
+        def f():
+            return torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            f()
+        best = None
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e9, None
+    except Exception as e:  # no FP8 GEMM in this torch build
+        return None, str(e).splitlines()[0][:200]
+
+
+def precision_mode(args, vj, torch, ix, w, build_s, binfo, log):
+    """--mode precision: the exact join (the brute-force scan of every query,
+    Sec. 3.2's NLJ) with BF16 and with FP8-e4m3 tiles on the same index.  Both
+    re-decide every candidate from the FP32 vectors (FP64 near eps), so their
+    rows are identical; the precision changes the tile throughput and the
+    candidate count.  Per precision: scan kernel time, TFLOP/s and fraction of
+    the tensor peak, candidates per query, whole-join time.  Error against FP64
+    on sampled queries: pair ids outside the 1e-4 eps band and the largest
+    relative distance error.  One JSON line."""
+    hbm, bf16_peak, kind = _peaks()
+    eps = calibrate_eps(vj, ix, w, w.target_matches)
+    flops = 2.0 * w.nq * w.nx * w.d
+    out = {"mode": "precision", "workload": f"{w.name}: X={w.nx} Q={w.nq} d={w.d} "
+           f"{'L2' if w.metric == 0 else 'cosine'}, eps for a mean of {w.target_matches:g} matches/query",
+           "eps": eps, "build_s": build_s, "build": binfo, "flops_per_scan": flops}
+    f8_peak, f8_err = fp8_gemm_peak(torch)
+    out["fp8_gemm_tflops_measured"] = f8_peak
+    if f8_err:
+        out["fp8_gemm_error"] = f8_err
+    results = {}
+    for name, prec, peak in (("bf16", vj.VJ_PREC_BF16, bf16_peak), ("fp8", vj.VJ_PREC_FP8, 2.0 * bf16_peak)):
+        vj.vj_set_join_params(ix, scan=prec)
+        r = vj.vj_join_exact(ix, eps)  # first call: the data-side tile rows and the candidate arrays
+        reps = []
+        for _ in range(max(1, args.reps)):
+            r = vj.vj_join_exact(ix, eps)
+            reps.append((r.stats["ms_scan"], r.stats["ms_total"]))
+        ms_scan = statistics.median(x[0] for x in reps)
+        ms_total = statistics.median(x[1] for x in reps)
+        nnz = int(r.offsets[-1])
+        results[name] = r
+        out[name] = {"ms_scan": ms_scan, "ms_total": ms_total, "scan_tflops": flops / ms_scan / 1e9,
+                     "peak_tflops": peak, "peak_kind": f"{kind} bf16 burst" + (" x 2 (nominal FP8:BF16)" if
+                                                                              name == "fp8" else ""),
+                     "frac": flops / ms_scan / 1e9 / peak,
+                     "candidates_per_query": r.stats["scan_candidates"] / w.nq, "pairs": nnz,
+                     "queries_per_s": w.nq / ms_total * 1e3}
+        if name == "fp8" and f8_peak:
+            out[name]["frac_of_measured_fp8_gemm"] = flops / ms_scan / 1e9 / f8_peak
+        log(f"{name}: {out[name]}")
+    vj.vj_set_join_params(ix, scan=vj.VJ_PREC_BF16)
+    rb, r8 = results["bf16"], results["fp8"]
+    out["same_rows"] = bool(np.array_equal(rb.offsets, r8.offsets) and np.array_equal(rb.ids, r8.ids))
+    # FP64 check on sampled queries: distances to every data vector on the GPU in FP64
+    rng = np.random.default_rng(w.seed + 11)
+    qs = np.sort(rng.choice(w.nq, size=min(64, w.nq), replace=False))
+    Xd = torch.from_numpy(host(w.X)).cuda()
+    Qs = torch.from_numpy(host(w.Q)[qs]).cuda().double()
+    band_n, diff_n, max_rel, checked = 0, 0, 0.0, 0
+    for i, q in enumerate(qs):
+        dd = torch.zeros(w.nx, dtype=torch.float64, device="cuda")
+        for a in range(0, w.nx, 1 << 18):
+            xb = Xd[a:a + (1 << 18)].double()
+            if w.metric == 0:
+                dd[a:a + len(xb)] = (xb - Qs[i]).pow(2).sum(1).sqrt()
+            else:
+                dd[a:a + len(xb)] = 1.0 - (xb @ Qs[i]) / (xb.norm(dim=1) * Qs[i].norm())
+        d64 = dd.cpu().numpy()
+        exp = set(np.nonzero(d64 < eps)[0].tolist())
+        lo, hi = int(rb.offsets[q]), int(rb.offsets[q + 1])
+        got = set(rb.ids[lo:hi].tolist())
+        near = set(np.nonzero(np.abs(d64 - eps) <= 1e-4 * eps)[0].tolist())
+        band_n += len(near)
+        diff_n += len((got ^ exp) - near)
+        for j in range(lo, hi):
+            x = int(rb.ids[j])
+            max_rel = max(max_rel, abs(float(rb.dists[j]) - d64[x]) / max(d64[x], 1e-30))
+            checked += 1
+    del Xd
+    out["fp64_check"] = {"queries": len(qs), "pairs_checked": checked, "pairs_differing_outside_band": diff_n,
+                         "pairs_in_band": band_n, "max_rel_dist_err": max_rel}
+    print(json.dumps(out), flush=True)
+
+
 VARIANT_SETTINGS = {
     "nnmap": [("BFS expansion", dict(work_sharing=0, adapt_hybrid=0, force_hybrid=0, hybrid_beam=256)),
               ("adaptive hybrid, queue 64", dict(work_sharing=0, adapt_hybrid=1, force_hybrid=0, hybrid_beam=64)),
@@ -686,7 +790,7 @@ def main():
     ap.add_argument("--collection-learned", action="store_true",
                     help="angular_collection: also time one shared predictor's learned route")
     ap.add_argument("--quiet", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "build", "join", "nnmap", "separate"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "build", "join", "nnmap", "separate", "precision"],
                     help="build: generate the workload and build the index only (profiling the build); join: "
                          "also run --reps joins with every query planned --plan (profiling the traversal); "
                          "nnmap: build an NN-Map index instead and time its joins (BFS, adaptive and forced "
@@ -739,6 +843,10 @@ def main():
     log(f"build {build_s:.1f}s {binfo}")
     if args.mode in VARIANT_SETTINGS:
         variant_mode(args, vj, torch, ix, w, build_s, binfo, log)
+        ix.free()
+        return
+    if args.mode == "precision":
+        precision_mode(args, vj, torch, ix, w, build_s, binfo, log)
         ix.free()
         return
     if args.mode != "bench":

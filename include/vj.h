@@ -69,8 +69,9 @@ typedef struct {
     int force_hybrid;     /* cfg.force_hybrid (Alg. 6), default 0 */
     int precision;        /* VJ_PREC_* of the kNN build's distance tiles: BF16 (default) sweeps on the
                              tensor cores, FP32 on the SIMT units; candidates are re-ranked with exact
-                             keys and certified either way, so the lists are the same.  FP8 is not
-                             implemented (VJ_ERR_ARG). */
+                             keys and certified either way, so the lists are the same.  FP8 is
+                             accepted only by the scan (the join-time field scan), not by the
+                             build (VJ_ERR_ARG). */
     int learned;          /* joins: 1 = plan every query with the attached predictor
                              (vj_attach_predictor) in place of Alg. 6's rule; default 0 */
     int route_bruteforce; /* reserved, must be 0 */
@@ -107,6 +108,14 @@ typedef struct {
                              the parent's result row (HARD); with sharing, queries run parents
                              first.  adapt_hybrid does not apply (the rule reads the merged
                              graph); force_hybrid does.  Exclusive with nnmap; default 0 */
+    int scan;             /* joins: VJ_PREC_* of the brute-force scan's tiles (vj_join_exact, routed
+                             queries): BF16 (default; FP32 selects it too, there is no FP32 tile
+                             path) or FP8 (E4M3 operands, a power-of-two scale per data row and one
+                             for the scanned query rows, FP32 accumulation).  Either way a pair is
+                             a candidate when its tile value is within a rounding bound of eps, and
+                             every candidate is re-decided from the FP32 vectors (FP64 near eps), so
+                             the result is the same; the precision changes the candidate count.
+                             A join-time field */
 } vj_params;
 
 /* Per-call counters and device timings of a join. */
@@ -382,6 +391,47 @@ vj_status vj_join_exact(vj_index *ix, float eps, vj_result **out);
 vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int64_t nq, int d,
                                 vj_metric metric, float eps, int64_t *offsets, int32_t *ids,
                                 float *dists, int64_t cap, int64_t *nnz, void *stream);
+
+/* Traversal tuning (no paper counterpart: the paper's join is single-threaded
+ * CPU code).  The GPU traversal gathers each vector row with a group of
+ * `lanes` threads holding `slots` 16-byte pieces each (a row of up to
+ * lanes * slots * 4 floats) and keeps `inflight` rows in flight per group; it
+ * runs as a persistent grid of `blocks` blocks, and the probe of N(q) streams
+ * rows through a ring of `probe_ring` stages per warp.  Every setting computes
+ * the same join (in-range decisions near eps are re-decided in FP64; only
+ * the FP32 summation order of a key changes), so tuning changes time only.
+ *
+ * vj_autotune times joins of the index at eps (the index's current join
+ * parameters and plan) under each candidate setting: the default class (the
+ * smallest that holds the row) and the next two larger ones, each with the
+ * full and half persistent grid, and, on a merged index, shallower probe
+ * rings for the default class.  Each setting runs one untimed join and then
+ * `reps` (1..10) timed ones; its time is the median device time of the whole
+ * join (vj_stats.ms_total).  A setting counts only when its joins give the
+ * same pair count and distance evaluations as the default setting.  The
+ * fastest is kept on the index for later joins (vj_join, vj_join_batch) and
+ * the report lists every setting tried.  The index's previous setting is
+ * restored on error. */
+#define VJ_TUNE_MAX 16
+typedef struct {
+    int n;                      /* settings tried (the first is the default) */
+    int lanes[VJ_TUNE_MAX];     /* threads per gathered row */
+    int slots[VJ_TUNE_MAX];     /* 16-byte pieces per thread */
+    int inflight[VJ_TUNE_MAX];  /* rows in flight per group */
+    int blocks[VJ_TUNE_MAX];    /* persistent blocks of the traversal */
+    int probe_ring[VJ_TUNE_MAX];/* probe ring stages per warp (0: no probe kernel) */
+    double ms[VJ_TUNE_MAX];     /* median device time of the join */
+    int valid[VJ_TUNE_MAX];     /* 1: same pairs and evaluations as the default */
+    int chosen;                 /* index of the setting kept on the index */
+} vj_tune_report;
+vj_status vj_autotune(vj_index *ix, float eps, int reps, vj_tune_report *report);
+
+/* Set the traversal setting directly (for instance the one vj_autotune chose
+ * on another index of the same row width).  lanes = 0 selects the default
+ * class (slots and inflight are then ignored); otherwise (lanes, slots,
+ * inflight) must name a class whose rows hold d floats, else VJ_ERR_ARG.
+ * blocks = 0 and probe_ring = 0 select the defaults; probe_ring is 2..8. */
+vj_status vj_set_tuning(vj_index *ix, int lanes, int slots, int inflight, int blocks, int probe_ring);
 
 /* Bounded dependency wait of soft work sharing (for tests of its failure
  * path; no paper counterpart).  max_polls > 0 limits the polls of a query's

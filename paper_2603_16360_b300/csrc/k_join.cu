@@ -1429,6 +1429,7 @@ struct PbParams {
     int rowbytes;  // bytes copied per row (16-byte multiple)
     int rowpitch;  // bytes between rows in the ring
     float* pkeys;  // [nq][R + 1]
+    const int32_t* porder;  // [nq] dispatch order (warp t probes query porder[t]), or nullptr: index order
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -1460,8 +1461,9 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_probe(const __grid_constant__
     constexpr int NG = 32 / G;  // rows per stage (one per lane group)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, g = lane & (G - 1);
-    const int64_t qi = (int64_t)blockIdx.x * PB_WARPS + warp;
-    if (qi >= P.nq) return;
+    const int64_t t = (int64_t)blockIdx.x * PB_WARPS + warp;
+    if (t >= P.nq) return;
+    const int64_t qi = P.porder ? (int64_t)P.porder[t] : t;
     unsigned char* ring = pb_raw + (size_t)warp * P.ring * NG * P.rowpitch;
     const int64_t qn = P.nx + qi;
     const int R = P.R;
@@ -1696,20 +1698,45 @@ JoinDispatch dispatch_t(int cls, int num_sms) {
 
 constexpr int JOIN_CLASSES = 9;
 
-JoinDispatch pick(int dp4, int num_sms) {
-    if (dp4 <= 8) return dispatch_t<8, 1, 4>(0, num_sms);
-    if (dp4 <= 16) return dispatch_t<8, 2, 4>(1, num_sms);
-    if (dp4 <= 32) return dispatch_t<8, 4, 2>(2, num_sms);
-    if (dp4 <= 64) return dispatch_t<16, 4, 2>(3, num_sms);
-    if (dp4 <= 128) return dispatch_t<32, 4, 2>(4, num_sms);
-    // up to 768 floats: six 16-byte slots per lane and two candidates in
-    // flight per warp (eight slots and one candidate left the warp waiting
-    // on one row's gathers at a time)
-    if (dp4 <= 192) return dispatch_t<32, 6, 2>(8, num_sms);
-    if (dp4 <= 256) return dispatch_t<32, 8, 1>(5, num_sms);
-    if (dp4 <= 512) return dispatch_t<32, 16, 1>(6, num_sms);
-    return dispatch_t<32, 32, 1>(7, num_sms);
+// the classes by row capacity (16-byte slots per row: G * NPL), with their
+// template parameters; the tuner may run a row on any class that holds it
+struct JoinClass {
+    int cls, G, NPL, U;
+};
+constexpr JoinClass JOIN_CLASS_TABLE[JOIN_CLASSES] = {{0, 8, 1, 4},  {1, 8, 2, 4},  {2, 8, 4, 2},
+                                                      {3, 16, 4, 2}, {4, 32, 4, 2}, {8, 32, 6, 2},
+                                                      {5, 32, 8, 1}, {6, 32, 16, 1}, {7, 32, 32, 1}};
+
+JoinDispatch dispatch_cls(int cls, int num_sms) {
+    switch (cls) {
+        case 0: return dispatch_t<8, 1, 4>(0, num_sms);
+        case 1: return dispatch_t<8, 2, 4>(1, num_sms);
+        case 2: return dispatch_t<8, 4, 2>(2, num_sms);
+        case 3: return dispatch_t<16, 4, 2>(3, num_sms);
+        case 4: return dispatch_t<32, 4, 2>(4, num_sms);
+        case 8: return dispatch_t<32, 6, 2>(8, num_sms);
+        case 5: return dispatch_t<32, 8, 1>(5, num_sms);
+        case 6: return dispatch_t<32, 16, 1>(6, num_sms);
+        default: return dispatch_t<32, 32, 1>(7, num_sms);
+    }
 }
+
+// the smallest class that holds a row of dp4 slots.  Up to 768 floats: six
+// 16-byte slots per lane and two candidates in flight per warp (eight slots
+// and one candidate left the warp waiting on one row's gathers at a time)
+int pick_cls_only(int dp4) {
+    if (dp4 <= 8) return 0;
+    if (dp4 <= 16) return 1;
+    if (dp4 <= 32) return 2;
+    if (dp4 <= 64) return 3;
+    if (dp4 <= 128) return 4;
+    if (dp4 <= 192) return 8;
+    if (dp4 <= 256) return 5;
+    if (dp4 <= 512) return 6;
+    return 7;
+}
+
+JoinDispatch pick(int dp4, int num_sms) { return dispatch_cls(pick_cls_only(dp4), num_sms); }
 
 // Host state of one join between its phases: setup (prologue, buffers,
 // parameters), the traversal passes (alone or inside a multi-instance
@@ -1791,7 +1818,11 @@ void join_setup(JoinRun& r) {
     ix->ctr.ensure(16, s);
 
     static_assert(FB * 32 <= CCAP, "BFS batch exceeds the candidate buffer");
-    r.jd = pick(ix->dp / 4, ix->num_sms);
+    r.jd = ix->tune_cls >= 0 ? dispatch_cls(ix->tune_cls, ix->num_sms) : pick(ix->dp / 4, ix->num_sms);
+    if (ix->tune_blocks > 0) {
+        r.jd.blocks = std::min(r.jd.blocks, ix->tune_blocks);
+        r.jd.blocks_multi = std::min(r.jd.blocks_multi, ix->tune_blocks);
+    }
     // global visited regions: up to 2^17 slots (64K visited nodes per query),
     // no larger than needed for the whole node set
     int gmax = 1 << 17;
@@ -1918,7 +1949,8 @@ void join_setup(JoinRun& r) {
         const int ng = 32 / r.jd.G;
         const int rowbytes = P.xb ? ((ix->d * 2 + 15) / 16) * 16 : ix->dp * 4;
         const int rowpitch = (rowbytes + 127) / 128 * 128;
-        const int ring = std::min(PB_RING, PB_STAGE_MAX / (ng * rowpitch));
+        int ring = std::min(PB_RING, PB_STAGE_MAX / (ng * rowpitch));
+        if (ix->tune_ring >= 2) ring = std::min(ring, ix->tune_ring);
         if (ring >= 2) {
             ix->pkeys.ensure((size_t)nq * (ix->R + 1), s);
             PbParams& B = r.pb;
@@ -1937,6 +1969,7 @@ void join_setup(JoinRun& r) {
             B.rowbytes = rowbytes;
             B.rowpitch = rowpitch;
             B.pkeys = ix->pkeys.p;
+            B.porder = ix->porder.n >= (size_t)nq ? ix->porder.p : nullptr;
             P.pkeys = ix->pkeys.p;
             r.probe = true;
         }
@@ -2376,3 +2409,17 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
     for (int i = 0; i < n; i++) VJ_CUDA(cudaStreamWaitEvent(ixs[i]->stream, ev.e[4], 0));
     par_for(n, [&](int i) { join_finish(runs[i], st + i, nnz_out + i); });
 }
+
+// ------------------------------------------------------------------ tuning
+// The traversal settings a tuner may choose for rows of dp4 slots: the
+// default class (the smallest that holds the row) and the next larger ones.
+int vj_join_class_count() { return JOIN_CLASSES; }
+void vj_join_class_info(int k, int* cls, int* G, int* NPL, int* U) {
+    const JoinClass& c = JOIN_CLASS_TABLE[k];
+    *cls = c.cls;
+    *G = c.G;
+    *NPL = c.NPL;
+    *U = c.U;
+}
+int vj_join_default_class(int dp4) { return pick_cls_only(dp4); }
+int vj_join_max_blocks(int cls, int num_sms) { return dispatch_cls(cls, num_sms).blocks; }

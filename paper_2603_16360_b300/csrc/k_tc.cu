@@ -28,6 +28,9 @@
 #include <climits>
 #include <functional>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "vj_device.cuh"
 #include "vj_internal.cuh"
 #include "vj_tc.cuh"
@@ -95,10 +98,16 @@ struct __align__(1024) WdSmem {
 // K-major, M = 128, N = 256
 constexpr uint32_t WD_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WD_BN >> 3) << 17) |
                               ((uint32_t)(WD_BM >> 4) << 24);
+// kind::f8f6f4 instruction descriptor: FP32 accumulate, E4M3 A and B (format
+// code 0), both K-major, M = 128, N = 256.  A k-block is then 128 E4M3
+// columns (the same 128-byte swizzle rows), four K = 32 steps.
+constexpr uint32_t WD_IDESC_F8 = (1u << 4) | ((uint32_t)(WD_BN >> 3) << 17) | ((uint32_t)(WD_BM >> 4) << 24);
 
 struct WdParams {
     int64_t nrows, ncols;  // A rows, B rows
-    int nkb;               // K blocks of 64 columns
+    int nkb;               // K blocks of 128 bytes (64 BF16 or 128 E4M3 columns)
+    int kk_last;           // K steps (of 32 bytes) in the last K block; 0: all four (its tail past the
+                           // row is zero, so skipping those steps changes nothing)
     int nrt;               // A row tiles
     int nct;               // B tiles a sweep visits (tile k of the sweep is B tile k * tstride)
     int tstride;
@@ -193,7 +202,7 @@ __device__ __forceinline__ void wd_append(const WdParams& P, const uint32_t (&va
     }
 }
 
-template <int EPI>
+template <int EPI, int F8 = 0>
 __global__ void __launch_bounds__(WD_THREADS, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, WdParams P) {
     extern __shared__ uint8_t wd_raw[];
@@ -242,8 +251,10 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                             break;
                         }
                         mbar_arrive_tx(&S.full[s], WD_A_BYTES + WD_B_BYTES);
-                        tma_load_2d(S.A[s], &tA, &S.full[s], kb * TC_BK, rt * WD_BM);
-                        tma_load_2d(S.B[s], &tB, &S.full[s], kb * TC_BK, ct * P.tstride * WD_BN);
+                        // x in elements of the map: 64 BF16 or 128 E4M3 bytes per K block
+                        const int kx = F8 ? kb * 128 : kb * TC_BK;
+                        tma_load_2d(S.A[s], &tA, &S.full[s], kx, rt * WD_BM);
+                        tma_load_2d(S.B[s], &tB, &S.full[s], kx, ct * P.tstride * WD_BN);
                         issued |= 1u << s;
                         last_ph = (last_ph & ~(1u << s)) | (ph << s);
                         if (++s == WD_STAGES) {
@@ -290,10 +301,18 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                         tc_fence_after();
                         const uint64_t ad = sdesc_sw128(su32(S.A[s]));
                         const uint64_t bd = sdesc_sw128(su32(S.B[s]));
+                        const int nkk = (kb == P.nkb - 1 && P.kk_last > 0) ? P.kk_last : TC_BK / 16;
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; kk++) {
-                            // advance 16 BF16 (32 bytes) along K inside the swizzled rows
-                            tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC, (kb | kk) != 0);
+                            // advance 32 bytes along K (16 BF16 or 32 E4M3) inside the swizzled rows
+                            if (kk < nkk) {
+                                if constexpr (F8)
+                                    tc_mma_f8(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC_F8,
+                                              (kb | kk) != 0);
+                                else
+                                    tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC,
+                                           (kb | kk) != 0);
+                            }
                         }
                         tc_commit(&S.empty[s]);
                         if (++s == WD_STAGES) {
@@ -1074,6 +1093,165 @@ __global__ void k_key_from_w(const float* __restrict__ sqn, const int32_t* __res
     ck[e] = sqn[nx + cq[e]] + sqn[cx[e]] - cw[e];
 }
 
+// ---------------------------------------------------------------- measured rounding bound
+// For tile rows that are not exact copies of the inputs, the bound on a tile
+// value comes from each row's own rounding error instead of the worst case
+// per coordinate.  With a^ = a + da and b^ = b + db the rows as the tiles hold
+// them (scale removed),
+//   |<a^, b^> - <a, b>| <= |da| |b| + |a| |db| + |da| |db|      (Cauchy-Schwarz),
+// and the tensor core's sum of the exact products deviates from <a^, b^> by at
+// most gamma |a^| |b^|.  The scanned rows enter through their largest |da| and
+// |a|, so the whole bound is a per-column constant of the epilogue.  a is the
+// input row (L2) or the exact unit vector a / |a| (cosine).
+constexpr float F8_MAX = 448.f;  // largest finite E4M3 value
+
+// largest power of two s with amax * s <= 448 (1 for a zero row)
+__device__ __forceinline__ float f8_scale(float amax) {
+    if (!(amax > 0.f)) return 1.f;
+    int e;
+    frexpf(F8_MAX / amax, &e);  // 448 / amax = m 2^e, m in [0.5, 1)
+    return ldexpf(1.f, e - 1);
+}
+
+__device__ __forceinline__ float f8_value(__nv_fp8_storage_t q) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+}
+
+// coordinate k of the row the tiles approximate: its FP32 value as quantised
+// (x, or x / |x| rounded to FP32) and its exact FP64 value
+__device__ __forceinline__ void tile_coord(const float* v, int k, int cosine, double inv, float& y, double& ex) {
+    const double x = (double)v[k];
+    ex = cosine ? x * inv : x;
+    y = (float)ex;
+}
+
+// largest |coordinate| over the rows (node ids rows[0..n)), as float bits
+__global__ void k_tile_amax(const float* __restrict__ vec, const double* __restrict__ sqn64, int dp, int d,
+                            int cosine, const int32_t* __restrict__ rows, int64_t n, unsigned int* __restrict__ amax) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t src = rows ? (int64_t)rows[r] : r;
+    const double nn = sqn64[src];
+    const double inv = (cosine && nn > 0.0) ? 1.0 / sqrt(nn) : 1.0;
+    float m = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        float y;
+        double ex;
+        tile_coord(vec + src * dp, k, cosine, inv, y, ex);
+        m = fmaxf(m, fabsf(y));
+    }
+    const unsigned int mb = __reduce_max_sync(VJ_FULL, __float_as_uint(m));
+    if (lane == 0) atomicMax(amax, mb);
+}
+
+// Tile rows of the rows `rows` (node ids; nullptr = 0..n-1), kb elements each
+// (zero past d), warp per row:
+//   F8 = 0: out is BF16 rows already written (k_to_bf16); only the error is
+//           measured;
+//   F8 = 1: out receives E4M3 bytes of y * s, s a power of two: the row's own
+//           scale (amax == nullptr) or the shared one from *amax; rs[r] = 1 / s.
+// err[r] = |row^ - row| in FP64, rounded up; emax / nmax (optional) collect the
+// largest error and the largest |row| (float bits, atomicMax).
+template <int F8>
+__global__ void k_tile_rows(const float* __restrict__ vec, const double* __restrict__ sqn64, int dp, int d,
+                            int cosine, const int32_t* __restrict__ rows, int64_t n, int kb,
+                            const unsigned int* __restrict__ amax, void* __restrict__ out, float* __restrict__ rs,
+                            float* __restrict__ err, unsigned int* __restrict__ emax, unsigned int* __restrict__ nmax) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t src = rows ? (int64_t)rows[r] : r;
+    const float* v = vec + src * dp;
+    const double nn = sqn64[src];
+    const double inv = (cosine && nn > 0.0) ? 1.0 / sqrt(nn) : 1.0;
+    float s = 1.f;
+    if constexpr (F8) {
+        float m;
+        if (amax) {
+            m = __uint_as_float(*amax);
+        } else {
+            m = 0.f;
+            for (int k = lane; k < d; k += 32) {
+                float y;
+                double ex;
+                tile_coord(v, k, cosine, inv, y, ex);
+                m = fmaxf(m, fabsf(y));
+            }
+            m = __uint_as_float(__reduce_max_sync(VJ_FULL, __float_as_uint(m)));
+        }
+        s = f8_scale(m);
+    }
+    double e2 = 0.0;
+    for (int k = lane; k < kb; k += 32) {
+        float y = 0.f;
+        double ex = 0.0;
+        if (k < d) tile_coord(v, k, cosine, inv, y, ex);
+        double got;
+        if constexpr (F8) {
+            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(y * s, __NV_SATFINITE, __NV_E4M3);
+            reinterpret_cast<uint8_t*>(out)[r * (int64_t)kb + k] = q;
+            got = (double)f8_value(q) / (double)s;
+        } else {
+            got = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(out)[r * (int64_t)kb + k]);
+        }
+        const double t = got - ex;
+        e2 += t * t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(VJ_FULL, e2, o);
+    if (lane == 0) {
+        const float e = __double2float_ru(sqrt(e2) * (1.0 + 1e-12));
+        if (F8 && rs) rs[r] = 1.f / s;
+        if (err) err[r] = e;
+        if (emax) atomicMax(emax, __float_as_uint(e));
+        if (nmax) atomicMax(nmax, __float_as_uint(__double2float_ru(cosine ? 1.0 : sqrt(nn))));
+    }
+}
+
+// Per data column c, the streamed epilogue's v = acc * cs + cb under the
+// measured bound (q[0] = largest |coordinate| of the scanned rows (FP8: their
+// shared scale), q[1] = their largest |da|, q[2] = their largest |a|):
+//   beta = Da |b| + A db + Da db + gamma (A + Da)(|b| + db)
+//   L2:     cs = 2 / (sa sb), cb = -|b|^2 + 2 beta   (candidate iff v > |a|^2 - eps^2 - margin)
+//   cosine: cs = 1 / (sa sb), cb = beta              (candidate iff v > 1 - eps - margin)
+// (BF16 tiles: sa = sb = 1.)
+__global__ void k_tile_cols(const double* __restrict__ sqn64, const float* __restrict__ xerr,
+                            const float* __restrict__ xrs, int64_t nx, int cosine, int f8,
+                            const unsigned int* __restrict__ q, double gamma, float* __restrict__ cs,
+                            float* __restrict__ cb) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nx) return;
+    const double sa = f8 ? (double)f8_scale(__uint_as_float(q[0])) : 1.0;
+    const double Da = (double)__uint_as_float(q[1]);
+    const double A = (double)__uint_as_float(q[2]);
+    const double nb = cosine ? 1.0 : sqrt(sqn64[c]);
+    const double db = (double)xerr[c];
+    const double beta = Da * nb + A * db + Da * db + gamma * (A + Da) * (nb + db);
+    const double rsb = f8 ? (double)xrs[c] : 1.0;  // 1 / sb
+    if (cosine) {
+        cs[c] = (float)(rsb / sa);
+        cb[c] = __double2float_ru(beta);
+    } else {
+        cs[c] = (float)(2.0 * rsb / sa);
+        cb[c] = __double2float_ru(-sqn64[c] + 2.0 * beta);
+    }
+}
+
+// per scanned row: the threshold of the measured-bound test (see k_tile_cols);
+// margin covers the FP32 rounding of the epilogue, of cb and of the threshold
+__global__ void k_tile_thr(const double* __restrict__ sqn64, const int32_t* __restrict__ node, int64_t n,
+                           int cosine, double eps_key, double maxnorm, float* __restrict__ thr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cosine) {
+        thr[i] = __double2float_rd(1.0 - eps_key - 1e-5);
+    } else {
+        const double margin = 1e-5 * (4.0 * maxnorm * maxnorm + eps_key);
+        thr[i] = __double2float_rd(sqn64[node[i]] - eps_key - margin);
+    }
+}
+
 }  // namespace
 
 // BF16 copy of every node and the bound constants of the tensor-core tiles
@@ -1156,6 +1334,36 @@ static void ensure_data_bf16(vj_index* ix) {
 
 void vj_ensure_bf16(vj_index* ix) { ensure_data_bf16(ix); }
 
+// E4M3 row bytes: d rounded up to 32 columns (one K step), at least one 128-byte box
+static int f8_row_bytes(int d) { return d <= 128 ? 128 : (d + 31) / 32 * 32; }
+
+// Data side of the measured-bound scan (built once per index): the FP8 rows
+// with their scales and error norms, or the error norms of the BF16 rows.
+static void ensure_scan_data(vj_index* ix, bool f8) {
+    cudaStream_t s = ix->stream;
+    const int cosine = ix->metric != VJ_L2 ? 1 : 0;
+    const int warps_grid = vj_div_up(ix->nx * 32, 256);
+    if (f8) {
+        const int kb8 = f8_row_bytes(ix->d);
+        if (ix->kb8 == kb8 && ix->x8.n >= (size_t)ix->nx * kb8) return;
+        ix->kb8 = kb8;
+        ix->x8.ensure((size_t)ix->nx * kb8, s);
+        ix->x8rs.ensure(ix->nx, s);
+        ix->x8err.ensure(ix->nx, s);
+        k_tile_rows<1><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
+                                                  kb8, nullptr, ix->x8.p, ix->x8rs.p, ix->x8err.p, nullptr, nullptr);
+        VJ_LAUNCH_CHECK();
+    } else {
+        if (ix->xerr_bf.n >= (size_t)ix->nx) return;
+        const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
+        ix->xerr_bf.ensure(ix->nx, s);
+        // the data rows are the first nx rows of the BF16 copy
+        k_tile_rows<0><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
+                                                  kp, nullptr, ix->xbf.p, nullptr, ix->xerr_bf.p, nullptr, nullptr);
+        VJ_LAUNCH_CHECK();
+    }
+}
+
 // Work split of a sweep of nrt row tiles over nct tiles: the tiles per unit
 // that minimise the busiest SM's load (its units' tiles plus `refill` tiles of
 // pipeline restart per unit)
@@ -1187,13 +1395,21 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
     ensure_data_bf16(ix);
     const bool cosine = ix->metric != VJ_L2;
-    // kp <= 128: resident query rows and the bias step; wider rows stream
-    // both operands through the ring
-    const bool resident = kp <= RS_MAX_KB * TC_BK;
+    const bool f8 = ix->p.scan == VJ_PREC_FP8;
+    // kp <= 128: resident query rows and the bias step; wider rows, and FP8
+    // tiles, stream both operands through the ring
+    const bool resident = !f8 && kp <= RS_MAX_KB * TC_BK;
+    // FP8 tiles, and BF16 tiles of inputs that are not BF16 values, take the
+    // measured rounding bound (each row's own rounding error)
+    const bool measured = f8 || (!resident && !ix->bf16_lossless);
+    const int kb8 = f8_row_bytes(ix->d);
     DBuf<__nv_bfloat16> abf;
+    DBuf<uint8_t> a8;
     DBuf<int32_t> aid, anode;
-    DBuf<float> an;
-    abf.alloc((size_t)nr * kp, s);
+    DBuf<float> an, mcs, mcb;
+    DBuf<unsigned int> qmax;
+    if (f8) a8.alloc((size_t)nr * kb8, s);
+    else abf.alloc((size_t)nr * kp, s);
     aid.alloc(nr, s);
     anode.alloc(nr, s);
     an.alloc(nr, s);
@@ -1203,11 +1419,44 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     // query rows: L2 scaled by 2 for the resident form (2<a,b> + bias), cosine
     // unit rows (raw rows for the streamed kernel on BF16-exact inputs)
     const float ascale = (!cosine && resident) ? 2.f : 1.f;
-    k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, ascale,
-                                                      (cosine && !ix->cos_raw) ? ix->invn.p : nullptr, abf.p);
-    VJ_LAUNCH_CHECK();
+    if (!f8) {
+        k_to_bf16<<<vj_div_up(nr * kp, 256), 256, 0, s>>>(ix->vec.p, ix->dp, ix->d, arow, 0, nr, kp, ascale,
+                                                          (cosine && !ix->cos_raw) ? ix->invn.p : nullptr, abf.p);
+        VJ_LAUNCH_CHECK();
+    }
     const float eps_key = cosine ? eps : eps * eps;
-    if (ix->cos_raw) {
+    if (measured) {
+        ensure_scan_data(ix, f8);
+        // qmax: largest |coordinate| (FP8: the shared scale), largest |da| and |a| of the scanned rows
+        qmax.alloc(3, s);
+        VJ_CUDA(cudaMemsetAsync(qmax.p, 0, 3 * sizeof(unsigned int), s));
+        const int wg = vj_div_up(nr * 32, 256);
+        const int ci = cosine ? 1 : 0;
+        if (f8) {
+            k_tile_amax<<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, qmax.p);
+            VJ_LAUNCH_CHECK();
+            k_tile_rows<1><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kb8, qmax.p, a8.p,
+                                              nullptr, nullptr, qmax.p + 1, qmax.p + 2);
+        } else {
+            k_tile_rows<0><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kp, nullptr, abf.p,
+                                              nullptr, nullptr, qmax.p + 1, qmax.p + 2);
+        }
+        VJ_LAUNCH_CHECK();
+        // gamma: the accumulation of the exact products.  BF16: FP32 sums of
+        // kp terms, 2 kp 2^-24 of the sum of magnitudes (any order).  FP8: the
+        // tensor core's precision inside one K = 32 step is not documented;
+        // with at least 13 bits kept per aligned addend a step loses at most
+        // 32 2^-13 = 2^-8 of its largest product, plus the FP32 sum of steps
+        const double gamma = f8 ? (1.0 / 256.0 + (double)(kb8 / 32 + 16) * 2.0 * (double)VJ_F32_U)
+                                : (double)(kp + 16) * 2.0 * (double)VJ_F32_U;
+        mcs.alloc(ix->nx, s);
+        mcb.alloc(ix->nx, s);
+        k_tile_cols<<<vj_div_up(ix->nx, 256), 256, 0, s>>>(ix->sqn64.p, f8 ? ix->x8err.p : ix->xerr_bf.p,
+                                                            f8 ? ix->x8rs.p : nullptr, ix->nx, ci, f8 ? 1 : 0,
+                                                            qmax.p, gamma, mcs.p, mcb.p);
+        VJ_LAUNCH_CHECK();
+        k_tile_thr<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn64.p, arow, nr, ci, (double)eps_key, ix->maxnorm, an.p);
+    } else if (ix->cos_raw) {
         k_row_thr_raw<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->invn.p, arow, nr, kp, eps_key, ix->tc_cb, an.p);
     } else {
         k_row_thr<<<vj_div_up(nr, 256), 256, 0, s>>>(ix->sqn.p, arow, nr, ix->metric, kp, eps_key, ix->tc_cb,
@@ -1227,7 +1476,7 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     WdParams W{};
     // integer inputs (exact BF16 products and FP32 sums): the scan hands out
     // each candidate's exact key, and no re-check from the vectors is needed
-    const bool want_keys = ck && !cosine && ix->bf16_exact;
+    const bool want_keys = ck && !cosine && ix->bf16_exact && !f8;
     if (resident) {
         ta = make_map(abf.p, nr, kp, 128);
         tb = make_map(ix->xbf.p, ix->nx, kp, RS_BN);
@@ -1271,27 +1520,42 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         const int grid = std::min(R.nunits, ix->num_sms);
         launch = [&, grid, smem]() { k_tc_res<EPI_SCAN><<<grid, RS_THREADS, smem, s>>>(ta, tab, tb, tbb, R); };
     } else {
-        ta = make_map(abf.p, nr, kp, WD_BM);
-        tb = make_map(ix->xbf.p, ix->nx, kp, WD_BN);
+        if (f8) {
+            ta = make_map_u8(a8.p, nr, kb8, WD_BM);
+            tb = make_map_u8(ix->x8.p, ix->nx, kb8, WD_BN);
+            W.nkb = (kb8 + 127) / 128;
+            W.kk_last = (ix->d + 31) / 32 - 4 * (W.nkb - 1);
+        } else {
+            ta = make_map(abf.p, nr, kp, WD_BM);
+            tb = make_map(ix->xbf.p, ix->nx, kp, WD_BN);
+            W.nkb = kp / TC_BK;
+            W.kk_last = 0;
+        }
         W.nrows = nr;
         W.ncols = ix->nx;
-        W.nkb = kp / TC_BK;
         W.nrt = (int)vj_div_up(nr, WD_BM);
         W.nct = (int)vj_div_up(ix->nx, WD_BN);
         W.tstride = 1;
         W.tpu = best_tiles_per_unit(W.nrt, W.nct, ix->num_sms, 1);
         W.nunits = W.nrt * (int)vj_div_up(W.nct, W.tpu);
-        W.cs = ix->wcs.p;  // data rows are the first nx nodes
-        W.cb = ix->wcb.p;
+        W.cs = measured ? mcs.p : ix->wcs.p;  // data rows are the first nx nodes
+        W.cb = measured ? mcb.p : ix->wcb.p;
         W.thr = an.p;
         W.a_ids = aid.p;
         W.ncand = ctr.p;
         W.err = err.p;
         W.spin_limit = spin_limit;
         const size_t smem = wide_smem();
-        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = std::min(W.nunits, ix->num_sms);
-        launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
+        if (f8) {
+            VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+            launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN, 1><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
+        } else {
+            VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+            launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
+        }
     }
     int64_t cap = std::max<int64_t>(cq.n, std::max<int64_t>(nr * 64, 1 << 20));
     unsigned long long hn = 0;
@@ -1339,6 +1603,10 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
     if (ms_out) *ms_out = ms;
     ix->last_scan_exact_keys = want_keys;
     abf.free_(s);
+    a8.free_(s);
+    mcs.free_(s);
+    mcb.free_(s);
+    qmax.free_(s);
     aid.free_(s);
     an.free_(s);
     anode.free_(s);

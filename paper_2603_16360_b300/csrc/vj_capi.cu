@@ -47,6 +47,7 @@ extern "C" void vj_default_params(vj_params* p) {
     p->input_on_device = 0;
     p->seed = 0;
     p->gather = VJ_PREC_FP32;
+    p->scan = VJ_PREC_BF16;
 }
 
 template <class F>
@@ -74,6 +75,8 @@ static void check_join_params(const vj_params& p) {
     VJ_REQUIRE(p.route_bruteforce == 0, VJ_ERR_ARG, "route_bruteforce is reserved and must be 0");
     VJ_REQUIRE(p.gather == VJ_PREC_FP32 || p.gather == VJ_PREC_BF16, VJ_ERR_ARG, "gather must be FP32 or BF16");
     VJ_REQUIRE(p.hybrid_seed_best == 0 || p.hybrid_seed_best == 1, VJ_ERR_ARG, "hybrid_seed_best must be 0 or 1");
+    VJ_REQUIRE(p.scan == VJ_PREC_FP32 || p.scan == VJ_PREC_BF16 || p.scan == VJ_PREC_FP8, VJ_ERR_ARG,
+               "scan must be FP32, BF16 or FP8");
 }
 
 static std::atomic<int64_t> g_live_indexes{0};
@@ -92,6 +95,7 @@ static void free_index(vj_index* ix) {
     ix->parent.free_(s);
     ix->order.free_(s);
     ix->depth.free_(s);
+    ix->porder.free_(s);
     ix->qstat.free_(s);
     ix->qdn.free_(s);
     ix->feat.free_(s);
@@ -103,6 +107,10 @@ static void free_index(vj_index* ix) {
     ix->xbf.free_(s);
     ix->wcs.free_(s);
     ix->wcb.free_(s);
+    ix->xerr_bf.free_(s);
+    ix->x8.free_(s);
+    ix->x8rs.free_(s);
+    ix->x8err.free_(s);
     ix->pkeys.free_(s);
     ix->nm_w.free_(s);
     ix->nm_wd.free_(s);
@@ -267,7 +275,120 @@ extern "C" vj_status vj_set_join_params(vj_index* ix, const vj_params* p) {
         ix->p.learned = p->learned;
         ix->p.gather = p->gather;
         ix->p.hybrid_seed_best = p->hybrid_seed_best;
+        ix->p.scan = p->scan;
     });
+}
+
+// class table position of `cls` (-1 if none)
+static int class_pos(int cls) {
+    for (int k = 0; k < vj_join_class_count(); k++) {
+        int c, G, NPL, U;
+        vj_join_class_info(k, &c, &G, &NPL, &U);
+        if (c == cls) return k;
+    }
+    return -1;
+}
+
+extern "C" vj_status vj_set_tuning(vj_index* ix, int lanes, int slots, int inflight, int blocks, int probe_ring) {
+    return guarded([&] {
+        VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
+        VJ_REQUIRE(blocks >= 0, VJ_ERR_ARG, "blocks must be >= 0");
+        VJ_REQUIRE(probe_ring == 0 || (probe_ring >= 2 && probe_ring <= 8), VJ_ERR_ARG,
+                   "probe_ring must be 0 or 2..8");
+        int cls = -1;
+        if (lanes != 0) {
+            for (int k = 0; k < vj_join_class_count() && cls < 0; k++) {
+                int c, G, NPL, U;
+                vj_join_class_info(k, &c, &G, &NPL, &U);
+                if (G == lanes && NPL == slots && U == inflight) {
+                    VJ_REQUIRE((int64_t)G * NPL >= ix->dp / 4, VJ_ERR_ARG,
+                               "the class holds %d floats per row, the index has %d", G * NPL * 4, ix->d);
+                    cls = c;
+                }
+            }
+            VJ_REQUIRE(cls >= 0, VJ_ERR_ARG, "no traversal class with lanes %d, slots %d, inflight %d", lanes,
+                       slots, inflight);
+        }
+        ix->tune_cls = cls;
+        ix->tune_blocks = blocks;
+        ix->tune_ring = probe_ring;
+    });
+}
+
+extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_report* rep) {
+    if (rep) memset(rep, 0, sizeof(*rep));
+    if (!ix) {
+        vj_set_error("index is NULL");
+        return VJ_ERR_ARG;
+    }
+    const int saved_cls = ix->tune_cls, saved_blocks = ix->tune_blocks, saved_ring = ix->tune_ring;
+    const vj_status st = guarded([&] {
+        VJ_REQUIRE(rep != nullptr, VJ_ERR_ARG, "report is NULL");
+        VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
+        VJ_REQUIRE(reps >= 1 && reps <= 10, VJ_ERR_ARG, "reps must be 1..10");
+        const int dp4 = ix->dp / 4;
+        const int k0 = class_pos(vj_join_default_class(dp4));
+        const bool probe = !ix->separate && !ix->nnmap;
+        struct Setting {
+            int cls, blocks, ring;
+        };
+        std::vector<Setting> set;
+        for (int k = k0; k < vj_join_class_count() && k < k0 + 3; k++) {
+            int c, G, NPL, U;
+            vj_join_class_info(k, &c, &G, &NPL, &U);
+            const int mb = vj_join_max_blocks(c, ix->num_sms);
+            set.push_back({c, mb, 0});
+            if (mb / 2 >= ix->num_sms) set.push_back({c, mb / 2, 0});
+        }
+        if (probe) {
+            set.push_back({set[0].cls, set[0].blocks, 4});
+            set.push_back({set[0].cls, set[0].blocks, 2});
+        }
+        int64_t nnz0 = -1, dc0 = -1;
+        double best = 1e300;
+        for (size_t i = 0; i < set.size() && (int)i < VJ_TUNE_MAX; i++) {
+            ix->tune_cls = set[i].cls;
+            ix->tune_blocks = set[i].blocks;
+            ix->tune_ring = set[i].ring;
+            std::vector<double> ms;
+            int64_t nnz = 0;
+            vj_stats s{};
+            for (int r = 0; r <= reps; r++) {
+                s = vj_stats{};
+                vj_run_join(ix, eps, 0, &s, &nnz);
+                if (r > 0) ms.push_back(s.ms_total);
+            }
+            std::sort(ms.begin(), ms.end());
+            const int n = rep->n++;
+            int c, G, NPL, U;
+            vj_join_class_info(class_pos(set[i].cls), &c, &G, &NPL, &U);
+            rep->lanes[n] = G;
+            rep->slots[n] = NPL;
+            rep->inflight[n] = U;
+            rep->blocks[n] = set[i].blocks;
+            rep->probe_ring[n] = probe ? (set[i].ring ? set[i].ring : 8) : 0;
+            rep->ms[n] = ms[ms.size() / 2];
+            if (i == 0) {
+                nnz0 = nnz;
+                dc0 = s.dist_computations;
+            }
+            rep->valid[n] = (nnz == nnz0 && s.dist_computations == dc0) ? 1 : 0;
+            if (rep->valid[n] && rep->ms[n] < best) {
+                best = rep->ms[n];
+                rep->chosen = n;
+            }
+        }
+        const Setting& ch = set[rep->chosen];
+        ix->tune_cls = ch.cls;
+        ix->tune_blocks = ch.blocks;
+        ix->tune_ring = ch.ring;
+    });
+    if (st != VJ_OK) {
+        ix->tune_cls = saved_cls;
+        ix->tune_blocks = saved_blocks;
+        ix->tune_ring = saved_ring;
+    }
+    return st;
 }
 
 extern "C" vj_status vj_set_wait_test(vj_index* ix, long long max_polls, int64_t hold_q) {

@@ -119,6 +119,7 @@ struct vj_index {
     DBuf<int32_t> parent; // [nq]
     DBuf<int32_t> order;  // [nq]
     DBuf<int32_t> depth;  // [nq]
+    DBuf<int32_t> porder; // [nq] probe dispatch order (MST preorder), empty without an MST
     int max_depth = 0;
     DBuf<__nv_bfloat16> xbf;   // [n][kp] BF16 copy of every node, data rows first (tensor-core tiles)
     DBuf<__nv_bfloat16> xbias; // [n][16] L2: three-term BF16 split of each node's scan bias
@@ -144,6 +145,14 @@ struct vj_index {
     bool bf16_lossless = false;  // every coordinate is exactly a BF16 value
     bool cos_raw = false;      // cosine, streamed tiles: xbf holds the raw (not unit) rows, scaled in the epilogue
     DBuf<float> wcs, wcb;      // [n] streamed tiles: per-column scale and bias of the accumulator
+    // streamed scan with the measured rounding bound (FP8 tiles, or BF16 tiles
+    // of inputs that are not BF16 values): per data row the FP64 norm of the
+    // tile row's rounding error (rounded up); FP8 also keeps its own copy of
+    // the data rows (kb8 bytes each, one power-of-two scale per row, 1/scale)
+    DBuf<float> xerr_bf;       // [nx] BF16 tile rows
+    DBuf<uint8_t> x8;          // [nx][kb8] E4M3
+    DBuf<float> x8rs, x8err;   // [nx]
+    int kb8 = 0;
     // NN-Map index (the paper's closing design): kNN lists over data columns
     // only, the graph G_X over data rows only, and per query its witness
     // (nearest data vector), the witness's FP64 distance and the OOD bit
@@ -159,6 +168,10 @@ struct vj_index {
     DBuf<int32_t> nm_w;        // [nq] witness
     DBuf<double> nm_wd;        // [nq] its distance (FP64)
     DBuf<uint8_t> nm_ood;      // [nq] OOD bit
+    // traversal setting chosen by vj_autotune / vj_set_tuning: join class
+    // (-1: the smallest that holds the row), persistent blocks and probe ring
+    // stages (0: the defaults)
+    int tune_cls = -1, tune_blocks = 0, tune_ring = 0;
     long long wait_polls = 0;  // dependency-wait limit of the traversal (0: the default)
     int hold_q = -1;           // test knob: a query that never publishes its cache (-1: none)
     double maxnorm = 0.0;      // largest vector norm (FP64)
@@ -221,6 +234,13 @@ void vj_scan_rows_csr(vj_index* ix, const int32_t* qrows, int64_t nr, float eps,
                       bool sort_rows = false);
 // approximate join; returns stats, leaves CSR in ix->offsets/out_id/out_d and per-query arrays
 void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz_out);
+// traversal classes for the tuner: the k-th of vj_join_class_count() in order
+// of row capacity (G * NPL 16-byte slots), the class pick() takes for dp4
+// slots, and the persistent blocks of a class
+int vj_join_class_count();
+void vj_join_class_info(int k, int* cls, int* G, int* NPL, int* U);
+int vj_join_default_class(int dp4);
+int vj_join_max_blocks(int cls, int num_sms);
 // free the idle traversal workspaces of the process-wide cache
 void vj_trav_space_trim();
 // joins of n distinct indexes (default budget) with fused traversal launches;

@@ -57,6 +57,15 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
+// FP8 operands (kind::f8f6f4, E4M3 x E4M3 per the instruction descriptor),
+// K = 32 per instruction: 32 bytes of each operand row, as for kind::f16
+__device__ __forceinline__ void tc_mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                  : "memory");
@@ -178,5 +187,19 @@ inline CUtensorMap make_map(const void* base, int64_t rows, int kp, int box_rows
     return m;
 }
 
+// 2-D byte (FP8) tensor map: rows x kb bytes, box (128 bytes x box_rows),
+// 128-byte swizzle; kb a multiple of 16, columns past kb read as zero
+inline CUtensorMap make_map_u8(const void* base, int64_t rows, int kb, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)kb, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kb};
+    cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    VJ_REQUIRE(r == CUDA_SUCCESS, VJ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return m;
+}
 
 }  // namespace vjtc

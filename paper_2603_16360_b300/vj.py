@@ -28,7 +28,7 @@ EXPORTS = ["vj_mlp_create", "vj_mlp_num_params", "vj_mlp_get_params", "vj_mlp_se
            "vj_join_device", "vj_join_batch", "vj_join_exact", "vj_join_exact_noalloc", "vj_export_graph", "vj_export_knn",
            "vj_index_info", "vj_build_info", "vj_result_free", "vj_free", "vj_last_error", "vj_set_wait_test",
            "vj_default_train_params", "vj_predictor_labels", "vj_train_predictor", "vj_join_switched",
-           "vj_export_nnmap"]
+           "vj_export_nnmap", "vj_autotune", "vj_set_tuning"]
 
 NOALLOC_MAX_QUERIES = 1 << 20
 
@@ -43,12 +43,23 @@ class VjError(RuntimeError):
         self.status = status
 
 
+VJ_TUNE_MAX = 16
+
+
+class vj_tune_report(C.Structure):
+    _fields_ = [("n", C.c_int), ("lanes", C.c_int * VJ_TUNE_MAX), ("slots", C.c_int * VJ_TUNE_MAX),
+                ("inflight", C.c_int * VJ_TUNE_MAX), ("blocks", C.c_int * VJ_TUNE_MAX),
+                ("probe_ring", C.c_int * VJ_TUNE_MAX), ("ms", C.c_double * VJ_TUNE_MAX),
+                ("valid", C.c_int * VJ_TUNE_MAX), ("chosen", C.c_int)]
+
+
 class vj_params(C.Structure):
     _fields_ = [("degree", C.c_int), ("knn_k", C.c_int), ("greedy_beam", C.c_int), ("conv_threshold", C.c_int),
                 ("hybrid_beam", C.c_int), ("work_sharing", C.c_int), ("adapt_hybrid", C.c_int),
                 ("force_hybrid", C.c_int), ("precision", C.c_int), ("learned", C.c_int),
                 ("route_bruteforce", C.c_int), ("input_on_device", C.c_int), ("seed", C.c_uint64),
-                ("gather", C.c_int), ("hybrid_seed_best", C.c_int), ("nnmap", C.c_int), ("separate", C.c_int)]
+                ("gather", C.c_int), ("hybrid_seed_best", C.c_int), ("nnmap", C.c_int), ("separate", C.c_int),
+                ("scan", C.c_int)]
 
 
 class vj_stats(C.Structure):
@@ -158,6 +169,10 @@ def load():
     lib.vj_train_predictor.restype = I
     lib.vj_set_wait_test.argtypes = [P, C.c_longlong, I64]
     lib.vj_set_wait_test.restype = I
+    lib.vj_autotune.argtypes = [P, C.c_float, I, C.POINTER(vj_tune_report)]
+    lib.vj_autotune.restype = I
+    lib.vj_set_tuning.argtypes = [P, I, I, I, I, I]
+    lib.vj_set_tuning.restype = I
     lib.vj_last_error.argtypes = []
     lib.vj_last_error.restype = C.c_char_p
     _lib = lib
@@ -482,6 +497,22 @@ def vj_train_predictor(ix: Index, eps: float, rows, **kw):
 def vj_set_wait_test(ix: Index, max_polls: int = 0, hold_q: int = -1):
     """Limit the soft-sharing dependency wait (0: default) and hold one query's publication (-1: none)."""
     _check(load().vj_set_wait_test(ix.handle, int(max_polls), int(hold_q)))
+
+
+def vj_autotune(ix: Index, eps: float, reps: int = 2) -> dict:
+    """Time the join at eps under each candidate traversal setting, keep the
+    fastest on the index; returns the settings tried and the chosen one."""
+    rep = vj_tune_report()
+    _check(load().vj_autotune(ix.handle, float(eps), int(reps), C.byref(rep)))
+    rows = [{"lanes": rep.lanes[i], "slots": rep.slots[i], "inflight": rep.inflight[i], "blocks": rep.blocks[i],
+             "probe_ring": rep.probe_ring[i], "ms": rep.ms[i], "valid": bool(rep.valid[i])} for i in range(rep.n)]
+    return {"settings": rows, "chosen": rep.chosen}
+
+
+def vj_set_tuning(ix: Index, lanes: int = 0, slots: int = 0, inflight: int = 0, blocks: int = 0,
+                  probe_ring: int = 0):
+    """Set the traversal setting (0 = default for each field)."""
+    _check(load().vj_set_tuning(ix.handle, int(lanes), int(slots), int(inflight), int(blocks), int(probe_ring)))
 
 
 def vj_set_plan(ix: Index, route=None, beam=None):
