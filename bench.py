@@ -579,6 +579,10 @@ def profile_modes(args, vj, ix, w, build_s, binfo):
                           gather=vj.VJ_PREC_BF16)
     if plan is not None:
         vj.vj_set_plan(ix, None, np.full(w.nq, plan, np.int32))
+    if args.tune:
+        # the traversal settings the tuner tries, their join times, and the one it keeps
+        print(json.dumps({"mode": "tune", "eps": eps, **vj.vj_autotune(ix, eps, reps=max(1, args.reps))}),
+              flush=True)
     for i in range(args.reps):
         st = vj.vj_join(ix, eps).stats
         print(json.dumps({"mode": "join", "plan": args.plan, "rep": i, "eps": eps, "ms_total": st["ms_total"],
@@ -799,6 +803,8 @@ def main():
     ap.add_argument("--plan", default="none", choices=["none", "bfs", "rule"],
                     help="--mode join: none = no expansion (the learned step's plan here), bfs, or the d1/d2 rule")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune", action="store_true", help="--mode join: run vj_autotune first and print its report")
+    ap.add_argument("--no-tune", action="store_true", help="bench: time both arms with the default traversal setting")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -895,13 +901,20 @@ def main():
     hbm, bf16, peak_kind = _peaks()
     # ---- time the plain arm (its setting re-applied)
     psetup()
+    # each arm runs with the traversal setting vj_autotune picks for it (untimed setup)
+    p_tune = None if args.no_tune else vj.vj_autotune(ix, eps, reps=2)
     p_ms, p_stats, _ = timed(vj, torch, ix, eps, 0, max(2, args.steps // 2), args.warmup, "plain_timed")
     plain_qps = ne / (p_ms / 1e3)
     vj.vj_set_plan(ix, None, None)
+    vj.vj_set_tuning(ix)
 
     learned, m = None, None
     if not args.plain_only:
         m, learned = learned_arm(vj, ix, eps, ex, w, log, caps=(0,) if w.d > 256 else (0, 64))
+        l_tune = None if args.no_tune else vj.vj_autotune(ix, eps, reps=2)
+        if l_tune:
+            log(f"learned arm tuning: {l_tune['settings'][l_tune['chosen']]}")
+        learned["tune"] = l_tune
         l_ms, l_stats, clk = timed(vj, torch, ix, eps, 0, args.steps, args.warmup, "learned_timed", clocks=True)
         r = vj.vj_join(ix, eps)
         learned.update({"ms": l_ms, "stats": l_stats, "clocks": clk, "recall": recall_of(r, ex, w.nx, (0, ne)),
@@ -978,7 +991,8 @@ def main():
            "l2": "inputs larger than L2 (FP32 vectors %.1f GB, BF16 copy %.1f GB)" % (
                (w.nx + w.nq) * w.d * 4 / 1e9, (w.nx + w.nq) * kp * 2 / 1e9),
            "plain_fp32": {"qps": plain_qps, "ms_per_step": p_ms, "recall": prec, "setting": pname,
-                          "sweep": psweep},
+                          "sweep": psweep,
+                          "tune": p_tune["settings"][p_tune["chosen"]] if p_tune else "default (--no-tune)"},
            "exact_join": {"ms": ex.stats["ms_total"], "ms_scan": ex.stats["ms_scan"],
                           "tflops": exact_flops / (ex.stats["ms_scan"] / 1e3) / 1e12},
            "seed": w.seed,
@@ -988,6 +1002,9 @@ def main():
         cfg["learned"] = {k: learned[k] for k in ("thr", "beam_cap", "sweep", "recall", "routed_frac",
                                                    "no_expansion_frac", "train_s", "train_report")}
         cfg["learned"]["ms_prologue"] = statistics.mean(s["ms_prologue"] for s in stats)
+        lt = learned.get("tune")
+        cfg["learned"]["tune"] = {"chosen": lt["settings"][lt["chosen"]], "tried": lt["settings"]} if lt else \
+            "default (--no-tune)"
         cfg["learned_vs_plain"] = value / plain_qps
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

@@ -397,7 +397,9 @@ vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int6
  * `lanes` threads holding `slots` 16-byte pieces each (a row of up to
  * lanes * slots * 4 floats) and keeps `inflight` rows in flight per group; it
  * runs as a persistent grid of `blocks` blocks, and the probe of N(q) streams
- * rows through a ring of `probe_ring` stages per warp.  Every setting computes
+ * rows through a ring of `probe_ring` stages per warp, each row as 16-byte
+ * copies issued by every lane or, with `probe_bulk`, as one bulk copy of the
+ * whole row by the copy engine.  Every setting computes
  * the same join (in-range decisions near eps are re-decided in FP64; only
  * the FP32 summation order of a key changes), so tuning changes time only.
  *
@@ -405,7 +407,8 @@ vj_status vj_join_exact_noalloc(const float *X, int64_t nx, const float *Q, int6
  * parameters and plan) under each candidate setting: the default class (the
  * smallest that holds the row) and the next two larger ones, each with the
  * full and half persistent grid, and, on a merged index, shallower probe
- * rings for the default class.  Each setting runs one untimed join and then
+ * rings and the bulk-copy probe for the default class.  Each setting runs one
+ * untimed join and then
  * `reps` (1..10) timed ones; its time is the median device time of the whole
  * join (vj_stats.ms_total).  A setting counts only when its joins give the
  * same pair count and distance evaluations as the default setting.  The
@@ -420,6 +423,7 @@ typedef struct {
     int inflight[VJ_TUNE_MAX];  /* rows in flight per group */
     int blocks[VJ_TUNE_MAX];    /* persistent blocks of the traversal */
     int probe_ring[VJ_TUNE_MAX];/* probe ring stages per warp (0: no probe kernel) */
+    int probe_bulk[VJ_TUNE_MAX];/* 1: the probe copies each row in one bulk copy */
     double ms[VJ_TUNE_MAX];     /* median device time of the join */
     int valid[VJ_TUNE_MAX];     /* 1: same pairs and evaluations as the default */
     int chosen;                 /* index of the setting kept on the index */
@@ -430,8 +434,10 @@ vj_status vj_autotune(vj_index *ix, float eps, int reps, vj_tune_report *report)
  * on another index of the same row width).  lanes = 0 selects the default
  * class (slots and inflight are then ignored); otherwise (lanes, slots,
  * inflight) must name a class whose rows hold d floats, else VJ_ERR_ARG.
- * blocks = 0 and probe_ring = 0 select the defaults; probe_ring is 2..8. */
-vj_status vj_set_tuning(vj_index *ix, int lanes, int slots, int inflight, int blocks, int probe_ring);
+ * blocks = 0 and probe_ring = 0 select the defaults; probe_ring is 2..8;
+ * probe_bulk is 0 (16-byte copies, the default) or 1. */
+vj_status vj_set_tuning(vj_index *ix, int lanes, int slots, int inflight, int blocks, int probe_ring,
+                        int probe_bulk);
 
 /* Bounded dependency wait of soft work sharing (for tests of its failure
  * path; no paper counterpart).  max_polls > 0 limits the polls of a query's

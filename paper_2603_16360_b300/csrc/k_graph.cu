@@ -751,34 +751,6 @@ __global__ void k_union_off(const int64_t* __restrict__ inoff, int64_t n, int R,
 }  // namespace
 
 
-// Preorder of the forest given by parent[] (-1 for a root): roots in index
-// order, each node's children in index order.
-static std::vector<int32_t> mst_preorder(const int32_t* parent, int64_t n) {
-    std::vector<int64_t> off(n + 1, 0);
-    for (int64_t v = 0; v < n; v++)
-        if (parent[v] >= 0) off[parent[v] + 1]++;
-    for (int64_t v = 0; v < n; v++) off[v + 1] += off[v];
-    std::vector<int32_t> kids(std::max<int64_t>(off[n], 1));
-    std::vector<int64_t> cur(off.begin(), off.end() - 1);
-    for (int64_t v = 0; v < n; v++)
-        if (parent[v] >= 0) kids[cur[parent[v]]++] = (int32_t)v;
-    std::vector<int32_t> pre, stack;
-    pre.reserve(n);
-    for (int64_t r = 0; r < n; r++) {
-        if (parent[r] >= 0) continue;
-        stack.push_back((int32_t)r);
-        while (!stack.empty()) {
-            const int32_t v = stack.back();
-            stack.pop_back();
-            pre.push_back(v);
-            for (int64_t k = off[v + 1]; k > off[v]; k--) stack.push_back(kids[k - 1]);
-        }
-    }
-    VJ_REQUIRE((int64_t)pre.size() == n, VJ_ERR_STATE, "MST preorder covers %lld of %lld queries",
-               (long long)pre.size(), (long long)n);
-    return pre;
-}
-
 void vj_build_graph(vj_index* ix) {
     cudaStream_t s = ix->stream;
     const int64_t n = ix->n, nx = ix->nx, nq = ix->nq;
@@ -934,12 +906,6 @@ void vj_build_graph(vj_index* ix) {
         VJ_CUDA(cudaMemcpyAsync(ix->order.p, ho.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         VJ_CUDA(cudaMemcpyAsync(ix->parent.p, hp.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         VJ_CUDA(cudaMemcpyAsync(ix->depth.p, hd.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        // the probe kernel's dispatch order: MST preorder (depth first, children
-        // by query index), so the queries in flight together are tree
-        // neighbours, close in space, and share the data rows they gather
-        std::vector<int32_t> pre = mst_preorder(hp.data(), nq);
-        ix->porder.ensure(nq, s);
-        VJ_CUDA(cudaMemcpyAsync(ix->porder.p, pre.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         VJ_CUDA(cudaStreamSynchronize(s));
         ix->max_depth = 1;
     } else {

@@ -171,6 +171,9 @@ struct JoinParams {
     // the entry), bit-identical to the traversal's own (nullptr: computed in
     // the traversal)
     const float* pkeys;
+    // soft sharing, pass 3: per query, 1 when an MST ancestor ends with a
+    // cache other than its pass-1 one (nullptr: every query waits)
+    const uint8_t* anc;
 };
 
 enum { QF_PROBED = 1 };
@@ -643,7 +646,11 @@ __device__ __forceinline__ bool join_query(const JoinParams& P, int t, WarpSmem*
             const int outc_q = P.outc[qi];
             const int cout_q = P.cout[qi];
             int sc = -1;
-            if (par >= 0 && lane == 0) {
+            // no ancestor changes its cache: the parent's final cache is its
+            // pass-1 cache, the seed pass 2 decided for, and nothing to wait for
+            if (par >= 0 && P.anc && !P.anc[qi]) {
+                sc = sca_q;
+            } else if (par >= 0 && lane == 0) {
                 long long spins = 0;
                 unsigned ns = 32;
                 for (;;) {
@@ -1429,7 +1436,9 @@ struct PbParams {
     int rowbytes;  // bytes copied per row (16-byte multiple)
     int rowpitch;  // bytes between rows in the ring
     float* pkeys;  // [nq][R + 1]
-    const int32_t* porder;  // [nq] dispatch order (warp t probes query porder[t]), or nullptr: index order
+    int bulk;      // 1: each row is one bulk copy (cp.async.bulk, mbarrier per stage)
+    unsigned long long* ctr;  // the join's counters (error word) for the bounded waits
+    long long spin_limit;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -1461,9 +1470,8 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_probe(const __grid_constant__
     constexpr int NG = 32 / G;  // rows per stage (one per lane group)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, g = lane & (G - 1);
-    const int64_t t = (int64_t)blockIdx.x * PB_WARPS + warp;
-    if (t >= P.nq) return;
-    const int64_t qi = P.porder ? (int64_t)P.porder[t] : t;
+    const int64_t qi = (int64_t)blockIdx.x * PB_WARPS + warp;
+    if (qi >= P.nq) return;
     unsigned char* ring = pb_raw + (size_t)warp * P.ring * NG * P.rowpitch;
     const int64_t qn = P.nx + qi;
     const int R = P.R;
@@ -1530,12 +1538,165 @@ __global__ void __launch_bounds__(PB_WARPS * 32) k_probe(const __grid_constant__
     cp_async_wait<0>();
 }
 
+// The same probe with one bulk copy per row (the copy engine moves the whole
+// row; one mbarrier per ring stage counts its bytes) instead of 16-byte
+// copies issued by every lane.  Every wait is bounded: on timeout the join's
+// error word is set and the warp stops (after its copies in flight land).
+__device__ __forceinline__ void pb_bar_init(uint64_t* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(b)) : "memory");
+}
+__device__ __forceinline__ void pb_bar_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool pb_bar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"((uint32_t)__cvta_generic_to_shared(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void pb_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(dst)),
+        "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(b))
+        : "memory");
+}
+
+template <int G, int NPL>
+__global__ void __launch_bounds__(PB_WARPS * 32) k_probe_bulk(const __grid_constant__ PbParams P) {
+    extern __shared__ __align__(16) unsigned char pbb_raw[];
+    constexpr int NG = 32 / G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / G, g = lane & (G - 1);
+    const int64_t qi = (int64_t)blockIdx.x * PB_WARPS + warp;
+    if (qi >= P.nq) return;
+    unsigned char* ring = pbb_raw + (size_t)warp * P.ring * NG * P.rowpitch;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(pbb_raw + (size_t)PB_WARPS * P.ring * NG * P.rowpitch) +
+                     warp * PB_RING;
+    if (lane == 0) {
+        for (int st = 0; st < P.ring; st++) pb_bar_init(bars + st);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t qn = P.nx + qi;
+    const int R = P.R;
+    const int vl = lane < R ? __ldg(P.adj + qn * R + lane) : -1;
+    float4 q[NPL];
+    load_slots<G, NPL>(P.vec, qn, P.dp4, g, q);
+    const float invq = P.metric ? __ldg(P.invn + qn) : 0.f;
+    const float invl = (P.metric && vl >= 0) ? __ldg(P.invn + vl) : 0.f;
+    const float inve = P.metric ? __ldg(P.invn + P.entry) : 0.f;
+    const int nstage = (R + 1 + NG - 1) / NG;
+    // lane 0 issues stage st: its rows' bytes on the stage's barrier, then one copy per row
+    auto issue = [&](int st) {
+        int v[NG];
+        uint32_t bytes = 0;
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int slot = st * NG + r;
+            const int vs = __shfl_sync(VJ_FULL, vl, slot & 31);
+            v[r] = slot < R ? vs : (slot == R ? P.entry : -1);
+            if (v[r] >= 0) bytes += (uint32_t)P.rowbytes;
+        }
+        if (lane == 0 && st < nstage) {
+            uint64_t* b = bars + (st % P.ring);
+            // the stage's buffer was read (generic proxy) before the copy engine refills it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            pb_bar_expect(b, bytes);
+            unsigned char* dst = ring + (size_t)(st % P.ring) * NG * P.rowpitch;
+#pragma unroll
+            for (int r = 0; r < NG; r++) {
+                if (v[r] < 0) continue;
+                const unsigned char* src =
+                    P.xb ? reinterpret_cast<const unsigned char*>(P.xb + (int64_t)v[r] * P.kpb)
+                         : reinterpret_cast<const unsigned char*>(P.vec + (int64_t)v[r] * P.dp4 * 4);
+                pb_bulk_copy(dst + (size_t)r * P.rowpitch, src, (uint32_t)P.rowbytes, b);
+            }
+        }
+    };
+    int issued = 0;  // stages issued so far (stage k uses slot k % ring, phase k / ring)
+    for (int st = 0; st < P.ring; st++)
+        if (st < nstage) {
+            issue(st);
+            issued = st + 1;
+        }
+    bool ok = true;
+    for (int st = 0; st < nstage; st++) {
+        uint64_t* b = bars + (st % P.ring);
+        const uint32_t par = (uint32_t)((st / P.ring) & 1);
+        bool got = false;
+        for (long long i = 0; i < P.spin_limit; i++) {
+            if (pb_bar_test(b, par)) {
+                got = true;
+                break;
+            }
+        }
+        if (!__all_sync(VJ_FULL, got)) {
+            ok = false;
+            break;
+        }
+        const int slot = st * NG + grp;
+        const int vs = __shfl_sync(VJ_FULL, vl, slot & 31);
+        const float ils = __shfl_sync(VJ_FULL, invl, slot & 31);
+        const int v = slot < R ? vs : (slot == R ? P.entry : -1);
+        const float il = slot < R ? ils : inve;
+        const unsigned char* row = ring + (size_t)(st % P.ring) * NG * P.rowpitch + (size_t)grp * P.rowpitch;
+        float a;
+        if (P.xb) {
+            uint2 xr[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; k++) {
+                const int idx = g + k * G;
+                xr[k] = idx < P.dp4 ? reinterpret_cast<const uint2*>(row)[idx] : make_uint2(0u, 0u);
+            }
+            a = group_sum<G>(slot_accum_bf16<NPL>(xr, q, P.metric));
+        } else {
+            float4 x[NPL];
+#pragma unroll
+            for (int k = 0; k < NPL; k++) {
+                const int idx = g + k * G;
+                x[k] = idx < P.dp4 ? reinterpret_cast<const float4*>(row)[idx] : f4zero();
+            }
+            a = group_sum<G>(slot_accum<NPL>(x, q, P.metric));
+        }
+        if (g == 0 && slot <= R)
+            P.pkeys[qi * (R + 1) + slot] = v < 0 ? FLT_MAX : (P.metric == 0 ? a : 1.0f - a * il * invq);
+        __syncwarp();  // the stage's buffer is read before it is refilled
+        if (st + P.ring < nstage) {
+            issue(st + P.ring);
+            issued = st + P.ring + 1;
+        }
+    }
+    if (!ok && lane == 0) {
+        atomicCAS(P.ctr + C_ERR, 0ull, (unsigned long long)VJ_DERR_WAIT_TIMEOUT);
+        atomicExch(P.ctr + C_ABORT, 1ull);
+        // the copies in flight land before the block's shared memory goes away:
+        // each slot's last issued stage completes its phase (bounded waits)
+        for (int k = max(0, issued - P.ring); k < issued; k++)
+            for (long long i = 0; i < P.spin_limit && !pb_bar_test(bars + (k % P.ring), (uint32_t)((k / P.ring) & 1));
+                 i++) {
+            }
+    }
+}
+
 template <int G, int NPL>
 void launch_probe_t(const PbParams& P, cudaStream_t st) {
     constexpr int NG = 32 / G;
     const size_t smem = (size_t)PB_WARPS * P.ring * NG * P.rowpitch;
-    VJ_CUDA(cudaFuncSetAttribute(k_probe<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_probe<G, NPL><<<(unsigned)vj_div_up(P.nq, PB_WARPS), PB_WARPS * 32, smem, st>>>(P);
+    if (P.bulk) {
+        const size_t sm2 = smem + (size_t)PB_WARPS * PB_RING * sizeof(uint64_t);
+        VJ_CUDA(cudaFuncSetAttribute(k_probe_bulk<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        k_probe_bulk<G, NPL><<<(unsigned)vj_div_up(P.nq, PB_WARPS), PB_WARPS * 32, sm2, st>>>(P);
+    } else {
+        VJ_CUDA(cudaFuncSetAttribute(k_probe<G, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_probe<G, NPL><<<(unsigned)vj_div_up(P.nq, PB_WARPS), PB_WARPS * 32, smem, st>>>(P);
+    }
     VJ_LAUNCH_CHECK();
 }
 
@@ -1648,6 +1809,45 @@ __global__ void k_merge_routed(const int32_t* __restrict__ routed, int64_t nr, c
     const int q = routed[i];
     seg[q] = base + soff[q];
     count[q] = (int32_t)(soff[q + 1] - soff[q]);
+}
+
+// Soft sharing, between passes 2 and 3.  A query is locally changed when,
+// with its parent's pass-1 cache as the seed, pass 2 decided a cache other
+// than its own pass-1 cache (one more visit that found a closer node, or a
+// re-run that did).  anc[q] = 1 when some MST ancestor of q is locally
+// changed.  A query with anc[q] = 0 has, by induction from the root, every
+// ancestor's final cache equal to its pass-1 cache, so its parent's final
+// cache is the seed pass 2 decided for: pass 3 commits it without waiting.
+// Pointer jumping over the parent links: after round k, anc covers the
+// ancestors up to 2^k levels up and jmp points 2^k levels up.
+__global__ void k_anc_init(const int32_t* __restrict__ parent, const uint8_t* __restrict__ outc,
+                           const int32_t* __restrict__ cout, const int32_t* __restrict__ cache1,
+                           const int32_t* __restrict__ cache2, int64_t nq, uint8_t* __restrict__ anc,
+                           int32_t* __restrict__ jmp) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const int32_t p = parent[q];
+    uint8_t a = 0;
+    if (p >= 0) {
+        const int o = outc[p];
+        a = (uint8_t)((o == 1 && cout[p] != cache1[p]) || (o == 2 && cache2[p] != cache1[p]));
+    }
+    anc[q] = a;
+    jmp[q] = p;
+}
+
+__global__ void k_anc_jump(const uint8_t* __restrict__ anc_in, const int32_t* __restrict__ jmp_in, int64_t nq,
+                           uint8_t* __restrict__ anc_out, int32_t* __restrict__ jmp_out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    uint8_t a = anc_in[q];
+    int32_t j = jmp_in[q];
+    if (j >= 0) {
+        a |= anc_in[j];
+        j = jmp_in[j];
+    }
+    anc_out[q] = a;
+    jmp_out[q] = j;
 }
 
 template <int G, int NPL, int U>
@@ -1766,6 +1966,32 @@ struct JoinRun {
         }
     }
 };
+
+// anc of k_anc_init / k_anc_jump for the join's index, after its pass 2 (on
+// the stream, no host wait); nullptr when every query must wait (the
+// wait-test knob holds a query back)
+const uint8_t* anc_compute(JoinRun& r, cudaStream_t s) {
+    vj_index* ix = r.ix;
+    const int64_t nq = ix->nq;
+    if (ix->hold_q >= 0 || nq == 0) return nullptr;
+    ix->anc.ensure(2 * (size_t)nq, s);
+    ix->jmp.ensure(2 * (size_t)nq, s);
+    uint8_t* a[2] = {ix->anc.p, ix->anc.p + nq};
+    int32_t* j[2] = {ix->jmp.p, ix->jmp.p + nq};
+    const JoinParams& P = r.P;
+    const int g = vj_div_up(nq, 256);
+    k_anc_init<<<g, 256, 0, s>>>(P.parent, P.outc, P.cout, P.cache1, P.cache2, nq, a[0], j[0]);
+    VJ_LAUNCH_CHECK();
+    r.launches++;
+    int cur = 0;
+    for (int64_t span = 1; span < (int64_t)ix->max_depth; span <<= 1) {
+        k_anc_jump<<<g, 256, 0, s>>>(a[cur], j[cur], nq, a[cur ^ 1], j[cur ^ 1]);
+        VJ_LAUNCH_CHECK();
+        r.launches++;
+        cur ^= 1;
+    }
+    return a[cur];
+}
 
 void join_setup(JoinRun& r) {
     vj_index* ix = r.ix;
@@ -1944,6 +2170,7 @@ void join_setup(JoinRun& r) {
     P.gbeam = ix->p.greedy_beam;
     // probe keys ahead of the traversal (merged index: every query probes N(q))
     P.pkeys = nullptr;
+    P.anc = nullptr;
     r.probe = false;
     if (!ix->separate && !ix->nnmap) {
         const int ng = 32 / r.jd.G;
@@ -1968,8 +2195,10 @@ void join_setup(JoinRun& r) {
             B.ring = ring;
             B.rowbytes = rowbytes;
             B.rowpitch = rowpitch;
+            B.bulk = ix->tune_bulk ? 1 : 0;
+            B.ctr = ix->ctr.p;
+            B.spin_limit = 1ll << 24;
             B.pkeys = ix->pkeys.p;
-            B.porder = ix->porder.n >= (size_t)nq ? ix->porder.p : nullptr;
             P.pkeys = ix->pkeys.p;
             r.probe = true;
         }
@@ -2268,8 +2497,10 @@ void vj_run_join(vj_index* ix, float eps, int budget, vj_stats* st, int64_t* nnz
             P.mode = 3;
             r.jd.launch(P, r.jd.blocks, s);
             VJ_CUDA(cudaEventRecord(ev.e[2], s));
+            P.anc = anc_compute(r, s);
             P.mode = 2;
             r.jd.launch(P, r.jd.blocks, s);
+            P.anc = nullptr;
             r.launches += 2;
         } else {
             P.mode = r.wait_first ? 4 : 0;
@@ -2369,6 +2600,7 @@ void vj_run_join_multi(vj_index* const* ixs, const float* eps, int n, vj_stats* 
                     for (int k = 0; k < nb; k++) {
                         JoinRun& r = runs[members[c0 + k]];
                         B.p[k].mode = r.soft ? soft_modes[ps] : (r.wait_first ? 4 : 0);
+                        B.p[k].anc = (r.soft && soft_modes[ps] == 2) ? anc_compute(r, s) : nullptr;
                         const int64_t qk = (r.soft || ps == 0) ? r.ix->nq : 0;
                         B.qstart[k + 1] = B.qstart[k] + qk;
                         if (ps > 0 && r.soft) r.launches++;

@@ -102,6 +102,13 @@ constexpr uint32_t WD_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(W
 // code 0), both K-major, M = 128, N = 256.  A k-block is then 128 E4M3
 // columns (the same 128-byte swizzle rows), four K = 32 steps.
 constexpr uint32_t WD_IDESC_F8 = (1u << 4) | ((uint32_t)(WD_BN >> 3) << 17) | ((uint32_t)(WD_BM >> 4) << 24);
+// kind::tf32 instruction descriptor: FP32 accumulate, TF32 A and B (format
+// code 2), both K-major, M = 128, N = 256; a k-block is 32 FP32 columns, four
+// K = 8 steps
+constexpr uint32_t WD_IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(WD_BN >> 3) << 17) |
+                                   ((uint32_t)(WD_BM >> 4) << 24);
+// operand kinds of the streamed kernel
+enum { KIND_BF16 = 0, KIND_E4M3 = 1, KIND_TF32 = 2 };
 
 struct WdParams {
     int64_t nrows, ncols;  // A rows, B rows
@@ -202,7 +209,7 @@ __device__ __forceinline__ void wd_append(const WdParams& P, const uint32_t (&va
     }
 }
 
-template <int EPI, int F8 = 0>
+template <int EPI, int KIND = KIND_BF16>
 __global__ void __launch_bounds__(WD_THREADS, 1)
     k_tc_wide(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, WdParams P) {
     extern __shared__ uint8_t wd_raw[];
@@ -251,8 +258,8 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                             break;
                         }
                         mbar_arrive_tx(&S.full[s], WD_A_BYTES + WD_B_BYTES);
-                        // x in elements of the map: 64 BF16 or 128 E4M3 bytes per K block
-                        const int kx = F8 ? kb * 128 : kb * TC_BK;
+                        // x in elements of the map: 64 BF16, 128 E4M3 or 32 FP32 per K block
+                        const int kx = kb * (KIND == KIND_E4M3 ? 128 : KIND == KIND_TF32 ? 32 : TC_BK);
                         tma_load_2d(S.A[s], &tA, &S.full[s], kx, rt * WD_BM);
                         tma_load_2d(S.B[s], &tB, &S.full[s], kx, ct * P.tstride * WD_BN);
                         issued |= 1u << s;
@@ -304,11 +311,14 @@ __global__ void __launch_bounds__(WD_THREADS, 1)
                         const int nkk = (kb == P.nkb - 1 && P.kk_last > 0) ? P.kk_last : TC_BK / 16;
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; kk++) {
-                            // advance 32 bytes along K (16 BF16 or 32 E4M3) inside the swizzled rows
+                            // advance 32 bytes along K (16 BF16, 32 E4M3 or 8 TF32) inside the swizzled rows
                             if (kk < nkk) {
-                                if constexpr (F8)
+                                if constexpr (KIND == KIND_E4M3)
                                     tc_mma_f8(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC_F8,
                                               (kb | kk) != 0);
+                                else if constexpr (KIND == KIND_TF32)
+                                    tc_mma_tf32(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC_TF32,
+                                                (kb | kk) != 0);
                                 else
                                     tc_mma(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), WD_IDESC,
                                            (kb | kk) != 0);
@@ -1145,15 +1155,24 @@ __global__ void k_tile_amax(const float* __restrict__ vec, const double* __restr
     if (lane == 0) atomicMax(amax, mb);
 }
 
+// TF32 value of x (round to nearest, ties away; the low 13 mantissa bits zero)
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 // Tile rows of the rows `rows` (node ids; nullptr = 0..n-1), kb elements each
 // (zero past d), warp per row:
-//   F8 = 0: out is BF16 rows already written (k_to_bf16); only the error is
-//           measured;
-//   F8 = 1: out receives E4M3 bytes of y * s, s a power of two: the row's own
-//           scale (amax == nullptr) or the shared one from *amax; rs[r] = 1 / s.
+//   KIND_BF16: out is BF16 rows already written (k_to_bf16); only the error
+//              is measured;
+//   KIND_E4M3: out receives E4M3 bytes of y * s, s a power of two: the row's
+//              own scale (amax == nullptr) or the shared one from *amax;
+//              rs[r] = 1 / s;
+//   KIND_TF32: out receives the TF32 values of y as FP32 words.
 // err[r] = |row^ - row| in FP64, rounded up; emax / nmax (optional) collect the
 // largest error and the largest |row| (float bits, atomicMax).
-template <int F8>
+template <int KIND>
 __global__ void k_tile_rows(const float* __restrict__ vec, const double* __restrict__ sqn64, int dp, int d,
                             int cosine, const int32_t* __restrict__ rows, int64_t n, int kb,
                             const unsigned int* __restrict__ amax, void* __restrict__ out, float* __restrict__ rs,
@@ -1166,7 +1185,7 @@ __global__ void k_tile_rows(const float* __restrict__ vec, const double* __restr
     const double nn = sqn64[src];
     const double inv = (cosine && nn > 0.0) ? 1.0 / sqrt(nn) : 1.0;
     float s = 1.f;
-    if constexpr (F8) {
+    if constexpr (KIND == KIND_E4M3) {
         float m;
         if (amax) {
             m = __uint_as_float(*amax);
@@ -1188,10 +1207,14 @@ __global__ void k_tile_rows(const float* __restrict__ vec, const double* __restr
         double ex = 0.0;
         if (k < d) tile_coord(v, k, cosine, inv, y, ex);
         double got;
-        if constexpr (F8) {
+        if constexpr (KIND == KIND_E4M3) {
             const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(y * s, __NV_SATFINITE, __NV_E4M3);
             reinterpret_cast<uint8_t*>(out)[r * (int64_t)kb + k] = q;
             got = (double)f8_value(q) / (double)s;
+        } else if constexpr (KIND == KIND_TF32) {
+            const float t = to_tf32(y);
+            reinterpret_cast<float*>(out)[r * (int64_t)kb + k] = t;
+            got = (double)t;
         } else {
             got = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(out)[r * (int64_t)kb + k]);
         }
@@ -1202,7 +1225,7 @@ __global__ void k_tile_rows(const float* __restrict__ vec, const double* __restr
     for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(VJ_FULL, e2, o);
     if (lane == 0) {
         const float e = __double2float_ru(sqrt(e2) * (1.0 + 1e-12));
-        if (F8 && rs) rs[r] = 1.f / s;
+        if (KIND == KIND_E4M3 && rs) rs[r] = 1.f / s;
         if (err) err[r] = e;
         if (emax) atomicMax(emax, __float_as_uint(e));
         if (nmax) atomicMax(nmax, __float_as_uint(__double2float_ru(cosine ? 1.0 : sqrt(nn))));
@@ -1337,6 +1360,46 @@ void vj_ensure_bf16(vj_index* ix) { ensure_data_bf16(ix); }
 // E4M3 row bytes: d rounded up to 32 columns (one K step), at least one 128-byte box
 static int f8_row_bytes(int d) { return d <= 128 ? 128 : (d + 31) / 32 * 32; }
 
+// TF32 rows of every node and the kNN sweeps' measured-bound columns (rows
+// wider than 128 columns whose coordinates are not BF16 values).  TF32 keeps
+// 11 significant bits: the bound is then far inside the spread of a row's
+// nearest keys, which the certificate of the kNN lists needs.
+static void ensure_knn_tf32(vj_index* ix) {
+    cudaStream_t s = ix->stream;
+    const int64_t n = ix->n;
+    const int kp32 = (ix->d + 31) / 32 * 32;
+    const int cosine = ix->metric != VJ_L2 ? 1 : 0;
+    ix->xtf.ensure((size_t)n * kp32, s);
+    ix->xerr_tf.ensure(n, s);
+    ix->kcs.ensure(n, s);
+    ix->kcb.ensure(n, s);
+    DBuf<unsigned int> q;
+    q.alloc(3, s);
+    VJ_CUDA(cudaMemsetAsync(q.p, 0, 3 * sizeof(unsigned int), s));
+    k_tile_rows<KIND_TF32><<<vj_div_up(n * 32, 256), 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine,
+                                                                  nullptr, n, kp32, nullptr, ix->xtf.p, nullptr,
+                                                                  ix->xerr_tf.p, q.p + 1, q.p + 2);
+    VJ_LAUNCH_CHECK();
+    // TF32 products are exact in FP32 (11 x 11 significant bits); the FP32
+    // sum of kp32 of them: 2 kp32 2^-24 of the sum of magnitudes
+    const double gamma = (double)(kp32 + 16) * 2.0 * (double)VJ_F32_U;
+    k_tile_cols<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn64.p, ix->xerr_tf.p, nullptr, n, cosine, 0, q.p, gamma,
+                                                   ix->kcs.p, ix->kcb.p);
+    VJ_LAUNCH_CHECK();
+    unsigned int h[3];
+    VJ_CUDA(cudaMemcpyAsync(h, q.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    VJ_CUDA(cudaStreamSynchronize(s));
+    q.free_(s);
+    float fd, fa;
+    memcpy(&fd, &h[1], 4);
+    memcpy(&fa, &h[2], 4);
+    const double Da = fd, A = fa;
+    // |tile key - key| for any pair: L2 2 (2 Da A + Da^2 + gamma (A + Da)^2); cosine (unit rows) the same with A = 1
+    const double beta = 2.0 * Da * A + Da * Da + gamma * (A + Da) * (A + Da);
+    ix->knn_beta = cosine ? beta : 2.0 * beta;
+    ix->knn_measured = true;
+}
+
 // Data side of the measured-bound scan (built once per index): the FP8 rows
 // with their scales and error norms, or the error norms of the BF16 rows.
 static void ensure_scan_data(vj_index* ix, bool f8) {
@@ -1350,7 +1413,7 @@ static void ensure_scan_data(vj_index* ix, bool f8) {
         ix->x8.ensure((size_t)ix->nx * kb8, s);
         ix->x8rs.ensure(ix->nx, s);
         ix->x8err.ensure(ix->nx, s);
-        k_tile_rows<1><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
+        k_tile_rows<KIND_E4M3><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
                                                   kb8, nullptr, ix->x8.p, ix->x8rs.p, ix->x8err.p, nullptr, nullptr);
         VJ_LAUNCH_CHECK();
     } else {
@@ -1358,7 +1421,7 @@ static void ensure_scan_data(vj_index* ix, bool f8) {
         const int kp = (ix->d + TC_BK - 1) / TC_BK * TC_BK;
         ix->xerr_bf.ensure(ix->nx, s);
         // the data rows are the first nx rows of the BF16 copy
-        k_tile_rows<0><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
+        k_tile_rows<KIND_BF16><<<warps_grid, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, cosine, nullptr, ix->nx,
                                                   kp, nullptr, ix->xbf.p, nullptr, ix->xerr_bf.p, nullptr, nullptr);
         VJ_LAUNCH_CHECK();
     }
@@ -1435,10 +1498,10 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         if (f8) {
             k_tile_amax<<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, qmax.p);
             VJ_LAUNCH_CHECK();
-            k_tile_rows<1><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kb8, qmax.p, a8.p,
+            k_tile_rows<KIND_E4M3><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kb8, qmax.p, a8.p,
                                               nullptr, nullptr, qmax.p + 1, qmax.p + 2);
         } else {
-            k_tile_rows<0><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kp, nullptr, abf.p,
+            k_tile_rows<KIND_BF16><<<wg, 256, 0, s>>>(ix->vec.p, ix->sqn64.p, ix->dp, ix->d, ci, arow, nr, kp, nullptr, abf.p,
                                               nullptr, nullptr, qmax.p + 1, qmax.p + 2);
         }
         VJ_LAUNCH_CHECK();
@@ -1548,9 +1611,9 @@ int64_t vj_tc_scan_candidates(vj_index* ix, const int32_t* qrows, int64_t nr, fl
         const size_t smem = wide_smem();
         const int grid = std::min(W.nunits, ix->num_sms);
         if (f8) {
-            VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN, KIND_E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-            launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN, 1><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
+            launch = [&, grid, smem]() { k_tc_wide<EPI_SCAN, KIND_E4M3><<<grid, WD_THREADS, smem, s>>>(ta, tb, W); };
         } else {
             VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
@@ -1823,7 +1886,13 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
             }
         });
     } else {
-        // streamed tiles: A and B are the BF16 copies of the block's rows and columns
+        // streamed tiles: A and B are the BF16 copies of the block's rows and
+        // columns, or their TF32 copies with the measured bound when the
+        // coordinates are not BF16 values
+        const bool tf32 = !ix->bf16_lossless;
+        const int kp32 = (ix->d + 31) / 32 * 32;
+        ix->knn_measured = false;
+        if (tf32) ensure_knn_tf32(ix);
         const size_t smem = wide_smem();
         struct WdBlk {
             CUtensorMap ta, tb;
@@ -1834,16 +1903,25 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         for (const Blk& b : blks) {
             if (b.nr <= 0) continue;
             WdBlk x;
-            x.ta = make_map(ix->xbf.p + (size_t)b.r0 * kpad, b.nr, kpad, WD_BM);
-            x.tb = make_map(ix->xbf.p + (size_t)b.c0 * kpad, b.nc, kpad, WD_BN);
             WdParams& W = x.W;
             W = WdParams{};
+            if (tf32) {
+                x.ta = make_map_f32(ix->xtf.p + (size_t)b.r0 * kp32, b.nr, kp32, WD_BM);
+                x.tb = make_map_f32(ix->xtf.p + (size_t)b.c0 * kp32, b.nc, kp32, WD_BN);
+                W.nkb = kp32 / 32;
+                W.kk_last = (ix->d + 7) / 8 - 4 * (W.nkb - 1);
+                W.cs = ix->kcs.p + b.c0;
+                W.cb = ix->kcb.p + b.c0;
+            } else {
+                x.ta = make_map(ix->xbf.p + (size_t)b.r0 * kpad, b.nr, kpad, WD_BM);
+                x.tb = make_map(ix->xbf.p + (size_t)b.c0 * kpad, b.nc, kpad, WD_BN);
+                W.nkb = kpad / TC_BK;
+                W.cs = ix->wcs.p + b.c0;
+                W.cb = ix->wcb.p + b.c0;
+            }
             W.nrows = b.nr;
             W.ncols = b.nc;
-            W.nkb = kpad / TC_BK;
             W.nrt = (int)vj_div_up(b.nr, WD_BM);
-            W.cs = ix->wcs.p + b.c0;
-            W.cb = ix->wcb.p + b.c0;
             W.err = err.p;
             W.spin_limit = spin_limit;
             W.row_base = b.r0;
@@ -1853,6 +1931,8 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
         }
         // 1. sample sweep: one unit per 128-row tile over every KNN_SAMPLE-th tile
         VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SAMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SAMPLE, KIND_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
         for (WdBlk& x : wb) {
             WdParams W = x.W;
             W.tstride = KNN_SAMPLE;
@@ -1860,7 +1940,9 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
             W.tpu = W.nct;
             W.nunits = W.nrt;
             W.top16 = top.p + W.row_base;
-            k_tc_wide<EPI_SAMPLE><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+            const int grid = std::min(W.nunits, ix->num_sms);
+            if (tf32) k_tc_wide<EPI_SAMPLE, KIND_TF32><<<grid, WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+            else k_tc_wide<EPI_SAMPLE><<<grid, WD_THREADS, smem, s>>>(x.ta, x.tb, W);
             VJ_LAUNCH_CHECK();
         }
         k_knn_thr<<<vj_div_up(n, 256), 256, 0, s>>>(top.p, n, thr.p);
@@ -1903,6 +1985,8 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
             }
         }
         VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VJ_CUDA(cudaFuncSetAttribute(k_tc_wide<EPI_SCAN, KIND_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
         sweep([&](int32_t* pq, int32_t* px, float* pw, int64_t c) {
             for (WdBlk& x : wb) {
                 WdParams W = x.W;
@@ -1910,9 +1994,12 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
                 W.cx = px;
                 W.cw = pw;
                 W.cap = c;
-                k_tc_wide<EPI_SCAN><<<std::min(W.nunits, ix->num_sms), WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+                const int grid = std::min(W.nunits, ix->num_sms);
+                if (tf32) k_tc_wide<EPI_SCAN, KIND_TF32><<<grid, WD_THREADS, smem, s>>>(x.ta, x.tb, W);
+                else k_tc_wide<EPI_SCAN><<<grid, WD_THREADS, smem, s>>>(x.ta, x.tb, W);
             }
         });
+        ix->xtf.free_(s);  // the TF32 rows serve the two sweeps only
     }
     const int64_t nc = (int64_t)hn;
 
@@ -1934,8 +2021,15 @@ bool vj_tc_knn_candidates(vj_index* ix, DBuf<int64_t>& off, DBuf<int32_t>& ids, 
                                                           ids.p, with_w ? cw_out->p : nullptr);
     VJ_LAUNCH_CHECK();
     row_thr.ensure(n, s);
-    k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, ix->invn.p, thr.p, n, ix->metric, ix->cos_raw ? 1 : 0,
-                                                  kpad, ix->tc_cb, ix->tc_c3, ix->tc_cbmax, ix->maxnorm, row_thr.p);
+    // measured bound: a node left out has v = 2<a^,b^> - |b|^2 + 2 beta_b <= thr (L2), so its
+    // key is at least |a|^2 - thr (cosine: 1 - thr); the BF16 form carries its bound constants
+    if (ix->knn_measured)
+        k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, ix->invn.p, thr.p, n, ix->metric, 0, kpad, 0.f, 0.f,
+                                                      0.f, ix->maxnorm, row_thr.p);
+    else
+        k_knn_bound<<<vj_div_up(n, 256), 256, 0, s>>>(ix->sqn.p, ix->invn.p, thr.p, n, ix->metric,
+                                                      ix->cos_raw ? 1 : 0, kpad, ix->tc_cb, ix->tc_c3, ix->tc_cbmax,
+                                                      ix->maxnorm, row_thr.p);
     VJ_LAUNCH_CHECK();
     if (wide) {
         // build-sized lists (hundreds of candidates per node) are not kept for later scans

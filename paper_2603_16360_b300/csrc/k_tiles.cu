@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(KC_WPB * 32)
                      const float* __restrict__ row_thr, int32_t* __restrict__ out_id, float* __restrict__ out_key,
                      int32_t* __restrict__ bad_rows, int* __restrict__ nbad, unsigned long long* __restrict__ nrechk,
                      const float* __restrict__ cw, const float* __restrict__ sqn, int raw, float cb, float c3,
-                     float maxnorm, const double* __restrict__ sqn64) {
+                     float maxnorm, const double* __restrict__ sqn64, double beta_abs) {
     extern __shared__ uint8_t kc_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     KcSmem& S = reinterpret_cast<KcSmem*>(kc_raw)[warp];
@@ -562,9 +562,10 @@ __global__ void __launch_bounds__(KC_WPB * 32)
         pref = true;
         bitonic_pairs(S.key, S.id, P2, lane);
         const double mx = (double)maxnorm;
-        const double beta = metric == 0
-                                ? (double)cb * sqrt((double)rn2) * mx + ((double)c3 + 4.0 * VJ_F32_U) * ((double)rn2 + mx * mx)
-                                : (double)cb + 4.0 * VJ_F32_U;
+        // beta_abs: the measured bound's |tile key - key| (TF32 tiles), 0 for the BF16 form
+        const double beta = beta_abs + (metric == 0 ? (double)cb * sqrt((double)rn2) * mx +
+                                                          ((double)c3 + 4.0 * VJ_F32_U) * ((double)rn2 + mx * mx)
+                                                    : (double)cb + 4.0 * VJ_F32_U);
         // the true K-th key is at most k~_K + beta, and the certificate below
         // needs its FP32 key with margin (at most (k~_K + beta)(1 + tol) + tol
         // before rounding slack) under every dropped candidate's lower bound
@@ -903,8 +904,9 @@ void vj_build_knn(vj_index* ix) {
                 VJ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
                 kern<<<vj_div_up(n, KC_WPB), KC_WPB * 32, smem, s>>>(
                     ix->vec.p, ix->invn.p, ix->dp, ix->d, n, ix->metric, K, coff.p, cids.p, cthr.p, ix->knn.p,
-                    ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->cos_raw ? 1 : 0, ix->tc_cb, ix->tc_c3,
-                    (float)(ix->maxnorm * 1.0001), ix->sqn64.p);
+                    ix->knnd.p, bad.p, nbad.p, nr.p, w, ix->sqn.p, ix->knn_measured ? 0 : (ix->cos_raw ? 1 : 0),
+                    ix->knn_measured ? 0.f : ix->tc_cb, ix->knn_measured ? 0.f : ix->tc_c3,
+                    (float)(ix->maxnorm * 1.0001), ix->sqn64.p, ix->knn_measured ? ix->knn_beta : 0.0);
             };
             VJ_DISPATCH_GN(dp4, {
                 if (dp4 > 128) launch(k_knn_rerank_csr<G, NPL, 4>);

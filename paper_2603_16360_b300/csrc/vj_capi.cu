@@ -95,7 +95,6 @@ static void free_index(vj_index* ix) {
     ix->parent.free_(s);
     ix->order.free_(s);
     ix->depth.free_(s);
-    ix->porder.free_(s);
     ix->qstat.free_(s);
     ix->qdn.free_(s);
     ix->feat.free_(s);
@@ -111,6 +110,12 @@ static void free_index(vj_index* ix) {
     ix->x8.free_(s);
     ix->x8rs.free_(s);
     ix->x8err.free_(s);
+    ix->xtf.free_(s);
+    ix->anc.free_(s);
+    ix->jmp.free_(s);
+    ix->xerr_tf.free_(s);
+    ix->kcs.free_(s);
+    ix->kcb.free_(s);
     ix->pkeys.free_(s);
     ix->nm_w.free_(s);
     ix->nm_wd.free_(s);
@@ -289,12 +294,14 @@ static int class_pos(int cls) {
     return -1;
 }
 
-extern "C" vj_status vj_set_tuning(vj_index* ix, int lanes, int slots, int inflight, int blocks, int probe_ring) {
+extern "C" vj_status vj_set_tuning(vj_index* ix, int lanes, int slots, int inflight, int blocks, int probe_ring,
+                                   int probe_bulk) {
     return guarded([&] {
         VJ_REQUIRE(ix != nullptr, VJ_ERR_ARG, "index is NULL");
         VJ_REQUIRE(blocks >= 0, VJ_ERR_ARG, "blocks must be >= 0");
         VJ_REQUIRE(probe_ring == 0 || (probe_ring >= 2 && probe_ring <= 8), VJ_ERR_ARG,
                    "probe_ring must be 0 or 2..8");
+        VJ_REQUIRE(probe_bulk == 0 || probe_bulk == 1, VJ_ERR_ARG, "probe_bulk must be 0 or 1");
         int cls = -1;
         if (lanes != 0) {
             for (int k = 0; k < vj_join_class_count() && cls < 0; k++) {
@@ -312,6 +319,7 @@ extern "C" vj_status vj_set_tuning(vj_index* ix, int lanes, int slots, int infli
         ix->tune_cls = cls;
         ix->tune_blocks = blocks;
         ix->tune_ring = probe_ring;
+        ix->tune_bulk = probe_bulk;
     });
 }
 
@@ -321,7 +329,8 @@ extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_repo
         vj_set_error("index is NULL");
         return VJ_ERR_ARG;
     }
-    const int saved_cls = ix->tune_cls, saved_blocks = ix->tune_blocks, saved_ring = ix->tune_ring;
+    const int saved_cls = ix->tune_cls, saved_blocks = ix->tune_blocks, saved_ring = ix->tune_ring,
+              saved_bulk = ix->tune_bulk;
     const vj_status st = guarded([&] {
         VJ_REQUIRE(rep != nullptr, VJ_ERR_ARG, "report is NULL");
         VJ_REQUIRE(eps > 0.f && eps == eps, VJ_ERR_ARG, "eps must be > 0");
@@ -330,19 +339,20 @@ extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_repo
         const int k0 = class_pos(vj_join_default_class(dp4));
         const bool probe = !ix->separate && !ix->nnmap;
         struct Setting {
-            int cls, blocks, ring;
+            int cls, blocks, ring, bulk;
         };
         std::vector<Setting> set;
         for (int k = k0; k < vj_join_class_count() && k < k0 + 3; k++) {
             int c, G, NPL, U;
             vj_join_class_info(k, &c, &G, &NPL, &U);
             const int mb = vj_join_max_blocks(c, ix->num_sms);
-            set.push_back({c, mb, 0});
-            if (mb / 2 >= ix->num_sms) set.push_back({c, mb / 2, 0});
+            set.push_back({c, mb, 0, 0});
+            if (mb / 2 >= ix->num_sms) set.push_back({c, mb / 2, 0, 0});
         }
         if (probe) {
-            set.push_back({set[0].cls, set[0].blocks, 4});
-            set.push_back({set[0].cls, set[0].blocks, 2});
+            set.push_back({set[0].cls, set[0].blocks, 4, 0});
+            set.push_back({set[0].cls, set[0].blocks, 2, 0});
+            set.push_back({set[0].cls, set[0].blocks, 0, 1});
         }
         int64_t nnz0 = -1, dc0 = -1;
         double best = 1e300;
@@ -350,6 +360,7 @@ extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_repo
             ix->tune_cls = set[i].cls;
             ix->tune_blocks = set[i].blocks;
             ix->tune_ring = set[i].ring;
+            ix->tune_bulk = set[i].bulk;
             std::vector<double> ms;
             int64_t nnz = 0;
             vj_stats s{};
@@ -367,6 +378,7 @@ extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_repo
             rep->inflight[n] = U;
             rep->blocks[n] = set[i].blocks;
             rep->probe_ring[n] = probe ? (set[i].ring ? set[i].ring : 8) : 0;
+            rep->probe_bulk[n] = probe ? set[i].bulk : 0;
             rep->ms[n] = ms[ms.size() / 2];
             if (i == 0) {
                 nnz0 = nnz;
@@ -382,11 +394,13 @@ extern "C" vj_status vj_autotune(vj_index* ix, float eps, int reps, vj_tune_repo
         ix->tune_cls = ch.cls;
         ix->tune_blocks = ch.blocks;
         ix->tune_ring = ch.ring;
+        ix->tune_bulk = ch.bulk;
     });
     if (st != VJ_OK) {
         ix->tune_cls = saved_cls;
         ix->tune_blocks = saved_blocks;
         ix->tune_ring = saved_ring;
+        ix->tune_bulk = saved_bulk;
     }
     return st;
 }

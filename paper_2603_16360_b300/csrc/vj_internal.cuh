@@ -119,7 +119,6 @@ struct vj_index {
     DBuf<int32_t> parent; // [nq]
     DBuf<int32_t> order;  // [nq]
     DBuf<int32_t> depth;  // [nq]
-    DBuf<int32_t> porder; // [nq] probe dispatch order (MST preorder), empty without an MST
     int max_depth = 0;
     DBuf<__nv_bfloat16> xbf;   // [n][kp] BF16 copy of every node, data rows first (tensor-core tiles)
     DBuf<__nv_bfloat16> xbias; // [n][16] L2: three-term BF16 split of each node's scan bias
@@ -153,6 +152,14 @@ struct vj_index {
     DBuf<uint8_t> x8;          // [nx][kb8] E4M3
     DBuf<float> x8rs, x8err;   // [nx]
     int kb8 = 0;
+    // kNN build of rows wider than 128 columns whose coordinates are not BF16
+    // values: TF32 tiles ([n][kp32] FP32 words holding TF32 values, freed after
+    // the sweeps) under the measured bound: per node the rounding error norm
+    // and the epilogue's column scale and bias; knn_beta bounds |tile key -
+    // key| for the re-rank's prefilter
+    DBuf<float> xtf, xerr_tf, kcs, kcb;
+    bool knn_measured = false;
+    double knn_beta = 0.0;
     // NN-Map index (the paper's closing design): kNN lists over data columns
     // only, the graph G_X over data rows only, and per query its witness
     // (nearest data vector), the witness's FP64 distance and the OOD bit
@@ -169,9 +176,9 @@ struct vj_index {
     DBuf<double> nm_wd;        // [nq] its distance (FP64)
     DBuf<uint8_t> nm_ood;      // [nq] OOD bit
     // traversal setting chosen by vj_autotune / vj_set_tuning: join class
-    // (-1: the smallest that holds the row), persistent blocks and probe ring
-    // stages (0: the defaults)
-    int tune_cls = -1, tune_blocks = 0, tune_ring = 0;
+    // (-1: the smallest that holds the row), persistent blocks, probe ring
+    // stages (0: the defaults) and the probe's copy (1: one bulk copy per row)
+    int tune_cls = -1, tune_blocks = 0, tune_ring = 0, tune_bulk = 0;
     long long wait_polls = 0;  // dependency-wait limit of the traversal (0: the default)
     int hold_q = -1;           // test knob: a query that never publishes its cache (-1: none)
     double maxnorm = 0.0;      // largest vector norm (FP64)
@@ -191,6 +198,8 @@ struct vj_index {
     DBuf<int32_t> cache2, steps2, count2;  // [nq] soft sharing: staged pass-2 re-runs
     DBuf<uint8_t> hyb2;
     DBuf<int64_t> seg2;
+    DBuf<uint8_t> anc;        // [2][nq] soft sharing: ancestor-changed flags (pointer jumping)
+    DBuf<int32_t> jmp;        // [2][nq] ... and the jump links
     DBuf<int32_t> order1;     // [nq] longest-first dispatch order (from the last join's visits)
     DBuf<int> cost_hist;
     bool have_costs = false;

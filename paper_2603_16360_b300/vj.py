@@ -49,7 +49,8 @@ VJ_TUNE_MAX = 16
 class vj_tune_report(C.Structure):
     _fields_ = [("n", C.c_int), ("lanes", C.c_int * VJ_TUNE_MAX), ("slots", C.c_int * VJ_TUNE_MAX),
                 ("inflight", C.c_int * VJ_TUNE_MAX), ("blocks", C.c_int * VJ_TUNE_MAX),
-                ("probe_ring", C.c_int * VJ_TUNE_MAX), ("ms", C.c_double * VJ_TUNE_MAX),
+                ("probe_ring", C.c_int * VJ_TUNE_MAX), ("probe_bulk", C.c_int * VJ_TUNE_MAX),
+                ("ms", C.c_double * VJ_TUNE_MAX),
                 ("valid", C.c_int * VJ_TUNE_MAX), ("chosen", C.c_int)]
 
 
@@ -171,7 +172,7 @@ def load():
     lib.vj_set_wait_test.restype = I
     lib.vj_autotune.argtypes = [P, C.c_float, I, C.POINTER(vj_tune_report)]
     lib.vj_autotune.restype = I
-    lib.vj_set_tuning.argtypes = [P, I, I, I, I, I]
+    lib.vj_set_tuning.argtypes = [P, I, I, I, I, I, I]
     lib.vj_set_tuning.restype = I
     lib.vj_last_error.argtypes = []
     lib.vj_last_error.restype = C.c_char_p
@@ -505,14 +506,16 @@ def vj_autotune(ix: Index, eps: float, reps: int = 2) -> dict:
     rep = vj_tune_report()
     _check(load().vj_autotune(ix.handle, float(eps), int(reps), C.byref(rep)))
     rows = [{"lanes": rep.lanes[i], "slots": rep.slots[i], "inflight": rep.inflight[i], "blocks": rep.blocks[i],
-             "probe_ring": rep.probe_ring[i], "ms": rep.ms[i], "valid": bool(rep.valid[i])} for i in range(rep.n)]
+             "probe_ring": rep.probe_ring[i], "probe_bulk": rep.probe_bulk[i], "ms": rep.ms[i],
+             "valid": bool(rep.valid[i])} for i in range(rep.n)]
     return {"settings": rows, "chosen": rep.chosen}
 
 
 def vj_set_tuning(ix: Index, lanes: int = 0, slots: int = 0, inflight: int = 0, blocks: int = 0,
-                  probe_ring: int = 0):
+                  probe_ring: int = 0, probe_bulk: int = 0):
     """Set the traversal setting (0 = default for each field)."""
-    _check(load().vj_set_tuning(ix.handle, int(lanes), int(slots), int(inflight), int(blocks), int(probe_ring)))
+    _check(load().vj_set_tuning(ix.handle, int(lanes), int(slots), int(inflight), int(blocks), int(probe_ring),
+                                int(probe_bulk)))
 
 
 def vj_set_plan(ix: Index, route=None, beam=None):

@@ -1,7 +1,8 @@
 """Traversal tuning: every setting the tuner may choose computes the same join.
 
 A setting is the gather layout of the traversal (lanes per row, 16-byte
-slots per lane, rows in flight), the persistent grid and the probe ring.
+slots per lane, rows in flight), the persistent grid, the probe ring and the
+probe's copy (16-byte copies per lane, or one bulk copy per row).
 In-range decisions near eps are re-decided in FP64 and cache ties too, so
 the pairs, visited counts and soft caches equal the default setting's and
 the oracle's; a pair's FP32 distance may differ in its last bits (the
@@ -67,7 +68,8 @@ def test_autotune_keeps_the_join(case, oracle):
         _same_join(base, tuned)
         # every class the tuner tried, set explicitly, gives the same join
         for r in rows:
-            vj.vj_set_tuning(ix, r["lanes"], r["slots"], r["inflight"], r["blocks"], r["probe_ring"])
+            vj.vj_set_tuning(ix, r["lanes"], r["slots"], r["inflight"], r["blocks"], r["probe_ring"],
+                             r["probe_bulk"])
             _same_join(base, vj.vj_join(ix, eps))
         # and the join equals the oracle's on the same graph
         adj, entry, parent, order, _ = vj.vj_export_graph(ix)
@@ -87,7 +89,7 @@ def test_tuning_applies_to_batched_joins():
     try:
         eps = [_eps(w, 8) for w in ws]
         for ix in ixs:
-            vj.vj_set_tuning(ix, 16, 4, 2, 0, 4)  # a larger class than the default for d = 100
+            vj.vj_set_tuning(ix, 16, 4, 2, 0, 4, 1)  # a larger class than the default for d = 100, bulk probe
         batch = vj.vj_join_batch(ixs, eps)
         for ix, e, b in zip(ixs, eps, batch):
             _same_join(vj.vj_join(ix, e), b)
@@ -103,7 +105,8 @@ def test_tuning_arguments_are_checked():
         for bad in [(8, 4, 2, 0, 0),    # 128 floats per row: too small for d = 300
                     (8, 3, 2, 0, 0),    # no such class
                     (0, 0, 0, -1, 0),   # negative grid
-                    (0, 0, 0, 0, 1)]:   # probe ring below 2
+                    (0, 0, 0, 0, 1),    # probe ring below 2
+                    (0, 0, 0, 0, 0, 2)]:  # probe_bulk not 0/1
             with pytest.raises(vj.VjError) as e:
                 vj.vj_set_tuning(ix, *bad)
             assert e.value.status == vj.VJ_ERR_ARG
