@@ -956,7 +956,9 @@ def main():
     dominant = max(rooflines, key=lambda k: k["ms_per_launch"])
     n_all = w.nx + w.nq
     kp = (w.d + 63) // 64 * 64
-    knn_flops = 2.0 * n_all * n_all * kp * (1.0 + 1.0 / 16)
+    # the kNN sweeps' tensor work: the sample sweep over every 16th tile, then the threshold sweep,
+    # which for rows wider than 128 columns computes each unordered pair once (symmetric tiles)
+    knn_flops = 2.0 * n_all * n_all * kp / 16 + (1.0 if kp > 128 else 2.0) * n_all * n_all * kp
     exact_flops = 2.0 * w.nq * w.nx * w.d
 
     # ---- end to end through the public call with a host result
