@@ -1115,9 +1115,11 @@ __global__ void k_key_from_w(const float* __restrict__ sqn, const int32_t* __res
 // input row (L2) or the exact unit vector a / |a| (cosine).
 constexpr float F8_MAX = 448.f;  // largest finite E4M3 value
 
-// largest power of two s with amax * s <= 448 (1 for a zero row)
+// largest power of two s with amax * s <= 448 (1 for a zero or vanishingly
+// small row, whose 448 / amax would overflow; its rounding error is then
+// measured like any other)
 __device__ __forceinline__ float f8_scale(float amax) {
-    if (!(amax > 0.f)) return 1.f;
+    if (!(amax > 1e-30f)) return 1.f;
     int e;
     frexpf(F8_MAX / amax, &e);  // 448 / amax = m 2^e, m in [0.5, 1)
     return ldexpf(1.f, e - 1);
