@@ -178,7 +178,7 @@ extern "C" vj_status vj_build(const float* X, int64_t nx, const float* Q, int64_
         if (p.knn_k <= 0) p.knn_k = 2 * p.degree;
         VJ_REQUIRE(p.knn_k >= p.degree && p.knn_k <= 112, VJ_ERR_ARG, "knn_k must be in [degree, 112]");
         VJ_REQUIRE(p.precision == VJ_PREC_FP32 || p.precision == VJ_PREC_BF16, VJ_ERR_ARG,
-                   "build tiles: FP32 or BF16 (FP8 is not implemented)");
+                   "build tiles: FP32 or BF16 (FP8 tiles serve the scan only: vj_params.scan)");
         VJ_REQUIRE(p.nnmap == 0 || p.nnmap == 1, VJ_ERR_ARG, "nnmap must be 0 or 1");
         VJ_REQUIRE(p.separate == 0 || p.separate == 1, VJ_ERR_ARG, "separate must be 0 or 1");
         VJ_REQUIRE(!(p.nnmap && p.separate), VJ_ERR_ARG, "nnmap and separate are exclusive");
