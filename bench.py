@@ -23,6 +23,10 @@ evaluated queries (the held-out rows are joined in every step too).
                  the library on the held-out queries (vj_train_predictor), and
                  BF16 gathers (exact here: every coordinate is a BF16 value).
 
+Before its timed steps each arm runs vj_autotune (untimed setup, like the
+training): the traversal setting it keeps gives the same join, only faster.
+--no-tune times both arms with the default setting.
+
 Prints one JSON line.  --impl reference times the CPU oracle's join (FP64,
 one thread) on whole MST subtrees of the same workload instead.
 """
