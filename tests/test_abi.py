@@ -105,3 +105,23 @@ def test_sources_name_no_build_notes_or_machine_paths():
         txt = open(f, errors="replace").read()
         for b in banned:
             assert b not in txt, (f, b)
+
+
+def test_tuning_and_scan_precision_arguments():
+    """The tuner's entry points reject a NULL index before any device work;
+    the scan precision defaults to BF16 tiles, and FP8 is a scan-only choice
+    (the build's tiles reject it)."""
+    lib = vj.load()
+    rep = vj.vj_tune_report()
+    assert lib.vj_autotune(None, 1.0, 1, C.byref(rep)) == vj.VJ_ERR_ARG
+    assert rep.n == 0
+    assert lib.vj_set_tuning(None, 0, 0, 0, 0, 0, 0) == vj.VJ_ERR_ARG
+    p = vj.default_params()
+    assert p.scan == vj.VJ_PREC_BF16 and p.precision == vj.VJ_PREC_BF16 and p.gather == vj.VJ_PREC_FP32
+    import numpy as np
+    X = np.zeros((4, 3), np.float32)
+    h = C.c_void_p()
+    bad = vj.default_params(precision=vj.VJ_PREC_FP8)
+    assert lib.vj_build(X.ctypes.data, 4, X.ctypes.data, 4, 3, 0, C.byref(bad), C.byref(h)) == vj.VJ_ERR_ARG
+    assert b"scan" in lib.vj_last_error()
+    assert h.value is None
